@@ -1,0 +1,374 @@
+"""Benchmark: pose energies/s and BPMFs/s of the FFT-correlation BPMF hot path.
+
+Workload (one step): 96^3 receptor grids at 0.25 A (2600 atoms, 5-20 A shell,
+40^3 site box), 4 receptor conformations, one 30-atom ligand with 2000 rigid
+configurations.  A step is the whole hot path through the C ABI: receptor
+spectra for the 4 conformations, the ligand batch (placement bounds, generalised
+charges), and bpmf_eval (spreading, forward FFT, spectral product-sum, inverse
+FFT fused with the site mask and log-sum-exp, FP64 merge).  Inputs are resident
+in HBM when the timed region starts; the L2 is flushed between timed steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pose energies/s & BPMFs/s, chosen form vs plain FP32 path at 0.01 kcal/mol"
+WORKLOAD = "protein-scale: 96^3 grid h=0.25 A, 4 receptor conformations, 30-atom ligand, 2000 configurations, 40^3 site box"
+N_CONF, N_REC, N_ATOMS = 2000, 4, 30
+FP32_LANES_PER_SM, N_SM = 128, 152
+# FP32 instructions per float-pair flop for the add/mul mix of the radix
+# stages (add: TwoSum 6 + 2 + FastTwoSum 3 = 11; mul: 1 + 3 FMA + 3 = 7; ~70 % adds)
+FF_INSTR_PER_FLOP = 9.8
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(rank):
+    # the same receptors on every rank; each rank its own ligand (weak scaling)
+    return synth.protein_scale(n_conf=N_CONF, n_rec=N_REC, seed=1001 + 0, n_atoms_lig=N_ATOMS) if rank == 0 else \
+        _rank_workload(rank)
+
+
+def _rank_workload(rank):
+    w = synth.protein_scale(n_conf=N_CONF, n_rec=N_REC, seed=1001, n_atoms_lig=N_ATOMS)
+    lig = synth.LigandInput(synth.ligand_params(5000 + rank, N_ATOMS), synth.ligand_configs(6000 + rank, N_ATOMS, N_CONF))
+    w.ligands = [lig]
+    return w
+
+
+def oracle_sample(w, n_sample):
+    import oracle
+    lig = w.ligands[0]
+    t = time.perf_counter()
+    ref = oracle.evaluate(w.receptors, lig.coords[:n_sample], lig.params.q, lig.params.eps, lig.params.R, w.kT)
+    dt = time.perf_counter() - t
+    return ref, dt
+
+
+def omp_cores():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    w = synth.protein_scale(n_conf=N_CONF, n_rec=N_REC, seed=1001, n_atoms_lig=N_ATOMS)
+    n_sample = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_sample(w, max(1, n_sample // 4))
+    times, poses = [], 0
+    for _ in range(args.steps):
+        ref, dt = oracle_sample(w, n_sample)
+        times.append(dt)
+        poses = int(ref["n_valid"].sum())
+    t = float(np.mean(times))
+    val = poses / t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "pose energies/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"first {n_sample} of {N_CONF} configurations x {N_REC} receptors per step",
+                       "l2": "n/a (CPU)"},
+            "bpmfs_per_s": N_REC * (n_sample / N_CONF) / t,
+            "cpu_baseline": {"value": val, "unit": "pose energies/s", "cores": omp_cores(), "kind": "oracle",
+                             "sample": f"{n_sample} configurations x {N_REC} receptors, all valid translations"},
+            "e2e": {"value": val, "unit": "pose energies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def alg_work(w, n_valid, mode):
+    """Algorithmic FLOPs (5 P log2 P per complex line transform, 8 per complex
+    multiply-add) and bytes per kernel for the whole step."""
+    P = 96
+    F2 = P // 2 + 1
+    Q = P * F2
+    S = 40
+    K = N_REC
+    J = N_CONF
+    lg = np.log2(P)
+    cfft = 5 * P * lg
+    E = 16 if mode == "ff" else 8
+    u = []
+    lig = w.ligands[0]
+    for j in range(J):
+        ext = (lig.coords[j].max(0) - lig.coords[j].min(0)).astype(np.float32)
+        u.append(np.minimum(np.ceil((ext / np.float32(0.25)).astype(np.float32)).astype(int) + 4, P))
+    u = np.array(u)
+    work = {}
+    # x-pass: forward of 3 channels, then per receptor product + inverse, per (y, zf) column
+    work["k_xfused"] = {"flops": J * Q * (3 * cfft + K * (cfft + 3 * 8 * P)),
+                        "bytes": float(np.sum(3 * u[:, 0] * Q * E) + J * K * 3 * P * Q * E / 2 * (2 if mode == "ff" else 1)
+                                       + J * K * S * Q * E)}
+    work["k_axis(y inv)"] = {"flops": J * K * S * F2 * cfft, "bytes": J * K * S * (Q + S * F2) * E}
+    work["k_zinv"] = {"flops": J * K * S * (S / 2) * cfft, "bytes": J * K * S * S * F2 * E}
+    return work
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_1708_07045_gb300 as pkg
+    from paper_1708_07045_gb300.session import Session
+    pkg.lib()
+
+    w = make_workload(rank)
+    lig = w.ligands[0]
+    dev = torch.device("cuda", local)
+    grids = [torch.from_numpy(r.grids).to(dev) for r in w.receptors]
+    coords = torch.from_numpy(np.ascontiguousarray(lig.coords.reshape(-1, 3))).to(dev)
+    params = [torch.from_numpy(getattr(lig.params, k)).to(dev) for k in ("q", "eps", "R")]
+    K, J = N_REC, N_CONF
+    outs = {"logZ": torch.empty((J, K), dtype=torch.float64, device=dev),
+            "n_valid": torch.empty((J, K), dtype=torch.int64, device=dev),
+            "bpmf": torch.empty((1, K), dtype=torch.float64, device=dev),
+            "dG": torch.empty(1, dtype=torch.float64, device=dev)}
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sess = Session(local)
+
+    def step(mode_id, host=False):
+        """One pass of the hot path; returns nothing (outputs in `outs` or host arrays)."""
+        recs = []
+        try:
+            for k, r in enumerate(w.receptors):
+                recs.append(pkg.bpmf_receptor_load(sess.ctx, host_grids[k] if host else grids[k], r.h, r.origin,
+                                                   r.site_lo, r.site_n, stream))
+            if host:
+                lh = pkg.bpmf_ligand_batch(sess.ctx, [N_ATOMS], [J], host_coords, *host_params, stream=stream)
+                o = host_outs
+            else:
+                lh = pkg.bpmf_ligand_batch(sess.ctx, [N_ATOMS], [J], coords, *params, stream=stream)
+                o = outs
+            pkg.bpmf_eval(sess.ctx, lh, recs, w.kT, mode_id, o["logZ"], o["n_valid"], o["bpmf"], o["dG"], stream)
+            pkg.bpmf_ligand_free(lh)
+        finally:
+            for r in recs:
+                pkg.bpmf_receptor_free(r)
+
+    def timed(mode_id, steps, warmup, prof=False):
+        for _ in range(warmup):
+            step(mode_id)
+        torch.cuda.synchronize()
+        if prof:
+            pkg.bpmf_profile_enable(sess.ctx, True)
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)  # evict the L2 between timed steps (untimed)
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(mode_id)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        prof_out = pkg.bpmf_profile(sess.ctx) if prof else None
+        if prof:
+            pkg.bpmf_profile_enable(sess.ctx, False)
+        t = float(np.mean(ts))
+        if dist is not None:
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t, ts, prof_out
+
+    modes = {"ff": pkg.BPMF_MODE_FF, "fp32": pkg.BPMF_MODE_FP32}
+    chosen = args.mode
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_ms, ts, prof = timed(modes[chosen], args.steps, args.warmup, prof=True)
+    clk = clocks.stop()
+    res_chosen = {k: v.cpu().numpy() for k, v in outs.items()}
+    other = "fp32" if chosen == "ff" else "ff"
+    t_other, _, _ = timed(modes[other], max(1, args.steps // 2), 1)
+    res_other = {k: v.cpu().numpy() for k, v in outs.items()}
+
+    n_poses = int(res_chosen["n_valid"].sum())
+    value = n_poses * world / (t_ms / 1e3)
+    bpmfs = K * world / (t_ms / 1e3)
+
+    # end to end: host (pinned) inputs and host outputs through the same C ABI
+    host_grids = [torch.from_numpy(r.grids).pin_memory() for r in w.receptors]
+    host_coords = torch.from_numpy(np.ascontiguousarray(lig.coords.reshape(-1, 3))).pin_memory()
+    host_params = [torch.from_numpy(getattr(lig.params, k)).pin_memory() for k in ("q", "eps", "R")]
+    host_outs = {"logZ": np.empty((J, K)), "n_valid": np.empty((J, K), dtype=np.int64), "bpmf": np.empty((1, K)),
+                 "dG": np.empty(1)}
+    step(modes[chosen], host=True)
+    e2e_ts = []
+    for _ in range(max(2, args.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(modes[chosen], host=True)
+        torch.cuda.synchronize()
+        e2e_ts.append(time.perf_counter() - t0)
+    e2e_t = float(np.mean(e2e_ts))
+    h2d = sum(g.numel() * 4 for g in host_grids) + host_coords.numel() * 4 + sum(p.numel() * 4 for p in host_params)
+    d2h = sum(v.nbytes for v in host_outs.values())
+
+    line = None
+    if rank == 0:
+        # accuracy and CPU baseline on a bounded oracle sample
+        cpu = None
+        acc = {}
+        if not args.no_cpu_baseline:
+            ref, dt = oracle_sample(w, args.ref_sample)
+            okz = np.isfinite(ref["logZ"])
+            ns = args.ref_sample
+            for name, res in ((chosen, res_chosen), (other, res_other)):
+                dz = np.abs(res["logZ"][:ns][okz] - ref["logZ"][okz]).max() * w.kT
+                import oracle
+                logS = res["logZ"][:ns] + np.log(np.maximum(res["n_valid"][:ns], 1))
+                dB = np.abs(oracle.bpmf(logS, res["n_valid"][:ns], w.kT) - ref["bpmf"]).max()
+                acc[name] = {"max_kT_dlogZ_kcal": float(dz), "max_dB_sample_kcal": float(dB),
+                             "meets_0.01": bool(dB <= 0.01 and dz <= 1e-3)}
+            cpu = {"value": int(ref["n_valid"].sum()) / dt, "unit": "pose energies/s", "cores": omp_cores(),
+                   "kind": "oracle", "sample": f"first {ns} of {N_CONF} configurations x {K} receptors, "
+                                              f"all valid translations ({dt:.1f} s)"}
+        # roofline of the dominant kernel, from the live per-kernel event times
+        work = alg_work(w, res_chosen["n_valid"], chosen)
+        top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else None
+        roof = None
+        if top:
+            name, (ms_tot, nl) = top
+            key = next((k for k in work if k.replace("k_", "") in name.replace("<ff>", "").replace("<fp32>", "")), None)
+            sm_hz = (clk["sm_mhz"] or 2070.0) * 1e6
+            if key is not None:
+                flops = work[key]["flops"] * args.steps
+                if chosen == "ff":
+                    peak = N_SM * FP32_LANES_PER_SM * sm_hz / FF_INSTR_PER_FLOP / 1e12
+                    ach = flops / (ms_tot / 1e3) / 1e12
+                    roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                            "frac": ach / peak, "traffic": None,
+                            "peak_note": "derived: 152 SM x 128 FP32 lanes x median SM clock / 9.8 FP32 "
+                                         "instructions per float-pair flop",
+                            "launches": nl, "ms_per_launch": ms_tot / nl}
+                else:
+                    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+                        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+                    by = work[key]["bytes"] * args.steps
+                    ach = by / (ms_tot / 1e3) / 1e9
+                    roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                            "frac": ach / peak, "traffic": None, "peak_note": "measured hbm_gbs (burst)",
+                            "launches": nl, "ms_per_launch": ms_tot / nl}
+        gpu_launches = int(sum(n for _, n in prof.values()) / args.steps) if prof else None
+        line = {"metric": METRIC, "value": value, "unit": "pose energies/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "ff (float-pair FP32)" if chosen == "ff" else "f32",
+                "data": "synthetic (seeded receptors and ligand chain, see DESIGN.md)",
+                "config": {"workload": WORKLOAD, "form": chosen, "l2": "flushed (512 MiB write) between timed steps",
+                           "poses_per_step": n_poses},
+                "bpmfs_per_s": bpmfs,
+                "fp32_path": {"value": n_poses * world / (t_other / 1e3) if other == "fp32" else None,
+                              "ms_per_step": t_other if other == "fp32" else None},
+                "ff_path": {"ms_per_step": t_other} if other == "ff" else {"ms_per_step": t_ms},
+                "accuracy_vs_oracle": acc,
+                "e2e": {"value": n_poses * world / e2e_t, "unit": "pose energies/s", "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_t * 1e3},
+                "gpu_launches": gpu_launches, "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    sess.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="ff", choices=["ff", "fp32"])
+    ap.add_argument("--ref-sample", type=int, default=24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * bpmf.h -- C ABI of the GB300 FFT-correlation BPMF library (libbpmf.so).
+ *
+ * Method: Nguyen, Zhou & Minh, "Using the Fast Fourier Transform in Binding
+ * Free Energy Calculations" (FFTdG).  For every rigid ligand configuration and
+ * every rigid receptor conformation, the receptor-ligand interaction energy of
+ * every grid translation is the cross-correlation of the receptor potential
+ * grids with the ligand's spread generalised charges (Eqs. general_form,
+ * receptor_grid, correlation_func), evaluated with FFTs (Eq.
+ * fft_correlation_func); the energies of the valid translations are reduced
+ * by exponential averaging to the binding potential of mean force (Eq.
+ * sample_mean_BPMF) and the BPMFs of the receptor conformations to the
+ * standard binding free energy (Eqs. standard_binding_fe, binding_FE_estimate).
+ *
+ * Conventions shared by every call
+ *  - Status: every int-returning call returns BPMF_OK (0), a negative
+ *    BPMF_ERR_* code, or the positive warning BPMF_WARN_NO_VALID.  No C++
+ *    exception crosses the ABI.  bpmf_last_error() gives a one-line reason.
+ *  - Pointers: array arguments may be host memory or device memory of the
+ *    context's GPU (detected per pointer with cudaPointerGetAttributes), except
+ *    the small per-ligand count arrays, which must be host memory.  Inputs are
+ *    borrowed for the duration of the call only; outputs belong to the caller.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Work
+ *    is stream ordered.  When every output is device memory the call returns
+ *    without waiting for the GPU; when any output is host memory the call
+ *    synchronises the stream before returning.
+ *  - Handles (bpmf_ctx_t, bpmf_rec_t, bpmf_lig_t) are library-owned until
+ *    their *_free / bpmf_destroy call.  A context is not thread safe.
+ *  - Units: lengths in Angstrom, energies in kcal/mol, charges in e.
+ */
+#ifndef BPMF_H
+#define BPMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BPMF_OK 0
+#define BPMF_ERR_INVALID_ARG (-1)
+#define BPMF_ERR_OOM (-2)
+#define BPMF_ERR_CUDA (-3)
+#define BPMF_ERR_TIMEOUT (-4)
+#define BPMF_ERR_SIZE_UNSUPPORTED (-5)
+/* warning: at least one (configuration, receptor) pair has no valid
+ * translation; its log Z is -inf (and a BPMF with no valid pose is +inf). */
+#define BPMF_WARN_NO_VALID 1
+
+/* Arithmetic of the correlation (forward transforms, spectral product,
+ * inverse transforms).  Spreading is FP32 in both; the merge is FP64.
+ *   BPMF_MODE_FP32 -- plain single precision.
+ *   BPMF_MODE_FF   -- compensated float pairs (hi + lo, ~44-48 bits) built
+ *                     from FP32 instructions; the form that meets a 1e-3
+ *                     kcal/mol energy tolerance on grids whose repulsive
+ *                     values reach 1e4. */
+#define BPMF_MODE_FP32 0u
+#define BPMF_MODE_FF 1u
+
+/* Largest supported ligand (atoms) and padded FFT edge. */
+#define BPMF_MAX_ATOMS 256
+#define BPMF_MAX_FFT_EDGE 256
+
+typedef struct bpmf_ctx *bpmf_ctx_t;
+typedef struct bpmf_rec *bpmf_rec_t;
+typedef struct bpmf_lig *bpmf_lig_t;
+
+/* Create a context bound to CUDA device `device`.  Errors: INVALID_ARG (no
+ * such device), CUDA. */
+int bpmf_create(int device, bpmf_ctx_t *out);
+void bpmf_destroy(bpmf_ctx_t ctx);
+
+/* One-line description of a status code (static storage). */
+const char *bpmf_status_string(int status);
+/* Reason for the last failing call on this context ("" if none). */
+const char *bpmf_last_error(bpmf_ctx_t ctx);
+
+/*
+ * bpmf_receptor_load -- take one rigid receptor conformation's potential
+ * grids (Eq. receptor_grid: one grid per term of Eq. general_form) and compute
+ * and cache their forward 3D real-to-complex spectra FT(G_R) (Eq.
+ * fft_correlation_func) on the GPU, in float-pair precision.
+ *
+ *  grids    [3][nx][ny][nz] float32, C order, terms in the order
+ *           electrostatic, LJ-repulsive, LJ-attractive (the -2 of the
+ *           attractive term and the Coulomb factor included).  Node (i,j,k)
+ *           sits at origin + (i,j,k) h.  Host or device.
+ *  h        grid spacing (> 0).
+ *  origin   [3] position of node (0,0,0) (informational; energies depend on
+ *           grid indices only).
+ *  site_lo, site_n
+ *           the site box in nodes: a translation m is sampled when the
+ *           ligand-box centre c = floor(u/2) lands at m + c in
+ *           [site_lo, site_lo + site_n) (Methodology, FFT-based BPMF
+ *           Estimation; translations whose ligand box leaves the grid are
+ *           discarded).  site_n >= 1 per axis.
+ *  out      receives the handle.  The spectra are zero padded to the
+ *           smallest 2^a 3^b 5^c 7^d edge >= n (exact for every kept
+ *           translation, which never wraps).
+ * Errors: INVALID_ARG, SIZE_UNSUPPORTED (padded edge > BPMF_MAX_FFT_EDGE),
+ * OOM, CUDA.
+ */
+int bpmf_receptor_load(bpmf_ctx_t ctx, const float *grids, int nx, int ny, int nz, double h,
+                       const double origin[3], const int site_lo[3], const int site_n[3], void *stream,
+                       bpmf_rec_t *out);
+void bpmf_receptor_free(bpmf_rec_t rec);
+
+/*
+ * bpmf_ligand_batch -- upload a batch of ligands and their rigid
+ * configurations (the randomly rotated apo-ensemble snapshots of Methodology,
+ * Ligand Sampling) and compute the generalised charges of Eq. general_form:
+ * gamma = (q, sqrt(eps) R^p_rep, sqrt(eps) R^p_att) per atom.
+ *
+ *  n_lig            number of ligands (>= 1).
+ *  n_atoms, n_conf  [n_lig] HOST arrays: atoms per ligand (1..BPMF_MAX_ATOMS)
+ *                   and configurations per ligand (>= 0).
+ *  coords           float32 concatenated [lig][conf][atom][3] (A), already
+ *                   rotated; host or device.
+ *  q, eps, R        float32 concatenated [lig][atom]; host or device.
+ *  p_rep, p_att     integer exponents of R in the repulsive / attractive
+ *                   factors (12 and 6 for the R-form of the synthetic
+ *                   recipe; 6 and 3 give the paper's sigma form), 0..32.
+ * The call synchronises `stream` once (it reads back each configuration's
+ * coordinate bounds, which fix the ligand-box sizes).
+ * Errors: INVALID_ARG, SIZE_UNSUPPORTED (too many atoms), OOM, CUDA.
+ */
+int bpmf_ligand_batch(bpmf_ctx_t ctx, int n_lig, const int *n_atoms, const int *n_conf, const float *coords,
+                      const float *q, const float *eps, const float *R, int p_rep, int p_att, void *stream,
+                      bpmf_lig_t *out);
+void bpmf_ligand_free(bpmf_lig_t lig);
+
+/*
+ * bpmf_eval -- the hot path.  For every ligand, configuration j and receptor
+ * k: spread the ligand (trilinear weights x gamma), forward 3D FFT, spectral
+ * conj-multiply-sum over the three terms against the cached receptor spectra,
+ * inverse FFT restricted to the site box, translation mask, and a
+ * max-shifted log-sum-exp, then an FP64 merge:
+ *    log S_jk = ln sum_{m valid} exp(-E_jk(m) / kT)
+ *    logZ_jk  = log S_jk - ln n_jk                (mean over translations)
+ *    B_k      = -kT [ ln sum_j S_jk - ln sum_j n_jk ]   (Eq. sample_mean_BPMF
+ *                                                      over all valid poses)
+ *    dG       = -kT ln[(1/K) sum_k exp(-B_k/kT)] - kT ln(V_site C)
+ * with C = 1/1660.539 A^-3 and V_site = h^3 * mean_jk n_jk (Eqs.
+ * standard_binding_fe and binding_FE_estimate with uniform receptor weights).
+ *
+ *  recs, K   receptor handles; all must share the grid spacing and the padded
+ *            FFT edges (else SIZE_UNSUPPORTED).
+ *  kT        > 0 (kcal/mol).
+ *  mode      BPMF_MODE_FP32 or BPMF_MODE_FF.
+ *  logZ      [total_conf][K] float64, total_conf = sum n_conf, ligand-major.
+ *  n_valid   [total_conf][K] int64 (may be NULL).
+ *  bpmf      [n_lig][K] float64 (may be NULL).
+ *  dG        [n_lig] float64 (may be NULL).
+ * Returns BPMF_WARN_NO_VALID when some n_jk = 0 (results still written).
+ * Errors: INVALID_ARG, SIZE_UNSUPPORTED, OOM, CUDA.
+ */
+int bpmf_eval(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, int K, double kT, unsigned mode, double *logZ,
+              int64_t *n_valid, double *bpmf, double *dG, void *stream);
+
+/*
+ * bpmf_export_energies -- debug export of one configuration's interaction
+ * energies E(m) over receptor `rec`'s site window, computed by the same
+ * kernels as bpmf_eval.  out: [S0][S1][S2] float64 (S = the receptor's
+ * site_n), entry s is translation m = site_lo + s - floor(u/2); +inf where
+ * the translation is discarded.  Host or device.
+ * Errors: INVALID_ARG, SIZE_UNSUPPORTED, OOM, CUDA.
+ */
+int bpmf_export_energies(bpmf_ctx_t ctx, bpmf_lig_t lig, bpmf_rec_t rec, int lig_index, int conf_index,
+                         unsigned mode, double *out, void *stream);
+
+/* Padded FFT edge the library uses for a grid edge n (0 if unsupported). */
+int bpmf_fft_edge(int n);
+
+/* Upper bound on the device workspace bpmf_eval may hold (bytes, default
+ * 3 GiB); configurations are processed in batches that fit.  Results do not
+ * depend on the batch size (every step is deterministic).  Errors:
+ * INVALID_ARG (bytes < 1 MiB). */
+int bpmf_set_workspace_limit(bpmf_ctx_t ctx, size_t bytes);
+
+/*
+ * Kernel timing (tracing).  While enabled, every kernel the library launches
+ * is bracketed by CUDA events recorded on the stream it runs on.
+ * bpmf_profile_enable(ctx, 1) clears the counters and starts recording,
+ * (ctx, 0) stops.  bpmf_profile_count waits for the recorded events and
+ * returns the number of distinct kernels seen; bpmf_profile_entry(i) gives
+ * kernel i's name (NUL-terminated, truncated to name_len), total device time
+ * in milliseconds and number of launches.  Errors: INVALID_ARG, CUDA.
+ */
+int bpmf_profile_enable(bpmf_ctx_t ctx, int on);
+int bpmf_profile_count(bpmf_ctx_t ctx);
+int bpmf_profile_entry(bpmf_ctx_t ctx, int i, char *name, int name_len, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BPMF_H */

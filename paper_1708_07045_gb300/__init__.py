@@ -1,0 +1,277 @@
+"""GB300 (sm_103a) FFT-correlation BPMF library: thin Python binding.
+
+The compute path is ``libbpmf.so`` (hand-written CUDA kernels behind the C ABI
+declared in ``include/bpmf.h``).  This module only marshals arguments: numpy
+arrays (host memory) or torch tensors (host or device memory) are passed as raw
+pointers, and every entry point keeps the C name.  Importing this module does
+not need a GPU; calling into the library does, and there is no CPU fallback:
+if the library is missing or no GPU is visible, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_HERE, "csrc")
+_INCLUDE = os.path.join(_ROOT, "include")
+LIB_PATH = os.path.join(_HERE, "libbpmf.so")
+_SOURCES = ["kernels.cu", "bpmf_api.cu"]
+_HEADERS = ["arith.cuh", "fft.cuh", "kernels.cuh"]
+
+BPMF_OK = 0
+BPMF_ERR_INVALID_ARG = -1
+BPMF_ERR_OOM = -2
+BPMF_ERR_CUDA = -3
+BPMF_ERR_TIMEOUT = -4
+BPMF_ERR_SIZE_UNSUPPORTED = -5
+BPMF_WARN_NO_VALID = 1
+BPMF_MODE_FP32 = 0
+BPMF_MODE_FF = 1
+BPMF_MAX_ATOMS = 256
+BPMF_MAX_FFT_EDGE = 256
+
+NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
+              "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
+
+
+class BpmfError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({_status_text(status)}){': ' + detail if detail else ''}")
+
+
+def _nvcc():
+    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return cand if os.path.exists(cand) else "nvcc"
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB_PATH):
+        return True
+    t = os.path.getmtime(LIB_PATH)
+    deps = [os.path.join(_CSRC, f) for f in _SOURCES + _HEADERS] + [os.path.join(_INCLUDE, "bpmf.h")]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA sources for sm_103a into an in-tree libbpmf.so
+    (translation units in parallel, then one link)."""
+    if not force and not _stale():
+        return LIB_PATH
+    nvcc = _nvcc()
+    objdir = os.path.join(_HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+
+    def compile_one(src):
+        obj = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc, *NVCC_FLAGS, "-c", os.path.join(_CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
+        if verbose:
+            print(r.stdout + r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(len(_SOURCES)) as ex:
+        objs = list(ex.map(compile_one, _SOURCES))
+    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+    r = subprocess.run([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", *objs, "-o", tmp],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+_SIGS = {
+    "bpmf_create": (_I, [_I, ctypes.POINTER(_P)]),
+    "bpmf_destroy": (None, [_P]),
+    "bpmf_status_string": (ctypes.c_char_p, [_I]),
+    "bpmf_last_error": (ctypes.c_char_p, [_P]),
+    "bpmf_receptor_load": (_I, [_P, _P, _I, _I, _I, _D, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "bpmf_receptor_free": (None, [_P]),
+    "bpmf_ligand_batch": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _I, _I, _P, ctypes.POINTER(_P)]),
+    "bpmf_ligand_free": (None, [_P]),
+    "bpmf_eval": (_I, [_P, _P, _P, _I, _D, ctypes.c_uint, _P, _P, _P, _P, _P]),
+    "bpmf_export_energies": (_I, [_P, _P, _P, _I, _I, ctypes.c_uint, _P, _P]),
+    "bpmf_fft_edge": (_I, [_I]),
+    "bpmf_set_workspace_limit": (_I, [_P, ctypes.c_size_t]),
+    "bpmf_profile_enable": (_I, [_P, _I]),
+    "bpmf_profile_count": (_I, [_P]),
+    "bpmf_profile_entry": (_I, [_P, _I, ctypes.c_char_p, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)]),
+}
+
+
+def lib():
+    """Load libbpmf.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _status_text(s):
+    try:
+        return lib().bpmf_status_string(int(s)).decode()
+    except Exception:  # library not loadable: describe without it
+        return str(s)
+
+
+# ------------------------------------------------------------------ marshalling
+def _ptr(a, dtype):
+    """Raw pointer of a numpy array or torch tensor (contiguous, given dtype)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
+               np.int64: torch.int64}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {tdt}")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"array must be a C-contiguous numpy {np.dtype(dtype).name} array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _check(rc, where, ctx=None):
+    if rc < 0:
+        detail = ""
+        if ctx is not None:
+            try:
+                detail = lib().bpmf_last_error(ctx).decode()
+            except Exception:
+                pass
+        raise BpmfError(rc, where, detail)
+    return rc
+
+
+# -------------------------------------------------------------------- C names
+def bpmf_create(device: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib().bpmf_create(int(device), ctypes.byref(h)), "bpmf_create")
+    return h
+
+
+def bpmf_destroy(ctx):
+    lib().bpmf_destroy(ctx)
+
+
+def bpmf_status_string(status: int) -> str:
+    return lib().bpmf_status_string(int(status)).decode()
+
+
+def bpmf_last_error(ctx) -> str:
+    return lib().bpmf_last_error(ctx).decode()
+
+
+def bpmf_fft_edge(n: int) -> int:
+    return int(lib().bpmf_fft_edge(int(n)))
+
+
+def bpmf_set_workspace_limit(ctx, nbytes: int):
+    _check(lib().bpmf_set_workspace_limit(ctx, int(nbytes)), "bpmf_set_workspace_limit", ctx)
+
+
+def bpmf_receptor_load(ctx, grids, h, origin, site_lo, site_n, stream=None):
+    """grids: [3, nx, ny, nz] float32 (numpy or torch, host or device)."""
+    nx, ny, nz = (int(v) for v in tuple(grids.shape)[1:])
+    o = np.ascontiguousarray(np.asarray(origin, dtype=np.float64).reshape(3))
+    lo = np.ascontiguousarray(np.asarray(site_lo, dtype=np.int32).reshape(3))
+    sn = np.ascontiguousarray(np.asarray(site_n, dtype=np.int32).reshape(3))
+    out = ctypes.c_void_p()
+    rc = lib().bpmf_receptor_load(ctx, _ptr(grids, np.float32), nx, ny, nz, float(h), _ptr(o, np.float64),
+                                  _ptr(lo, np.int32), _ptr(sn, np.int32), _stream(stream), ctypes.byref(out))
+    _check(rc, "bpmf_receptor_load", ctx)
+    return out
+
+
+def bpmf_receptor_free(rec):
+    lib().bpmf_receptor_free(rec)
+
+
+def bpmf_ligand_batch(ctx, n_atoms, n_conf, coords, q, eps, R, p_rep=12, p_att=6, stream=None):
+    """n_atoms, n_conf: per-ligand counts (host); coords float32 [sum conf*atoms, 3];
+    q, eps, R float32 [sum atoms] (numpy or torch, host or device)."""
+    na = np.ascontiguousarray(np.asarray(n_atoms, dtype=np.int32).reshape(-1))
+    nc = np.ascontiguousarray(np.asarray(n_conf, dtype=np.int32).reshape(-1))
+    out = ctypes.c_void_p()
+    rc = lib().bpmf_ligand_batch(ctx, int(na.size), _ptr(na, np.int32), _ptr(nc, np.int32),
+                                 _ptr(coords, np.float32), _ptr(q, np.float32), _ptr(eps, np.float32),
+                                 _ptr(R, np.float32), int(p_rep), int(p_att), _stream(stream), ctypes.byref(out))
+    _check(rc, "bpmf_ligand_batch", ctx)
+    return out
+
+
+def bpmf_ligand_free(lig):
+    lib().bpmf_ligand_free(lig)
+
+
+def bpmf_eval(ctx, lig, recs, kT, mode, logZ, n_valid=None, bpmf=None, dG=None, stream=None) -> int:
+    """Outputs are caller-allocated (numpy or torch, host or device):
+    logZ float64 [total_conf, K], n_valid int64 [total_conf, K], bpmf float64
+    [n_lig, K], dG float64 [n_lig].  Returns BPMF_OK or BPMF_WARN_NO_VALID."""
+    K = len(recs)
+    arr = (ctypes.c_void_p * K)(*[r.value if isinstance(r, ctypes.c_void_p) else r for r in recs])
+    rc = lib().bpmf_eval(ctx, lig, ctypes.cast(arr, ctypes.c_void_p), K, float(kT), int(mode),
+                         _ptr(logZ, np.float64), _ptr(n_valid, np.int64), _ptr(bpmf, np.float64),
+                         _ptr(dG, np.float64), _stream(stream))
+    return _check(rc, "bpmf_eval", ctx)
+
+
+def bpmf_export_energies(ctx, lig, rec, lig_index, conf_index, mode, out, stream=None) -> int:
+    """out: float64 [S0, S1, S2] (the receptor's site box), host or device."""
+    rc = lib().bpmf_export_energies(ctx, lig, rec, int(lig_index), int(conf_index), int(mode),
+                                    _ptr(out, np.float64), _stream(stream))
+    return _check(rc, "bpmf_export_energies", ctx)
+
+
+def bpmf_profile_enable(ctx, on: bool = True):
+    _check(lib().bpmf_profile_enable(ctx, 1 if on else 0), "bpmf_profile_enable", ctx)
+
+
+def bpmf_profile_count(ctx) -> int:
+    return _check(lib().bpmf_profile_count(ctx), "bpmf_profile_count", ctx)
+
+
+def bpmf_profile_entry(ctx, i: int):
+    """(kernel name, total device ms, launches) of recorded kernel i."""
+    buf = ctypes.create_string_buffer(128)
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib().bpmf_profile_entry(ctx, int(i), buf, 128, ctypes.byref(ms), ctypes.byref(n)),
+           "bpmf_profile_entry", ctx)
+    return buf.value.decode(), ms.value, n.value
+
+
+def bpmf_profile(ctx) -> dict:
+    """{kernel name: (total ms, launches)} recorded since profiling was enabled."""
+    return {name: (ms, n) for name, ms, n in (bpmf_profile_entry(ctx, i) for i in range(bpmf_profile_count(ctx)))}

@@ -1,0 +1,932 @@
+// C-ABI layer: handles, plans, twiddle tables, workspace and the launch
+// sequence of the hot path.  Host-side logic only; every arithmetic step of
+// the correlation runs in the kernels of kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/bpmf.h"
+#include "kernels.cuh"
+
+using namespace bpmf;
+
+// ---------------------------------------------------------------- handles
+struct ProfRec {
+  const char *name;
+  cudaEvent_t a, b;
+};
+
+struct bpmf_ctx {
+  int device = 0;
+  bool prof = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<std::string> prof_names;
+  std::vector<double> prof_ms;
+  std::vector<long long> prof_n;
+  std::string err;
+  std::map<int, float4 *> tw;  // twiddle tables per transform length
+  void *ws = nullptr;          // grow-only device workspace
+  size_t ws_bytes = 0;
+  size_t ws_budget = size_t(3) << 30;
+};
+
+struct bpmf_rec {
+  bpmf_ctx *ctx = nullptr;
+  int N[3] = {0, 0, 0}, P[3] = {0, 0, 0}, F2 = 0;
+  long long Q = 0;
+  double h = 0;
+  double origin[3] = {0, 0, 0};
+  int site_lo[3] = {0, 0, 0}, site_n[3] = {0, 0, 0};
+  float2 *hi = nullptr, *lo = nullptr;  // [3][P0][Q]
+};
+
+struct bpmf_lig {
+  bpmf_ctx *ctx = nullptr;
+  int n_lig = 0;
+  std::vector<int> n_atoms, n_conf, atom_off, conf_off, coord_off;
+  long long total_conf = 0, total_atoms = 0, total_coord_atoms = 0;
+  float *coords = nullptr;  // device [coord_atoms][3]
+  float *gamma = nullptr;   // device [3][total_atoms]
+  std::vector<float> minmax;  // host [total_conf][6]
+};
+
+namespace {
+
+struct Fail {
+  int code;
+};
+
+int set_err(bpmf_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      last_msg = std::string(#call) + ": " + cudaGetErrorString(e_);                            \
+      throw Fail{e_ == cudaErrorMemoryAllocation ? BPMF_ERR_OOM : BPMF_ERR_CUDA};              \
+    }                                                                                          \
+  } while (0)
+
+thread_local std::string last_msg;
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// smallest 2^a 3^b 5^c 7^d >= n with a >= 1
+int smooth_edge(int n) {
+  if (n < 2) n = 2;
+  for (int p = n; p <= BPMF_MAX_FFT_EDGE; ++p) {
+    if (p % 2) continue;
+    int m = p;
+    for (int r : {2, 3, 5, 7})
+      while (m % r == 0) m /= r;
+    if (m == 1) return p;
+  }
+  return 0;
+}
+
+FftPlan make_plan(int P) {
+  FftPlan pl{};
+  pl.n = P;
+  int m = P, k = 0;
+  while (m % 8 == 0) pl.r[k++] = 8, m /= 8;
+  while (m % 4 == 0) pl.r[k++] = 4, m /= 4;
+  while (m % 2 == 0) pl.r[k++] = 2, m /= 2;
+  for (int r : {3, 5, 7})
+    while (m % r == 0) pl.r[k++] = r, m /= r;
+  pl.nst = k;
+  return pl;
+}
+
+const float4 *twiddles(bpmf_ctx *c, int P) {
+  auto it = c->tw.find(P);
+  if (it != c->tw.end()) return it->second;
+  std::vector<float4> h(P);
+  const long double two_pi = 6.283185307179586476925286766559L;
+  for (int k = 0; k < P; ++k) {
+    // exp(-2 pi i k / P) from the exact fraction k / P
+    long double a = two_pi * (long double)k / (long double)P;
+    long double re = cosl(a), im = -sinl(a);
+    float rh = (float)re, ih = (float)im;
+    h[k] = make_float4(rh, ih, (float)(re - (long double)rh), (float)(im - (long double)ih));
+  }
+  float4 *d = nullptr;
+  CK(cudaMalloc(&d, sizeof(float4) * P));
+  CK(cudaMemcpy(d, h.data(), sizeof(float4) * P, cudaMemcpyHostToDevice));
+  c->tw[P] = d;
+  return d;
+}
+
+void *workspace(bpmf_ctx *c, size_t bytes, cudaStream_t st) {
+  if (bytes <= c->ws_bytes) return c->ws;
+  if (c->ws) {
+    CK(cudaStreamSynchronize(st));
+    CK(cudaFree(c->ws));
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+  }
+  CK(cudaMalloc(&c->ws, bytes));
+  c->ws_bytes = bytes;
+  return c->ws;
+}
+
+inline size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+cudaEvent_t pool_event(bpmf_ctx *c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  return e;
+}
+
+// Launch `fn` (returning cudaError_t); when profiling, bracket it with events.
+template <class F>
+void launch(bpmf_ctx *c, const char *name, cudaStream_t st, F &&fn) {
+  if (!c->prof) {
+    CK(fn());
+    return;
+  }
+  ProfRec r{name, pool_event(c), pool_event(c)};
+  CK(cudaEventRecord(r.a, st));
+  CK(fn());
+  CK(cudaEventRecord(r.b, st));
+  c->pending.push_back(r);
+}
+
+void prof_drain(bpmf_ctx *c) {
+  for (auto &r : c->pending) {
+    CK(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    size_t i = 0;
+    while (i < c->prof_names.size() && c->prof_names[i] != r.name) ++i;
+    if (i == c->prof_names.size()) {
+      c->prof_names.push_back(r.name);
+      c->prof_ms.push_back(0.0);
+      c->prof_n.push_back(0);
+    }
+    c->prof_ms[i] += ms;
+    c->prof_n[i] += 1;
+    c->event_pool.push_back(r.a);
+    c->event_pool.push_back(r.b);
+  }
+  c->pending.clear();
+}
+
+void split_ff(double v, float &hi, float &lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+// ligand-box extent, decided in single precision exactly as the oracle does
+int box_extent(float lo, float hi, float hf) {
+  volatile float ext = hi - lo;
+  volatile float r = ext / hf;
+  return (int)std::ceil(r) + 4;
+}
+
+// temporary device copy of a host or device input
+struct DevIn {
+  const void *p = nullptr;
+  void *own = nullptr;
+  cudaStream_t st = nullptr;
+  DevIn(const void *src, size_t bytes, cudaStream_t s) : st(s) {
+    if (!src) throw Fail{BPMF_ERR_INVALID_ARG};
+    if (is_device_ptr(src)) {
+      p = src;
+    } else {
+      CK(cudaMallocAsync(&own, bytes ? bytes : 1, st));
+      CK(cudaMemcpyAsync(own, src, bytes, cudaMemcpyHostToDevice, st));
+      p = own;
+    }
+  }
+  ~DevIn() {
+    if (own) cudaFreeAsync(own, st);
+  }
+};
+
+// Runs the eval launch sequence for one batch of configurations.
+struct BatchGeom {
+  int U[3];
+  int P[3], F2;
+  long long Q;
+  int S[3];
+  int K;
+};
+
+size_t batch_bytes_per_conf(const BatchGeom &g, size_t E) {
+  const size_t box = 3ull * g.U[0] * g.U[1] * g.U[2] * 4;
+  const size_t lz = 3ull * g.U[0] * g.U[1] * g.F2 * E;
+  const size_t ly = 3ull * g.U[0] * g.Q * E;
+  const size_t x2 = (size_t)g.K * g.S[0] * g.Q * E;
+  const size_t y2 = (size_t)g.K * g.S[0] * g.S[1] * g.F2 * E;
+  return align_up(box) + align_up(lz) + align_up(ly) + align_up(x2) + align_up(y2);
+}
+
+template <class T>
+void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, const ConfMeta *d_meta,
+               const PairInfo *d_info, const float2 *const *d_rhi, const float2 *const *d_rlo, double h,
+               float nscale_hi, float nscale_lo, float escale_hi, float escale_lo, float4 *d_part,
+               double *export_E, char *ws, cudaStream_t st) {
+  const size_t E = sizeof(cx<T>);
+  char *p = ws;
+  float *box = reinterpret_cast<float *>(p);
+  p += align_up(3ull * batch * g.U[0] * g.U[1] * g.U[2] * 4);
+  void *lz = p;
+  p += align_up(3ull * batch * g.U[0] * g.U[1] * g.F2 * E);
+  void *ly = p;
+  p += align_up(3ull * batch * g.U[0] * g.Q * E);
+  void *x2 = p;
+  p += align_up((size_t)batch * g.K * g.S[0] * g.Q * E);
+  void *y2 = p;
+
+  float hh, hl;
+  split_ff(h, hh, hl);
+  SpreadArgs sa{lg->coords, lg->gamma, (int)lg->total_atoms, d_meta, hh, hl, g.U[0], g.U[1], g.U[2], box};
+  launch(c, "k_spread", st, [&] { return launch_spread(sa, batch, st); });
+
+  ZfwdArgs za{};
+  za.in = box;
+  za.n_rows = 3ll * batch * g.U[0] * g.U[1];
+  za.w_in = g.U[2];
+  za.in_stride = g.U[2];
+  za.out = lz;
+  za.out_stride = g.F2;
+  za.plan = make_plan(g.P[2]);
+  za.tw = twiddles(c, g.P[2]);
+  za.L = 16;
+  launch(c, sizeof(T) == 4 ? "k_zfwd<fp32>" : "k_zfwd<ff>", st, [&] { return launch_zfwd<T>(za, st); });
+
+  AxisArgs ya{};
+  ya.in = lz;
+  ya.out = ly;
+  ya.P = g.P[1];
+  ya.n_in = g.U[1];
+  ya.n_out = g.P[1];
+  ya.n_outer = 3ll * batch * g.U[0];
+  ya.inner = g.F2;
+  ya.in_os = (long long)g.U[1] * g.F2;
+  ya.out_os = (long long)g.P[1] * g.F2;
+  ya.info = nullptr;
+  ya.w0_div = 1;
+  ya.axis = 1;
+  ya.inverse = 0;
+  ya.plan = make_plan(g.P[1]);
+  ya.tw = twiddles(c, g.P[1]);
+  ya.LW = 16;
+  launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y fwd)" : "k_axis<ff>(y fwd)", st, [&] { return launch_axis<T>(ya, st); });
+
+  XfusedArgs xa{};
+  xa.ly = ly;
+  xa.U0 = g.U[0];
+  xa.Q = g.Q;
+  xa.K = g.K;
+  xa.rhi = d_rhi;
+  xa.rlo = d_rlo;
+  xa.x2 = x2;
+  xa.S0 = g.S[0];
+  xa.info = d_info;
+  xa.plan = make_plan(g.P[0]);
+  xa.tw = twiddles(c, g.P[0]);
+  xa.LW = sizeof(T) == 4 ? 16 : 8;
+  launch(c, sizeof(T) == 4 ? "k_xfused<fp32>" : "k_xfused<ff>", st, [&] { return launch_xfused<T>(xa, batch, st); });
+
+  AxisArgs yi{};
+  yi.in = x2;
+  yi.out = y2;
+  yi.P = g.P[1];
+  yi.n_in = g.P[1];
+  yi.n_out = g.S[1];
+  yi.n_outer = (long long)batch * g.K * g.S[0];
+  yi.inner = g.F2;
+  yi.in_os = g.Q;
+  yi.out_os = (long long)g.S[1] * g.F2;
+  yi.info = d_info;
+  yi.w0_div = g.S[0];
+  yi.axis = 1;
+  yi.inverse = 1;
+  yi.plan = make_plan(g.P[1]);
+  yi.tw = twiddles(c, g.P[1]);
+  yi.LW = 16;
+  launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y inv)" : "k_axis<ff>(y inv)", st, [&] { return launch_axis<T>(yi, st); });
+
+  ZinvArgs zi{};
+  zi.y2 = y2;
+  zi.K = g.K;
+  zi.S0 = g.S[0];
+  zi.S1 = g.S[1];
+  zi.S2 = g.S[2];
+  zi.F2 = g.F2;
+  zi.info = d_info;
+  zi.nscale_hi = nscale_hi;
+  zi.nscale_lo = nscale_lo;
+  zi.escale_hi = escale_hi;
+  zi.escale_lo = escale_lo;
+  zi.part = d_part;
+  zi.export_E = export_E;
+  zi.plan = make_plan(g.P[2]);
+  zi.tw = twiddles(c, g.P[2]);
+  launch(c, sizeof(T) == 4 ? "k_zinv<fp32>" : "k_zinv<ff>", st, [&] { return launch_zinv<T>(zi, batch, st); });
+}
+
+void check_recs(const bpmf_rec_t *recs, int K, bpmf_ctx *c) {
+  for (int k = 0; k < K; ++k) {
+    if (!recs[k] || recs[k]->ctx != c) throw Fail{BPMF_ERR_INVALID_ARG};
+    for (int d = 0; d < 3; ++d)
+      if (recs[k]->P[d] != recs[0]->P[d]) {
+        last_msg = "receptors in one bpmf_eval call must share padded FFT edges";
+        throw Fail{BPMF_ERR_SIZE_UNSUPPORTED};
+      }
+    if (recs[k]->h != recs[0]->h) {
+      last_msg = "receptors in one bpmf_eval call must share the grid spacing";
+      throw Fail{BPMF_ERR_SIZE_UNSUPPORTED};
+    }
+  }
+}
+
+// Host-side per-ligand tables: placement metadata per configuration and the
+// site window / valid count per (configuration, receptor).
+void ligand_tables(const bpmf_lig *lg, int li, const bpmf_rec_t *recs, int K, double h, std::vector<ConfMeta> &meta,
+                   std::vector<PairInfo> &info, std::vector<long long> &nvalid) {
+  const int J = lg->n_conf[li];
+  const float hf = (float)h;
+  meta.resize(J);
+  info.resize((size_t)J * K);
+  nvalid.resize((size_t)J * K);
+  for (int j = 0; j < J; ++j) {
+    const long long cj = lg->conf_off[li] + j;
+    const float *mm = &lg->minmax[6 * cj];
+    ConfMeta m{};
+    for (int d = 0; d < 3; ++d) {
+      m.lo[d] = mm[d];
+      m.u[d] = box_extent(mm[d], mm[3 + d], hf);
+    }
+    m.atom_off = (int)(lg->coord_off[li] + (long long)j * lg->n_atoms[li]);
+    m.n_atoms = lg->n_atoms[li];
+    m.gamma_off = lg->atom_off[li];
+    meta[j] = m;
+    for (int k = 0; k < K; ++k) {
+      PairInfo pi{};
+      long long n = 1;
+      for (int d = 0; d < 3; ++d) {
+        const int w0 = recs[k]->site_lo[d] - m.u[d] / 2;
+        const int sa = std::max(0, -w0);
+        const int sb = std::min(recs[k]->site_n[d] - 1, recs[k]->N[d] - 1 - m.u[d] - w0);
+        pi.w0[d] = w0;
+        pi.sa[d] = sa;
+        pi.sb[d] = sb;
+        n *= (sb >= sa) ? (sb - sa + 1) : 0;
+      }
+      info[(size_t)j * K + k] = pi;
+      nvalid[(size_t)j * K + k] = n;
+    }
+  }
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+const char *bpmf_status_string(int s) {
+  switch (s) {
+    case BPMF_OK: return "ok";
+    case BPMF_ERR_INVALID_ARG: return "invalid argument";
+    case BPMF_ERR_OOM: return "out of device memory";
+    case BPMF_ERR_CUDA: return "CUDA error";
+    case BPMF_ERR_TIMEOUT: return "timeout";
+    case BPMF_ERR_SIZE_UNSUPPORTED: return "size unsupported";
+    case BPMF_WARN_NO_VALID: return "warning: some configuration has no valid translation";
+    default: return "unknown status";
+  }
+}
+
+const char *bpmf_last_error(bpmf_ctx_t ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int bpmf_fft_edge(int n) { return n >= 1 ? smooth_edge(n) : 0; }
+
+int bpmf_profile_enable(bpmf_ctx_t c, int on) {
+  if (!c) return BPMF_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  try {
+    prof_drain(c);
+  } catch (Fail f) {
+    return set_err(c, f.code, last_msg);
+  }
+  c->prof = on != 0;
+  if (c->prof) {
+    c->prof_names.clear();
+    c->prof_ms.clear();
+    c->prof_n.clear();
+  }
+  return BPMF_OK;
+}
+
+int bpmf_profile_count(bpmf_ctx_t c) {
+  if (!c) return BPMF_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  try {
+    prof_drain(c);
+  } catch (Fail f) {
+    return set_err(c, f.code, last_msg);
+  }
+  return (int)c->prof_names.size();
+}
+
+int bpmf_profile_entry(bpmf_ctx_t c, int i, char *name, int name_len, double *total_ms, int64_t *launches) {
+  if (!c || i < 0 || i >= (int)c->prof_names.size()) return BPMF_ERR_INVALID_ARG;
+  if (name && name_len > 0) {
+    std::strncpy(name, c->prof_names[i].c_str(), (size_t)name_len - 1);
+    name[name_len - 1] = '\0';
+  }
+  if (total_ms) *total_ms = c->prof_ms[i];
+  if (launches) *launches = c->prof_n[i];
+  return BPMF_OK;
+}
+
+int bpmf_set_workspace_limit(bpmf_ctx_t c, size_t bytes) {
+  if (!c || bytes < (size_t(1) << 20)) return set_err(c, BPMF_ERR_INVALID_ARG, "workspace limit below 1 MiB");
+  c->ws_budget = bytes;
+  return BPMF_OK;
+}
+
+int bpmf_create(int device, bpmf_ctx_t *out) {
+  if (!out) return BPMF_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return BPMF_ERR_CUDA;
+  }
+  if (device < 0 || device >= n) return BPMF_ERR_INVALID_ARG;
+  bpmf_ctx *c = new (std::nothrow) bpmf_ctx();
+  if (!c) return BPMF_ERR_OOM;
+  c->device = device;
+  DeviceGuard g(device);
+  if (cudaFree(nullptr) != cudaSuccess) {  // establish the primary context
+    cudaGetLastError();
+    delete c;
+    return BPMF_ERR_CUDA;
+  }
+  *out = c;
+  return BPMF_OK;
+}
+
+void bpmf_destroy(bpmf_ctx_t c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  for (auto &kv : c->tw) cudaFree(kv.second);
+  if (c->ws) cudaFree(c->ws);
+  for (auto &r : c->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz, double h, const double origin[3],
+                       const int site_lo[3], const int site_n[3], void *stream, bpmf_rec_t *out) {
+  if (!c || !out || !grids || !site_lo || !site_n) return set_err(c, BPMF_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (nx < 2 || ny < 2 || nz < 2 || !(h > 0.0))
+    return set_err(c, BPMF_ERR_INVALID_ARG, "grid edges must be >= 2 and h > 0");
+  for (int d = 0; d < 3; ++d)
+    if (site_n[d] < 1) return set_err(c, BPMF_ERR_INVALID_ARG, "site_n must be >= 1");
+  const int N[3] = {nx, ny, nz};
+  int P[3];
+  for (int d = 0; d < 3; ++d) {
+    P[d] = smooth_edge(N[d]);
+    if (!P[d]) return set_err(c, BPMF_ERR_SIZE_UNSUPPORTED, "padded FFT edge exceeds BPMF_MAX_FFT_EDGE");
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  bpmf_rec *r = new (std::nothrow) bpmf_rec();
+  if (!r) return set_err(c, BPMF_ERR_OOM, "host allocation");
+  void *tz = nullptr, *ty = nullptr, *tx = nullptr;
+  try {
+    r->ctx = c;
+    for (int d = 0; d < 3; ++d) {
+      r->N[d] = N[d];
+      r->P[d] = P[d];
+      r->site_lo[d] = site_lo[d];
+      r->site_n[d] = site_n[d];
+      r->origin[d] = origin ? origin[d] : 0.0;
+    }
+    r->h = h;
+    r->F2 = P[2] / 2 + 1;
+    r->Q = (long long)P[1] * r->F2;
+    const size_t vol = (size_t)nx * ny * nz;
+    DevIn g(grids, 3 * vol * sizeof(float), st);
+    const size_t E = sizeof(cx<ff>);
+    CK(cudaMallocAsync(&tz, 3ull * nx * ny * r->F2 * E, st));
+    CK(cudaMallocAsync(&ty, 3ull * nx * r->Q * E, st));
+    CK(cudaMallocAsync(&tx, 3ull * P[0] * r->Q * E, st));
+    CK(cudaMalloc(&r->hi, 3ull * P[0] * r->Q * sizeof(float2)));
+    CK(cudaMalloc(&r->lo, 3ull * P[0] * r->Q * sizeof(float2)));
+    // z: R2C of every (t, x, y) row
+    ZfwdArgs za{};
+    za.in = static_cast<const float *>(g.p);
+    za.n_rows = 3ll * nx * ny;
+    za.w_in = nz;
+    za.in_stride = nz;
+    za.out = tz;
+    za.out_stride = r->F2;
+    za.plan = make_plan(P[2]);
+    za.tw = twiddles(c, P[2]);
+    za.L = 16;
+    launch(c, "k_zfwd<ff>(receptor)", st, [&] { return launch_zfwd<ff>(za, st); });
+    // y
+    AxisArgs ya{};
+    ya.in = tz;
+    ya.out = ty;
+    ya.P = P[1];
+    ya.n_in = ny;
+    ya.n_out = P[1];
+    ya.n_outer = 3ll * nx;
+    ya.inner = r->F2;
+    ya.in_os = (long long)ny * r->F2;
+    ya.out_os = r->Q;
+    ya.w0_div = 1;
+    ya.axis = 1;
+    ya.plan = make_plan(P[1]);
+    ya.tw = twiddles(c, P[1]);
+    ya.LW = 16;
+    launch(c, "k_axis<ff>(receptor y)", st, [&] { return launch_axis<ff>(ya, st); });
+    // x
+    AxisArgs xa{};
+    xa.in = ty;
+    xa.out = tx;
+    xa.P = P[0];
+    xa.n_in = nx;
+    xa.n_out = P[0];
+    xa.n_outer = 3;
+    xa.inner = r->Q;
+    xa.in_os = (long long)nx * r->Q;
+    xa.out_os = (long long)P[0] * r->Q;
+    xa.w0_div = 1;
+    xa.axis = 0;
+    xa.plan = make_plan(P[0]);
+    xa.tw = twiddles(c, P[0]);
+    xa.LW = 16;
+    launch(c, "k_axis<ff>(receptor x)", st, [&] { return launch_axis<ff>(xa, st); });
+    launch(c, "k_split_ff", st, [&] { return launch_split_ff(tx, r->hi, r->lo, 3ll * P[0] * r->Q, st); });
+    CK(cudaFreeAsync(tz, st));
+    tz = nullptr;
+    CK(cudaFreeAsync(ty, st));
+    ty = nullptr;
+    CK(cudaFreeAsync(tx, st));
+    tx = nullptr;
+    if (!is_device_ptr(grids)) CK(cudaStreamSynchronize(st));
+  } catch (Fail f) {
+    if (tz) cudaFreeAsync(tz, st);
+    if (ty) cudaFreeAsync(ty, st);
+    if (tx) cudaFreeAsync(tx, st);
+    bpmf_receptor_free(r);
+    return set_err(c, f.code, last_msg);
+  }
+  *out = r;
+  c->err.clear();
+  return BPMF_OK;
+}
+
+void bpmf_receptor_free(bpmf_rec_t r) {
+  if (!r) return;
+  if (r->ctx) {
+    DeviceGuard g(r->ctx->device);
+    if (r->hi) cudaFree(r->hi);
+    if (r->lo) cudaFree(r->lo);
+  }
+  delete r;
+}
+
+int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_conf, const float *coords,
+                      const float *q, const float *eps, const float *R, int p_rep, int p_att, void *stream,
+                      bpmf_lig_t *out) {
+  if (!c || !out || n_lig < 1 || !n_atoms || !n_conf || !q || !eps || !R)
+    return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or n_lig < 1");
+  *out = nullptr;
+  if (p_rep < 0 || p_rep > 32 || p_att < 0 || p_att > 32)
+    return set_err(c, BPMF_ERR_INVALID_ARG, "exponents must lie in 0..32");
+  bpmf_lig *lg = new (std::nothrow) bpmf_lig();
+  if (!lg) return set_err(c, BPMF_ERR_OOM, "host allocation");
+  DeviceGuard dg(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  int *d_off = nullptr, *d_nat = nullptr;
+  float *d_mm = nullptr;
+  try {
+    lg->ctx = c;
+    lg->n_lig = n_lig;
+    lg->n_atoms.assign(n_atoms, n_atoms + n_lig);
+    lg->n_conf.assign(n_conf, n_conf + n_lig);
+    lg->atom_off.resize(n_lig);
+    lg->conf_off.resize(n_lig);
+    lg->coord_off.resize(n_lig);
+    for (int i = 0; i < n_lig; ++i) {
+      if (n_atoms[i] < 1 || n_conf[i] < 0) {
+        last_msg = "n_atoms must be >= 1 and n_conf >= 0";
+        throw Fail{BPMF_ERR_INVALID_ARG};
+      }
+      if (n_atoms[i] > BPMF_MAX_ATOMS) {
+        last_msg = "ligand has more than BPMF_MAX_ATOMS atoms";
+        throw Fail{BPMF_ERR_SIZE_UNSUPPORTED};
+      }
+      lg->atom_off[i] = (int)lg->total_atoms;
+      lg->conf_off[i] = (int)lg->total_conf;
+      lg->coord_off[i] = (int)lg->total_coord_atoms;
+      lg->total_atoms += n_atoms[i];
+      lg->total_conf += n_conf[i];
+      lg->total_coord_atoms += (long long)n_conf[i] * n_atoms[i];
+    }
+    if (lg->total_coord_atoms > 0 && !coords) {
+      last_msg = "coords is null";
+      throw Fail{BPMF_ERR_INVALID_ARG};
+    }
+    const size_t na = lg->total_atoms;
+    CK(cudaMalloc(&lg->gamma, 3 * na * sizeof(float)));
+    CK(cudaMalloc(&lg->coords, std::max<size_t>(1, 3 * lg->total_coord_atoms) * sizeof(float)));
+    {
+      DevIn dq(q, na * sizeof(float), st), de(eps, na * sizeof(float), st), dr(R, na * sizeof(float), st);
+      launch(c, "k_gamma", st, [&] {
+        return launch_gamma((const float *)dq.p, (const float *)de.p, (const float *)dr.p, (int)na, p_rep, p_att,
+                            lg->gamma, st);
+      });
+    }
+    if (lg->total_coord_atoms > 0)
+      CK(cudaMemcpyAsync(lg->coords, coords, 3 * lg->total_coord_atoms * sizeof(float), cudaMemcpyDefault, st));
+    const long long TC = lg->total_conf;
+    std::vector<int> off(std::max<long long>(TC, 1)), nat(std::max<long long>(TC, 1));
+    for (int i = 0; i < n_lig; ++i)
+      for (int j = 0; j < n_conf[i]; ++j) {
+        off[lg->conf_off[i] + j] = lg->coord_off[i] + j * n_atoms[i];
+        nat[lg->conf_off[i] + j] = n_atoms[i];
+      }
+    lg->minmax.assign(6 * std::max<long long>(TC, 1), 0.f);
+    if (TC > 0) {
+      CK(cudaMallocAsync(&d_off, TC * sizeof(int), st));
+      CK(cudaMallocAsync(&d_nat, TC * sizeof(int), st));
+      CK(cudaMallocAsync(&d_mm, 6 * TC * sizeof(float), st));
+      CK(cudaMemcpyAsync(d_off, off.data(), TC * sizeof(int), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_nat, nat.data(), TC * sizeof(int), cudaMemcpyHostToDevice, st));
+      launch(c, "k_minmax", st, [&] { return launch_minmax(lg->coords, d_off, d_nat, (int)TC, d_mm, st); });
+      CK(cudaMemcpyAsync(lg->minmax.data(), d_mm, 6 * TC * sizeof(float), cudaMemcpyDeviceToHost, st));
+      CK(cudaFreeAsync(d_off, st));
+      d_off = nullptr;
+      CK(cudaFreeAsync(d_nat, st));
+      d_nat = nullptr;
+      CK(cudaFreeAsync(d_mm, st));
+      d_mm = nullptr;
+    }
+    CK(cudaStreamSynchronize(st));
+  } catch (Fail f) {
+    if (d_off) cudaFreeAsync(d_off, st);
+    if (d_nat) cudaFreeAsync(d_nat, st);
+    if (d_mm) cudaFreeAsync(d_mm, st);
+    bpmf_ligand_free(lg);
+    return set_err(c, f.code, last_msg);
+  }
+  *out = lg;
+  c->err.clear();
+  return BPMF_OK;
+}
+
+void bpmf_ligand_free(bpmf_lig_t lg) {
+  if (!lg) return;
+  if (lg->ctx) {
+    DeviceGuard g(lg->ctx->device);
+    if (lg->coords) cudaFree(lg->coords);
+    if (lg->gamma) cudaFree(lg->gamma);
+  }
+  delete lg;
+}
+
+namespace {
+
+// Shared driver of bpmf_eval and bpmf_export_energies.
+int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
+              double *logZ, int64_t *n_valid, double *bpmf_out, double *dG, cudaStream_t st, int only_lig,
+              int only_conf, double *export_E) {
+  check_recs(recs, K, c);
+  const bpmf_rec *r0 = recs[0];
+  const double h = r0->h;
+  const bool use_ff = (mode == BPMF_MODE_FF);
+  const size_t E = use_ff ? sizeof(cx<ff>) : sizeof(cx<float>);
+  int S[3] = {0, 0, 0};
+  for (int k = 0; k < K; ++k)
+    for (int d = 0; d < 3; ++d) S[d] = std::max(S[d], recs[k]->site_n[d]);
+  const double norm = 1.0 / ((double)r0->P[0] * r0->P[1] * r0->P[2]);
+  float nsh, nsl, esh, esl;
+  split_ff(-norm / kT, nsh, nsl);
+  split_ff(norm, esh, esl);
+
+  // receptor spectrum pointer tables (device)
+  std::vector<const float2 *> hrhi(K), hrlo(K);
+  for (int k = 0; k < K; ++k) {
+    hrhi[k] = recs[k]->hi;
+    hrlo[k] = recs[k]->lo;
+  }
+  bool warn = false;
+  const int lig_begin = only_lig >= 0 ? only_lig : 0;
+  const int lig_end = only_lig >= 0 ? only_lig + 1 : lg->n_lig;
+  long long conf_base = 0;
+  for (int li = 0; li < lig_begin; ++li) conf_base += lg->n_conf[li];
+
+  std::vector<ConfMeta> meta;
+  std::vector<PairInfo> info;
+  std::vector<long long> nv;
+  for (int li = lig_begin; li < lig_end; ++li) {
+    ligand_tables(lg, li, recs, K, h, meta, info, nv);
+    int J = lg->n_conf[li];
+    int j_first = 0;
+    if (only_conf >= 0) {
+      if (only_conf >= J) throw Fail{BPMF_ERR_INVALID_ARG};
+      j_first = only_conf;
+      J = 1;
+    }
+    // ligand-wide box size (clamped to the FFT edges)
+    int Umax[3] = {1, 1, 1};
+    for (int j = j_first; j < j_first + J; ++j)
+      for (int d = 0; d < 3; ++d) Umax[d] = std::max(Umax[d], std::min(meta[j].u[d], r0->P[d]));
+    for (int j = j_first; j < j_first + J; ++j)
+      for (int k = 0; k < K; ++k)
+        if (nv[(size_t)j * K + k] == 0) warn = true;
+    BatchGeom g{};
+    for (int d = 0; d < 3; ++d) {
+      g.U[d] = Umax[d];
+      g.P[d] = r0->P[d];
+      g.S[d] = S[d];
+    }
+    g.F2 = r0->F2;
+    g.Q = r0->Q;
+    g.K = K;
+    const size_t per_conf = batch_bytes_per_conf(g, E);
+    // fixed part of the workspace: tables, partials, merge outputs
+    const size_t JK = (size_t)std::max(J, 1) * K;
+    const size_t fixed = align_up(sizeof(ConfMeta) * std::max(J, 1)) + align_up(sizeof(PairInfo) * JK) +
+                         align_up(sizeof(long long) * JK) + align_up(sizeof(float4) * JK * S[0]) +
+                         align_up(sizeof(double) * 2 * JK) + align_up(sizeof(double) * (K + 1)) +
+                         align_up(2 * sizeof(void *) * K);
+    int B = (int)std::max<size_t>(1, (c->ws_budget > fixed ? c->ws_budget - fixed : 0) / per_conf);
+    B = std::min(B, std::max(J, 1));
+    char *ws = static_cast<char *>(workspace(c, fixed + per_conf * B, st));
+    char *p = ws;
+    ConfMeta *d_meta = reinterpret_cast<ConfMeta *>(p);
+    p += align_up(sizeof(ConfMeta) * std::max(J, 1));
+    PairInfo *d_info = reinterpret_cast<PairInfo *>(p);
+    p += align_up(sizeof(PairInfo) * JK);
+    long long *d_nv = reinterpret_cast<long long *>(p);
+    p += align_up(sizeof(long long) * JK);
+    float4 *d_part = reinterpret_cast<float4 *>(p);
+    p += align_up(sizeof(float4) * JK * S[0]);
+    double *d_logZ = reinterpret_cast<double *>(p);  // + logS scratch
+    p += align_up(sizeof(double) * 2 * JK);
+    double *d_B = reinterpret_cast<double *>(p);  // [K] + dG
+    p += align_up(sizeof(double) * (K + 1));
+    const float2 **d_rptr = reinterpret_cast<const float2 **>(p);
+    p += align_up(2 * sizeof(void *) * K);
+    char *d_batch = p;
+    if (J > 0) {
+      CK(cudaMemcpyAsync(d_meta, meta.data() + j_first, sizeof(ConfMeta) * J, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_info, info.data() + (size_t)j_first * K, sizeof(PairInfo) * J * K,
+                         cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_nv, nv.data() + (size_t)j_first * K, sizeof(long long) * J * K, cudaMemcpyHostToDevice,
+                         st));
+    }
+    CK(cudaMemcpyAsync(d_rptr, hrhi.data(), sizeof(void *) * K, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_rptr + K, hrlo.data(), sizeof(void *) * K, cudaMemcpyHostToDevice, st));
+    for (int b0 = 0; b0 < J; b0 += B) {
+      const int nb = std::min(B, J - b0);
+      BatchGeom gb = g;
+      for (int d = 0; d < 3; ++d) {
+        gb.U[d] = 1;
+        for (int j = b0; j < b0 + nb; ++j) gb.U[d] = std::max(gb.U[d], std::min(meta[j_first + j].u[d], r0->P[d]));
+      }
+      if (use_ff)
+        run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * K, d_rptr, d_rptr + K, h, nsh, nsl, esh,
+                      esl, d_part + (size_t)b0 * K * S[0], export_E, d_batch, st);
+      else
+        run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * K, d_rptr, nullptr, h, nsh, nsl, esh,
+                         esl, d_part + (size_t)b0 * K * S[0], export_E, d_batch, st);
+    }
+    if (export_E) break;
+    MergeArgs ma{};
+    ma.part = d_part;
+    ma.nvalid = d_nv;
+    ma.J = J;
+    ma.K = K;
+    ma.S0 = S[0];
+    ma.kT = kT;
+    ma.vsite_scale = h * h * h / 1660.5390;
+    ma.logZ = d_logZ;
+    ma.bpmf = d_B;
+    ma.dG = d_B + K;
+    ma.nvalid_out = nullptr;
+    launch(c, "k_merge", st, [&] { return launch_merge(ma, st); });
+    const long long ob = conf_base;
+    if (J > 0) {
+      CK(cudaMemcpyAsync(logZ + ob * K, d_logZ, sizeof(double) * J * K, cudaMemcpyDefault, st));
+      if (n_valid) CK(cudaMemcpyAsync(n_valid + ob * K, d_nv, sizeof(int64_t) * J * K, cudaMemcpyDefault, st));
+    }
+    if (bpmf_out) CK(cudaMemcpyAsync(bpmf_out + (size_t)li * K, d_B, sizeof(double) * K, cudaMemcpyDefault, st));
+    if (dG) CK(cudaMemcpyAsync(dG + li, d_B + K, sizeof(double), cudaMemcpyDefault, st));
+    // the next ligand reuses the workspace; stream order keeps these copies first
+    conf_base += lg->n_conf[li];
+  }
+  if (!export_E && ((logZ && !is_device_ptr(logZ)) || (n_valid && !is_device_ptr(n_valid)) ||
+                    (bpmf_out && !is_device_ptr(bpmf_out)) || (dG && !is_device_ptr(dG))))
+    CK(cudaStreamSynchronize(st));
+  return warn ? BPMF_WARN_NO_VALID : BPMF_OK;
+}
+
+}  // namespace
+
+int bpmf_eval(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode, double *logZ,
+              int64_t *n_valid, double *bpmf_out, double *dG, void *stream) {
+  if (!c || !lg || !recs || K < 1 || !(kT > 0.0) || (!logZ && lg && lg->total_conf > 0))
+    return set_err(c, BPMF_ERR_INVALID_ARG, "null argument, K < 1 or kT <= 0");
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF) return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
+  if (lg->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "ligand batch from another context");
+  DeviceGuard dg(c->device);
+  try {
+    last_msg.clear();
+    int rc = eval_impl(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, (cudaStream_t)stream, -1, -1, nullptr);
+    c->err.clear();
+    return rc;
+  } catch (Fail f) {
+    return set_err(c, f.code, last_msg.empty() ? bpmf_status_string(f.code) : last_msg);
+  } catch (std::bad_alloc &) {
+    return set_err(c, BPMF_ERR_OOM, "host allocation");
+  }
+}
+
+int bpmf_export_energies(bpmf_ctx_t c, bpmf_lig_t lg, bpmf_rec_t rec, int lig_index, int conf_index, unsigned mode,
+                         double *out, void *stream) {
+  if (!c || !lg || !rec || !out || lig_index < 0 || lig_index >= lg->n_lig || conf_index < 0 ||
+      conf_index >= lg->n_conf[lig_index])
+    return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or index out of range");
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF) return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
+  DeviceGuard dg(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  double *d_out = nullptr;
+  const size_t n = (size_t)rec->site_n[0] * rec->site_n[1] * rec->site_n[2];
+  try {
+    last_msg.clear();
+    const bool dev = is_device_ptr(out);
+    if (dev) {
+      d_out = out;
+    } else {
+      CK(cudaMallocAsync(&d_out, n * sizeof(double), st));
+    }
+    bpmf_rec_t recs[1] = {rec};
+    eval_impl(c, lg, recs, 1, 1.0, mode, nullptr, nullptr, nullptr, nullptr, st, lig_index, conf_index, d_out);
+    if (!dev) {
+      CK(cudaMemcpyAsync(out, d_out, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaFreeAsync(d_out, st));
+      d_out = nullptr;
+      CK(cudaStreamSynchronize(st));
+    }
+  } catch (Fail f) {
+    if (d_out && d_out != out) cudaFreeAsync(d_out, st);
+    return set_err(c, f.code, last_msg.empty() ? bpmf_status_string(f.code) : last_msg);
+  }
+  c->err.clear();
+  return BPMF_OK;
+}
+
+}  // extern "C"

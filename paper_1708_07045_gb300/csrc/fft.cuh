@@ -1,0 +1,133 @@
+// CTA-wide mixed-radix Stockham FFT over a tile of lines held in shared
+// memory (Eq. fft_correlation_func needs forward and inverse 3D DFTs; each is
+// three passes of these 1D line transforms).
+//
+// Element n of line l lives at buf[n * es + l * ls].  Strided passes (lines
+// along y or x, consecutive lines = consecutive innermost indices) use
+// es = number of lines, ls = 1; contiguous passes (lines along z) use es = 1,
+// ls = P + 1 (odd, so a warp touching consecutive lines hits distinct banks).
+//
+// Stage with radix R after Ns points have been combined (Ns = product of the
+// earlier radices): butterfly i in [0, P/R) reads x[i + r P/R], multiplies by
+// w_P^(r (i mod Ns) P/(Ns R)), takes an R-point DFT and writes to
+// (i / Ns) Ns R + (i mod Ns) + r Ns.  Radices 8, 4, 2 are hand-written; 3, 5
+// and 7 use the R-point DFT matrix read from the same twiddle table.
+#pragma once
+#include "arith.cuh"
+
+namespace bpmf {
+
+struct FftPlan {
+  int n;       // transform length P
+  int nst;     // number of stages
+  int r[12];   // radix of each stage, product = n
+};
+
+template <class T, int R>
+__device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, int P) {
+  if constexpr (R == 2) {
+    cx<T> a = v[0], b = v[1];
+    v[0] = c_add(a, b);
+    v[1] = c_sub(a, b);
+  } else if constexpr (R == 4) {
+    cx<T> a = c_add(v[0], v[2]), b = c_sub(v[0], v[2]);
+    cx<T> c = c_add(v[1], v[3]), d = c_rot(c_sub(v[1], v[3]), inv);
+    v[0] = c_add(a, c);
+    v[2] = c_sub(a, c);
+    v[1] = c_add(b, d);
+    v[3] = c_sub(b, d);
+  } else if constexpr (R == 8) {
+    cx<T> a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k] = c_add(v[k], v[k + 4]);
+      b[k] = c_sub(v[k], v[k + 4]);
+    }
+    // b1 *= w8, b2 *= w8^2 = -i (fwd), b3 *= w8^3; conjugated for inverse
+    const float4 q = tw[P / 8];                 // exp(-i pi/4): (c, -c)
+    const T c = s_mk<T>(q.x, q.z);                 // cos(pi/4) as hi/lo
+    {
+      T x = b[1].re, y = b[1].im;
+      b[1] = inv ? cx<T>{s_mul(s_sub(x, y), c), s_mul(s_add(x, y), c)}
+                 : cx<T>{s_mul(s_add(x, y), c), s_mul(s_sub(y, x), c)};
+    }
+    b[2] = c_rot(b[2], inv);
+    {
+      T x = b[3].re, y = b[3].im;
+      b[3] = inv ? cx<T>{s_neg(s_mul(s_add(x, y), c)), s_mul(s_sub(x, y), c)}
+                 : cx<T>{s_mul(s_sub(y, x), c), s_neg(s_mul(s_add(x, y), c))};
+    }
+    dft_small<T, 4>(a, inv, tw, P);
+    dft_small<T, 4>(b, inv, tw, P);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      v[2 * m] = a[m];
+      v[2 * m + 1] = b[m];
+    }
+  } else {
+    // odd radix: X[a] = sum_b v[b] w_R^(a b), w_R^m = tw[m P / R]
+    cx<T> out[R];
+    const int st = P / R;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      cx<T> acc = v[0];
+#pragma unroll
+      for (int b = 1; b < R; ++b) acc = c_add(acc, c_mul(v[b], tw_load<T>(tw[((a * b) % R) * st], inv)));
+      out[a] = acc;
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) v[a] = out[a];
+  }
+}
+
+template <class T, int R>
+__device__ __forceinline__ void fft_stage(const cx<T> *src, cx<T> *dst, int es, int ls, int nlines, int P, int Ns,
+                                          const float4 *tw, bool inv) {
+  const int nb = P / R;
+  const int items = nb * nlines;
+  const int tstride = P / (Ns * R);
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int l = it % nlines, i = it / nlines;
+    const int j = i % Ns;
+    cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(i + r * nb) * es + l * ls];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], tw_load<T>(tw[r * j * tstride], inv));
+    }
+    dft_small<T, R>(v, inv, tw, P);
+    const int o = (i / Ns) * Ns * R + j;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(o + r * Ns) * es + l * ls] = v[r];
+  }
+}
+
+// Transforms nlines lines in place-by-ping-pong.  Data must be in b0 and
+// visible to the CTA (caller syncs before).  Returns the buffer holding the
+// result; the CTA is synchronised on return.
+template <class T>
+__device__ cx<T> *cta_fft(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, const FftPlan &pl, const float4 *tw,
+                          bool inv) {
+  int Ns = 1;
+  cx<T> *src = b0, *dst = b1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int R = pl.r[s];
+    switch (R) {
+      case 8: fft_stage<T, 8>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      case 4: fft_stage<T, 4>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      case 2: fft_stage<T, 2>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      case 3: fft_stage<T, 3>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      case 5: fft_stage<T, 5>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      default: fft_stage<T, 7>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+    }
+    __syncthreads();
+    cx<T> *t = src;
+    src = dst;
+    dst = t;
+    Ns *= R;
+  }
+  return src;
+}
+
+}  // namespace bpmf

@@ -1,0 +1,563 @@
+// Hot-path kernels: ligand spreading, forward R2C/C2C passes, the fused
+// x-pass (forward ligand DFT, conj-multiply-sum with every receptor spectrum,
+// inverse DFT, site window), the inverse y-pass, the inverse C2R z-pass fused
+// with the site mask and a max-shifted log-sum-exp, and the FP64 merge into
+// log Z_jk, the BPMF per receptor and the standard binding free energy.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "kernels.cuh"
+
+namespace bpmf {
+
+// --------------------------------------------------------------------------
+// small helpers
+__device__ __forceinline__ int imod(int a, int m) {
+  int r = a % m;
+  return r < 0 ? r + m : r;
+}
+
+template <class T>
+__device__ __forceinline__ void st_cx(void *base, long long idx, cx<T> v) {
+  reinterpret_cast<cx<T> *>(base)[idx] = v;
+}
+template <class T>
+__device__ __forceinline__ cx<T> ld_cx(const void *base, long long idx) {
+  return reinterpret_cast<const cx<T> *>(base)[idx];
+}
+
+// receptor spectrum element from hi / lo planes
+__device__ __forceinline__ cx<float> ld_rec(const float2 *hi, const float2 *, long long idx, float) {
+  float2 a = hi[idx];
+  return cx<float>{a.x, a.y};
+}
+__device__ __forceinline__ cx<ff> ld_rec(const float2 *hi, const float2 *lo, long long idx, ff) {
+  float2 a = hi[idx], b = lo[idx];
+  return cx<ff>{ff{a.x, b.x}, ff{a.y, b.y}};
+}
+
+__device__ __forceinline__ void load_tw(float4 *s_tw, const float4 *tw, int P) {
+  for (int i = threadIdx.x; i < P; i += blockDim.x) s_tw[i] = tw[i];
+}
+
+// --------------------------------------------------------------------------
+// generalised charges (Eqs. electrostatic, repulsive_LJ, attractive_LJ):
+// gamma = (q, sqrt(eps) R^p_rep, sqrt(eps) R^p_att)
+__global__ void k_gamma(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, float *g) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float se = sqrtf(eps[i]);
+  float r = R[i], pr = 1.f, pa = 1.f;
+  for (int k = 0; k < p_rep; ++k) pr = __fmul_rn(pr, r);
+  for (int k = 0; k < p_att; ++k) pa = __fmul_rn(pa, r);
+  g[i] = q[i];
+  g[n + i] = __fmul_rn(se, pr);
+  g[2 * n + i] = __fmul_rn(se, pa);
+}
+
+cudaError_t launch_gamma(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, float *gamma,
+                         cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_gamma<<<(n + 127) / 128, 128, 0, st>>>(q, eps, R, n, p_rep, p_att, gamma);
+  return cudaGetLastError();
+}
+
+// per-configuration coordinate bounds (placement, "FFT-based BPMF Estimation")
+__global__ void k_minmax(const float *xyz, const int *off, const int *nat, int n_conf, float *out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_conf) return;
+  const float *x = xyz + 3ll * off[j];
+  float lo[3] = {x[0], x[1], x[2]}, hi[3] = {x[0], x[1], x[2]};
+  for (int i = 1; i < nat[j]; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fminf(lo[d], x[3 * i + d]);
+      hi[d] = fmaxf(hi[d], x[3 * i + d]);
+    }
+  for (int d = 0; d < 3; ++d) {
+    out[6 * j + d] = lo[d];
+    out[6 * j + 3 + d] = hi[d];
+  }
+}
+
+cudaError_t launch_minmax(const float *coords, const int *off, const int *nat, int n_conf, float *out,
+                          cudaStream_t st) {
+  if (n_conf <= 0) return cudaSuccess;
+  k_minmax<<<(n_conf + 127) / 128, 128, 0, st>>>(coords, off, nat, n_conf, out);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// (a) spreading.  CTA = (configuration, x-plane of the ligand box).  Each atom
+// is placed (lowest coordinate 2 spacings above plane 0) with its grid-unit
+// position carried as a float pair, then its 8 trilinear corner weights times
+// gamma_t are accumulated in shared memory.  Accumulation is in 64-bit fixed
+// point (per-channel power-of-two scale from sum |gamma|), so the result is
+// exact, order independent and deterministic; it is rounded to FP32 once.
+constexpr int kMaxAtoms = 256;
+
+__global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
+  const int ix = blockIdx.x;
+  const int j = blockIdx.y;
+  const ConfMeta m = a.meta[j];
+  __shared__ int s_c[kMaxAtoms][3];
+  __shared__ float s_f[kMaxAtoms][3];
+  __shared__ float s_red[3][8];
+  __shared__ int s_e[3];
+  extern __shared__ unsigned long long s_plane[];  // [U1][U2]
+  const int n = m.n_atoms;
+  const ff h{a.h_hi, a.h_lo};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int d = 0; d < 3; ++d) {
+      const float x = a.coords[3ll * (m.atom_off + i) + d];
+      ff dx = two_sum(x, -m.lo[d]);  // exact x - lo
+      // g = dx / h + 2 in float-pair precision
+      const float q1 = __fdiv_rn(dx.hi, h.hi);
+      const float p = __fmul_rn(q1, h.hi);
+      const float pe = __fmaf_rn(q1, h.hi, -p);
+      float r = __fsub_rn(__fsub_rn(dx.hi, p), pe);
+      r = __fadd_rn(r, __fsub_rn(dx.lo, __fmul_rn(q1, h.lo)));
+      const float q2 = __fdiv_rn(r, h.hi);
+      ff g = s_add(fast_two_sum(q1, q2), ff{2.f, 0.f});
+      float c = floorf(g.hi);
+      if (g.hi == c && g.lo < 0.f) c -= 1.f;
+      float f = __fadd_rn(__fsub_rn(g.hi, c), g.lo);
+      f = fminf(fmaxf(f, 0.f), 1.f);
+      s_c[i][d] = (int)c;
+      s_f[i][d] = f;
+    }
+  }
+  // per-channel fixed-point scale
+  float sa[3] = {0.f, 0.f, 0.f};
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    for (int t = 0; t < 3; ++t) sa[t] += fabsf(a.gamma[(long long)t * a.gamma_stride + m.gamma_off + i]);
+  for (int t = 0; t < 3; ++t) {
+    float v = sa[t];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_red[t][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    float v = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_red[threadIdx.x][w];
+    // 2^e * (sum |gamma| * 1.01) < 2^61 keeps every partial sum in range
+    s_e[threadIdx.x] = v > 0.f ? 60 - ilogbf(v * 1.01f) - 1 : 0;
+  }
+  __syncthreads();
+  const int plane = a.U1 * a.U2;
+  for (int t = 0; t < 3; ++t) {
+    for (int i = threadIdx.x; i < plane; i += blockDim.x) s_plane[i] = 0ull;
+    __syncthreads();
+    const int e = s_e[t];
+    for (int it = threadIdx.x; it < n * 8; it += blockDim.x) {
+      const int i = it >> 3, dx = (it >> 2) & 1, dy = (it >> 1) & 1, dz = it & 1;
+      if (s_c[i][0] + dx != ix) continue;
+      const float wx = dx ? s_f[i][0] : 1.f - s_f[i][0];
+      const float wy = dy ? s_f[i][1] : 1.f - s_f[i][1];
+      const float wz = dz ? s_f[i][2] : 1.f - s_f[i][2];
+      const float gm = a.gamma[(long long)t * a.gamma_stride + m.gamma_off + i];
+      const float v = __fmul_rn(__fmul_rn(__fmul_rn(wx, wy), wz), gm);
+      const long long iv = __float2ll_rn(ldexpf(v, e));
+      const int y = s_c[i][1] + dy, z = s_c[i][2] + dz;
+      if (y < a.U1 && z < a.U2) atomicAdd(&s_plane[y * a.U2 + z], (unsigned long long)iv);
+    }
+    __syncthreads();
+    float *dst = a.box + (((long long)j * 3 + t) * a.U0 + ix) * plane;
+    for (int i = threadIdx.x; i < plane; i += blockDim.x)
+      dst[i] = ldexpf(__ll2float_rn((long long)s_plane[i]), -e);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_spread(const SpreadArgs &a, int batch, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  const size_t smem = sizeof(unsigned long long) * (size_t)a.U1 * a.U2;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_spread<<<dim3(a.U0, batch), 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// (b) R2C along the contiguous axis: two real rows packed as one complex line.
+template <class T>
+__global__ void __launch_bounds__(256) k_zfwd(ZfwdArgs a) {
+  extern __shared__ float4 smem[];
+  const int P = a.plan.n, L = a.L, ls = P + 1, F = P / 2 + 1;
+  float4 *s_tw = smem;
+  cx<T> *b0 = reinterpret_cast<cx<T> *>(smem + P);
+  cx<T> *b1 = b0 + L * ls;
+  load_tw(s_tw, a.tw, P);
+  const long long r0 = (long long)blockIdx.x * 2 * L;
+  for (int idx = threadIdx.x; idx < L * P; idx += blockDim.x) {
+    const int l = idx / P, n = idx % P;
+    const long long ra = r0 + 2 * l, rb = ra + 1;
+    float va = 0.f, vb = 0.f;
+    if (n < a.w_in) {
+      if (ra < a.n_rows) va = a.in[ra * a.in_stride + n];
+      if (rb < a.n_rows) vb = a.in[rb * a.in_stride + n];
+    }
+    b0[l * ls + n] = cx<T>{s_from<T>(va), s_from<T>(vb)};
+  }
+  __syncthreads();
+  cx<T> *res = cta_fft<T>(b0, b1, 1, ls, L, a.plan, s_tw, false);
+  const T half = s_from<T>(0.5f);
+  for (int idx = threadIdx.x; idx < L * F; idx += blockDim.x) {
+    const int l = idx / F, k = idx % F;
+    const long long ra = r0 + 2 * l, rb = ra + 1;
+    const cx<T> zk = res[l * ls + k];
+    const cx<T> zn = c_conj(res[l * ls + (k == 0 ? 0 : P - k)]);
+    // A = (Z_k + conj Z_{P-k}) / 2,  B = -i (Z_k - conj Z_{P-k}) / 2
+    const cx<T> s = c_add(zk, zn), d = c_sub(zk, zn);
+    if (ra < a.n_rows) st_cx<T>(a.out, ra * a.out_stride + k, cx<T>{s_mul(s.re, half), s_mul(s.im, half)});
+    if (rb < a.n_rows) st_cx<T>(a.out, rb * a.out_stride + k, cx<T>{s_mul(d.im, half), s_neg(s_mul(d.re, half))});
+  }
+}
+
+template <class T>
+cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st) {
+  if (a.n_rows <= 0) return cudaSuccess;
+  const int P = a.plan.n;
+  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)a.L * (P + 1);
+  cudaError_t e = cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (a.n_rows + 2 * a.L - 1) / (2 * a.L);
+  k_zfwd<T><<<(unsigned)blocks, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// C2C along a strided axis for a tile of LW consecutive innermost indices.
+template <class T>
+__global__ void __launch_bounds__(256) k_axis(AxisArgs a) {
+  extern __shared__ float4 smem[];
+  const int P = a.plan.n, LW = a.LW;
+  float4 *s_tw = smem;
+  cx<T> *b0 = reinterpret_cast<cx<T> *>(smem + P);
+  cx<T> *b1 = b0 + P * LW;
+  load_tw(s_tw, a.tw, P);
+  const long long ntile = (a.inner + LW - 1) / LW;
+  const long long o = blockIdx.x / ntile;
+  const long long i0 = (blockIdx.x % ntile) * LW;
+  for (int idx = threadIdx.x; idx < P * LW; idx += blockDim.x) {
+    const int n = idx / LW, l = idx % LW;
+    const long long i = i0 + l;
+    cx<T> v = c_zero<T>();
+    if (n < a.n_in && i < a.inner) v = ld_cx<T>(a.in, o * a.in_os + n * a.inner + i);
+    b0[idx] = v;
+  }
+  __syncthreads();
+  cx<T> *res = cta_fft<T>(b0, b1, LW, 1, LW, a.plan, s_tw, a.inverse != 0);
+  const int w0 = a.info ? a.info[o / a.w0_div].w0[a.axis] : 0;
+  for (int idx = threadIdx.x; idx < a.n_out * LW; idx += blockDim.x) {
+    const int s = idx / LW, l = idx % LW;
+    const long long i = i0 + l;
+    if (i < a.inner) st_cx<T>(a.out, o * a.out_os + s * a.inner + i, res[imod(w0 + s, P) * LW + l]);
+  }
+}
+
+template <class T>
+cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
+  if (a.n_outer <= 0 || a.inner <= 0) return cudaSuccess;
+  const int P = a.plan.n;
+  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * a.LW;
+  cudaError_t e = cudaFuncSetAttribute(k_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks = a.n_outer * ((a.inner + a.LW - 1) / a.LW);
+  k_axis<T><<<(unsigned)blocks, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// (b)+(c)+(d, first inverse pass) along x.  CTA = (configuration, tile of LW
+// consecutive (y, zf) columns).  Forward DFT of the 3 ligand channels, then
+// for each receptor k: P_k = sum_t R_{k,t} conj(L_t), inverse DFT, keep the
+// site window along x.  The ligand spectrum never leaves shared memory.
+template <class T>
+__global__ void __launch_bounds__(256) k_xfused(XfusedArgs a) {
+  extern __shared__ float4 smem[];
+  const int P = a.plan.n, LW = a.LW, L3 = 3 * LW;
+  float4 *s_tw = smem;
+  cx<T> *bA = reinterpret_cast<cx<T> *>(smem + P);
+  cx<T> *bB = bA + P * L3;
+  load_tw(s_tw, a.tw, P);
+  const long long ntile = (a.Q + LW - 1) / LW;
+  const int j = blockIdx.x / ntile;
+  const long long q0 = (blockIdx.x % ntile) * LW;
+  for (int idx = threadIdx.x; idx < P * L3; idx += blockDim.x) {
+    const int x = idx / L3, c = idx % L3, t = c / LW, l = c % LW;
+    const long long q = q0 + l;
+    cx<T> v = c_zero<T>();
+    if (x < a.U0 && q < a.Q) v = ld_cx<T>(a.ly, (((long long)j * 3 + t) * a.U0 + x) * a.Q + q);
+    bA[idx] = v;
+  }
+  __syncthreads();
+  cx<T> *Lsp = cta_fft<T>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
+  cx<T> *W1 = (Lsp == bA) ? bB : bA;
+  cx<T> *W2 = W1 + P * LW;
+  for (int k = 0; k < a.K; ++k) {
+    const float2 *rh = a.rhi[k];
+    const float2 *rl = a.rlo ? a.rlo[k] : nullptr;
+    for (int idx = threadIdx.x; idx < P * LW; idx += blockDim.x) {
+      const int x = idx / LW, l = idx % LW;
+      const long long q = q0 + l;
+      cx<T> acc = c_zero<T>();
+      if (q < a.Q) {
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const cx<T> r = ld_rec(rh, rl, ((long long)t * P + x) * a.Q + q, T{});
+          acc = c_add(acc, c_mulconj(r, Lsp[x * L3 + t * LW + l]));
+        }
+      }
+      W1[idx] = acc;
+    }
+    __syncthreads();
+    cx<T> *res = cta_fft<T>(W1, W2, LW, 1, LW, a.plan, s_tw, true);
+    const int w0 = a.info[j * a.K + k].w0[0];
+    for (int idx = threadIdx.x; idx < a.S0 * LW; idx += blockDim.x) {
+      const int s = idx / LW, l = idx % LW;
+      const long long q = q0 + l;
+      if (q < a.Q) st_cx<T>(a.x2, (((long long)j * a.K + k) * a.S0 + s) * a.Q + q, res[imod(w0 + s, P) * LW + l]);
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  const int P = a.plan.n;
+  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * 3 * a.LW;
+  cudaError_t e = cudaFuncSetAttribute(k_xfused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (long long)batch * ((a.Q + a.LW - 1) / a.LW);
+  k_xfused<T><<<(unsigned)blocks, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// (d) last inverse pass: C2R along z of two packed rows, 1/(P0 P1 P2) scale,
+// site mask, then a max-shifted log-sum-exp over this CTA's (s1, s2) plane.
+__device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ bool ff_gt(float a, float b) { return a > b; }
+
+template <class T>
+__global__ void __launch_bounds__(256) k_zinv(ZinvArgs a) {
+  extern __shared__ float4 smem[];
+  const int P = a.plan.n, F = a.F2, ls = P + 1;
+  const int L = (a.S1 + 1) / 2;
+  float4 *s_tw = smem;
+  cx<T> *b0 = reinterpret_cast<cx<T> *>(smem + P);
+  cx<T> *b1 = b0 + L * ls;
+  T *xs = reinterpret_cast<T *>(b1 + L * ls);  // [S1*S2]
+  __shared__ T s_red[8];
+  __shared__ float s_sum[8];
+  load_tw(s_tw, a.tw, P);
+  const int s0 = blockIdx.x % a.S0;
+  const int jk = blockIdx.x / a.S0;  // j * K + k
+  const PairInfo inf = a.info[jk];
+  const long long base = (long long)blockIdx.x * a.S1 * F;
+  const bool row_ok = (s0 >= inf.sa[0] && s0 <= inf.sb[0]);
+  for (int idx = threadIdx.x; idx < L * P; idx += blockDim.x) {
+    const int l = idx / P, n = idx % P;
+    const int ra = 2 * l, rb = ra + 1;
+    cx<T> A = c_zero<T>(), B = c_zero<T>();
+    const bool up = n <= P / 2;
+    const int kk = up ? n : P - n;
+    const bool real_bin = (kk == 0) || (2 * kk == P);
+    if (row_ok) {
+      A = ld_cx<T>(a.y2, base + (long long)ra * F + kk);
+      if (rb < a.S1) B = ld_cx<T>(a.y2, base + (long long)rb * F + kk);
+    }
+    if (real_bin) {
+      A.im = s_zero<T>();
+      B.im = s_zero<T>();
+    }
+    if (!up) {
+      A = c_conj(A);
+      B = c_conj(B);
+    }
+    b0[l * ls + n] = cx<T>{s_sub(A.re, B.im), s_add(A.im, B.re)};
+  }
+  __syncthreads();
+  cx<T> *res = cta_fft<T>(b0, b1, 1, ls, L, a.plan, s_tw, true);
+  const T nscale = s_mk<T>(a.nscale_hi, a.nscale_lo);
+  const T escale = s_mk<T>(a.escale_hi, a.escale_lo);
+  const int nS = a.S1 * a.S2;
+  T vmax = s_mk<T>(-CUDART_INF_F, 0.f);
+  for (int idx = threadIdx.x; idx < nS; idx += blockDim.x) {
+    const int s1 = idx / a.S2, s2 = idx % a.S2;
+    const bool ok = row_ok && s1 >= inf.sa[1] && s1 <= inf.sb[1] && s2 >= inf.sa[2] && s2 <= inf.sb[2];
+    T x = s_mk<T>(-CUDART_INF_F, 0.f);
+    if (ok) {
+      const cx<T> z = res[(s1 >> 1) * ls + imod(inf.w0[2] + s2, P)];
+      const T val = (s1 & 1) ? z.im : z.re;
+      x = s_mul(val, nscale);
+      if (ff_gt(x, vmax)) vmax = x;
+    }
+    xs[idx] = x;
+    if (a.export_E && jk == 0) {
+      double e = CUDART_INF;
+      if (ok) {
+        const cx<T> z = res[(s1 >> 1) * ls + imod(inf.w0[2] + s2, P)];
+        const T E = s_mul((s1 & 1) ? z.im : z.re, escale);
+        e = (double)s_hi(E) + (double)s_lo(E);
+      }
+      a.export_E[((long long)s0 * a.S1 + s1) * a.S2 + s2] = e;
+    }
+  }
+  // block max
+  for (int o = 16; o > 0; o >>= 1) {
+    T other = s_mk<T>(__shfl_xor_sync(0xffffffffu, s_hi(vmax), o), __shfl_xor_sync(0xffffffffu, s_lo(vmax), o));
+    if (ff_gt(other, vmax)) vmax = other;
+  }
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = vmax;
+  __syncthreads();
+  T M = s_red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+    if (ff_gt(s_red[w], M)) M = s_red[w];
+  float acc = 0.f;
+  if (s_hi(M) > -CUDART_INF_F) {
+    for (int idx = threadIdx.x; idx < nS; idx += blockDim.x) {
+      const T x = xs[idx];
+      if (s_hi(x) > -CUDART_INF_F) {
+        const float d = __fadd_rn(__fsub_rn(s_hi(x), s_hi(M)), __fsub_rn(s_lo(x), s_lo(M)));
+        acc += expf(d);
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_sum[w];
+    a.part[blockIdx.x] = make_float4(s_hi(M), s_lo(M), s, 0.f);
+  }
+}
+
+template <class T>
+cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  const int P = a.plan.n, L = (a.S1 + 1) / 2;
+  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)L * (P + 1) + sizeof(T) * (size_t)a.S1 * a.S2;
+  cudaError_t e = cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_zinv<T><<<(unsigned)((long long)batch * a.K * a.S0), 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// FP64 merge (Eq. sample_mean_BPMF pooled over every valid pose; Eqs.
+// standard_binding_fe / binding_FE_estimate with uniform receptor weights):
+//   log S_jk = M* + ln sum_c s_c exp(M_c - M*)      over the S0 partials
+//   log Z_jk = log S_jk - ln n_jk
+//   B_k      = -kT [ LSE_j log S_jk - ln sum_j n_jk ]
+//   dG       = -kT [ LSE_k (-B_k / kT) - ln K ] - kT ln(V_site C)
+__global__ void __launch_bounds__(256) k_merge(MergeArgs a, double *logS) {
+  __shared__ double s_d[256];
+  __shared__ long long s_l[256];
+  const int JK = a.J * a.K;
+  for (int p = threadIdx.x; p < JK; p += blockDim.x) {
+    const float4 *pp = a.part + (long long)p * a.S0;
+    double Mx = -CUDART_INF;
+    for (int c = 0; c < a.S0; ++c)
+      if (pp[c].z > 0.f) Mx = fmax(Mx, (double)pp[c].x + (double)pp[c].y);
+    double s = 0.0;
+    if (Mx > -CUDART_INF)
+      for (int c = 0; c < a.S0; ++c)
+        if (pp[c].z > 0.f) s += (double)pp[c].z * exp((double)pp[c].x + (double)pp[c].y - Mx);
+    const long long n = a.nvalid[p];
+    const double ls = (s > 0.0 && n > 0) ? Mx + log(s) : -CUDART_INF;
+    logS[p] = ls;
+    a.logZ[p] = n > 0 ? ls - log((double)n) : -CUDART_INF;
+    if (a.nvalid_out) a.nvalid_out[p] = n;
+  }
+  __syncthreads();
+  long long ntot_all = 0;
+  for (int k = 0; k < a.K; ++k) {
+    double mx = -CUDART_INF;
+    long long nt = 0;
+    for (int j = threadIdx.x; j < a.J; j += blockDim.x) {
+      mx = fmax(mx, logS[(long long)j * a.K + k]);
+      nt += a.nvalid[(long long)j * a.K + k];
+    }
+    s_d[threadIdx.x] = mx;
+    s_l[threadIdx.x] = nt;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) {
+        s_d[threadIdx.x] = fmax(s_d[threadIdx.x], s_d[threadIdx.x + o]);
+        s_l[threadIdx.x] += s_l[threadIdx.x + o];
+      }
+      __syncthreads();
+    }
+    const double M = s_d[0];
+    const long long ntot = s_l[0];
+    __syncthreads();
+    double acc = 0.0;
+    if (M > -CUDART_INF)
+      for (int j = threadIdx.x; j < a.J; j += blockDim.x) {
+        const double v = logS[(long long)j * a.K + k];
+        if (v > -CUDART_INF) acc += exp(v - M);
+      }
+    s_d[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) s_d[threadIdx.x] += s_d[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double B = (ntot > 0 && s_d[0] > 0.0) ? -a.kT * (M + log(s_d[0]) - log((double)ntot)) : CUDART_INF;
+      a.bpmf[k] = B;
+    }
+    ntot_all += ntot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && a.dG) {
+    double mx = -CUDART_INF;
+    for (int k = 0; k < a.K; ++k) mx = fmax(mx, -a.bpmf[k] / a.kT);
+    double s = 0.0;
+    if (mx > -CUDART_INF)
+      for (int k = 0; k < a.K; ++k) s += exp(-a.bpmf[k] / a.kT - mx);
+    const double nmean = (double)ntot_all / ((double)a.J * a.K);
+    a.dG[0] = (s > 0.0 && nmean > 0.0)
+                  ? -a.kT * (mx + log(s) - log((double)a.K)) - a.kT * log(a.vsite_scale * nmean)
+                  : CUDART_INF;
+  }
+}
+
+cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st) {
+  // logS scratch lives right after logZ's J*K entries in the caller's device
+  // workspace; the C-ABI layer passes it through logZ + J*K.
+  k_merge<<<1, 256, 0, st>>>(a, a.logZ + (long long)a.J * a.K);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+__global__ void k_split_ff(const cx<ff> *spec, float2 *hi, float2 *lo, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cx<ff> v = spec[i];
+  hi[i] = make_float2(v.re.hi, v.im.hi);
+  lo[i] = make_float2(v.re.lo, v.im.lo);
+}
+
+cudaError_t launch_split_ff(const void *spec, float2 *hi, float2 *lo, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_split_ff<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const cx<ff> *>(spec), hi, lo, n);
+  return cudaGetLastError();
+}
+
+// explicit instantiations
+template cudaError_t launch_zfwd<float>(const ZfwdArgs &, cudaStream_t);
+template cudaError_t launch_zfwd<ff>(const ZfwdArgs &, cudaStream_t);
+template cudaError_t launch_axis<float>(const AxisArgs &, cudaStream_t);
+template cudaError_t launch_axis<ff>(const AxisArgs &, cudaStream_t);
+template cudaError_t launch_xfused<float>(const XfusedArgs &, int, cudaStream_t);
+template cudaError_t launch_xfused<ff>(const XfusedArgs &, int, cudaStream_t);
+template cudaError_t launch_zinv<float>(const ZinvArgs &, int, cudaStream_t);
+template cudaError_t launch_zinv<ff>(const ZinvArgs &, int, cudaStream_t);
+
+}  // namespace bpmf

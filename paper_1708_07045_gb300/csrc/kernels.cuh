@@ -1,0 +1,117 @@
+// Kernel argument blocks and launch wrappers shared by the C-ABI layer and
+// the kernel translation units.
+#pragma once
+#include <cstdint>
+
+#include "fft.cuh"
+
+namespace bpmf {
+
+// Per-configuration placement metadata (computed from the FP32 coordinates).
+struct ConfMeta {
+  float lo[3];   // minimum coordinate per axis (A)
+  int u[3];      // ligand-box extent in nodes for the receptor spacing in use
+  int atom_off;  // first atom of this configuration in the coordinate array
+  int n_atoms;
+  int gamma_off; // first atom of this ligand in the gamma arrays
+  int pad;
+};
+
+// Per (configuration, receptor) site window: output s_d in [0, S_d) maps to
+// translation m_d = w0_d + s_d; s_d is valid when sa_d <= s_d <= sb_d.
+struct PairInfo {
+  int w0[3];
+  int sa[3];
+  int sb[3];
+  int pad;
+};
+
+struct SpreadArgs {
+  const float *coords;     // [atoms][3]
+  const float *gamma;      // [3][total_atoms]
+  int gamma_stride;        // total atoms (channel stride)
+  const ConfMeta *meta;    // [batch]
+  float h_hi, h_lo;        // grid spacing as a float pair
+  int U0, U1, U2;          // ligand-box array dims (max over the batch)
+  float *box;              // [batch][3][U0][U1][U2]
+};
+
+struct ZfwdArgs {          // real rows -> half spectra along the contiguous axis
+  const float *in;
+  long long n_rows;
+  int w_in;                // stored width; zero beyond
+  long long in_stride;     // floats between rows
+  void *out;               // cx<T> rows of F = P/2+1
+  long long out_stride;    // cx<T> elements between rows
+  FftPlan plan;
+  const float4 *tw;
+  int L;                   // complex lines per CTA (2L real rows)
+};
+
+struct AxisArgs {          // C2C along a strided axis, pruned input / output
+  const void *in;
+  void *out;
+  int P, n_in, n_out;
+  long long n_outer, inner;
+  long long in_os, out_os; // cx<T> elements between consecutive outer indices
+  const PairInfo *info;    // output window start w0 = info[o / w0_div].w0[axis]
+  int w0_div, axis;
+  int inverse;
+  FftPlan plan;
+  const float4 *tw;
+  int LW;
+};
+
+struct XfusedArgs {        // x: forward ligand DFT, product with each receptor, inverse, window
+  const void *ly;          // [batch][3][U0][Q] cx<T>
+  int U0;
+  long long Q;
+  int K;
+  const float2 *const *rhi;  // [K] -> [3][P0][Q]
+  const float2 *const *rlo;  // [K] (ff only)
+  void *x2;                // [batch][K][S0][Q] cx<T>
+  int S0;
+  const PairInfo *info;    // [batch][K]
+  FftPlan plan;
+  const float4 *tw;
+  int LW;
+};
+
+struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp partials
+  const void *y2;          // [batch][K][S0][S1][F2] cx<T>
+  int K, S0, S1, S2, F2;
+  const PairInfo *info;    // [batch][K]
+  float nscale_hi, nscale_lo;   // -1 / (kT P0 P1 P2)
+  float escale_hi, escale_lo;   // 1 / (P0 P1 P2) (energy export)
+  float4 *part;            // [batch][K][S0] {M_hi, M_lo, s, 0}
+  double *export_E;        // optional [S0][S1][S2] energies (+inf masked), batch entry 0, receptor 0
+  FftPlan plan;
+  const float4 *tw;
+};
+
+struct MergeArgs {
+  const float4 *part;      // [J][K][S0]
+  const long long *nvalid; // [J][K]
+  int J, K, S0;
+  double kT;
+  double vsite_scale;      // h^3 * C_standard
+  double *logZ;            // [J][K]
+  double *bpmf;            // [K]
+  double *dG;              // [1]
+  long long *nvalid_out;   // [J][K] (may alias caller buffer)
+};
+
+// ---- launch wrappers (kernels.cu) --------------------------------------------
+cudaError_t launch_spread(const SpreadArgs &a, int batch, cudaStream_t st);
+template <class T> cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st);
+template <class T> cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st);
+template <class T> cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st);
+template <class T> cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st);
+cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st);
+cudaError_t launch_split_ff(const void *spec, float2 *hi, float2 *lo, long long n, cudaStream_t st);
+cudaError_t launch_gamma(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, float *gamma,
+                         cudaStream_t st);
+cudaError_t launch_minmax(const float *coords, const int *conf_atom_off, const int *conf_natoms, int n_conf,
+                          float *out_minmax, cudaStream_t st);
+
+}  // namespace bpmf

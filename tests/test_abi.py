@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/bpmf.h declares (CPU only; no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1708_07045_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bpmf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bpmf_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_hot_path_calls():
+    names = _declared()
+    for n in ("bpmf_create", "bpmf_receptor_load", "bpmf_ligand_batch", "bpmf_eval", "bpmf_export_energies",
+              "bpmf_receptor_free", "bpmf_ligand_free", "bpmf_destroy", "bpmf_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(pkg.build())
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(_declared()) == set(pkg._SIGS), "python binding must wrap every C entry point"
+
+
+def test_host_only_entry_points():
+    # pure host functions: no device work
+    assert pkg.bpmf_status_string(0) == "ok"
+    assert "size" in pkg.bpmf_status_string(pkg.BPMF_ERR_SIZE_UNSUPPORTED)
+    assert pkg.bpmf_fft_edge(32) == 32
+    assert pkg.bpmf_fft_edge(96) == 96
+    assert pkg.bpmf_fft_edge(97) == 98      # 2 * 7^2
+
+    def smooth_even(p):
+        if p % 2:
+            return False
+        for r in (2, 3, 5, 7):
+            while p % r == 0:
+                p //= r
+        return p == 1
+
+    for n in range(2, 257):
+        p = pkg.bpmf_fft_edge(n)
+        assert p >= n and smooth_even(p)
+        assert not any(smooth_even(v) for v in range(n, p))
+    assert pkg.bpmf_fft_edge(257) == 0
+
+
+def test_python_binding_rejects_wrong_dtypes():
+    import numpy as np
+    with pytest.raises(TypeError):
+        pkg._ptr(np.zeros(3, dtype=np.float64), np.float32)
+    with pytest.raises(TypeError):
+        pkg._ptr(np.zeros((3, 3), dtype=np.float32).T, np.float32)
