@@ -55,7 +55,7 @@ struct bpmf_lig {
   std::vector<int> n_atoms, n_conf, atom_off, conf_off, coord_off;
   long long total_conf = 0, total_atoms = 0, total_coord_atoms = 0;
   float *coords = nullptr;  // device [coord_atoms][3]
-  float *gamma = nullptr;   // device [3][total_atoms]
+  float2 *gamma = nullptr;  // device [3][total_atoms] float pairs
   std::vector<float> minmax;  // host [total_conf][6]
 };
 
@@ -251,7 +251,7 @@ struct BatchGeom {
 };
 
 size_t batch_bytes_per_conf(const BatchGeom &g, size_t E) {
-  const size_t box = 3ull * g.U[0] * g.U[1] * g.U[2] * 4;
+  const size_t box = 3ull * g.U[0] * g.U[1] * g.U[2] * sizeof(float2);
   const size_t lz = 3ull * g.U[0] * g.U[1] * g.F2 * E;
   const size_t ly = 3ull * g.U[0] * g.Q * E;
   const size_t x2 = (size_t)g.K * g.S[0] * g.Q * E;
@@ -266,8 +266,8 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
                double *export_E, char *ws, cudaStream_t st) {
   const size_t E = sizeof(cx<T>);
   char *p = ws;
-  float *box = reinterpret_cast<float *>(p);
-  p += align_up(3ull * batch * g.U[0] * g.U[1] * g.U[2] * 4);
+  float2 *box = reinterpret_cast<float2 *>(p);
+  p += align_up(3ull * batch * g.U[0] * g.U[1] * g.U[2] * sizeof(float2));
   void *lz = p;
   p += align_up(3ull * batch * g.U[0] * g.U[1] * g.F2 * E);
   void *ly = p;
@@ -282,7 +282,8 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   launch(c, "k_spread", st, [&] { return launch_spread(sa, batch, st); });
 
   ZfwdArgs za{};
-  za.in = box;
+  za.in = reinterpret_cast<const float *>(box);
+  za.in_pairs = 1;
   za.n_rows = 3ll * batch * g.U[0] * g.U[1];
   za.w_in = g.U[2];
   za.in_stride = g.U[2];
@@ -679,7 +680,7 @@ int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_
       throw Fail{BPMF_ERR_INVALID_ARG};
     }
     const size_t na = lg->total_atoms;
-    CK(cudaMalloc(&lg->gamma, 3 * na * sizeof(float)));
+    CK(cudaMalloc(&lg->gamma, 3 * na * sizeof(float2)));
     CK(cudaMalloc(&lg->coords, std::max<size_t>(1, 3 * lg->total_coord_atoms) * sizeof(float)));
     {
       DevIn dq(q, na * sizeof(float), st), de(eps, na * sizeof(float), st), dr(R, na * sizeof(float), st);
@@ -783,6 +784,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     int Umax[3] = {1, 1, 1};
     for (int j = j_first; j < j_first + J; ++j)
       for (int d = 0; d < 3; ++d) Umax[d] = std::max(Umax[d], std::min(meta[j].u[d], r0->P[d]));
+    Umax[1] += Umax[1] & 1;
     for (int j = j_first; j < j_first + J; ++j)
       for (int k = 0; k < K; ++k)
         if (nv[(size_t)j * K + k] == 0) warn = true;
@@ -837,6 +839,9 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         gb.U[d] = 1;
         for (int j = b0; j < b0 + nb; ++j) gb.U[d] = std::max(gb.U[d], std::min(meta[j_first + j].u[d], r0->P[d]));
       }
+      // z rows are transformed in (y, y+1) pairs: an even y extent keeps each
+      // pair inside one plane, so results do not depend on the batching
+      gb.U[1] += gb.U[1] & 1;
       if (use_ff)
         run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * K, d_rptr, d_rptr + K, h, nsh, nsl, esh,
                       esl, d_part + (size_t)b0 * K * S[0], export_E, d_batch, st);

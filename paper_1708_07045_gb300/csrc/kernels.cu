@@ -42,20 +42,30 @@ __device__ __forceinline__ void load_tw(float4 *s_tw, const float4 *tw, int P) {
 
 // --------------------------------------------------------------------------
 // generalised charges (Eqs. electrostatic, repulsive_LJ, attractive_LJ):
-// gamma = (q, sqrt(eps) R^p_rep, sqrt(eps) R^p_att)
-__global__ void k_gamma(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, float *g) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float se = sqrtf(eps[i]);
-  float r = R[i], pr = 1.f, pa = 1.f;
-  for (int k = 0; k < p_rep; ++k) pr = __fmul_rn(pr, r);
-  for (int k = 0; k < p_att; ++k) pa = __fmul_rn(pa, r);
-  g[i] = q[i];
-  g[n + i] = __fmul_rn(se, pr);
-  g[2 * n + i] = __fmul_rn(se, pa);
+// gamma = (q, sqrt(eps) R^p_rep, sqrt(eps) R^p_att), carried as float pairs
+// {hi, lo}: g[t * n + i].
+__device__ __forceinline__ ff ff_sqrt(float a) {
+  const float s = __fsqrt_rn(a);
+  if (s == 0.f) return ff{0.f, 0.f};
+  const float r = __fmaf_rn(-s, s, a);  // exact residual a - s^2
+  return fast_two_sum(s, __fdiv_rn(r, __fmul_rn(2.f, s)));
 }
 
-cudaError_t launch_gamma(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, float *gamma,
+__global__ void k_gamma(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, float2 *g) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ff se = ff_sqrt(eps[i]);
+  const ff r{R[i], 0.f};
+  ff pr{1.f, 0.f}, pa{1.f, 0.f};
+  for (int k = 0; k < p_rep; ++k) pr = s_mul(pr, r);
+  for (int k = 0; k < p_att; ++k) pa = s_mul(pa, r);
+  const ff gr = s_mul(se, pr), ga = s_mul(se, pa);
+  g[i] = make_float2(q[i], 0.f);
+  g[n + i] = make_float2(gr.hi, gr.lo);
+  g[2 * n + i] = make_float2(ga.hi, ga.lo);
+}
+
+cudaError_t launch_gamma(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, float2 *gamma,
                          cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_gamma<<<(n + 127) / 128, 128, 0, st>>>(q, eps, R, n, p_rep, p_att, gamma);
@@ -90,9 +100,10 @@ cudaError_t launch_minmax(const float *coords, const int *off, const int *nat, i
 // (a) spreading.  CTA = (configuration, x-plane of the ligand box).  Each atom
 // is placed (lowest coordinate 2 spacings above plane 0) with its grid-unit
 // position carried as a float pair, then its 8 trilinear corner weights times
-// gamma_t are accumulated in shared memory.  Accumulation is in 64-bit fixed
-// point (per-channel power-of-two scale from sum |gamma|), so the result is
-// exact, order independent and deterministic; it is rounded to FP32 once.
+// gamma_t (float-pair products) are accumulated in shared memory in 64-bit
+// fixed point (per-channel power-of-two scale from sum |gamma|): the sums are
+// exact, order independent and deterministic.  Each node is written once as a
+// float pair {hi, lo}.
 constexpr int kMaxAtoms = 256;
 
 __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
@@ -100,7 +111,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
   const int j = blockIdx.y;
   const ConfMeta m = a.meta[j];
   __shared__ int s_c[kMaxAtoms][3];
-  __shared__ float s_f[kMaxAtoms][3];
+  __shared__ ff s_f[kMaxAtoms][3];
   __shared__ float s_red[3][8];
   __shared__ int s_e[3];
   extern __shared__ unsigned long long s_plane[];  // [U1][U2]
@@ -120,8 +131,9 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
       ff g = s_add(fast_two_sum(q1, q2), ff{2.f, 0.f});
       float c = floorf(g.hi);
       if (g.hi == c && g.lo < 0.f) c -= 1.f;
-      float f = __fadd_rn(__fsub_rn(g.hi, c), g.lo);
-      f = fminf(fmaxf(f, 0.f), 1.f);
+      ff f = two_sum(__fsub_rn(g.hi, c), g.lo);  // g.hi - c is exact
+      if (f.hi < 0.f) f = ff{0.f, 0.f};
+      if (f.hi > 1.f || (f.hi == 1.f && f.lo > 0.f)) f = ff{1.f, 0.f};
       s_c[i][d] = (int)c;
       s_f[i][d] = f;
     }
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
   // per-channel fixed-point scale
   float sa[3] = {0.f, 0.f, 0.f};
   for (int i = threadIdx.x; i < n; i += blockDim.x)
-    for (int t = 0; t < 3; ++t) sa[t] += fabsf(a.gamma[(long long)t * a.gamma_stride + m.gamma_off + i]);
+    for (int t = 0; t < 3; ++t) sa[t] += fabsf(a.gamma[(long long)t * a.gamma_stride + m.gamma_off + i].x);
   for (int t = 0; t < 3; ++t) {
     float v = sa[t];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -139,11 +151,12 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
   if (threadIdx.x < 3) {
     float v = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_red[threadIdx.x][w];
-    // 2^e * (sum |gamma| * 1.01) < 2^61 keeps every partial sum in range
-    s_e[threadIdx.x] = v > 0.f ? 60 - ilogbf(v * 1.01f) - 1 : 0;
+    // 2^e * (sum |gamma| * 1.01) < 2^60 keeps every partial sum in range
+    s_e[threadIdx.x] = v > 0.f ? 59 - ilogbf(v * 1.01f) : 0;
   }
   __syncthreads();
   const int plane = a.U1 * a.U2;
+  const ff one{1.f, 0.f};
   for (int t = 0; t < 3; ++t) {
     for (int i = threadIdx.x; i < plane; i += blockDim.x) s_plane[i] = 0ull;
     __syncthreads();
@@ -151,19 +164,23 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
     for (int it = threadIdx.x; it < n * 8; it += blockDim.x) {
       const int i = it >> 3, dx = (it >> 2) & 1, dy = (it >> 1) & 1, dz = it & 1;
       if (s_c[i][0] + dx != ix) continue;
-      const float wx = dx ? s_f[i][0] : 1.f - s_f[i][0];
-      const float wy = dy ? s_f[i][1] : 1.f - s_f[i][1];
-      const float wz = dz ? s_f[i][2] : 1.f - s_f[i][2];
-      const float gm = a.gamma[(long long)t * a.gamma_stride + m.gamma_off + i];
-      const float v = __fmul_rn(__fmul_rn(__fmul_rn(wx, wy), wz), gm);
-      const long long iv = __float2ll_rn(ldexpf(v, e));
+      const ff wx = dx ? s_f[i][0] : s_sub(one, s_f[i][0]);
+      const ff wy = dy ? s_f[i][1] : s_sub(one, s_f[i][1]);
+      const ff wz = dz ? s_f[i][2] : s_sub(one, s_f[i][2]);
+      const float2 g2 = a.gamma[(long long)t * a.gamma_stride + m.gamma_off + i];
+      const ff v = s_mul(s_mul(s_mul(wx, wy), wz), ff{g2.x, g2.y});
+      const long long iv = __float2ll_rn(ldexpf(v.hi, e)) + __float2ll_rn(ldexpf(v.lo, e));
       const int y = s_c[i][1] + dy, z = s_c[i][2] + dz;
       if (y < a.U1 && z < a.U2) atomicAdd(&s_plane[y * a.U2 + z], (unsigned long long)iv);
     }
     __syncthreads();
-    float *dst = a.box + (((long long)j * 3 + t) * a.U0 + ix) * plane;
-    for (int i = threadIdx.x; i < plane; i += blockDim.x)
-      dst[i] = ldexpf(__ll2float_rn((long long)s_plane[i]), -e);
+    float2 *dst = a.box + (((long long)j * 3 + t) * a.U0 + ix) * plane;
+    for (int i = threadIdx.x; i < plane; i += blockDim.x) {
+      const long long v = (long long)s_plane[i];
+      const float hi = __ll2float_rn(v);
+      const float lo = __ll2float_rn(v - __float2ll_rn(hi));  // exact remainder, then rounded
+      dst[i] = make_float2(ldexpf(hi, -e), ldexpf(lo, -e));
+    }
     __syncthreads();
   }
 }
@@ -193,12 +210,18 @@ __global__ void __launch_bounds__(256) k_zfwd(ZfwdArgs a) {
   for (int idx = threadIdx.x; idx < L * P; idx += blockDim.x) {
     const int l = idx / P, n = idx % P;
     const long long ra = r0 + 2 * l, rb = ra + 1;
-    float va = 0.f, vb = 0.f;
+    float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
     if (n < a.w_in) {
-      if (ra < a.n_rows) va = a.in[ra * a.in_stride + n];
-      if (rb < a.n_rows) vb = a.in[rb * a.in_stride + n];
+      if (a.in_pairs) {
+        const float2 *in2 = reinterpret_cast<const float2 *>(a.in);
+        if (ra < a.n_rows) va = in2[ra * a.in_stride + n];
+        if (rb < a.n_rows) vb = in2[rb * a.in_stride + n];
+      } else {
+        if (ra < a.n_rows) va.x = a.in[ra * a.in_stride + n];
+        if (rb < a.n_rows) vb.x = a.in[rb * a.in_stride + n];
+      }
     }
-    b0[l * ls + n] = cx<T>{s_from<T>(va), s_from<T>(vb)};
+    b0[l * ls + n] = cx<T>{s_mk<T>(va.x, va.y), s_mk<T>(vb.x, vb.y)};
   }
   __syncthreads();
   cx<T> *res = cta_fft<T>(b0, b1, 1, ls, L, a.plan, s_tw, false);

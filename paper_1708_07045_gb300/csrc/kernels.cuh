@@ -28,19 +28,20 @@ struct PairInfo {
 
 struct SpreadArgs {
   const float *coords;     // [atoms][3]
-  const float *gamma;      // [3][total_atoms]
+  const float2 *gamma;     // [3][total_atoms] float pairs
   int gamma_stride;        // total atoms (channel stride)
   const ConfMeta *meta;    // [batch]
   float h_hi, h_lo;        // grid spacing as a float pair
   int U0, U1, U2;          // ligand-box array dims (max over the batch)
-  float *box;              // [batch][3][U0][U1][U2]
+  float2 *box;             // [batch][3][U0][U1][U2] float pairs
 };
 
 struct ZfwdArgs {          // real rows -> half spectra along the contiguous axis
-  const float *in;
+  const float *in;         // rows of floats, or of float pairs when in_pairs
+  int in_pairs;
   long long n_rows;
   int w_in;                // stored width; zero beyond
-  long long in_stride;     // floats between rows
+  long long in_stride;     // elements (floats or pairs) between rows
   void *out;               // cx<T> rows of F = P/2+1
   long long out_stride;    // cx<T> elements between rows
   FftPlan plan;
@@ -109,7 +110,7 @@ template <class T> cudaError_t launch_xfused(const XfusedArgs &a, int batch, cud
 template <class T> cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st);
 cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st);
 cudaError_t launch_split_ff(const void *spec, float2 *hi, float2 *lo, long long n, cudaStream_t st);
-cudaError_t launch_gamma(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, float *gamma,
+cudaError_t launch_gamma(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, float2 *gamma,
                          cudaStream_t st);
 cudaError_t launch_minmax(const float *coords, const int *conf_atom_off, const int *conf_natoms, int n_conf,
                           float *out_minmax, cudaStream_t st);
