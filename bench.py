@@ -260,7 +260,7 @@ def run_ours(args):
     clk = clocks.stop()
     res_chosen = {k: v.cpu().numpy() for k, v in outs.items()}
     other = "fp32" if chosen == "ff" else "ff"
-    t_other, _, _ = timed(modes[other], max(1, args.steps // 2), 1)
+    t_other, _, prof_other = timed(modes[other], max(1, args.steps // 2), 1, prof=True)
     res_other = {k: v.cpu().numpy() for k, v in outs.items()}
 
     n_poses = int(res_chosen["n_valid"].sum())
@@ -342,6 +342,7 @@ def run_ours(args):
                 "fp32_path": {"value": n_poses * world / (t_other / 1e3) if other == "fp32" else None,
                               "ms_per_step": t_other if other == "fp32" else None},
                 "ff_path": {"ms_per_step": t_other} if other == "ff" else {"ms_per_step": t_ms},
+                "kernels_ms_per_step_other_form": {k: v[0] / max(1, args.steps // 2) for k, v in prof_other.items()},
                 "accuracy_vs_oracle": acc,
                 "e2e": {"value": n_poses * world / e2e_t, "unit": "pose energies/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_t * 1e3},
@@ -364,7 +365,11 @@ def main():
     ap.add_argument("--mode", default="ff", choices=["ff", "fp32"])
     ap.add_argument("--ref-sample", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-conf", type=int, default=N_CONF,
+                    help="configurations per step (default: the full workload; smaller values are for profiling)")
     args = ap.parse_args()
+    global N_CONF
+    N_CONF = args.n_conf
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

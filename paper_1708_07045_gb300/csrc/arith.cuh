@@ -82,14 +82,32 @@ template <class T>
 __device__ __forceinline__ cx<T> c_sub(cx<T> a, cx<T> b) {
   return cx<T>{s_sub(a.re, b.re), s_sub(a.im, b.im)};
 }
+// a*b + c*d for float pairs with one TwoSum: both products' error terms and
+// the cross terms are gathered by FMA before a single renormalisation.
+__device__ __forceinline__ ff ff_dot2(ff a, ff b, ff c, ff d) {
+  const float p1 = __fmul_rn(a.hi, b.hi);
+  float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  e1 = __fmaf_rn(a.hi, b.lo, e1);
+  e1 = __fmaf_rn(a.lo, b.hi, e1);
+  const float p2 = __fmul_rn(c.hi, d.hi);
+  float e2 = __fmaf_rn(c.hi, d.hi, -p2);
+  e2 = __fmaf_rn(c.hi, d.lo, e2);
+  e2 = __fmaf_rn(c.lo, d.hi, e2);
+  const ff s = two_sum(p1, p2);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e1, e2)));
+}
+__device__ __forceinline__ float ff_dot2(float a, float b, float c, float d) {
+  return __fmaf_rn(a, b, __fmul_rn(c, d));
+}
+
 template <class T>
 __device__ __forceinline__ cx<T> c_mul(cx<T> a, cx<T> b) {
-  return cx<T>{s_sub(s_mul(a.re, b.re), s_mul(a.im, b.im)), s_add(s_mul(a.re, b.im), s_mul(a.im, b.re))};
+  return cx<T>{ff_dot2(a.re, b.re, s_neg(a.im), b.im), ff_dot2(a.re, b.im, a.im, b.re)};
 }
 // a * conj(b)
 template <class T>
 __device__ __forceinline__ cx<T> c_mulconj(cx<T> a, cx<T> b) {
-  return cx<T>{s_add(s_mul(a.re, b.re), s_mul(a.im, b.im)), s_sub(s_mul(a.im, b.re), s_mul(a.re, b.im))};
+  return cx<T>{ff_dot2(a.re, b.re, a.im, b.im), ff_dot2(a.im, b.re, s_neg(a.re), b.im)};
 }
 template <class T>
 __device__ __forceinline__ cx<T> c_conj(cx<T> a) {

@@ -164,6 +164,13 @@ void *workspace(bpmf_ctx *c, size_t bytes, cudaStream_t st) {
 
 inline size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
+// lines per CTA for a strided pass over `inner` columns: at most `cap`, with
+// the columns split into equal tiles
+int pick_lw(long long inner, int cap = 16) {
+  const long long nt = (inner + cap - 1) / cap;
+  return (int)((inner + nt - 1) / nt);
+}
+
 cudaEvent_t pool_event(bpmf_ctx *c) {
   if (!c->event_pool.empty()) {
     cudaEvent_t e = c->event_pool.back();
@@ -178,13 +185,20 @@ cudaEvent_t pool_event(bpmf_ctx *c) {
 // Launch `fn` (returning cudaError_t); when profiling, bracket it with events.
 template <class F>
 void launch(bpmf_ctx *c, const char *name, cudaStream_t st, F &&fn) {
+  auto run = [&] {
+    cudaError_t e = fn();
+    if (e != cudaSuccess) {
+      last_msg = std::string(name) + ": " + cudaGetErrorString(e);
+      throw Fail{e == cudaErrorMemoryAllocation ? BPMF_ERR_OOM : BPMF_ERR_CUDA};
+    }
+  };
   if (!c->prof) {
-    CK(fn());
+    run();
     return;
   }
   ProfRec r{name, pool_event(c), pool_event(c)};
   CK(cudaEventRecord(r.a, st));
-  CK(fn());
+  run();
   CK(cudaEventRecord(r.b, st));
   c->pending.push_back(r);
 }
@@ -310,7 +324,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   ya.inverse = 0;
   ya.plan = make_plan(g.P[1]);
   ya.tw = twiddles(c, g.P[1]);
-  ya.LW = 16;
+  ya.LW = pick_lw(ya.inner);
   launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y fwd)" : "k_axis<ff>(y fwd)", st, [&] { return launch_axis<T>(ya, st); });
 
   XfusedArgs xa{};
@@ -344,7 +358,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   yi.inverse = 1;
   yi.plan = make_plan(g.P[1]);
   yi.tw = twiddles(c, g.P[1]);
-  yi.LW = 16;
+  yi.LW = pick_lw(yi.inner);
   launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y inv)" : "k_axis<ff>(y inv)", st, [&] { return launch_axis<T>(yi, st); });
 
   ZinvArgs zi{};
@@ -588,7 +602,7 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
     ya.axis = 1;
     ya.plan = make_plan(P[1]);
     ya.tw = twiddles(c, P[1]);
-    ya.LW = 16;
+    ya.LW = pick_lw(ya.inner);
     launch(c, "k_axis<ff>(receptor y)", st, [&] { return launch_axis<ff>(ya, st); });
     // x
     AxisArgs xa{};
@@ -798,12 +812,34 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     g.Q = r0->Q;
     g.K = K;
     const size_t per_conf = batch_bytes_per_conf(g, E);
+    // configurations are processed sorted by ligand-box extent, so each batch's
+    // box (the maximum over its members) stays tight; the merge scatters the
+    // results back to the caller's order
+    std::vector<int> order(J);
+    for (int i = 0; i < J; ++i) order[i] = j_first + i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      for (int d = 0; d < 3; ++d)
+        if (meta[a].u[d] != meta[b].u[d]) return meta[a].u[d] < meta[b].u[d];
+      return false;
+    });
+    std::vector<ConfMeta> meta_s(std::max(J, 1));
+    std::vector<PairInfo> info_s((size_t)std::max(J, 1) * K);
+    std::vector<long long> nv_s((size_t)std::max(J, 1) * K);
+    std::vector<int> ord_s(std::max(J, 1));
+    for (int i = 0; i < J; ++i) {
+      meta_s[i] = meta[order[i]];
+      ord_s[i] = order[i] - j_first;
+      for (int k = 0; k < K; ++k) {
+        info_s[(size_t)i * K + k] = info[(size_t)order[i] * K + k];
+        nv_s[(size_t)i * K + k] = nv[(size_t)order[i] * K + k];
+      }
+    }
     // fixed part of the workspace: tables, partials, merge outputs
     const size_t JK = (size_t)std::max(J, 1) * K;
     const size_t fixed = align_up(sizeof(ConfMeta) * std::max(J, 1)) + align_up(sizeof(PairInfo) * JK) +
-                         align_up(sizeof(long long) * JK) + align_up(sizeof(float4) * JK * S[0]) +
-                         align_up(sizeof(double) * 2 * JK) + align_up(sizeof(double) * (K + 1)) +
-                         align_up(2 * sizeof(void *) * K);
+                         align_up(sizeof(long long) * JK) * 2 + align_up(sizeof(float4) * JK * S[0]) +
+                         align_up(sizeof(double) * JK) * 2 + align_up(sizeof(double) * (K + 1)) +
+                         align_up(2 * sizeof(void *) * K) + align_up(sizeof(int) * std::max(J, 1));
     int B = (int)std::max<size_t>(1, (c->ws_budget > fixed ? c->ws_budget - fixed : 0) / per_conf);
     B = std::min(B, std::max(J, 1));
     char *ws = static_cast<char *>(workspace(c, fixed + per_conf * B, st));
@@ -812,23 +848,28 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     p += align_up(sizeof(ConfMeta) * std::max(J, 1));
     PairInfo *d_info = reinterpret_cast<PairInfo *>(p);
     p += align_up(sizeof(PairInfo) * JK);
-    long long *d_nv = reinterpret_cast<long long *>(p);
+    long long *d_nv = reinterpret_cast<long long *>(p);  // processing order
+    p += align_up(sizeof(long long) * JK);
+    long long *d_nvout = reinterpret_cast<long long *>(p);  // caller order
     p += align_up(sizeof(long long) * JK);
     float4 *d_part = reinterpret_cast<float4 *>(p);
     p += align_up(sizeof(float4) * JK * S[0]);
-    double *d_logZ = reinterpret_cast<double *>(p);  // + logS scratch
-    p += align_up(sizeof(double) * 2 * JK);
+    double *d_logZ = reinterpret_cast<double *>(p);
+    p += align_up(sizeof(double) * JK);
+    double *d_logS = reinterpret_cast<double *>(p);
+    p += align_up(sizeof(double) * JK);
     double *d_B = reinterpret_cast<double *>(p);  // [K] + dG
     p += align_up(sizeof(double) * (K + 1));
     const float2 **d_rptr = reinterpret_cast<const float2 **>(p);
     p += align_up(2 * sizeof(void *) * K);
+    int *d_order = reinterpret_cast<int *>(p);
+    p += align_up(sizeof(int) * std::max(J, 1));
     char *d_batch = p;
     if (J > 0) {
-      CK(cudaMemcpyAsync(d_meta, meta.data() + j_first, sizeof(ConfMeta) * J, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(d_info, info.data() + (size_t)j_first * K, sizeof(PairInfo) * J * K,
-                         cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(d_nv, nv.data() + (size_t)j_first * K, sizeof(long long) * J * K, cudaMemcpyHostToDevice,
-                         st));
+      CK(cudaMemcpyAsync(d_meta, meta_s.data(), sizeof(ConfMeta) * J, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_info, info_s.data(), sizeof(PairInfo) * J * K, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_nv, nv_s.data(), sizeof(long long) * J * K, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(d_order, ord_s.data(), sizeof(int) * J, cudaMemcpyHostToDevice, st));
     }
     CK(cudaMemcpyAsync(d_rptr, hrhi.data(), sizeof(void *) * K, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_rptr + K, hrlo.data(), sizeof(void *) * K, cudaMemcpyHostToDevice, st));
@@ -837,7 +878,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       BatchGeom gb = g;
       for (int d = 0; d < 3; ++d) {
         gb.U[d] = 1;
-        for (int j = b0; j < b0 + nb; ++j) gb.U[d] = std::max(gb.U[d], std::min(meta[j_first + j].u[d], r0->P[d]));
+        for (int j = b0; j < b0 + nb; ++j) gb.U[d] = std::max(gb.U[d], std::min(meta_s[j].u[d], r0->P[d]));
       }
       // z rows are transformed in (y, y+1) pairs: an even y extent keeps each
       // pair inside one plane, so results do not depend on the batching
@@ -858,15 +899,17 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     ma.S0 = S[0];
     ma.kT = kT;
     ma.vsite_scale = h * h * h / 1660.5390;
+    ma.order = d_order;
+    ma.logS = d_logS;
     ma.logZ = d_logZ;
     ma.bpmf = d_B;
     ma.dG = d_B + K;
-    ma.nvalid_out = nullptr;
+    ma.nvalid_out = d_nvout;
     launch(c, "k_merge", st, [&] { return launch_merge(ma, st); });
     const long long ob = conf_base;
     if (J > 0) {
       CK(cudaMemcpyAsync(logZ + ob * K, d_logZ, sizeof(double) * J * K, cudaMemcpyDefault, st));
-      if (n_valid) CK(cudaMemcpyAsync(n_valid + ob * K, d_nv, sizeof(int64_t) * J * K, cudaMemcpyDefault, st));
+      if (n_valid) CK(cudaMemcpyAsync(n_valid + ob * K, d_nvout, sizeof(int64_t) * J * K, cudaMemcpyDefault, st));
     }
     if (bpmf_out) CK(cudaMemcpyAsync(bpmf_out + (size_t)li * K, d_B, sizeof(double) * K, cudaMemcpyDefault, st));
     if (dG) CK(cudaMemcpyAsync(dG + li, d_B + K, sizeof(double), cudaMemcpyDefault, st));

@@ -64,8 +64,19 @@ __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, 
       v[2 * m] = a[m];
       v[2 * m + 1] = b[m];
     }
+  } else if constexpr (R == 3) {
+    // X0 = a + (b + c);  X1,2 = a - (b + c)/2 -/+ i (sqrt(3)/2)(b - c)  (forward)
+    const float4 q = tw[P / 3];                  // exp(-2 pi i / 3) = (-1/2, -sqrt(3)/2)
+    const T s3 = s_neg(s_mk<T>(q.y, q.w));       // sqrt(3)/2 as hi/lo
+    const T half = s_mk<T>(0.5f, 0.f);
+    const cx<T> sp = c_add(v[1], v[2]), sm = c_sub(v[1], v[2]);
+    const cx<T> t1 = c_sub(v[0], cx<T>{s_mul(sp.re, half), s_mul(sp.im, half)});
+    const cx<T> t2 = c_rot(cx<T>{s_mul(sm.re, s3), s_mul(sm.im, s3)}, inv);  // -i t (fwd), +i t (inv)
+    v[0] = c_add(v[0], sp);
+    v[1] = c_add(t1, t2);
+    v[2] = c_sub(t1, t2);
   } else {
-    // odd radix: X[a] = sum_b v[b] w_R^(a b), w_R^m = tw[m P / R]
+    // radix 5, 7: X[a] = sum_b v[b] w_R^(a b), w_R^m = tw[m P / R]
     cx<T> out[R];
     const int st = P / R;
 #pragma unroll

@@ -17,6 +17,17 @@ __device__ __forceinline__ int imod(int a, int m) {
   return r < 0 ? r + m : r;
 }
 
+// Threads per CTA and minimum resident CTAs per SM: float-pair kernels use
+// smaller CTAs capped at 128 registers so that 4 can share an SM.
+template <class T>
+struct KCfg {
+  static constexpr int threads = 256, min_blocks = 2;
+};
+template <>
+struct KCfg<ff> {
+  static constexpr int threads = 128, min_blocks = 4;
+};
+
 template <class T>
 __device__ __forceinline__ void st_cx(void *base, long long idx, cx<T> v) {
   reinterpret_cast<cx<T> *>(base)[idx] = v;
@@ -188,10 +199,9 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
 cudaError_t launch_spread(const SpreadArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   const size_t smem = sizeof(unsigned long long) * (size_t)a.U1 * a.U2;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  // static + dynamic shared memory may pass the 48 KB default: always opt in
+  cudaError_t e = cudaFuncSetAttribute(k_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   k_spread<<<dim3(a.U0, batch), 256, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -199,7 +209,7 @@ cudaError_t launch_spread(const SpreadArgs &a, int batch, cudaStream_t st) {
 // --------------------------------------------------------------------------
 // (b) R2C along the contiguous axis: two real rows packed as one complex line.
 template <class T>
-__global__ void __launch_bounds__(256) k_zfwd(ZfwdArgs a) {
+__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zfwd(ZfwdArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, L = a.L, ls = P + 1, F = P / 2 + 1;
   float4 *s_tw = smem;
@@ -246,14 +256,14 @@ cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long blocks = (a.n_rows + 2 * a.L - 1) / (2 * a.L);
-  k_zfwd<T><<<(unsigned)blocks, 256, smem, st>>>(a);
+  k_zfwd<T><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------
 // C2C along a strided axis for a tile of LW consecutive innermost indices.
 template <class T>
-__global__ void __launch_bounds__(256) k_axis(AxisArgs a) {
+__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_axis(AxisArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, LW = a.LW;
   float4 *s_tw = smem;
@@ -288,7 +298,7 @@ cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long blocks = a.n_outer * ((a.inner + a.LW - 1) / a.LW);
-  k_axis<T><<<(unsigned)blocks, 256, smem, st>>>(a);
+  k_axis<T><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -298,7 +308,7 @@ cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
 // for each receptor k: P_k = sum_t R_{k,t} conj(L_t), inverse DFT, keep the
 // site window along x.  The ligand spectrum never leaves shared memory.
 template <class T>
-__global__ void __launch_bounds__(256) k_xfused(XfusedArgs a) {
+__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfused(XfusedArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, LW = a.LW, L3 = 3 * LW;
   float4 *s_tw = smem;
@@ -355,7 +365,7 @@ cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_xfused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long blocks = (long long)batch * ((a.Q + a.LW - 1) / a.LW);
-  k_xfused<T><<<(unsigned)blocks, 256, smem, st>>>(a);
+  k_xfused<T><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -366,7 +376,7 @@ __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi 
 __device__ __forceinline__ bool ff_gt(float a, float b) { return a > b; }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_zinv(ZinvArgs a) {
+__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zinv(ZinvArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, F = a.F2, ls = P + 1;
   const int L = (a.S1 + 1) / 2;
@@ -467,7 +477,7 @@ cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st) {
   const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)L * (P + 1) + sizeof(T) * (size_t)a.S1 * a.S2;
   cudaError_t e = cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_zinv<T><<<(unsigned)((long long)batch * a.K * a.S0), 256, smem, st>>>(a);
+  k_zinv<T><<<(unsigned)((long long)batch * a.K * a.S0), KCfg<T>::threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -494,8 +504,10 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a, double *logS) {
     const long long n = a.nvalid[p];
     const double ls = (s > 0.0 && n > 0) ? Mx + log(s) : -CUDART_INF;
     logS[p] = ls;
-    a.logZ[p] = n > 0 ? ls - log((double)n) : -CUDART_INF;
-    if (a.nvalid_out) a.nvalid_out[p] = n;
+    // sorted position -> caller's configuration order
+    const long long q = (long long)(a.order ? a.order[p / a.K] : p / a.K) * a.K + p % a.K;
+    a.logZ[q] = n > 0 ? ls - log((double)n) : -CUDART_INF;
+    if (a.nvalid_out) a.nvalid_out[q] = n;
   }
   __syncthreads();
   long long ntot_all = 0;
@@ -552,9 +564,7 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a, double *logS) {
 }
 
 cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st) {
-  // logS scratch lives right after logZ's J*K entries in the caller's device
-  // workspace; the C-ABI layer passes it through logZ + J*K.
-  k_merge<<<1, 256, 0, st>>>(a, a.logZ + (long long)a.J * a.K);
+  k_merge<<<1, 256, 0, st>>>(a, a.logS);
   return cudaGetLastError();
 }
 

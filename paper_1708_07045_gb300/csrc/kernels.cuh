@@ -91,15 +91,17 @@ struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp pa
 };
 
 struct MergeArgs {
-  const float4 *part;      // [J][K][S0]
-  const long long *nvalid; // [J][K]
+  const float4 *part;      // [J][K][S0], configurations in processing order
+  const long long *nvalid; // [J][K], processing order
+  const int *order;        // [J] processing position -> caller's configuration index (null: identity)
+  double *logS;            // [J][K] scratch
   int J, K, S0;
   double kT;
   double vsite_scale;      // h^3 * C_standard
-  double *logZ;            // [J][K]
+  double *logZ;            // [J][K], caller's order
   double *bpmf;            // [K]
   double *dG;              // [1]
-  long long *nvalid_out;   // [J][K] (may alias caller buffer)
+  long long *nvalid_out;   // [J][K], caller's order (may be null)
 };
 
 // ---- launch wrappers (kernels.cu) --------------------------------------------
