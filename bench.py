@@ -357,6 +357,7 @@ def run_ours(args):
 
 
 def main():
+    global N_CONF
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -368,7 +369,6 @@ def main():
     ap.add_argument("--n-conf", type=int, default=N_CONF,
                     help="configurations per step (default: the full workload; smaller values are for profiling)")
     args = ap.parse_args()
-    global N_CONF
     N_CONF = args.n_conf
     if args.impl == "reference":
         return run_reference(args)
