@@ -15,6 +15,8 @@
 //
 // Every operation uses the explicit round-to-nearest intrinsics so that the
 // compiler cannot contract or reassociate the error-free transformations.
+// Adds and multiplies return lazily normalised pairs; values are renormalised
+// once per butterfly output and before every store.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -31,6 +33,7 @@ __device__ __forceinline__ float s_mul(float a, float b) { return __fmul_rn(a, b
 __device__ __forceinline__ float s_neg(float a) { return -a; }
 __device__ __forceinline__ float s_hi(float a) { return a; }
 __device__ __forceinline__ float s_lo(float) { return 0.f; }
+__device__ __forceinline__ float s_norm(float a) { return a; }
 
 // ---- ff ------------------------------------------------------------------
 __device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
@@ -44,19 +47,23 @@ __device__ __forceinline__ ff two_sum(float a, float b) {
   float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
   return ff{s, e};
 }
+// Lazy float-pair add: the error-free sum of the high parts plus both low
+// parts, NOT renormalised (|lo| may reach a few ulp(hi)); every operation
+// below accepts such operands, and s_norm renormalises where a canonical pair
+// is needed (shared / global stores, comparisons).
 __device__ __forceinline__ ff s_add(ff a, ff b) {
   ff s = two_sum(a.hi, b.hi);
-  float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
-  return fast_two_sum(s.hi, e);
+  return ff{s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
 }
+__device__ __forceinline__ ff s_norm(ff a) { return fast_two_sum(a.hi, a.lo); }
 __device__ __forceinline__ ff s_neg(ff a) { return ff{-a.hi, -a.lo}; }
 __device__ __forceinline__ ff s_sub(ff a, ff b) { return s_add(a, s_neg(b)); }
-__device__ __forceinline__ ff s_mul(ff a, ff b) {
+__device__ __forceinline__ ff s_mul(ff a, ff b) {  // lazy, like s_add
   float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
-  return fast_two_sum(p, e);
+  return ff{p, e};
 }
 __device__ __forceinline__ float s_hi(ff a) { return a.hi; }
 __device__ __forceinline__ float s_lo(ff a) { return a.lo; }
@@ -94,7 +101,7 @@ __device__ __forceinline__ ff ff_dot2(ff a, ff b, ff c, ff d) {
   e2 = __fmaf_rn(c.hi, d.lo, e2);
   e2 = __fmaf_rn(c.lo, d.hi, e2);
   const ff s = two_sum(p1, p2);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e1, e2)));
+  return ff{s.hi, __fadd_rn(s.lo, __fadd_rn(e1, e2))};  // lazy
 }
 __device__ __forceinline__ float ff_dot2(float a, float b, float c, float d) {
   return __fmaf_rn(a, b, __fmul_rn(c, d));
@@ -121,6 +128,10 @@ __device__ __forceinline__ cx<T> c_rot(cx<T> a, bool inverse) {
 template <class T>
 __device__ __forceinline__ cx<T> c_scale(cx<T> a, T s) {
   return cx<T>{s_mul(a.re, s), s_mul(a.im, s)};
+}
+template <class T>
+__device__ __forceinline__ cx<T> c_norm(cx<T> a) {
+  return cx<T>{s_norm(a.re), s_norm(a.im)};
 }
 template <class T>
 __device__ __forceinline__ cx<T> c_zero() {

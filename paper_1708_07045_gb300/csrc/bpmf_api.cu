@@ -339,7 +339,6 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   xa.info = d_info;
   xa.plan = make_plan(g.P[0]);
   xa.tw = twiddles(c, g.P[0]);
-  xa.LW = sizeof(T) == 4 ? 16 : 8;
   launch(c, sizeof(T) == 4 ? "k_xfused<fp32>" : "k_xfused<ff>", st, [&] { return launch_xfused<T>(xa, batch, st); });
 
   AxisArgs yi{};

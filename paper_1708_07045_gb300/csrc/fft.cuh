@@ -91,9 +91,10 @@ __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, 
   }
 }
 
-template <class T, int R>
-__device__ __forceinline__ void fft_stage(const cx<T> *src, cx<T> *dst, int es, int ls, int nlines, int P, int Ns,
+template <class T, int R, int NL>
+__device__ __forceinline__ void fft_stage(const cx<T> *src, cx<T> *dst, int es, int ls, int nlines_rt, int P, int Ns,
                                           const float4 *tw, bool inv) {
+  const int nlines = NL > 0 ? NL : nlines_rt;  // compile-time line count when given
   const int nb = P / R;
   const int items = nb * nlines;
   const int tstride = P / (Ns * R);
@@ -110,14 +111,15 @@ __device__ __forceinline__ void fft_stage(const cx<T> *src, cx<T> *dst, int es, 
     dft_small<T, R>(v, inv, tw, P);
     const int o = (i / Ns) * Ns * R + j;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[(o + r * Ns) * es + l * ls] = v[r];
+    for (int r = 0; r < R; ++r) dst[(o + r * Ns) * es + l * ls] = c_norm(v[r]);
   }
 }
 
 // Transforms nlines lines in place-by-ping-pong.  Data must be in b0 and
 // visible to the CTA (caller syncs before).  Returns the buffer holding the
-// result; the CTA is synchronised on return.
-template <class T>
+// result; the CTA is synchronised on return.  NL > 0 fixes the line count at
+// compile time (it must equal nlines).
+template <class T, int NL = 0>
 __device__ cx<T> *cta_fft(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, const FftPlan &pl, const float4 *tw,
                           bool inv) {
   int Ns = 1;
@@ -125,12 +127,12 @@ __device__ cx<T> *cta_fft(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, cons
   for (int s = 0; s < pl.nst; ++s) {
     const int R = pl.r[s];
     switch (R) {
-      case 8: fft_stage<T, 8>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
-      case 4: fft_stage<T, 4>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
-      case 2: fft_stage<T, 2>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
-      case 3: fft_stage<T, 3>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
-      case 5: fft_stage<T, 5>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
-      default: fft_stage<T, 7>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      case 8: fft_stage<T, 8, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      case 4: fft_stage<T, 4, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      case 2: fft_stage<T, 2, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      case 3: fft_stage<T, 3, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      case 5: fft_stage<T, 5, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
+      default: fft_stage<T, 7, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
     }
     __syncthreads();
     cx<T> *t = src;

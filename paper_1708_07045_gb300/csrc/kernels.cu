@@ -21,16 +21,16 @@ __device__ __forceinline__ int imod(int a, int m) {
 // smaller CTAs capped at 128 registers so that 4 can share an SM.
 template <class T>
 struct KCfg {
-  static constexpr int threads = 256, min_blocks = 2;
+  static constexpr int threads = 256, min_blocks = 2, xlw = 16;
 };
 template <>
 struct KCfg<ff> {
-  static constexpr int threads = 128, min_blocks = 4;
+  static constexpr int threads = 128, min_blocks = 4, xlw = 8;
 };
 
 template <class T>
 __device__ __forceinline__ void st_cx(void *base, long long idx, cx<T> v) {
-  reinterpret_cast<cx<T> *>(base)[idx] = v;
+  reinterpret_cast<cx<T> *>(base)[idx] = c_norm(v);
 }
 template <class T>
 __device__ __forceinline__ cx<T> ld_cx(const void *base, long long idx) {
@@ -70,7 +70,7 @@ __global__ void k_gamma(const float *q, const float *eps, const float *R, int n,
   ff pr{1.f, 0.f}, pa{1.f, 0.f};
   for (int k = 0; k < p_rep; ++k) pr = s_mul(pr, r);
   for (int k = 0; k < p_att; ++k) pa = s_mul(pa, r);
-  const ff gr = s_mul(se, pr), ga = s_mul(se, pa);
+  const ff gr = s_norm(s_mul(se, pr)), ga = s_norm(s_mul(se, pa));
   g[i] = make_float2(q[i], 0.f);
   g[n + i] = make_float2(gr.hi, gr.lo);
   g[2 * n + i] = make_float2(ga.hi, ga.lo);
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
       float r = __fsub_rn(__fsub_rn(dx.hi, p), pe);
       r = __fadd_rn(r, __fsub_rn(dx.lo, __fmul_rn(q1, h.lo)));
       const float q2 = __fdiv_rn(r, h.hi);
-      ff g = s_add(fast_two_sum(q1, q2), ff{2.f, 0.f});
+      ff g = s_norm(s_add(fast_two_sum(q1, q2), ff{2.f, 0.f}));
       float c = floorf(g.hi);
       if (g.hi == c && g.lo < 0.f) c -= 1.f;
       ff f = two_sum(__fsub_rn(g.hi, c), g.lo);  // g.hi - c is exact
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
       const ff wy = dy ? s_f[i][1] : s_sub(one, s_f[i][1]);
       const ff wz = dz ? s_f[i][2] : s_sub(one, s_f[i][2]);
       const float2 g2 = a.gamma[(long long)t * a.gamma_stride + m.gamma_off + i];
-      const ff v = s_mul(s_mul(s_mul(wx, wy), wz), ff{g2.x, g2.y});
+      const ff v = s_norm(s_mul(s_mul(s_mul(wx, wy), wz), ff{g2.x, g2.y}));
       const long long iv = __float2ll_rn(ldexpf(v.hi, e)) + __float2ll_rn(ldexpf(v.lo, e));
       const int y = s_c[i][1] + dy, z = s_c[i][2] + dz;
       if (y < a.U1 && z < a.U2) atomicAdd(&s_plane[y * a.U2 + z], (unsigned long long)iv);
@@ -308,16 +308,18 @@ cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
 // for each receptor k: P_k = sum_t R_{k,t} conj(L_t), inverse DFT, keep the
 // site window along x.  The ligand spectrum never leaves shared memory.
 template <class T>
-__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfused(XfusedArgs a) {
+__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfused(XfusedArgs a, int batch) {
   extern __shared__ float4 smem[];
-  const int P = a.plan.n, LW = a.LW, L3 = 3 * LW;
+  constexpr int LW = KCfg<T>::xlw, L3 = 3 * LW;
+  const int P = a.plan.n;
   float4 *s_tw = smem;
   cx<T> *bA = reinterpret_cast<cx<T> *>(smem + P);
   cx<T> *bB = bA + P * L3;
   load_tw(s_tw, a.tw, P);
-  const long long ntile = (a.Q + LW - 1) / LW;
-  const int j = blockIdx.x / ntile;
-  const long long q0 = (blockIdx.x % ntile) * LW;
+  // tile-major order: CTAs resident together share a column tile across many
+  // configurations, so that tile's receptor spectra are served from L2
+  const int j = blockIdx.x % batch;
+  const long long q0 = (long long)(blockIdx.x / batch) * LW;
   for (int idx = threadIdx.x; idx < P * L3; idx += blockDim.x) {
     const int x = idx / L3, c = idx % L3, t = c / LW, l = c % LW;
     const long long q = q0 + l;
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfuse
     bA[idx] = v;
   }
   __syncthreads();
-  cx<T> *Lsp = cta_fft<T>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
+  cx<T> *Lsp = cta_fft<T, L3>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
   cx<T> *W1 = (Lsp == bA) ? bB : bA;
   cx<T> *W2 = W1 + P * LW;
   for (int k = 0; k < a.K; ++k) {
@@ -343,10 +345,10 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfuse
           acc = c_add(acc, c_mulconj(r, Lsp[x * L3 + t * LW + l]));
         }
       }
-      W1[idx] = acc;
+      W1[idx] = c_norm(acc);
     }
     __syncthreads();
-    cx<T> *res = cta_fft<T>(W1, W2, LW, 1, LW, a.plan, s_tw, true);
+    cx<T> *res = cta_fft<T, LW>(W1, W2, LW, 1, LW, a.plan, s_tw, true);
     const int w0 = a.info[j * a.K + k].w0[0];
     for (int idx = threadIdx.x; idx < a.S0 * LW; idx += blockDim.x) {
       const int s = idx / LW, l = idx % LW;
@@ -361,11 +363,12 @@ template <class T>
 cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   const int P = a.plan.n;
-  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * 3 * a.LW;
+  constexpr int LW = KCfg<T>::xlw;
+  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * 3 * LW;
   cudaError_t e = cudaFuncSetAttribute(k_xfused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long blocks = (long long)batch * ((a.Q + a.LW - 1) / a.LW);
-  k_xfused<T><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
+  const long long blocks = (long long)batch * ((a.Q + LW - 1) / LW);
+  k_xfused<T><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a, batch);
   return cudaGetLastError();
 }
 
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zinv(
       A = c_conj(A);
       B = c_conj(B);
     }
-    b0[l * ls + n] = cx<T>{s_sub(A.re, B.im), s_add(A.im, B.re)};
+    b0[l * ls + n] = c_norm(cx<T>{s_sub(A.re, B.im), s_add(A.im, B.re)});
   }
   __syncthreads();
   cx<T> *res = cta_fft<T>(b0, b1, 1, ls, L, a.plan, s_tw, true);
@@ -426,7 +429,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zinv(
     if (ok) {
       const cx<T> z = res[(s1 >> 1) * ls + imod(inf.w0[2] + s2, P)];
       const T val = (s1 & 1) ? z.im : z.re;
-      x = s_mul(val, nscale);
+      x = s_norm(s_mul(val, nscale));
       if (ff_gt(x, vmax)) vmax = x;
     }
     xs[idx] = x;
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zinv(
       double e = CUDART_INF;
       if (ok) {
         const cx<T> z = res[(s1 >> 1) * ls + imod(inf.w0[2] + s2, P)];
-        const T E = s_mul((s1 & 1) ? z.im : z.re, escale);
+        const T E = s_norm(s_mul((s1 & 1) ? z.im : z.re, escale));
         e = (double)s_hi(E) + (double)s_lo(E);
       }
       a.export_E[((long long)s0 * a.S1 + s1) * a.S2 + s2] = e;

@@ -75,7 +75,6 @@ struct XfusedArgs {        // x: forward ligand DFT, product with each receptor,
   const PairInfo *info;    // [batch][K]
   FftPlan plan;
   const float4 *tw;
-  int LW;
 };
 
 struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp partials
