@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace bpmf {
@@ -49,6 +51,27 @@ __device__ __forceinline__ cx<ff> ld_rec(const float2 *hi, const float2 *lo, lon
 
 __device__ __forceinline__ void load_tw(float4 *s_tw, const float4 *tw, int P) {
   for (int i = threadIdx.x; i < P; i += blockDim.x) s_tw[i] = tw[i];
+}
+
+// Asynchronous global -> shared copy of one element (8 or 16 bytes), zero
+// filled when !valid (no bytes are read then).  All copies a thread issues are
+// in flight together; cp_async_wait_all() + __syncthreads() publish them.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? BYTES : 0;
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(src), "n"(BYTES), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <class T>
+__device__ __forceinline__ void cp_cx(cx<T> *dst, const void *base, long long idx, bool valid) {
+  const cx<T> *b = reinterpret_cast<const cx<T> *>(base);
+  cp_async<sizeof(cx<T>)>(dst, valid ? b + idx : b, valid);
 }
 
 // --------------------------------------------------------------------------
@@ -220,19 +243,25 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zfwd(
   for (int idx = threadIdx.x; idx < L * P; idx += blockDim.x) {
     const int l = idx / P, n = idx % P;
     const long long ra = r0 + 2 * l, rb = ra + 1;
-    float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
-    if (n < a.w_in) {
-      if (a.in_pairs) {
-        const float2 *in2 = reinterpret_cast<const float2 *>(a.in);
-        if (ra < a.n_rows) va = in2[ra * a.in_stride + n];
-        if (rb < a.n_rows) vb = in2[rb * a.in_stride + n];
+    const bool va = n < a.w_in && ra < a.n_rows, vb = n < a.w_in && rb < a.n_rows;
+    cx<T> *d = &b0[l * ls + n];
+    if (a.in_pairs) {
+      // float-pair rows: row ra -> real part, row rb -> imaginary part
+      const float2 *in2 = reinterpret_cast<const float2 *>(a.in);
+      if constexpr (sizeof(T) == 8) {
+        cp_async<8>(&d->re, va ? in2 + ra * a.in_stride + n : in2, va);
+        cp_async<8>(&d->im, vb ? in2 + rb * a.in_stride + n : in2, vb);
       } else {
-        if (ra < a.n_rows) va.x = a.in[ra * a.in_stride + n];
-        if (rb < a.n_rows) vb.x = a.in[rb * a.in_stride + n];
+        cp_async<4>(&d->re, va ? &in2[ra * a.in_stride + n].x : a.in, va);
+        cp_async<4>(&d->im, vb ? &in2[rb * a.in_stride + n].x : a.in, vb);
       }
+    } else {
+      const float x = va ? a.in[ra * a.in_stride + n] : 0.f;
+      const float y = vb ? a.in[rb * a.in_stride + n] : 0.f;
+      *d = cx<T>{s_from<T>(x), s_from<T>(y)};
     }
-    b0[l * ls + n] = cx<T>{s_mk<T>(va.x, va.y), s_mk<T>(vb.x, vb.y)};
   }
+  cp_async_wait_all();
   __syncthreads();
   cx<T> *res = cta_fft<T>(b0, b1, 1, ls, L, a.plan, s_tw, false);
   const T half = s_from<T>(0.5f);
@@ -273,13 +302,14 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_axis(
   const long long ntile = (a.inner + LW - 1) / LW;
   const long long o = blockIdx.x / ntile;
   const long long i0 = (blockIdx.x % ntile) * LW;
-  for (int idx = threadIdx.x; idx < P * LW; idx += blockDim.x) {
+  const int n_in = a.n_in < P ? a.n_in : P;
+  for (int idx = threadIdx.x; idx < n_in * LW; idx += blockDim.x) {
     const int n = idx / LW, l = idx % LW;
     const long long i = i0 + l;
-    cx<T> v = c_zero<T>();
-    if (n < a.n_in && i < a.inner) v = ld_cx<T>(a.in, o * a.in_os + n * a.inner + i);
-    b0[idx] = v;
+    cp_cx<T>(&b0[idx], a.in, o * a.in_os + n * a.inner + i, i < a.inner);
   }
+  for (int idx = n_in * LW + threadIdx.x; idx < P * LW; idx += blockDim.x) b0[idx] = c_zero<T>();
+  cp_async_wait_all();
   __syncthreads();
   cx<T> *res = cta_fft<T>(b0, b1, LW, 1, LW, a.plan, s_tw, a.inverse != 0);
   const int w0 = a.info ? a.info[o / a.w0_div].w0[a.axis] : 0;
@@ -320,13 +350,14 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfuse
   // configurations, so that tile's receptor spectra are served from L2
   const int j = blockIdx.x % batch;
   const long long q0 = (long long)(blockIdx.x / batch) * LW;
-  for (int idx = threadIdx.x; idx < P * L3; idx += blockDim.x) {
+  const int U0 = a.U0 < P ? a.U0 : P;
+  for (int idx = threadIdx.x; idx < U0 * L3; idx += blockDim.x) {
     const int x = idx / L3, c = idx % L3, t = c / LW, l = c % LW;
     const long long q = q0 + l;
-    cx<T> v = c_zero<T>();
-    if (x < a.U0 && q < a.Q) v = ld_cx<T>(a.ly, (((long long)j * 3 + t) * a.U0 + x) * a.Q + q);
-    bA[idx] = v;
+    cp_cx<T>(&bA[idx], a.ly, (((long long)j * 3 + t) * a.U0 + x) * a.Q + q, q < a.Q);
   }
+  for (int idx = U0 * L3 + threadIdx.x; idx < P * L3; idx += blockDim.x) bA[idx] = c_zero<T>();
+  cp_async_wait_all();
   __syncthreads();
   cx<T> *Lsp = cta_fft<T, L3>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
   cx<T> *W1 = (Lsp == bA) ? bB : bA;
@@ -334,6 +365,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfuse
   for (int k = 0; k < a.K; ++k) {
     const float2 *rh = a.rhi[k];
     const float2 *rl = a.rlo ? a.rlo[k] : nullptr;
+#pragma unroll 2
     for (int idx = threadIdx.x; idx < P * LW; idx += blockDim.x) {
       const int x = idx / LW, l = idx % LW;
       const long long q = q0 + l;
@@ -386,7 +418,8 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zinv(
   float4 *s_tw = smem;
   cx<T> *b0 = reinterpret_cast<cx<T> *>(smem + P);
   cx<T> *b1 = b0 + L * ls;
-  T *xs = reinterpret_cast<T *>(b1 + L * ls);  // [S1*S2]
+  const int b1n = L * ls > a.S1 * F ? L * ls : a.S1 * F;
+  T *xs = reinterpret_cast<T *>(b1 + b1n);  // [S1*S2]
   __shared__ T s_red[8];
   __shared__ float s_sum[8];
   load_tw(s_tw, a.tw, P);
@@ -395,6 +428,14 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zinv(
   const PairInfo inf = a.info[jk];
   const long long base = (long long)blockIdx.x * a.S1 * F;
   const bool row_ok = (s0 >= inf.sa[0] && s0 <= inf.sb[0]);
+  // stage the [S1][F2] block of half spectra with asynchronous copies (b1 is
+  // sized for it), then pack row pairs as z = A + iB with Hermitian extension
+  cx<T> *stg = b1;
+  if (row_ok) {
+    for (int idx = threadIdx.x; idx < a.S1 * F; idx += blockDim.x) cp_cx<T>(&stg[idx], a.y2, base + idx, true);
+    cp_async_wait_all();
+  }
+  __syncthreads();
   for (int idx = threadIdx.x; idx < L * P; idx += blockDim.x) {
     const int l = idx / P, n = idx % P;
     const int ra = 2 * l, rb = ra + 1;
@@ -403,8 +444,8 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zinv(
     const int kk = up ? n : P - n;
     const bool real_bin = (kk == 0) || (2 * kk == P);
     if (row_ok) {
-      A = ld_cx<T>(a.y2, base + (long long)ra * F + kk);
-      if (rb < a.S1) B = ld_cx<T>(a.y2, base + (long long)rb * F + kk);
+      A = stg[ra * F + kk];
+      if (rb < a.S1) B = stg[rb * F + kk];
     }
     if (real_bin) {
       A.im = s_zero<T>();
@@ -477,7 +518,8 @@ template <class T>
 cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   const int P = a.plan.n, L = (a.S1 + 1) / 2;
-  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)L * (P + 1) + sizeof(T) * (size_t)a.S1 * a.S2;
+  const size_t b1n = std::max((size_t)L * (P + 1), (size_t)a.S1 * a.F2);
+  const size_t smem = sizeof(float4) * P + sizeof(cx<T>) * ((size_t)L * (P + 1) + b1n) + sizeof(T) * (size_t)a.S1 * a.S2;
   cudaError_t e = cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_zinv<T><<<(unsigned)((long long)batch * a.K * a.S0), KCfg<T>::threads, smem, st>>>(a);
@@ -491,27 +533,31 @@ cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st) {
 //   log Z_jk = log S_jk - ln n_jk
 //   B_k      = -kT [ LSE_j log S_jk - ln sum_j n_jk ]
 //   dG       = -kT [ LSE_k (-B_k / kT) - ln K ] - kT ln(V_site C)
-__global__ void __launch_bounds__(256) k_merge(MergeArgs a, double *logS) {
+__global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
+  const int JK = a.J * a.K;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= JK) return;
+  const float4 *pp = a.part + (long long)p * a.S0;
+  double Mx = -CUDART_INF;
+  for (int c = 0; c < a.S0; ++c)
+    if (pp[c].z > 0.f) Mx = fmax(Mx, (double)pp[c].x + (double)pp[c].y);
+  double s = 0.0;
+  if (Mx > -CUDART_INF)
+    for (int c = 0; c < a.S0; ++c)
+      if (pp[c].z > 0.f) s += (double)pp[c].z * exp((double)pp[c].x + (double)pp[c].y - Mx);
+  const long long n = a.nvalid[p];
+  const double ls = (s > 0.0 && n > 0) ? Mx + log(s) : -CUDART_INF;
+  a.logS[p] = ls;
+  // processing position -> caller's configuration order
+  const long long q = (long long)(a.order ? a.order[p / a.K] : p / a.K) * a.K + p % a.K;
+  a.logZ[q] = n > 0 ? ls - log((double)n) : -CUDART_INF;
+  if (a.nvalid_out) a.nvalid_out[q] = n;
+}
+
+__global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
   __shared__ double s_d[256];
   __shared__ long long s_l[256];
-  const int JK = a.J * a.K;
-  for (int p = threadIdx.x; p < JK; p += blockDim.x) {
-    const float4 *pp = a.part + (long long)p * a.S0;
-    double Mx = -CUDART_INF;
-    for (int c = 0; c < a.S0; ++c)
-      if (pp[c].z > 0.f) Mx = fmax(Mx, (double)pp[c].x + (double)pp[c].y);
-    double s = 0.0;
-    if (Mx > -CUDART_INF)
-      for (int c = 0; c < a.S0; ++c)
-        if (pp[c].z > 0.f) s += (double)pp[c].z * exp((double)pp[c].x + (double)pp[c].y - Mx);
-    const long long n = a.nvalid[p];
-    const double ls = (s > 0.0 && n > 0) ? Mx + log(s) : -CUDART_INF;
-    logS[p] = ls;
-    // sorted position -> caller's configuration order
-    const long long q = (long long)(a.order ? a.order[p / a.K] : p / a.K) * a.K + p % a.K;
-    a.logZ[q] = n > 0 ? ls - log((double)n) : -CUDART_INF;
-    if (a.nvalid_out) a.nvalid_out[q] = n;
-  }
+  const double *logS = a.logS;
   __syncthreads();
   long long ntot_all = 0;
   for (int k = 0; k < a.K; ++k) {
@@ -567,7 +613,9 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a, double *logS) {
 }
 
 cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st) {
-  k_merge<<<1, 256, 0, st>>>(a, a.logS);
+  const int JK = a.J * a.K;
+  if (JK > 0) k_merge_pairs<<<(JK + 127) / 128, 128, 0, st>>>(a);
+  k_merge<<<1, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
