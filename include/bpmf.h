@@ -191,6 +191,42 @@ int bpmf_profile_enable(bpmf_ctx_t ctx, int on);
 int bpmf_profile_count(bpmf_ctx_t ctx);
 int bpmf_profile_entry(bpmf_ctx_t ctx, int i, char *name, int name_len, double *total_ms, int64_t *launches);
 
+/*
+ * bpmf_export_energies_static -- the energy export of bpmf_export_energies
+ * for callers that cannot allocate device memory.  The paper has no
+ * counterpart; it exists for callers such as code running inside another
+ * framework's pre-reserved memory pool, or threads that must not call
+ * cudaMalloc/cudaFree because those synchronise the device.  It allocates
+ * nothing: every intermediate (twiddle tables, generalised charges, the
+ * receptor spectra, the ligand grid and all transform passes) lives in one
+ * library-owned static device array of BPMF_STATIC_SCRATCH_BYTES, which every
+ * GPU that loads this library holds until the process exits.
+ *
+ *  grids      [3][nx][ny][nz] float32 receptor grids (as bpmf_receptor_load),
+ *             DEVICE memory of the current device.
+ *  h, site_lo, site_n   as bpmf_receptor_load (site_lo / site_n host arrays).
+ *  n_atoms, coords [n_atoms][3], q, eps, R [n_atoms]: one ligand
+ *             configuration, DEVICE memory; p_rep, p_att as bpmf_ligand_batch.
+ *  mode       BPMF_MODE_FP32 or BPMF_MODE_FF.
+ *  out        [S0][S1][S2] float64 DEVICE memory (S = site_n): energy of
+ *             translation m = site_lo + s - floor(u/2), +inf where discarded;
+ *             the same values bpmf_export_energies returns.
+ * Runs on the current device and on `stream`, and synchronises `stream`
+ * before returning.  The first call on a device resolves the array's device
+ * address (cudaGetSymbolAddress) once; make that first call before any stream
+ * capture.  Every call shares the one array and leaves its contents behind:
+ * calls whose GPU work overlaps (other threads, other streams) race and must be
+ * serialised by the caller.
+ * Errors: INVALID_ARG; SIZE_UNSUPPORTED when the grid or the ligand box needs
+ * more scratch than BPMF_STATIC_SCRATCH_BYTES (a 96^3 grid with a ligand box
+ * up to ~60 nodes per edge fits) or exceeds the other limits; CUDA.
+ */
+#define BPMF_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int bpmf_export_energies_static(const float *grids, int nx, int ny, int nz, double h, const int site_lo[3],
+                                const int site_n[3], int n_atoms, const float *coords, const float *q,
+                                const float *eps, const float *R, int p_rep, int p_att, unsigned mode, double *out,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "libbpmf.so")
-_SOURCES = ["kernels.cu", "bpmf_api.cu"]
+_SOURCES = ["kernels.cu", "bpmf_api.cu", "bpmf_static.cu"]
 _HEADERS = ["arith.cuh", "fft.cuh", "kernels.cuh"]
 
 BPMF_OK = 0
@@ -112,6 +112,8 @@ _SIGS = {
     "bpmf_profile_enable": (_I, [_P, _I]),
     "bpmf_profile_count": (_I, [_P]),
     "bpmf_profile_entry": (_I, [_P, _I, ctypes.c_char_p, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)]),
+    "bpmf_export_energies_static": (_I, [_P, _I, _I, _I, _D, _P, _P, _I, _P, _P, _P, _P, _I, _I, ctypes.c_uint, _P,
+                                         _P]),
 }
 
 
@@ -275,3 +277,23 @@ def bpmf_profile_entry(ctx, i: int):
 def bpmf_profile(ctx) -> dict:
     """{kernel name: (total ms, launches)} recorded since profiling was enabled."""
     return {name: (ms, n) for name, ms, n in (bpmf_profile_entry(ctx, i) for i in range(bpmf_profile_count(ctx)))}
+
+
+BPMF_STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
+
+
+def bpmf_export_energies_static(grids, h, site_lo, site_n, coords, q, eps, R, mode, out, p_rep=12, p_att=6,
+                                stream=None) -> int:
+    """Energy export that allocates no device memory (scratch lives in the
+    library's static device array).  grids, coords, q, eps, R and out must be
+    device tensors on the current device; returns the status code."""
+    nx, ny, nz = (int(v) for v in tuple(grids.shape)[1:])
+    lo = np.ascontiguousarray(np.asarray(site_lo, dtype=np.int32).reshape(3))
+    sn = np.ascontiguousarray(np.asarray(site_n, dtype=np.int32).reshape(3))
+    n_atoms = int(tuple(coords.shape)[0])
+    rc = lib().bpmf_export_energies_static(_ptr(grids, np.float32), nx, ny, nz, float(h), _ptr(lo, np.int32),
+                                           _ptr(sn, np.int32), n_atoms, _ptr(coords, np.float32),
+                                           _ptr(q, np.float32), _ptr(eps, np.float32), _ptr(R, np.float32),
+                                           int(p_rep), int(p_att), int(mode), _ptr(out, np.float64),
+                                           _stream(stream))
+    return _check(rc, "bpmf_export_energies_static")
