@@ -177,6 +177,71 @@ def alg_work(w, n_valid, mode):
     return work
 
 
+def cufft_leg(torch, w, dev, chunk=48):
+    """Timed comparison only (never the product path): the same correlation in
+    FP32 with unpruned torch.fft (cuFFT) R2C/C2R transforms; spreading, the
+    spectral product, site window, mask and log-sum-exp in torch.  Returns
+    (ms per step including the receptor transforms, log Z [J, K])."""
+    lig = w.ligands[0]
+    r0 = w.receptors[0]
+    K = len(w.receptors)
+    shape = r0.shape
+    P = shape[0]
+    J, n = lig.coords.shape[0], lig.coords.shape[1]
+    h = r0.h
+    kT = w.kT
+    coords = torch.from_numpy(lig.coords).to(dev)
+    q, eps, R = (torch.from_numpy(getattr(lig.params, k)).to(dev) for k in ("q", "eps", "R"))
+    gam = torch.stack([q, torch.sqrt(eps) * R ** 12, torch.sqrt(eps) * R ** 6])  # [3, n]
+    ext = (lig.coords.max(1) - lig.coords.min(1)).astype(np.float32)
+    u = np.ceil((ext / np.float32(h)).astype(np.float32)).astype(np.int64) + 4  # [J, 3]
+    S = np.array(r0.site_n)
+    lo_site = np.array(r0.site_lo)
+    Nn = np.array(shape)
+    w0 = lo_site[None, :] - u // 2  # [J, 3]
+    sidx = [torch.arange(int(S[d]), device=dev) for d in range(3)]
+    grids = [torch.from_numpy(r.grids).to(dev) for r in w.receptors]
+    out = torch.empty((J, K), dtype=torch.float64, device=dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    Rf = torch.stack([torch.fft.rfftn(g, dim=(1, 2, 3)) for g in grids])  # [K, 3, P, P, F]
+    corner = torch.tensor([[dx, dy, dz] for dx in (0, 1) for dy in (0, 1) for dz in (0, 1)], device=dev)
+    for j0 in range(0, J, chunk):
+        B = min(chunk, J - j0)
+        x = coords[j0:j0 + B]
+        g = (x - x.min(dim=1, keepdim=True).values) / h + 2.0
+        c0 = torch.floor(g)
+        f = g - c0
+        c0 = c0.long()
+        L = torch.zeros((B, 3, P * P * P), device=dev)
+        for ci in range(8):
+            d = corner[ci]
+            wgt = torch.prod(torch.where(d.bool(), f, 1.0 - f), dim=-1)  # [B, n]
+            idx = (((c0[..., 0] + d[0]) * P + (c0[..., 1] + d[1])) * P + (c0[..., 2] + d[2]))  # [B, n]
+            for t in range(3):
+                L[:, t].scatter_add_(1, idx, wgt * gam[t][None, :])
+        Lf = torch.fft.rfftn(L.view(B, 3, P, P, P), dim=(2, 3, 4))
+        w0b = torch.from_numpy(w0[j0:j0 + B]).to(dev)
+        ub = torch.from_numpy(u[j0:j0 + B]).to(dev)
+        for k in range(K):
+            E = torch.fft.irfftn((Rf[k][None] * torch.conj(Lf)).sum(1), s=(P, P, P), dim=(1, 2, 3))  # [B, P, P, P]
+            m = [w0b[:, d][:, None] + sidx[d][None, :] for d in range(3)]  # [B, S_d]
+            ok = [(m[d] >= 0) & (m[d] <= int(Nn[d]) - 1 - ub[:, d][:, None]) for d in range(3)]
+            mi = [torch.remainder(m[d], P) for d in range(3)]
+            win = E[torch.arange(B, device=dev)[:, None, None, None], mi[0][:, :, None, None],
+                    mi[1][:, None, :, None], mi[2][:, None, None, :]]
+            valid = ok[0][:, :, None, None] & ok[1][:, None, :, None] & ok[2][:, None, None, :]
+            xk = torch.where(valid, -win / kT, torch.full_like(win, -float("inf")))
+            ls = torch.logsumexp(xk.reshape(B, -1).double(), dim=1)
+            nv = valid.reshape(B, -1).sum(1).double()
+            out[j0:j0 + B, k] = torch.where(nv > 0, ls - torch.log(nv.clamp(min=1)), torch.full_like(ls, -float("inf")))
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), out.cpu().numpy()
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -286,6 +351,14 @@ def run_ours(args):
     h2d = sum(g.numel() * 4 for g in host_grids) + host_coords.numel() * 4 + sum(p.numel() * 4 for p in host_params)
     d2h = sum(v.nbytes for v in host_outs.values())
 
+    cufft = None
+    if rank == 0 and not args.no_cufft:
+        cufft_leg(torch, w, dev)  # warm-up (plans, allocator)
+        t_cu, logZ_cu = cufft_leg(torch, w, dev)
+        cufft = {"ms_per_step": t_cu, "value": n_poses / (t_cu / 1e3), "unit": "pose energies/s",
+                 "what": "FP32, unpruned torch.fft (cuFFT) R2C/C2R, spreading/product/mask/LSE in torch; "
+                         "timed comparison only, not the product path"}
+
     line = None
     if rank == 0:
         # accuracy and CPU baseline on a bounded oracle sample
@@ -295,7 +368,10 @@ def run_ours(args):
             ref, dt = oracle_sample(w, args.ref_sample)
             okz = np.isfinite(ref["logZ"])
             ns = args.ref_sample
-            for name, res in ((chosen, res_chosen), (other, res_other)):
+            cmp = [(chosen, res_chosen), (other, res_other)]
+            if cufft is not None:
+                cmp.append(("cufft_fp32", {"logZ": logZ_cu, "n_valid": res_chosen["n_valid"]}))
+            for name, res in cmp:
                 dz = np.abs(res["logZ"][:ns][okz] - ref["logZ"][okz]).max() * w.kT
                 import oracle
                 logS = res["logZ"][:ns] + np.log(np.maximum(res["n_valid"][:ns], 1))
@@ -343,6 +419,7 @@ def run_ours(args):
                               "ms_per_step": t_other if other == "fp32" else None},
                 "ff_path": {"ms_per_step": t_other} if other == "ff" else {"ms_per_step": t_ms},
                 "kernels_ms_per_step_other_form": {k: v[0] / max(1, args.steps // 2) for k, v in prof_other.items()},
+                "cufft_fp32_path": cufft,
                 "accuracy_vs_oracle": acc,
                 "e2e": {"value": n_poses * world / e2e_t, "unit": "pose energies/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_t * 1e3},
@@ -366,6 +443,7 @@ def main():
     ap.add_argument("--mode", default="ff", choices=["ff", "fp32"])
     ap.add_argument("--ref-sample", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison leg")
     ap.add_argument("--n-conf", type=int, default=N_CONF,
                     help="configurations per step (default: the full workload; smaller values are for profiling)")
     args = ap.parse_args()
