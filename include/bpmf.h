@@ -144,8 +144,10 @@ void bpmf_ligand_free(bpmf_lig_t lig);
  * with C = 1/1660.539 A^-3 and V_site = h^3 * mean_jk n_jk (Eqs.
  * standard_binding_fe and binding_FE_estimate with uniform receptor weights).
  *
- *  recs, K   receptor handles; all must share the grid spacing and the padded
- *            FFT edges (else SIZE_UNSUPPORTED).
+ *  recs, K   receptor handles; all must share the grid spacing (else
+ *            SIZE_UNSUPPORTED).  Receptors with different grid sizes are
+ *            processed in groups of equal padded FFT edges; the ligand's
+ *            forward transforms are shared within a group.
  *  kT        > 0 (kcal/mol).
  *  mode      BPMF_MODE_FP32 or BPMF_MODE_FF.
  *  logZ      [total_conf][K] float64, total_conf = sum n_conf, ligand-major.
@@ -177,6 +179,27 @@ int bpmf_fft_edge(int n);
  * depend on the batch size (every step is deterministic).  Errors:
  * INVALID_ARG (bytes < 1 MiB). */
 int bpmf_set_workspace_limit(bpmf_ctx_t ctx, size_t bytes);
+
+/*
+ * bpmf_set_graph_mode -- when on, bpmf_eval records its whole device-side
+ * launch sequence (table upload, every batch of every receptor group, the
+ * merges, the result copies) into a CUDA graph on first use and replays the
+ * graph on later calls with the same ligand handle, receptor handles, mode,
+ * kT, output pointers and launch shapes.  Requires a non-default stream and
+ * device-memory outputs (otherwise the call runs without a graph).  Results
+ * are bit-identical with and without graphs.  Errors: INVALID_ARG.
+ */
+int bpmf_set_graph_mode(bpmf_ctx_t ctx, int on);
+
+/*
+ * bpmf_autotune -- time bpmf_eval on (lig, recs) under candidate launch
+ * shapes (configurations per batch, lines per CTA of the strided passes, rows
+ * per CTA of the z pass) and keep the fastest for every padded grid size of
+ * `recs` and this mode.  The FFT plan itself is fixed, so every choice gives
+ * bit-identical results.  Runs ~10 evaluations and synchronises `stream`.
+ * Errors: INVALID_ARG, SIZE_UNSUPPORTED, OOM, CUDA.
+ */
+int bpmf_autotune(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, int K, unsigned mode, void *stream);
 
 /*
  * Kernel timing (tracing).  While enabled, every kernel the library launches

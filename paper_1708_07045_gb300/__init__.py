@@ -112,6 +112,8 @@ _SIGS = {
     "bpmf_profile_enable": (_I, [_P, _I]),
     "bpmf_profile_count": (_I, [_P]),
     "bpmf_profile_entry": (_I, [_P, _I, ctypes.c_char_p, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)]),
+    "bpmf_set_graph_mode": (_I, [_P, _I]),
+    "bpmf_autotune": (_I, [_P, _P, _P, _I, ctypes.c_uint, _P]),
     "bpmf_export_energies_static": (_I, [_P, _I, _I, _I, _D, _P, _P, _I, _P, _P, _P, _P, _I, _I, ctypes.c_uint, _P,
                                          _P]),
 }
@@ -254,6 +256,17 @@ def bpmf_export_energies(ctx, lig, rec, lig_index, conf_index, mode, out, stream
     rc = lib().bpmf_export_energies(ctx, lig, rec, int(lig_index), int(conf_index), int(mode),
                                     _ptr(out, np.float64), _stream(stream))
     return _check(rc, "bpmf_export_energies", ctx)
+
+
+def bpmf_set_graph_mode(ctx, on: bool = True):
+    _check(lib().bpmf_set_graph_mode(ctx, 1 if on else 0), "bpmf_set_graph_mode", ctx)
+
+
+def bpmf_autotune(ctx, lig, recs, mode, stream=None):
+    K = len(recs)
+    arr = (ctypes.c_void_p * K)(*[r.value if isinstance(r, ctypes.c_void_p) else r for r in recs])
+    _check(lib().bpmf_autotune(ctx, lig, ctypes.cast(arr, ctypes.c_void_p), K, int(mode), _stream(stream)),
+           "bpmf_autotune", ctx)
 
 
 def bpmf_profile_enable(ctx, on: bool = True):

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <new>
 #include <string>
@@ -37,10 +38,27 @@ struct bpmf_ctx {
   void *ws = nullptr;          // grow-only device workspace
   size_t ws_bytes = 0;
   size_t ws_budget = size_t(3) << 30;
+  unsigned long long next_id = 1;  // handle identities (graph cache keys)
+  void *pinned = nullptr;          // pinned host staging of the eval tables
+  size_t pinned_bytes = 0;
+  cudaEvent_t pinned_busy = nullptr;  // recorded after the last copy / graph replay reading `pinned`
+  bool graph_mode = false;         // replay bpmf_eval as a CUDA graph
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned long long> gkey;
+  // launch shapes chosen by bpmf_autotune, per (P0, P1, P2, mode); none of
+  // them changes a result bit (every line transform is independent)
+  struct Tune {
+    int batch_cap = 0;  // configurations per batch (0: as many as the workspace holds)
+    int axis_lw = 16;   // lines per CTA cap of the strided passes
+    int zfwd_l = 16;    // complex lines per CTA of the z R2C pass
+  };
+  std::map<std::vector<int>, Tune> tune;
+  bool warn_last = false;  // BPMF_WARN_NO_VALID of the plan behind the cached graph
 };
 
 struct bpmf_rec {
   bpmf_ctx *ctx = nullptr;
+  unsigned long long id = 0;
   int N[3] = {0, 0, 0}, P[3] = {0, 0, 0}, F2 = 0;
   long long Q = 0;
   double h = 0;
@@ -51,6 +69,7 @@ struct bpmf_rec {
 
 struct bpmf_lig {
   bpmf_ctx *ctx = nullptr;
+  unsigned long long id = 0;
   int n_lig = 0;
   std::vector<int> n_atoms, n_conf, atom_off, conf_off, coord_off;
   long long total_conf = 0, total_atoms = 0, total_coord_atoms = 0;
@@ -192,7 +211,8 @@ void launch(bpmf_ctx *c, const char *name, cudaStream_t st, F &&fn) {
       throw Fail{e == cudaErrorMemoryAllocation ? BPMF_ERR_OOM : BPMF_ERR_CUDA};
     }
   };
-  if (!c->prof) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!c->prof || (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)) {
     run();
     return;
   }
@@ -277,7 +297,7 @@ template <class T>
 void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, const ConfMeta *d_meta,
                const PairInfo *d_info, const float2 *const *d_rhi, const float2 *const *d_rlo, double h,
                float nscale_hi, float nscale_lo, float escale_hi, float escale_lo, float4 *d_part,
-               double *export_E, char *ws, cudaStream_t st) {
+               double *export_E, char *ws, cudaStream_t st, const bpmf_ctx::Tune &tn) {
   const size_t E = sizeof(cx<T>);
   char *p = ws;
   float2 *box = reinterpret_cast<float2 *>(p);
@@ -305,7 +325,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   za.out_stride = g.F2;
   za.plan = make_plan(g.P[2]);
   za.tw = twiddles(c, g.P[2]);
-  za.L = 16;
+  za.L = tn.zfwd_l;
   launch(c, sizeof(T) == 4 ? "k_zfwd<fp32>" : "k_zfwd<ff>", st, [&] { return launch_zfwd<T>(za, st); });
 
   AxisArgs ya{};
@@ -324,7 +344,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   ya.inverse = 0;
   ya.plan = make_plan(g.P[1]);
   ya.tw = twiddles(c, g.P[1]);
-  ya.LW = pick_lw(ya.inner);
+  ya.LW = pick_lw(ya.inner, tn.axis_lw);
   launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y fwd)" : "k_axis<ff>(y fwd)", st, [&] { return launch_axis<T>(ya, st); });
 
   XfusedArgs xa{};
@@ -357,7 +377,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   yi.inverse = 1;
   yi.plan = make_plan(g.P[1]);
   yi.tw = twiddles(c, g.P[1]);
-  yi.LW = pick_lw(yi.inner);
+  yi.LW = pick_lw(yi.inner, tn.axis_lw);
   launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y inv)" : "k_axis<ff>(y inv)", st, [&] { return launch_axis<T>(yi, st); });
 
   ZinvArgs zi{};
@@ -382,11 +402,6 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
 void check_recs(const bpmf_rec_t *recs, int K, bpmf_ctx *c) {
   for (int k = 0; k < K; ++k) {
     if (!recs[k] || recs[k]->ctx != c) throw Fail{BPMF_ERR_INVALID_ARG};
-    for (int d = 0; d < 3; ++d)
-      if (recs[k]->P[d] != recs[0]->P[d]) {
-        last_msg = "receptors in one bpmf_eval call must share padded FFT edges";
-        throw Fail{BPMF_ERR_SIZE_UNSUPPORTED};
-      }
     if (recs[k]->h != recs[0]->h) {
       last_msg = "receptors in one bpmf_eval call must share the grid spacing";
       throw Fail{BPMF_ERR_SIZE_UNSUPPORTED};
@@ -494,6 +509,12 @@ int bpmf_profile_entry(bpmf_ctx_t c, int i, char *name, int name_len, double *to
   return BPMF_OK;
 }
 
+int bpmf_set_graph_mode(bpmf_ctx_t c, int on) {
+  if (!c) return BPMF_ERR_INVALID_ARG;
+  c->graph_mode = on != 0;
+  return BPMF_OK;
+}
+
 int bpmf_set_workspace_limit(bpmf_ctx_t c, size_t bytes) {
   if (!c || bytes < (size_t(1) << 20)) return set_err(c, BPMF_ERR_INVALID_ARG, "workspace limit below 1 MiB");
   c->ws_budget = bytes;
@@ -532,6 +553,12 @@ void bpmf_destroy(bpmf_ctx_t c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->pinned_busy) {
+    cudaEventSynchronize(c->pinned_busy);
+    cudaEventDestroy(c->pinned_busy);
+  }
+  if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
 }
 
@@ -556,6 +583,7 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
   void *tz = nullptr, *ty = nullptr, *tx = nullptr;
   try {
     r->ctx = c;
+    r->id = c->next_id++;
     for (int d = 0; d < 3; ++d) {
       r->N[d] = N[d];
       r->P[d] = P[d];
@@ -666,6 +694,7 @@ int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_
   float *d_mm = nullptr;
   try {
     lg->ctx = c;
+    lg->id = c->next_id++;
     lg->n_lig = n_lig;
     lg->n_atoms.assign(n_atoms, n_atoms + n_lig);
     lg->n_conf.assign(n_conf, n_conf + n_lig);
@@ -753,171 +782,338 @@ void bpmf_ligand_free(bpmf_lig_t lg) {
 namespace {
 
 // Shared driver of bpmf_eval and bpmf_export_energies.
+bool lg_warn_cached(const bpmf_ctx *c) { return c->warn_last; }
+
+// Receptors that share padded FFT edges share the ligand's forward transforms.
+struct RecGroup {
+  int P[3] = {0, 0, 0};
+  int S[3] = {0, 0, 0};  // max site edges over the group
+  int F2 = 0;
+  long long Q = 0;
+  std::vector<int> ks;   // receptor indices (call order)
+};
+
+std::vector<RecGroup> group_receptors(const bpmf_rec_t *recs, int K) {
+  std::vector<RecGroup> gs;
+  for (int k = 0; k < K; ++k) {
+    const bpmf_rec *r = recs[k];
+    size_t i = 0;
+    while (i < gs.size() && !(gs[i].P[0] == r->P[0] && gs[i].P[1] == r->P[1] && gs[i].P[2] == r->P[2])) ++i;
+    if (i == gs.size()) {
+      RecGroup g;
+      for (int d = 0; d < 3; ++d) g.P[d] = r->P[d];
+      g.F2 = r->F2;
+      g.Q = r->Q;
+      gs.push_back(g);
+    }
+    gs[i].ks.push_back(k);
+    for (int d = 0; d < 3; ++d) gs[i].S[d] = std::max(gs[i].S[d], r->site_n[d]);
+  }
+  return gs;
+}
+
+bpmf_ctx::Tune tune_for(bpmf_ctx *c, const int P[3], unsigned mode) {
+  auto it = c->tune.find(std::vector<int>{P[0], P[1], P[2], (int)mode});
+  return it == c->tune.end() ? bpmf_ctx::Tune{} : it->second;
+}
+
+// Host plan of one bpmf_eval call: every table of every ligand and receptor
+// group lives in one pinned blob uploaded with a single copy, so the execute
+// phase issues no host-synchronising call and can be captured as a graph.
+struct LigPlan {
+  int li = 0, J = 0, j_first = 0;
+  size_t off_meta = 0, off_order = 0, off_nv = 0;   // blob offsets
+  std::vector<size_t> off_info;                     // per group: [J][Kg] PairInfo
+  std::vector<size_t> off_kmap, off_rptr;           // per group
+  std::vector<std::array<int, 3>> Umax;             // per group
+  std::vector<std::vector<std::array<int, 3>>> Ub;  // per group, per batch
+  std::vector<int> B;                               // per group batch size
+  size_t fixed = 0, batch_bytes = 0;
+};
+
 int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
               double *logZ, int64_t *n_valid, double *bpmf_out, double *dG, cudaStream_t st, int only_lig,
               int only_conf, double *export_E) {
   check_recs(recs, K, c);
-  const bpmf_rec *r0 = recs[0];
-  const double h = r0->h;
+  const double h = recs[0]->h;
   const bool use_ff = (mode == BPMF_MODE_FF);
   const size_t E = use_ff ? sizeof(cx<ff>) : sizeof(cx<float>);
-  int S[3] = {0, 0, 0};
-  for (int k = 0; k < K; ++k)
-    for (int d = 0; d < 3; ++d) S[d] = std::max(S[d], recs[k]->site_n[d]);
-  const double norm = 1.0 / ((double)r0->P[0] * r0->P[1] * r0->P[2]);
-  float nsh, nsl, esh, esl;
-  split_ff(-norm / kT, nsh, nsl);
-  split_ff(norm, esh, esl);
-
-  // receptor spectrum pointer tables (device)
-  std::vector<const float2 *> hrhi(K), hrlo(K);
-  for (int k = 0; k < K; ++k) {
-    hrhi[k] = recs[k]->hi;
-    hrlo[k] = recs[k]->lo;
-  }
-  bool warn = false;
+  const std::vector<RecGroup> groups = group_receptors(recs, K);
   const int lig_begin = only_lig >= 0 ? only_lig : 0;
   const int lig_end = only_lig >= 0 ? only_lig + 1 : lg->n_lig;
-  long long conf_base = 0;
-  for (int li = 0; li < lig_begin; ++li) conf_base += lg->n_conf[li];
+  const bool host_out = !export_E && ((logZ && !is_device_ptr(logZ)) || (n_valid && !is_device_ptr(n_valid)) ||
+                                      (bpmf_out && !is_device_ptr(bpmf_out)) || (dG && !is_device_ptr(dG)));
+  // graph replay: same handles, mode, kT and output buffers as the cached graph
+  const bool use_graph = c->graph_mode && !export_E && !host_out && st != nullptr && !c->prof;
+  std::vector<unsigned long long> key;
+  if (use_graph) {
+    key = {lg->id, (unsigned long long)K, mode, (unsigned long long)c->ws_budget};
+    for (int k = 0; k < K; ++k) key.push_back(recs[k]->id);
+    unsigned long long kb;
+    std::memcpy(&kb, &kT, sizeof(kb));
+    key.push_back(kb);
+    for (const void *q : {(const void *)logZ, (const void *)n_valid, (const void *)bpmf_out, (const void *)dG})
+      key.push_back((unsigned long long)(uintptr_t)q);
+    for (const auto &g : groups) {
+      const bpmf_ctx::Tune t = tune_for(c, g.P, mode);
+      key.insert(key.end(), {(unsigned long long)t.batch_cap, (unsigned long long)t.axis_lw,
+                             (unsigned long long)t.zfwd_l});
+    }
+    if (c->gexec && key == c->gkey) {
+      CK(cudaGraphLaunch(c->gexec, st));
+      CK(cudaEventRecord(c->pinned_busy, st));
+      return lg_warn_cached(c) ? BPMF_WARN_NO_VALID : BPMF_OK;
+    }
+  }
 
+  // ---------------------------------------------------------------- plan
+  std::vector<char> blob;
+  auto put = [&](const void *src, size_t bytes) {
+    const size_t o = blob.size();
+    blob.resize(o + align_up(bytes));
+    if (bytes) std::memcpy(blob.data() + o, src, bytes);
+    return o;
+  };
+  bool warn = false;
+  std::vector<LigPlan> plans;
   std::vector<ConfMeta> meta;
   std::vector<PairInfo> info;
   std::vector<long long> nv;
+  size_t ws_need = 0;
   for (int li = lig_begin; li < lig_end; ++li) {
     ligand_tables(lg, li, recs, K, h, meta, info, nv);
-    int J = lg->n_conf[li];
-    int j_first = 0;
+    LigPlan pl;
+    pl.li = li;
+    pl.J = lg->n_conf[li];
     if (only_conf >= 0) {
-      if (only_conf >= J) throw Fail{BPMF_ERR_INVALID_ARG};
-      j_first = only_conf;
-      J = 1;
+      if (only_conf >= pl.J) throw Fail{BPMF_ERR_INVALID_ARG};
+      pl.j_first = only_conf;
+      pl.J = 1;
     }
-    // ligand-wide box size (clamped to the FFT edges)
-    int Umax[3] = {1, 1, 1};
-    for (int j = j_first; j < j_first + J; ++j)
-      for (int d = 0; d < 3; ++d) Umax[d] = std::max(Umax[d], std::min(meta[j].u[d], r0->P[d]));
-    Umax[1] += Umax[1] & 1;
-    for (int j = j_first; j < j_first + J; ++j)
-      for (int k = 0; k < K; ++k)
-        if (nv[(size_t)j * K + k] == 0) warn = true;
-    BatchGeom g{};
-    for (int d = 0; d < 3; ++d) {
-      g.U[d] = Umax[d];
-      g.P[d] = r0->P[d];
-      g.S[d] = S[d];
-    }
-    g.F2 = r0->F2;
-    g.Q = r0->Q;
-    g.K = K;
-    const size_t per_conf = batch_bytes_per_conf(g, E);
-    // configurations are processed sorted by ligand-box extent, so each batch's
-    // box (the maximum over its members) stays tight; the merge scatters the
-    // results back to the caller's order
+    const int J = pl.J;
+    // process configurations sorted by ligand-box extent, so each batch's box
+    // (the maximum over its members) stays tight; the merge scatters results
+    // back to the caller's order
     std::vector<int> order(J);
-    for (int i = 0; i < J; ++i) order[i] = j_first + i;
+    for (int i = 0; i < J; ++i) order[i] = pl.j_first + i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
       for (int d = 0; d < 3; ++d)
         if (meta[a].u[d] != meta[b].u[d]) return meta[a].u[d] < meta[b].u[d];
       return false;
     });
     std::vector<ConfMeta> meta_s(std::max(J, 1));
-    std::vector<PairInfo> info_s((size_t)std::max(J, 1) * K);
     std::vector<long long> nv_s((size_t)std::max(J, 1) * K);
     std::vector<int> ord_s(std::max(J, 1));
     for (int i = 0; i < J; ++i) {
       meta_s[i] = meta[order[i]];
-      ord_s[i] = order[i] - j_first;
+      ord_s[i] = order[i] - pl.j_first;
       for (int k = 0; k < K; ++k) {
-        info_s[(size_t)i * K + k] = info[(size_t)order[i] * K + k];
         nv_s[(size_t)i * K + k] = nv[(size_t)order[i] * K + k];
+        if (nv_s[(size_t)i * K + k] == 0) warn = true;
       }
     }
-    // fixed part of the workspace: tables, partials, merge outputs
+    pl.off_meta = put(meta_s.data(), sizeof(ConfMeta) * J);
+    pl.off_order = put(ord_s.data(), sizeof(int) * J);
+    pl.off_nv = put(nv_s.data(), sizeof(long long) * J * K);
     const size_t JK = (size_t)std::max(J, 1) * K;
-    const size_t fixed = align_up(sizeof(ConfMeta) * std::max(J, 1)) + align_up(sizeof(PairInfo) * JK) +
-                         align_up(sizeof(long long) * JK) * 2 + align_up(sizeof(float4) * JK * S[0]) +
-                         align_up(sizeof(double) * JK) * 2 + align_up(sizeof(double) * (K + 1)) +
-                         align_up(2 * sizeof(void *) * K) + align_up(sizeof(int) * std::max(J, 1));
-    int B = (int)std::max<size_t>(1, (c->ws_budget > fixed ? c->ws_budget - fixed : 0) / per_conf);
-    B = std::min(B, std::max(J, 1));
-    char *ws = static_cast<char *>(workspace(c, fixed + per_conf * B, st));
-    char *p = ws;
-    ConfMeta *d_meta = reinterpret_cast<ConfMeta *>(p);
-    p += align_up(sizeof(ConfMeta) * std::max(J, 1));
-    PairInfo *d_info = reinterpret_cast<PairInfo *>(p);
-    p += align_up(sizeof(PairInfo) * JK);
-    long long *d_nv = reinterpret_cast<long long *>(p);  // processing order
-    p += align_up(sizeof(long long) * JK);
-    long long *d_nvout = reinterpret_cast<long long *>(p);  // caller order
-    p += align_up(sizeof(long long) * JK);
-    float4 *d_part = reinterpret_cast<float4 *>(p);
-    p += align_up(sizeof(float4) * JK * S[0]);
-    double *d_logZ = reinterpret_cast<double *>(p);
-    p += align_up(sizeof(double) * JK);
-    double *d_logS = reinterpret_cast<double *>(p);
-    p += align_up(sizeof(double) * JK);
-    double *d_B = reinterpret_cast<double *>(p);  // [K] + dG
-    p += align_up(sizeof(double) * (K + 1));
-    const float2 **d_rptr = reinterpret_cast<const float2 **>(p);
-    p += align_up(2 * sizeof(void *) * K);
-    int *d_order = reinterpret_cast<int *>(p);
-    p += align_up(sizeof(int) * std::max(J, 1));
-    char *d_batch = p;
-    if (J > 0) {
-      CK(cudaMemcpyAsync(d_meta, meta_s.data(), sizeof(ConfMeta) * J, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(d_info, info_s.data(), sizeof(PairInfo) * J * K, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(d_nv, nv_s.data(), sizeof(long long) * J * K, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(d_order, ord_s.data(), sizeof(int) * J, cudaMemcpyHostToDevice, st));
-    }
-    CK(cudaMemcpyAsync(d_rptr, hrhi.data(), sizeof(void *) * K, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_rptr + K, hrlo.data(), sizeof(void *) * K, cudaMemcpyHostToDevice, st));
-    for (int b0 = 0; b0 < J; b0 += B) {
-      const int nb = std::min(B, J - b0);
-      BatchGeom gb = g;
-      for (int d = 0; d < 3; ++d) {
-        gb.U[d] = 1;
-        for (int j = b0; j < b0 + nb; ++j) gb.U[d] = std::max(gb.U[d], std::min(meta_s[j].u[d], r0->P[d]));
+    size_t fixed = align_up(sizeof(long long) * JK) + align_up(sizeof(double) * JK) * 2 +
+                   align_up(sizeof(double) * (K + 1));
+    size_t batch_bytes = 0;
+    for (const auto &g : groups) {
+      const int Kg = (int)g.ks.size();
+      std::vector<PairInfo> info_g((size_t)std::max(J, 1) * Kg);
+      for (int i = 0; i < J; ++i)
+        for (int kg = 0; kg < Kg; ++kg) info_g[(size_t)i * Kg + kg] = info[(size_t)order[i] * K + g.ks[kg]];
+      pl.off_info.push_back(put(info_g.data(), sizeof(PairInfo) * J * Kg));
+      pl.off_kmap.push_back(put(g.ks.data(), sizeof(int) * Kg));
+      std::vector<const float2 *> rp(2 * Kg);
+      for (int kg = 0; kg < Kg; ++kg) {
+        rp[kg] = recs[g.ks[kg]]->hi;
+        rp[Kg + kg] = recs[g.ks[kg]]->lo;
       }
-      // z rows are transformed in (y, y+1) pairs: an even y extent keeps each
-      // pair inside one plane, so results do not depend on the batching
-      gb.U[1] += gb.U[1] & 1;
-      if (use_ff)
-        run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * K, d_rptr, d_rptr + K, h, nsh, nsl, esh,
-                      esl, d_part + (size_t)b0 * K * S[0], export_E, d_batch, st);
-      else
-        run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * K, d_rptr, nullptr, h, nsh, nsl, esh,
-                         esl, d_part + (size_t)b0 * K * S[0], export_E, d_batch, st);
+      pl.off_rptr.push_back(put(rp.data(), sizeof(void *) * 2 * Kg));
+      std::array<int, 3> Um{1, 1, 1};
+      for (int i = 0; i < J; ++i)
+        for (int d = 0; d < 3; ++d) Um[d] = std::max(Um[d], std::min(meta_s[i].u[d], g.P[d]));
+      Um[1] += Um[1] & 1;
+      pl.Umax.push_back(Um);
+      BatchGeom bg{};
+      for (int d = 0; d < 3; ++d) {
+        bg.U[d] = Um[d];
+        bg.P[d] = g.P[d];
+        bg.S[d] = g.S[d];
+      }
+      bg.F2 = g.F2;
+      bg.Q = g.Q;
+      bg.K = Kg;
+      const size_t per_conf = batch_bytes_per_conf(bg, E);
+      const size_t part = align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
+      const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
+      int B = (int)std::max<size_t>(1, (c->ws_budget > fixed + part ? c->ws_budget - fixed - part : 0) / per_conf);
+      if (tn.batch_cap > 0) B = std::min(B, tn.batch_cap);
+      B = std::min(B, std::max(J, 1));
+      pl.B.push_back(B);
+      std::vector<std::array<int, 3>> ub;
+      for (int b0 = 0; b0 < J; b0 += B) {
+        std::array<int, 3> U{1, 1, 1};
+        for (int i = b0; i < std::min(J, b0 + B); ++i)
+          for (int d = 0; d < 3; ++d) U[d] = std::max(U[d], std::min(meta_s[i].u[d], g.P[d]));
+        // z rows are transformed in (y, y+1) pairs: an even y extent keeps each
+        // pair inside one plane, so results do not depend on the batching
+        U[1] += U[1] & 1;
+        ub.push_back(U);
+      }
+      pl.Ub.push_back(ub);
+      batch_bytes = std::max(batch_bytes, part + per_conf * B);
     }
-    if (export_E) break;
-    MergeArgs ma{};
-    ma.part = d_part;
-    ma.nvalid = d_nv;
-    ma.J = J;
-    ma.K = K;
-    ma.S0 = S[0];
-    ma.kT = kT;
-    ma.vsite_scale = h * h * h / 1660.5390;
-    ma.order = d_order;
-    ma.logS = d_logS;
-    ma.logZ = d_logZ;
-    ma.bpmf = d_B;
-    ma.dG = d_B + K;
-    ma.nvalid_out = d_nvout;
-    launch(c, "k_merge", st, [&] { return launch_merge(ma, st); });
-    const long long ob = conf_base;
-    if (J > 0) {
-      CK(cudaMemcpyAsync(logZ + ob * K, d_logZ, sizeof(double) * J * K, cudaMemcpyDefault, st));
-      if (n_valid) CK(cudaMemcpyAsync(n_valid + ob * K, d_nvout, sizeof(int64_t) * J * K, cudaMemcpyDefault, st));
-    }
-    if (bpmf_out) CK(cudaMemcpyAsync(bpmf_out + (size_t)li * K, d_B, sizeof(double) * K, cudaMemcpyDefault, st));
-    if (dG) CK(cudaMemcpyAsync(dG + li, d_B + K, sizeof(double), cudaMemcpyDefault, st));
-    // the next ligand reuses the workspace; stream order keeps these copies first
-    conf_base += lg->n_conf[li];
+    pl.fixed = fixed;
+    pl.batch_bytes = batch_bytes;
+    ws_need = std::max(ws_need, fixed + batch_bytes);
+    plans.push_back(std::move(pl));
   }
-  if (!export_E && ((logZ && !is_device_ptr(logZ)) || (n_valid && !is_device_ptr(n_valid)) ||
-                    (bpmf_out && !is_device_ptr(bpmf_out)) || (dG && !is_device_ptr(dG))))
-    CK(cudaStreamSynchronize(st));
+  const size_t blob_bytes = align_up(blob.size());
+  // device resources are made ready before any work is queued (and so before
+  // a capture begins): workspace, pinned staging, twiddle tables
+  char *ws = static_cast<char *>(workspace(c, blob_bytes + ws_need, st));
+  // the pinned staging is rewritten: wait for the last copy or graph replay
+  // that reads it, and drop the cached graph, whose copy node points at it
+  if (!c->pinned_busy) CK(cudaEventCreateWithFlags(&c->pinned_busy, cudaEventDisableTiming));
+  CK(cudaEventSynchronize(c->pinned_busy));
+  if (c->gexec) {
+    CK(cudaGraphExecDestroy(c->gexec));
+    c->gexec = nullptr;
+    c->gkey.clear();
+  }
+  if (blob_bytes > c->pinned_bytes) {
+    if (c->pinned) {
+      CK(cudaFreeHost(c->pinned));
+      c->pinned = nullptr;
+      c->pinned_bytes = 0;
+    }
+    CK(cudaMallocHost(&c->pinned, blob_bytes));
+    c->pinned_bytes = blob_bytes;
+  }
+  if (!blob.empty()) std::memcpy(c->pinned, blob.data(), blob.size());
+  for (const auto &g : groups)
+    for (int d = 0; d < 3; ++d) twiddles(c, g.P[d]);
+  c->warn_last = warn;
+
+  // -------------------------------------------------------------- execute
+  if (use_graph) CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  try {
+    char *tab = ws;
+    char *lw = ws + blob_bytes;
+    if (blob_bytes) {
+      CK(cudaMemcpyAsync(tab, c->pinned, blob.size(), cudaMemcpyHostToDevice, st));
+      if (!use_graph) CK(cudaEventRecord(c->pinned_busy, st));
+    }
+    long long conf_base = 0;
+    for (int li = 0; li < lig_begin; ++li) conf_base += lg->n_conf[li];
+    for (const LigPlan &pl : plans) {
+      const int J = pl.J;
+      const size_t JK = (size_t)std::max(J, 1) * K;
+      char *p = lw;
+      long long *d_nvout = reinterpret_cast<long long *>(p);
+      p += align_up(sizeof(long long) * JK);
+      double *d_logZ = reinterpret_cast<double *>(p);
+      p += align_up(sizeof(double) * JK);
+      double *d_logS = reinterpret_cast<double *>(p);
+      p += align_up(sizeof(double) * JK);
+      double *d_B = reinterpret_cast<double *>(p);
+      p += align_up(sizeof(double) * (K + 1));
+      char *d_grp = p;  // partials + batch buffers, reused group by group
+      const ConfMeta *d_meta = reinterpret_cast<const ConfMeta *>(tab + pl.off_meta);
+      const int *d_order = reinterpret_cast<const int *>(tab + pl.off_order);
+      const long long *d_nv = reinterpret_cast<const long long *>(tab + pl.off_nv);
+      for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const RecGroup &g = groups[gi];
+        const int Kg = (int)g.ks.size();
+        const PairInfo *d_info = reinterpret_cast<const PairInfo *>(tab + pl.off_info[gi]);
+        const float2 *const *d_rptr = reinterpret_cast<const float2 *const *>(tab + pl.off_rptr[gi]);
+        float4 *d_part = reinterpret_cast<float4 *>(d_grp);
+        char *d_batch = d_grp + align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
+        const double norm = 1.0 / ((double)g.P[0] * g.P[1] * g.P[2]);
+        float nsh, nsl, esh, esl;
+        split_ff(-norm / kT, nsh, nsl);
+        split_ff(norm, esh, esl);
+        const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
+        const int B = pl.B[gi];
+        for (int b0 = 0, bi = 0; b0 < J; b0 += B, ++bi) {
+          const int nb = std::min(B, J - b0);
+          BatchGeom gb{};
+          for (int d = 0; d < 3; ++d) {
+            gb.U[d] = pl.Ub[gi][bi][d];
+            gb.P[d] = g.P[d];
+            gb.S[d] = g.S[d];
+          }
+          gb.F2 = g.F2;
+          gb.Q = g.Q;
+          gb.K = Kg;
+          if (use_ff)
+            run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, d_rptr + Kg, h, nsh, nsl,
+                          esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn);
+          else
+            run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, nullptr, h, nsh, nsl,
+                             esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn);
+        }
+        if (export_E) continue;
+        MergeArgs ma{};
+        ma.part = d_part;
+        ma.nvalid = d_nv;
+        ma.order = d_order;
+        ma.kmap = reinterpret_cast<const int *>(tab + pl.off_kmap[gi]);
+        ma.Kg = Kg;
+        ma.J = J;
+        ma.K = K;
+        ma.S0 = g.S[0];
+        ma.logS = d_logS;
+        ma.logZ = d_logZ;
+        ma.nvalid_out = d_nvout;
+        launch(c, "k_merge", st, [&] { return launch_merge_pairs(ma, st); });
+      }
+      if (export_E) break;
+      MergeArgs mf{};
+      mf.nvalid = d_nv;
+      mf.J = J;
+      mf.K = K;
+      mf.kT = kT;
+      mf.vsite_scale = h * h * h / 1660.5390;
+      mf.logS = d_logS;
+      mf.logZ = d_logZ;
+      mf.bpmf = d_B;
+      mf.dG = d_B + K;
+      launch(c, "k_merge", st, [&] { return launch_merge(mf, st); });
+      if (J > 0) {
+        CK(cudaMemcpyAsync(logZ + conf_base * K, d_logZ, sizeof(double) * J * K, cudaMemcpyDefault, st));
+        if (n_valid)
+          CK(cudaMemcpyAsync(n_valid + conf_base * K, d_nvout, sizeof(int64_t) * J * K, cudaMemcpyDefault, st));
+      }
+      if (bpmf_out)
+        CK(cudaMemcpyAsync(bpmf_out + (size_t)pl.li * K, d_B, sizeof(double) * K, cudaMemcpyDefault, st));
+      if (dG) CK(cudaMemcpyAsync(dG + pl.li, d_B + K, sizeof(double), cudaMemcpyDefault, st));
+      // the next ligand reuses the workspace; stream order keeps these copies first
+      conf_base += lg->n_conf[pl.li];
+    }
+  } catch (Fail f) {
+    if (use_graph) {
+      cudaGraph_t gr = nullptr;
+      cudaStreamEndCapture(st, &gr);
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+    }
+    throw;
+  }
+  if (use_graph) {
+    cudaGraph_t gr = nullptr;
+    CK(cudaStreamEndCapture(st, &gr));
+    const cudaError_t ie = cudaGraphInstantiate(&c->gexec, gr, 0);
+    cudaGraphDestroy(gr);
+    CK(ie);
+    c->gkey = key;
+    CK(cudaGraphLaunch(c->gexec, st));
+    CK(cudaEventRecord(c->pinned_busy, st));
+  }
+  if (host_out) CK(cudaStreamSynchronize(st));
   return warn ? BPMF_WARN_NO_VALID : BPMF_OK;
 }
 
@@ -940,6 +1136,80 @@ int bpmf_eval(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double
   } catch (std::bad_alloc &) {
     return set_err(c, BPMF_ERR_OOM, "host allocation");
   }
+}
+
+int bpmf_autotune(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, unsigned mode, void *stream) {
+  if (!c || !lg || !recs || K < 1 || lg->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or K < 1");
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF) return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
+  DeviceGuard dg(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long JK = std::max<long long>(1, lg->total_conf) * K;
+  double *d_logZ = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool prof = c->prof, graph = c->graph_mode;
+  try {
+    last_msg.clear();
+    check_recs(recs, K, c);
+    c->prof = false;
+    c->graph_mode = false;
+    CK(cudaMallocAsync(&d_logZ, sizeof(double) * JK, st));
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    std::vector<std::vector<int>> keys;
+    for (const auto &g : group_receptors(recs, K)) keys.push_back({g.P[0], g.P[1], g.P[2], (int)mode});
+    auto apply = [&](const bpmf_ctx::Tune &t) {
+      for (const auto &k : keys) c->tune[k] = t;
+    };
+    auto timeit = [&](const bpmf_ctx::Tune &t) {
+      apply(t);
+      eval_impl(c, lg, recs, K, 1.0, mode, d_logZ, nullptr, nullptr, nullptr, st, -1, -1, nullptr);
+      CK(cudaEventRecord(e0, st));
+      eval_impl(c, lg, recs, K, 1.0, mode, d_logZ, nullptr, nullptr, nullptr, st, -1, -1, nullptr);
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      return ms;
+    };
+    // coordinate descent over launch shapes that leave every result bit unchanged
+    bpmf_ctx::Tune best;
+    float tbest = timeit(best);
+    for (int cap : {256, 128, 64, 32}) {
+      bpmf_ctx::Tune t = best;
+      t.batch_cap = cap;
+      const float tt = timeit(t);
+      if (tt < tbest) tbest = tt, best = t;
+    }
+    for (int lw : {8}) {
+      bpmf_ctx::Tune t = best;
+      t.axis_lw = lw;
+      const float tt = timeit(t);
+      if (tt < tbest) tbest = tt, best = t;
+    }
+    for (int l : {8}) {
+      bpmf_ctx::Tune t = best;
+      t.zfwd_l = l;
+      const float tt = timeit(t);
+      if (tt < tbest) tbest = tt, best = t;
+    }
+    apply(best);
+    CK(cudaFreeAsync(d_logZ, st));
+    d_logZ = nullptr;
+    CK(cudaStreamSynchronize(st));
+  } catch (Fail f) {
+    if (d_logZ) cudaFreeAsync(d_logZ, st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    c->prof = prof;
+    c->graph_mode = graph;
+    return set_err(c, f.code, last_msg.empty() ? bpmf_status_string(f.code) : last_msg);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->prof = prof;
+  c->graph_mode = graph;
+  c->err.clear();
+  return BPMF_OK;
 }
 
 int bpmf_export_energies(bpmf_ctx_t c, bpmf_lig_t lg, bpmf_rec_t rec, int lig_index, int conf_index, unsigned mode,

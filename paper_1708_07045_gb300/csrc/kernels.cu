@@ -534,9 +534,11 @@ cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st) {
 //   B_k      = -kT [ LSE_j log S_jk - ln sum_j n_jk ]
 //   dG       = -kT [ LSE_k (-B_k / kT) - ln K ] - kT ln(V_site C)
 __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
-  const int JK = a.J * a.K;
+  const int JK = a.J * a.Kg;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= JK) return;
+  const int j = p / a.Kg, kg = p % a.Kg;
+  const int k = a.kmap ? a.kmap[kg] : kg;
   const float4 *pp = a.part + (long long)p * a.S0;
   double Mx = -CUDART_INF;
   for (int c = 0; c < a.S0; ++c)
@@ -545,11 +547,12 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
   if (Mx > -CUDART_INF)
     for (int c = 0; c < a.S0; ++c)
       if (pp[c].z > 0.f) s += (double)pp[c].z * exp((double)pp[c].x + (double)pp[c].y - Mx);
-  const long long n = a.nvalid[p];
+  const long long pk = (long long)j * a.K + k;
+  const long long n = a.nvalid[pk];
   const double ls = (s > 0.0 && n > 0) ? Mx + log(s) : -CUDART_INF;
-  a.logS[p] = ls;
+  a.logS[pk] = ls;
   // processing position -> caller's configuration order
-  const long long q = (long long)(a.order ? a.order[p / a.K] : p / a.K) * a.K + p % a.K;
+  const long long q = (long long)(a.order ? a.order[j] : j) * a.K + k;
   a.logZ[q] = n > 0 ? ls - log((double)n) : -CUDART_INF;
   if (a.nvalid_out) a.nvalid_out[q] = n;
 }
@@ -612,9 +615,13 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
   }
 }
 
-cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st) {
-  const int JK = a.J * a.K;
+cudaError_t launch_merge_pairs(const MergeArgs &a, cudaStream_t st) {
+  const int JK = a.J * a.Kg;
   if (JK > 0) k_merge_pairs<<<(JK + 127) / 128, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st) {
   k_merge<<<1, 256, 0, st>>>(a);
   return cudaGetLastError();
 }

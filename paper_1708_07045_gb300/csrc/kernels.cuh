@@ -90,10 +90,12 @@ struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp pa
 };
 
 struct MergeArgs {
-  const float4 *part;      // [J][K][S0], configurations in processing order
-  const long long *nvalid; // [J][K], processing order
+  const float4 *part;      // [J][Kg][S0] of one receptor group, processing order
+  const long long *nvalid; // [J][K], processing order, all receptors
   const int *order;        // [J] processing position -> caller's configuration index (null: identity)
-  double *logS;            // [J][K] scratch
+  const int *kmap;         // [Kg] group-local receptor -> receptor index in the call (null: identity)
+  int Kg;                  // receptors in the group (k_merge_pairs)
+  double *logS;            // [J][K] scratch, processing order
   int J, K, S0;
   double kT;
   double vsite_scale;      // h^3 * C_standard
@@ -109,7 +111,8 @@ template <class T> cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st);
 template <class T> cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st);
 template <class T> cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st);
 template <class T> cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st);
-cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st);
+cudaError_t launch_merge_pairs(const MergeArgs &a, cudaStream_t st);  // per receptor group
+cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st);        // B_k and dG over all receptors
 cudaError_t launch_split_ff(const void *spec, float2 *hi, float2 *lo, long long n, cudaStream_t st);
 cudaError_t launch_gamma(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, float2 *gamma,
                          cudaStream_t st);

@@ -216,10 +216,10 @@ def test_bad_arguments_return_status(pkg, small):
         assert e.value.status == pkg.BPMF_ERR_SIZE_UNSUPPORTED
         assert pkg.lib().bpmf_eval(s.ctx, None, None, 0, 1.0, 0, None, None, None, None, None) == \
             pkg.BPMF_ERR_INVALID_ARG
-        # receptors whose padded edges differ cannot share one evaluation
+        # receptors with different grid spacings cannot share one evaluation
         r1 = s.load_receptor(r)
         g2 = np.zeros((3, 40, 32, 32), dtype=np.float32)
-        r2 = pkg.bpmf_receptor_load(s.ctx, g2, r.h, r.origin, r.site_lo, r.site_n)
+        r2 = pkg.bpmf_receptor_load(s.ctx, g2, r.h * 1.5, r.origin, r.site_lo, r.site_n)
         lh, _, _ = s.load_ligands([small.ligands[0]])
         with pytest.raises(pkg.BpmfError) as e:
             s.eval(lh, [r1, r2], KT, pkg.BPMF_MODE_FF, total_conf=64)
