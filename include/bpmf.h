@@ -201,6 +201,83 @@ int bpmf_set_graph_mode(bpmf_ctx_t ctx, int on);
  */
 int bpmf_autotune(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, int K, unsigned mode, void *stream);
 
+/* bpmf_valid_counts -- number of valid translations n_jk of every
+ * configuration against every receptor (the ligand-box filter of bpmf_eval),
+ * computed on the host from the configurations' coordinate bounds.
+ * n_valid: HOST int64 [total_conf][K].  Errors: INVALID_ARG, SIZE_UNSUPPORTED. */
+int bpmf_valid_counts(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, int K, int64_t *n_valid);
+
+/* ------------------------------------------------------------------------
+ * Learned proposal over configurations.  A small MLP predicts, from a
+ * configuration's features, log sum_k S_jk (its weight in the sample mean of
+ * Eq. sample_mean_BPMF).  Configurations are then drawn from
+ * q_j = mix * softmax(pred)_j + (1 - mix) / J, and the BPMF is estimated by
+ * importance weighting, which stays unbiased for Z_k = sum_j S_jk thanks to
+ * the uniform component.  The full enumeration (bpmf_eval) is the fallback and
+ * the judge of its error.
+ * ------------------------------------------------------------------------ */
+#define BPMF_N_FEATURES 24
+
+/* bpmf_features -- per configuration, 24 float32 features:
+ *  [0..3]   unit quaternion (w >= 0) of the rotation from the principal frame
+ *           of the gyration tensor (axes by ascending moment, first two signed
+ *           by a positive third moment, right-handed) to the lab frame;
+ *  [4..6]   ligand-box extents u_d = ceil((max - min) / h) + 4 (nodes);
+ *  [7..9]   principal moments of the gyration tensor (A^2), ascending;
+ *  [10]     radius of gyration (A);  [11] end-to-end (first-last atom) distance;
+ *  [12..15] sin, cos of the torsions of atoms (0,1,2,3) and (1,2,3,4);
+ *  [16..23] atom counts in the 8 classes (R > 1.75) x (eps > 0.125) x (q > 0).
+ * out: [total_conf][24], host or device.  Synchronises `stream`.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int bpmf_features(bpmf_ctx_t ctx, bpmf_lig_t lig, double h, float *out, void *stream);
+
+typedef struct bpmf_mlp *bpmf_mlp_t;
+
+/* Number of parameters of an MLP with n_in inputs, `depth` hidden ReLU layers
+ * of `width` units and one output (0 for invalid sizes). */
+long long bpmf_mlp_param_count(int n_in, int width, int depth);
+
+/* bpmf_mlp_create -- an MLP n_in -> width (ReLU) -> ... -> width (ReLU) -> 1.
+ *  params  HOST float32, packed layer by layer: W_l [in_l][out_l] row-major,
+ *          then b_l [out_l]; bpmf_mlp_param_count() values.
+ *  norm    HOST float32 [2 n_in + 2]: input shift[n_in], input scale[n_in],
+ *          target shift, target scale (inputs are (x - shift) / scale; the
+ *          network predicts (y - shift) / scale).
+ * Weights are kept in FP32 (master copy for Adam); every GEMM rounds its
+ * operands to bf16 and runs on the tensor cores with FP32 accumulation.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int bpmf_mlp_create(bpmf_ctx_t ctx, int n_in, int width, int depth, const float *params, const float *norm,
+                    bpmf_mlp_t *out);
+void bpmf_mlp_free(bpmf_mlp_t mlp);
+/* Copy the current FP32 parameters (packed as in bpmf_mlp_create) to HOST params. */
+int bpmf_mlp_get_params(bpmf_mlp_t mlp, float *params);
+/* y[B] = prediction for features X[B][n_in]; both DEVICE memory. Stream ordered. */
+int bpmf_mlp_forward(bpmf_ctx_t ctx, bpmf_mlp_t mlp, const float *X, int B, float *y, void *stream);
+/* One training step on (X[B][n_in], t[B]) (DEVICE): mean squared error in
+ * normalised units, backward pass, and (apply != 0) one Adam step with
+ * learning rate lr (beta 0.9 / 0.999, eps 1e-8).  loss (host or device,
+ * optional) receives the loss before the step; grads (device, optional) the
+ * packed parameter gradients.  Synchronises `stream`. */
+int bpmf_mlp_train_step(bpmf_ctx_t ctx, bpmf_mlp_t mlp, const float *X, const float *t, int B, float lr, int apply,
+                        float *loss, float *grads, void *stream);
+
+/* bpmf_proposal_sample -- q = mix softmax(pred) + (1 - mix)/J over J
+ * configurations (FP64); for each caller-supplied uniform u_s in [0,1) the
+ * index of the first configuration whose cumulative q exceeds u_s, and q of
+ * that configuration.  pred [J] float32, u [M] float64, idx [M] int32, q_s [M]
+ * float64: DEVICE memory.  Stream ordered.  Errors: INVALID_ARG, OOM, CUDA. */
+int bpmf_proposal_sample(bpmf_ctx_t ctx, const float *pred, int J, double mix, const double *u, int M, int *idx,
+                         double *q_s, void *stream);
+
+/* bpmf_proposal_bpmf -- importance-weighted BPMF per receptor from M sampled
+ * configurations: Z_k = (1/M) sum_s S_{j_s k} / q_s with S = exp(logZ) n,
+ * B_k = -kT [ln Z_k - ln n_tot_k].  logZ_s [M][K], n_s [M][K] (as returned by
+ * bpmf_eval for the sampled configurations), q_s [M], n_tot [K] (valid
+ * translations summed over all J configurations), bpmf [K]: DEVICE memory,
+ * FP64 arithmetic.  Errors: INVALID_ARG, CUDA. */
+int bpmf_proposal_bpmf(bpmf_ctx_t ctx, const double *logZ_s, const int64_t *n_s, const double *q_s, int M, int K,
+                       const int64_t *n_tot, double kT, double *bpmf, void *stream);
+
 /*
  * Kernel timing (tracing).  While enabled, every kernel the library launches
  * is bracketed by CUDA events recorded on the stream it runs on.

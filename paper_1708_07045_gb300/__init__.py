@@ -22,8 +22,8 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "libbpmf.so")
-_SOURCES = ["kernels.cu", "bpmf_api.cu", "bpmf_static.cu"]
-_HEADERS = ["arith.cuh", "fft.cuh", "kernels.cuh"]
+_SOURCES = ["kernels.cu", "bpmf_api.cu", "bpmf_static.cu", "proposal.cu", "bpmf_proposal.cu"]
+_HEADERS = ["arith.cuh", "fft.cuh", "kernels.cuh", "proposal.cuh"]
 
 BPMF_OK = 0
 BPMF_ERR_INVALID_ARG = -1
@@ -113,6 +113,16 @@ _SIGS = {
     "bpmf_profile_count": (_I, [_P]),
     "bpmf_profile_entry": (_I, [_P, _I, ctypes.c_char_p, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)]),
     "bpmf_set_graph_mode": (_I, [_P, _I]),
+    "bpmf_features": (_I, [_P, _P, _D, _P, _P]),
+    "bpmf_valid_counts": (_I, [_P, _P, _P, _I, _P]),
+    "bpmf_mlp_param_count": (ctypes.c_longlong, [_I, _I, _I]),
+    "bpmf_mlp_create": (_I, [_P, _I, _I, _I, _P, _P, ctypes.POINTER(_P)]),
+    "bpmf_mlp_free": (None, [_P]),
+    "bpmf_mlp_get_params": (_I, [_P, _P]),
+    "bpmf_mlp_forward": (_I, [_P, _P, _P, _I, _P, _P]),
+    "bpmf_mlp_train_step": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, _I, _P, _P, _P]),
+    "bpmf_proposal_sample": (_I, [_P, _P, _I, _D, _P, _I, _P, _P, _P]),
+    "bpmf_proposal_bpmf": (_I, [_P, _P, _P, _P, _I, _I, _P, _D, _P, _P]),
     "bpmf_autotune": (_I, [_P, _P, _P, _I, ctypes.c_uint, _P]),
     "bpmf_export_energies_static": (_I, [_P, _I, _I, _I, _D, _P, _P, _I, _P, _P, _P, _P, _I, _I, ctypes.c_uint, _P,
                                          _P]),
@@ -310,3 +320,76 @@ def bpmf_export_energies_static(grids, h, site_lo, site_n, coords, q, eps, R, mo
                                            int(p_rep), int(p_att), int(mode), _ptr(out, np.float64),
                                            _stream(stream))
     return _check(rc, "bpmf_export_energies_static")
+
+
+BPMF_N_FEATURES = 24
+
+
+def bpmf_features(ctx, lig, h, out, stream=None):
+    """out: float32 [total_conf, 24] (numpy or torch, host or device)."""
+    _check(lib().bpmf_features(ctx, lig, float(h), _ptr(out, np.float32), _stream(stream)), "bpmf_features", ctx)
+
+
+def bpmf_mlp_param_count(n_in, width, depth) -> int:
+    return int(lib().bpmf_mlp_param_count(int(n_in), int(width), int(depth)))
+
+
+def bpmf_mlp_create(ctx, n_in, width, depth, params, norm):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    nm = np.ascontiguousarray(norm, dtype=np.float32)
+    if p.size != bpmf_mlp_param_count(n_in, width, depth) or nm.size != 2 * n_in + 2:
+        raise ValueError("parameter / normalisation sizes do not match the network shape")
+    out = ctypes.c_void_p()
+    _check(lib().bpmf_mlp_create(ctx, int(n_in), int(width), int(depth), _ptr(p, np.float32),
+                                 _ptr(nm, np.float32), ctypes.byref(out)), "bpmf_mlp_create", ctx)
+    return out
+
+
+def bpmf_mlp_free(mlp):
+    lib().bpmf_mlp_free(mlp)
+
+
+def bpmf_mlp_get_params(mlp, n_params):
+    out = np.empty(int(n_params), dtype=np.float32)
+    _check(lib().bpmf_mlp_get_params(mlp, _ptr(out, np.float32)), "bpmf_mlp_get_params")
+    return out
+
+
+def bpmf_mlp_forward(ctx, mlp, X, y, stream=None):
+    B = int(tuple(X.shape)[0])
+    _check(lib().bpmf_mlp_forward(ctx, mlp, _ptr(X, np.float32), B, _ptr(y, np.float32), _stream(stream)),
+           "bpmf_mlp_forward", ctx)
+
+
+def bpmf_mlp_train_step(ctx, mlp, X, t, lr, apply=True, grads=None, stream=None) -> float:
+    B = int(tuple(X.shape)[0])
+    loss = np.zeros(1, dtype=np.float32)
+    _check(lib().bpmf_mlp_train_step(ctx, mlp, _ptr(X, np.float32), _ptr(t, np.float32), B, float(lr),
+                                     1 if apply else 0, _ptr(loss, np.float32),
+                                     _ptr(grads, np.float32) if grads is not None else None, _stream(stream)),
+           "bpmf_mlp_train_step", ctx)
+    return float(loss[0])
+
+
+def bpmf_proposal_sample(ctx, pred, mix, u, idx, q_s, stream=None):
+    J = int(tuple(pred.shape)[0])
+    M = int(tuple(u.shape)[0])
+    _check(lib().bpmf_proposal_sample(ctx, _ptr(pred, np.float32), J, float(mix), _ptr(u, np.float64), M,
+                                      _ptr(idx, np.int32), _ptr(q_s, np.float64), _stream(stream)),
+           "bpmf_proposal_sample", ctx)
+
+
+def bpmf_proposal_bpmf(ctx, logZ_s, n_s, q_s, n_tot, kT, bpmf, stream=None):
+    M, K = (int(v) for v in tuple(logZ_s.shape))
+    _check(lib().bpmf_proposal_bpmf(ctx, _ptr(logZ_s, np.float64), _ptr(n_s, np.int64), _ptr(q_s, np.float64), M,
+                                    K, _ptr(n_tot, np.int64), float(kT), _ptr(bpmf, np.float64), _stream(stream)),
+           "bpmf_proposal_bpmf", ctx)
+
+
+def bpmf_valid_counts(ctx, lig, recs, total_conf):
+    K = len(recs)
+    arr = (ctypes.c_void_p * K)(*[r.value if isinstance(r, ctypes.c_void_p) else r for r in recs])
+    out = np.empty((int(total_conf), K), dtype=np.int64)
+    _check(lib().bpmf_valid_counts(ctx, lig, ctypes.cast(arr, ctypes.c_void_p), K, _ptr(out, np.int64)),
+           "bpmf_valid_counts", ctx)
+    return out

@@ -75,6 +75,7 @@ struct bpmf_lig {
   long long total_conf = 0, total_atoms = 0, total_coord_atoms = 0;
   float *coords = nullptr;  // device [coord_atoms][3]
   float2 *gamma = nullptr;  // device [3][total_atoms] float pairs
+  float *q = nullptr, *eps = nullptr, *R = nullptr;  // device [total_atoms] (configuration features)
   std::vector<float> minmax;  // host [total_conf][6]
 };
 
@@ -450,6 +451,32 @@ void ligand_tables(const bpmf_lig *lg, int li, const bpmf_rec_t *recs, int K, do
 
 }  // namespace
 
+// ------------------------------------------- accessors for bpmf_proposal.cu
+int bpmf_internal_device(bpmf_ctx_t c) { return c ? c->device : 0; }
+void bpmf_internal_set_error(bpmf_ctx_t c, const std::string &m) {
+  if (c) c->err = m;
+}
+int bpmf_internal_ligand_arrays(bpmf_lig_t lg, const float **coords, const float **q, const float **eps,
+                                const float **R, std::vector<int> *conf_off, std::vector<int> *conf_nat,
+                                std::vector<int> *conf_lig, std::vector<int> *lig_atom_off) {
+  if (!lg) return BPMF_ERR_INVALID_ARG;
+  *coords = lg->coords;
+  *q = lg->q;
+  *eps = lg->eps;
+  *R = lg->R;
+  conf_off->clear();
+  conf_nat->clear();
+  conf_lig->clear();
+  lig_atom_off->assign(lg->atom_off.begin(), lg->atom_off.end());
+  for (int i = 0; i < lg->n_lig; ++i)
+    for (int j = 0; j < lg->n_conf[i]; ++j) {
+      conf_off->push_back(lg->coord_off[i] + j * lg->n_atoms[i]);
+      conf_nat->push_back(lg->n_atoms[i]);
+      conf_lig->push_back(i);
+    }
+  return BPMF_OK;
+}
+
 // ===================================================================== ABI
 extern "C" {
 
@@ -506,6 +533,26 @@ int bpmf_profile_entry(bpmf_ctx_t c, int i, char *name, int name_len, double *to
   }
   if (total_ms) *total_ms = c->prof_ms[i];
   if (launches) *launches = c->prof_n[i];
+  return BPMF_OK;
+}
+
+int bpmf_valid_counts(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, int64_t *n_valid) {
+  if (!c || !lg || !recs || K < 1 || !n_valid || lg->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "null argument");
+  try {
+    last_msg.clear();
+    check_recs(recs, K, c);
+    std::vector<ConfMeta> meta;
+    std::vector<PairInfo> info;
+    std::vector<long long> nv;
+    long long off = 0;
+    for (int li = 0; li < lg->n_lig; ++li) {
+      ligand_tables(lg, li, recs, K, recs[0]->h, meta, info, nv);
+      for (size_t i = 0; i < (size_t)lg->n_conf[li] * K; ++i) n_valid[off + i] = nv[i];
+      off += (long long)lg->n_conf[li] * K;
+    }
+  } catch (Fail f) {
+    return set_err(c, f.code, last_msg);
+  }
   return BPMF_OK;
 }
 
@@ -723,6 +770,12 @@ int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_
     }
     const size_t na = lg->total_atoms;
     CK(cudaMalloc(&lg->gamma, 3 * na * sizeof(float2)));
+    CK(cudaMalloc(&lg->q, na * sizeof(float)));
+    CK(cudaMalloc(&lg->eps, na * sizeof(float)));
+    CK(cudaMalloc(&lg->R, na * sizeof(float)));
+    CK(cudaMemcpyAsync(lg->q, q, na * sizeof(float), cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(lg->eps, eps, na * sizeof(float), cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(lg->R, R, na * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaMalloc(&lg->coords, std::max<size_t>(1, 3 * lg->total_coord_atoms) * sizeof(float)));
     {
       DevIn dq(q, na * sizeof(float), st), de(eps, na * sizeof(float), st), dr(R, na * sizeof(float), st);
@@ -775,6 +828,8 @@ void bpmf_ligand_free(bpmf_lig_t lg) {
     DeviceGuard g(lg->ctx->device);
     if (lg->coords) cudaFree(lg->coords);
     if (lg->gamma) cudaFree(lg->gamma);
+    for (float *p : {lg->q, lg->eps, lg->R})
+      if (p) cudaFree(p);
   }
   delete lg;
 }
