@@ -57,6 +57,15 @@ extern "C" {
  *                     values reach 1e4. */
 #define BPMF_MODE_FP32 0u
 #define BPMF_MODE_FF 1u
+/*   BPMF_MODE_SPLIT_BF16 -- the FP32 form with every radix-32 stage (padded
+ *                     edges divisible by 32) run as a dense tensor-core
+ *                     contraction: the 64 x 64 real DFT-32 matrix times the
+ *                     twiddled data, each split into bf16 high and low parts,
+ *                     three products (hi.hi + hi.lo + lo.hi) accumulated in
+ *                     FP32.  About 2^-16 relative error per stage: coarser than
+ *                     FP32, with the error against the oracle reported per
+ *                     result.  Other edges fall back to the FP32 stages. */
+#define BPMF_MODE_SPLIT_BF16 2u
 
 /* Largest supported ligand (atoms) and padded FFT edge. */
 #define BPMF_MAX_ATOMS 256
@@ -149,7 +158,7 @@ void bpmf_ligand_free(bpmf_lig_t lig);
  *            processed in groups of equal padded FFT edges; the ligand's
  *            forward transforms are shared within a group.
  *  kT        > 0 (kcal/mol).
- *  mode      BPMF_MODE_FP32 or BPMF_MODE_FF.
+ *  mode      BPMF_MODE_FP32, BPMF_MODE_FF or BPMF_MODE_SPLIT_BF16.
  *  logZ      [total_conf][K] float64, total_conf = sum n_conf, ligand-major.
  *  n_valid   [total_conf][K] int64 (may be NULL).
  *  bpmf      [n_lig][K] float64 (may be NULL).

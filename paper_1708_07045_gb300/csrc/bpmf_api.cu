@@ -35,6 +35,7 @@ struct bpmf_ctx {
   std::vector<long long> prof_n;
   std::string err;
   std::map<int, float4 *> tw;  // twiddle tables per transform length
+  uint4 *tca = nullptr;        // tensor-core radix-32 fragment table (split-bf16 mode)
   void *ws = nullptr;          // grow-only device workspace
   size_t ws_bytes = 0;
   size_t ws_budget = size_t(3) << 30;
@@ -137,6 +138,11 @@ int smooth_edge(int n) {
   return 0;
 }
 
+// Fragment tables of the tensor-core radix-32 stage: the real 64 x 64 DFT-32
+// matrix (rows 2r'+c', columns 2r+c), split into bf16 high and low parts and
+// laid out in mma.sync m16n8k16 A-fragment order, forward then inverse.
+const uint4 *tc_table(bpmf_ctx *c);
+
 FftPlan make_plan(int P) {
   FftPlan pl{};
   pl.n = P;
@@ -147,6 +153,17 @@ FftPlan make_plan(int P) {
   for (int r : {3, 5, 7})
     while (m % r == 0) pl.r[k++] = r, m /= r;
   pl.nst = k;
+  return pl;
+}
+
+// split-bf16 plan: the radix-32 factor as a final tensor-core stage when 32 | P
+FftPlan make_plan_split(bpmf_ctx *c, int P) {
+  if (P % 32) return make_plan(P);
+  FftPlan pl = make_plan(P / 32);
+  pl.n = P;
+  if (P == 32) pl.nst = 0;
+  pl.r[pl.nst++] = 32;
+  pl.tca = tc_table(c);
   return pl;
 }
 
@@ -166,6 +183,56 @@ const float4 *twiddles(bpmf_ctx *c, int P) {
   CK(cudaMalloc(&d, sizeof(float4) * P));
   CK(cudaMemcpy(d, h.data(), sizeof(float4) * P, cudaMemcpyHostToDevice));
   c->tw[P] = d;
+  return d;
+}
+
+static inline unsigned short bf16_bits(float v) {  // round to nearest even
+  unsigned u;
+  std::memcpy(&u, &v, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (unsigned short)(u >> 16);
+}
+static inline float bf16_val(unsigned short b) {
+  const unsigned u = (unsigned)b << 16;
+  float v;
+  std::memcpy(&v, &u, 4);
+  return v;
+}
+
+const uint4 *tc_table(bpmf_ctx *c) {
+  if (c->tca) return c->tca;
+  std::vector<uint4> h(2 * 2 * 4 * 4 * 32);
+  const long double two_pi = 6.283185307179586476925286766559L;
+  for (int dir = 0; dir < 2; ++dir) {
+    float A[64][64];
+    for (int rp = 0; rp < 32; ++rp)
+      for (int r = 0; r < 32; ++r) {
+        const long double a = two_pi * (long double)((rp * r) % 32) / 32.0L;
+        const float wr = (float)cosl(a), wi = (float)((dir ? 1 : -1) * sinl(a));
+        A[2 * rp][2 * r] = wr;
+        A[2 * rp][2 * r + 1] = -wi;
+        A[2 * rp + 1][2 * r] = wi;
+        A[2 * rp + 1][2 * r + 1] = wr;
+      }
+    for (int term = 0; term < 2; ++term)
+      for (int t = 0; t < 4; ++t)
+        for (int q = 0; q < 4; ++q)
+          for (int lane = 0; lane < 32; ++lane) {
+            const int gid = lane >> 2, tig = lane & 3;
+            auto part = [&](int m, int k) {
+              const unsigned short hb = bf16_bits(A[m][k]);
+              return term == 0 ? hb : bf16_bits(A[m][k] - bf16_val(hb));
+            };
+            auto pack = [&](int m, int k) { return (unsigned)part(m, k) | ((unsigned)part(m, k + 1) << 16); };
+            const int m = 16 * t + gid, k = 16 * q + 2 * tig;
+            h[(((dir * 2 + term) * 4 + t) * 4 + q) * 32 + lane] =
+                make_uint4(pack(m, k), pack(m + 8, k), pack(m, k + 8), pack(m + 8, k + 8));
+          }
+  }
+  uint4 *d = nullptr;
+  CK(cudaMalloc(&d, sizeof(uint4) * h.size()));
+  CK(cudaMemcpy(d, h.data(), sizeof(uint4) * h.size(), cudaMemcpyHostToDevice));
+  c->tca = d;
   return d;
 }
 
@@ -298,7 +365,8 @@ template <class T>
 void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, const ConfMeta *d_meta,
                const PairInfo *d_info, const float2 *const *d_rhi, const float2 *const *d_rlo, double h,
                float nscale_hi, float nscale_lo, float escale_hi, float escale_lo, float4 *d_part,
-               double *export_E, char *ws, cudaStream_t st, const bpmf_ctx::Tune &tn) {
+               double *export_E, char *ws, cudaStream_t st, const bpmf_ctx::Tune &tn, bool split = false) {
+  auto plan = [&](int P) { return split ? make_plan_split(c, P) : make_plan(P); };
   const size_t E = sizeof(cx<T>);
   char *p = ws;
   float2 *box = reinterpret_cast<float2 *>(p);
@@ -324,7 +392,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   za.in_stride = g.U[2];
   za.out = lz;
   za.out_stride = g.F2;
-  za.plan = make_plan(g.P[2]);
+  za.plan = plan(g.P[2]);
   za.tw = twiddles(c, g.P[2]);
   za.L = tn.zfwd_l;
   launch(c, sizeof(T) == 4 ? "k_zfwd<fp32>" : "k_zfwd<ff>", st, [&] { return launch_zfwd<T>(za, st); });
@@ -343,7 +411,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   ya.w0_div = 1;
   ya.axis = 1;
   ya.inverse = 0;
-  ya.plan = make_plan(g.P[1]);
+  ya.plan = plan(g.P[1]);
   ya.tw = twiddles(c, g.P[1]);
   ya.LW = pick_lw(ya.inner, tn.axis_lw);
   launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y fwd)" : "k_axis<ff>(y fwd)", st, [&] { return launch_axis<T>(ya, st); });
@@ -358,7 +426,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   xa.x2 = x2;
   xa.S0 = g.S[0];
   xa.info = d_info;
-  xa.plan = make_plan(g.P[0]);
+  xa.plan = plan(g.P[0]);
   xa.tw = twiddles(c, g.P[0]);
   launch(c, sizeof(T) == 4 ? "k_xfused<fp32>" : "k_xfused<ff>", st, [&] { return launch_xfused<T>(xa, batch, st); });
 
@@ -376,7 +444,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   yi.w0_div = g.S[0];
   yi.axis = 1;
   yi.inverse = 1;
-  yi.plan = make_plan(g.P[1]);
+  yi.plan = plan(g.P[1]);
   yi.tw = twiddles(c, g.P[1]);
   yi.LW = pick_lw(yi.inner, tn.axis_lw);
   launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y inv)" : "k_axis<ff>(y inv)", st, [&] { return launch_axis<T>(yi, st); });
@@ -395,7 +463,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   zi.escale_lo = escale_lo;
   zi.part = d_part;
   zi.export_E = export_E;
-  zi.plan = make_plan(g.P[2]);
+  zi.plan = plan(g.P[2]);
   zi.tw = twiddles(c, g.P[2]);
   launch(c, sizeof(T) == 4 ? "k_zinv<fp32>" : "k_zinv<ff>", st, [&] { return launch_zinv<T>(zi, batch, st); });
 }
@@ -594,6 +662,7 @@ void bpmf_destroy(bpmf_ctx_t c) {
   if (!c) return;
   DeviceGuard g(c->device);
   for (auto &kv : c->tw) cudaFree(kv.second);
+  if (c->tca) cudaFree(c->tca);
   if (c->ws) cudaFree(c->ws);
   for (auto &r : c->pending) {
     cudaEventDestroy(r.a);
@@ -892,8 +961,10 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   check_recs(recs, K, c);
   const double h = recs[0]->h;
   const bool use_ff = (mode == BPMF_MODE_FF);
+  const bool split = (mode == BPMF_MODE_SPLIT_BF16);
   const size_t E = use_ff ? sizeof(cx<ff>) : sizeof(cx<float>);
   const std::vector<RecGroup> groups = group_receptors(recs, K);
+  if (split) tc_table(c);
   const int lig_begin = only_lig >= 0 ? only_lig : 0;
   const int lig_end = only_lig >= 0 ? only_lig + 1 : lg->n_lig;
   const bool host_out = !export_E && ((logZ && !is_device_ptr(logZ)) || (n_valid && !is_device_ptr(n_valid)) ||
@@ -1109,7 +1180,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
                           esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn);
           else
             run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, nullptr, h, nsh, nsl,
-                             esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn);
+                             esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, split);
         }
         if (export_E) continue;
         MergeArgs ma{};
@@ -1178,7 +1249,8 @@ int bpmf_eval(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double
               int64_t *n_valid, double *bpmf_out, double *dG, void *stream) {
   if (!c || !lg || !recs || K < 1 || !(kT > 0.0) || (!logZ && lg && lg->total_conf > 0))
     return set_err(c, BPMF_ERR_INVALID_ARG, "null argument, K < 1 or kT <= 0");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF) return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16)
+    return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   if (lg->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "ligand batch from another context");
   DeviceGuard dg(c->device);
   try {
@@ -1195,7 +1267,8 @@ int bpmf_eval(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double
 
 int bpmf_autotune(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, unsigned mode, void *stream) {
   if (!c || !lg || !recs || K < 1 || lg->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or K < 1");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF) return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16)
+    return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   DeviceGuard dg(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   const long long JK = std::max<long long>(1, lg->total_conf) * K;
@@ -1272,7 +1345,8 @@ int bpmf_export_energies(bpmf_ctx_t c, bpmf_lig_t lg, bpmf_rec_t rec, int lig_in
   if (!c || !lg || !rec || !out || lig_index < 0 || lig_index >= lg->n_lig || conf_index < 0 ||
       conf_index >= lg->n_conf[lig_index])
     return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or index out of range");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF) return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16)
+    return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   DeviceGuard dg(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   double *d_out = nullptr;

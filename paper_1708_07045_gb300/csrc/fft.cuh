@@ -13,14 +13,18 @@
 // (i / Ns) Ns R + (i mod Ns) + r Ns.  Radices 8, 4, 2 are hand-written; 3, 5
 // and 7 use the R-point DFT matrix read from the same twiddle table.
 #pragma once
+#include <type_traits>
+
 #include "arith.cuh"
+#include "tc_dft.cuh"
 
 namespace bpmf {
 
 struct FftPlan {
   int n;       // transform length P
   int nst;     // number of stages
-  int r[12];   // radix of each stage, product = n
+  int r[12];   // radix of each stage, product = n; 32 = tensor-core stage
+  const uint4 *tca;  // fragment table of the tensor-core radix-32 stage (split-bf16), or null
 };
 
 template <class T, int R>
@@ -127,6 +131,9 @@ __device__ cx<T> *cta_fft(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, cons
   for (int s = 0; s < pl.nst; ++s) {
     const int R = pl.r[s];
     switch (R) {
+      case 32:
+        if constexpr (std::is_same<T, float>::value) tc_dft32_stage(src, dst, es, ls, nlines, pl.n, Ns, tw, inv, pl.tca);
+        break;
       case 8: fft_stage<T, 8, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
       case 4: fft_stage<T, 4, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
       case 2: fft_stage<T, 2, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;

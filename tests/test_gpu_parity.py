@@ -261,3 +261,51 @@ def test_protein_scale_full_size_parity(pkg, protein):
     dG_all = oracle.dG(B_all, KT, oracle.site_volume(out["n_valid"], protein.receptors[0].h))
     assert abs(out["dG"][0] - dG_all) <= 1e-9 * max(1.0, abs(dG_all))
     print("protein-scale BPMF", out["bpmf"][0], "dG", out["dG"][0])
+
+
+# -------------------------------------------------- split-bf16 tensor-core form
+def test_split_bf16_tensor_core_stage_errors_are_reported_and_bounded(pkg, small, small_ref):
+    """BPMF_MODE_SPLIT_BF16: the radix-32 stages run as three-term bf16
+    tensor-core contractions (~2^-16 relative per stage).  Its energy error
+    against the oracle must stay within 2^8 times the FP32 bound (bf16 pairs
+    carry 16 significant bits instead of 24); the error is printed."""
+    r, l = small.receptors[0], small.ligands[0]
+    gam = oracle.gamma(l.params.q, l.params.eps, l.params.R)
+    E_ref, _ = oracle.pose_energies(r.grids, r.h, r.site_lo, r.site_n, l.coords[0], gam)
+    with _session(pkg) as s:
+        rh = s.load_receptor(r)
+        lh, _, _ = s.load_ligands([l])
+        E_s = s.export_energies(lh, rh, 0, 0, r.site_n, pkg.BPMF_MODE_SPLIT_BF16)
+        E_f = s.export_energies(lh, rh, 0, 0, r.site_n, pkg.BPMF_MODE_FP32)
+        rc, out = s.eval(lh, [rh], KT, pkg.BPMF_MODE_SPLIT_BF16, n_lig=1, total_conf=64)
+    ok = np.isfinite(E_ref)
+    assert np.array_equal(np.isinf(E_s), ~ok)
+    bound = _fp32_bound(r.grids, gam, r.shape) * 2 ** 8
+    es = np.abs(E_s[ok] - E_ref[ok])
+    ef = np.abs(E_f[ok] - E_ref[ok])
+    dB = abs(out["bpmf"][0, 0] - small_ref["bpmf"][0])
+    print(f"split-bf16: max |dE| {es.max():.3g} (FP32 {ef.max():.3g}) kcal/mol, |dB| {dB:.3g}, bound {bound:.3g}")
+    assert es.max() <= bound
+    # the tensor-core stage really changes the arithmetic (it is not the FP32 path)
+    assert not np.array_equal(E_s, E_f)
+    assert np.array_equal(out["n_valid"], small_ref["n_valid"])
+
+
+def test_split_bf16_protein_scale_runs_with_mixed_stages(pkg, protein):
+    """96 = 3 x 32: a CUDA-core radix-3 stage followed by the tensor-core
+    radix-32 stage, on a sample of the full-size workload."""
+    lig = protein.ligands[0]
+    sub = synth.LigandInput(lig.params, lig.coords[:16])
+    ref = oracle.evaluate(protein.receptors, sub.coords, lig.params.q, lig.params.eps, lig.params.R, KT)
+    with _session(pkg) as s:
+        rhs = [s.load_receptor(r) for r in protein.receptors]
+        lh, _, _ = s.load_ligands([sub])
+        rc, out = s.eval(lh, rhs, KT, pkg.BPMF_MODE_SPLIT_BF16, n_lig=1, total_conf=16)
+    assert np.array_equal(out["n_valid"], ref["n_valid"])
+    ok = np.isfinite(ref["logZ"])
+    dz = np.abs(out["logZ"][ok] - ref["logZ"][ok]).max() * KT
+    g = protein.receptors[0].grids
+    bound = _fp32_bound(g, ref["gamma"], protein.receptors[0].shape) * 2 ** 8
+    print(f"split-bf16 protein scale: max kT|dlogZ| {dz:.3g} kcal/mol, |dB| "
+          f"{np.abs(out['bpmf'][0] - ref['bpmf']).max():.3g} (bound {bound:.3g})")
+    assert np.isfinite(dz) and dz <= bound
