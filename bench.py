@@ -242,6 +242,114 @@ def cufft_leg(torch, w, dev, chunk=48):
     return a.elapsed_time(b), out.cpu().numpy()
 
 
+def precision_sweep(torch, pkg, sess, w, dev, stream, n_sample=8, n_eval=64):
+    """Precision variant of the workload: LJr clip 1e3 / 1e4 / 1e5 (grids
+    regenerated with the same seeds), every form against the FP64 oracle on
+    the first n_sample configurations: max kT |d log Z|, max |dE| within 20 kT
+    of the minimum over two exported configurations, and the BPMF of the
+    sample."""
+    import oracle
+    lig = w.ligands[0]
+    out = {}
+    modes = {"ff": pkg.BPMF_MODE_FF, "fp32": pkg.BPMF_MODE_FP32, "split_bf16": pkg.BPMF_MODE_SPLIT_BF16}
+    for clip in (1e3, 1e4, 1e5):
+        wc = synth.protein_scale(n_conf=n_eval, n_rec=N_REC, seed=1001, clip=clip, n_atoms_lig=N_ATOMS)
+        wc.ligands = [synth.LigandInput(lig.params, lig.coords[:n_eval])]
+        ref = oracle.evaluate(wc.receptors, lig.coords[:n_sample], lig.params.q, lig.params.eps, lig.params.R, w.kT)
+        gam = ref["gamma"]
+        E_ref = [oracle.pose_energies(wc.receptors[0].grids, wc.receptors[0].h, wc.receptors[0].site_lo,
+                                      wc.receptors[0].site_n, lig.coords[j], gam)[0] for j in (0, 1)]
+        recs = [pkg.bpmf_receptor_load(sess.ctx, r.grids, r.h, r.origin, r.site_lo, r.site_n) for r in wc.receptors]
+        lh = pkg.bpmf_ligand_batch(sess.ctx, [N_ATOMS], [n_eval], np.ascontiguousarray(lig.coords[:n_eval].reshape(-1, 3)),
+                                   lig.params.q, lig.params.eps, lig.params.R)
+        row = {}
+        for name, mid in modes.items():
+            logZ = np.empty((n_eval, N_REC))
+            nv = np.empty((n_eval, N_REC), dtype=np.int64)
+            pkg.bpmf_eval(sess.ctx, lh, recs, w.kT, mid, logZ, nv, None, None)
+            ok = np.isfinite(ref["logZ"])
+            dz = float(np.abs(logZ[:n_sample][ok] - ref["logZ"][ok]).max() * w.kT)
+            logS = logZ[:n_sample] + np.log(np.maximum(nv[:n_sample], 1))
+            dB = float(np.abs(oracle.bpmf(logS, nv[:n_sample], w.kT) - ref["bpmf"]).max())
+            dE = 0.0
+            for j in (0, 1):
+                E = np.empty(tuple(wc.receptors[0].site_n))
+                pkg.bpmf_export_energies(sess.ctx, lh, recs[0], 0, j, mid, E)
+                Er = E_ref[j]
+                win = np.isfinite(Er) & (Er <= Er[np.isfinite(Er)].min() + 20 * w.kT)
+                dE = max(dE, float(np.abs(E[win] - Er[win]).max()))
+            row[name] = {"max_kT_dlogZ_kcal": dz, "max_dE_20kT_kcal": dE, "max_dB_sample_kcal": dB,
+                         "meets_tolerance": bool(dE <= 1e-3 and dB <= 1e-2)}
+        pkg.bpmf_ligand_free(lh)
+        for r in recs:
+            pkg.bpmf_receptor_free(r)
+        out["clip_%g" % clip] = row
+    return {"sample": f"first {n_sample} configurations x {N_REC} receptors (energies: 2 configurations, receptor 0)",
+            "results": out}
+
+
+def learned_proposal_leg(torch, pkg, sess, w, dev, stream, res_train, coords_train, params_train, budget_frac=0.1):
+    """Train the MLP proposal on the benchmark ligand's full enumeration, then
+    estimate the BPMFs of a held-out ligand from a 10 % budget; the full
+    enumeration of the held-out ligand is the judge and the time baseline."""
+    from paper_1708_07045_gb300 import proposal as PP
+    K, J = N_REC, N_CONF
+    recs = [pkg.bpmf_receptor_load(sess.ctx, r.grids, r.h, r.origin, r.site_lo, r.site_n) for r in w.receptors]
+    h = w.receptors[0].h
+    try:
+        lh_tr = pkg.bpmf_ligand_batch(sess.ctx, [N_ATOMS], [J], coords_train, *params_train)
+        X = PP.features(sess.ctx, lh_tr, J, h, dev)
+        pkg.bpmf_ligand_free(lh_tr)
+        t = PP.config_targets(res_train["logZ"], res_train["n_valid"])
+        ok = np.isfinite(t)
+        Xtr = X[torch.from_numpy(np.nonzero(ok)[0]).to(dev)].contiguous()
+        net = PP.LearnedProposal(sess.ctx, PP.fit_norm(Xtr.cpu().numpy(), t[ok]))
+        t0 = time.perf_counter()
+        losses = net.fit(Xtr, torch.from_numpy(t[ok].astype(np.float32)).to(dev), epochs=8, batch=256)
+        t_train = time.perf_counter() - t0
+        held = synth.LigandInput(synth.ligand_params(7001, N_ATOMS), synth.ligand_configs(7002, N_ATOMS, J))
+        coords = torch.from_numpy(held.coords).to(dev)
+        params = [torch.from_numpy(getattr(held.params, k)).to(dev) for k in ("q", "eps", "R")]
+        lh = pkg.bpmf_ligand_batch(sess.ctx, [N_ATOMS], [J], coords.reshape(-1, 3), *params)
+        # full enumeration: judge and time baseline
+        logZ = torch.empty((J, K), dtype=torch.float64, device=dev)
+        nv = torch.empty((J, K), dtype=torch.int64, device=dev)
+        B = torch.empty((1, K), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pkg.bpmf_eval(sess.ctx, lh, recs, w.kT, pkg.BPMF_MODE_FF, logZ, nv, B, None)
+        torch.cuda.synchronize()
+        t_full = time.perf_counter() - t0
+        B_full = B.cpu().numpy()[0]
+        n_tot = pkg.bpmf_valid_counts(sess.ctx, lh, recs, J).sum(axis=0)
+        M = int(budget_frac * J)
+        res = {}
+        for name, mix in (("trained", 0.8), ("uniform", 0.0)):
+            errs, times = [], []
+            for seed in range(6):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if name == "trained":
+                    pred = net.predict(PP.features(sess.ctx, lh, J, h, dev))
+                else:
+                    pred = torch.zeros(J, dtype=torch.float32, device=dev)
+                Bp, _, _ = PP.proposal_bpmf(sess.ctx, recs, w.kT, coords, params, pred, M, mix=mix, seed=seed,
+                                            n_tot=n_tot)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+                errs.append(np.abs(Bp - B_full).max())
+            res[name] = {"median_abs_dB_kcal": float(np.median(errs)), "max_abs_dB_kcal": float(np.max(errs)),
+                         "ms": float(np.median(times) * 1e3), "speedup_vs_full": float(t_full / np.median(times))}
+        pkg.bpmf_ligand_free(lh)
+        net.free()
+        return {"budget": budget_frac, "full_enumeration_ms": t_full * 1e3, "train_s": t_train,
+                "final_train_loss": float(losses[-1]), "held_out": "ligand seeds 7001/7002, 2000 configurations",
+                **res}
+    finally:
+        for r in recs:
+            pkg.bpmf_receptor_free(r)
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -351,6 +459,18 @@ def run_ours(args):
     h2d = sum(g.numel() * 4 for g in host_grids) + host_coords.numel() * 4 + sum(p.numel() * 4 for p in host_params)
     d2h = sum(v.nbytes for v in host_outs.values())
 
+    # split-bf16 tensor-core form on the same workload
+    t_split, _, prof_split = timed(pkg.BPMF_MODE_SPLIT_BF16, max(1, args.steps // 2), 1, prof=True)
+    res_split = {k: v.cpu().numpy() for k, v in outs.items()}
+
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = precision_sweep(torch, pkg, sess, w, dev, stream)
+
+    proposal = None
+    if rank == 0 and not args.no_proposal:
+        proposal = learned_proposal_leg(torch, pkg, sess, w, dev, stream, res_chosen, coords, params)
+
     cufft = None
     if rank == 0 and not args.no_cufft:
         cufft_leg(torch, w, dev)  # warm-up (plans, allocator)
@@ -368,7 +488,7 @@ def run_ours(args):
             ref, dt = oracle_sample(w, args.ref_sample)
             okz = np.isfinite(ref["logZ"])
             ns = args.ref_sample
-            cmp = [(chosen, res_chosen), (other, res_other)]
+            cmp = [(chosen, res_chosen), (other, res_other), ("split_bf16", res_split)]
             if cufft is not None:
                 cmp.append(("cufft_fp32", {"logZ": logZ_cu, "n_valid": res_chosen["n_valid"]}))
             for name, res in cmp:
@@ -419,6 +539,11 @@ def run_ours(args):
                               "ms_per_step": t_other if other == "fp32" else None},
                 "ff_path": {"ms_per_step": t_other} if other == "ff" else {"ms_per_step": t_ms},
                 "kernels_ms_per_step_other_form": {k: v[0] / max(1, args.steps // 2) for k, v in prof_other.items()},
+                "split_bf16_path": {"value": n_poses * world / (t_split / 1e3), "ms_per_step": t_split,
+                                    "kernels_ms_per_step": {k: v[0] / max(1, args.steps // 2)
+                                                            for k, v in prof_split.items()}},
+                "precision_sweep": sweep,
+                "learned_proposal": proposal,
                 "cufft_fp32_path": cufft,
                 "accuracy_vs_oracle": acc,
                 "e2e": {"value": n_poses * world / e2e_t, "unit": "pose energies/s", "h2d_bytes_per_step": int(h2d),
@@ -444,6 +569,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the LJr clip / precision sweep")
+    ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal leg")
     ap.add_argument("--n-conf", type=int, default=N_CONF,
                     help="configurations per step (default: the full workload; smaller values are for profiling)")
     args = ap.parse_args()

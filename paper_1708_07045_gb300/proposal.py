@@ -45,7 +45,7 @@ def config_targets(logZ: np.ndarray, n_valid: np.ndarray) -> np.ndarray:
     with np.errstate(divide="ignore"):
         ls = np.where(n_valid > 0, logZ + np.log(np.maximum(n_valid, 1)), -np.inf)
     m = ls.max(axis=1, keepdims=True)
-    with np.errstate(invalid="ignore"):
+    with np.errstate(invalid="ignore", divide="ignore"):
         s = np.where(np.isfinite(m[:, 0]), m[:, 0] + np.log(np.exp(ls - np.where(np.isfinite(m), m, 0)).sum(1)),
                      -np.inf)
     return s
