@@ -251,12 +251,6 @@ void *workspace(bpmf_ctx *c, size_t bytes, cudaStream_t st) {
 
 inline size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
-// lines per CTA for a strided pass over `inner` columns: at most `cap`, with
-// the columns split into equal tiles
-int pick_lw(long long inner, int cap = 16) {
-  const long long nt = (inner + cap - 1) / cap;
-  return (int)((inner + nt - 1) / nt);
-}
 
 cudaEvent_t pool_event(bpmf_ctx *c) {
   if (!c->event_pool.empty()) {
@@ -413,7 +407,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   ya.inverse = 0;
   ya.plan = plan(g.P[1]);
   ya.tw = twiddles(c, g.P[1]);
-  ya.LW = pick_lw(ya.inner, tn.axis_lw);
+  ya.LW = tn.axis_lw;
   launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y fwd)" : "k_axis<ff>(y fwd)", st, [&] { return launch_axis<T>(ya, st); });
 
   XfusedArgs xa{};
@@ -446,7 +440,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   yi.inverse = 1;
   yi.plan = plan(g.P[1]);
   yi.tw = twiddles(c, g.P[1]);
-  yi.LW = pick_lw(yi.inner, tn.axis_lw);
+  yi.LW = tn.axis_lw;
   launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y inv)" : "k_axis<ff>(y inv)", st, [&] { return launch_axis<T>(yi, st); });
 
   ZinvArgs zi{};
@@ -745,7 +739,7 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
     ya.axis = 1;
     ya.plan = make_plan(P[1]);
     ya.tw = twiddles(c, P[1]);
-    ya.LW = pick_lw(ya.inner);
+    ya.LW = 16;
     launch(c, "k_axis<ff>(receptor y)", st, [&] { return launch_axis<ff>(ya, st); });
     // x
     AxisArgs xa{};

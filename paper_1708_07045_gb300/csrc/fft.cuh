@@ -115,7 +115,7 @@ __device__ __forceinline__ void fft_stage(const cx<T> *src, cx<T> *dst, int es, 
     dft_small<T, R>(v, inv, tw, P);
     const int o = (i / Ns) * Ns * R + j;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[(o + r * Ns) * es + l * ls] = c_norm(v[r]);
+    for (int r = 0; r < R; ++r) dst[(o + r * Ns) * es + l * ls] = v[r];  // lazy pairs; stores renormalise
   }
 }
 

@@ -298,25 +298,35 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_axis(
   float4 *s_tw = smem;
   cx<T> *b0 = reinterpret_cast<cx<T> *>(smem + P);
   cx<T> *b1 = b0 + P * LW;
+  __shared__ long long s_in[64], s_out[64];  // per tile column: base offsets of input / output
+  __shared__ int s_w0[64];
   load_tw(s_tw, a.tw, P);
-  const long long ntile = (a.inner + LW - 1) / LW;
-  const long long o = blockIdx.x / ntile;
-  const long long i0 = (blockIdx.x % ntile) * LW;
+  // columns are the flattened (outer, inner) pairs, so a tile never wastes
+  // lanes on a short inner edge
+  const long long ncols = a.n_outer * a.inner;
+  const long long c0 = (long long)blockIdx.x * LW;
+  if (threadIdx.x < LW) {
+    const long long c = c0 + threadIdx.x;
+    const long long o = c < ncols ? c / a.inner : 0, i = c < ncols ? c % a.inner : 0;
+    s_in[threadIdx.x] = c < ncols ? o * a.in_os + i : -1;
+    s_out[threadIdx.x] = c < ncols ? o * a.out_os + i : -1;
+    s_w0[threadIdx.x] = a.info ? a.info[o / a.w0_div].w0[a.axis] : 0;
+  }
+  __syncthreads();
   const int n_in = a.n_in < P ? a.n_in : P;
   for (int idx = threadIdx.x; idx < n_in * LW; idx += blockDim.x) {
     const int n = idx / LW, l = idx % LW;
-    const long long i = i0 + l;
-    cp_cx<T>(&b0[idx], a.in, o * a.in_os + n * a.inner + i, i < a.inner);
+    const long long base = s_in[l];
+    cp_cx<T>(&b0[idx], a.in, base + n * a.inner, base >= 0);
   }
   for (int idx = n_in * LW + threadIdx.x; idx < P * LW; idx += blockDim.x) b0[idx] = c_zero<T>();
   cp_async_wait_all();
   __syncthreads();
   cx<T> *res = cta_fft<T>(b0, b1, LW, 1, LW, a.plan, s_tw, a.inverse != 0);
-  const int w0 = a.info ? a.info[o / a.w0_div].w0[a.axis] : 0;
   for (int idx = threadIdx.x; idx < a.n_out * LW; idx += blockDim.x) {
     const int s = idx / LW, l = idx % LW;
-    const long long i = i0 + l;
-    if (i < a.inner) st_cx<T>(a.out, o * a.out_os + s * a.inner + i, res[imod(w0 + s, P) * LW + l]);
+    const long long base = s_out[l];
+    if (base >= 0) st_cx<T>(a.out, base + s * a.inner, res[imod(s_w0[l] + s, P) * LW + l]);
   }
 }
 
@@ -327,7 +337,8 @@ cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
   const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * a.LW;
   cudaError_t e = cudaFuncSetAttribute(k_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long blocks = a.n_outer * ((a.inner + a.LW - 1) / a.LW);
+  if (a.LW < 1 || a.LW > 64) return cudaErrorInvalidValue;
+  const long long blocks = (a.n_outer * a.inner + a.LW - 1) / a.LW;
   k_axis<T><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -411,7 +422,7 @@ __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi 
 __device__ __forceinline__ bool ff_gt(float a, float b) { return a > b; }
 
 template <class T>
-__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zinv(ZinvArgs a) {
+__global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, F = a.F2, ls = P + 1;
   const int L = (a.S1 + 1) / 2;
@@ -522,7 +533,7 @@ cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st) {
   const size_t smem = sizeof(float4) * P + sizeof(cx<T>) * ((size_t)L * (P + 1) + b1n) + sizeof(T) * (size_t)a.S1 * a.S2;
   cudaError_t e = cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_zinv<T><<<(unsigned)((long long)batch * a.K * a.S0), KCfg<T>::threads, smem, st>>>(a);
+  k_zinv<T><<<(unsigned)((long long)batch * a.K * a.S0), 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
