@@ -150,4 +150,108 @@ __device__ cx<T> *cta_fft(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, cons
   return src;
 }
 
+// ---------------------------------------------------------------------------
+// Compile-time plans for common transform lengths: radices, stage strides and
+// the line count are constants, so the per-butterfly index arithmetic folds
+// away.  Same Stockham stages (and the same rounding) as the generic engine.
+template <int P>
+struct CtPlan {
+  static constexpr int nst = 0;
+  __host__ __device__ static constexpr int r(int) { return 1; }
+};
+template <>
+struct CtPlan<32> {
+  static constexpr int nst = 2;
+  __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : 4; }
+};
+template <>
+struct CtPlan<64> {
+  static constexpr int nst = 2;
+  __host__ __device__ static constexpr int r(int) { return 8; }
+};
+template <>
+struct CtPlan<96> {
+  static constexpr int nst = 3;
+  __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : (s == 1 ? 4 : 3); }
+};
+template <>
+struct CtPlan<128> {
+  static constexpr int nst = 3;
+  __host__ __device__ static constexpr int r(int s) { return s < 2 ? 8 : 2; }
+};
+template <int P>
+__host__ __device__ constexpr bool ct_supported() {
+  return CtPlan<P>::nst > 0;
+}
+template <int P, int S>
+__host__ __device__ constexpr int ct_ns() {  // product of the radices before stage S
+  int n = 1;
+  for (int i = 0; i < S; ++i) n *= CtPlan<P>::r(i);
+  return n;
+}
+
+template <class T, int P, int S, int NL, int ES, int LS, int NT>
+__device__ __forceinline__ void fft_stage_ct(const cx<T> *src, cx<T> *dst, const float4 *tw, bool inv) {
+  constexpr int R = CtPlan<P>::r(S);
+  constexpr int Ns = ct_ns<P, S>();
+  constexpr int nb = P / R;
+  constexpr int items = nb * NL;
+  constexpr int tstride = P / (Ns * R);
+#pragma unroll 1
+  for (int it = threadIdx.x; it < items; it += NT) {
+    const int l = it % NL, i = it / NL;
+    const int j = i % Ns;
+    cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(i + r * nb) * ES + l * LS];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], tw_load<T>(tw[r * j * tstride], inv));
+    }
+    dft_small<T, R>(v, inv, tw, P);
+    const int o = (i / Ns) * Ns * R + j;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(o + r * Ns) * ES + l * LS] = v[r];
+  }
+}
+
+template <class T, int P, int S, int NL, int ES, int LS, int NT>
+__device__ __forceinline__ cx<T> *cta_fft_ct_from(cx<T> *src, cx<T> *dst, const float4 *tw, bool inv) {
+  if constexpr (S == CtPlan<P>::nst) {
+    return src;
+  } else {
+    fft_stage_ct<T, P, S, NL, ES, LS, NT>(src, dst, tw, inv);
+    __syncthreads();
+    return cta_fft_ct_from<T, P, S + 1, NL, ES, LS, NT>(dst, src, tw, inv);
+  }
+}
+
+// Compile-time counterpart of cta_fft for P in {32, 64, 96, 128}; NT must
+// equal blockDim.x.
+template <class T, int P, int NL, int ES, int LS, int NT>
+__device__ __forceinline__ cx<T> *cta_fft_ct(cx<T> *b0, cx<T> *b1, const float4 *tw, bool inv) {
+  return cta_fft_ct_from<T, P, 0, NL, ES, LS, NT>(b0, b1, tw, inv);
+}
+
+// Transform with the compile-time engine when the plan and line count match a
+// specialisation (lines contiguous: CONTIG, element stride 1, line stride
+// P + 1; otherwise element stride NL, line stride 1), else the generic engine.
+template <class T, int NL, int NT, bool CONTIG>
+__device__ __forceinline__ cx<T> *cta_fft_auto(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, const FftPlan &pl,
+                                               const float4 *tw, bool inv) {
+  if (nlines == NL && pl.tca == nullptr) {
+    switch (pl.n) {
+      case 96:
+        return CONTIG ? cta_fft_ct<T, 96, NL, 1, 97, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 96, NL, NL, 1, NT>(b0, b1, tw, inv);
+      case 64:
+        return CONTIG ? cta_fft_ct<T, 64, NL, 1, 65, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 64, NL, NL, 1, NT>(b0, b1, tw, inv);
+      case 32:
+        return CONTIG ? cta_fft_ct<T, 32, NL, 1, 33, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 32, NL, NL, 1, NT>(b0, b1, tw, inv);
+      default:
+        break;
+    }
+  }
+  return cta_fft<T>(b0, b1, es, ls, nlines, pl, tw, inv);
+}
+
 }  // namespace bpmf

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zfwd(
   }
   cp_async_wait_all();
   __syncthreads();
-  cx<T> *res = cta_fft<T>(b0, b1, 1, ls, L, a.plan, s_tw, false);
+  cx<T> *res = cta_fft_auto<T, 16, KCfg<T>::threads, true>(b0, b1, 1, ls, L, a.plan, s_tw, false);
   const T half = s_from<T>(0.5f);
   for (int idx = threadIdx.x; idx < L * F; idx += blockDim.x) {
     const int l = idx / F, k = idx % F;
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_axis(
   for (int idx = n_in * LW + threadIdx.x; idx < P * LW; idx += blockDim.x) b0[idx] = c_zero<T>();
   cp_async_wait_all();
   __syncthreads();
-  cx<T> *res = cta_fft<T>(b0, b1, LW, 1, LW, a.plan, s_tw, a.inverse != 0);
+  cx<T> *res = cta_fft_auto<T, 16, KCfg<T>::threads, false>(b0, b1, LW, 1, LW, a.plan, s_tw, a.inverse != 0);
   for (int idx = threadIdx.x; idx < a.n_out * LW; idx += blockDim.x) {
     const int s = idx / LW, l = idx % LW;
     const long long base = s_out[l];
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfuse
   for (int idx = U0 * L3 + threadIdx.x; idx < P * L3; idx += blockDim.x) bA[idx] = c_zero<T>();
   cp_async_wait_all();
   __syncthreads();
-  cx<T> *Lsp = cta_fft<T, L3>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
+  cx<T> *Lsp = cta_fft_auto<T, L3, KCfg<T>::threads, false>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
   cx<T> *W1 = (Lsp == bA) ? bB : bA;
   cx<T> *W2 = W1 + P * LW;
   for (int k = 0; k < a.K; ++k) {
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfuse
       W1[idx] = c_norm(acc);
     }
     __syncthreads();
-    cx<T> *res = cta_fft<T, LW>(W1, W2, LW, 1, LW, a.plan, s_tw, true);
+    cx<T> *res = cta_fft_auto<T, LW, KCfg<T>::threads, false>(W1, W2, LW, 1, LW, a.plan, s_tw, true);
     const int w0 = a.info[j * a.K + k].w0[0];
     for (int idx = threadIdx.x; idx < a.S0 * LW; idx += blockDim.x) {
       const int s = idx / LW, l = idx % LW;
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
     b0[l * ls + n] = c_norm(cx<T>{s_sub(A.re, B.im), s_add(A.im, B.re)});
   }
   __syncthreads();
-  cx<T> *res = cta_fft<T>(b0, b1, 1, ls, L, a.plan, s_tw, true);
+  cx<T> *res = cta_fft_auto<T, 20, 256, true>(b0, b1, 1, ls, L, a.plan, s_tw, true);
   const T nscale = s_mk<T>(a.nscale_hi, a.nscale_lo);
   const T escale = s_mk<T>(a.escale_hi, a.escale_lo);
   const int nS = a.S1 * a.S2;
