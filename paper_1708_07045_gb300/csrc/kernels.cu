@@ -190,38 +190,47 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
   }
   __syncthreads();
   const int plane = a.U1 * a.U2;
+  // the plane is accumulated in chunks of whole y rows that fit the shared buffer
+  const int rows = a.chunk_rows;
   const ff one{1.f, 0.f};
   for (int t = 0; t < 3; ++t) {
-    for (int i = threadIdx.x; i < plane; i += blockDim.x) s_plane[i] = 0ull;
-    __syncthreads();
     const int e = s_e[t];
-    for (int it = threadIdx.x; it < n * 8; it += blockDim.x) {
-      const int i = it >> 3, dx = (it >> 2) & 1, dy = (it >> 1) & 1, dz = it & 1;
-      if (s_c[i][0] + dx != ix) continue;
-      const ff wx = dx ? s_f[i][0] : s_sub(one, s_f[i][0]);
-      const ff wy = dy ? s_f[i][1] : s_sub(one, s_f[i][1]);
-      const ff wz = dz ? s_f[i][2] : s_sub(one, s_f[i][2]);
-      const float2 g2 = a.gamma[(long long)t * a.gamma_stride + m.gamma_off + i];
-      const ff v = s_norm(s_mul(s_mul(s_mul(wx, wy), wz), ff{g2.x, g2.y}));
-      const long long iv = __float2ll_rn(ldexpf(v.hi, e)) + __float2ll_rn(ldexpf(v.lo, e));
-      const int y = s_c[i][1] + dy, z = s_c[i][2] + dz;
-      if (y < a.U1 && z < a.U2) atomicAdd(&s_plane[y * a.U2 + z], (unsigned long long)iv);
-    }
-    __syncthreads();
     float2 *dst = a.box + (((long long)j * 3 + t) * a.U0 + ix) * plane;
-    for (int i = threadIdx.x; i < plane; i += blockDim.x) {
-      const long long v = (long long)s_plane[i];
-      const float hi = __ll2float_rn(v);
-      const float lo = __ll2float_rn(v - __float2ll_rn(hi));  // exact remainder, then rounded
-      dst[i] = make_float2(ldexpf(hi, -e), ldexpf(lo, -e));
+    for (int y0 = 0; y0 < a.U1; y0 += rows) {
+      const int ny = min(rows, a.U1 - y0), cells = ny * a.U2;
+      for (int i = threadIdx.x; i < cells; i += blockDim.x) s_plane[i] = 0ull;
+      __syncthreads();
+      for (int it = threadIdx.x; it < n * 8; it += blockDim.x) {
+        const int i = it >> 3, dx = (it >> 2) & 1, dy = (it >> 1) & 1, dz = it & 1;
+        if (s_c[i][0] + dx != ix) continue;
+        const int y = s_c[i][1] + dy - y0, z = s_c[i][2] + dz;
+        if (y < 0 || y >= ny || z >= a.U2) continue;
+        const ff wx = dx ? s_f[i][0] : s_sub(one, s_f[i][0]);
+        const ff wy = dy ? s_f[i][1] : s_sub(one, s_f[i][1]);
+        const ff wz = dz ? s_f[i][2] : s_sub(one, s_f[i][2]);
+        const float2 g2 = a.gamma[(long long)t * a.gamma_stride + m.gamma_off + i];
+        const ff v = s_norm(s_mul(s_mul(s_mul(wx, wy), wz), ff{g2.x, g2.y}));
+        const long long iv = __float2ll_rn(ldexpf(v.hi, e)) + __float2ll_rn(ldexpf(v.lo, e));
+        atomicAdd(&s_plane[y * a.U2 + z], (unsigned long long)iv);
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+        const long long v = (long long)s_plane[i];
+        const float hi = __ll2float_rn(v);
+        const float lo = __ll2float_rn(v - __float2ll_rn(hi));  // exact remainder, then rounded
+        dst[(long long)y0 * a.U2 + i] = make_float2(ldexpf(hi, -e), ldexpf(lo, -e));
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
-cudaError_t launch_spread(const SpreadArgs &a, int batch, cudaStream_t st) {
+cudaError_t launch_spread(const SpreadArgs &a_in, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  const size_t smem = sizeof(unsigned long long) * (size_t)a.U1 * a.U2;
+  SpreadArgs a = a_in;
+  // at most 96 KB of 64-bit accumulators per CTA, in whole y rows
+  a.chunk_rows = std::max(1, std::min(a.U1, (int)((96 * 1024) / (sizeof(unsigned long long) * std::max(a.U2, 1)))));
+  const size_t smem = sizeof(unsigned long long) * (size_t)a.chunk_rows * a.U2;
   // static + dynamic shared memory may pass the 48 KB default: always opt in
   cudaError_t e = cudaFuncSetAttribute(k_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -34,6 +34,7 @@ struct SpreadArgs {
   float h_hi, h_lo;        // grid spacing as a float pair
   int U0, U1, U2;          // ligand-box array dims (max over the batch)
   float2 *box;             // [batch][3][U0][U1][U2] float pairs
+  int chunk_rows;          // y rows accumulated per shared-memory pass (set by launch_spread)
 };
 
 struct ZfwdArgs {          // real rows -> half spectra along the contiguous axis
