@@ -33,6 +33,18 @@ FP32_LANES_PER_SM, N_SM = 128, 152
 # FP32 instructions per float-pair flop for the add/mul mix of the radix
 # stages (add: TwoSum 6 + 2 + FastTwoSum 3 = 11; mul: 1 + 3 FMA + 3 = 7; ~70 % adds)
 FF_INSTR_PER_FLOP = 9.8
+# DRAM bytes (read + write) per configuration of the fused x pass, from the ncu
+# capture summarised in profiles/xfused_ff_traffic.md; valid only for the kernel
+# sources it was taken with
+XFUSED_TRAFFIC = {"bytes_per_conf": 23.3e6, "src_sha": "01d5667b8a6266cb"}
+
+
+def kernel_src_sha():
+    import hashlib
+    d = os.path.join(ROOT, "paper_1708_07045_gb300", "csrc")
+    src = b"".join(open(os.path.join(d, f), "rb").read()
+                   for f in ("kernels.cu", "fft.cuh", "arith.cuh", "kernels.cuh", "tc_dft.cuh"))
+    return hashlib.sha256(src).hexdigest()[:16]
 
 
 def dist_env():
@@ -514,8 +526,13 @@ def run_ours(args):
                 if chosen == "ff":
                     peak = N_SM * FP32_LANES_PER_SM * sm_hz / FF_INSTR_PER_FLOP / 1e12
                     ach = flops / (ms_tot / 1e3) / 1e12
+                    traffic = None
+                    if name == "k_xfused<ff>" and kernel_src_sha() == XFUSED_TRAFFIC["src_sha"]:
+                        traffic = XFUSED_TRAFFIC["bytes_per_conf"] * N_CONF * args.steps / nl
                     roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                            "frac": ach / peak, "traffic": None,
+                            "frac": ach / peak, "traffic": traffic,
+                            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (scaled "
+                                            "from a 45-configuration launch by configurations per launch)",
                             "peak_note": "derived: 152 SM x 128 FP32 lanes x median SM clock / 9.8 FP32 "
                                          "instructions per float-pair flop",
                             "launches": nl, "ms_per_launch": ms_tot / nl}
