@@ -47,6 +47,19 @@ def kernel_src_sha():
     return hashlib.sha256(src).hexdigest()[:16]
 
 
+def aggregate(t_ms_local, poses_local, dist=None, device=None):
+    """Whole-job throughput under weak scaling: the slowest rank's time (max
+    over ranks) and the poses of all ranks.  Returns (t_ms, poses_total)."""
+    if dist is None:
+        return t_ms_local, poses_local
+    import torch
+    t = torch.tensor([float(t_ms_local)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(poses_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -430,11 +443,7 @@ def run_ours(args):
         prof_out = pkg.bpmf_profile(sess.ctx) if prof else None
         if prof:
             pkg.bpmf_profile_enable(sess.ctx, False)
-        t = float(np.mean(ts))
-        if dist is not None:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t, _ = aggregate(float(np.mean(ts)), 0.0, dist, dev)
         return t, ts, prof_out
 
     modes = {"ff": pkg.BPMF_MODE_FF, "fp32": pkg.BPMF_MODE_FP32}
@@ -449,7 +458,8 @@ def run_ours(args):
     res_other = {k: v.cpu().numpy() for k, v in outs.items()}
 
     n_poses = int(res_chosen["n_valid"].sum())
-    value = n_poses * world / (t_ms / 1e3)
+    _, poses_all = aggregate(t_ms, n_poses, dist, dev)
+    value = poses_all / (t_ms / 1e3)
     bpmfs = K * world / (t_ms / 1e3)
 
     # end to end: host (pinned) inputs and host outputs through the same C ABI
