@@ -141,6 +141,21 @@ def oracle_sample(w, n_sample):
     return ref, dt
 
 
+def sized_sample(w, n_req, target_s=12.0):
+    """The oracle on a bounded sample of the workload: ``n_req``
+    configurations if given, else the first 24, scaled up to about
+    ``target_s`` seconds of CPU work.  Returns (result, seconds, n)."""
+    if n_req > 0:
+        ref, dt = oracle_sample(w, n_req)
+        return ref, dt, n_req
+    n = 24
+    ref, dt = oracle_sample(w, n)
+    if dt < 0.5 * target_s:
+        n = int(min(N_CONF, max(n, n * target_s / max(dt, 1e-3))))
+        ref, dt = oracle_sample(w, n)
+    return ref, dt, n
+
+
 def omp_cores():
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v else os.cpu_count()
@@ -152,6 +167,8 @@ def run_reference(args):
         return 0
     w = synth.protein_scale(n_conf=N_CONF, n_rec=N_REC, seed=1001, n_atoms_lig=N_ATOMS)
     n_sample = args.ref_sample
+    if n_sample <= 0:  # about 10 s of CPU work per step
+        _, _, n_sample = sized_sample(w, 0, target_s=10.0)
     for _ in range(args.warmup):
         oracle_sample(w, max(1, n_sample // 4))
     times, poses = [], 0
@@ -507,9 +524,8 @@ def run_ours(args):
         cpu = None
         acc = {}
         if not args.no_cpu_baseline:
-            ref, dt = oracle_sample(w, args.ref_sample)
+            ref, dt, ns = sized_sample(w, args.ref_sample)
             okz = np.isfinite(ref["logZ"])
-            ns = args.ref_sample
             cmp = [(chosen, res_chosen), (other, res_other), ("split_bf16", res_split)]
             if cufft is not None:
                 cmp.append(("cufft_fp32", {"logZ": logZ_cu, "n_valid": res_chosen["n_valid"]}))
@@ -593,7 +609,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="ff", choices=["ff", "fp32"])
-    ap.add_argument("--ref-sample", type=int, default=24)
+    ap.add_argument("--ref-sample", type=int, default=0,
+                    help="oracle configurations per CPU sample (0: sized to about 10 s of CPU work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the LJr clip / precision sweep")

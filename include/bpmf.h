@@ -170,6 +170,26 @@ int bpmf_eval(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, int K, dou
               int64_t *n_valid, double *bpmf, double *dG, void *stream);
 
 /*
+ * bpmf_eval_dominant -- bpmf_eval plus the dominant-state quantities
+ * (Section "Dominant state approximation": the minimum interaction energy used
+ * in place of the exponential average, per receptor snapshot, then combined
+ * over snapshots by the minimum or by an exponential average).  They come out
+ * of the same pass: the minimum is the maximum -E/kT that the inverse pass
+ * already keeps for its shifted log-sum-exp.
+ *   psi_min  [total_conf][K] float64 (may be null): min over the valid
+ *            translations of E (kcal/mol) for each (configuration, receptor);
+ *            +inf where n_jk = 0.
+ *   psi_dom  [n_lig][K + 2] float64 (may be null): per ligand, entries 0..K-1
+ *            are min_j psi_min[j][k]; entry K the minimum over receptors;
+ *            entry K + 1 is -kT ln( (1/K) sum_k exp(-psi_dom[k] / kT) ).
+ * At least one of psi_min, psi_dom must be non-null; host or device memory.
+ * The other arguments, results and errors are those of bpmf_eval.
+ */
+int bpmf_eval_dominant(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
+                       double *logZ, int64_t *n_valid, double *bpmf, double *dG, double *psi_min, double *psi_dom,
+                       void *stream);
+
+/*
  * bpmf_export_energies -- debug export of one configuration's interaction
  * energies E(m) over receptor `rec`'s site window, computed by the same
  * kernels as bpmf_eval.  out: [S0][S1][S2] float64 (S = the receptor's
@@ -286,6 +306,31 @@ int bpmf_proposal_sample(bpmf_ctx_t ctx, const float *pred, int J, double mix, c
  * FP64 arithmetic.  Errors: INVALID_ARG, CUDA. */
 int bpmf_proposal_bpmf(bpmf_ctx_t ctx, const double *logZ_s, const int64_t *n_s, const double *q_s, int M, int K,
                        const int64_t *n_tot, double kT, double *bpmf, void *stream);
+
+/*
+ * bpmf_sir_poses -- sampling importance resampling of M poses of ligand
+ * `lig_index` against receptor `rec`, with weight exp(-E/kT) over all its
+ * (configuration, translation) poses (Section "Implicit solvent": poses drawn
+ * from the bound state by sampling importance resampling before the
+ * single-step perturbation).  Exact two-stage draw in FP64:
+ *   conf[s] = first j with sum_{i<=j} S_i > u1[s] sum_i S_i, where
+ *             S_j = n_valid[j][k] exp(logZ[j][k]) (inverse CDF over configurations);
+ *   pose[s] = first window index t with sum_{i<=t} exp(-E_i/kT) >
+ *             u2[s] sum_i exp(-E_i/kT), E = the energies of configuration
+ *             conf[s] as bpmf_export_energies returns them (same mode).
+ * The window index t = (s0 S1 + s1) S2 + s2 is translation
+ * m_d = site_lo_d + s_d - floor(u_d/2) (u = the configuration's ligand box).
+ *  logZ, n_valid  [J][K] float64 / int64 for this ligand's J configurations,
+ *                 as bpmf_eval returns them (column k = this receptor);
+ *  u1, u2         [M] float64 uniforms in [0, 1);  conf, pose [M] int32 out
+ *                 (-1 where no pose has finite weight).
+ * All arrays DEVICE memory.  Runs one energy export per distinct drawn
+ * configuration and synchronises `stream`.
+ * Errors: INVALID_ARG, SIZE_UNSUPPORTED, OOM, CUDA.
+ */
+int bpmf_sir_poses(bpmf_ctx_t ctx, bpmf_lig_t lig, int lig_index, bpmf_rec_t rec, int K, int k, double kT,
+                   unsigned mode, const double *logZ, const int64_t *n_valid, const double *u1, const double *u2,
+                   int M, int *conf, int *pose, void *stream);
 
 /*
  * Kernel timing (tracing).  While enabled, every kernel the library launches

@@ -107,6 +107,7 @@ _SIGS = {
     "bpmf_ligand_batch": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _I, _I, _P, ctypes.POINTER(_P)]),
     "bpmf_ligand_free": (None, [_P]),
     "bpmf_eval": (_I, [_P, _P, _P, _I, _D, ctypes.c_uint, _P, _P, _P, _P, _P]),
+    "bpmf_eval_dominant": (_I, [_P, _P, _P, _I, _D, ctypes.c_uint, _P, _P, _P, _P, _P, _P, _P]),
     "bpmf_export_energies": (_I, [_P, _P, _P, _I, _I, ctypes.c_uint, _P, _P]),
     "bpmf_fft_edge": (_I, [_I]),
     "bpmf_set_workspace_limit": (_I, [_P, ctypes.c_size_t]),
@@ -124,6 +125,7 @@ _SIGS = {
     "bpmf_mlp_train_step": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, _I, _P, _P, _P]),
     "bpmf_proposal_sample": (_I, [_P, _P, _I, _D, _P, _I, _P, _P, _P]),
     "bpmf_proposal_bpmf": (_I, [_P, _P, _P, _P, _I, _I, _P, _D, _P, _P]),
+    "bpmf_sir_poses": (_I, [_P, _P, _I, _P, _I, _I, _D, ctypes.c_uint, _P, _P, _P, _P, _I, _P, _P, _P]),
     "bpmf_autotune": (_I, [_P, _P, _P, _I, ctypes.c_uint, _P]),
     "bpmf_export_energies_static": (_I, [_P, _I, _I, _I, _D, _P, _P, _I, _P, _P, _P, _P, _I, _I, ctypes.c_uint, _P,
                                          _P]),
@@ -262,6 +264,20 @@ def bpmf_eval(ctx, lig, recs, kT, mode, logZ, n_valid=None, bpmf=None, dG=None, 
     return _check(rc, "bpmf_eval", ctx)
 
 
+def bpmf_eval_dominant(ctx, lig, recs, kT, mode, logZ, n_valid=None, bpmf=None, dG=None, psi_min=None,
+                       psi_dom=None, stream=None) -> int:
+    """bpmf_eval plus psi_min float64 [total_conf, K] (minimum energy over the
+    valid translations) and psi_dom float64 [n_lig, K + 2] (per receptor
+    minimum over configurations, their minimum, their exponential average)."""
+    K = len(recs)
+    arr = (ctypes.c_void_p * K)(*[r.value if isinstance(r, ctypes.c_void_p) else r for r in recs])
+    rc = lib().bpmf_eval_dominant(ctx, lig, ctypes.cast(arr, ctypes.c_void_p), K, float(kT), int(mode),
+                                  _ptr(logZ, np.float64), _ptr(n_valid, np.int64), _ptr(bpmf, np.float64),
+                                  _ptr(dG, np.float64), _ptr(psi_min, np.float64), _ptr(psi_dom, np.float64),
+                                  _stream(stream))
+    return _check(rc, "bpmf_eval_dominant", ctx)
+
+
 def bpmf_export_energies(ctx, lig, rec, lig_index, conf_index, mode, out, stream=None) -> int:
     """out: float64 [S0, S1, S2] (the receptor's site box), host or device."""
     rc = lib().bpmf_export_energies(ctx, lig, rec, int(lig_index), int(conf_index), int(mode),
@@ -385,6 +401,19 @@ def bpmf_proposal_bpmf(ctx, logZ_s, n_s, q_s, n_tot, kT, bpmf, stream=None):
     _check(lib().bpmf_proposal_bpmf(ctx, _ptr(logZ_s, np.float64), _ptr(n_s, np.int64), _ptr(q_s, np.float64), M,
                                     K, _ptr(n_tot, np.int64), float(kT), _ptr(bpmf, np.float64), _stream(stream)),
            "bpmf_proposal_bpmf", ctx)
+
+
+def bpmf_sir_poses(ctx, lig, lig_index, rec, k, kT, mode, logZ, n_valid, u1, u2, conf, pose, stream=None):
+    """Device tensors: logZ float64 [J, K], n_valid int64 [J, K] of ligand
+    lig_index, u1/u2 float64 [M]; conf/pose int32 [M] out."""
+    J, K = (int(v) for v in tuple(logZ.shape))
+    M = int(tuple(u1.shape)[0])
+    if tuple(u2.shape)[0] != M or tuple(conf.shape)[0] != M or tuple(pose.shape)[0] != M:
+        raise ValueError("u1, u2, conf and pose must have the same length")
+    _check(lib().bpmf_sir_poses(ctx, lig, int(lig_index), rec, K, int(k), float(kT), int(mode),
+                                _ptr(logZ, np.float64), _ptr(n_valid, np.int64), _ptr(u1, np.float64),
+                                _ptr(u2, np.float64), M, _ptr(conf, np.int32), _ptr(pose, np.int32),
+                                _stream(stream)), "bpmf_sir_poses", ctx)
 
 
 def bpmf_valid_counts(ctx, lig, recs, total_conf):

@@ -16,6 +16,7 @@
 
 #include "../../include/bpmf.h"
 #include "kernels.cuh"
+#include "proposal.cuh"
 
 using namespace bpmf;
 
@@ -951,7 +952,7 @@ struct LigPlan {
 
 int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
               double *logZ, int64_t *n_valid, double *bpmf_out, double *dG, cudaStream_t st, int only_lig,
-              int only_conf, double *export_E) {
+              int only_conf, double *export_E, double *Emin = nullptr, double *Dom = nullptr) {
   check_recs(recs, K, c);
   const double h = recs[0]->h;
   const bool use_ff = (mode == BPMF_MODE_FF);
@@ -962,7 +963,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   const int lig_begin = only_lig >= 0 ? only_lig : 0;
   const int lig_end = only_lig >= 0 ? only_lig + 1 : lg->n_lig;
   const bool host_out = !export_E && ((logZ && !is_device_ptr(logZ)) || (n_valid && !is_device_ptr(n_valid)) ||
-                                      (bpmf_out && !is_device_ptr(bpmf_out)) || (dG && !is_device_ptr(dG)));
+                                      (bpmf_out && !is_device_ptr(bpmf_out)) || (dG && !is_device_ptr(dG)) ||
+                                      (Emin && !is_device_ptr(Emin)) || (Dom && !is_device_ptr(Dom)));
   // graph replay: same handles, mode, kT and output buffers as the cached graph
   const bool use_graph = c->graph_mode && !export_E && !host_out && st != nullptr && !c->prof;
   std::vector<unsigned long long> key;
@@ -972,7 +974,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     unsigned long long kb;
     std::memcpy(&kb, &kT, sizeof(kb));
     key.push_back(kb);
-    for (const void *q : {(const void *)logZ, (const void *)n_valid, (const void *)bpmf_out, (const void *)dG})
+    for (const void *q : {(const void *)logZ, (const void *)n_valid, (const void *)bpmf_out, (const void *)dG,
+                          (const void *)Emin, (const void *)Dom})
       key.push_back((unsigned long long)(uintptr_t)q);
     for (const auto &g : groups) {
       const bpmf_ctx::Tune t = tune_for(c, g.P, mode);
@@ -1036,8 +1039,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     pl.off_order = put(ord_s.data(), sizeof(int) * J);
     pl.off_nv = put(nv_s.data(), sizeof(long long) * J * K);
     const size_t JK = (size_t)std::max(J, 1) * K;
-    size_t fixed = align_up(sizeof(long long) * JK) + align_up(sizeof(double) * JK) * 2 +
-                   align_up(sizeof(double) * (K + 1));
+    size_t fixed = align_up(sizeof(long long) * JK) + align_up(sizeof(double) * JK) * 3 +
+                   align_up(sizeof(double) * (2 * K + 3));
     size_t batch_bytes = 0;
     for (const auto &g : groups) {
       const int Kg = (int)g.ks.size();
@@ -1139,8 +1142,10 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       p += align_up(sizeof(double) * JK);
       double *d_logS = reinterpret_cast<double *>(p);
       p += align_up(sizeof(double) * JK);
+      double *d_emin = reinterpret_cast<double *>(p);
+      p += align_up(sizeof(double) * JK);
       double *d_B = reinterpret_cast<double *>(p);
-      p += align_up(sizeof(double) * (K + 1));
+      p += align_up(sizeof(double) * (2 * K + 3));  // bpmf [K], dG, dominant-state [K + 2]
       char *d_grp = p;  // partials + batch buffers, reused group by group
       const ConfMeta *d_meta = reinterpret_cast<const ConfMeta *>(tab + pl.off_meta);
       const int *d_order = reinterpret_cast<const int *>(tab + pl.off_order);
@@ -1189,6 +1194,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         ma.logS = d_logS;
         ma.logZ = d_logZ;
         ma.nvalid_out = d_nvout;
+        ma.kT = kT;
+        ma.emin = d_emin;
         launch(c, "k_merge", st, [&] { return launch_merge_pairs(ma, st); });
       }
       if (export_E) break;
@@ -1202,15 +1209,21 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       mf.logZ = d_logZ;
       mf.bpmf = d_B;
       mf.dG = d_B + K;
+      mf.emin = d_emin;
+      mf.dom = Dom ? d_B + K + 1 : nullptr;
       launch(c, "k_merge", st, [&] { return launch_merge(mf, st); });
       if (J > 0) {
         CK(cudaMemcpyAsync(logZ + conf_base * K, d_logZ, sizeof(double) * J * K, cudaMemcpyDefault, st));
         if (n_valid)
           CK(cudaMemcpyAsync(n_valid + conf_base * K, d_nvout, sizeof(int64_t) * J * K, cudaMemcpyDefault, st));
+        if (Emin) CK(cudaMemcpyAsync(Emin + conf_base * K, d_emin, sizeof(double) * J * K, cudaMemcpyDefault, st));
       }
       if (bpmf_out)
         CK(cudaMemcpyAsync(bpmf_out + (size_t)pl.li * K, d_B, sizeof(double) * K, cudaMemcpyDefault, st));
       if (dG) CK(cudaMemcpyAsync(dG + pl.li, d_B + K, sizeof(double), cudaMemcpyDefault, st));
+      if (Dom)
+        CK(cudaMemcpyAsync(Dom + (size_t)pl.li * (K + 2), d_B + K + 1, sizeof(double) * (K + 2), cudaMemcpyDefault,
+                           st));
       // the next ligand reuses the workspace; stream order keeps these copies first
       conf_base += lg->n_conf[pl.li];
     }
@@ -1239,8 +1252,9 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
 
 }  // namespace
 
-int bpmf_eval(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode, double *logZ,
-              int64_t *n_valid, double *bpmf_out, double *dG, void *stream) {
+namespace {
+int eval_entry(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode, double *logZ,
+               int64_t *n_valid, double *bpmf_out, double *dG, double *psi_min, double *psi_dom, void *stream) {
   if (!c || !lg || !recs || K < 1 || !(kT > 0.0) || (!logZ && lg && lg->total_conf > 0))
     return set_err(c, BPMF_ERR_INVALID_ARG, "null argument, K < 1 or kT <= 0");
   if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16)
@@ -1249,7 +1263,8 @@ int bpmf_eval(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double
   DeviceGuard dg(c->device);
   try {
     last_msg.clear();
-    int rc = eval_impl(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, (cudaStream_t)stream, -1, -1, nullptr);
+    int rc = eval_impl(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, (cudaStream_t)stream, -1, -1, nullptr,
+                       psi_min, psi_dom);
     c->err.clear();
     return rc;
   } catch (Fail f) {
@@ -1257,6 +1272,19 @@ int bpmf_eval(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double
   } catch (std::bad_alloc &) {
     return set_err(c, BPMF_ERR_OOM, "host allocation");
   }
+}
+}  // namespace
+
+int bpmf_eval(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode, double *logZ,
+              int64_t *n_valid, double *bpmf_out, double *dG, void *stream) {
+  return eval_entry(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, nullptr, nullptr, stream);
+}
+
+int bpmf_eval_dominant(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
+                       double *logZ, int64_t *n_valid, double *bpmf_out, double *dG, double *psi_min,
+                       double *psi_dom, void *stream) {
+  if (!psi_min && !psi_dom) return set_err(c, BPMF_ERR_INVALID_ARG, "psi_min and psi_dom both null");
+  return eval_entry(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, psi_min, psi_dom, stream);
 }
 
 int bpmf_autotune(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, unsigned mode, void *stream) {
@@ -1364,6 +1392,67 @@ int bpmf_export_energies(bpmf_ctx_t c, bpmf_lig_t lg, bpmf_rec_t rec, int lig_in
   } catch (Fail f) {
     if (d_out && d_out != out) cudaFreeAsync(d_out, st);
     return set_err(c, f.code, last_msg.empty() ? bpmf_status_string(f.code) : last_msg);
+  }
+  c->err.clear();
+  return BPMF_OK;
+}
+
+int bpmf_sir_poses(bpmf_ctx_t c, bpmf_lig_t lg, int lig_index, bpmf_rec_t rec, int K, int k, double kT, unsigned mode,
+                   const double *logZ, const int64_t *n_valid, const double *u1, const double *u2, int M, int *conf,
+                   int *pose, void *stream) {
+  if (!c || !lg || !rec || !logZ || !n_valid || !u1 || !u2 || !conf || !pose || lig_index < 0 ||
+      lig_index >= lg->n_lig || K < 1 || k < 0 || k >= K || !(kT > 0.0) || M < 0)
+    return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or index out of range");
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16)
+    return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
+  if (lg->ctx != c || rec->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "handle from another context");
+  for (const void *q : {(const void *)logZ, (const void *)n_valid, (const void *)u1, (const void *)u2,
+                        (const void *)conf, (const void *)pose})
+    if (!is_device_ptr(q)) return set_err(c, BPMF_ERR_INVALID_ARG, "bpmf_sir_poses takes device memory");
+  const int J = lg->n_conf[lig_index];
+  if (M == 0 || J == 0) {
+    c->err.clear();
+    return BPMF_OK;
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nS = rec->site_n[0] * rec->site_n[1] * rec->site_n[2];
+  double *d_cdf = nullptr, *d_E = nullptr;
+  try {
+    last_msg.clear();
+    CK(cudaMallocAsync(&d_cdf, sizeof(double) * std::max(J, nS), st));
+    CK(cudaMallocAsync(&d_E, sizeof(double) * std::max(nS, 1), st));
+    CK(cudaMemsetAsync(pose, 0xff, sizeof(int) * M, st));  // -1 until a translation is drawn
+    launch(c, "k_sir_configs", st, [&] {
+      return launch_sir_configs(logZ, reinterpret_cast<const long long *>(n_valid), J, K, k, u1, M, d_cdf, conf, st);
+    });
+    std::vector<int> h_conf(M);
+    CK(cudaMemcpyAsync(h_conf.data(), conf, sizeof(int) * M, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<int> js;
+    for (int v : h_conf)
+      if (v >= 0) js.push_back(v);
+    std::sort(js.begin(), js.end());
+    js.erase(std::unique(js.begin(), js.end()), js.end());
+    bpmf_rec_t recs[1] = {rec};
+    for (int j : js) {
+      eval_impl(c, lg, recs, 1, 1.0, mode, nullptr, nullptr, nullptr, nullptr, st, lig_index, j, d_E);
+      launch(c, "k_sir_translations", st,
+             [&] { return launch_sir_translations(d_E, nS, kT, u2, conf, j, M, d_cdf, pose, st); });
+    }
+    CK(cudaFreeAsync(d_E, st));
+    d_E = nullptr;
+    CK(cudaFreeAsync(d_cdf, st));
+    d_cdf = nullptr;
+    CK(cudaStreamSynchronize(st));
+  } catch (Fail f) {
+    if (d_E) cudaFreeAsync(d_E, st);
+    if (d_cdf) cudaFreeAsync(d_cdf, st);
+    return set_err(c, f.code, last_msg.empty() ? bpmf_status_string(f.code) : last_msg);
+  } catch (std::bad_alloc &) {
+    if (d_E) cudaFreeAsync(d_E, st);
+    if (d_cdf) cudaFreeAsync(d_cdf, st);
+    return set_err(c, BPMF_ERR_OOM, "host allocation");
   }
   c->err.clear();
   return BPMF_OK;

@@ -391,11 +391,10 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfuse
       const long long q = q0 + l;
       cx<T> acc = c_zero<T>();
       if (q < a.Q) {
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const cx<T> r = ld_rec(rh, rl, ((long long)t * P + x) * a.Q + q, T{});
-          acc = c_add(acc, c_mulconj(r, Lsp[x * L3 + t * LW + l]));
-        }
+        const long long ri = (long long)x * a.Q + q, rs = (long long)P * a.Q;
+        const cx<T> r0 = ld_rec(rh, rl, ri, T{}), r1 = ld_rec(rh, rl, ri + rs, T{}), r2 = ld_rec(rh, rl, ri + 2 * rs, T{});
+        const cx<T> *lx = Lsp + x * L3 + l;
+        acc = c_add(c_add(c_mulconj(r0, lx[0]), c_mulconj(r1, lx[LW])), c_mulconj(r2, lx[2 * LW]));
       }
       W1[idx] = c_norm(acc);
     }
@@ -575,6 +574,8 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
   const long long q = (long long)(a.order ? a.order[j] : j) * a.K + k;
   a.logZ[q] = n > 0 ? ls - log((double)n) : -CUDART_INF;
   if (a.nvalid_out) a.nvalid_out[q] = n;
+  // dominant-state energy: the largest -E/kT of all partials, back to kcal/mol
+  if (a.emin) a.emin[q] = (Mx > -CUDART_INF && n > 0) ? -a.kT * Mx : CUDART_INF;
 }
 
 __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
@@ -621,6 +622,32 @@ __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
     }
     ntot_all += ntot;
     __syncthreads();
+  }
+  // dominant-state estimates (Section "Dominant state"): the minimum
+  // interaction energy per receptor, its minimum and exponential average over
+  // receptors
+  if (a.dom && a.emin) {
+    for (int k = 0; k < a.K; ++k) {
+      double mn = CUDART_INF;
+      for (int j = threadIdx.x; j < a.J; j += blockDim.x) mn = fmin(mn, a.emin[(long long)j * a.K + k]);
+      s_d[threadIdx.x] = mn;
+      __syncthreads();
+      for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s_d[threadIdx.x] = fmin(s_d[threadIdx.x], s_d[threadIdx.x + o]);
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) a.dom[k] = s_d[0];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      double mn = CUDART_INF;
+      for (int k = 0; k < a.K; ++k) mn = fmin(mn, a.dom[k]);
+      double s = 0.0;
+      if (mn < CUDART_INF)
+        for (int k = 0; k < a.K; ++k) s += exp(-(a.dom[k] - mn) / a.kT);
+      a.dom[a.K] = mn;
+      a.dom[a.K + 1] = mn < CUDART_INF ? mn - a.kT * (log(s) - log((double)a.K)) : CUDART_INF;
+    }
   }
   if (threadIdx.x == 0 && a.dG) {
     double mx = -CUDART_INF;

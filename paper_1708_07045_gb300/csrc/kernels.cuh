@@ -104,6 +104,9 @@ struct MergeArgs {
   double *bpmf;            // [K]
   double *dG;              // [1]
   long long *nvalid_out;   // [J][K], caller's order (may be null)
+  double *emin;            // [J][K], caller's order: minimum energy over valid translations (may be null)
+  double *dom;             // [K + 2] (k_merge, with emin): min over configurations per receptor, the min over
+                           // receptors, and -kT ln mean_k exp(-min_k / kT) (may be null)
 };
 
 // ---- launch wrappers (kernels.cu) --------------------------------------------

@@ -440,4 +440,114 @@ cudaError_t launch_is_estimate(const double *logZ_s, const long long *n_s, const
   return cudaGetLastError();
 }
 
+// --------------------------------------------------------------------------
+// Sampling importance resampling of poses with weight exp(-E / kT) (FP64).
+// The draw over all (configuration, translation) poses of one receptor is
+// taken exactly in two stages: the configuration j with probability
+// S_j / sum_j S_j (S_j = n_j exp(log Z_j), the sum of exp(-E/kT) over j's
+// valid translations), then, within j, the translation with probability
+// exp(-E_s / kT) / S_j.  Each stage is an inverse CDF on caller uniforms:
+// the first index whose cumulative weight exceeds u * total.
+//
+// Cumulative weights: thread t owns the contiguous chunk [t C, (t+1) C) of
+// the n weights; chunk sums, their exclusive prefix (thread 0, in order),
+// then every thread writes its chunk's prefix.  The order of additions is
+// fixed, so draws are deterministic.
+template <class W>
+__device__ double block_cdf(int n, W weight, double *cdf, double *s_d) {
+  const int C = (n + blockDim.x - 1) / blockDim.x;
+  const int b = threadIdx.x * C, e = min(n, b + C);
+  double acc = 0.0;
+  for (int i = b; i < e; ++i) acc += weight(i);
+  s_d[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double c = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const double v = s_d[t];
+      s_d[t] = c;
+      c += v;
+    }
+  }
+  __syncthreads();
+  double c = s_d[threadIdx.x];
+  for (int i = b; i < e; ++i) {
+    c += weight(i);
+    cdf[i] = c;
+  }
+  __syncthreads();
+  return cdf[n - 1];
+}
+
+__device__ int inverse_cdf(const double *cdf, int n, double x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cdf[mid] > x) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ double block_max(double v, double *s_d) {
+  s_d[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) s_d[threadIdx.x] = fmax(s_d[threadIdx.x], s_d[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double r = s_d[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_sir_configs(const double *logZ, const long long *nvalid, int J, int K, int k,
+                                                     const double *u, int M, double *cdf, int *conf) {
+  __shared__ double s_d[256];
+  auto logS = [&](int j) {
+    const long long n = nvalid[(long long)j * K + k];
+    return n > 0 ? logZ[(long long)j * K + k] + log((double)n) : -CUDART_INF;
+  };
+  double mx = -CUDART_INF;
+  for (int j = threadIdx.x; j < J; j += blockDim.x) mx = fmax(mx, logS(j));
+  const double M0 = block_max(mx, s_d);
+  double total = 0.0;
+  if (M0 > -CUDART_INF)
+    total = block_cdf(J, [&](int j) {
+      const double v = logS(j);
+      return v > -CUDART_INF ? exp(v - M0) : 0.0;
+    }, cdf, s_d);
+  for (int s = threadIdx.x; s < M; s += blockDim.x) conf[s] = total > 0.0 ? inverse_cdf(cdf, J, u[s] * total) : -1;
+}
+
+__global__ void __launch_bounds__(256) k_sir_translations(const double *E, int nS, double kT, const double *u,
+                                                          const int *conf, int j, int M, double *cdf, int *pick) {
+  __shared__ double s_d[256];
+  double mx = -CUDART_INF;
+  for (int i = threadIdx.x; i < nS; i += blockDim.x) mx = fmax(mx, -E[i] / kT);
+  const double M0 = block_max(mx, s_d);
+  double total = 0.0;
+  if (M0 > -CUDART_INF)
+    total = block_cdf(nS, [&](int i) {
+      const double v = -E[i] / kT;
+      return v > -CUDART_INF ? exp(v - M0) : 0.0;
+    }, cdf, s_d);
+  for (int s = threadIdx.x; s < M; s += blockDim.x)
+    if (conf[s] == j) pick[s] = total > 0.0 ? inverse_cdf(cdf, nS, u[s] * total) : -1;
+}
+
+cudaError_t launch_sir_configs(const double *logZ, const long long *nvalid, int J, int K, int k, const double *u,
+                               int M, double *cdf, int *conf, cudaStream_t st) {
+  if (J <= 0 || M <= 0) return cudaSuccess;
+  k_sir_configs<<<1, 256, 0, st>>>(logZ, nvalid, J, K, k, u, M, cdf, conf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sir_translations(const double *E, int nS, double kT, const double *u, const int *conf, int j, int M,
+                                    double *cdf, int *pick, cudaStream_t st) {
+  if (nS <= 0 || M <= 0) return cudaSuccess;
+  k_sir_translations<<<1, 256, 0, st>>>(E, nS, kT, u, conf, j, M, cdf, pick);
+  return cudaGetLastError();
+}
+
 }  // namespace bpmf

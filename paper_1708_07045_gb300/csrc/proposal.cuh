@@ -37,5 +37,9 @@ cudaError_t launch_proposal(const float *pred, int J, double mix, const double *
                             int *idx, double *q_s, cudaStream_t st);
 cudaError_t launch_is_estimate(const double *logZ_s, const long long *n_s, const double *q_s, int M, int K,
                                const long long *n_tot, double kT, double *bpmf, cudaStream_t st);
+cudaError_t launch_sir_configs(const double *logZ, const long long *nvalid, int J, int K, int k, const double *u,
+                               int M, double *cdf, int *conf, cudaStream_t st);
+cudaError_t launch_sir_translations(const double *E, int nS, double kT, const double *u, const int *conf, int j, int M,
+                                    double *cdf, int *pick, cudaStream_t st);
 
 }  // namespace bpmf
