@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
     src = os.path.join(_HERE, "oracle.c")
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fno-fast-math", "-shared", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fno-fast-math", "-ffp-contract=off", "-shared", "-fPIC",
                                "-o", tmp, src, "-lm"])
         os.replace(tmp, _SO)
     return _SO
@@ -61,10 +61,14 @@ def _load():
             lp = ctypes.POINTER(ctypes.c_int64)
             lib.oracle_place.argtypes = [ctypes.c_int, fp, ctypes.c_double, dp, ip]
             lib.oracle_place.restype = ctypes.c_int
-            lib.oracle_pose_energies.argtypes = [fp, ip, ctypes.c_double, ip, ip, ctypes.c_int, fp, dp, dp, lp]
+            bp = ctypes.POINTER(ctypes.c_ubyte)
+            lib.oracle_pose_energies.argtypes = [fp, ip, ctypes.c_double, ip, ip, ctypes.c_int, fp, dp, fp, bp,
+                                                 dp, lp]
             lib.oracle_pose_energies.restype = ctypes.c_int
             lib.oracle_logS_batch.argtypes = [fp, ip, ctypes.c_double, ip, ip, ctypes.c_int, ctypes.c_int,
-                                              fp, dp, ctypes.c_double, dp, lp, dp]
+                                              fp, dp, fp, bp, ctypes.c_double, dp, lp, dp]
+            lib.oracle_ligand_occupancy.argtypes = [ctypes.c_int, fp, fp, ctypes.c_double, ip, ctypes.c_int]
+            lib.oracle_ligand_occupancy.restype = ctypes.c_int
             lib.oracle_logS_batch.restype = ctypes.c_int
             lib.oracle_count_valid.argtypes = [ip, ip, ip, ip]
             lib.oracle_count_valid.restype = ctypes.c_int64
@@ -109,27 +113,58 @@ def count_valid(dims, u, site_lo, site_n) -> int:
                                           _p(_i3(site_lo), ctypes.c_int), _p(_i3(site_n), ctypes.c_int)))
 
 
-def pose_energies(grids, h, site_lo, site_n, coords, gam):
+def _occ_args(occ, R, shape):
+    """(R pointer, occupancy pointer, keep-alive arrays) for the C calls."""
+    if occ is None:
+        return None, None, ()
+    if R is None:
+        raise ValueError("an occupancy grid needs the ligand R")
+    o = np.ascontiguousarray(occ, dtype=np.uint8)
+    if o.shape != tuple(shape):
+        raise ValueError("occupancy grid shape differs from the grids")
+    r = np.ascontiguousarray(R, dtype=np.float32)
+    return _p(r, ctypes.c_float), _p(o, ctypes.c_ubyte), (o, r)
+
+
+def ligand_occupancy(coords, R, h):
+    """Occupied ligand-box nodes [count, 3] of one configuration (Eq.
+    occupancy_grid, decided in single precision as documented in oracle.c)."""
+    c = np.ascontiguousarray(coords, dtype=np.float32)
+    r = np.ascontiguousarray(R, dtype=np.float32)
+    lib = _load()
+    n = lib.oracle_ligand_occupancy(c.shape[0], _p(c, ctypes.c_float), _p(r, ctypes.c_float), float(h), None, 0)
+    if n < 0:
+        raise ValueError("oracle_ligand_occupancy failed")
+    out = np.empty((max(n, 1), 3), dtype=np.int32)
+    lib.oracle_ligand_occupancy(c.shape[0], _p(c, ctypes.c_float), _p(r, ctypes.c_float), float(h),
+                                _p(out, ctypes.c_int), n)
+    return out[:n]
+
+
+def pose_energies(grids, h, site_lo, site_n, coords, gam, occ=None, R=None):
     """FP64 energies [S0, S1, S2] of one configuration over the site window
-    (+inf where the translation is filtered out), and the valid count."""
+    (+inf where the translation is filtered out or, with a receptor occupancy
+    grid ``occ`` and the ligand's ``R``, clashes), and the valid count
+    (clashing translations included)."""
     g = np.ascontiguousarray(grids, dtype=np.float32)
     c = np.ascontiguousarray(coords, dtype=np.float32)
     gm = np.ascontiguousarray(gam, dtype=np.float64)
     sn = _i3(site_n)
     E = np.empty(tuple(int(v) for v in sn), dtype=np.float64)
     n = np.zeros(1, dtype=np.int64)
+    rp, op, _keep = _occ_args(occ, R, g.shape[1:])
     rc = _load().oracle_pose_energies(_p(g, ctypes.c_float), _p(_i3(g.shape[1:]), ctypes.c_int), float(h),
                                       _p(_i3(site_lo), ctypes.c_int), _p(sn, ctypes.c_int), c.shape[0],
-                                      _p(c, ctypes.c_float), _p(gm, ctypes.c_double), _p(E, ctypes.c_double),
-                                      _p(n, ctypes.c_int64))
+                                      _p(c, ctypes.c_float), _p(gm, ctypes.c_double), rp, op,
+                                      _p(E, ctypes.c_double), _p(n, ctypes.c_int64))
     if rc != 0:
         raise ValueError("oracle_pose_energies: invalid arguments")
     return E, int(n[0])
 
 
-def logS_batch(grids, h, site_lo, site_n, coords, gam, kT):
+def logS_batch(grids, h, site_lo, site_n, coords, gam, kT, occ=None, R=None):
     """log S_jk, n_jk and min E_jk for every configuration j of ``coords``
-    [J, n, 3] against one receptor."""
+    [J, n, 3] against one receptor (clashes as in ``pose_energies``)."""
     g = np.ascontiguousarray(grids, dtype=np.float32)
     c = np.ascontiguousarray(coords, dtype=np.float32)
     gm = np.ascontiguousarray(gam, dtype=np.float64)
@@ -137,9 +172,10 @@ def logS_batch(grids, h, site_lo, site_n, coords, gam, kT):
     logS = np.empty(J, dtype=np.float64)
     nv = np.empty(J, dtype=np.int64)
     emin = np.empty(J, dtype=np.float64)
+    rp, op, _keep = _occ_args(occ, R, g.shape[1:])
     rc = _load().oracle_logS_batch(_p(g, ctypes.c_float), _p(_i3(g.shape[1:]), ctypes.c_int), float(h),
                                    _p(_i3(site_lo), ctypes.c_int), _p(_i3(site_n), ctypes.c_int), J, n,
-                                   _p(c, ctypes.c_float), _p(gm, ctypes.c_double), float(kT),
+                                   _p(c, ctypes.c_float), _p(gm, ctypes.c_double), rp, op, float(kT),
                                    _p(logS, ctypes.c_double), _p(nv, ctypes.c_int64), _p(emin, ctypes.c_double))
     if rc != 0:
         raise ValueError("oracle_logS_batch: invalid arguments")
@@ -190,7 +226,9 @@ def evaluate(receptors, coords, q, eps, R, kT, p_rep: int = 12, p_att: int = 6):
     nv = np.empty((J, K), dtype=np.int64)
     emin = np.empty((J, K))
     for k, r in enumerate(receptors):
-        logS[:, k], nv[:, k], emin[:, k] = logS_batch(r.grids, r.h, r.site_lo, r.site_n, coords, gam, kT)
+        occ = getattr(r, "occ", None)
+        logS[:, k], nv[:, k], emin[:, k] = logS_batch(r.grids, r.h, r.site_lo, r.site_n, coords, gam, kT,
+                                                      occ=occ, R=R if occ is not None else None)
     B = bpmf(logS, nv, kT)
     h = receptors[0].h
     vs = site_volume(nv, h)

@@ -61,8 +61,12 @@ def _load():
             lib.gridgen_build.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, d, ctypes.c_int, d, d, d, d,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                          ctypes.c_double, ctypes.c_double]
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double]
             lib.gridgen_build.restype = ctypes.c_int
+            lib.gridgen_occupancy.argtypes = [ctypes.POINTER(ctypes.c_ubyte), ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_double, d, ctypes.c_int, d, d,
+                                              ctypes.c_double]
+            lib.gridgen_occupancy.restype = None
             _lib = lib
     return _lib
 
@@ -107,9 +111,14 @@ def grid_origin(shape, h: float) -> np.ndarray:
     return -np.asarray([n // 2 for n in shape], dtype=np.float64) * h
 
 
+OCC_SCALE = 2.0 ** (-1.0 / 6.0)  # occupancy / cutoff radius in units of R (sigma)
+
+
 def receptor_grids(atoms: Atoms, shape, h: float, clamp: float = 0.5, clip: float = 1e4,
-                   p_rep: float = 12.0, p_att: float = 6.0, coulomb: float = COULOMB):
-    """Return (grids float32 [3, nx, ny, nz] = elec, LJr, LJa; origin float64 [3])."""
+                   p_rep: float = 12.0, p_att: float = 6.0, coulomb: float = COULOMB, cutoff: float = 0.0):
+    """Return (grids float32 [3, nx, ny, nz] = elec, LJr, LJa; origin float64 [3]).
+    ``cutoff`` > 0 zeroes every term of atom j within cutoff * R_j (used with
+    occupancy grids, clamp and clip then 0)."""
     nx, ny, nz = (int(s) for s in shape)
     origin = grid_origin((nx, ny, nz), h)
     out = np.empty((3, nx, ny, nz), dtype=np.float32)
@@ -120,10 +129,21 @@ def receptor_grids(atoms: Atoms, shape, h: float, clamp: float = 0.5, clip: floa
     o = np.ascontiguousarray(origin)
     rc = _load().gridgen_build(out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), nx, ny, nz, float(h),
                                _dp(o), len(q), _dp(xyz), _dp(q), _dp(eps), _dp(R), float(p_rep),
-                               float(p_att), float(coulomb), float(clamp), float(clip))
+                               float(p_att), float(coulomb), float(clamp), float(clip), float(cutoff))
     if rc != 0:
         raise MemoryError("gridgen_build failed")
     return out, origin
+
+
+def receptor_occupancy(atoms: Atoms, shape, h: float, scale: float = OCC_SCALE) -> np.ndarray:
+    """uint8 [nx, ny, nz]: 1 where some atom j has |r_j - n| < scale * R_j."""
+    nx, ny, nz = (int(s) for s in shape)
+    o = np.ascontiguousarray(grid_origin((nx, ny, nz), h))
+    out = np.empty((nx, ny, nz), dtype=np.uint8)
+    _load().gridgen_occupancy(out.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), nx, ny, nz, float(h), _dp(o),
+                              len(atoms.R), _dp(np.ascontiguousarray(atoms.xyz, dtype=np.float64)),
+                              _dp(np.ascontiguousarray(atoms.R, dtype=np.float64)), float(scale))
+    return out
 
 
 @dataclass
@@ -198,6 +218,7 @@ class ReceptorInput:
     origin: np.ndarray
     site_lo: tuple
     site_n: tuple
+    occ: np.ndarray | None = None  # uint8 [nx, ny, nz] occupancy grid, or None
 
     @property
     def shape(self):
@@ -249,6 +270,38 @@ def protein_scale(n_conf: int = 2000, n_rec: int = 4, seed: int = 1001, clip: fl
     lig = ligand_params(seed + 1, n_atoms_lig)
     coords = ligand_configs(seed + 2, n_atoms_lig, n_conf)
     return Workload("protein-scale 96^3 h=0.25 J=%d K=%d %d atoms" % (n_conf, n_rec, n_atoms_lig),
+                    recs, [LigandInput(lig, coords)])
+
+
+def plain_small_occ(n_conf: int = 64, seed: int = 1000, shell=(6.0, 12.0), n_atoms: int = 200) -> Workload:
+    """plain_small with the paper's clash treatment: grids with V = 0 inside
+    2^(-1/6) R_j (no clamp, no clip) and the receptor occupancy grid."""
+    atoms = receptor_atoms(seed, n_atoms, *shell)
+    g, o = receptor_grids(atoms, (32, 32, 32), 0.375, clamp=0.0, clip=0.0, cutoff=OCC_SCALE)
+    occ = receptor_occupancy(atoms, (32, 32, 32), 0.375)
+    lo, sn = central_site((32, 32, 32), 16)
+    lig = ligand_params(seed + 1, 12)
+    coords = ligand_configs(seed + 2, 12, n_conf)
+    return Workload("occupancy 32^3 h=0.375 J=%d K=1 12 atoms" % n_conf,
+                    [ReceptorInput(g, 0.375, o, lo, sn, occ)], [LigandInput(lig, coords)])
+
+
+def protein_scale_occ(n_conf: int = 2000, n_rec: int = 4, seed: int = 1001, n_atoms_lig: int = 30) -> Workload:
+    """protein_scale with the paper's clash treatment (cutoff grids and
+    receptor occupancy grids).  The receptor is a 10-22 A shell at 0.05
+    atoms per A^3 (2020 atoms), so the 30-atom ligand fits the pocket at part
+    of its translations."""
+    base = receptor_atoms(seed, 2020, 10.0, 22.0)
+    recs = []
+    for k in range(n_rec):
+        atoms = jitter(base, 0.3, seed + 100 * (k + 1))
+        g, o = receptor_grids(atoms, (96, 96, 96), 0.25, clamp=0.0, clip=0.0, cutoff=OCC_SCALE)
+        occ = receptor_occupancy(atoms, (96, 96, 96), 0.25)
+        lo, sn = central_site((96, 96, 96), 40)
+        recs.append(ReceptorInput(g, 0.25, o, lo, sn, occ))
+    lig = ligand_params(seed + 1, n_atoms_lig)
+    coords = ligand_configs(seed + 2, n_atoms_lig, n_conf)
+    return Workload("occupancy protein-scale 96^3 h=0.25 J=%d K=%d %d atoms" % (n_conf, n_rec, n_atoms_lig),
                     recs, [LigandInput(lig, coords)])
 
 
