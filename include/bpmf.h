@@ -116,6 +116,30 @@ int bpmf_receptor_load(bpmf_ctx_t ctx, const float *grids, int nx, int ny, int n
 void bpmf_receptor_free(bpmf_rec_t rec);
 
 /*
+ * bpmf_receptor_set_occupancy -- attach the receptor occupancy grid of the
+ * steric-clash treatment (Eq. occupancy_grid; methodology, "FFT-based BPMF
+ * Estimation": receptor grids built with V(r) = 0 inside 2^(-1/6) sigma, clashes
+ * detected by correlating the receptor and ligand occupancy grids).
+ *   occ  [nx][ny][nz] uint8 (0 = free, nonzero = occupied), the receptor's
+ *        own grid dimensions; host or device; NULL detaches the grid.
+ * With a grid attached, every evaluation against this receptor treats a
+ * valid translation as clashing when some occupied ligand node lands on an
+ * occupied receptor node (nodes outside the grid are free); a clashing pose
+ * keeps its place in the sample (it counts in n_valid) with infinite energy:
+ * it adds nothing to S, is +inf in bpmf_export_energies and is never drawn
+ * by bpmf_sir_poses.  The ligand occupancy grid marks node n when
+ * |p_i - n|^2 < 2^(-1/3) (R_i / h)^2 for some atom i, with p_i the atom's
+ * position in grid units after placement and R the size parameter given to
+ * bpmf_ligand_batch, each step rounded to IEEE single precision in the order
+ * p = (x - min x) / h + 2, r = R / h, threshold = (r r) 2^(-1/3),
+ * distance = ((dx dx + dy dy) + dz dz).  The library copies the grid into
+ * bit tables (about 6 (nx (nz + 64) / 8 + 8) ny bytes of device memory).
+ * Synchronises `stream`.  Errors: INVALID_ARG, OOM, CUDA; bpmf_eval returns
+ * SIZE_UNSUPPORTED when an occupancy radius exceeds 60 grid spacings.
+ */
+int bpmf_receptor_set_occupancy(bpmf_ctx_t ctx, bpmf_rec_t rec, const uint8_t *occ, void *stream);
+
+/*
  * bpmf_ligand_batch -- upload a batch of ligands and their rigid
  * configurations (the randomly rotated apo-ensemble snapshots of Methodology,
  * Ligand Sampling) and compute the generalised charges of Eq. general_form:

@@ -22,7 +22,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "libbpmf.so")
-_SOURCES = ["kernels.cu", "bpmf_api.cu", "bpmf_static.cu", "proposal.cu", "bpmf_proposal.cu"]
+_SOURCES = ["kernels.cu", "occupancy.cu", "bpmf_api.cu", "bpmf_static.cu", "proposal.cu", "bpmf_proposal.cu"]
 _HEADERS = ["arith.cuh", "fft.cuh", "kernels.cuh", "proposal.cuh", "tc_dft.cuh"]
 
 BPMF_OK = 0
@@ -109,6 +109,7 @@ _SIGS = {
     "bpmf_eval": (_I, [_P, _P, _P, _I, _D, ctypes.c_uint, _P, _P, _P, _P, _P]),
     "bpmf_eval_dominant": (_I, [_P, _P, _P, _I, _D, ctypes.c_uint, _P, _P, _P, _P, _P, _P, _P]),
     "bpmf_export_energies": (_I, [_P, _P, _P, _I, _I, ctypes.c_uint, _P, _P]),
+    "bpmf_receptor_set_occupancy": (_I, [_P, _P, _P, _P]),
     "bpmf_fft_edge": (_I, [_I]),
     "bpmf_set_workspace_limit": (_I, [_P, ctypes.c_size_t]),
     "bpmf_profile_enable": (_I, [_P, _I]),
@@ -233,6 +234,22 @@ def bpmf_receptor_load(ctx, grids, h, origin, site_lo, site_n, stream=None):
 
 def bpmf_receptor_free(rec):
     lib().bpmf_receptor_free(rec)
+
+
+def bpmf_receptor_set_occupancy(ctx, rec, occ, stream=None):
+    """occ: uint8 [nx, ny, nz] (numpy or torch, host or device), or None to detach."""
+    if occ is None:
+        p = None
+    elif hasattr(occ, "data_ptr"):
+        import torch
+        if occ.dtype != torch.uint8 or not occ.is_contiguous():
+            raise TypeError("occupancy tensor must be contiguous uint8")
+        p = ctypes.c_void_p(occ.data_ptr())
+    else:
+        a = np.ascontiguousarray(occ, dtype=np.uint8)
+        occ = a
+        p = ctypes.c_void_p(a.ctypes.data)
+    _check(lib().bpmf_receptor_set_occupancy(ctx, rec, p, _stream(stream)), "bpmf_receptor_set_occupancy", ctx)
 
 
 def bpmf_ligand_batch(ctx, n_atoms, n_conf, coords, q, eps, R, p_rep=12, p_att=6, stream=None):

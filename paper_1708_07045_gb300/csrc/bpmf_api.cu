@@ -67,6 +67,8 @@ struct bpmf_rec {
   double origin[3] = {0, 0, 0};
   int site_lo[3] = {0, 0, 0}, site_n[3] = {0, 0, 0};
   float2 *hi = nullptr, *lo = nullptr;  // [3][P0][Q]
+  uint32_t *occ = nullptr;              // occupancy sparse tables [kOccLevels][N0][occW][N1], or null
+  int occW = 0;
 };
 
 struct bpmf_lig {
@@ -79,6 +81,7 @@ struct bpmf_lig {
   float2 *gamma = nullptr;  // device [3][total_atoms] float pairs
   float *q = nullptr, *eps = nullptr, *R = nullptr;  // device [total_atoms] (configuration features)
   std::vector<float> minmax;  // host [total_conf][6]
+  std::vector<float> R_host;  // host [total_atoms] (occupancy radii)
 };
 
 namespace {
@@ -345,7 +348,10 @@ struct BatchGeom {
   long long Q;
   int S[3];
   int K;
+  int occ_cap = 0;  // ligand occupancy runs per configuration (0: no clash channel)
 };
+
+int clash_words(int S2) { return (S2 + 31) / 32; }
 
 size_t batch_bytes_per_conf(const BatchGeom &g, size_t E) {
   const size_t box = 3ull * g.U[0] * g.U[1] * g.U[2] * sizeof(float2);
@@ -353,14 +359,32 @@ size_t batch_bytes_per_conf(const BatchGeom &g, size_t E) {
   const size_t ly = 3ull * g.U[0] * g.Q * E;
   const size_t x2 = (size_t)g.K * g.S[0] * g.Q * E;
   const size_t y2 = (size_t)g.K * g.S[0] * g.S[1] * g.F2 * E;
-  return align_up(box) + align_up(lz) + align_up(ly) + align_up(x2) + align_up(y2);
+  size_t occ = 0;
+  if (g.occ_cap > 0)
+    occ = align_up((size_t)g.occ_cap * sizeof(OccRun)) + align_up(sizeof(int)) +
+          align_up((size_t)g.K * g.S[0] * g.S[1] * clash_words(g.S[2]) * sizeof(uint32_t));
+  return align_up(box) + align_up(lz) + align_up(ly) + align_up(x2) + align_up(y2) + occ;
+}
+
+// Upper bound on the occupancy runs of one configuration: every merged
+// interval of a row comes from an atom whose disk covers the row (at most
+// (2 ceil(r) + 1)^2 rows per atom, r = R / h in nodes), and a long interval
+// splits into pieces of at most 63 nodes over a row extent of at most
+// u2 + 2 ceil(r) + 6 nodes.
+int occ_run_cap(int n_atoms, float rmax_nodes, int u2) {
+  const int rc = (int)std::ceil(rmax_nodes);
+  const long long disk = (long long)(2 * rc + 1) * (2 * rc + 1);
+  const long long nC = (long long)u2 + 2 * rc + 6;
+  const long long cap = (long long)n_atoms * disk * (2 + nC / 63);
+  return (int)std::min<long long>(cap, 1ll << 28);
 }
 
 template <class T>
 void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, const ConfMeta *d_meta,
                const PairInfo *d_info, const float2 *const *d_rhi, const float2 *const *d_rlo, double h,
                float nscale_hi, float nscale_lo, float escale_hi, float escale_lo, float4 *d_part,
-               double *export_E, char *ws, cudaStream_t st, const bpmf_ctx::Tune &tn, bool split = false) {
+               double *export_E, char *ws, cudaStream_t st, const bpmf_ctx::Tune &tn, bool split = false,
+               const OccTab *d_tabs = nullptr) {
   auto plan = [&](int P) { return split ? make_plan_split(c, P) : make_plan(P); };
   const size_t E = sizeof(cx<T>);
   char *p = ws;
@@ -373,6 +397,33 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   void *x2 = p;
   p += align_up((size_t)batch * g.K * g.S[0] * g.Q * E);
   void *y2 = p;
+  p += align_up((size_t)batch * g.K * g.S[0] * g.S[1] * g.F2 * E);
+  uint32_t *clash = nullptr;
+  const int CW = clash_words(g.S[2]);
+  if (g.occ_cap > 0 && d_tabs) {
+    OccRun *runs = reinterpret_cast<OccRun *>(p);
+    p += align_up((size_t)batch * g.occ_cap * sizeof(OccRun));
+    int *n_runs = reinterpret_cast<int *>(p);
+    p += align_up((size_t)batch * sizeof(int));
+    clash = reinterpret_cast<uint32_t *>(p);
+    OccRunsArgs ra{lg->coords, lg->R, d_meta, (float)h, g.occ_cap, runs, n_runs};
+    launch(c, "k_occ_runs", st, [&] { return launch_occ_runs(ra, batch, st); });
+    ClashArgs ca{};
+    ca.runs = runs;
+    ca.n_runs = n_runs;
+    ca.cap = g.occ_cap;
+    ca.tabs = d_tabs;
+    ca.info = d_info;
+    ca.K = g.K;
+    ca.S0 = g.S[0];
+    ca.S1 = g.S[1];
+    ca.S2 = g.S[2];
+    ca.CW = CW;
+    ca.T1 = std::min(g.S[1], 256);
+    ca.T0 = std::max(1, std::min(g.S[0], 256 / ca.T1));
+    ca.clash = clash;
+    launch(c, "k_clash", st, [&] { return launch_clash(ca, batch, st); });
+  }
 
   float hh, hl;
   split_ff(h, hh, hl);
@@ -458,6 +509,8 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   zi.escale_lo = escale_lo;
   zi.part = d_part;
   zi.export_E = export_E;
+  zi.clash = clash;
+  zi.CW = CW;
   zi.plan = plan(g.P[2]);
   zi.tw = twiddles(c, g.P[2]);
   launch(c, sizeof(T) == 4 ? "k_zinv<fp32>" : "k_zinv<ff>", st, [&] { return launch_zinv<T>(zi, batch, st); });
@@ -785,8 +838,44 @@ void bpmf_receptor_free(bpmf_rec_t r) {
     DeviceGuard g(r->ctx->device);
     if (r->hi) cudaFree(r->hi);
     if (r->lo) cudaFree(r->lo);
+    if (r->occ) cudaFree(r->occ);
   }
   delete r;
+}
+
+int bpmf_receptor_set_occupancy(bpmf_ctx_t c, bpmf_rec_t r, const uint8_t *occ, void *stream) {
+  if (!c || !r || r->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "null receptor or receptor of another context");
+  DeviceGuard dg(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t *tab = nullptr;
+  try {
+    last_msg.clear();
+    if (occ) {
+      const int W = (r->N[2] + kOccZPad + 31) / 32 + 2;
+      const size_t words = (size_t)kOccLevels * r->N[0] * W * r->N[1];
+      DevIn o(occ, (size_t)r->N[0] * r->N[1] * r->N[2], st);
+      CK(cudaMalloc(&tab, words * sizeof(uint32_t)));
+      launch(c, "k_occ_table", st, [&] {
+        return launch_occ_table(static_cast<const unsigned char *>(o.p), r->N[0], r->N[1], r->N[2], W, tab, st);
+      });
+      CK(cudaStreamSynchronize(st));
+      if (r->occ) cudaFree(r->occ);
+      r->occ = tab;
+      r->occW = W;
+      tab = nullptr;
+    } else if (r->occ) {
+      CK(cudaStreamSynchronize(st));
+      cudaFree(r->occ);
+      r->occ = nullptr;
+      r->occW = 0;
+    }
+    r->id = c->next_id++;  // results change: a new identity for the graph cache
+  } catch (Fail f) {
+    if (tab) cudaFree(tab);
+    return set_err(c, f.code, last_msg);
+  }
+  c->err.clear();
+  return BPMF_OK;
 }
 
 int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_conf, const float *coords,
@@ -840,6 +929,8 @@ int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_
     CK(cudaMemcpyAsync(lg->q, q, na * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaMemcpyAsync(lg->eps, eps, na * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaMemcpyAsync(lg->R, R, na * sizeof(float), cudaMemcpyDefault, st));
+    lg->R_host.resize(na);
+    CK(cudaMemcpyAsync(lg->R_host.data(), lg->R, na * sizeof(float), cudaMemcpyDeviceToHost, st));
     CK(cudaMalloc(&lg->coords, std::max<size_t>(1, 3 * lg->total_coord_atoms) * sizeof(float)));
     {
       DevIn dq(q, na * sizeof(float), st), de(eps, na * sizeof(float), st), dr(R, na * sizeof(float), st);
@@ -944,6 +1035,8 @@ struct LigPlan {
   size_t off_meta = 0, off_order = 0, off_nv = 0;   // blob offsets
   std::vector<size_t> off_info;                     // per group: [J][Kg] PairInfo
   std::vector<size_t> off_kmap, off_rptr;           // per group
+  std::vector<size_t> off_occ;                      // per group: [Kg] OccTab (unused when occ_cap is 0)
+  std::vector<int> occ_cap;                         // per group: runs per configuration, 0 without occupancy
   std::vector<std::array<int, 3>> Umax;             // per group
   std::vector<std::vector<std::array<int, 3>>> Ub;  // per group, per batch
   std::vector<int> B;                               // per group batch size
@@ -1055,6 +1148,14 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         rp[Kg + kg] = recs[g.ks[kg]]->lo;
       }
       pl.off_rptr.push_back(put(rp.data(), sizeof(void *) * 2 * Kg));
+      std::vector<OccTab> ot(Kg);
+      bool any_occ = false;
+      for (int kg = 0; kg < Kg; ++kg) {
+        const bpmf_rec *r = recs[g.ks[kg]];
+        ot[kg] = OccTab{r->occ, r->N[0], r->N[1], r->N[2], r->occW};
+        any_occ = any_occ || r->occ;
+      }
+      pl.off_occ.push_back(put(ot.data(), sizeof(OccTab) * Kg));
       std::array<int, 3> Um{1, 1, 1};
       for (int i = 0; i < J; ++i)
         for (int d = 0; d < 3; ++d) Um[d] = std::max(Um[d], std::min(meta_s[i].u[d], g.P[d]));
@@ -1069,6 +1170,18 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       bg.F2 = g.F2;
       bg.Q = g.Q;
       bg.K = Kg;
+      if (any_occ && J > 0) {
+        float rmax = 0.f;
+        const float hf = (float)h;
+        for (int i = 0; i < lg->n_atoms[li]; ++i)
+          rmax = std::max(rmax, std::fabs(lg->R_host[lg->atom_off[li] + i] / hf));
+        if (!(rmax <= 60.f)) {
+          last_msg = "occupancy radius above 60 grid spacings";
+          throw Fail{BPMF_ERR_SIZE_UNSUPPORTED};
+        }
+        bg.occ_cap = occ_run_cap(lg->n_atoms[li], rmax, Um[2]);
+      }
+      pl.occ_cap.push_back(bg.occ_cap);
       const size_t per_conf = batch_bytes_per_conf(bg, E);
       const size_t part = align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
       const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
@@ -1174,12 +1287,14 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
           gb.F2 = g.F2;
           gb.Q = g.Q;
           gb.K = Kg;
+          gb.occ_cap = pl.occ_cap[gi];
+          const OccTab *d_tabs = reinterpret_cast<const OccTab *>(tab + pl.off_occ[gi]);
           if (use_ff)
             run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, d_rptr + Kg, h, nsh, nsl,
-                          esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn);
+                          esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, false, d_tabs);
           else
             run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, nullptr, h, nsh, nsl,
-                             esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, split);
+                             esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, split, d_tabs);
         }
         if (export_E) continue;
         MergeArgs ma{};

@@ -484,7 +484,11 @@ __global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
   T vmax = s_mk<T>(-CUDART_INF_F, 0.f);
   for (int idx = threadIdx.x; idx < nS; idx += blockDim.x) {
     const int s1 = idx / a.S2, s2 = idx % a.S2;
-    const bool ok = row_ok && s1 >= inf.sa[1] && s1 <= inf.sb[1] && s2 >= inf.sa[2] && s2 <= inf.sb[2];
+    bool ok = row_ok && s1 >= inf.sa[1] && s1 <= inf.sb[1] && s2 >= inf.sa[2] && s2 <= inf.sb[2];
+    if (ok && a.clash) {  // a clashing translation has infinite energy (it stays counted in n)
+      const uint32_t w = a.clash[((long long)blockIdx.x * a.S1 + s1) * a.CW + (s2 >> 5)];
+      ok = !((w >> (s2 & 31)) & 1u);
+    }
     T x = s_mk<T>(-CUDART_INF_F, 0.f);
     if (ok) {
       const cx<T> z = res[(s1 >> 1) * ls + imod(inf.w0[2] + s2, P)];

@@ -78,6 +78,48 @@ struct XfusedArgs {        // x: forward ligand DFT, product with each receptor,
   const float4 *tw;
 };
 
+// ---- steric clashes (Eq. occupancy_grid) -----------------------------------
+// Receptor occupancy as bit rows along z with sparse-table dilations:
+// level v holds D_v(z) = OR_{t < 2^v} occ(z + t), bit (z + kOccZPad) of the
+// row, for z outside [0, N2) occ = 0.  Layout [v][X][w][Y] (u32 words w,
+// Y fastest).
+constexpr int kOccLevels = 6;
+constexpr int kOccZPad = 64;
+
+struct OccTab {            // one receptor's tables (tab null: no occupancy grid)
+  const uint32_t *tab;
+  int N0, N1, N2, W;
+};
+
+// One run of occupied ligand nodes along z in the ligand-box frame: nodes
+// (a, b, c0 .. c0 + len - 1), covered by the two level-lv windows at c0 and
+// c0 + dc (dc = len - 2^lv, 0 <= dc < 2^lv).
+struct OccRun {
+  short a, b, c0;
+  unsigned char dc, lv;
+};
+
+struct OccRunsArgs {
+  const float *coords;     // [atoms][3]
+  const float *R;          // [total_atoms] LJ size parameter (occupancy radius 2^(-1/6) R)
+  const ConfMeta *meta;    // [batch]
+  float h;
+  int cap;                 // runs per configuration
+  OccRun *runs;            // [batch][cap]
+  int *n_runs;             // [batch]
+};
+
+struct ClashArgs {
+  const OccRun *runs;      // [batch][cap]
+  const int *n_runs;       // [batch]
+  int cap;
+  const OccTab *tabs;      // [K]
+  const PairInfo *info;    // [batch][K]
+  int K, S0, S1, S2, CW;   // CW = 32-bit words per (s0, s1) row of flags
+  int T0, T1;              // translations (s0, s1) per CTA
+  uint32_t *clash;         // [batch][K][S0][S1][CW], bit s2: translation clashes
+};
+
 struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp partials
   const void *y2;          // [batch][K][S0][S1][F2] cx<T>
   int K, S0, S1, S2, F2;
@@ -86,6 +128,8 @@ struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp pa
   float escale_hi, escale_lo;   // 1 / (P0 P1 P2) (energy export)
   float4 *part;            // [batch][K][S0] {M_hi, M_lo, s, 0}
   double *export_E;        // optional [S0][S1][S2] energies (+inf masked), batch entry 0, receptor 0
+  const uint32_t *clash;   // optional [batch][K][S0][S1][CW] clash flags (excluded, +inf when exported)
+  int CW;
   FftPlan plan;
   const float4 *tw;
 };
@@ -109,7 +153,11 @@ struct MergeArgs {
                            // receptors, and -kT ln mean_k exp(-min_k / kT) (may be null)
 };
 
-// ---- launch wrappers (kernels.cu) --------------------------------------------
+// ---- launch wrappers (kernels.cu, occupancy.cu) -------------------------------
+cudaError_t launch_occ_table(const unsigned char *occ, int N0, int N1, int N2, int W, uint32_t *tab,
+                             cudaStream_t st);
+cudaError_t launch_occ_runs(const OccRunsArgs &a, int batch, cudaStream_t st);
+cudaError_t launch_clash(const ClashArgs &a, int batch, cudaStream_t st);
 cudaError_t launch_spread(const SpreadArgs &a, int batch, cudaStream_t st);
 template <class T> cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st);
 template <class T> cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st);

@@ -1,0 +1,309 @@
+// Steric clashes (Eq. occupancy_grid): a translation clashes when an occupied
+// node of the ligand occupancy grid lands on an occupied node of the receptor
+// occupancy grid, i.e. when the correlation of the two grids is positive.
+//
+// The grids are binary, so the correlation's sign is computed exactly with bit
+// operations instead of a fourth FFT channel:
+//   * the receptor grid becomes bit rows along z with sparse-table dilations
+//     D_v(z) = OR_{t < 2^v} occ(z + t) (k_occ_table, once per receptor);
+//   * each configuration's occupied ligand nodes become runs along z
+//     (k_occ_runs), every run being the OR of two level-v windows;
+//   * for 32 translations along z at once, a run hits when either window of
+//     the receptor row it lands on has a set bit: one funnel shift per window
+//     (k_clash).
+// Node occupancy of the ligand is decided in IEEE single precision, each
+// operation rounded in a fixed order (position, threshold, squared distance),
+// so that it is a function of the FP32 inputs alone.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "kernels.cuh"
+
+namespace bpmf {
+
+// 2^(-1/3): squared ratio of the occupancy radius 2^(-1/6) R to R
+#define OCC_R2_SCALE 0.79370052598409973737585281963615f
+
+// ---------------------------------------------------------------- receptor
+__global__ void k_occ_table(const unsigned char *occ, int N0, int N1, int N2, int W, uint32_t *tab) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N0 * N1) return;
+  const int X = (int)(t / N1), Y = (int)(t % N1);
+  const unsigned char *row = occ + ((long long)X * N1 + Y) * N2;
+  const long long lvs = (long long)N0 * W * N1;  // level stride
+  uint32_t *base = tab + (long long)X * W * N1 + Y;
+  // level 0: the bits themselves
+  for (int w = 0; w < W; ++w) {
+    uint32_t v = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int z = 32 * w + b - kOccZPad;
+      if (z >= 0 && z < N2 && row[z]) v |= 1u << b;
+    }
+    base[(long long)w * N1] = v;
+  }
+  // level v from level v-1: D_v(z) = D_{v-1}(z) | D_{v-1}(z + 2^(v-1))
+  for (int lv = 1; lv < kOccLevels; ++lv) {
+    const int sh = 1 << (lv - 1);
+    const uint32_t *src = base + (lv - 1) * lvs;
+    uint32_t *dst = base + lv * lvs;
+    uint32_t cur = src[0];
+    for (int w = 0; w < W; ++w) {
+      const uint32_t nxt = (w + 1 < W) ? src[(long long)(w + 1) * N1] : 0u;
+      dst[(long long)w * N1] = cur | __funnelshift_r(cur, nxt, sh);
+      cur = nxt;
+    }
+  }
+}
+
+cudaError_t launch_occ_table(const unsigned char *occ, int N0, int N1, int N2, int W, uint32_t *tab,
+                             cudaStream_t st) {
+  const long long n = (long long)N0 * N1;
+  if (n <= 0) return cudaSuccess;
+  k_occ_table<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(occ, N0, N1, N2, W, tab);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ ligand
+constexpr int kRowIntervals = 192;  // disjoint z intervals one row can hold (>= ceil(extent / 2))
+
+__device__ __forceinline__ bool node_occupied(float s2, float pz, float thr, int c) {
+  const float dz = __fsub_rn((float)c, pz);
+  return __fadd_rn(s2, __fmul_rn(dz, dz)) < thr;
+}
+
+// One CTA per configuration: atom positions in the ligand-box frame,
+// occupied-node intervals per (a, b) row, merged, split into runs of at most
+// 63 nodes, compacted in row order.
+__global__ void __launch_bounds__(256) k_occ_runs(OccRunsArgs a) {
+  __shared__ float s_p[3][256], s_thr[256];
+  __shared__ float s_red[4][8];
+  __shared__ int s_cnt[256];
+  __shared__ int s_base;
+  const ConfMeta m = a.meta[blockIdx.x];
+  const int n = m.n_atoms;
+  const int tid = threadIdx.x;
+  float pmin[3] = {CUDART_INF_F, CUDART_INF_F, CUDART_INF_F}, pmax[3] = {-CUDART_INF_F, -CUDART_INF_F,
+                                                                          -CUDART_INF_F};
+  float rmax = 0.f;
+  for (int i = tid; i < n; i += blockDim.x) {
+    const float *x = a.coords + 3ll * (m.atom_off + i);
+    for (int d = 0; d < 3; ++d) {
+      const float p = __fadd_rn(__fdiv_rn(__fsub_rn(x[d], m.lo[d]), a.h), 2.0f);
+      s_p[d][i] = p;
+      pmin[d] = fminf(pmin[d], p);
+      pmax[d] = fmaxf(pmax[d], p);
+    }
+    const float r = __fdiv_rn(a.R[m.gamma_off + i], a.h);
+    s_thr[i] = __fmul_rn(__fmul_rn(r, r), OCC_R2_SCALE);
+    rmax = fmaxf(rmax, fabsf(r));
+  }
+  // block reductions of the position range and the largest radius
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int d = 0; d < 3; ++d) {
+      pmin[d] = fminf(pmin[d], __shfl_xor_sync(0xffffffffu, pmin[d], o));
+      pmax[d] = fmaxf(pmax[d], __shfl_xor_sync(0xffffffffu, pmax[d], o));
+    }
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
+  if ((tid & 31) == 0) {
+    for (int d = 0; d < 3; ++d) {
+      s_red[d][tid >> 5] = pmin[d];
+    }
+    s_red[3][tid >> 5] = rmax;
+  }
+  __syncthreads();
+  float lo3[3], hi3[3], R0 = 0.f;
+  for (int d = 0; d < 3; ++d) lo3[d] = CUDART_INF_F;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    for (int d = 0; d < 3; ++d) lo3[d] = fminf(lo3[d], s_red[d][w]);
+    R0 = fmaxf(R0, s_red[3][w]);
+  }
+  __syncthreads();
+  if ((tid & 31) == 0)
+    for (int d = 0; d < 3; ++d) s_red[d][tid >> 5] = pmax[d];
+  __syncthreads();
+  for (int d = 0; d < 3; ++d) {
+    hi3[d] = -CUDART_INF_F;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) hi3[d] = fmaxf(hi3[d], s_red[d][w]);
+  }
+  int alo = (int)floorf(lo3[0] - R0) - 1, ahi = (int)ceilf(hi3[0] + R0) + 1;
+  int blo = (int)floorf(lo3[1] - R0) - 1, bhi = (int)ceilf(hi3[1] + R0) + 1;
+  // a row holds at most ceil(nC / 2) disjoint intervals; a longer z extent
+  // belongs to a box no receptor grid of at most 256 nodes admits (no valid
+  // translation), and such a configuration gets no runs
+  bool sane = n > 0 && R0 < 1e4f;
+  for (int d = 0; d < 3; ++d) sane = sane && fabsf(lo3[d]) < 1e6f && fabsf(hi3[d]) < 1e6f;
+  if (!sane) {
+    alo = blo = 0;
+    ahi = bhi = -1;
+  }
+  const int clo = sane ? (int)floorf(lo3[2] - R0) - 1 : 0, chi = sane ? (int)ceilf(hi3[2] + R0) + 1 : -1;
+  const int nC = chi - clo + 1;
+  const int nA = ahi - alo + 1, nB = bhi - blo + 1;
+  const long long rows = (nA > 0 && nB > 0 && nC <= 2 * kRowIntervals) ? (long long)nA * nB : 0;
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  OccRun *out = a.runs + (long long)blockIdx.x * a.cap;
+  short iv_lo[kRowIntervals], iv_hi[kRowIntervals];
+  for (long long r0 = 0; r0 < rows; r0 += blockDim.x) {
+    const long long row = r0 + tid;
+    int nI = 0;
+    int ra = 0, rb = 0;
+    if (row < rows) {
+      ra = alo + (int)(row / nB);
+      rb = blo + (int)(row % nB);
+      for (int i = 0; i < n; ++i) {
+        const float dx = __fsub_rn((float)ra, s_p[0][i]), dy = __fsub_rn((float)rb, s_p[1][i]);
+        const float s2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        const float thr = s_thr[i];
+        if (!(s2 < thr)) continue;
+        const float pz = s_p[2][i];
+        // the occupied nodes of one atom in a row form an interval around
+        // the node nearest p_z (the rounded squared distance is monotone in
+        // |c - p_z|)
+        const int cn = (int)rintf(pz);
+        if (!node_occupied(s2, pz, thr, cn)) continue;
+        int c0 = cn, c1 = cn;
+        while (c0 > clo && node_occupied(s2, pz, thr, c0 - 1)) --c0;
+        while (c1 < chi && node_occupied(s2, pz, thr, c1 + 1)) ++c1;
+        // insert [c0, c1] into the sorted list of disjoint intervals, merging
+        // overlapping or adjacent ones
+        int k = 0;
+        while (k < nI && iv_hi[k] < c0 - 1) ++k;
+        int e = k;
+        while (e < nI && iv_lo[e] <= c1 + 1) {
+          c0 = min(c0, (int)iv_lo[e]);
+          c1 = max(c1, (int)iv_hi[e]);
+          ++e;
+        }
+        const int removed = e - k;
+        if (removed == 0) {
+          if (nI < kRowIntervals) {
+            for (int t = nI; t > k; --t) {
+              iv_lo[t] = iv_lo[t - 1];
+              iv_hi[t] = iv_hi[t - 1];
+            }
+            ++nI;
+          }
+        } else if (removed > 1) {
+          for (int t = k + 1; t + removed - 1 < nI; ++t) {
+            iv_lo[t] = iv_lo[t + removed - 1];
+            iv_hi[t] = iv_hi[t + removed - 1];
+          }
+          nI -= removed - 1;
+        }
+        iv_lo[k] = (short)c0;
+        iv_hi[k] = (short)c1;
+      }
+    }
+    // runs of at most 63 nodes
+    int cnt = 0;
+    for (int k = 0; k < nI; ++k) cnt += (iv_hi[k] - iv_lo[k] + 63) / 63;
+    s_cnt[tid] = cnt;
+    __syncthreads();
+    if (tid == 0) {  // exclusive prefix in row order
+      int c = s_base;
+      for (int t = 0; t < (int)blockDim.x; ++t) {
+        const int v = s_cnt[t];
+        s_cnt[t] = c;
+        c += v;
+      }
+      s_base = c;
+    }
+    __syncthreads();
+    int o = s_cnt[tid];
+    for (int k = 0; k < nI; ++k) {
+      for (int c = iv_lo[k]; c <= iv_hi[k]; c += 63) {
+        const int len = min(63, iv_hi[k] - c + 1);
+        const int lv = min(5, 31 - __clz(len));
+        if (o < a.cap) {
+          OccRun rr;
+          rr.a = (short)ra;
+          rr.b = (short)rb;
+          rr.c0 = (short)c;
+          rr.dc = (unsigned char)(len - (1 << lv));
+          rr.lv = (unsigned char)lv;
+          out[o] = rr;
+        }
+        ++o;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) a.n_runs[blockIdx.x] = min(s_base, a.cap);
+}
+
+cudaError_t launch_occ_runs(const OccRunsArgs &a, int batch, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  k_occ_runs<<<batch, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- clash
+__device__ __forceinline__ uint32_t occ_word(const uint32_t *row, int w, int W, int N1) {
+  return (w >= 0 && w < W) ? __ldg(row + (long long)w * N1) : 0u;
+}
+
+// One CTA per (configuration, receptor, tile of T0 x T1 translations in
+// (s0, s1)); every thread owns one (s0, s1) and the flags of all s2 in
+// 64-translation groups (two 32-bit words).
+__global__ void __launch_bounds__(256) k_clash(ClashArgs a) {
+  const int n0 = (a.S0 + a.T0 - 1) / a.T0, n1 = (a.S1 + a.T1 - 1) / a.T1;
+  const int tile = blockIdx.x % (n0 * n1);
+  const int pair = blockIdx.x / (n0 * n1);  // j * K + k
+  const int j = pair / a.K, k = pair % a.K;
+  const int ty = threadIdx.x / a.T1, tx = threadIdx.x % a.T1;
+  const int s0 = (tile / n1) * a.T0 + ty, s1 = (tile % n1) * a.T1 + tx;
+  const bool active = ty < a.T0 && s0 < a.S0 && s1 < a.S1;
+  const OccTab t = a.tabs[k];
+  const PairInfo inf = a.info[pair];
+  const bool valid = active && t.tab && s0 >= inf.sa[0] && s0 <= inf.sb[0] && s1 >= inf.sa[1] && s1 <= inf.sb[1];
+  uint32_t *dst = a.clash + (((long long)pair * a.S0 + s0) * a.S1 + s1) * a.CW;
+  const int nr = a.n_runs[j];
+  const OccRun *runs = a.runs + (long long)j * a.cap;
+  const long long lvs = (long long)t.N0 * t.W * t.N1;
+  const int X0 = inf.w0[0] + s0, Y0 = inf.w0[1] + s1;
+  for (int g = 0; g < a.CW; g += 2) {
+    uint32_t acc0 = 0u, acc1 = 0u;
+    // flags beyond S2 are never read: a word is complete once every bit
+    // below S2 is set
+    const int nb0 = min(32, a.S2 - 32 * g), nb1 = min(32, a.S2 - 32 * (g + 1));
+    const uint32_t full0 = nb0 >= 32 ? 0xffffffffu : ((1u << nb0) - 1u);
+    const uint32_t full1 = nb1 <= 0 ? 0u : (nb1 >= 32 ? 0xffffffffu : ((1u << nb1) - 1u));
+    const int zb = inf.w0[2] + 64 * g + kOccZPad;
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+      const bool done = !valid || ((acc0 & full0) == full0 && (acc1 & full1) == full1);
+      if (__all_sync(0xffffffffu, done)) break;
+      const int r1 = min(nr, r0 + 32);
+      if (!valid) continue;
+      for (int r = r0; r < r1; ++r) {
+        const OccRun rr = runs[r];
+        const int X = X0 + rr.a, Y = Y0 + rr.b;
+        if (X < 0 || X >= t.N0 || Y < 0 || Y >= t.N1) continue;
+        const uint32_t *row = t.tab + rr.lv * lvs + (long long)X * t.W * t.N1 + Y;
+        const int bA = zb + rr.c0, bB = bA + rr.dc;
+        const int wA = bA >> 5, wB = bB >> 5;
+        const uint32_t l0 = occ_word(row, wA, t.W, t.N1), l1 = occ_word(row, wA + 1, t.W, t.N1),
+                       l2 = occ_word(row, wA + 2, t.W, t.N1), l3 = occ_word(row, wA + 3, t.W, t.N1);
+        const int shA = bA & 31, shB = bB & 31;
+        const bool nextB = wB != wA;  // wB is wA or wA + 1
+        const uint32_t m0 = nextB ? l1 : l0, m1 = nextB ? l2 : l1, m2 = nextB ? l3 : l2;
+        acc0 |= __funnelshift_r(l0, l1, shA) | __funnelshift_r(m0, m1, shB);
+        acc1 |= __funnelshift_r(l1, l2, shA) | __funnelshift_r(m1, m2, shB);
+      }
+    }
+    if (active) {
+      dst[g] = acc0;
+      if (g + 1 < a.CW) dst[g + 1] = acc1;
+    }
+  }
+}
+
+cudaError_t launch_clash(const ClashArgs &a, int batch, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  const long long tiles = (long long)((a.S0 + a.T0 - 1) / a.T0) * ((a.S1 + a.T1 - 1) / a.T1);
+  k_clash<<<(unsigned)(tiles * batch * a.K), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace bpmf

@@ -6,7 +6,8 @@ from __future__ import annotations
 import numpy as np
 
 from . import (BPMF_MODE_FF, bpmf_create, bpmf_destroy, bpmf_eval, bpmf_export_energies, bpmf_ligand_batch,
-               bpmf_ligand_free, bpmf_receptor_free, bpmf_receptor_load, bpmf_set_workspace_limit)
+               bpmf_ligand_free, bpmf_receptor_free, bpmf_receptor_load, bpmf_receptor_set_occupancy,
+               bpmf_set_workspace_limit)
 
 
 class Session:
@@ -27,6 +28,8 @@ class Session:
         h = bpmf_receptor_load(self.ctx, r.grids if grids is None else grids, r.h, r.origin, r.site_lo,
                                r.site_n, stream)
         self._recs.append(h)
+        if getattr(r, "occ", None) is not None:
+            bpmf_receptor_set_occupancy(self.ctx, h, r.occ, stream)
         return h
 
     def load_ligands(self, ligands, p_rep=12, p_att=6, coords=None, params=None, stream=None):
