@@ -361,7 +361,7 @@ size_t batch_bytes_per_conf(const BatchGeom &g, size_t E) {
   const size_t y2 = (size_t)g.K * g.S[0] * g.S[1] * g.F2 * E;
   size_t occ = 0;
   if (g.occ_cap > 0)
-    occ = align_up((size_t)g.occ_cap * sizeof(OccRun)) + align_up(sizeof(int)) +
+    occ = align_up(2 * (size_t)g.occ_cap * sizeof(OccRun)) + align_up(sizeof(int)) +
           align_up((size_t)g.K * g.S[0] * g.S[1] * clash_words(g.S[2]) * sizeof(uint32_t));
   return align_up(box) + align_up(lz) + align_up(ly) + align_up(x2) + align_up(y2) + occ;
 }
@@ -402,7 +402,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   const int CW = clash_words(g.S[2]);
   if (g.occ_cap > 0 && d_tabs) {
     OccRun *runs = reinterpret_cast<OccRun *>(p);
-    p += align_up((size_t)batch * g.occ_cap * sizeof(OccRun));
+    p += align_up(2 * (size_t)batch * g.occ_cap * sizeof(OccRun));
     int *n_runs = reinterpret_cast<int *>(p);
     p += align_up((size_t)batch * sizeof(int));
     clash = reinterpret_cast<uint32_t *>(p);
@@ -419,8 +419,6 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     ca.S1 = g.S[1];
     ca.S2 = g.S[2];
     ca.CW = CW;
-    ca.T1 = std::min(g.S[1], 256);
-    ca.T0 = std::max(1, std::min(g.S[0], 256 / ca.T1));
     ca.clash = clash;
     launch(c, "k_clash", st, [&] { return launch_clash(ca, batch, st); });
   }
@@ -1175,6 +1173,10 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         const float hf = (float)h;
         for (int i = 0; i < lg->n_atoms[li]; ++i)
           rmax = std::max(rmax, std::fabs(lg->R_host[lg->atom_off[li] + i] / hf));
+        if (g.S[2] > 256) {
+          last_msg = "site boxes above 256 translations along z with an occupancy grid";
+          throw Fail{BPMF_ERR_SIZE_UNSUPPORTED};
+        }
         if (!(rmax <= 60.f)) {
           last_msg = "occupancy radius above 60 grid spacings";
           throw Fail{BPMF_ERR_SIZE_UNSUPPORTED};

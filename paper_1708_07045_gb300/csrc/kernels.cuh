@@ -105,18 +105,18 @@ struct OccRunsArgs {
   const ConfMeta *meta;    // [batch]
   float h;
   int cap;                 // runs per configuration
-  OccRun *runs;            // [batch][cap]
+  OccRun *runs;            // [batch][2][cap]: row order, then sorted by level (longest first)
   int *n_runs;             // [batch]
 };
 
 struct ClashArgs {
-  const OccRun *runs;      // [batch][cap]
+  const OccRun *runs;      // [batch][2][cap] (k_occ_runs)
   const int *n_runs;       // [batch]
   int cap;
   const OccTab *tabs;      // [K]
   const PairInfo *info;    // [batch][K]
   int K, S0, S1, S2, CW;   // CW = 32-bit words per (s0, s1) row of flags
-  int T0, T1;              // translations (s0, s1) per CTA
+  int T0, T1;              // translations (s0, s1) per CTA (set by launch_clash)
   uint32_t *clash;         // [batch][K][S0][S1][CW], bit s2: translation clashes
 };
 
@@ -157,7 +157,7 @@ struct MergeArgs {
 cudaError_t launch_occ_table(const unsigned char *occ, int N0, int N1, int N2, int W, uint32_t *tab,
                              cudaStream_t st);
 cudaError_t launch_occ_runs(const OccRunsArgs &a, int batch, cudaStream_t st);
-cudaError_t launch_clash(const ClashArgs &a, int batch, cudaStream_t st);
+cudaError_t launch_clash(ClashArgs a, int batch, cudaStream_t st);
 cudaError_t launch_spread(const SpreadArgs &a, int batch, cudaStream_t st);
 template <class T> cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st);
 template <class T> cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st);

@@ -17,6 +17,9 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <algorithm>
+#include <cstdint>
+
 #include "kernels.cuh"
 
 namespace bpmf {
@@ -74,10 +77,10 @@ __device__ __forceinline__ bool node_occupied(float s2, float pz, float thr, int
 // One CTA per configuration: atom positions in the ligand-box frame,
 // occupied-node intervals per (a, b) row, merged, split into runs of at most
 // 63 nodes, compacted in row order.
-__global__ void __launch_bounds__(256) k_occ_runs(OccRunsArgs a) {
+__global__ void __launch_bounds__(512) k_occ_runs(OccRunsArgs a) {
   __shared__ float s_p[3][256], s_thr[256];
-  __shared__ float s_red[4][8];
-  __shared__ int s_cnt[256];
+  __shared__ float s_red[4][16];
+  __shared__ int s_cnt[16];
   __shared__ int s_base;
   const ConfMeta m = a.meta[blockIdx.x];
   const int n = m.n_atoms;
@@ -140,18 +143,21 @@ __global__ void __launch_bounds__(256) k_occ_runs(OccRunsArgs a) {
   const int clo = sane ? (int)floorf(lo3[2] - R0) - 1 : 0, chi = sane ? (int)ceilf(hi3[2] + R0) + 1 : -1;
   const int nC = chi - clo + 1;
   const int nA = ahi - alo + 1, nB = bhi - blo + 1;
-  const long long rows = (nA > 0 && nB > 0 && nC <= 2 * kRowIntervals) ? (long long)nA * nB : 0;
+  // (sane bounds keep nA, nB below 2e6 + 2e4; rows beyond 2^31 do not occur
+  // for boxes a receptor grid of at most 256 nodes admits)
+  const long long rows_ll = (nA > 0 && nB > 0 && nC <= 2 * kRowIntervals) ? (long long)nA * nB : 0;
+  const long long rows = rows_ll < (1ll << 30) ? rows_ll : 0;
   if (tid == 0) s_base = 0;
   __syncthreads();
-  OccRun *out = a.runs + (long long)blockIdx.x * a.cap;
+  OccRun *out = a.runs + (long long)blockIdx.x * 2 * a.cap;
   short iv_lo[kRowIntervals], iv_hi[kRowIntervals];
-  for (long long r0 = 0; r0 < rows; r0 += blockDim.x) {
-    const long long row = r0 + tid;
+  for (int r0 = 0; r0 < (int)rows; r0 += blockDim.x) {
+    const int row = r0 + tid;
     int nI = 0;
     int ra = 0, rb = 0;
-    if (row < rows) {
-      ra = alo + (int)(row / nB);
-      rb = blo + (int)(row % nB);
+    if (row < (int)rows) {
+      ra = alo + row / nB;
+      rb = blo + row % nB;
       for (int i = 0; i < n; ++i) {
         const float dx = __fsub_rn((float)ra, s_p[0][i]), dy = __fsub_rn((float)rb, s_p[1][i]);
         const float s2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
@@ -199,19 +205,20 @@ __global__ void __launch_bounds__(256) k_occ_runs(OccRunsArgs a) {
     // runs of at most 63 nodes
     int cnt = 0;
     for (int k = 0; k < nI; ++k) cnt += (iv_hi[k] - iv_lo[k] + 63) / 63;
-    s_cnt[tid] = cnt;
-    __syncthreads();
-    if (tid == 0) {  // exclusive prefix in row order
-      int c = s_base;
-      for (int t = 0; t < (int)blockDim.x; ++t) {
-        const int v = s_cnt[t];
-        s_cnt[t] = c;
-        c += v;
-      }
-      s_base = c;
+    // exclusive prefix in row order: within the warp by shuffles, then over
+    // the warp totals
+    const int lane = tid & 31, warp = tid >> 5;
+    int incl = cnt;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
     }
+    if (lane == 31) s_cnt[warp] = incl;
     __syncthreads();
-    int o = s_cnt[tid];
+    int o = s_base + incl - cnt;
+    for (int w = 0; w < warp; ++w) o += s_cnt[w];
+    __syncthreads();
+    if (tid == blockDim.x - 1) s_base = o + cnt;
     for (int k = 0; k < nI; ++k) {
       for (int c = iv_lo[k]; c <= iv_hi[k]; c += 63) {
         const int len = min(63, iv_hi[k] - c + 1);
@@ -230,12 +237,43 @@ __global__ void __launch_bounds__(256) k_occ_runs(OccRunsArgs a) {
     }
     __syncthreads();
   }
-  if (tid == 0) a.n_runs[blockIdx.x] = min(s_base, a.cap);
+  __syncthreads();
+  // stable partition by level, longest windows first, into the second half
+  // of the configuration's buffer: the clash test meets long runs (the ones
+  // likeliest to hit) first and walks neighbouring rows of one table
+  const int nr = min(s_base, a.cap);
+  OccRun *sorted = out + a.cap;
+  const int seg = (nr + blockDim.x - 1) / blockDim.x;
+  const int r_lo = min(nr, tid * seg), r_hi = min(nr, r_lo + seg);
+  int base = 0;
+  for (int lv = kOccLevels - 1; lv >= 0; --lv) {
+    int cnt = 0;
+    for (int r = r_lo; r < r_hi; ++r) cnt += out[r].lv == lv;
+    const int lane = tid & 31, warp = tid >> 5;
+    int incl = cnt;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    __syncthreads();
+    if (lane == 31) s_cnt[warp] = incl;
+    __syncthreads();
+    int o = base + incl - cnt;
+    int total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      if (w < warp) o += s_cnt[w];
+      total += s_cnt[w];
+    }
+    for (int r = r_lo; r < r_hi; ++r)
+      if (out[r].lv == lv) sorted[o++] = out[r];
+    base += total;
+  }
+  if (tid == 0) a.n_runs[blockIdx.x] = nr;
 }
 
 cudaError_t launch_occ_runs(const OccRunsArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  k_occ_runs<<<batch, 256, 0, st>>>(a);
+  k_occ_runs<<<batch, 512, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -246,61 +284,137 @@ __device__ __forceinline__ uint32_t occ_word(const uint32_t *row, int w, int W, 
 
 // One CTA per (configuration, receptor, tile of T0 x T1 translations in
 // (s0, s1)); every thread owns one (s0, s1) and the flags of all s2 in
-// 64-translation groups (two 32-bit words).
+// 64-translation groups (two 32-bit words).  Runs come level-sorted (see
+// k_occ_runs), so consecutive runs read neighbouring rows of one table (the
+// L1 serves them); a warp stops once every flag of its lanes is set.  Each
+// chunk of runs is first turned into table-word offsets and shift amounts
+// shared by the whole CTA; when every row and word the CTA can touch lies in
+// the table, the inner loop needs no bounds checks.
+constexpr int kClashChunk = 2048;
+
 __global__ void __launch_bounds__(256) k_clash(ClashArgs a) {
+  __shared__ uint2 s_ri[kClashChunk];  // {table-word offset, shA | shB << 5 | nextB << 10}
   const int n0 = (a.S0 + a.T0 - 1) / a.T0, n1 = (a.S1 + a.T1 - 1) / a.T1;
   const int tile = blockIdx.x % (n0 * n1);
   const int pair = blockIdx.x / (n0 * n1);  // j * K + k
   const int j = pair / a.K, k = pair % a.K;
   const int ty = threadIdx.x / a.T1, tx = threadIdx.x % a.T1;
-  const int s0 = (tile / n1) * a.T0 + ty, s1 = (tile % n1) * a.T1 + tx;
+  const int s0_t = (tile / n1) * a.T0, s1_t = (tile % n1) * a.T1;
+  const int s0 = s0_t + ty, s1 = s1_t + tx;
   const bool active = ty < a.T0 && s0 < a.S0 && s1 < a.S1;
   const OccTab t = a.tabs[k];
   const PairInfo inf = a.info[pair];
   const bool valid = active && t.tab && s0 >= inf.sa[0] && s0 <= inf.sb[0] && s1 >= inf.sa[1] && s1 <= inf.sb[1];
   uint32_t *dst = a.clash + (((long long)pair * a.S0 + s0) * a.S1 + s1) * a.CW;
-  const int nr = a.n_runs[j];
-  const OccRun *runs = a.runs + (long long)j * a.cap;
-  const long long lvs = (long long)t.N0 * t.W * t.N1;
-  const int X0 = inf.w0[0] + s0, Y0 = inf.w0[1] + s1;
-  for (int g = 0; g < a.CW; g += 2) {
-    uint32_t acc0 = 0u, acc1 = 0u;
-    // flags beyond S2 are never read: a word is complete once every bit
-    // below S2 is set
-    const int nb0 = min(32, a.S2 - 32 * g), nb1 = min(32, a.S2 - 32 * (g + 1));
-    const uint32_t full0 = nb0 >= 32 ? 0xffffffffu : ((1u << nb0) - 1u);
-    const uint32_t full1 = nb1 <= 0 ? 0u : (nb1 >= 32 ? 0xffffffffu : ((1u << nb1) - 1u));
-    const int zb = inf.w0[2] + 64 * g + kOccZPad;
-    for (int r0 = 0; r0 < nr; r0 += 32) {
-      const bool done = !valid || ((acc0 & full0) == full0 && (acc1 & full1) == full1);
-      if (__all_sync(0xffffffffu, done)) break;
-      const int r1 = min(nr, r0 + 32);
-      if (!valid) continue;
-      for (int r = r0; r < r1; ++r) {
-        const OccRun rr = runs[r];
-        const int X = X0 + rr.a, Y = Y0 + rr.b;
-        if (X < 0 || X >= t.N0 || Y < 0 || Y >= t.N1) continue;
-        const uint32_t *row = t.tab + rr.lv * lvs + (long long)X * t.W * t.N1 + Y;
-        const int bA = zb + rr.c0, bB = bA + rr.dc;
-        const int wA = bA >> 5, wB = bB >> 5;
-        const uint32_t l0 = occ_word(row, wA, t.W, t.N1), l1 = occ_word(row, wA + 1, t.W, t.N1),
-                       l2 = occ_word(row, wA + 2, t.W, t.N1), l3 = occ_word(row, wA + 3, t.W, t.N1);
-        const int shA = bA & 31, shB = bB & 31;
-        const bool nextB = wB != wA;  // wB is wA or wA + 1
-        const uint32_t m0 = nextB ? l1 : l0, m1 = nextB ? l2 : l1, m2 = nextB ? l3 : l2;
-        acc0 |= __funnelshift_r(l0, l1, shA) | __funnelshift_r(m0, m1, shB);
-        acc1 |= __funnelshift_r(l1, l2, shA) | __funnelshift_r(m1, m2, shB);
-      }
+  const int nr = t.tab ? a.n_runs[j] : 0;
+  const OccRun *runs = a.runs + (long long)j * 2 * a.cap + a.cap;  // level-sorted half
+  const int ys = t.N1, xs = t.W * t.N1, lvs = t.N0 * t.W * t.N1;  // < 2^31 words (N <= 256, W <= 12)
+  // translations the CTA evaluates (valid lanes only)
+  const int v0lo = max(s0_t, inf.sa[0]), v0hi = min(min(s0_t + a.T0, a.S0) - 1, inf.sb[0]);
+  const int v1lo = max(s1_t, inf.sa[1]), v1hi = min(min(s1_t + a.T1, a.S1) - 1, inf.sb[1]);
+  const int zb0 = inf.w0[2] + kOccZPad;
+  const int npairs = (a.CW + 1) / 2;
+  uint32_t acc[2][4];  // up to 8 flag words (S2 <= 256)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[0][q] = acc[1][q] = 0u;
+  const uint32_t *base = t.tab + (long long)(inf.w0[0] + (valid ? s0 : v0lo)) * xs + (inf.w0[1] + (valid ? s1 : v1lo));
+  for (int c0r = 0; c0r < nr && v0lo <= v0hi && v1lo <= v1hi; c0r += kClashChunk) {
+    const int nc = min(kClashChunk, nr - c0r);
+    __syncthreads();
+    int amin = 1 << 30, namax = 1 << 30, bmin = 1 << 30, nbmax = 1 << 30, wmin = 1 << 30, nwmax = 1 << 30;
+    for (int r = threadIdx.x; r < nc; r += blockDim.x) {
+      const OccRun rr = runs[c0r + r];
+      const int bA = zb0 + rr.c0, bB = bA + rr.dc;
+      const int wA = bA >> 5;
+      const int nextB = (bB >> 5) != wA;
+      s_ri[r] = make_uint2((unsigned)(rr.lv * lvs + rr.a * xs + rr.b + wA * ys),
+                           (unsigned)((bA & 31) | ((bB & 31) << 5) | (nextB << 10)));
+      amin = min(amin, (int)rr.a);
+      namax = min(namax, -(int)rr.a);
+      bmin = min(bmin, (int)rr.b);
+      nbmax = min(nbmax, -(int)rr.b);
+      wmin = min(wmin, wA);
+      nwmax = min(nwmax, -wA);
     }
-    if (active) {
-      dst[g] = acc0;
-      if (g + 1 < a.CW) dst[g + 1] = acc1;
+    // CTA-wide extremes (six minima over the warps)
+    int v[6] = {amin, namax, bmin, nbmax, wmin, nwmax};
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      for (int o = 16; o > 0; o >>= 1) v[q] = min(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+    __shared__ int s_v[6][8];
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) s_v[q][threadIdx.x >> 5] = v[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      v[q] = s_v[q][0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v[q] = min(v[q], s_v[q][w]);
+    }
+    // every row and word in the table: no checks in the loop
+    const bool fast = inf.w0[0] + v0lo + v[0] >= 0 && inf.w0[0] + v0hi - v[1] < t.N0 &&
+                      inf.w0[1] + v1lo + v[2] >= 0 && inf.w0[1] + v1hi - v[3] < t.N1 && v[4] >= 0 &&
+                      -v[5] + 2 * (npairs - 1) + 3 < t.W;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (g >= npairs) break;
+      uint32_t a0 = acc[0][g], a1 = acc[1][g];
+      const int nb0 = min(32, a.S2 - 64 * g), nb1 = min(32, a.S2 - 64 * g - 32);
+      const uint32_t full0 = nb0 >= 32 ? 0xffffffffu : ((1u << nb0) - 1u);
+      const uint32_t full1 = nb1 <= 0 ? 0u : (nb1 >= 32 ? 0xffffffffu : ((1u << nb1) - 1u));
+      const int gofs = 2 * g * ys;
+      for (int r0 = 0; r0 < nc; r0 += 16) {
+        const bool done = !valid || ((a0 & full0) == full0 && (a1 & full1) == full1);
+        if (__all_sync(0xffffffffu, done)) break;
+        const int r1 = min(nc, r0 + 16);
+        if (fast) {
+          if (valid)
+            for (int r = r0; r < r1; ++r) {
+              const uint2 ri = s_ri[r];
+              const uint32_t *p = base + (int)ri.x + gofs;
+              const int shA = ri.y & 31, shB = (ri.y >> 5) & 31;
+              const bool nextB = (ri.y >> 10) & 1;
+              const uint32_t l0 = __ldg(p), l1 = __ldg(p + ys), l2 = __ldg(p + 2 * ys);
+              const uint32_t l3 = nextB ? __ldg(p + 3 * ys) : 0u;
+              const uint32_t m0 = nextB ? l1 : l0, m1 = nextB ? l2 : l1, m2 = nextB ? l3 : l2;
+              a0 |= __funnelshift_r(l0, l1, shA) | __funnelshift_r(m0, m1, shB);
+              a1 |= __funnelshift_r(l1, l2, shA) | __funnelshift_r(m1, m2, shB);
+            }
+        } else if (valid) {
+          for (int r = r0; r < r1; ++r) {
+            const OccRun rr = runs[c0r + r];
+            const int X = inf.w0[0] + s0 + rr.a, Y = inf.w0[1] + s1 + rr.b;
+            if (X < 0 || X >= t.N0 || Y < 0 || Y >= t.N1) continue;
+            const uint32_t *row = t.tab + (long long)rr.lv * lvs + (long long)X * xs + Y;
+            const int bA = zb0 + 64 * g + rr.c0, bB = bA + rr.dc;
+            const int wA = bA >> 5, shA = bA & 31, shB = bB & 31;
+            const bool nextB = (bB >> 5) != wA;
+            const uint32_t l0 = occ_word(row, wA, t.W, t.N1), l1 = occ_word(row, wA + 1, t.W, t.N1),
+                           l2 = occ_word(row, wA + 2, t.W, t.N1);
+            const uint32_t l3 = nextB ? occ_word(row, wA + 3, t.W, t.N1) : 0u;
+            const uint32_t m0 = nextB ? l1 : l0, m1 = nextB ? l2 : l1, m2 = nextB ? l3 : l2;
+            a0 |= __funnelshift_r(l0, l1, shA) | __funnelshift_r(m0, m1, shB);
+            a1 |= __funnelshift_r(l1, l2, shA) | __funnelshift_r(m1, m2, shB);
+          }
+        }
+      }
+      acc[0][g] = a0;
+      acc[1][g] = a1;
     }
   }
+  if (active)
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (2 * g < a.CW) dst[2 * g] = acc[0][g];
+      if (2 * g + 1 < a.CW) dst[2 * g + 1] = acc[1][g];
+    }
 }
 
-cudaError_t launch_clash(const ClashArgs &a, int batch, cudaStream_t st) {
+cudaError_t launch_clash(ClashArgs a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
+  if (a.CW > 8) return cudaErrorInvalidValue;  // flags of at most 256 translations along z per thread
+  a.T1 = std::min(a.S1, 256);
+  a.T0 = std::max(1, std::min(a.S0, 256 / a.T1));
   const long long tiles = (long long)((a.S0 + a.T0 - 1) / a.T0) * ((a.S1 + a.T1 - 1) / a.T1);
   k_clash<<<(unsigned)(tiles * batch * a.K), 256, 0, st>>>(a);
   return cudaGetLastError();
