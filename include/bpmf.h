@@ -133,7 +133,8 @@ void bpmf_receptor_free(bpmf_rec_t rec);
  * bpmf_ligand_batch, each step rounded to IEEE single precision in the order
  * p = (x - min x) / h + 2, r = R / h, threshold = (r r) 2^(-1/3),
  * distance = ((dx dx + dy dy) + dz dz).  The library copies the grid into
- * bit tables (about 6 (nx (nz + 64) / 8 + 8) ny bytes of device memory).
+ * bit tables (32 run-length dilations with 16 zero rows on each side of x
+ * and y: about 32 (nx + 32)(ny + 32)(nz + 128) / 8 bytes of device memory).
  * Synchronises `stream`.  Errors: INVALID_ARG, OOM, CUDA; bpmf_eval returns
  * SIZE_UNSUPPORTED when an occupancy radius exceeds 60 grid spacings.
  */

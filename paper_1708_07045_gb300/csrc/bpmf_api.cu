@@ -67,7 +67,7 @@ struct bpmf_rec {
   double origin[3] = {0, 0, 0};
   int site_lo[3] = {0, 0, 0}, site_n[3] = {0, 0, 0};
   float2 *hi = nullptr, *lo = nullptr;  // [3][P0][Q]
-  uint32_t *occ = nullptr;              // occupancy sparse tables [kOccLevels][N0][occW][N1], or null
+  uint32_t *occ = nullptr;              // occupancy tables [kOccLevels][N0 + 32][occW][N1 + 32], or null
   int occW = 0;
 };
 
@@ -850,7 +850,7 @@ int bpmf_receptor_set_occupancy(bpmf_ctx_t c, bpmf_rec_t r, const uint8_t *occ, 
     last_msg.clear();
     if (occ) {
       const int W = (r->N[2] + kOccZPad + 31) / 32 + 2;
-      const size_t words = (size_t)kOccLevels * r->N[0] * W * r->N[1];
+      const size_t words = (size_t)kOccLevels * (r->N[0] + 2 * kOccXYPad) * W * (r->N[1] + 2 * kOccXYPad);
       DevIn o(occ, (size_t)r->N[0] * r->N[1] * r->N[2], st);
       CK(cudaMalloc(&tab, words * sizeof(uint32_t)));
       launch(c, "k_occ_table", st, [&] {

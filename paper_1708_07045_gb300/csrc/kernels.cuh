@@ -79,24 +79,25 @@ struct XfusedArgs {        // x: forward ligand DFT, product with each receptor,
 };
 
 // ---- steric clashes (Eq. occupancy_grid) -----------------------------------
-// Receptor occupancy as bit rows along z with sparse-table dilations:
-// level v holds D_v(z) = OR_{t < 2^v} occ(z + t), bit (z + kOccZPad) of the
-// row, for z outside [0, N2) occ = 0.  Layout [v][X][w][Y] (u32 words w,
-// Y fastest).
-constexpr int kOccLevels = 6;
+// Receptor occupancy as bit rows along z with one dilation per run length:
+// level v holds D_v(z) = OR_{t <= v} occ(z + t) (runs of v + 1 nodes), bit
+// (z + kOccZPad) of the row, for z outside [0, N2) occ = 0.  Layout
+// [v][X + kOccXYPad][w][Y + kOccXYPad] (u32 words w, Y fastest), with
+// kOccXYPad zero rows on both sides of x and y.
+constexpr int kOccLevels = 32;
 constexpr int kOccZPad = 64;
+constexpr int kOccXYPad = 16;
 
 struct OccTab {            // one receptor's tables (tab null: no occupancy grid)
   const uint32_t *tab;
-  int N0, N1, N2, W;
+  int N0, N1, N2, W;       // grid edges and words per row (padded rows: N + 2 kOccXYPad)
 };
 
 // One run of occupied ligand nodes along z in the ligand-box frame: nodes
-// (a, b, c0 .. c0 + len - 1), covered by the two level-lv windows at c0 and
-// c0 + dc (dc = len - 2^lv, 0 <= dc < 2^lv).
+// (a, b, c0 .. c0 + lv), read as the single level-lv window at c0.
 struct OccRun {
   short a, b, c0;
-  unsigned char dc, lv;
+  unsigned char dc, lv;    // dc unused (0)
 };
 
 struct OccRunsArgs {
@@ -105,7 +106,7 @@ struct OccRunsArgs {
   const ConfMeta *meta;    // [batch]
   float h;
   int cap;                 // runs per configuration
-  OccRun *runs;            // [batch][2][cap]: row order, then sorted by level (longest first)
+  OccRun *runs;            // [batch][2][cap]: row order, then sorted by length (longest first)
   int *n_runs;             // [batch]
 };
 

@@ -4,13 +4,13 @@
 //
 // The grids are binary, so the correlation's sign is computed exactly with bit
 // operations instead of a fourth FFT channel:
-//   * the receptor grid becomes bit rows along z with sparse-table dilations
-//     D_v(z) = OR_{t < 2^v} occ(z + t) (k_occ_table, once per receptor);
-//   * each configuration's occupied ligand nodes become runs along z
-//     (k_occ_runs), every run being the OR of two level-v windows;
-//   * for 32 translations along z at once, a run hits when either window of
-//     the receptor row it lands on has a set bit: one funnel shift per window
-//     (k_clash).
+//   * the receptor grid becomes bit rows along z with one dilation per run
+//     length, D_v(z) = OR_{t <= v} occ(z + t), v < 32 (k_occ_table, once per
+//     receptor);
+//   * each configuration's occupied ligand nodes become runs of at most 32
+//     nodes along z (k_occ_runs);
+//   * for 32 translations along z at once, a run of length v + 1 hits where
+//     the level-v row it lands on has a set bit: one funnel shift (k_clash).
 // Node occupancy of the ligand is decided in IEEE single precision, each
 // operation rounded in a fixed order (position, threshold, squared distance),
 // so that it is a function of the FP32 inputs alone.
@@ -32,9 +32,10 @@ __global__ void k_occ_table(const unsigned char *occ, int N0, int N1, int N2, in
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)N0 * N1) return;
   const int X = (int)(t / N1), Y = (int)(t % N1);
+  const int Q0 = N0 + 2 * kOccXYPad, Q1 = N1 + 2 * kOccXYPad;
   const unsigned char *row = occ + ((long long)X * N1 + Y) * N2;
-  const long long lvs = (long long)N0 * W * N1;  // level stride
-  uint32_t *base = tab + (long long)X * W * N1 + Y;
+  const long long lvs = (long long)Q0 * W * Q1;  // level stride
+  uint32_t *base = tab + (long long)(X + kOccXYPad) * W * Q1 + (Y + kOccXYPad);
   // level 0: the bits themselves
   for (int w = 0; w < W; ++w) {
     uint32_t v = 0;
@@ -42,18 +43,16 @@ __global__ void k_occ_table(const unsigned char *occ, int N0, int N1, int N2, in
       const int z = 32 * w + b - kOccZPad;
       if (z >= 0 && z < N2 && row[z]) v |= 1u << b;
     }
-    base[(long long)w * N1] = v;
+    base[(long long)w * Q1] = v;
   }
-  // level v from level v-1: D_v(z) = D_{v-1}(z) | D_{v-1}(z + 2^(v-1))
+  // level v from level v-1: D_v(z) = D_{v-1}(z) | occ(z + v)
+  const uint32_t *raw = base;
   for (int lv = 1; lv < kOccLevels; ++lv) {
-    const int sh = 1 << (lv - 1);
     const uint32_t *src = base + (lv - 1) * lvs;
     uint32_t *dst = base + lv * lvs;
-    uint32_t cur = src[0];
     for (int w = 0; w < W; ++w) {
-      const uint32_t nxt = (w + 1 < W) ? src[(long long)(w + 1) * N1] : 0u;
-      dst[(long long)w * N1] = cur | __funnelshift_r(cur, nxt, sh);
-      cur = nxt;
+      const uint32_t r0 = raw[(long long)w * Q1], r1 = (w + 1 < W) ? raw[(long long)(w + 1) * Q1] : 0u;
+      dst[(long long)w * Q1] = src[(long long)w * Q1] | __funnelshift_r(r0, r1, lv);
     }
   }
 }
@@ -62,6 +61,9 @@ cudaError_t launch_occ_table(const unsigned char *occ, int N0, int N1, int N2, i
                              cudaStream_t st) {
   const long long n = (long long)N0 * N1;
   if (n <= 0) return cudaSuccess;
+  const size_t words = (size_t)kOccLevels * (N0 + 2 * kOccXYPad) * W * (N1 + 2 * kOccXYPad);
+  cudaError_t e = cudaMemsetAsync(tab, 0, words * sizeof(uint32_t), st);  // zero margins
+  if (e != cudaSuccess) return e;
   k_occ_table<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(occ, N0, N1, N2, W, tab);
   return cudaGetLastError();
 }
@@ -76,7 +78,7 @@ __device__ __forceinline__ bool node_occupied(float s2, float pz, float thr, int
 
 // One CTA per configuration: atom positions in the ligand-box frame,
 // occupied-node intervals per (a, b) row, merged, split into runs of at most
-// 63 nodes, compacted in row order.
+// 32 nodes, compacted in row order, then ordered by length.
 __global__ void __launch_bounds__(512) k_occ_runs(OccRunsArgs a) {
   __shared__ float s_p[3][256], s_thr[256];
   __shared__ float s_red[4][16];
@@ -202,9 +204,9 @@ __global__ void __launch_bounds__(512) k_occ_runs(OccRunsArgs a) {
         iv_hi[k] = (short)c1;
       }
     }
-    // runs of at most 63 nodes
+    // runs of at most 32 nodes
     int cnt = 0;
-    for (int k = 0; k < nI; ++k) cnt += (iv_hi[k] - iv_lo[k] + 63) / 63;
+    for (int k = 0; k < nI; ++k) cnt += (iv_hi[k] - iv_lo[k] + kOccLevels) / kOccLevels;
     // exclusive prefix in row order: within the warp by shuffles, then over
     // the warp totals
     const int lane = tid & 31, warp = tid >> 5;
@@ -220,16 +222,15 @@ __global__ void __launch_bounds__(512) k_occ_runs(OccRunsArgs a) {
     __syncthreads();
     if (tid == blockDim.x - 1) s_base = o + cnt;
     for (int k = 0; k < nI; ++k) {
-      for (int c = iv_lo[k]; c <= iv_hi[k]; c += 63) {
-        const int len = min(63, iv_hi[k] - c + 1);
-        const int lv = min(5, 31 - __clz(len));
+      for (int c = iv_lo[k]; c <= iv_hi[k]; c += kOccLevels) {
+        const int len = min(kOccLevels, iv_hi[k] - c + 1);
         if (o < a.cap) {
           OccRun rr;
           rr.a = (short)ra;
           rr.b = (short)rb;
           rr.c0 = (short)c;
-          rr.dc = (unsigned char)(len - (1 << lv));
-          rr.lv = (unsigned char)lv;
+          rr.dc = 0;
+          rr.lv = (unsigned char)(len - 1);
           out[o] = rr;
         }
         ++o;
@@ -238,35 +239,45 @@ __global__ void __launch_bounds__(512) k_occ_runs(OccRunsArgs a) {
     __syncthreads();
   }
   __syncthreads();
-  // stable partition by level, longest windows first, into the second half
-  // of the configuration's buffer: the clash test meets long runs (the ones
-  // likeliest to hit) first and walks neighbouring rows of one table
+  // stable partition by length, longest first, into the second half of the
+  // configuration's buffer: the clash test meets long runs (the ones likeliest
+  // to hit) first and walks neighbouring rows of one table
   const int nr = min(s_base, a.cap);
   OccRun *sorted = out + a.cap;
-  const int seg = (nr + blockDim.x - 1) / blockDim.x;
-  const int r_lo = min(nr, tid * seg), r_hi = min(nr, r_lo + seg);
-  int base = 0;
-  for (int lv = kOccLevels - 1; lv >= 0; --lv) {
-    int cnt = 0;
-    for (int r = r_lo; r < r_hi; ++r) cnt += out[r].lv == lv;
-    const int lane = tid & 31, warp = tid >> 5;
-    int incl = cnt;
-    for (int d = 1; d < 32; d <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += v;
+  // warp w owns lengths lv = w, w + 16 (512 threads): count them with
+  // ballots over the run list, then write each length's runs in order
+  __shared__ int s_len[kOccLevels + 1];
+  {
+    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int lv = warp; lv < kOccLevels; lv += nw) {
+      int c = 0;
+      for (int r0 = 0; r0 < nr; r0 += 32) {
+        const int r = r0 + lane;
+        c += __popc(__ballot_sync(0xffffffffu, r < nr && out[r].lv == lv));
+      }
+      if (lane == 0) s_len[lv] = c;
     }
     __syncthreads();
-    if (lane == 31) s_cnt[warp] = incl;
-    __syncthreads();
-    int o = base + incl - cnt;
-    int total = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      if (w < warp) o += s_cnt[w];
-      total += s_cnt[w];
+    if (tid == 0) {  // longest first
+      int c = 0;
+      for (int lv = kOccLevels - 1; lv >= 0; --lv) {
+        const int n = s_len[lv];
+        s_len[lv] = c;
+        c += n;
+      }
     }
-    for (int r = r_lo; r < r_hi; ++r)
-      if (out[r].lv == lv) sorted[o++] = out[r];
-    base += total;
+    __syncthreads();
+    for (int lv = warp; lv < kOccLevels; lv += nw) {
+      int o = s_len[lv];
+      for (int r0 = 0; r0 < nr; r0 += 32) {
+        const int r = r0 + lane;
+        OccRun rr;
+        const bool m = r < nr && (rr = out[r]).lv == lv;
+        const unsigned bal = __ballot_sync(0xffffffffu, m);
+        if (m) sorted[o + __popc(bal & ((1u << lane) - 1u))] = rr;
+        o += __popc(bal);
+      }
+    }
   }
   if (tid == 0) a.n_runs[blockIdx.x] = nr;
 }
@@ -284,7 +295,7 @@ __device__ __forceinline__ uint32_t occ_word(const uint32_t *row, int w, int W, 
 
 // One CTA per (configuration, receptor, tile of T0 x T1 translations in
 // (s0, s1)); every thread owns one (s0, s1) and the flags of all s2 in
-// 64-translation groups (two 32-bit words).  Runs come level-sorted (see
+// 64-translation groups (two 32-bit words).  Runs come sorted by length (see
 // k_occ_runs), so consecutive runs read neighbouring rows of one table (the
 // L1 serves them); a warp stops once every flag of its lanes is set.  Each
 // chunk of runs is first turned into table-word offsets and shift amounts
@@ -293,7 +304,7 @@ __device__ __forceinline__ uint32_t occ_word(const uint32_t *row, int w, int W, 
 constexpr int kClashChunk = 2048;
 
 __global__ void __launch_bounds__(256) k_clash(ClashArgs a) {
-  __shared__ uint2 s_ri[kClashChunk];  // {table-word offset, shA | shB << 5 | nextB << 10}
+  __shared__ uint2 s_ri[kClashChunk];  // {table-word offset, bit shift}
   const int n0 = (a.S0 + a.T0 - 1) / a.T0, n1 = (a.S1 + a.T1 - 1) / a.T1;
   const int tile = blockIdx.x % (n0 * n1);
   const int pair = blockIdx.x / (n0 * n1);  // j * K + k
@@ -308,7 +319,7 @@ __global__ void __launch_bounds__(256) k_clash(ClashArgs a) {
   uint32_t *dst = a.clash + (((long long)pair * a.S0 + s0) * a.S1 + s1) * a.CW;
   const int nr = t.tab ? a.n_runs[j] : 0;
   const OccRun *runs = a.runs + (long long)j * 2 * a.cap + a.cap;  // level-sorted half
-  const int ys = t.N1, xs = t.W * t.N1, lvs = t.N0 * t.W * t.N1;  // < 2^31 words (N <= 256, W <= 12)
+  const int ys = t.N1 + 2 * kOccXYPad, xs = t.W * ys, lvs = (t.N0 + 2 * kOccXYPad) * xs;  // < 2^31 words
   // translations the CTA evaluates (valid lanes only)
   const int v0lo = max(s0_t, inf.sa[0]), v0hi = min(min(s0_t + a.T0, a.S0) - 1, inf.sb[0]);
   const int v1lo = max(s1_t, inf.sa[1]), v1hi = min(min(s1_t + a.T1, a.S1) - 1, inf.sb[1]);
@@ -317,18 +328,17 @@ __global__ void __launch_bounds__(256) k_clash(ClashArgs a) {
   uint32_t acc[2][4];  // up to 8 flag words (S2 <= 256)
 #pragma unroll
   for (int q = 0; q < 4; ++q) acc[0][q] = acc[1][q] = 0u;
-  const uint32_t *base = t.tab + (long long)(inf.w0[0] + (valid ? s0 : v0lo)) * xs + (inf.w0[1] + (valid ? s1 : v1lo));
+  const uint32_t *base = t.tab + (long long)(inf.w0[0] + (valid ? s0 : v0lo) + kOccXYPad) * xs +
+                         (inf.w0[1] + (valid ? s1 : v1lo) + kOccXYPad);
   for (int c0r = 0; c0r < nr && v0lo <= v0hi && v1lo <= v1hi; c0r += kClashChunk) {
     const int nc = min(kClashChunk, nr - c0r);
     __syncthreads();
     int amin = 1 << 30, namax = 1 << 30, bmin = 1 << 30, nbmax = 1 << 30, wmin = 1 << 30, nwmax = 1 << 30;
     for (int r = threadIdx.x; r < nc; r += blockDim.x) {
       const OccRun rr = runs[c0r + r];
-      const int bA = zb0 + rr.c0, bB = bA + rr.dc;
+      const int bA = zb0 + rr.c0;
       const int wA = bA >> 5;
-      const int nextB = (bB >> 5) != wA;
-      s_ri[r] = make_uint2((unsigned)(rr.lv * lvs + rr.a * xs + rr.b + wA * ys),
-                           (unsigned)((bA & 31) | ((bB & 31) << 5) | (nextB << 10)));
+      s_ri[r] = make_uint2((unsigned)(rr.lv * lvs + rr.a * xs + rr.b + wA * ys), (unsigned)(bA & 31));
       amin = min(amin, (int)rr.a);
       namax = min(namax, -(int)rr.a);
       bmin = min(bmin, (int)rr.b);
@@ -352,9 +362,9 @@ __global__ void __launch_bounds__(256) k_clash(ClashArgs a) {
       for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v[q] = min(v[q], s_v[q][w]);
     }
     // every row and word in the table: no checks in the loop
-    const bool fast = inf.w0[0] + v0lo + v[0] >= 0 && inf.w0[0] + v0hi - v[1] < t.N0 &&
-                      inf.w0[1] + v1lo + v[2] >= 0 && inf.w0[1] + v1hi - v[3] < t.N1 && v[4] >= 0 &&
-                      -v[5] + 2 * (npairs - 1) + 3 < t.W;
+    const bool fast = inf.w0[0] + v0lo + v[0] >= -kOccXYPad && inf.w0[0] + v0hi - v[1] < t.N0 + kOccXYPad &&
+                      inf.w0[1] + v1lo + v[2] >= -kOccXYPad && inf.w0[1] + v1hi - v[3] < t.N1 + kOccXYPad &&
+                      v[4] >= 0 && -v[5] + 2 * (npairs - 1) + 2 < t.W;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       if (g >= npairs) break;
@@ -368,33 +378,47 @@ __global__ void __launch_bounds__(256) k_clash(ClashArgs a) {
         if (__all_sync(0xffffffffu, done)) break;
         const int r1 = min(nc, r0 + 16);
         if (fast) {
-          if (valid)
-            for (int r = r0; r < r1; ++r) {
-              const uint2 ri = s_ri[r];
-              const uint32_t *p = base + (int)ri.x + gofs;
-              const int shA = ri.y & 31, shB = (ri.y >> 5) & 31;
-              const bool nextB = (ri.y >> 10) & 1;
-              const uint32_t l0 = __ldg(p), l1 = __ldg(p + ys), l2 = __ldg(p + 2 * ys);
-              const uint32_t l3 = nextB ? __ldg(p + 3 * ys) : 0u;
-              const uint32_t m0 = nextB ? l1 : l0, m1 = nextB ? l2 : l1, m2 = nextB ? l3 : l2;
-              a0 |= __funnelshift_r(l0, l1, shA) | __funnelshift_r(m0, m1, shB);
-              a1 |= __funnelshift_r(l1, l2, shA) | __funnelshift_r(m1, m2, shB);
+          if (valid) {
+            const uint32_t *bg = base + gofs;
+            int r = r0;
+            for (; r + 4 <= r1; r += 4) {  // four runs' loads in flight
+              uint2 ri[4];
+              uint32_t l[4][3];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) ri[q] = s_ri[r + q];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const uint32_t *p = bg + (int)ri[q].x;
+                l[q][0] = __ldg(p);
+                l[q][1] = __ldg(p + ys);
+                l[q][2] = __ldg(p + 2 * ys);
+              }
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                a0 |= __funnelshift_r(l[q][0], l[q][1], ri[q].y);
+                a1 |= __funnelshift_r(l[q][1], l[q][2], ri[q].y);
+              }
             }
+            for (; r < r1; ++r) {
+              const uint2 ri = s_ri[r];
+              const uint32_t *p = bg + (int)ri.x;
+              const uint32_t l0 = __ldg(p), l1 = __ldg(p + ys), l2 = __ldg(p + 2 * ys);
+              a0 |= __funnelshift_r(l0, l1, ri.y);
+              a1 |= __funnelshift_r(l1, l2, ri.y);
+            }
+          }
         } else if (valid) {
           for (int r = r0; r < r1; ++r) {
             const OccRun rr = runs[c0r + r];
             const int X = inf.w0[0] + s0 + rr.a, Y = inf.w0[1] + s1 + rr.b;
             if (X < 0 || X >= t.N0 || Y < 0 || Y >= t.N1) continue;
-            const uint32_t *row = t.tab + (long long)rr.lv * lvs + (long long)X * xs + Y;
-            const int bA = zb0 + 64 * g + rr.c0, bB = bA + rr.dc;
-            const int wA = bA >> 5, shA = bA & 31, shB = bB & 31;
-            const bool nextB = (bB >> 5) != wA;
-            const uint32_t l0 = occ_word(row, wA, t.W, t.N1), l1 = occ_word(row, wA + 1, t.W, t.N1),
-                           l2 = occ_word(row, wA + 2, t.W, t.N1);
-            const uint32_t l3 = nextB ? occ_word(row, wA + 3, t.W, t.N1) : 0u;
-            const uint32_t m0 = nextB ? l1 : l0, m1 = nextB ? l2 : l1, m2 = nextB ? l3 : l2;
-            a0 |= __funnelshift_r(l0, l1, shA) | __funnelshift_r(m0, m1, shB);
-            a1 |= __funnelshift_r(l1, l2, shA) | __funnelshift_r(m1, m2, shB);
+            const uint32_t *row = t.tab + (long long)rr.lv * lvs + (long long)(X + kOccXYPad) * xs + (Y + kOccXYPad);
+            const int bA = zb0 + 64 * g + rr.c0;
+            const int wA = bA >> 5, shA = bA & 31;
+            const uint32_t l0 = occ_word(row, wA, t.W, ys), l1 = occ_word(row, wA + 1, t.W, ys),
+                           l2 = occ_word(row, wA + 2, t.W, ys);
+            a0 |= __funnelshift_r(l0, l1, shA);
+            a1 |= __funnelshift_r(l1, l2, shA);
           }
         }
       }
