@@ -349,6 +349,7 @@ struct BatchGeom {
   int S[3];
   int K;
   int occ_cap = 0;  // ligand occupancy runs per configuration (0: no clash channel)
+  int occ_rb = 1;   // CTAs per configuration building the runs
 };
 
 int clash_words(int S2) { return (S2 + 31) / 32; }
@@ -406,7 +407,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     int *n_runs = reinterpret_cast<int *>(p);
     p += align_up((size_t)batch * sizeof(int));
     clash = reinterpret_cast<uint32_t *>(p);
-    OccRunsArgs ra{lg->coords, lg->R, d_meta, (float)h, g.occ_cap, runs, n_runs};
+    OccRunsArgs ra{lg->coords, lg->R, d_meta, (float)h, g.occ_cap, runs, n_runs, g.occ_rb};
     launch(c, "k_occ_runs", st, [&] { return launch_occ_runs(ra, batch, st); });
     ClashArgs ca{};
     ca.runs = runs;
@@ -1035,6 +1036,7 @@ struct LigPlan {
   std::vector<size_t> off_kmap, off_rptr;           // per group
   std::vector<size_t> off_occ;                      // per group: [Kg] OccTab (unused when occ_cap is 0)
   std::vector<int> occ_cap;                         // per group: runs per configuration, 0 without occupancy
+  std::vector<int> occ_rb;                          // per group: CTAs per configuration building runs
   std::vector<std::array<int, 3>> Umax;             // per group
   std::vector<std::vector<std::array<int, 3>>> Ub;  // per group, per batch
   std::vector<int> B;                               // per group batch size
@@ -1182,8 +1184,12 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
           throw Fail{BPMF_ERR_SIZE_UNSUPPORTED};
         }
         bg.occ_cap = occ_run_cap(lg->n_atoms[li], rmax, Um[2]);
+        // (a, b) rows of a configuration: about (u0 + 2 r + 4)(u1 + 2 r + 4), 256 per CTA
+        const long long rows = (long long)(Um[0] + 2 * (int)std::ceil(rmax) + 4) * (Um[1] + 2 * (int)std::ceil(rmax) + 4);
+        bg.occ_rb = (int)std::max<long long>(1, std::min<long long>(32, (rows + 255) / 256));
       }
       pl.occ_cap.push_back(bg.occ_cap);
+      pl.occ_rb.push_back(bg.occ_rb);
       const size_t per_conf = batch_bytes_per_conf(bg, E);
       const size_t part = align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
       const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
@@ -1290,6 +1296,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
           gb.Q = g.Q;
           gb.K = Kg;
           gb.occ_cap = pl.occ_cap[gi];
+          gb.occ_rb = pl.occ_rb[gi];
           const OccTab *d_tabs = reinterpret_cast<const OccTab *>(tab + pl.off_occ[gi]);
           if (use_ff)
             run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, d_rptr + Kg, h, nsh, nsl,

@@ -106,8 +106,9 @@ struct OccRunsArgs {
   const ConfMeta *meta;    // [batch]
   float h;
   int cap;                 // runs per configuration
-  OccRun *runs;            // [batch][2][cap]: row order, then sorted by length (longest first)
+  OccRun *runs;            // [batch][2][cap]: as found, then sorted by length (longest first)
   int *n_runs;             // [batch]
+  int rb;                  // CTAs per configuration
 };
 
 struct ClashArgs {

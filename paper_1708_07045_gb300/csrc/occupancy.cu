@@ -76,15 +76,16 @@ __device__ __forceinline__ bool node_occupied(float s2, float pz, float thr, int
   return __fadd_rn(s2, __fmul_rn(dz, dz)) < thr;
 }
 
-// One CTA per configuration: atom positions in the ligand-box frame,
-// occupied-node intervals per (a, b) row, merged, split into runs of at most
-// 32 nodes, compacted in row order, then ordered by length.
-__global__ void __launch_bounds__(512) k_occ_runs(OccRunsArgs a) {
+// rb CTAs per configuration: atom positions in the ligand-box frame, then,
+// for each CTA's share of the (a, b) rows, the occupied-node intervals of a
+// row, merged and split into runs of at most 32 nodes.
+__global__ void __launch_bounds__(256) k_occ_runs(OccRunsArgs a) {
   __shared__ float s_p[3][256], s_thr[256];
-  __shared__ float s_red[4][16];
-  __shared__ int s_cnt[16];
+  __shared__ float s_red[4][8];
+  __shared__ int s_cnt[8];
   __shared__ int s_base;
-  const ConfMeta m = a.meta[blockIdx.x];
+  const int cfg = blockIdx.x / a.rb, part = blockIdx.x % a.rb;
+  const ConfMeta m = a.meta[cfg];
   const int n = m.n_atoms;
   const int tid = threadIdx.x;
   float pmin[3] = {CUDART_INF_F, CUDART_INF_F, CUDART_INF_F}, pmax[3] = {-CUDART_INF_F, -CUDART_INF_F,
@@ -149,15 +150,18 @@ __global__ void __launch_bounds__(512) k_occ_runs(OccRunsArgs a) {
   // for boxes a receptor grid of at most 256 nodes admits)
   const long long rows_ll = (nA > 0 && nB > 0 && nC <= 2 * kRowIntervals) ? (long long)nA * nB : 0;
   const long long rows = rows_ll < (1ll << 30) ? rows_ll : 0;
-  if (tid == 0) s_base = 0;
-  __syncthreads();
-  OccRun *out = a.runs + (long long)blockIdx.x * 2 * a.cap;
+  OccRun *out = a.runs + (long long)cfg * 2 * a.cap;
+  // this CTA's share of the rows; its runs go to space reserved with an
+  // atomic add per chunk (the order of chunks across CTAs is free: the clash
+  // flags are an OR over runs, and k_occ_sort orders runs by length)
+  const int rpp = (int)((rows + a.rb - 1) / a.rb);
+  const int row_lo = part * rpp, row_hi = min((int)rows, row_lo + rpp);
   short iv_lo[kRowIntervals], iv_hi[kRowIntervals];
-  for (int r0 = 0; r0 < (int)rows; r0 += blockDim.x) {
+  for (int r0 = row_lo; r0 < row_hi; r0 += blockDim.x) {
     const int row = r0 + tid;
     int nI = 0;
     int ra = 0, rb = 0;
-    if (row < (int)rows) {
+    if (row < row_hi) {
       ra = alo + row / nB;
       rb = blo + row % nB;
       for (int i = 0; i < n; ++i) {
@@ -207,8 +211,8 @@ __global__ void __launch_bounds__(512) k_occ_runs(OccRunsArgs a) {
     // runs of at most 32 nodes
     int cnt = 0;
     for (int k = 0; k < nI; ++k) cnt += (iv_hi[k] - iv_lo[k] + kOccLevels) / kOccLevels;
-    // exclusive prefix in row order: within the warp by shuffles, then over
-    // the warp totals
+    // exclusive prefix within the chunk: within the warp by shuffles, then
+    // over the warp totals; one atomic add reserves the chunk's space
     const int lane = tid & 31, warp = tid >> 5;
     int incl = cnt;
     for (int d = 1; d < 32; d <<= 1) {
@@ -217,10 +221,11 @@ __global__ void __launch_bounds__(512) k_occ_runs(OccRunsArgs a) {
     }
     if (lane == 31) s_cnt[warp] = incl;
     __syncthreads();
-    int o = s_base + incl - cnt;
+    int o = incl - cnt;
     for (int w = 0; w < warp; ++w) o += s_cnt[w];
+    if (tid == blockDim.x - 1) s_base = atomicAdd(a.n_runs + cfg, o + cnt);
     __syncthreads();
-    if (tid == blockDim.x - 1) s_base = o + cnt;
+    o += s_base;
     for (int k = 0; k < nI; ++k) {
       for (int c = iv_lo[k]; c <= iv_hi[k]; c += kOccLevels) {
         const int len = min(kOccLevels, iv_hi[k] - c + 1);
@@ -238,53 +243,61 @@ __global__ void __launch_bounds__(512) k_occ_runs(OccRunsArgs a) {
     }
     __syncthreads();
   }
+}
+
+// One CTA per configuration: stable partition of its runs by length, longest
+// first, into the second half of its buffer, so that the clash test meets
+// long runs (the ones likeliest to hit) first and walks neighbouring rows of
+// one table.  Warp w owns the lengths lv = w, w + 16: it counts them with
+// ballots over the run list, then writes each length's runs in order.
+__global__ void __launch_bounds__(512) k_occ_sort(OccRunsArgs a) {
+  __shared__ int s_len[kOccLevels];
+  const int tid = threadIdx.x;
+  const OccRun *out = a.runs + (long long)blockIdx.x * 2 * a.cap;
+  OccRun *sorted = a.runs + (long long)blockIdx.x * 2 * a.cap + a.cap;
+  const int nr = min(a.n_runs[blockIdx.x], a.cap);
+  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int lv = warp; lv < kOccLevels; lv += nw) {
+    int c = 0;
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+      const int r = r0 + lane;
+      c += __popc(__ballot_sync(0xffffffffu, r < nr && out[r].lv == lv));
+    }
+    if (lane == 0) s_len[lv] = c;
+  }
   __syncthreads();
-  // stable partition by length, longest first, into the second half of the
-  // configuration's buffer: the clash test meets long runs (the ones likeliest
-  // to hit) first and walks neighbouring rows of one table
-  const int nr = min(s_base, a.cap);
-  OccRun *sorted = out + a.cap;
-  // warp w owns lengths lv = w, w + 16 (512 threads): count them with
-  // ballots over the run list, then write each length's runs in order
-  __shared__ int s_len[kOccLevels + 1];
-  {
-    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (int lv = warp; lv < kOccLevels; lv += nw) {
-      int c = 0;
-      for (int r0 = 0; r0 < nr; r0 += 32) {
-        const int r = r0 + lane;
-        c += __popc(__ballot_sync(0xffffffffu, r < nr && out[r].lv == lv));
-      }
-      if (lane == 0) s_len[lv] = c;
-    }
-    __syncthreads();
-    if (tid == 0) {  // longest first
-      int c = 0;
-      for (int lv = kOccLevels - 1; lv >= 0; --lv) {
-        const int n = s_len[lv];
-        s_len[lv] = c;
-        c += n;
-      }
-    }
-    __syncthreads();
-    for (int lv = warp; lv < kOccLevels; lv += nw) {
-      int o = s_len[lv];
-      for (int r0 = 0; r0 < nr; r0 += 32) {
-        const int r = r0 + lane;
-        OccRun rr;
-        const bool m = r < nr && (rr = out[r]).lv == lv;
-        const unsigned bal = __ballot_sync(0xffffffffu, m);
-        if (m) sorted[o + __popc(bal & ((1u << lane) - 1u))] = rr;
-        o += __popc(bal);
-      }
+  if (tid == 0) {  // longest first
+    int c = 0;
+    for (int lv = kOccLevels - 1; lv >= 0; --lv) {
+      const int n = s_len[lv];
+      s_len[lv] = c;
+      c += n;
     }
   }
+  __syncthreads();
+  for (int lv = warp; lv < kOccLevels; lv += nw) {
+    int o = s_len[lv];
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+      const int r = r0 + lane;
+      OccRun rr;
+      const bool mt = r < nr && (rr = out[r]).lv == lv;
+      const unsigned bal = __ballot_sync(0xffffffffu, mt);
+      if (mt) sorted[o + __popc(bal & ((1u << lane) - 1u))] = rr;
+      o += __popc(bal);
+    }
+  }
+  __syncthreads();
   if (tid == 0) a.n_runs[blockIdx.x] = nr;
 }
 
 cudaError_t launch_occ_runs(const OccRunsArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  k_occ_runs<<<batch, 512, 0, st>>>(a);
+  cudaError_t e = cudaMemsetAsync(a.n_runs, 0, sizeof(int) * batch, st);
+  if (e != cudaSuccess) return e;
+  k_occ_runs<<<batch * a.rb, 256, 0, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_occ_sort<<<batch, 512, 0, st>>>(a);
   return cudaGetLastError();
 }
 
