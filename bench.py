@@ -36,15 +36,27 @@ FF_INSTR_PER_FLOP = 9.8
 # DRAM bytes (read + write) per configuration of the fused x pass, from the ncu
 # capture summarised in profiles/xfused_ff_traffic.md; valid only for the kernel
 # sources it was taken with
-XFUSED_TRAFFIC = {"bytes_per_conf": 23.3e6, "src_sha": "01d5667b8a6266cb"}
+XFUSED_TRAFFIC = {"bytes_per_conf": 23.3e6, "src_sha": "b5cbafc644a9eb5a"}
 
 
-def kernel_src_sha():
+def kernel_src_sha(texts=None):
+    """Fingerprint of the code k_xfused compiles from: the kernel's own section
+    of kernels.cu, the shared prelude and helpers before the first kernel, its
+    argument struct, and the FFT / arithmetic headers."""
     import hashlib
     d = os.path.join(ROOT, "paper_1708_07045_gb300", "csrc")
-    src = b"".join(open(os.path.join(d, f), "rb").read()
-                   for f in ("kernels.cu", "fft.cuh", "arith.cuh", "kernels.cuh", "tc_dft.cuh"))
-    return hashlib.sha256(src).hexdigest()[:16]
+    if texts is None:
+        texts = {f: open(os.path.join(d, f)).read()
+                 for f in ("kernels.cu", "kernels.cuh", "fft.cuh", "arith.cuh", "tc_dft.cuh")}
+    marker = "// " + "-" * 74 + "\n"
+    secs = texts["kernels.cu"].split(marker)
+    prelude = marker.join(secs[:2])
+    xsec = next(sec for sec in secs if "k_xfused(XfusedArgs" in sec)
+    h = texts["kernels.cuh"]
+    i0 = h.index("struct XfusedArgs")
+    xstruct = h[i0:h.index("};", i0)]
+    src = "".join([prelude, xsec, xstruct, texts["fft.cuh"], texts["arith.cuh"], texts["tc_dft.cuh"]])
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def aggregate(t_ms_local, poses_local, dist=None, device=None):
@@ -330,7 +342,7 @@ def precision_sweep(torch, pkg, sess, w, dev, stream, n_sample=8, n_eval=64):
             "results": out}
 
 
-def occupancy_leg(torch, pkg, sess, dev, stream, steps, n_acc=2):
+def occupancy_leg(torch, pkg, sess, dev, stream, steps, n_acc=4, n_energy=2):
     """The steric-clash treatment (Eq. occupancy_grid) on the pocket variant
     of the protein-scale workload: cutoff grids plus receptor occupancy grids,
     same sizes (96^3 at 0.25 A, 40^3 site, 30 atoms, 2000 configurations, 4
@@ -348,14 +360,14 @@ def occupancy_leg(torch, pkg, sess, dev, stream, steps, n_acc=2):
     B = torch.empty((1, K), dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step():
+    def step(mode=pkg.BPMF_MODE_FF):
         recs = []
         try:
             for k, r in enumerate(w.receptors):
                 recs.append(pkg.bpmf_receptor_load(sess.ctx, grids[k], r.h, r.origin, r.site_lo, r.site_n, stream))
                 pkg.bpmf_receptor_set_occupancy(sess.ctx, recs[-1], occs[k], stream)
             lh = pkg.bpmf_ligand_batch(sess.ctx, [N_ATOMS], [J], coords, *params, stream=stream)
-            pkg.bpmf_eval(sess.ctx, lh, recs, w.kT, pkg.BPMF_MODE_FF, logZ, nv, B, None, stream)
+            pkg.bpmf_eval(sess.ctx, lh, recs, w.kT, mode, logZ, nv, B, None, stream)
             pkg.bpmf_ligand_free(lh)
         finally:
             for r in recs:
@@ -386,13 +398,55 @@ def occupancy_leg(torch, pkg, sess, dev, stream, steps, n_acc=2):
     dz = float(np.abs(lz[:n_acc][fin] - ref["logZ"][fin]).max() * w.kT) if fin.any() else None
     with np.errstate(divide="ignore"):
         free = float(np.isfinite(lz).mean())
+    # the plain FP32 form on the bounded (cutoff) grids of this workload
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    step(pkg.BPMF_MODE_FP32)
+    b.record(stream)
+    torch.cuda.synchronize()
+    lz32 = logZ.cpu().numpy()
+    fin32 = fin & np.isfinite(lz32[:n_acc])
+    dz32 = float(np.abs(lz32[:n_acc][fin32] - ref["logZ"][fin32]).max() * w.kT) if fin32.any() else None
+    # per-pose energies of both forms inside the 20 kT window (the tolerance's
+    # own terms), n_energy configurations x every receptor
+    gam = oracle.gamma(lig.params.q, lig.params.eps, lig.params.R)
+    dE = {"ff": 0.0, "fp32": 0.0}
+    lh = pkg.bpmf_ligand_batch(sess.ctx, [N_ATOMS], [J], coords, *params, stream=stream)
+    recs = []
+    try:
+        for k, r in enumerate(w.receptors):
+            recs.append(pkg.bpmf_receptor_load(sess.ctx, grids[k], r.h, r.origin, r.site_lo, r.site_n, stream))
+            pkg.bpmf_receptor_set_occupancy(sess.ctx, recs[-1], occs[k], stream)
+        for j in range(n_energy):
+            for k, r in enumerate(w.receptors):
+                E_ref, _ = oracle.pose_energies(r.grids, r.h, r.site_lo, r.site_n, lig.coords[j], gam, occ=r.occ,
+                                                R=lig.params.R)
+                ok = np.isfinite(E_ref)
+                if not ok.any():
+                    continue
+                win = ok & (E_ref <= E_ref[ok].min() + 20 * w.kT)
+                for name, mode in (("ff", pkg.BPMF_MODE_FF), ("fp32", pkg.BPMF_MODE_FP32)):
+                    E = np.empty(tuple(int(v) for v in r.site_n))
+                    pkg.bpmf_export_energies(sess.ctx, lh, recs[k], 0, j, mode, E)
+                    dE[name] = max(dE[name], float(np.abs(E[win] - E_ref[win]).max()))
+    finally:
+        for rr in recs:
+            pkg.bpmf_receptor_free(rr)
+        pkg.bpmf_ligand_free(lh)
+    fp32 = {"ms_per_step": a.elapsed_time(b), "max_kT_dlogZ_kcal": dz32, "max_dE_20kT_kcal": dE["fp32"],
+            "mask_and_counts_exact": bool(np.array_equal(np.isfinite(lz32[:n_acc]), fin)),
+            "meets_1e-3": bool(dz32 is not None and dz32 <= 1e-3 and dE["fp32"] <= 1e-3)}
     return {"workload": "occupancy protein-scale: 96^3 grid h=0.25 A, pocket receptor (10-22 A shell, 2020 atoms), "
                         "4 conformations, 30-atom ligand, 2000 configurations, 40^3 site box",
             "ms_per_step": t, "value": int(n.sum()) / (t / 1e3), "unit": "pose energies/s",
             "configurations_with_a_free_translation": free,
             "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
-            "accuracy_vs_oracle": {"configurations": n_acc, "mask_and_counts_exact": same_mask,
-                                   "max_kT_dlogZ_kcal": dz}}
+            "accuracy_vs_oracle": {"configurations": n_acc, "energy_configurations": n_energy,
+                                   "mask_and_counts_exact": same_mask, "max_kT_dlogZ_kcal": dz,
+                                   "max_dE_20kT_kcal": dE["ff"]},
+            "fp32_form": fp32}
 
 
 def learned_proposal_leg(torch, pkg, sess, w, dev, stream, res_train, coords_train, params_train, budget_frac=0.1):

@@ -148,3 +148,32 @@ def test_protein_scale_occupancy_sampled_parity(pkg):
     assert np.array_equal(np.isfinite(out["logZ"]), fin) and fin.any()
     assert np.abs(out["logZ"][fin] - ref["logZ"][fin]).max() * KT <= E_TOL
     assert np.abs(out["bpmf"][0] - ref["bpmf"]).max() <= B_TOL
+
+
+def test_fp32_form_on_cutoff_grids(pkg):
+    """The cutoff grids of the clash treatment are bounded, so the plain FP32
+    form's roundoff bound (8 eps sqrt(log2 P^3) rms(G_t) ||gamma_t||, summed
+    over t) is small.  The mask must be exact; energies inside the 20 kT
+    window stay under that bound (printed next to the 1e-3 tolerance)."""
+    w = synth.protein_scale_occ(n_conf=3, n_rec=1)
+    r, l = w.receptors[0], w.ligands[0]
+    gam = oracle.gamma(l.params.q, l.params.eps, l.params.R)
+    eps = 2.0 ** -24
+    lg = np.sqrt(np.log2(96.0 ** 3))
+    bound = sum(8 * eps * lg * np.sqrt(np.mean(r.grids[t].astype(np.float64) ** 2)) * np.linalg.norm(gam[t])
+                for t in range(3))
+    worst = 0.0
+    with _session() as s:
+        rh = s.load_receptor(r)
+        lh, _, _ = s.load_ligands([l])
+        for j in range(3):
+            E_ref, _ = oracle.pose_energies(r.grids, r.h, r.site_lo, r.site_n, l.coords[j], gam, occ=r.occ,
+                                            R=l.params.R)
+            E = s.export_energies(lh, rh, 0, j, r.site_n, pkg.BPMF_MODE_FP32)
+            assert np.array_equal(np.isinf(E), np.isinf(E_ref))
+            ok = np.isfinite(E_ref)
+            if ok.any():
+                win = ok & (E_ref <= E_ref[ok].min() + 20 * KT)
+                worst = max(worst, float(np.abs(E[win] - E_ref[win]).max()))
+    print(f"FP32 on cutoff grids: max |dE| in the 20 kT window {worst:.2e} kcal/mol, derived bound {bound:.2e}")
+    assert worst <= bound
