@@ -74,3 +74,27 @@ def sir_configs(logS, u):
 def sir_translations(E, kT, u):
     """Flattened translation index per uniform within one configuration."""
     return _inverse_cdf(translation_weights(E, kT), u)
+
+
+def bootstrap(logS, n_valid, kT, h, u):
+    """Bootstrap of the pooled BPMF and the standard binding free energy over
+    configurations (results, the BPMF uncertainty: configurations resampled
+    with replacement).  logS, n_valid [J, K]; u [R, J] uniforms: replicate r
+    draws configuration min(J - 1, floor(u J)) for each of its J slots.
+    Returns reps [R, K + 1] (B_k, then dG) and stats [2, K + 1] (mean and
+    sample standard deviation, ddof 1, over replicates)."""
+    from . import bpmf, dG, site_volume
+    logS = np.asarray(logS, dtype=np.float64)
+    n = np.asarray(n_valid, dtype=np.int64)
+    J, K = logS.shape
+    u = np.asarray(u, dtype=np.float64)
+    R = u.shape[0]
+    reps = np.empty((R, K + 1))
+    for r in range(R):
+        idx = np.minimum(J - 1, np.floor(u[r] * J).astype(np.int64))
+        B = bpmf(logS[idx], n[idx], kT)
+        reps[r, :K] = B
+        vs = site_volume(n[idx], h)
+        reps[r, K] = dG(B, kT, vs) if np.isfinite(B).any() and vs > 0 else np.inf
+    stats = np.stack([reps.mean(axis=0), reps.std(axis=0, ddof=1) if R > 1 else np.zeros(K + 1)])
+    return reps, stats

@@ -123,3 +123,58 @@ def test_two_stage_draw_is_the_flat_pose_distribution():
     u = (np.arange(N) + 0.5) / N
     flat_idx = S._inverse_cdf(p_flat, u)
     assert np.all(np.abs(np.bincount(flat_idx, minlength=flat.size) - N * p_flat) <= 1.0 + 1e-9)
+
+
+def _logS_table(J=5, K=3, seed=4):
+    rng = np.random.default_rng(seed)
+    n = rng.integers(1, 500, (J, K))
+    logZ = rng.normal(-20, 6, (J, K))
+    return logZ + np.log(n), n
+
+
+def test_bootstrap_identity_and_single_configuration():
+    """A replicate that draws every configuration once is the full estimate;
+    one that draws a single configuration J times is that configuration's
+    own B = -kT log Z and dG with its own site volume."""
+    logS, n = _logS_table()
+    J, K = logS.shape
+    h = 0.25
+    u = np.vstack([(np.arange(J) + 0.5) / J, np.zeros(J)])
+    reps, _ = S.bootstrap(logS, n, KT, h, u)
+    B = oracle.bpmf(logS, n, KT)
+    assert np.allclose(reps[0, :K], B, rtol=1e-13, atol=1e-10)
+    assert abs(reps[0, K] - oracle.dG(B, KT, oracle.site_volume(n, h))) <= 1e-10
+    own = -KT * (logS[0] - np.log(n[0]))
+    assert np.allclose(reps[1, :K], own, rtol=1e-13, atol=1e-10)
+    # closed form of dG for one configuration: -kT ln mean_k exp(-B_k/kT) - kT ln(h^3 mean_k n_k C)
+    ref = -KT * logsumexp(-own / KT, b=np.full(K, 1.0 / K)) - KT * np.log(h ** 3 * n[0].mean() * oracle.C_STANDARD)
+    assert abs(reps[1, K] - ref) <= 1e-10
+
+
+def test_bootstrap_two_configurations_exact_distribution():
+    """Two configurations: a replicate of two slots is one of four equally
+    likely ordered draws; the bootstrap mean and variance over stratified
+    uniforms converge to the exact moments of those four outcomes."""
+    logS, n = _logS_table(J=2, K=2, seed=9)
+    h = 0.375
+    outcomes = []
+    for a in range(2):
+        for b in range(2):
+            idx = np.array([a, b])
+            Bk = oracle.bpmf(logS[idx], n[idx], KT)
+            outcomes.append(np.append(Bk, oracle.dG(Bk, KT, oracle.site_volume(n[idx], h))))
+    outcomes = np.array(outcomes)
+    # stratified: every ordered pair equally often
+    u = np.array([[x, y] for x in (0.25, 0.75) for y in (0.25, 0.75)] * 25)
+    reps, stats = S.bootstrap(logS, n, KT, h, u)
+    assert np.allclose(stats[0], outcomes.mean(axis=0), rtol=1e-12, atol=1e-9)
+    R = u.shape[0]
+    var = outcomes.var(axis=0) * R / (R - 1)
+    assert np.allclose(stats[1] ** 2, var, rtol=1e-9, atol=1e-12)
+
+
+def test_bootstrap_constant_replicates_have_zero_spread():
+    logS, n = _logS_table()
+    u = np.tile((np.arange(5) + 0.5) / 5, (6, 1))
+    reps, stats = S.bootstrap(logS, n, KT, 0.25, u)
+    assert np.all(reps == reps[0]) and np.all(stats[1] <= 1e-12 * np.abs(stats[0]))
