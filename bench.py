@@ -589,6 +589,24 @@ def run_ours(args):
     t_ms, ts, prof = timed(modes[chosen], args.steps, args.warmup, prof=True)
     clk = clocks.stop()
     res_chosen = {k: v.cpu().numpy() for k, v in outs.items()}
+    # bootstrap uncertainty of B_k and dG over the 2000 configurations (1000
+    # replicates, uniforms from a seeded generator), on the device results
+    boot = None
+    if rank == 0:
+        R_boot = 1000
+        u_boot = torch.from_numpy(np.random.default_rng(77).random((R_boot, J))).to(dev)
+        st_boot = torch.empty((2, K + 1), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        eb0 = torch.cuda.Event(enable_timing=True)
+        eb1 = torch.cuda.Event(enable_timing=True)
+        eb0.record(stream)
+        pkg.bpmf_bootstrap(sess.ctx, outs["logZ"], outs["n_valid"], w.kT, w.receptors[0].h, u_boot, None, st_boot,
+                           stream)
+        eb1.record(stream)
+        torch.cuda.synchronize()
+        sb = st_boot.cpu().numpy()
+        boot = {"replicates": R_boot, "bpmf": res_chosen["bpmf"][0].tolist(), "sigma_bpmf_kcal": sb[1, :K].tolist(),
+                "dG": float(res_chosen["dG"][0]), "sigma_dG_kcal": float(sb[1, K]), "ms": eb0.elapsed_time(eb1)}
     other = "fp32" if chosen == "ff" else "ff"
     t_other, _, prof_other = timed(modes[other], max(1, args.steps // 2), 1, prof=True)
     res_other = {k: v.cpu().numpy() for k, v in outs.items()}
@@ -710,6 +728,7 @@ def run_ours(args):
                                                             for k, v in prof_split.items()}},
                 "precision_sweep": sweep,
                 "occupancy_path": occupancy,
+                "bootstrap": boot,
                 "learned_proposal": proposal,
                 "cufft_fp32_path": cufft,
                 "accuracy_vs_oracle": acc,

@@ -358,6 +358,24 @@ int bpmf_sir_poses(bpmf_ctx_t ctx, bpmf_lig_t lig, int lig_index, bpmf_rec_t rec
                    int M, int *conf, int *pose, void *stream);
 
 /*
+ * bpmf_bootstrap -- bootstrap uncertainty of the pooled BPMF and of the
+ * standard binding free energy (results, "BPMF uncertainty": configurations
+ * resampled with replacement), FP64.  Replicate r fills J slots with
+ * configurations j = min(J - 1, floor(u[r][i] J)) and evaluates, per
+ * receptor k, B_k = -kT [ln sum_slots n_jk exp(logZ_jk) - ln sum_slots n_jk],
+ * then dG = -kT ln((1/K) sum_k exp(-B_k/kT)) - kT ln(h^3 C mean n) exactly as
+ * bpmf_eval does for the full set (C = 1/1660.539 A^-3).
+ *   logZ, n_valid  [J][K] as bpmf_eval returns them for one ligand;
+ *   u              [R][J] float64 uniforms in [0, 1);
+ *   rep            [R][K + 1] out (B_k, then dG per replicate), may be null;
+ *   stats          [2][K + 1] out: mean, then sample standard deviation
+ *                  (ddof 1) over replicates, may be null (not both).
+ * All arrays DEVICE memory; stream ordered.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+int bpmf_bootstrap(bpmf_ctx_t ctx, const double *logZ, const int64_t *n_valid, int J, int K, double kT, double h,
+                   const double *u, int R, double *rep, double *stats, void *stream);
+
+/*
  * Kernel timing (tracing).  While enabled, every kernel the library launches
  * is bracketed by CUDA events recorded on the stream it runs on.
  * bpmf_profile_enable(ctx, 1) clears the counters and starts recording,

@@ -127,6 +127,7 @@ _SIGS = {
     "bpmf_proposal_sample": (_I, [_P, _P, _I, _D, _P, _I, _P, _P, _P]),
     "bpmf_proposal_bpmf": (_I, [_P, _P, _P, _P, _I, _I, _P, _D, _P, _P]),
     "bpmf_sir_poses": (_I, [_P, _P, _I, _P, _I, _I, _D, ctypes.c_uint, _P, _P, _P, _P, _I, _P, _P, _P]),
+    "bpmf_bootstrap": (_I, [_P, _P, _P, _I, _I, _D, _D, _P, _I, _P, _P, _P]),
     "bpmf_autotune": (_I, [_P, _P, _P, _I, ctypes.c_uint, _P]),
     "bpmf_export_energies_static": (_I, [_P, _I, _I, _I, _D, _P, _P, _I, _P, _P, _P, _P, _I, _I, ctypes.c_uint, _P,
                                          _P]),
@@ -431,6 +432,18 @@ def bpmf_sir_poses(ctx, lig, lig_index, rec, k, kT, mode, logZ, n_valid, u1, u2,
                                 _ptr(logZ, np.float64), _ptr(n_valid, np.int64), _ptr(u1, np.float64),
                                 _ptr(u2, np.float64), M, _ptr(conf, np.int32), _ptr(pose, np.int32),
                                 _stream(stream)), "bpmf_sir_poses", ctx)
+
+
+def bpmf_bootstrap(ctx, logZ, n_valid, kT, h, u, rep=None, stats=None, stream=None):
+    """Device tensors: logZ float64 [J, K], n_valid int64 [J, K], u float64
+    [R, J]; rep float64 [R, K + 1] and / or stats float64 [2, K + 1] out."""
+    J, K = (int(v) for v in tuple(logZ.shape))
+    R = int(tuple(u.shape)[0])
+    if tuple(u.shape) != (R, J):
+        raise ValueError("u must be [R, J]")
+    _check(lib().bpmf_bootstrap(ctx, _ptr(logZ, np.float64), _ptr(n_valid, np.int64), J, K, float(kT), float(h),
+                                _ptr(u, np.float64), R, _ptr(rep, np.float64), _ptr(stats, np.float64),
+                                _stream(stream)), "bpmf_bootstrap", ctx)
 
 
 def bpmf_valid_counts(ctx, lig, recs, total_conf):

@@ -340,4 +340,27 @@ int bpmf_proposal_bpmf(bpmf_ctx_t c, const double *logZ_s, const int64_t *n_s, c
   return BPMF_OK;
 }
 
+int bpmf_bootstrap(bpmf_ctx_t c, const double *logZ, const int64_t *n_valid, int J, int K, double kT, double h,
+                   const double *u, int R, double *rep, double *stats, void *stream) {
+  if (!c || !logZ || !n_valid || !u || J < 1 || K < 1 || R < 1 || !(kT > 0.0) || !(h > 0.0) || (!rep && !stats))
+    return BPMF_ERR_INVALID_ARG;
+  Dev dv(bpmf_internal_device(c));
+  cudaStream_t st = (cudaStream_t)stream;
+  double *buf = nullptr;
+  try {
+    double *r = rep;
+    if (!r) {
+      PCK(cudaMallocAsync(&buf, sizeof(double) * (size_t)R * (K + 1), st));
+      r = buf;
+    }
+    PCK(launch_bootstrap(logZ, reinterpret_cast<const long long *>(n_valid), J, K, kT, h * h * h / 1660.5390, u, R,
+                         r, stats, st));
+    if (buf) PCK(cudaFreeAsync(buf, st));
+  } catch (PFail f) {
+    if (buf) cudaFreeAsync(buf, st);
+    return fail(c, f.code);
+  }
+  return BPMF_OK;
+}
+
 }  // extern "C"

@@ -550,4 +550,110 @@ cudaError_t launch_sir_translations(const double *E, int nS, double kT, const do
   return cudaGetLastError();
 }
 
+// --------------------------------------------------------------------------
+// Bootstrap of the pooled BPMF and the standard binding free energy over
+// configurations (FP64).  Replicate r fills its J slots with configurations
+// j = min(J - 1, floor(u J)) and evaluates, per receptor k,
+//   B_k = -kT [ln sum_slots S_jk - ln sum_slots n_jk],  S = n exp(log Z),
+// then dG = -kT ln((1/K) sum_k exp(-B_k / kT)) - kT ln(h^3 C mean n) as the
+// full estimate does.  One CTA per replicate; rep [R][K + 1].
+__global__ void __launch_bounds__(256) k_bootstrap(const double *logZ, const long long *nvalid, int J, int K, double kT,
+                                                   double vscale, const double *u, int R, double *rep) {
+  __shared__ double s_d[256];
+  __shared__ long long s_l[256];
+  const int r = blockIdx.x;
+  const double *ur = u + (long long)r * J;
+  double *out = rep + (long long)r * (K + 1);
+  long long ntot_all = 0;
+  for (int k = 0; k < K; ++k) {
+    double mx = -CUDART_INF;
+    long long nt = 0;
+    for (int i = threadIdx.x; i < J; i += blockDim.x) {
+      const int j = min(J - 1, (int)floor(ur[i] * (double)J));
+      const long long n = nvalid[(long long)j * K + k];
+      if (n > 0) mx = fmax(mx, logZ[(long long)j * K + k] + log((double)n));
+      nt += n;
+    }
+    const double M = block_max(mx, s_d);
+    s_l[threadIdx.x] = nt;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) s_l[threadIdx.x] += s_l[threadIdx.x + o];
+      __syncthreads();
+    }
+    const long long ntot = s_l[0];
+    __syncthreads();
+    double acc = 0.0;
+    if (M > -CUDART_INF)
+      for (int i = threadIdx.x; i < J; i += blockDim.x) {
+        const int j = min(J - 1, (int)floor(ur[i] * (double)J));
+        const long long n = nvalid[(long long)j * K + k];
+        if (n > 0) {
+          const double v = logZ[(long long)j * K + k] + log((double)n);
+          if (v > -CUDART_INF) acc += exp(v - M);
+        }
+      }
+    s_d[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) s_d[threadIdx.x] += s_d[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0)
+      out[k] = (ntot > 0 && s_d[0] > 0.0) ? -kT * (M + log(s_d[0]) - log((double)ntot)) : CUDART_INF;
+    ntot_all += ntot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double mx = -CUDART_INF;
+    for (int k = 0; k < K; ++k) mx = fmax(mx, -out[k] / kT);
+    double s = 0.0;
+    if (mx > -CUDART_INF)
+      for (int k = 0; k < K; ++k) s += exp(-out[k] / kT - mx);
+    const double nmean = (double)ntot_all / ((double)J * K);
+    out[K] = (s > 0.0 && nmean > 0.0) ? -kT * (mx + log(s) - log((double)K)) - kT * log(vscale * nmean) : CUDART_INF;
+  }
+}
+
+// Mean and sample standard deviation (ddof 1) of every column of rep.
+__global__ void __launch_bounds__(256) k_bootstrap_stats(const double *rep, int R, int C, double *stats) {
+  __shared__ double s_d[256];
+  const int c = blockIdx.x;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) acc += rep[(long long)r * C + c];
+  s_d[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) s_d[threadIdx.x] += s_d[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double mean = s_d[0] / R;
+  __syncthreads();
+  acc = 0.0;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    const double d = rep[(long long)r * C + c] - mean;
+    acc += d * d;
+  }
+  s_d[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) s_d[threadIdx.x] += s_d[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    stats[c] = mean;
+    stats[C + c] = R > 1 ? sqrt(s_d[0] / (R - 1)) : 0.0;
+  }
+}
+
+cudaError_t launch_bootstrap(const double *logZ, const long long *nvalid, int J, int K, double kT, double vscale,
+                             const double *u, int R, double *rep, double *stats, cudaStream_t st) {
+  if (R <= 0 || J <= 0) return cudaSuccess;
+  k_bootstrap<<<R, 256, 0, st>>>(logZ, nvalid, J, K, kT, vscale, u, R, rep);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !stats) return e;
+  k_bootstrap_stats<<<K + 1, 256, 0, st>>>(rep, R, K + 1, stats);
+  return cudaGetLastError();
+}
+
 }  // namespace bpmf

@@ -41,5 +41,7 @@ cudaError_t launch_sir_configs(const double *logZ, const long long *nvalid, int 
                                int M, double *cdf, int *conf, cudaStream_t st);
 cudaError_t launch_sir_translations(const double *E, int nS, double kT, const double *u, const int *conf, int j, int M,
                                     double *cdf, int *pick, cudaStream_t st);
+cudaError_t launch_bootstrap(const double *logZ, const long long *nvalid, int J, int K, double kT, double vscale,
+                             const double *u, int R, double *rep, double *stats, cudaStream_t st);
 
 }  // namespace bpmf

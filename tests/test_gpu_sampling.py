@@ -190,3 +190,38 @@ def test_sir_no_valid_pose_and_bad_arguments(env, case):
         pkg.bpmf_sir_poses(s.ctx, lh, 0, rh, 1, KT, pkg.BPMF_MODE_FF, logZ, nv, torch.zeros(2).double().cuda(),
                            torch.zeros(2).double().cuda(), torch.empty(2, dtype=torch.int32, device="cuda"),
                            torch.empty(2, dtype=torch.int32, device="cuda"))
+
+
+def test_bootstrap_matches_oracle(env, case):
+    """Bootstrap replicates of B_k and dG: with the library's own log Z the
+    replicates equal the FP64 reference to rounding; against the oracle's log
+    S they stay within the BPMF tolerance; the identity replicate reproduces
+    bpmf_eval's BPMF and dG."""
+    torch, pkg, s = env
+    recs, ligs, refs = case
+    rh = [s.load_receptor(r) for r in recs]
+    lig, ref = ligs[0], refs[0]
+    lh, _, _ = s.load_ligands([lig])
+    J, K, R = lig.coords.shape[0], 2, 200
+    logZ = torch.empty((J, K), dtype=torch.float64, device="cuda")
+    nv = torch.empty((J, K), dtype=torch.int64, device="cuda")
+    B = torch.empty((1, K), dtype=torch.float64, device="cuda")
+    dG = torch.empty(1, dtype=torch.float64, device="cuda")
+    pkg.bpmf_eval(s.ctx, lh, rh, KT, pkg.BPMF_MODE_FF, logZ, nv, B, dG)
+    u = np.random.default_rng(21).random((R, J))
+    u[0] = (np.arange(J) + 0.5) / J  # identity replicate
+    rep = torch.empty((R, K + 1), dtype=torch.float64, device="cuda")
+    stats = torch.empty((2, K + 1), dtype=torch.float64, device="cuda")
+    pkg.bpmf_bootstrap(s.ctx, logZ, nv, KT, recs[0].h, torch.from_numpy(u).cuda(), rep, stats)
+    rep_, stats_ = rep.cpu().numpy(), stats.cpu().numpy()
+    lz, n = logZ.cpu().numpy(), nv.cpu().numpy()
+    with np.errstate(divide="ignore"):
+        logS = np.where(n > 0, lz + np.log(np.maximum(n, 1)), -np.inf)
+    r_ref, s_ref = S.bootstrap(logS, n, KT, recs[0].h, u)
+    assert np.allclose(rep_, r_ref, rtol=1e-12, atol=1e-9)
+    assert np.allclose(stats_, s_ref, rtol=1e-9, atol=1e-9)
+    assert np.allclose(rep_[0, :K], B.cpu().numpy()[0], rtol=1e-12, atol=1e-9)
+    assert abs(rep_[0, K] - dG.item()) <= 1e-9
+    r_or, s_or = S.bootstrap(ref["logS"], ref["n_valid"], KT, recs[0].h, u)
+    assert np.abs(rep_ - r_or).max() <= 1e-2
+    assert np.all(stats_[1] > 0)
