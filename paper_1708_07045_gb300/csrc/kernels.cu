@@ -433,116 +433,146 @@ template <class T>
 __global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, F = a.F2, ls = P + 1;
-  const int L = (a.S1 + 1) / 2;
+  const int Lc = a.Lc;  // row pairs per chunk (all of them when they fit)
   float4 *s_tw = smem;
   cx<T> *b0 = reinterpret_cast<cx<T> *>(smem + P);
-  cx<T> *b1 = b0 + L * ls;
-  const int b1n = L * ls > a.S1 * F ? L * ls : a.S1 * F;
-  T *xs = reinterpret_cast<T *>(b1 + b1n);  // [S1*S2]
+  cx<T> *b1 = b0 + Lc * ls;
+  const int b1n = Lc * ls > 2 * Lc * F ? Lc * ls : 2 * Lc * F;
+  T *xs = reinterpret_cast<T *>(b1 + b1n);  // [2 Lc * S2]
   __shared__ T s_red[8];
   __shared__ float s_sum[8];
   load_tw(s_tw, a.tw, P);
   const int s0 = blockIdx.x % a.S0;
   const int jk = blockIdx.x / a.S0;  // j * K + k
   const PairInfo inf = a.info[jk];
-  const long long base = (long long)blockIdx.x * a.S1 * F;
   const bool row_ok = (s0 >= inf.sa[0] && s0 <= inf.sb[0]);
-  // stage the [S1][F2] block of half spectra with asynchronous copies (b1 is
-  // sized for it), then pack row pairs as z = A + iB with Hermitian extension
-  cx<T> *stg = b1;
-  if (row_ok) {
-    for (int idx = threadIdx.x; idx < a.S1 * F; idx += blockDim.x) cp_cx<T>(&stg[idx], a.y2, base + idx, true);
-    cp_async_wait_all();
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < L * P; idx += blockDim.x) {
-    const int l = idx / P, n = idx % P;
-    const int ra = 2 * l, rb = ra + 1;
-    cx<T> A = c_zero<T>(), B = c_zero<T>();
-    const bool up = n <= P / 2;
-    const int kk = up ? n : P - n;
-    const bool real_bin = (kk == 0) || (2 * kk == P);
-    if (row_ok) {
-      A = stg[ra * F + kk];
-      if (rb < a.S1) B = stg[rb * F + kk];
-    }
-    if (real_bin) {
-      A.im = s_zero<T>();
-      B.im = s_zero<T>();
-    }
-    if (!up) {
-      A = c_conj(A);
-      B = c_conj(B);
-    }
-    b0[l * ls + n] = c_norm(cx<T>{s_sub(A.re, B.im), s_add(A.im, B.re)});
-  }
-  __syncthreads();
-  cx<T> *res = cta_fft_auto<T, 20, 256, true>(b0, b1, 1, ls, L, a.plan, s_tw, true);
   const T nscale = s_mk<T>(a.nscale_hi, a.nscale_lo);
   const T escale = s_mk<T>(a.escale_hi, a.escale_lo);
-  const int nS = a.S1 * a.S2;
-  T vmax = s_mk<T>(-CUDART_INF_F, 0.f);
-  for (int idx = threadIdx.x; idx < nS; idx += blockDim.x) {
-    const int s1 = idx / a.S2, s2 = idx % a.S2;
-    bool ok = row_ok && s1 >= inf.sa[1] && s1 <= inf.sb[1] && s2 >= inf.sa[2] && s2 <= inf.sb[2];
-    if (ok && a.clash) {  // a clashing translation has infinite energy (it stays counted in n)
-      const uint32_t w = a.clash[((long long)blockIdx.x * a.S1 + s1) * a.CW + (s2 >> 5)];
-      ok = !((w >> (s2 & 31)) & 1u);
+  // running max-shifted sum over the chunks: M_run and s_run relative to it
+  T M_run = s_mk<T>(-CUDART_INF_F, 0.f);
+  float s_run = 0.f;
+  for (int r0 = 0; r0 < a.S1; r0 += 2 * Lc) {
+    const int nrow = min(2 * Lc, a.S1 - r0), L = (nrow + 1) / 2;
+    const long long base = ((long long)blockIdx.x * a.S1 + r0) * F;
+    // stage this chunk's [rows][F2] half spectra with asynchronous copies,
+    // then pack row pairs as z = A + iB with Hermitian extension
+    cx<T> *stg = b1;
+    __syncthreads();
+    if (row_ok) {
+      for (int idx = threadIdx.x; idx < nrow * F; idx += blockDim.x) cp_cx<T>(&stg[idx], a.y2, base + idx, true);
+      cp_async_wait_all();
     }
-    T x = s_mk<T>(-CUDART_INF_F, 0.f);
-    if (ok) {
-      const cx<T> z = res[(s1 >> 1) * ls + imod(inf.w0[2] + s2, P)];
-      const T val = (s1 & 1) ? z.im : z.re;
-      x = s_norm(s_mul(val, nscale));
-      if (ff_gt(x, vmax)) vmax = x;
-    }
-    xs[idx] = x;
-    if (a.export_E && jk == 0) {
-      double e = CUDART_INF;
-      if (ok) {
-        const cx<T> z = res[(s1 >> 1) * ls + imod(inf.w0[2] + s2, P)];
-        const T E = s_norm(s_mul((s1 & 1) ? z.im : z.re, escale));
-        e = (double)s_hi(E) + (double)s_lo(E);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < L * P; idx += blockDim.x) {
+      const int l = idx / P, n = idx % P;
+      const int ra = 2 * l, rb = ra + 1;
+      cx<T> A = c_zero<T>(), B = c_zero<T>();
+      const bool up = n <= P / 2;
+      const int kk = up ? n : P - n;
+      const bool real_bin = (kk == 0) || (2 * kk == P);
+      if (row_ok) {
+        A = stg[ra * F + kk];
+        if (rb < nrow) B = stg[rb * F + kk];
       }
-      a.export_E[((long long)s0 * a.S1 + s1) * a.S2 + s2] = e;
+      if (real_bin) {
+        A.im = s_zero<T>();
+        B.im = s_zero<T>();
+      }
+      if (!up) {
+        A = c_conj(A);
+        B = c_conj(B);
+      }
+      b0[l * ls + n] = c_norm(cx<T>{s_sub(A.re, B.im), s_add(A.im, B.re)});
     }
-  }
-  // block max
-  for (int o = 16; o > 0; o >>= 1) {
-    T other = s_mk<T>(__shfl_xor_sync(0xffffffffu, s_hi(vmax), o), __shfl_xor_sync(0xffffffffu, s_lo(vmax), o));
-    if (ff_gt(other, vmax)) vmax = other;
-  }
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = vmax;
-  __syncthreads();
-  T M = s_red[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-    if (ff_gt(s_red[w], M)) M = s_red[w];
-  float acc = 0.f;
-  if (s_hi(M) > -CUDART_INF_F) {
+    __syncthreads();
+    cx<T> *res = cta_fft_auto<T, 20, 256, true>(b0, b1, 1, ls, L, a.plan, s_tw, true);
+    const int nS = nrow * a.S2;
+    T vmax = s_mk<T>(-CUDART_INF_F, 0.f);
     for (int idx = threadIdx.x; idx < nS; idx += blockDim.x) {
-      const T x = xs[idx];
-      if (s_hi(x) > -CUDART_INF_F) {
-        const float d = __fadd_rn(__fsub_rn(s_hi(x), s_hi(M)), __fsub_rn(s_lo(x), s_lo(M)));
-        acc += expf(d);
+      const int r = idx / a.S2, s2 = idx % a.S2, s1 = r0 + r;
+      bool ok = row_ok && s1 >= inf.sa[1] && s1 <= inf.sb[1] && s2 >= inf.sa[2] && s2 <= inf.sb[2];
+      if (ok && a.clash) {  // a clashing translation has infinite energy (it stays counted in n)
+        const uint32_t w = a.clash[((long long)blockIdx.x * a.S1 + s1) * a.CW + (s2 >> 5)];
+        ok = !((w >> (s2 & 31)) & 1u);
+      }
+      T x = s_mk<T>(-CUDART_INF_F, 0.f);
+      if (ok) {
+        const cx<T> z = res[(r >> 1) * ls + imod(inf.w0[2] + s2, P)];
+        const T val = (r & 1) ? z.im : z.re;
+        x = s_norm(s_mul(val, nscale));
+        if (ff_gt(x, vmax)) vmax = x;
+      }
+      xs[idx] = x;
+      if (a.export_E && jk == 0) {
+        double e = CUDART_INF;
+        if (ok) {
+          const cx<T> z = res[(r >> 1) * ls + imod(inf.w0[2] + s2, P)];
+          const T E = s_norm(s_mul((r & 1) ? z.im : z.re, escale));
+          e = (double)s_hi(E) + (double)s_lo(E);
+        }
+        a.export_E[((long long)s0 * a.S1 + s1) * a.S2 + s2] = e;
       }
     }
-  }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
+    // block max of the chunk
+    for (int o = 16; o > 0; o >>= 1) {
+      T other = s_mk<T>(__shfl_xor_sync(0xffffffffu, s_hi(vmax), o), __shfl_xor_sync(0xffffffffu, s_lo(vmax), o));
+      if (ff_gt(other, vmax)) vmax = other;
+    }
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = vmax;
+    __syncthreads();
+    T M = s_red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (ff_gt(s_red[w], M)) M = s_red[w];
+    float acc = 0.f;
+    if (s_hi(M) > -CUDART_INF_F) {
+      for (int idx = threadIdx.x; idx < nS; idx += blockDim.x) {
+        const T x = xs[idx];
+        if (s_hi(x) > -CUDART_INF_F) {
+          const float d = __fadd_rn(__fsub_rn(s_hi(x), s_hi(M)), __fsub_rn(s_lo(x), s_lo(M)));
+          acc += expf(d);
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = acc;
+    __syncthreads();
     float s = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_sum[w];
-    a.part[blockIdx.x] = make_float4(s_hi(M), s_lo(M), s, 0.f);
+    // combine with the earlier chunks (one chunk: M_run = M, s_run = s)
+    if (s_hi(M) > -CUDART_INF_F) {
+      if (!(s_hi(M_run) > -CUDART_INF_F)) {
+        M_run = M;
+        s_run = s;
+      } else if (ff_gt(M, M_run)) {
+        s_run = s_run * expf(__fadd_rn(__fsub_rn(s_hi(M_run), s_hi(M)), __fsub_rn(s_lo(M_run), s_lo(M)))) + s;
+        M_run = M;
+      } else {
+        s_run += s * expf(__fadd_rn(__fsub_rn(s_hi(M), s_hi(M_run)), __fsub_rn(s_lo(M), s_lo(M_run))));
+      }
+    }
   }
+  if (threadIdx.x == 0) a.part[blockIdx.x] = make_float4(s_hi(M_run), s_lo(M_run), s_run, 0.f);
 }
 
 template <class T>
-cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st) {
+size_t zinv_smem(const ZinvArgs &a, int Lc) {
+  const int P = a.plan.n;
+  const size_t b1n = std::max((size_t)Lc * (P + 1), (size_t)2 * Lc * a.F2);
+  return sizeof(float4) * P + sizeof(cx<T>) * ((size_t)Lc * (P + 1) + b1n) + sizeof(T) * (size_t)2 * Lc * a.S2;
+}
+
+template <class T>
+cudaError_t launch_zinv(const ZinvArgs &a_in, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  const int P = a.plan.n, L = (a.S1 + 1) / 2;
-  const size_t b1n = std::max((size_t)L * (P + 1), (size_t)a.S1 * a.F2);
-  const size_t smem = sizeof(float4) * P + sizeof(cx<T>) * ((size_t)L * (P + 1) + b1n) + sizeof(T) * (size_t)a.S1 * a.S2;
+  ZinvArgs a = a_in;
+  // all row pairs of the site window in one chunk when they fit in shared
+  // memory (227 KB per CTA), else the largest chunk that does
+  const int L = (a.S1 + 1) / 2;
+  int Lc = L;
+  while (Lc > 1 && zinv_smem<T>(a, Lc) > 227 * 1024) --Lc;
+  if (zinv_smem<T>(a, Lc) > 227 * 1024) return cudaErrorInvalidValue;
+  a.Lc = Lc;
+  const size_t smem = zinv_smem<T>(a, Lc);
   cudaError_t e = cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_zinv<T><<<(unsigned)((long long)batch * a.K * a.S0), 256, smem, st>>>(a);

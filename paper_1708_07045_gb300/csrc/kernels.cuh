@@ -132,6 +132,7 @@ struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp pa
   double *export_E;        // optional [S0][S1][S2] energies (+inf masked), batch entry 0, receptor 0
   const uint32_t *clash;   // optional [batch][K][S0][S1][CW] clash flags (excluded, +inf when exported)
   int CW;
+  int Lc;                  // row pairs per shared-memory chunk (set by launch_zinv)
   FftPlan plan;
   const float4 *tw;
 };

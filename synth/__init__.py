@@ -305,6 +305,25 @@ def protein_scale_occ(n_conf: int = 2000, n_rec: int = 4, seed: int = 1001, n_at
                     recs, [LigandInput(lig, coords)])
 
 
+def whole_surface(n_conf: int = 64, n_rec: int = 1, seed: int = 1003, n_atoms_lig: int = 30, site: int = 200,
+                  n_atoms_rec: int = 1600) -> Workload:
+    """The larger grid of the paper: 248^3 nodes at 0.25 A (62 A) around a
+    whole protein-sized receptor (a 20 A ball of 1600 atoms), with a central
+    site box of ``site``^3 translations that covers the surface; 30-atom
+    ligand."""
+    base = receptor_atoms(seed, n_atoms_rec, 0.0, 20.0)
+    recs = []
+    for k in range(n_rec):
+        atoms = jitter(base, 0.3, seed + 100 * (k + 1))
+        g, o = receptor_grids(atoms, (248, 248, 248), 0.25)
+        lo, sn = central_site((248, 248, 248), site)
+        recs.append(ReceptorInput(g, 0.25, o, lo, sn))
+    lig = ligand_params(seed + 1, n_atoms_lig)
+    coords = ligand_configs(seed + 2, n_atoms_lig, n_conf)
+    return Workload("whole-surface 248^3 h=0.25 J=%d K=%d %d atoms, %d^3 site" % (n_conf, n_rec, n_atoms_lig, site),
+                    recs, [LigandInput(lig, coords)])
+
+
 def batched_uneven(n_lig: int = 141, n_conf: int = 500, n_rec: int = 10, seed: int = 1002,
                    clip: float = 1e4, sizes=(64, 112), sites=(24, 40), atoms_range=(8, 60)) -> Workload:
     """Many ligands of uneven atom counts against receptor conformations of
