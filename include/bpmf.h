@@ -66,6 +66,20 @@ extern "C" {
  *                     FP32, with the error against the oracle reported per
  *                     result.  Other edges fall back to the FP32 stages. */
 #define BPMF_MODE_SPLIT_BF16 2u
+/*   BPMF_MODE_REFINE -- the FP32 correlation for every translation, then an
+ *     exact re-evaluation, in FP64, of the translations that can matter.  The
+ *     FP32 correlation error stays below B = 8 eps32 sqrt(log2 P0 P1 P2)
+ *     sum_t rms(G_t) ||gamma_t||_2.  Every translation whose FP32 energy lies
+ *     within W + 2B of the configuration's FP32 minimum (W = kT max(20,
+ *     ln(1e5 n)), n the site-window size) is re-evaluated as the direct sum
+ *     the correlation equals: sum_i sum_t gamma_t,i trilinear(G_t, g_i + m).
+ *     Every translation within W of the true minimum is among them; the others
+ *     keep their FP32 energies and together weigh less than 1e-5 of S.  The
+ *     energies that can carry weight are exact, and so are log Z, BPMF and dG
+ *     up to that 1e-5, at about the FP32 form's cost.  Exported energies
+ *     outside the window are the FP32 values.  The receptor handle keeps a
+ *     device copy of its FP32 grids for this form. */
+#define BPMF_MODE_REFINE 3u
 
 /* Largest supported ligand (atoms) and padded FFT edge. */
 #define BPMF_MAX_ATOMS 256
@@ -183,7 +197,7 @@ void bpmf_ligand_free(bpmf_lig_t lig);
  *            processed in groups of equal padded FFT edges; the ligand's
  *            forward transforms are shared within a group.
  *  kT        > 0 (kcal/mol).
- *  mode      BPMF_MODE_FP32, BPMF_MODE_FF or BPMF_MODE_SPLIT_BF16.
+ *  mode      BPMF_MODE_FP32, BPMF_MODE_FF, BPMF_MODE_SPLIT_BF16 or BPMF_MODE_REFINE.
  *  logZ      [total_conf][K] float64, total_conf = sum n_conf, ligand-major.
  *  n_valid   [total_conf][K] int64 (may be NULL).
  *  bpmf      [n_lig][K] float64 (may be NULL).

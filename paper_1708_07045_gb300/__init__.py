@@ -22,7 +22,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "libbpmf.so")
-_SOURCES = ["kernels.cu", "occupancy.cu", "bpmf_api.cu", "bpmf_static.cu", "proposal.cu", "bpmf_proposal.cu"]
+_SOURCES = ["kernels.cu", "occupancy.cu", "refine.cu", "bpmf_api.cu", "bpmf_static.cu", "proposal.cu", "bpmf_proposal.cu"]
 _HEADERS = ["arith.cuh", "fft.cuh", "kernels.cuh", "proposal.cuh", "tc_dft.cuh"]
 
 BPMF_OK = 0
@@ -35,6 +35,7 @@ BPMF_WARN_NO_VALID = 1
 BPMF_MODE_FP32 = 0
 BPMF_MODE_FF = 1
 BPMF_MODE_SPLIT_BF16 = 2
+BPMF_MODE_REFINE = 3
 BPMF_MAX_ATOMS = 256
 BPMF_MAX_FFT_EDGE = 256
 

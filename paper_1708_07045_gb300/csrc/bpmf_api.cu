@@ -69,6 +69,8 @@ struct bpmf_rec {
   float2 *hi = nullptr, *lo = nullptr;  // [3][P0][Q]
   uint32_t *occ = nullptr;              // occupancy tables [kOccLevels][N0 + 32][occW][N1 + 32], or null
   int occW = 0;
+  float *grid = nullptr;                // the FP32 grids [3][N0][N1][N2] (refined form)
+  double *sumsq = nullptr;              // [3] their sums of squares (FP32 error bound)
 };
 
 struct bpmf_lig {
@@ -82,6 +84,9 @@ struct bpmf_lig {
   float *q = nullptr, *eps = nullptr, *R = nullptr;  // device [total_atoms] (configuration features)
   std::vector<float> minmax;  // host [total_conf][6]
   std::vector<float> R_host;  // host [total_atoms] (occupancy radii)
+  std::vector<float> q_host, eps_host;  // host [total_atoms] (FP32 error bound)
+  double *gamma64 = nullptr;  // device [3][total_atoms] FP64 generalised charges (refined form)
+  int p_rep = 12, p_att = 6;
 };
 
 namespace {
@@ -350,6 +355,7 @@ struct BatchGeom {
   int K;
   int occ_cap = 0;  // ligand occupancy runs per configuration (0: no clash channel)
   int occ_rb = 1;   // CTAs per configuration building the runs
+  bool refine = false;  // refined form: FP32 energies kept for k_refine
 };
 
 int clash_words(int S2) { return (S2 + 31) / 32; }
@@ -364,7 +370,11 @@ size_t batch_bytes_per_conf(const BatchGeom &g, size_t E) {
   if (g.occ_cap > 0)
     occ = align_up(2 * (size_t)g.occ_cap * sizeof(OccRun)) + align_up(sizeof(int)) +
           align_up((size_t)g.K * g.S[0] * g.S[1] * clash_words(g.S[2]) * sizeof(uint32_t));
-  return align_up(box) + align_up(lz) + align_up(ly) + align_up(x2) + align_up(y2) + occ;
+  size_t ref = 0;
+  if (g.refine)
+    ref = align_up((size_t)g.K * g.S[0] * g.S[1] * g.S[2] * sizeof(float)) +
+          align_up((size_t)g.K * g.S[0] * sizeof(float));
+  return align_up(box) + align_up(lz) + align_up(ly) + align_up(x2) + align_up(y2) + occ + ref;
 }
 
 // Upper bound on the occupancy runs of one configuration: every merged
@@ -385,7 +395,8 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
                const PairInfo *d_info, const float2 *const *d_rhi, const float2 *const *d_rlo, double h,
                float nscale_hi, float nscale_lo, float escale_hi, float escale_lo, float4 *d_part,
                double *export_E, char *ws, cudaStream_t st, const bpmf_ctx::Tune &tn, bool split = false,
-               const OccTab *d_tabs = nullptr) {
+               const OccTab *d_tabs = nullptr, const RefTab *d_rtabs = nullptr, const double *gnorm = nullptr,
+               double kT = 1.0) {
   auto plan = [&](int P) { return split ? make_plan_split(c, P) : make_plan(P); };
   const size_t E = sizeof(cx<T>);
   char *p = ws;
@@ -407,6 +418,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     int *n_runs = reinterpret_cast<int *>(p);
     p += align_up((size_t)batch * sizeof(int));
     clash = reinterpret_cast<uint32_t *>(p);
+    p += align_up((size_t)batch * g.K * g.S[0] * g.S[1] * CW * sizeof(uint32_t));
     OccRunsArgs ra{lg->coords, lg->R, d_meta, (float)h, g.occ_cap, runs, n_runs, g.occ_rb};
     launch(c, "k_occ_runs", st, [&] { return launch_occ_runs(ra, batch, st); });
     ClashArgs ca{};
@@ -422,6 +434,13 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     ca.CW = CW;
     ca.clash = clash;
     launch(c, "k_clash", st, [&] { return launch_clash(ca, batch, st); });
+  }
+  float *Ebuf = nullptr, *pmin = nullptr;
+  if (g.refine) {
+    Ebuf = reinterpret_cast<float *>(p);
+    p += align_up((size_t)batch * g.K * g.S[0] * g.S[1] * g.S[2] * sizeof(float));
+    pmin = reinterpret_cast<float *>(p);
+    p += align_up((size_t)batch * g.K * g.S[0] * sizeof(float));
   }
 
   float hh, hl;
@@ -507,12 +526,36 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   zi.escale_hi = escale_hi;
   zi.escale_lo = escale_lo;
   zi.part = d_part;
-  zi.export_E = export_E;
+  zi.export_E = g.refine ? nullptr : export_E;
+  zi.Ebuf = Ebuf;
+  zi.plane_min = pmin;
   zi.clash = clash;
   zi.CW = CW;
   zi.plan = plan(g.P[2]);
   zi.tw = twiddles(c, g.P[2]);
   launch(c, sizeof(T) == 4 ? "k_zinv<fp32>" : "k_zinv<ff>", st, [&] { return launch_zinv<T>(zi, batch, st); });
+  if (g.refine) {
+    RefineArgs ra{};
+    ra.E = Ebuf;
+    ra.plane_min = pmin;
+    ra.meta = d_meta;
+    ra.info = d_info;
+    ra.tabs = d_rtabs;
+    for (int t = 0; t < 3; ++t) ra.gnorm[t] = gnorm[t];
+    ra.log2P3 = std::log2((double)g.P[0] * g.P[1] * g.P[2]);
+    ra.coords = lg->coords;
+    ra.gamma64 = lg->gamma64;
+    ra.gamma_stride = (int)lg->total_atoms;
+    ra.h = h;
+    ra.kT = kT;
+    ra.K = g.K;
+    ra.S0 = g.S[0];
+    ra.S1 = g.S[1];
+    ra.S2 = g.S[2];
+    ra.part = d_part;
+    ra.export_E = export_E;
+    launch(c, "k_refine", st, [&] { return launch_refine(ra, batch, st); });
+  }
 }
 
 void check_recs(const bpmf_rec_t *recs, int K, bpmf_ctx *c) {
@@ -759,6 +802,10 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
     r->Q = (long long)P[1] * r->F2;
     const size_t vol = (size_t)nx * ny * nz;
     DevIn g(grids, 3 * vol * sizeof(float), st);
+    CK(cudaMalloc(&r->grid, 3 * vol * sizeof(float)));
+    CK(cudaMemcpyAsync(r->grid, g.p, 3 * vol * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMalloc(&r->sumsq, 3 * sizeof(double)));
+    launch(c, "k_sumsq", st, [&] { return launch_sumsq(r->grid, (long long)vol, r->sumsq, st); });
     const size_t E = sizeof(cx<ff>);
     CK(cudaMallocAsync(&tz, 3ull * nx * ny * r->F2 * E, st));
     CK(cudaMallocAsync(&ty, 3ull * nx * r->Q * E, st));
@@ -838,6 +885,8 @@ void bpmf_receptor_free(bpmf_rec_t r) {
     if (r->hi) cudaFree(r->hi);
     if (r->lo) cudaFree(r->lo);
     if (r->occ) cudaFree(r->occ);
+    if (r->grid) cudaFree(r->grid);
+    if (r->sumsq) cudaFree(r->sumsq);
   }
   delete r;
 }
@@ -930,12 +979,23 @@ int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_
     CK(cudaMemcpyAsync(lg->R, R, na * sizeof(float), cudaMemcpyDefault, st));
     lg->R_host.resize(na);
     CK(cudaMemcpyAsync(lg->R_host.data(), lg->R, na * sizeof(float), cudaMemcpyDeviceToHost, st));
+    lg->q_host.resize(na);
+    lg->eps_host.resize(na);
+    CK(cudaMemcpyAsync(lg->q_host.data(), lg->q, na * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(lg->eps_host.data(), lg->eps, na * sizeof(float), cudaMemcpyDeviceToHost, st));
+    lg->p_rep = p_rep;
+    lg->p_att = p_att;
+    CK(cudaMalloc(&lg->gamma64, 3 * std::max<size_t>(na, 1) * sizeof(double)));
     CK(cudaMalloc(&lg->coords, std::max<size_t>(1, 3 * lg->total_coord_atoms) * sizeof(float)));
     {
       DevIn dq(q, na * sizeof(float), st), de(eps, na * sizeof(float), st), dr(R, na * sizeof(float), st);
       launch(c, "k_gamma", st, [&] {
         return launch_gamma((const float *)dq.p, (const float *)de.p, (const float *)dr.p, (int)na, p_rep, p_att,
                             lg->gamma, st);
+      });
+      launch(c, "k_gamma64", st, [&] {
+        return launch_gamma64((const float *)dq.p, (const float *)de.p, (const float *)dr.p, (int)na, p_rep, p_att,
+                              lg->gamma64, st);
       });
     }
     if (lg->total_coord_atoms > 0)
@@ -984,6 +1044,7 @@ void bpmf_ligand_free(bpmf_lig_t lg) {
     if (lg->gamma) cudaFree(lg->gamma);
     for (float *p : {lg->q, lg->eps, lg->R})
       if (p) cudaFree(p);
+    if (lg->gamma64) cudaFree(lg->gamma64);
   }
   delete lg;
 }
@@ -1035,6 +1096,8 @@ struct LigPlan {
   std::vector<size_t> off_info;                     // per group: [J][Kg] PairInfo
   std::vector<size_t> off_kmap, off_rptr;           // per group
   std::vector<size_t> off_occ;                      // per group: [Kg] OccTab (unused when occ_cap is 0)
+  std::vector<size_t> off_ref;                      // per group: [Kg] RefTab (refined form)
+  double gnorm[3] = {0, 0, 0};                      // ||gamma_t||_2 of the ligand
   std::vector<int> occ_cap;                         // per group: runs per configuration, 0 without occupancy
   std::vector<int> occ_rb;                          // per group: CTAs per configuration building runs
   std::vector<std::array<int, 3>> Umax;             // per group
@@ -1050,6 +1113,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   const double h = recs[0]->h;
   const bool use_ff = (mode == BPMF_MODE_FF);
   const bool split = (mode == BPMF_MODE_SPLIT_BF16);
+  const bool refine = (mode == BPMF_MODE_REFINE);
   const size_t E = use_ff ? sizeof(cx<ff>) : sizeof(cx<float>);
   const std::vector<RecGroup> groups = group_receptors(recs, K);
   if (split) tc_table(c);
@@ -1100,6 +1164,15 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     ligand_tables(lg, li, recs, K, h, meta, info, nv);
     LigPlan pl;
     pl.li = li;
+    for (int i = 0; i < lg->n_atoms[li]; ++i) {
+      const int ai = lg->atom_off[li] + i;
+      const double q = lg->q_host[ai], se = std::sqrt((double)lg->eps_host[ai]), R = lg->R_host[ai];
+      const double gr = se * std::pow(R, lg->p_rep), ga = se * std::pow(R, lg->p_att);
+      pl.gnorm[0] += q * q;
+      pl.gnorm[1] += gr * gr;
+      pl.gnorm[2] += ga * ga;
+    }
+    for (int t = 0; t < 3; ++t) pl.gnorm[t] = std::sqrt(pl.gnorm[t]);
     pl.J = lg->n_conf[li];
     if (only_conf >= 0) {
       if (only_conf >= pl.J) throw Fail{BPMF_ERR_INVALID_ARG};
@@ -1156,6 +1229,12 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         any_occ = any_occ || r->occ;
       }
       pl.off_occ.push_back(put(ot.data(), sizeof(OccTab) * Kg));
+      std::vector<RefTab> rt(Kg);
+      for (int kg = 0; kg < Kg; ++kg) {
+        const bpmf_rec *r = recs[g.ks[kg]];
+        rt[kg] = RefTab{r->grid, r->sumsq, r->N[0], r->N[1], r->N[2]};
+      }
+      pl.off_ref.push_back(put(rt.data(), sizeof(RefTab) * Kg));
       std::array<int, 3> Um{1, 1, 1};
       for (int i = 0; i < J; ++i)
         for (int d = 0; d < 3; ++d) Um[d] = std::max(Um[d], std::min(meta_s[i].u[d], g.P[d]));
@@ -1190,6 +1269,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       }
       pl.occ_cap.push_back(bg.occ_cap);
       pl.occ_rb.push_back(bg.occ_rb);
+      bg.refine = refine;
       const size_t per_conf = batch_bytes_per_conf(bg, E);
       const size_t part = align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
       const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
@@ -1297,13 +1377,16 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
           gb.K = Kg;
           gb.occ_cap = pl.occ_cap[gi];
           gb.occ_rb = pl.occ_rb[gi];
+          gb.refine = refine;
+          const RefTab *d_rtabs = reinterpret_cast<const RefTab *>(tab + pl.off_ref[gi]);
           const OccTab *d_tabs = reinterpret_cast<const OccTab *>(tab + pl.off_occ[gi]);
           if (use_ff)
             run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, d_rptr + Kg, h, nsh, nsl,
                           esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, false, d_tabs);
           else
             run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, nullptr, h, nsh, nsl,
-                             esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, split, d_tabs);
+                             esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, split, d_tabs,
+                             d_rtabs, pl.gnorm, kT);
         }
         if (export_E) continue;
         MergeArgs ma{};
@@ -1381,7 +1464,7 @@ int eval_entry(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, doubl
                int64_t *n_valid, double *bpmf_out, double *dG, double *psi_min, double *psi_dom, void *stream) {
   if (!c || !lg || !recs || K < 1 || !(kT > 0.0) || (!logZ && lg && lg->total_conf > 0))
     return set_err(c, BPMF_ERR_INVALID_ARG, "null argument, K < 1 or kT <= 0");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16)
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE)
     return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   if (lg->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "ligand batch from another context");
   DeviceGuard dg(c->device);
@@ -1413,7 +1496,7 @@ int bpmf_eval_dominant(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int 
 
 int bpmf_autotune(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, unsigned mode, void *stream) {
   if (!c || !lg || !recs || K < 1 || lg->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or K < 1");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16)
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE)
     return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   DeviceGuard dg(c->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1491,7 +1574,7 @@ int bpmf_export_energies(bpmf_ctx_t c, bpmf_lig_t lg, bpmf_rec_t rec, int lig_in
   if (!c || !lg || !rec || !out || lig_index < 0 || lig_index >= lg->n_lig || conf_index < 0 ||
       conf_index >= lg->n_conf[lig_index])
     return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or index out of range");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16)
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE)
     return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   DeviceGuard dg(c->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1527,7 +1610,7 @@ int bpmf_sir_poses(bpmf_ctx_t c, bpmf_lig_t lg, int lig_index, bpmf_rec_t rec, i
   if (!c || !lg || !rec || !logZ || !n_valid || !u1 || !u2 || !conf || !pose || lig_index < 0 ||
       lig_index >= lg->n_lig || K < 1 || k < 0 || k >= K || !(kT > 0.0) || M < 0)
     return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or index out of range");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16)
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE)
     return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   if (lg->ctx != c || rec->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "handle from another context");
   for (const void *q : {(const void *)logZ, (const void *)n_valid, (const void *)u1, (const void *)u2,

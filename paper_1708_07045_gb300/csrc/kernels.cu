@@ -488,6 +488,7 @@ __global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
     cx<T> *res = cta_fft_auto<T, 20, 256, true>(b0, b1, 1, ls, L, a.plan, s_tw, true);
     const int nS = nrow * a.S2;
     T vmax = s_mk<T>(-CUDART_INF_F, 0.f);
+    float emin = CUDART_INF_F;  // refined form: plane minimum of the energies
     for (int idx = threadIdx.x; idx < nS; idx += blockDim.x) {
       const int r = idx / a.S2, s2 = idx % a.S2, s1 = r0 + r;
       bool ok = row_ok && s1 >= inf.sa[1] && s1 <= inf.sb[1] && s2 >= inf.sa[2] && s2 <= inf.sb[2];
@@ -503,6 +504,15 @@ __global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
         if (ff_gt(x, vmax)) vmax = x;
       }
       xs[idx] = x;
+      if (a.Ebuf) {
+        float ef = CUDART_INF_F;
+        if (ok) {
+          const cx<T> z = res[(r >> 1) * ls + imod(inf.w0[2] + s2, P)];
+          ef = s_hi(s_norm(s_mul((r & 1) ? z.im : z.re, escale)));
+          emin = fminf(emin, ef);
+        }
+        a.Ebuf[(((long long)blockIdx.x * a.S1) + s1) * a.S2 + s2] = ef;
+      }
       if (a.export_E && jk == 0) {
         double e = CUDART_INF;
         if (ok) {
@@ -512,6 +522,17 @@ __global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
         }
         a.export_E[((long long)s0 * a.S1 + s1) * a.S2 + s2] = e;
       }
+    }
+    if (a.Ebuf) {  // plane minimum (s_sum doubles as scratch; it is rewritten below after a barrier)
+      for (int o = 16; o > 0; o >>= 1) emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+      if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = emin;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float v = s_sum[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fminf(v, s_sum[w]);
+        a.plane_min[blockIdx.x] = r0 == 0 ? v : fminf(a.plane_min[blockIdx.x], v);
+      }
+      __syncthreads();
     }
     // block max of the chunk
     for (int o = 16; o > 0; o >>= 1) {

@@ -133,6 +133,8 @@ struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp pa
   const uint32_t *clash;   // optional [batch][K][S0][S1][CW] clash flags (excluded, +inf when exported)
   int CW;
   int Lc;                  // row pairs per shared-memory chunk (set by launch_zinv)
+  float *Ebuf;             // optional [batch][K][S0][S1][S2] energies (+inf masked), refined form
+  float *plane_min;        // with Ebuf: [batch][K][S0] minimum energy of each s0 plane
   FftPlan plan;
   const float4 *tw;
 };
@@ -156,7 +158,35 @@ struct MergeArgs {
                            // receptors, and -kT ln mean_k exp(-min_k / kT) (may be null)
 };
 
-// ---- launch wrappers (kernels.cu, occupancy.cu) -------------------------------
+// ---- refined form (refine.cu) -----------------------------------------------
+struct RefTab {            // one receptor's grids, FP32 [3][N0][N1][N2]
+  const float *grid;
+  const double *sumsq;     // [3] sum of squares of each grid (FP32 error bound)
+  int N0, N1, N2;
+};
+
+struct RefineArgs {
+  const float *E;          // [batch][K][S0][S1][S2] FP32 energies (+inf masked)
+  const float *plane_min;  // [batch][K][S0]
+  const ConfMeta *meta;    // [batch]
+  const PairInfo *info;    // [batch][K]
+  const RefTab *tabs;      // [K]
+  double gnorm[3];         // ||gamma_t||_2 of the ligand (FP32 error bound)
+  double log2P3;           // log2(P0 P1 P2) of the group
+  const float *coords;     // [atoms][3]
+  const double *gamma64;   // [3][gamma_stride] FP64 generalised charges
+  int gamma_stride;
+  double h, kT;
+  int K, S0, S1, S2;
+  float4 *part;            // [batch][K][S0] LSE partials (entry 0 of each pair; the others emptied)
+  double *export_E;        // optional, batch entry 0, receptor 0: [S0][S1][S2] (exact where refined)
+};
+
+// ---- launch wrappers (kernels.cu, occupancy.cu, refine.cu) -------------------
+cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st);
+cudaError_t launch_gamma64(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, double *g,
+                           cudaStream_t st);
+cudaError_t launch_sumsq(const float *g, long long vol, double *out, cudaStream_t st);
 cudaError_t launch_occ_table(const unsigned char *occ, int N0, int N1, int N2, int W, uint32_t *tab,
                              cudaStream_t st);
 cudaError_t launch_occ_runs(const OccRunsArgs &a, int batch, cudaStream_t st);

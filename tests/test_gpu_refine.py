@@ -1,0 +1,125 @@
+"""The refined form (BPMF_MODE_REFINE: FP32 correlation, exact FP64
+re-evaluation of every translation that can carry weight) against the FP64
+oracle, through the C ABI.
+
+Inside the 20 kT window the energies are the exact direct sum, so they match
+the oracle to FP64 rounding (1e-9 of the grid scale).  log Z, BPMF and dG
+must meet the benchmark spec's tolerances (1e-3 and 0.01 kcal/mol); the excluded
+translations weigh less than 1e-5 of S by construction, so the measured error
+is far below."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import sampling as S
+import synth
+
+pytestmark = pytest.mark.gpu
+
+KT = synth.KT
+E_TOL, B_TOL = 1e-3, 1e-2
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    import paper_1708_07045_gb300 as p
+    p.lib()
+    return p
+
+
+def _session():
+    from paper_1708_07045_gb300.session import Session
+    return Session(0)
+
+
+def _scale(r, gam):
+    return sum(np.abs(r.grids[t]).max() * np.abs(gam[t]).sum() for t in range(3))
+
+
+@pytest.mark.parametrize("conf", [0, 7, 30])
+def test_refined_energies_exact_in_window(pkg, conf):
+    w = synth.plain_small(n_conf=32)
+    r, l = w.receptors[0], w.ligands[0]
+    gam = oracle.gamma(l.params.q, l.params.eps, l.params.R)
+    E_ref, _ = oracle.pose_energies(r.grids, r.h, r.site_lo, r.site_n, l.coords[conf], gam)
+    with _session() as s:
+        rh = s.load_receptor(r)
+        lh, _, _ = s.load_ligands([l])
+        E = s.export_energies(lh, rh, 0, conf, r.site_n, pkg.BPMF_MODE_REFINE)
+    assert np.array_equal(np.isinf(E), np.isinf(E_ref))
+    ok = np.isfinite(E_ref)
+    win = ok & (E_ref <= E_ref[ok].min() + 20 * KT)
+    assert np.abs(E[win] - E_ref[win]).max() <= 1e-9 * _scale(r, gam)
+
+
+def test_refined_eval_protein_scale_sample(pkg):
+    w = synth.protein_scale(n_conf=8, n_rec=4)
+    l = w.ligands[0]
+    ref = oracle.evaluate(w.receptors, l.coords, l.params.q, l.params.eps, l.params.R, KT)
+    with _session() as s:
+        rhs = [s.load_receptor(r) for r in w.receptors]
+        lh, _, _ = s.load_ligands([l])
+        _, out = s.eval(lh, rhs, KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=8)
+        pmin = np.empty((8, 4))
+        pdom = np.empty((1, 6))
+        pkg.bpmf_eval_dominant(s.ctx, lh, rhs, KT, pkg.BPMF_MODE_REFINE, np.empty((8, 4)), None, None, None, pmin,
+                               pdom)
+    assert np.array_equal(out["n_valid"], ref["n_valid"])
+    fin = np.isfinite(ref["logZ"])
+    assert np.array_equal(np.isfinite(out["logZ"]), fin)
+    assert np.abs(out["logZ"][fin] - ref["logZ"][fin]).max() * KT <= E_TOL
+    assert np.abs(out["bpmf"][0] - ref["bpmf"]).max() <= B_TOL
+    assert abs(out["dG"][0] - ref["dG"]) <= B_TOL
+    # the minimum is a refined energy: exact
+    assert np.abs(pmin - ref["Emin"]).max() <= 1e-9 * np.abs(ref["Emin"]).max()
+    assert np.abs(pdom[0] - S.dominant(ref["Emin"], KT)).max() <= 1e-6
+
+
+def test_refined_eval_with_clashes(pkg):
+    w = synth.plain_small_occ(n_conf=32)
+    r, l = w.receptors[0], w.ligands[0]
+    ref = oracle.evaluate([r], l.coords, l.params.q, l.params.eps, l.params.R, KT)
+    with _session() as s:
+        rh = s.load_receptor(r)
+        lh, _, _ = s.load_ligands([l])
+        _, out = s.eval(lh, [rh], KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=32)
+    assert np.array_equal(out["n_valid"], ref["n_valid"])
+    fin = np.isfinite(ref["logZ"])
+    assert np.array_equal(np.isfinite(out["logZ"]), fin) and fin.any()
+    assert np.abs(out["logZ"][fin] - ref["logZ"][fin]).max() * KT <= E_TOL
+    assert abs(out["bpmf"][0, 0] - ref["bpmf"][0]) <= B_TOL
+
+
+def test_refined_eval_whole_surface_window(pkg):
+    w = synth.whole_surface(n_conf=2)
+    r0, l = w.receptors[0], w.ligands[0]
+    lo, sn = synth.central_site(r0.shape, 64)
+    r = synth.ReceptorInput(r0.grids, r0.h, r0.origin, lo, sn)
+    ref = oracle.evaluate([r], l.coords, l.params.q, l.params.eps, l.params.R, KT)
+    with _session() as s:
+        rh = s.load_receptor(r)
+        lh, _, _ = s.load_ligands([l])
+        _, out = s.eval(lh, [rh], KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=2)
+    assert np.array_equal(out["n_valid"], ref["n_valid"])
+    assert np.abs(out["logZ"] - ref["logZ"]).max() * KT <= E_TOL
+
+
+def test_refined_matches_float_pairs_on_batches(pkg):
+    """Uneven ligands and receptor groups in one call: the refined and the
+    float-pair forms agree within the tolerance."""
+    w = synth.batched_uneven(n_lig=3, n_conf=24, n_rec=3)
+    with _session() as s:
+        rhs = [s.load_receptor(r) for r in w.receptors]
+        lh, _, nconf = s.load_ligands(w.ligands)
+        T = sum(nconf)
+        _, a = s.eval(lh, rhs, KT, pkg.BPMF_MODE_FF, n_lig=3, total_conf=T)
+        _, b = s.eval(lh, rhs, KT, pkg.BPMF_MODE_REFINE, n_lig=3, total_conf=T)
+    assert np.array_equal(a["n_valid"], b["n_valid"])
+    fin = np.isfinite(a["logZ"])
+    assert np.array_equal(np.isfinite(b["logZ"]), fin)
+    assert np.abs(a["logZ"][fin] - b["logZ"][fin]).max() * KT <= E_TOL
+    okb = np.isfinite(a["bpmf"])
+    assert np.abs(a["bpmf"][okb] - b["bpmf"][okb]).max() <= B_TOL
