@@ -373,7 +373,8 @@ size_t batch_bytes_per_conf(const BatchGeom &g, size_t E) {
   size_t ref = 0;
   if (g.refine)
     ref = align_up((size_t)g.K * g.S[0] * g.S[1] * g.S[2] * sizeof(float)) +
-          align_up((size_t)g.K * g.S[0] * sizeof(float));
+          align_up((size_t)g.K * g.S[0] * sizeof(float)) + align_up((size_t)g.K * sizeof(double)) +
+          2 * align_up((size_t)g.K * sizeof(float));
   return align_up(box) + align_up(lz) + align_up(ly) + align_up(x2) + align_up(y2) + occ + ref;
 }
 
@@ -436,11 +437,19 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     launch(c, "k_clash", st, [&] { return launch_clash(ca, batch, st); });
   }
   float *Ebuf = nullptr, *pmin = nullptr;
+  double *wnd = nullptr;
+  float *pmin_pair = nullptr, *thresh = nullptr;
   if (g.refine) {
     Ebuf = reinterpret_cast<float *>(p);
     p += align_up((size_t)batch * g.K * g.S[0] * g.S[1] * g.S[2] * sizeof(float));
     pmin = reinterpret_cast<float *>(p);
     p += align_up((size_t)batch * g.K * g.S[0] * sizeof(float));
+    wnd = reinterpret_cast<double *>(p);
+    p += align_up((size_t)g.K * sizeof(double));
+    pmin_pair = reinterpret_cast<float *>(p);
+    p += align_up((size_t)batch * g.K * sizeof(float));
+    thresh = reinterpret_cast<float *>(p);
+    p += align_up((size_t)batch * g.K * sizeof(float));
   }
 
   float hh, hl;
@@ -526,7 +535,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   zi.escale_hi = escale_hi;
   zi.escale_lo = escale_lo;
   zi.part = d_part;
-  zi.export_E = g.refine ? nullptr : export_E;
+  zi.export_E = export_E;  // refined form: k_refine rewrites the planes it refines
   zi.Ebuf = Ebuf;
   zi.plane_min = pmin;
   zi.clash = clash;
@@ -548,6 +557,10 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     ra.gamma_stride = (int)lg->total_atoms;
     ra.h = h;
     ra.kT = kT;
+    ra.ikT = (float)(1.0 / kT);
+    ra.window = wnd;
+    ra.pmin_pair = pmin_pair;
+    ra.thresh = thresh;
     ra.K = g.K;
     ra.S0 = g.S[0];
     ra.S1 = g.S[1];

@@ -177,8 +177,12 @@ struct RefineArgs {
   const double *gamma64;   // [3][gamma_stride] FP64 generalised charges
   int gamma_stride;
   double h, kT;
+  float ikT;               // 1 / kT in FP32 (weights outside the window)
+  double *window;          // [K] scratch: W + 2B per receptor (k_window)
+  float *pmin_pair;        // [batch][K] scratch: FP32 minimum per pair
+  float *thresh;           // [batch][K] scratch: threshold per pair
   int K, S0, S1, S2;
-  float4 *part;            // [batch][K][S0] LSE partials (entry 0 of each pair; the others emptied)
+  float4 *part;            // [batch][K][S0] LSE partials (planes with candidates rewritten)
   double *export_E;        // optional, batch entry 0, receptor 0: [S0][S1][S2] (exact where refined)
 };
 

@@ -9,14 +9,16 @@
 // window) keeps the weight of the translations left at their FP32 values
 // below 1e-5 of S.
 //
-// k_refine, one CTA per (configuration, receptor):
-//   * T = min_s0 (plane minimum) + W + 2B;
+// k_window (W + 2B per receptor), k_threshold (per pair: T = FP32 minimum +
+// W + 2B), then k_refine, one CTA per (configuration, receptor, s0 plane);
+// planes whose minimum lies above T keep the FP32 partial of k_zinv (all
+// their weights lie below e^(-W/kT) of the largest), the others:
 //   * every FP32 energy <= T is a candidate; a warp evaluates its
 //     candidates together (lanes over atoms, FP64, shuffle reduction);
 //   * S = sum over candidates of exp(-E_exact/kT) + sum over the others of
-//     exp(-E_fp32/kT), max-shifted, written as one LSE partial of the pair
-//     (the merge is unchanged), and the exported energies (exact where
-//     refined) when asked.
+//     exp(-E_fp32/kT), max-shifted, written as the plane's LSE partial (the
+//     merge is unchanged), and the exported energies (exact where refined)
+//     when asked.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -49,59 +51,55 @@ __device__ __forceinline__ double trilinear64(const float *G, int N0, int N1, in
 __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
   __shared__ double s_g[3][256];    // atom positions in the ligand-box frame (grid units), FP64
   __shared__ double s_gam[3][256];  // gamma_t,i, FP64
-  __shared__ float s_min[8];
-  __shared__ double s_mx[8], s_sm[8], s_non[8];
-  const int pair = blockIdx.x;  // j * K + k
+  __shared__ double s_mx[8], s_sm[8];
+  __shared__ float s_non[8];
+  const int s0 = blockIdx.x % a.S0;
+  const int pair = blockIdx.x / a.S0;  // j * K + k
   const int j = pair / a.K, k = pair % a.K;
+  // the pair's threshold (k_threshold): a plane whose FP32 minimum lies above
+  // it has no candidate, and the FP32 partial k_zinv wrote for it stands
+  const float Tf = a.thresh[pair];
+  const float *pm = a.plane_min + (long long)pair * a.S0;
+  if (!(pm[s0] <= Tf)) return;
   const ConfMeta m = a.meta[j];
   const PairInfo inf = a.info[pair];
   const RefTab t = a.tabs[k];
   const int n = m.n_atoms;
-  const double h = a.h;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float *x = a.coords + 3ll * (m.atom_off + i);
-    for (int d = 0; d < 3; ++d) s_g[d][i] = ((double)x[d] - (double)m.lo[d]) / h + 2.0;
-    for (int c = 0; c < 3; ++c) s_gam[c][i] = a.gamma64[(long long)c * a.gamma_stride + m.gamma_off + i];
-  }
-  // FP32 minimum of the pair
-  const float *pm = a.plane_min + (long long)pair * a.S0;
-  float mn = CUDART_INF_F;
-  for (int s0 = threadIdx.x; s0 < a.S0; s0 += blockDim.x) mn = fminf(mn, pm[s0]);
-  for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-  if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = mn;
-  __syncthreads();
-  float Mf = s_min[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) Mf = fminf(Mf, s_min[w]);
+  const float Mf = a.pmin_pair[pair];
   const double M = (double)Mf;
   const double kT = a.kT;
-  const long long nS = (long long)a.S0 * a.S1 * a.S2;
-  // FP32 correlation error bound B = 8 eps sqrt(log2 P^3) sum_t rms(G_t) ||gamma_t||
-  // and the window W + 2B
-  const double vol = (double)t.N0 * t.N1 * t.N2;
-  double B = 0.0;
-  for (int c = 0; c < 3; ++c) B += sqrt(t.sumsq[c] / vol) * a.gnorm[c];
-  B *= 8.0 * 5.9604644775390625e-08 * sqrt(a.log2P3);
-  const double W = kT * fmax(20.0, log(1e5 * (double)nS));
-  const double T = M + W + 2.0 * B;
-  const float *E = a.E + (long long)pair * nS;
+  {
+    const double h = a.h;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float *x = a.coords + 3ll * (m.atom_off + i);
+      for (int d = 0; d < 3; ++d) s_g[d][i] = ((double)x[d] - (double)m.lo[d]) / h + 2.0;
+      for (int c = 0; c < 3; ++c) s_gam[c][i] = a.gamma64[(long long)c * a.gamma_stride + m.gamma_off + i];
+    }
+    __syncthreads();
+  }
+  const int nP = a.S1 * a.S2;
+  const float *E = a.E + (long long)blockIdx.x * nP;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double mx = -CUDART_INF, sm = 0.0;  // exact candidates, max-shifted (per warp, identical on its lanes)
-  double non = 0.0;                   // the others, relative to exp(-M / kT) (per thread)
-  const bool exp_out = a.export_E && pair == 0;
+  // the others, relative to exp(-M / kT), per thread: each lies below
+  // e^(-W/kT) of the largest weight, so single precision is ample for them
+  float non_f = 0.f;
+  const float ikT = a.ikT;
+  double *expo = (a.export_E && pair == 0) ? a.export_E + (long long)s0 * nP : nullptr;
   if (Mf < CUDART_INF_F) {
-    for (long long b0 = (long long)warp * 32; b0 < nS; b0 += (long long)blockDim.x) {
-      const long long idx = b0 + lane;
-      const float e = idx < nS ? E[idx] : CUDART_INF_F;
+    for (int b0 = warp * 32; b0 < nP; b0 += blockDim.x) {
+      const int idx = b0 + lane;
+      const float e = idx < nP ? E[idx] : CUDART_INF_F;
       const bool fin = e < CUDART_INF_F;
-      const bool cand = fin && (double)e <= T;
-      if (fin && !cand) non += exp(-((double)e - M) / kT);
-      if (exp_out && idx < nS && !cand) a.export_E[idx] = fin ? (double)e : CUDART_INF;
+      const bool cand = fin && e <= Tf;
+      if (fin && !cand) non_f += __expf(-(e - Mf) * ikT);
+      if (expo && idx < nP && !cand) expo[idx] = fin ? (double)e : CUDART_INF;
       unsigned bal = __ballot_sync(0xffffffffu, cand);
       while (bal) {
         const int src = __ffs(bal) - 1;
         bal &= bal - 1;
-        const long long ci = b0 + src;
-        const int s2 = (int)(ci % a.S2), s1 = (int)((ci / a.S2) % a.S1), s0 = (int)(ci / ((long long)a.S1 * a.S2));
+        const int ci = b0 + src;
+        const int s2 = ci % a.S2, s1 = ci / a.S2;
         const double m0 = inf.w0[0] + s0, m1 = inf.w0[1] + s1, m2 = inf.w0[2] + s2;
         double part = 0.0;
         for (int i = lane; i < n; i += 32) {
@@ -118,12 +116,14 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
         } else {
           sm += exp(v - mx);
         }
-        if (exp_out && lane == 0) a.export_E[ci] = ex;
+        if (expo && lane == 0) expo[ci] = ex;
       }
     }
   }
-  // CTA: combine the warps' exact sums and the threads' FP32 remainders
-  non = warp_sum_d(non);
+  // CTA: combine the warps' exact sums and the threads' FP32 remainders into
+  // this plane's LSE partial {level hi, level lo, sum relative to the level}
+  for (int o = 16; o > 0; o >>= 1) non_f += __shfl_xor_sync(0xffffffffu, non_f, o);
+  const float non = non_f;
   if (lane == 0) {
     s_mx[warp] = mx;
     s_sm[warp] = sm;
@@ -133,27 +133,61 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
   if (threadIdx.x == 0) {
     double MX = -CUDART_INF;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) MX = fmax(MX, s_mx[w]);
-    double S = 0.0, NON = 0.0;
+    double S = 0.0, NON = 0.0;  // (NON summed in order from FP32 warp sums)
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      if (s_mx[w] > -CUDART_INF) S += s_sm[w] * exp(s_mx[w] - MX);
+      if (s_mx[w] > -CUDART_INF) S += s_mx[w] == MX ? s_sm[w] : s_sm[w] * exp(s_mx[w] - MX);
       NON += s_non[w];
     }
-    float4 *out = a.part + (long long)pair * a.S0;
-    if (MX > -CUDART_INF) {
+    if (!(MX > -CUDART_INF) && NON > 0.0) {  // no candidate here: level of the FP32 minimum
+      MX = -M / kT;
+      S = NON;
+    } else if (MX > -CUDART_INF && NON > 0.0) {
       S += NON * exp(-M / kT - MX);
-      const float hi = (float)MX;
-      out[0] = make_float4(hi, (float)(MX - (double)hi), (float)S, 0.f);
-    } else {
-      out[0] = make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
     }
+    const float hi = (float)MX;
+    a.part[blockIdx.x] = MX > -CUDART_INF ? make_float4(hi, (float)(MX - (double)hi), (float)S, 0.f)
+                                          : make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
   }
-  for (int s0 = 1 + threadIdx.x; s0 < a.S0; s0 += blockDim.x)
-    a.part[(long long)pair * a.S0 + s0] = make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
+}
+
+// The window W + 2B of every receptor of a batch (one thread each): the FP32
+// correlation error bound B = 8 eps sqrt(log2 P^3) sum_t rms(G_t) ||gamma_t||
+// and W = kT max(20, ln(1e5 n)), n = S0 S1 S2 translations.
+__global__ void k_window(const RefTab *tabs, int K, double g0, double g1, double g2, double log2P3, double kT,
+                         double nS, double *window) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const RefTab t = tabs[k];
+  const double vol = (double)t.N0 * t.N1 * t.N2;
+  const double B = 8.0 * 5.9604644775390625e-08 * sqrt(log2P3) *
+                   (sqrt(t.sumsq[0] / vol) * g0 + sqrt(t.sumsq[1] / vol) * g1 + sqrt(t.sumsq[2] / vol) * g2);
+  window[k] = kT * fmax(20.0, log(1e5 * nS)) + 2.0 * B;
+}
+
+// Per (configuration, receptor): the FP32 minimum over its planes and the
+// threshold, that minimum plus the receptor's window, rounded up to FP32.
+__global__ void k_threshold(const float *plane_min, int n_pairs, int S0, int K, const double *window, float *pmin_pair,
+                            float *thresh) {
+  const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pr >= n_pairs) return;
+  float mn = CUDART_INF_F;
+  for (int q = 0; q < S0; ++q) mn = fminf(mn, plane_min[(long long)pr * S0 + q]);
+  pmin_pair[pr] = mn;
+  thresh[pr] = mn < CUDART_INF_F ? __double2float_ru((double)mn + window[pr % K]) : -CUDART_INF_F;
 }
 
 cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  k_refine<<<(unsigned)(batch * a.K), 256, 0, st>>>(a);
+  k_window<<<(a.K + 127) / 128, 128, 0, st>>>(a.tabs, a.K, a.gnorm[0], a.gnorm[1], a.gnorm[2], a.log2P3, a.kT,
+                                              (double)a.S0 * a.S1 * a.S2, a.window);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n_pairs = batch * a.K;
+  k_threshold<<<(n_pairs + 127) / 128, 128, 0, st>>>(a.plane_min, n_pairs, a.S0, a.K, a.window, a.pmin_pair,
+                                                     a.thresh);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_refine<<<(unsigned)((long long)batch * a.K * a.S0), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
