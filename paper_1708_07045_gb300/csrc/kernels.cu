@@ -23,11 +23,11 @@ __device__ __forceinline__ int imod(int a, int m) {
 // smaller CTAs capped at 128 registers so that 4 can share an SM.
 template <class T>
 struct KCfg {
-  static constexpr int threads = 256, min_blocks = 2, xlw = 16;
+  static constexpr int threads = 256, min_blocks = 2, xlw = 16, x_min_blocks = 3;
 };
 template <>
 struct KCfg<ff> {
-  static constexpr int threads = 128, min_blocks = 4, xlw = 8;
+  static constexpr int threads = 128, min_blocks = 4, xlw = 8, x_min_blocks = 4;
 };
 
 template <class T>
@@ -358,7 +358,7 @@ cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
 // for each receptor k: P_k = sum_t R_{k,t} conj(L_t), inverse DFT, keep the
 // site window along x.  The ligand spectrum never leaves shared memory.
 template <class T>
-__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_xfused(XfusedArgs a, int batch) {
+__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfused(XfusedArgs a, int batch) {
   extern __shared__ float4 smem[];
   constexpr int LW = KCfg<T>::xlw, L3 = 3 * LW;
   const int P = a.plan.n;
