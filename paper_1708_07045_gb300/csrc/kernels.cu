@@ -23,11 +23,11 @@ __device__ __forceinline__ int imod(int a, int m) {
 // smaller CTAs capped at 128 registers so that 4 can share an SM.
 template <class T>
 struct KCfg {
-  static constexpr int threads = 256, min_blocks = 2, xlw = 16, x_min_blocks = 3;
+  static constexpr int threads = 256, min_blocks = 2, xlw = 16, x_min_blocks = 3, a_min_blocks = 3, z_min_blocks = 3;
 };
 template <>
 struct KCfg<ff> {
-  static constexpr int threads = 128, min_blocks = 4, xlw = 8, x_min_blocks = 4;
+  static constexpr int threads = 128, min_blocks = 4, xlw = 8, x_min_blocks = 4, a_min_blocks = 4, z_min_blocks = 4;
 };
 
 template <class T>
@@ -241,7 +241,7 @@ cudaError_t launch_spread(const SpreadArgs &a_in, int batch, cudaStream_t st) {
 // --------------------------------------------------------------------------
 // (b) R2C along the contiguous axis: two real rows packed as one complex line.
 template <class T>
-__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_zfwd(ZfwdArgs a) {
+__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::z_min_blocks) k_zfwd(ZfwdArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, L = a.L, ls = P + 1, F = P / 2 + 1;
   float4 *s_tw = smem;
@@ -301,7 +301,7 @@ cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st) {
 // --------------------------------------------------------------------------
 // C2C along a strided axis for a tile of LW consecutive innermost indices.
 template <class T>
-__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::min_blocks) k_axis(AxisArgs a) {
+__global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::a_min_blocks) k_axis(AxisArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, LW = a.LW;
   float4 *s_tw = smem;
