@@ -454,40 +454,62 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
 
   float hh, hl;
   split_ff(h, hh, hl);
-  SpreadArgs sa{lg->coords, lg->gamma, (int)lg->total_atoms, d_meta, hh, hl, g.U[0], g.U[1], g.U[2], box};
-  launch(c, "k_spread", st, [&] { return launch_spread(sa, batch, st); });
+  if (sizeof(T) == 4 && !split) {
+    // FP32 forms: the y-z spectra straight from the atoms (spreading + z and y passes in one)
+    LigSpecArgs la{};
+    la.coords = lg->coords;
+    la.gamma = lg->gamma;
+    la.gamma_stride = (int)lg->total_atoms;
+    la.meta = d_meta;
+    la.h_hi = hh;
+    la.h_lo = hl;
+    la.U0 = g.U[0];
+    la.U1 = g.U[1];
+    la.U2 = g.U[2];
+    la.P1 = g.P[1];
+    la.P2 = g.P[2];
+    la.F2 = g.F2;
+    la.Q = g.Q;
+    la.tw1 = twiddles(c, g.P[1]);
+    la.tw2 = twiddles(c, g.P[2]);
+    la.ly = reinterpret_cast<float2 *>(ly);
+    launch(c, "k_ligspec", st, [&] { return launch_ligspec(la, batch, st); });
+  } else {
+    SpreadArgs sa{lg->coords, lg->gamma, (int)lg->total_atoms, d_meta, hh, hl, g.U[0], g.U[1], g.U[2], box};
+    launch(c, "k_spread", st, [&] { return launch_spread(sa, batch, st); });
 
-  ZfwdArgs za{};
-  za.in = reinterpret_cast<const float *>(box);
-  za.in_pairs = 1;
-  za.n_rows = 3ll * batch * g.U[0] * g.U[1];
-  za.w_in = g.U[2];
-  za.in_stride = g.U[2];
-  za.out = lz;
-  za.out_stride = g.F2;
-  za.plan = plan(g.P[2]);
-  za.tw = twiddles(c, g.P[2]);
-  za.L = tn.zfwd_l;
-  launch(c, sizeof(T) == 4 ? "k_zfwd<fp32>" : "k_zfwd<ff>", st, [&] { return launch_zfwd<T>(za, st); });
+    ZfwdArgs za{};
+    za.in = reinterpret_cast<const float *>(box);
+    za.in_pairs = 1;
+    za.n_rows = 3ll * batch * g.U[0] * g.U[1];
+    za.w_in = g.U[2];
+    za.in_stride = g.U[2];
+    za.out = lz;
+    za.out_stride = g.F2;
+    za.plan = plan(g.P[2]);
+    za.tw = twiddles(c, g.P[2]);
+    za.L = tn.zfwd_l;
+    launch(c, sizeof(T) == 4 ? "k_zfwd<fp32>" : "k_zfwd<ff>", st, [&] { return launch_zfwd<T>(za, st); });
 
-  AxisArgs ya{};
-  ya.in = lz;
-  ya.out = ly;
-  ya.P = g.P[1];
-  ya.n_in = g.U[1];
-  ya.n_out = g.P[1];
-  ya.n_outer = 3ll * batch * g.U[0];
-  ya.inner = g.F2;
-  ya.in_os = (long long)g.U[1] * g.F2;
-  ya.out_os = (long long)g.P[1] * g.F2;
-  ya.info = nullptr;
-  ya.w0_div = 1;
-  ya.axis = 1;
-  ya.inverse = 0;
-  ya.plan = plan(g.P[1]);
-  ya.tw = twiddles(c, g.P[1]);
-  ya.LW = tn.axis_lw;
-  launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y fwd)" : "k_axis<ff>(y fwd)", st, [&] { return launch_axis<T>(ya, st); });
+    AxisArgs ya{};
+    ya.in = lz;
+    ya.out = ly;
+    ya.P = g.P[1];
+    ya.n_in = g.U[1];
+    ya.n_out = g.P[1];
+    ya.n_outer = 3ll * batch * g.U[0];
+    ya.inner = g.F2;
+    ya.in_os = (long long)g.U[1] * g.F2;
+    ya.out_os = (long long)g.P[1] * g.F2;
+    ya.info = nullptr;
+    ya.w0_div = 1;
+    ya.axis = 1;
+    ya.inverse = 0;
+    ya.plan = plan(g.P[1]);
+    ya.tw = twiddles(c, g.P[1]);
+    ya.LW = tn.axis_lw;
+    launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y fwd)" : "k_axis<ff>(y fwd)", st, [&] { return launch_axis<T>(ya, st); });
+  }
 
   XfusedArgs xa{};
   xa.ly = ly;

@@ -37,6 +37,20 @@ struct SpreadArgs {
   int chunk_rows;          // y rows accumulated per shared-memory pass (set by launch_spread)
 };
 
+struct LigSpecArgs {        // ligand y-z spectra straight from the atoms (FP32 forms)
+  const float *coords;     // [atoms][3]
+  const float2 *gamma;     // [3][total_atoms] float pairs (hi parts used)
+  int gamma_stride;
+  const ConfMeta *meta;    // [batch]
+  float h_hi, h_lo;
+  int U0, U1, U2;          // ligand-box array dims (max over the batch)
+  int P1, P2, F2;          // transform sizes, F2 = P2 / 2 + 1
+  long long Q;             // P1 * F2
+  const float4 *tw1, *tw2; // exp(-2 pi i k / P) tables for P1, P2
+  float2 *ly;              // [batch][3][U0][Q]
+  int chunk;               // atoms per shared-memory pass (set by launch_ligspec)
+};
+
 struct ZfwdArgs {          // real rows -> half spectra along the contiguous axis
   const float *in;         // rows of floats, or of float pairs when in_pairs
   int in_pairs;
@@ -186,7 +200,7 @@ struct RefineArgs {
   double *export_E;        // optional, batch entry 0, receptor 0: [S0][S1][S2] (exact where refined)
 };
 
-// ---- launch wrappers (kernels.cu, occupancy.cu, refine.cu) -------------------
+// ---- launch wrappers (kernels.cu, ligspec.cu, occupancy.cu, refine.cu) ---------
 cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st);
 cudaError_t launch_gamma64(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, double *g,
                            cudaStream_t st);
@@ -196,6 +210,7 @@ cudaError_t launch_occ_table(const unsigned char *occ, int N0, int N1, int N2, i
 cudaError_t launch_occ_runs(const OccRunsArgs &a, int batch, cudaStream_t st);
 cudaError_t launch_clash(ClashArgs a, int batch, cudaStream_t st);
 cudaError_t launch_spread(const SpreadArgs &a, int batch, cudaStream_t st);
+cudaError_t launch_ligspec(const LigSpecArgs &a, int batch, cudaStream_t st);
 template <class T> cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st);
 template <class T> cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st);
 template <class T> cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st);
