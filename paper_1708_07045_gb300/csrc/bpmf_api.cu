@@ -71,6 +71,15 @@ struct bpmf_rec {
   int occW = 0;
   float *grid = nullptr;                // the FP32 grids [3][N0][N1][N2] (refined form)
   double *sumsq = nullptr;              // [3] their sums of squares (FP32 error bound)
+  // spectra of the grids cropped to a box of transform edges P around the
+  // site, made on first use, per P (the uncropped spectrum is hi / lo)
+  struct Crop {
+    int c0[3] = {0, 0, 0};              // first node of the crop
+    float2 *hi = nullptr, *lo = nullptr;  // [3][P0][P1 (P2/2+1)]
+    double *sumsq = nullptr;            // [3] over the cropped nodes
+    double vol = 0;                     // cropped nodes per channel
+  };
+  std::map<std::array<int, 3>, Crop> crops;
 };
 
 struct bpmf_lig {
@@ -632,6 +641,7 @@ void ligand_tables(const bpmf_lig *lg, int li, const bpmf_rec_t *recs, int K, do
         const int sa = std::max(0, -w0);
         const int sb = std::min(recs[k]->site_n[d] - 1, recs[k]->N[d] - 1 - m.u[d] - w0);
         pi.w0[d] = w0;
+        pi.wc[d] = w0;  // uncropped transforms
         pi.sa[d] = sa;
         pi.sb[d] = sb;
         n *= (sb >= sa) ? (sb - sa + 1) : 0;
@@ -803,6 +813,190 @@ void bpmf_destroy(bpmf_ctx_t c) {
   delete c;
 }
 
+namespace {
+
+// Spectra of nrec receptors' three grids, src [nrec][3][e0][e1][e2]
+// zero-padded to transform edges P (Eq. fft_correlation_func, receptor side):
+// z R2C, then y and x C2C, in float pairs, split into each receptor's hi / lo
+// planes [3][P0][P1 (P2/2+1)].
+void grid_spectrum(bpmf_ctx *c, const float *src, int nrec, const int e[3], const int P[3], float2 *const *hi,
+                   float2 *const *lo, cudaStream_t st) {
+  const int F2 = P[2] / 2 + 1;
+  const long long Q = (long long)P[1] * F2;
+  const long long nch = 3ll * nrec;
+  const size_t E = sizeof(cx<ff>);
+  void *tz = nullptr, *ty = nullptr, *tx = nullptr;
+  try {
+    CK(cudaMallocAsync(&tz, nch * e[0] * e[1] * F2 * E, st));
+    CK(cudaMallocAsync(&ty, nch * e[0] * Q * E, st));
+    CK(cudaMallocAsync(&tx, nch * P[0] * Q * E, st));
+    // z: R2C of every (channel, x, y) row
+    ZfwdArgs za{};
+    za.in = src;
+    za.n_rows = nch * e[0] * e[1];
+    za.w_in = e[2];
+    za.in_stride = e[2];
+    za.out = tz;
+    za.out_stride = F2;
+    za.plan = make_plan(P[2]);
+    za.tw = twiddles(c, P[2]);
+    za.L = 16;
+    launch(c, "k_zfwd<ff>(receptor)", st, [&] { return launch_zfwd<ff>(za, st); });
+    // y
+    AxisArgs ya{};
+    ya.in = tz;
+    ya.out = ty;
+    ya.P = P[1];
+    ya.n_in = e[1];
+    ya.n_out = P[1];
+    ya.n_outer = nch * e[0];
+    ya.inner = F2;
+    ya.in_os = (long long)e[1] * F2;
+    ya.out_os = Q;
+    ya.w0_div = 1;
+    ya.axis = 1;
+    ya.plan = make_plan(P[1]);
+    ya.tw = twiddles(c, P[1]);
+    ya.LW = 16;
+    launch(c, "k_axis<ff>(receptor y)", st, [&] { return launch_axis<ff>(ya, st); });
+    // x
+    AxisArgs xa{};
+    xa.in = ty;
+    xa.out = tx;
+    xa.P = P[0];
+    xa.n_in = e[0];
+    xa.n_out = P[0];
+    xa.n_outer = nch;
+    xa.inner = Q;
+    xa.in_os = (long long)e[0] * Q;
+    xa.out_os = (long long)P[0] * Q;
+    xa.w0_div = 1;
+    xa.axis = 0;
+    xa.plan = make_plan(P[0]);
+    xa.tw = twiddles(c, P[0]);
+    xa.LW = 16;
+    launch(c, "k_axis<ff>(receptor x)", st, [&] { return launch_axis<ff>(xa, st); });
+    for (int m = 0; m < nrec; ++m) {
+      const cx<ff> *spec = static_cast<const cx<ff> *>(tx) + 3ll * m * P[0] * Q;
+      launch(c, "k_split_ff", st, [&] { return launch_split_ff(spec, hi[m], lo[m], 3ll * P[0] * Q, st); });
+    }
+    CK(cudaFreeAsync(tz, st));
+    tz = nullptr;
+    CK(cudaFreeAsync(ty, st));
+    ty = nullptr;
+    CK(cudaFreeAsync(tx, st));
+    tx = nullptr;
+  } catch (Fail) {
+    if (tz) cudaFreeAsync(tz, st);
+    if (ty) cudaFreeAsync(ty, st);
+    if (tx) cudaFreeAsync(tx, st);
+    throw;
+  }
+}
+
+int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Views of receptors' spectra for transform edges Pc <= P: the stored one of
+// a receptor when Pc == P, else its grids cropped to Pc nodes per axis around
+// the site.  Crops made on first use (stream st) are transformed together.
+// Every node that a translation of the site window reaches with a ligand box
+// of edge u lies in the crop when Pc >= site_n + u - 1: the crop starts
+// floor((site_n - Pc) / 2) nodes from the site, moved inside the grid.
+std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *> &rs, const std::array<int, 3> &Pc,
+                                      cudaStream_t st, bool &made) {
+  std::vector<bpmf_rec::Crop> out(rs.size());
+  std::vector<size_t> todo;
+  std::vector<std::array<int, 3>> ext;
+  std::vector<int> alias(rs.size(), -1);  // a receptor passed more than once
+  int Emax[3] = {1, 1, 1};
+  for (size_t m = 0; m < rs.size(); ++m) {
+    bpmf_rec *r = rs[m];
+    for (size_t m2 = 0; m2 < m && alias[m] < 0; ++m2)
+      if (rs[m2] == r) alias[m] = (int)m2;
+    if (alias[m] >= 0) continue;
+    if (Pc[0] == r->P[0] && Pc[1] == r->P[1] && Pc[2] == r->P[2]) {
+      out[m].hi = r->hi;
+      out[m].lo = r->lo;
+      out[m].sumsq = r->sumsq;
+      out[m].vol = (double)r->N[0] * r->N[1] * r->N[2];
+      continue;
+    }
+    auto it = r->crops.find(Pc);
+    if (it != r->crops.end()) {
+      out[m] = it->second;
+      continue;
+    }
+    std::array<int, 3> e{};
+    for (int d = 0; d < 3; ++d) {
+      const int c0 = r->site_lo[d] + floor_div(r->site_n[d] - Pc[d], 2);
+      out[m].c0[d] = std::max(0, std::min(c0, std::max(0, r->N[d] - Pc[d])));
+      e[d] = std::min(Pc[d], r->N[d] - out[m].c0[d]);
+      Emax[d] = std::max(Emax[d], e[d]);
+    }
+    out[m].vol = (double)e[0] * e[1] * e[2];
+    todo.push_back(m);
+    ext.push_back(e);
+  }
+  auto resolve = [&] {
+    for (size_t m = 0; m < rs.size(); ++m)
+      if (alias[m] >= 0) out[m] = out[alias[m]];
+  };
+  if (todo.empty()) {
+    resolve();
+    return out;
+  }
+  const int n = (int)todo.size();
+  const long long Q = (long long)Pc[1] * (Pc[2] / 2 + 1);
+  const long long chan = (long long)Emax[0] * Emax[1] * Emax[2];
+  float *buf = nullptr;
+  std::vector<float2 *> his(n, nullptr), los(n, nullptr);
+  try {
+    for (int i = 0; i < n; ++i) {
+      bpmf_rec::Crop &cr = out[todo[i]];
+      CK(cudaMalloc(&cr.hi, 3ull * Pc[0] * Q * sizeof(float2)));
+      CK(cudaMalloc(&cr.lo, 3ull * Pc[0] * Q * sizeof(float2)));
+      CK(cudaMalloc(&cr.sumsq, 3 * sizeof(double)));
+      his[i] = cr.hi;
+      los[i] = cr.lo;
+    }
+    CK(cudaMallocAsync(&buf, 3ull * n * chan * sizeof(float), st));
+    for (int i = 0; i < n; ++i) {
+      bpmf_rec *r = rs[todo[i]];
+      bpmf_rec::Crop &cr = out[todo[i]];
+      const int e[3] = {ext[i][0], ext[i][1], ext[i][2]};
+      float *dst = buf + 3ll * i * chan;
+      launch(c, "k_crop", st, [&] { return launch_crop(r->grid, r->N, cr.c0, e, Emax, dst, cr.sumsq, st); });
+    }
+    const int P3[3] = {Pc[0], Pc[1], Pc[2]};
+    grid_spectrum(c, buf, n, Emax, P3, his.data(), los.data(), st);
+    CK(cudaFreeAsync(buf, st));
+    buf = nullptr;
+  } catch (Fail) {
+    if (buf) cudaFreeAsync(buf, st);
+    cudaStreamSynchronize(st);
+    for (int i = 0; i < n; ++i) {
+      bpmf_rec::Crop &cr = out[todo[i]];
+      if (cr.hi) cudaFree(cr.hi);
+      if (cr.lo) cudaFree(cr.lo);
+      if (cr.sumsq) cudaFree(cr.sumsq);
+    }
+    throw;
+  }
+  for (int i = 0; i < n; ++i) rs[todo[i]]->crops[Pc] = out[todo[i]];
+  made = true;
+  resolve();
+  return out;
+}
+
+// Transform edge of a crop that holds a reach of W nodes: the full edge P,
+// or the smooth edge near 5P/6 when W fits in it.
+int crop_edge(int W, int P) {
+  const int p1 = smooth_edge((5 * P + 5) / 6);
+  return (p1 > 0 && p1 < P && W <= p1) ? p1 : P;
+}
+
+}  // namespace
+
 int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz, double h, const double origin[3],
                        const int site_lo[3], const int site_n[3], void *stream, bpmf_rec_t *out) {
   if (!c || !out || !grids || !site_lo || !site_n) return set_err(c, BPMF_ERR_INVALID_ARG, "null argument");
@@ -821,7 +1015,6 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
   cudaStream_t st = (cudaStream_t)stream;
   bpmf_rec *r = new (std::nothrow) bpmf_rec();
   if (!r) return set_err(c, BPMF_ERR_OOM, "host allocation");
-  void *tz = nullptr, *ty = nullptr, *tx = nullptr;
   try {
     r->ctx = c;
     r->id = c->next_id++;
@@ -841,70 +1034,11 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
     CK(cudaMemcpyAsync(r->grid, g.p, 3 * vol * sizeof(float), cudaMemcpyDeviceToDevice, st));
     CK(cudaMalloc(&r->sumsq, 3 * sizeof(double)));
     launch(c, "k_sumsq", st, [&] { return launch_sumsq(r->grid, (long long)vol, r->sumsq, st); });
-    const size_t E = sizeof(cx<ff>);
-    CK(cudaMallocAsync(&tz, 3ull * nx * ny * r->F2 * E, st));
-    CK(cudaMallocAsync(&ty, 3ull * nx * r->Q * E, st));
-    CK(cudaMallocAsync(&tx, 3ull * P[0] * r->Q * E, st));
     CK(cudaMalloc(&r->hi, 3ull * P[0] * r->Q * sizeof(float2)));
     CK(cudaMalloc(&r->lo, 3ull * P[0] * r->Q * sizeof(float2)));
-    // z: R2C of every (t, x, y) row
-    ZfwdArgs za{};
-    za.in = static_cast<const float *>(g.p);
-    za.n_rows = 3ll * nx * ny;
-    za.w_in = nz;
-    za.in_stride = nz;
-    za.out = tz;
-    za.out_stride = r->F2;
-    za.plan = make_plan(P[2]);
-    za.tw = twiddles(c, P[2]);
-    za.L = 16;
-    launch(c, "k_zfwd<ff>(receptor)", st, [&] { return launch_zfwd<ff>(za, st); });
-    // y
-    AxisArgs ya{};
-    ya.in = tz;
-    ya.out = ty;
-    ya.P = P[1];
-    ya.n_in = ny;
-    ya.n_out = P[1];
-    ya.n_outer = 3ll * nx;
-    ya.inner = r->F2;
-    ya.in_os = (long long)ny * r->F2;
-    ya.out_os = r->Q;
-    ya.w0_div = 1;
-    ya.axis = 1;
-    ya.plan = make_plan(P[1]);
-    ya.tw = twiddles(c, P[1]);
-    ya.LW = 16;
-    launch(c, "k_axis<ff>(receptor y)", st, [&] { return launch_axis<ff>(ya, st); });
-    // x
-    AxisArgs xa{};
-    xa.in = ty;
-    xa.out = tx;
-    xa.P = P[0];
-    xa.n_in = nx;
-    xa.n_out = P[0];
-    xa.n_outer = 3;
-    xa.inner = r->Q;
-    xa.in_os = (long long)nx * r->Q;
-    xa.out_os = (long long)P[0] * r->Q;
-    xa.w0_div = 1;
-    xa.axis = 0;
-    xa.plan = make_plan(P[0]);
-    xa.tw = twiddles(c, P[0]);
-    xa.LW = 16;
-    launch(c, "k_axis<ff>(receptor x)", st, [&] { return launch_axis<ff>(xa, st); });
-    launch(c, "k_split_ff", st, [&] { return launch_split_ff(tx, r->hi, r->lo, 3ll * P[0] * r->Q, st); });
-    CK(cudaFreeAsync(tz, st));
-    tz = nullptr;
-    CK(cudaFreeAsync(ty, st));
-    ty = nullptr;
-    CK(cudaFreeAsync(tx, st));
-    tx = nullptr;
+    grid_spectrum(c, static_cast<const float *>(g.p), 1, N, P, &r->hi, &r->lo, st);
     if (!is_device_ptr(grids)) CK(cudaStreamSynchronize(st));
   } catch (Fail f) {
-    if (tz) cudaFreeAsync(tz, st);
-    if (ty) cudaFreeAsync(ty, st);
-    if (tx) cudaFreeAsync(tx, st);
     bpmf_receptor_free(r);
     return set_err(c, f.code, last_msg);
   }
@@ -922,6 +1056,11 @@ void bpmf_receptor_free(bpmf_rec_t r) {
     if (r->occ) cudaFree(r->occ);
     if (r->grid) cudaFree(r->grid);
     if (r->sumsq) cudaFree(r->sumsq);
+    for (auto &kv : r->crops) {
+      if (kv.second.hi) cudaFree(kv.second.hi);
+      if (kv.second.lo) cudaFree(kv.second.lo);
+      if (kv.second.sumsq) cudaFree(kv.second.sumsq);
+    }
   }
   delete r;
 }
@@ -1125,19 +1264,31 @@ bpmf_ctx::Tune tune_for(bpmf_ctx *c, const int P[3], unsigned mode) {
 // Host plan of one bpmf_eval call: every table of every ligand and receptor
 // group lives in one pinned blob uploaded with a single copy, so the execute
 // phase issues no host-synchronising call and can be captured as a graph.
+// Configurations of one group that share a crop of every receptor grid of the
+// group (transform edges P): contiguous processing positions [j0, j1).
+struct BucketPlan {
+  int P[3] = {0, 0, 0}, F2 = 0;
+  long long Q = 0;
+  int j0 = 0, j1 = 0;
+  int B = 1;                           // configurations per batch
+  size_t off_rptr = 0, off_ref = 0;    // blob: [2 Kg] spectrum pointers (hi, then lo), [Kg] RefTab
+  std::vector<std::array<int, 3>> Ub;  // ligand box per batch
+};
+
+struct GroupPlan {
+  size_t off_meta = 0, off_order = 0;  // blob: [J] ConfMeta and caller's index, processing order
+  size_t off_info = 0;                 // blob: [J][Kg] PairInfo, processing order
+  size_t off_kmap = 0, off_occ = 0;    // blob: [Kg] receptor index, [Kg] OccTab
+  int occ_cap = 0;                     // occupancy runs per configuration, 0 without occupancy
+  int occ_rb = 1;                      // CTAs per configuration building runs
+  std::vector<BucketPlan> buckets;
+};
+
 struct LigPlan {
   int li = 0, J = 0, j_first = 0;
-  size_t off_meta = 0, off_order = 0, off_nv = 0;   // blob offsets
-  std::vector<size_t> off_info;                     // per group: [J][Kg] PairInfo
-  std::vector<size_t> off_kmap, off_rptr;           // per group
-  std::vector<size_t> off_occ;                      // per group: [Kg] OccTab (unused when occ_cap is 0)
-  std::vector<size_t> off_ref;                      // per group: [Kg] RefTab (refined form)
-  double gnorm[3] = {0, 0, 0};                      // ||gamma_t||_2 of the ligand
-  std::vector<int> occ_cap;                         // per group: runs per configuration, 0 without occupancy
-  std::vector<int> occ_rb;                          // per group: CTAs per configuration building runs
-  std::vector<std::array<int, 3>> Umax;             // per group
-  std::vector<std::vector<std::array<int, 3>>> Ub;  // per group, per batch
-  std::vector<int> B;                               // per group batch size
+  size_t off_nv = 0;                   // blob: [J][K] valid counts, caller's order
+  double gnorm[3] = {0, 0, 0};         // ||gamma_t||_2 of the ligand
+  std::vector<GroupPlan> gp;           // per receptor group
   size_t fixed = 0, batch_bytes = 0;
 };
 
@@ -1195,6 +1346,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   std::vector<PairInfo> info;
   std::vector<long long> nv;
   size_t ws_need = 0;
+  bool crops_made = false;
   for (int li = lig_begin; li < lig_end; ++li) {
     ligand_tables(lg, li, recs, K, h, meta, info, nv);
     LigPlan pl;
@@ -1215,47 +1367,48 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       pl.J = 1;
     }
     const int J = pl.J;
-    // process configurations sorted by ligand-box extent, so each batch's box
-    // (the maximum over its members) stays tight; the merge scatters results
-    // back to the caller's order
-    std::vector<int> order(J);
-    for (int i = 0; i < J; ++i) order[i] = pl.j_first + i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-      for (int d = 0; d < 3; ++d)
-        if (meta[a].u[d] != meta[b].u[d]) return meta[a].u[d] < meta[b].u[d];
-      return false;
-    });
-    std::vector<ConfMeta> meta_s(std::max(J, 1));
-    std::vector<long long> nv_s((size_t)std::max(J, 1) * K);
-    std::vector<int> ord_s(std::max(J, 1));
-    for (int i = 0; i < J; ++i) {
-      meta_s[i] = meta[order[i]];
-      ord_s[i] = order[i] - pl.j_first;
+    std::vector<long long> nv_c((size_t)std::max(J, 1) * K);
+    for (int i = 0; i < J; ++i)
       for (int k = 0; k < K; ++k) {
-        nv_s[(size_t)i * K + k] = nv[(size_t)order[i] * K + k];
-        if (nv_s[(size_t)i * K + k] == 0) warn = true;
+        nv_c[(size_t)i * K + k] = nv[(size_t)(pl.j_first + i) * K + k];
+        if (nv_c[(size_t)i * K + k] == 0) warn = true;
       }
-    }
-    pl.off_meta = put(meta_s.data(), sizeof(ConfMeta) * J);
-    pl.off_order = put(ord_s.data(), sizeof(int) * J);
-    pl.off_nv = put(nv_s.data(), sizeof(long long) * J * K);
+    pl.off_nv = put(nv_c.data(), sizeof(long long) * J * K);
     const size_t JK = (size_t)std::max(J, 1) * K;
     size_t fixed = align_up(sizeof(long long) * JK) + align_up(sizeof(double) * JK) * 3 +
                    align_up(sizeof(double) * (2 * K + 3));
     size_t batch_bytes = 0;
     for (const auto &g : groups) {
       const int Kg = (int)g.ks.size();
-      std::vector<PairInfo> info_g((size_t)std::max(J, 1) * Kg);
+      GroupPlan gpn;
+      const ConfMeta *mj = meta.data() + pl.j_first;
+      // transform edges per configuration: a crop edge that holds every
+      // receptor node the site windows of the group reach with this
+      // configuration's ligand box (the split-bf16 form keeps the full edges)
+      std::vector<std::array<int, 3>> pc(std::max(J, 1));
       for (int i = 0; i < J; ++i)
-        for (int kg = 0; kg < Kg; ++kg) info_g[(size_t)i * Kg + kg] = info[(size_t)order[i] * K + g.ks[kg]];
-      pl.off_info.push_back(put(info_g.data(), sizeof(PairInfo) * J * Kg));
-      pl.off_kmap.push_back(put(g.ks.data(), sizeof(int) * Kg));
-      std::vector<const float2 *> rp(2 * Kg);
-      for (int kg = 0; kg < Kg; ++kg) {
-        rp[kg] = recs[g.ks[kg]]->hi;
-        rp[Kg + kg] = recs[g.ks[kg]]->lo;
-      }
-      pl.off_rptr.push_back(put(rp.data(), sizeof(void *) * 2 * Kg));
+        for (int d = 0; d < 3; ++d) {
+          int W = 0;
+          for (int kg = 0; kg < Kg; ++kg)
+            W = std::max(W, recs[g.ks[kg]]->site_n[d] + std::min(mj[i].u[d], g.P[d]) - 1);
+          pc[i][d] = split ? g.P[d] : crop_edge(W, g.P[d]);
+        }
+      // processing order: by crop, then by ligand-box extent, so each batch's
+      // box (the maximum over its members) stays tight; the merge scatters
+      // results back to the caller's order
+      std::vector<int> order(std::max(J, 1), 0);
+      for (int i = 0; i < J; ++i) order[i] = i;
+      std::stable_sort(order.begin(), order.begin() + J, [&](int a, int b) {
+        if (pc[a] != pc[b]) return pc[a] < pc[b];
+        for (int d = 0; d < 3; ++d)
+          if (mj[a].u[d] != mj[b].u[d]) return mj[a].u[d] < mj[b].u[d];
+        return false;
+      });
+      std::vector<ConfMeta> meta_s(std::max(J, 1));
+      for (int i = 0; i < J; ++i) meta_s[i] = mj[order[i]];
+      gpn.off_meta = put(meta_s.data(), sizeof(ConfMeta) * J);
+      gpn.off_order = put(order.data(), sizeof(int) * J);
+      gpn.off_kmap = put(g.ks.data(), sizeof(int) * Kg);
       std::vector<OccTab> ot(Kg);
       bool any_occ = false;
       for (int kg = 0; kg < Kg; ++kg) {
@@ -1263,26 +1416,13 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         ot[kg] = OccTab{r->occ, r->N[0], r->N[1], r->N[2], r->occW};
         any_occ = any_occ || r->occ;
       }
-      pl.off_occ.push_back(put(ot.data(), sizeof(OccTab) * Kg));
-      std::vector<RefTab> rt(Kg);
-      for (int kg = 0; kg < Kg; ++kg) {
-        const bpmf_rec *r = recs[g.ks[kg]];
-        rt[kg] = RefTab{r->grid, r->sumsq, r->N[0], r->N[1], r->N[2]};
-      }
-      pl.off_ref.push_back(put(rt.data(), sizeof(RefTab) * Kg));
+      gpn.off_occ = put(ot.data(), sizeof(OccTab) * Kg);
       std::array<int, 3> Um{1, 1, 1};
       for (int i = 0; i < J; ++i)
         for (int d = 0; d < 3; ++d) Um[d] = std::max(Um[d], std::min(meta_s[i].u[d], g.P[d]));
       Um[1] += Um[1] & 1;
-      pl.Umax.push_back(Um);
       BatchGeom bg{};
-      for (int d = 0; d < 3; ++d) {
-        bg.U[d] = Um[d];
-        bg.P[d] = g.P[d];
-        bg.S[d] = g.S[d];
-      }
-      bg.F2 = g.F2;
-      bg.Q = g.Q;
+      for (int d = 0; d < 3; ++d) bg.S[d] = g.S[d];
       bg.K = Kg;
       if (any_occ && J > 0) {
         float rmax = 0.f;
@@ -1302,28 +1442,69 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         const long long rows = (long long)(Um[0] + 2 * (int)std::ceil(rmax) + 4) * (Um[1] + 2 * (int)std::ceil(rmax) + 4);
         bg.occ_rb = (int)std::max<long long>(1, std::min<long long>(32, (rows + 255) / 256));
       }
-      pl.occ_cap.push_back(bg.occ_cap);
-      pl.occ_rb.push_back(bg.occ_rb);
+      gpn.occ_cap = bg.occ_cap;
+      gpn.occ_rb = bg.occ_rb;
       bg.refine = refine;
-      const size_t per_conf = batch_bytes_per_conf(bg, E);
       const size_t part = align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
       const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
-      int B = (int)std::max<size_t>(1, (c->ws_budget > fixed + part ? c->ws_budget - fixed - part : 0) / per_conf);
-      if (tn.batch_cap > 0) B = std::min(B, tn.batch_cap);
-      B = std::min(B, std::max(J, 1));
-      pl.B.push_back(B);
-      std::vector<std::array<int, 3>> ub;
-      for (int b0 = 0; b0 < J; b0 += B) {
-        std::array<int, 3> U{1, 1, 1};
-        for (int i = b0; i < std::min(J, b0 + B); ++i)
-          for (int d = 0; d < 3; ++d) U[d] = std::max(U[d], std::min(meta_s[i].u[d], g.P[d]));
-        // z rows are transformed in (y, y+1) pairs: an even y extent keeps each
-        // pair inside one plane, so results do not depend on the batching
-        U[1] += U[1] & 1;
-        ub.push_back(U);
+      std::vector<PairInfo> info_g((size_t)std::max(J, 1) * Kg);
+      for (int j0 = 0; j0 < J;) {
+        int j1 = j0;
+        while (j1 < J && pc[order[j1]] == pc[order[j0]]) ++j1;
+        BucketPlan bk;
+        const std::array<int, 3> Pc = pc[order[j0]];
+        for (int d = 0; d < 3; ++d) bk.P[d] = Pc[d];
+        bk.F2 = Pc[2] / 2 + 1;
+        bk.Q = (long long)Pc[1] * bk.F2;
+        bk.j0 = j0;
+        bk.j1 = j1;
+        std::vector<const float2 *> rp(2 * Kg);
+        std::vector<RefTab> rt(Kg);
+        std::vector<bpmf_rec *> rg(Kg);
+        for (int kg = 0; kg < Kg; ++kg) rg[kg] = recs[g.ks[kg]];
+        const std::vector<bpmf_rec::Crop> crs = rec_crops(c, rg, Pc, st, crops_made);
+        for (int kg = 0; kg < Kg; ++kg) {
+          bpmf_rec *r = rg[kg];
+          const bpmf_rec::Crop &cr = crs[kg];
+          rp[kg] = cr.hi;
+          rp[Kg + kg] = cr.lo;
+          rt[kg] = RefTab{r->grid, cr.sumsq, r->N[0], r->N[1], r->N[2], cr.vol};
+          for (int i = j0; i < j1; ++i) {
+            PairInfo pi = info[(size_t)(pl.j_first + order[i]) * K + g.ks[kg]];
+            for (int d = 0; d < 3; ++d) pi.wc[d] = pi.w0[d] - cr.c0[d];
+            info_g[(size_t)i * Kg + kg] = pi;
+          }
+        }
+        bk.off_rptr = put(rp.data(), sizeof(void *) * 2 * Kg);
+        bk.off_ref = put(rt.data(), sizeof(RefTab) * Kg);
+        for (int d = 0; d < 3; ++d) twiddles(c, Pc[d]);
+        BatchGeom bb = bg;
+        for (int d = 0; d < 3; ++d) {
+          bb.U[d] = std::min(Um[d], Pc[d]);
+          bb.P[d] = Pc[d];
+        }
+        bb.F2 = bk.F2;
+        bb.Q = bk.Q;
+        const size_t per_conf = batch_bytes_per_conf(bb, E);
+        int B = (int)std::max<size_t>(1, (c->ws_budget > fixed + part ? c->ws_budget - fixed - part : 0) / per_conf);
+        if (tn.batch_cap > 0) B = std::min(B, tn.batch_cap);
+        B = std::min(B, j1 - j0);
+        bk.B = B;
+        for (int b0 = j0; b0 < j1; b0 += B) {
+          std::array<int, 3> U{1, 1, 1};
+          for (int i = b0; i < std::min(j1, b0 + B); ++i)
+            for (int d = 0; d < 3; ++d) U[d] = std::max(U[d], std::min(meta_s[i].u[d], Pc[d]));
+          // z rows are transformed in (y, y+1) pairs: an even y extent keeps each
+          // pair inside one plane, so results do not depend on the batching
+          U[1] += U[1] & 1;
+          bk.Ub.push_back(U);
+        }
+        batch_bytes = std::max(batch_bytes, part + per_conf * B);
+        gpn.buckets.push_back(std::move(bk));
+        j0 = j1;
       }
-      pl.Ub.push_back(ub);
-      batch_bytes = std::max(batch_bytes, part + per_conf * B);
+      gpn.off_info = put(info_g.data(), sizeof(PairInfo) * J * Kg);
+      pl.gp.push_back(std::move(gpn));
     }
     pl.fixed = fixed;
     pl.batch_bytes = batch_bytes;
@@ -1355,6 +1536,9 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   if (!blob.empty()) std::memcpy(c->pinned, blob.data(), blob.size());
   for (const auto &g : groups)
     for (int d = 0; d < 3; ++d) twiddles(c, g.P[d]);
+  // new receptor crops were made on this stream: complete them before any
+  // other stream can read them
+  if (crops_made) CK(cudaStreamSynchronize(st));
   c->warn_last = warn;
 
   // -------------------------------------------------------------- execute
@@ -1383,52 +1567,53 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       double *d_B = reinterpret_cast<double *>(p);
       p += align_up(sizeof(double) * (2 * K + 3));  // bpmf [K], dG, dominant-state [K + 2]
       char *d_grp = p;  // partials + batch buffers, reused group by group
-      const ConfMeta *d_meta = reinterpret_cast<const ConfMeta *>(tab + pl.off_meta);
-      const int *d_order = reinterpret_cast<const int *>(tab + pl.off_order);
       const long long *d_nv = reinterpret_cast<const long long *>(tab + pl.off_nv);
       for (size_t gi = 0; gi < groups.size(); ++gi) {
         const RecGroup &g = groups[gi];
+        const GroupPlan &gp = pl.gp[gi];
         const int Kg = (int)g.ks.size();
-        const PairInfo *d_info = reinterpret_cast<const PairInfo *>(tab + pl.off_info[gi]);
-        const float2 *const *d_rptr = reinterpret_cast<const float2 *const *>(tab + pl.off_rptr[gi]);
+        const ConfMeta *d_meta = reinterpret_cast<const ConfMeta *>(tab + gp.off_meta);
+        const PairInfo *d_info = reinterpret_cast<const PairInfo *>(tab + gp.off_info);
+        const OccTab *d_tabs = reinterpret_cast<const OccTab *>(tab + gp.off_occ);
         float4 *d_part = reinterpret_cast<float4 *>(d_grp);
         char *d_batch = d_grp + align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
-        const double norm = 1.0 / ((double)g.P[0] * g.P[1] * g.P[2]);
-        float nsh, nsl, esh, esl;
-        split_ff(-norm / kT, nsh, nsl);
-        split_ff(norm, esh, esl);
         const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
-        const int B = pl.B[gi];
-        for (int b0 = 0, bi = 0; b0 < J; b0 += B, ++bi) {
-          const int nb = std::min(B, J - b0);
-          BatchGeom gb{};
-          for (int d = 0; d < 3; ++d) {
-            gb.U[d] = pl.Ub[gi][bi][d];
-            gb.P[d] = g.P[d];
-            gb.S[d] = g.S[d];
+        for (const BucketPlan &bk : gp.buckets) {
+          const double norm = 1.0 / ((double)bk.P[0] * bk.P[1] * bk.P[2]);
+          float nsh, nsl, esh, esl;
+          split_ff(-norm / kT, nsh, nsl);
+          split_ff(norm, esh, esl);
+          const float2 *const *d_rptr = reinterpret_cast<const float2 *const *>(tab + bk.off_rptr);
+          const RefTab *d_rtabs = reinterpret_cast<const RefTab *>(tab + bk.off_ref);
+          for (int b0 = bk.j0, bi = 0; b0 < bk.j1; b0 += bk.B, ++bi) {
+            const int nb = std::min(bk.B, bk.j1 - b0);
+            BatchGeom gb{};
+            for (int d = 0; d < 3; ++d) {
+              gb.U[d] = bk.Ub[bi][d];
+              gb.P[d] = bk.P[d];
+              gb.S[d] = g.S[d];
+            }
+            gb.F2 = bk.F2;
+            gb.Q = bk.Q;
+            gb.K = Kg;
+            gb.occ_cap = gp.occ_cap;
+            gb.occ_rb = gp.occ_rb;
+            gb.refine = refine;
+            if (use_ff)
+              run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, d_rptr + Kg, h, nsh, nsl,
+                            esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, false, d_tabs);
+            else
+              run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, nullptr, h, nsh, nsl,
+                               esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, split, d_tabs,
+                               d_rtabs, pl.gnorm, kT);
           }
-          gb.F2 = g.F2;
-          gb.Q = g.Q;
-          gb.K = Kg;
-          gb.occ_cap = pl.occ_cap[gi];
-          gb.occ_rb = pl.occ_rb[gi];
-          gb.refine = refine;
-          const RefTab *d_rtabs = reinterpret_cast<const RefTab *>(tab + pl.off_ref[gi]);
-          const OccTab *d_tabs = reinterpret_cast<const OccTab *>(tab + pl.off_occ[gi]);
-          if (use_ff)
-            run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, d_rptr + Kg, h, nsh, nsl,
-                          esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, false, d_tabs);
-          else
-            run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, nullptr, h, nsh, nsl,
-                             esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, split, d_tabs,
-                             d_rtabs, pl.gnorm, kT);
         }
         if (export_E) continue;
         MergeArgs ma{};
         ma.part = d_part;
         ma.nvalid = d_nv;
-        ma.order = d_order;
-        ma.kmap = reinterpret_cast<const int *>(tab + pl.off_kmap[gi]);
+        ma.order = reinterpret_cast<const int *>(tab + gp.off_order);
+        ma.kmap = reinterpret_cast<const int *>(tab + gp.off_kmap);
         ma.Kg = Kg;
         ma.J = J;
         ma.K = K;

@@ -285,6 +285,7 @@ extern "C" int bpmf_export_energies_static(const float *grids, int nx, int ny, i
       m.u[d] = (int)std::ceil(rat) + 4;
       const int w0 = site_lo[d] - m.u[d] / 2;
       pi.w0[d] = w0;
+      pi.wc[d] = w0;
       pi.sa[d] = std::max(0, -w0);
       pi.sb[d] = std::min(site_n[d] - 1, N[d] - 1 - m.u[d] - w0);
       U[d] = std::max(1, std::min(m.u[d], P[d]));

@@ -10,8 +10,8 @@
 // Stage with radix R after Ns points have been combined (Ns = product of the
 // earlier radices): butterfly i in [0, P/R) reads x[i + r P/R], multiplies by
 // w_P^(r (i mod Ns) P/(Ns R)), takes an R-point DFT and writes to
-// (i / Ns) Ns R + (i mod Ns) + r Ns.  Radices 8, 4, 2 are hand-written; 3, 5
-// and 7 use the R-point DFT matrix read from the same twiddle table.
+// (i / Ns) Ns R + (i mod Ns) + r Ns.  Radices 8, 4, 2, 3 and 5 are hand-written;
+// 7 uses the R-point DFT matrix read from the same twiddle table.
 #pragma once
 #include <type_traits>
 
@@ -79,8 +79,28 @@ __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, 
     v[0] = c_add(v[0], sp);
     v[1] = c_add(t1, t2);
     v[2] = c_sub(t1, t2);
+  } else if constexpr (R == 5) {
+    // with w = exp(-2 pi i / 5) = c1 - i sa, w^2 = c2 - i sb and w^(5-m) the
+    // conjugate of w^m, the pairs (1, 4) and (2, 3) combine as
+    //   X1,4 = v0 + c1 (v1 + v4) + c2 (v2 + v3) -/+ i (sa (v1 - v4) + sb (v2 - v3))
+    //   X2,3 = v0 + c2 (v1 + v4) + c1 (v2 + v3) -/+ i (sb (v1 - v4) - sa (v2 - v3))
+    // (forward; the inverse flips the sign of i)
+    const float4 q1 = tw[P / 5], q2 = tw[2 * (P / 5)];
+    const T c1 = s_mk<T>(q1.x, q1.z), sa = s_neg(s_mk<T>(q1.y, q1.w));
+    const T c2 = s_mk<T>(q2.x, q2.z), sb = s_neg(s_mk<T>(q2.y, q2.w));
+    const cx<T> s1 = c_add(v[1], v[4]), d1 = c_sub(v[1], v[4]);
+    const cx<T> s2 = c_add(v[2], v[3]), d2 = c_sub(v[2], v[3]);
+    const cx<T> t1 = c_add(v[0], cx<T>{s_add(s_mul(s1.re, c1), s_mul(s2.re, c2)), s_add(s_mul(s1.im, c1), s_mul(s2.im, c2))});
+    const cx<T> t2 = c_add(v[0], cx<T>{s_add(s_mul(s1.re, c2), s_mul(s2.re, c1)), s_add(s_mul(s1.im, c2), s_mul(s2.im, c1))});
+    const cx<T> u1 = c_rot(cx<T>{s_add(s_mul(d1.re, sa), s_mul(d2.re, sb)), s_add(s_mul(d1.im, sa), s_mul(d2.im, sb))}, inv);
+    const cx<T> u2 = c_rot(cx<T>{s_sub(s_mul(d1.re, sb), s_mul(d2.re, sa)), s_sub(s_mul(d1.im, sb), s_mul(d2.im, sa))}, inv);
+    v[0] = c_add(v[0], c_add(s1, s2));
+    v[1] = c_add(t1, u1);
+    v[4] = c_sub(t1, u1);
+    v[2] = c_add(t2, u2);
+    v[3] = c_sub(t2, u2);
   } else {
-    // radix 5, 7: X[a] = sum_b v[b] w_R^(a b), w_R^m = tw[m P / R]
+    // radix 7: X[a] = sum_b v[b] w_R^(a b), w_R^m = tw[m P / R]
     cx<T> out[R];
     const int st = P / R;
 #pragma unroll
@@ -175,6 +195,16 @@ struct CtPlan<96> {
   __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : (s == 1 ? 4 : 3); }
 };
 template <>
+struct CtPlan<80> {
+  static constexpr int nst = 3;
+  __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : (s == 1 ? 2 : 5); }
+};
+template <>
+struct CtPlan<72> {
+  static constexpr int nst = 3;
+  __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : 3; }
+};
+template <>
 struct CtPlan<128> {
   static constexpr int nst = 3;
   __host__ __device__ static constexpr int r(int s) { return s < 2 ? 8 : 2; }
@@ -226,7 +256,7 @@ __device__ __forceinline__ cx<T> *cta_fft_ct_from(cx<T> *src, cx<T> *dst, const 
   }
 }
 
-// Compile-time counterpart of cta_fft for P in {32, 64, 96, 128}; NT must
+// Compile-time counterpart of cta_fft for P in {32, 64, 72, 80, 96, 128}; NT must
 // equal blockDim.x.
 template <class T, int P, int NL, int ES, int LS, int NT>
 __device__ __forceinline__ cx<T> *cta_fft_ct(cx<T> *b0, cx<T> *b1, const float4 *tw, bool inv) {
@@ -243,6 +273,10 @@ __device__ __forceinline__ cx<T> *cta_fft_auto(cx<T> *b0, cx<T> *b1, int es, int
     switch (pl.n) {
       case 96:
         return CONTIG ? cta_fft_ct<T, 96, NL, 1, 97, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 96, NL, NL, 1, NT>(b0, b1, tw, inv);
+      case 80:
+        return CONTIG ? cta_fft_ct<T, 80, NL, 1, 81, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 80, NL, NL, 1, NT>(b0, b1, tw, inv);
+      case 72:
+        return CONTIG ? cta_fft_ct<T, 72, NL, 1, 73, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 72, NL, NL, 1, NT>(b0, b1, tw, inv);
       case 64:
         return CONTIG ? cta_fft_ct<T, 64, NL, 1, 65, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 64, NL, NL, 1, NT>(b0, b1, tw, inv);
       case 32:

@@ -23,11 +23,13 @@ __device__ __forceinline__ int imod(int a, int m) {
 // smaller CTAs capped at 128 registers so that 4 can share an SM.
 template <class T>
 struct KCfg {
-  static constexpr int threads = 256, min_blocks = 2, xlw = 16, x_min_blocks = 3, a_min_blocks = 3, z_min_blocks = 3;
+  static constexpr int threads = 256, min_blocks = 2, xlw = 8, xconf = 2, x_min_blocks = 3, a_min_blocks = 3,
+                       z_min_blocks = 3, zi_min_blocks = 3;
 };
 template <>
 struct KCfg<ff> {
-  static constexpr int threads = 128, min_blocks = 4, xlw = 8, x_min_blocks = 4, a_min_blocks = 4, z_min_blocks = 4;
+  static constexpr int threads = 128, min_blocks = 4, xlw = 8, xconf = 1, x_min_blocks = 4, a_min_blocks = 4,
+                       z_min_blocks = 4, zi_min_blocks = 2;
 };
 
 template <class T>
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::a_min_blocks) k_axi
     const long long o = c < ncols ? c / a.inner : 0, i = c < ncols ? c % a.inner : 0;
     s_in[threadIdx.x] = c < ncols ? o * a.in_os + i : -1;
     s_out[threadIdx.x] = c < ncols ? o * a.out_os + i : -1;
-    s_w0[threadIdx.x] = a.info ? a.info[o / a.w0_div].w0[a.axis] : 0;
+    s_w0[threadIdx.x] = a.info ? a.info[o / a.w0_div].wc[a.axis] : 0;
   }
   __syncthreads();
   const int n_in = a.n_in < P ? a.n_in : P;
@@ -353,14 +355,16 @@ cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
 }
 
 // --------------------------------------------------------------------------
-// (b)+(c)+(d, first inverse pass) along x.  CTA = (configuration, tile of LW
-// consecutive (y, zf) columns).  Forward DFT of the 3 ligand channels, then
-// for each receptor k: P_k = sum_t R_{k,t} conj(L_t), inverse DFT, keep the
-// site window along x.  The ligand spectrum never leaves shared memory.
+// (b)+(c)+(d, first inverse pass) along x.  CTA = (G configurations, tile of
+// LW consecutive (y, zf) columns).  Forward DFT of the 3 ligand channels of
+// each configuration, then for each receptor k: P_k = sum_t R_{k,t} conj(L_t),
+// inverse DFT, keep the site window along x.  Each receptor element is loaded
+// once per CTA and used for all G configurations; the ligand spectra never
+// leave shared memory.
 template <class T>
 __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfused(XfusedArgs a, int batch) {
   extern __shared__ float4 smem[];
-  constexpr int LW = KCfg<T>::xlw, L3 = 3 * LW;
+  constexpr int LW = KCfg<T>::xlw, G = KCfg<T>::xconf, LG = G * LW, L3 = 3 * LG;
   const int P = a.plan.n;
   float4 *s_tw = smem;
   cx<T> *bA = reinterpret_cast<cx<T> *>(smem + P);
@@ -368,43 +372,52 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfu
   load_tw(s_tw, a.tw, P);
   // tile-major order: CTAs resident together share a column tile across many
   // configurations, so that tile's receptor spectra are served from L2
-  const int j = blockIdx.x % batch;
-  const long long q0 = (long long)(blockIdx.x / batch) * LW;
+  const int nJG = (batch + G - 1) / G;
+  const int j0 = (blockIdx.x % nJG) * G;
+  const long long q0 = (long long)(blockIdx.x / nJG) * LW;
   const int U0 = a.U0 < P ? a.U0 : P;
+  // ligand columns: c = (g * 3 + t) * LW + l
   for (int idx = threadIdx.x; idx < U0 * L3; idx += blockDim.x) {
-    const int x = idx / L3, c = idx % L3, t = c / LW, l = c % LW;
+    const int x = idx / L3, c = idx % L3, gt = c / LW, l = c % LW;
+    const int j = j0 + gt / 3, t = gt % 3;
     const long long q = q0 + l;
-    cp_cx<T>(&bA[idx], a.ly, (((long long)j * 3 + t) * a.U0 + x) * a.Q + q, q < a.Q);
+    cp_cx<T>(&bA[idx], a.ly, (((long long)j * 3 + t) * a.U0 + x) * a.Q + q, q < a.Q && j < batch);
   }
   for (int idx = U0 * L3 + threadIdx.x; idx < P * L3; idx += blockDim.x) bA[idx] = c_zero<T>();
   cp_async_wait_all();
   __syncthreads();
   cx<T> *Lsp = cta_fft_auto<T, L3, KCfg<T>::threads, false>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
   cx<T> *W1 = (Lsp == bA) ? bB : bA;
-  cx<T> *W2 = W1 + P * LW;
+  cx<T> *W2 = W1 + P * LG;
   for (int k = 0; k < a.K; ++k) {
     const float2 *rh = a.rhi[k];
     const float2 *rl = a.rlo ? a.rlo[k] : nullptr;
-#pragma unroll 2
     for (int idx = threadIdx.x; idx < P * LW; idx += blockDim.x) {
       const int x = idx / LW, l = idx % LW;
       const long long q = q0 + l;
-      cx<T> acc = c_zero<T>();
+      cx<T> r0 = c_zero<T>(), r1 = c_zero<T>(), r2 = c_zero<T>();
       if (q < a.Q) {
         const long long ri = (long long)x * a.Q + q, rs = (long long)P * a.Q;
-        const cx<T> r0 = ld_rec(rh, rl, ri, T{}), r1 = ld_rec(rh, rl, ri + rs, T{}), r2 = ld_rec(rh, rl, ri + 2 * rs, T{});
-        const cx<T> *lx = Lsp + x * L3 + l;
-        acc = c_add(c_add(c_mulconj(r0, lx[0]), c_mulconj(r1, lx[LW])), c_mulconj(r2, lx[2 * LW]));
+        r0 = ld_rec(rh, rl, ri, T{});
+        r1 = ld_rec(rh, rl, ri + rs, T{});
+        r2 = ld_rec(rh, rl, ri + 2 * rs, T{});
       }
-      W1[idx] = c_norm(acc);
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const cx<T> *lx = Lsp + x * L3 + g * 3 * LW + l;
+        const cx<T> acc = c_add(c_add(c_mulconj(r0, lx[0]), c_mulconj(r1, lx[LW])), c_mulconj(r2, lx[2 * LW]));
+        W1[x * LG + g * LW + l] = c_norm(acc);
+      }
     }
     __syncthreads();
-    cx<T> *res = cta_fft_auto<T, LW, KCfg<T>::threads, false>(W1, W2, LW, 1, LW, a.plan, s_tw, true);
-    const int w0 = a.info[j * a.K + k].w0[0];
-    for (int idx = threadIdx.x; idx < a.S0 * LW; idx += blockDim.x) {
-      const int s = idx / LW, l = idx % LW;
+    cx<T> *res = cta_fft_auto<T, LG, KCfg<T>::threads, false>(W1, W2, LG, 1, LG, a.plan, s_tw, true);
+    for (int idx = threadIdx.x; idx < a.S0 * LG; idx += blockDim.x) {
+      const int s = idx / LG, c = idx % LG, j = j0 + c / LW, l = c % LW;
       const long long q = q0 + l;
-      if (q < a.Q) st_cx<T>(a.x2, (((long long)j * a.K + k) * a.S0 + s) * a.Q + q, res[imod(w0 + s, P) * LW + l]);
+      if (q < a.Q && j < batch) {
+        const int w0 = a.info[j * a.K + k].wc[0];
+        st_cx<T>(a.x2, (((long long)j * a.K + k) * a.S0 + s) * a.Q + q, res[imod(w0 + s, P) * LG + c]);
+      }
     }
     __syncthreads();
   }
@@ -414,11 +427,11 @@ template <class T>
 cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   const int P = a.plan.n;
-  constexpr int LW = KCfg<T>::xlw;
-  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * 3 * LW;
+  constexpr int LW = KCfg<T>::xlw, G = KCfg<T>::xconf;
+  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * 3 * G * LW;
   cudaError_t e = cudaFuncSetAttribute(k_xfused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long blocks = (long long)batch * ((a.Q + LW - 1) / LW);
+  const long long blocks = (long long)((batch + G - 1) / G) * ((a.Q + LW - 1) / LW);
   k_xfused<T><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a, batch);
   return cudaGetLastError();
 }
@@ -430,7 +443,7 @@ __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi 
 __device__ __forceinline__ bool ff_gt(float a, float b) { return a > b; }
 
 template <class T>
-__global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
+__global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, F = a.F2, ls = P + 1;
   const int Lc = a.Lc;  // row pairs per chunk (all of them when they fit)
@@ -498,7 +511,7 @@ __global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
       }
       T x = s_mk<T>(-CUDART_INF_F, 0.f);
       if (ok) {
-        const cx<T> z = res[(r >> 1) * ls + imod(inf.w0[2] + s2, P)];
+        const cx<T> z = res[(r >> 1) * ls + imod(inf.wc[2] + s2, P)];
         const T val = (r & 1) ? z.im : z.re;
         x = s_norm(s_mul(val, nscale));
         if (ff_gt(x, vmax)) vmax = x;
@@ -507,7 +520,7 @@ __global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
       if (a.Ebuf) {
         float ef = CUDART_INF_F;
         if (ok) {
-          const cx<T> z = res[(r >> 1) * ls + imod(inf.w0[2] + s2, P)];
+          const cx<T> z = res[(r >> 1) * ls + imod(inf.wc[2] + s2, P)];
           ef = s_hi(s_norm(s_mul((r & 1) ? z.im : z.re, escale)));
           emin = fminf(emin, ef);
         }
@@ -516,7 +529,7 @@ __global__ void __launch_bounds__(256, 2) k_zinv(ZinvArgs a) {
       if (a.export_E && jk == 0) {
         double e = CUDART_INF;
         if (ok) {
-          const cx<T> z = res[(r >> 1) * ls + imod(inf.w0[2] + s2, P)];
+          const cx<T> z = res[(r >> 1) * ls + imod(inf.wc[2] + s2, P)];
           const T E = s_norm(s_mul((r & 1) ? z.im : z.re, escale));
           e = (double)s_hi(E) + (double)s_lo(E);
         }
@@ -621,12 +634,11 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
   if (Mx > -CUDART_INF)
     for (int c = 0; c < a.S0; ++c)
       if (pp[c].z > 0.f) s += (double)pp[c].z * exp((double)pp[c].x + (double)pp[c].y - Mx);
-  const long long pk = (long long)j * a.K + k;
-  const long long n = a.nvalid[pk];
-  const double ls = (s > 0.0 && n > 0) ? Mx + log(s) : -CUDART_INF;
-  a.logS[pk] = ls;
   // processing position -> caller's configuration order
   const long long q = (long long)(a.order ? a.order[j] : j) * a.K + k;
+  const long long n = a.nvalid[q];
+  const double ls = (s > 0.0 && n > 0) ? Mx + log(s) : -CUDART_INF;
+  a.logS[q] = ls;
   a.logZ[q] = n > 0 ? ls - log((double)n) : -CUDART_INF;
   if (a.nvalid_out) a.nvalid_out[q] = n;
   // dominant-state energy: the largest -E/kT of all partials, back to kcal/mol
@@ -740,6 +752,53 @@ __global__ void k_split_ff(const cx<ff> *spec, float2 *hi, float2 *lo, long long
 cudaError_t launch_split_ff(const void *spec, float2 *hi, float2 *lo, long long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_split_ff<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const cx<ff> *>(spec), hi, lo, n);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// The receptor grids cropped to the box [c0, c0 + e) and zero-padded to the
+// extents E >= e (CTA row blockIdx.y = channel t):
+//   out[t][i][j][l] = grid[t][c0_0 + i][c0_1 + j][c0_2 + l] (i, j, l < e), else 0,
+// and the sum of squares of each cropped channel (FP32 error bound).  CTA
+// column blockIdx.x walks (i, j) rows; threads walk l.
+__global__ void __launch_bounds__(256) k_crop(const float *grid, int N0, int N1, int N2, int c00, int c01, int c02,
+                                              int e0, int e1, int e2, int E0, int E1, int E2, float *out,
+                                              double *sumsq) {
+  __shared__ double s_d[8];
+  const int t = blockIdx.y;
+  double acc = 0.0;
+  for (int row = blockIdx.x; row < E0 * E1; row += gridDim.x) {
+    const int ix = row / E1, jy = row % E1;
+    float *dst = out + (((long long)t * E0 + ix) * E1 + jy) * E2;
+    const bool in = ix < e0 && jy < e1;
+    const float *src = grid + (((long long)t * N0 + c00 + ix) * N1 + c01 + jy) * N2 + c02;
+    for (int l = threadIdx.x; l < E2; l += blockDim.x) {
+      const float v = (in && l < e2) ? src[l] : 0.f;
+      dst[l] = v;
+      acc += (double)v * v;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s_d[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_d[w];
+    atomicAdd(sumsq + t, v);
+  }
+}
+
+cudaError_t launch_crop(const float *grid, const int N[3], const int c0[3], const int e[3], const int E[3],
+                        float *out, double *sumsq, cudaStream_t st) {
+  for (int d = 0; d < 3; ++d)
+    if (c0[d] < 0 || e[d] < 1 || c0[d] + e[d] > N[d] || E[d] < e[d]) return cudaErrorInvalidValue;
+  cudaError_t err = cudaMemsetAsync(sumsq, 0, 3 * sizeof(double), st);
+  if (err != cudaSuccess) return err;
+  const int rows = E[0] * E[1];
+  const int blocks = std::min(rows, 152 * 4);
+  const int threads = E[2] >= 128 ? 128 : (E[2] >= 64 ? 64 : 32);
+  k_crop<<<dim3(blocks, 3), threads, 0, st>>>(grid, N[0], N[1], N[2], c0[0], c0[1], c0[2], e[0], e[1], e[2], E[0],
+                                              E[1], E[2], out, sumsq);
   return cudaGetLastError();
 }
 

@@ -18,12 +18,14 @@ struct ConfMeta {
 };
 
 // Per (configuration, receptor) site window: output s_d in [0, S_d) maps to
-// translation m_d = w0_d + s_d; s_d is valid when sa_d <= s_d <= sb_d.
+// translation m_d = w0_d + s_d; s_d is valid when sa_d <= s_d <= sb_d.  The
+// transforms run on the receptor grid cropped at node c0 (0 when uncropped):
+// translation m_d sits at index wc_d + s_d = m_d - c0_d of the correlation.
 struct PairInfo {
   int w0[3];
   int sa[3];
   int sb[3];
-  int pad;
+  int wc[3];
 };
 
 struct SpreadArgs {
@@ -70,7 +72,7 @@ struct AxisArgs {          // C2C along a strided axis, pruned input / output
   int P, n_in, n_out;
   long long n_outer, inner;
   long long in_os, out_os; // cx<T> elements between consecutive outer indices
-  const PairInfo *info;    // output window start w0 = info[o / w0_div].w0[axis]
+  const PairInfo *info;    // output window start info[o / w0_div].wc[axis]
   int w0_div, axis;
   int inverse;
   FftPlan plan;
@@ -155,11 +157,11 @@ struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp pa
 
 struct MergeArgs {
   const float4 *part;      // [J][Kg][S0] of one receptor group, processing order
-  const long long *nvalid; // [J][K], processing order, all receptors
+  const long long *nvalid; // [J][K], caller's order, all receptors
   const int *order;        // [J] processing position -> caller's configuration index (null: identity)
   const int *kmap;         // [Kg] group-local receptor -> receptor index in the call (null: identity)
   int Kg;                  // receptors in the group (k_merge_pairs)
-  double *logS;            // [J][K] scratch, processing order
+  double *logS;            // [J][K] scratch, caller's order
   int J, K, S0;
   double kT;
   double vsite_scale;      // h^3 * C_standard
@@ -175,8 +177,9 @@ struct MergeArgs {
 // ---- refined form (refine.cu) -----------------------------------------------
 struct RefTab {            // one receptor's grids, FP32 [3][N0][N1][N2]
   const float *grid;
-  const double *sumsq;     // [3] sum of squares of each grid (FP32 error bound)
+  const double *sumsq;     // [3] sum of squares of each grid over the transformed (cropped) nodes
   int N0, N1, N2;
+  double vol;              // transformed nodes per channel (FP32 error bound: rms = sqrt(sumsq / vol))
 };
 
 struct RefineArgs {
@@ -205,6 +208,8 @@ cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st);
 cudaError_t launch_gamma64(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, double *g,
                            cudaStream_t st);
 cudaError_t launch_sumsq(const float *g, long long vol, double *out, cudaStream_t st);
+cudaError_t launch_crop(const float *grid, const int N[3], const int c0[3], const int e[3], const int E[3],
+                        float *out, double *sumsq, cudaStream_t st);
 cudaError_t launch_occ_table(const unsigned char *occ, int N0, int N1, int N2, int W, uint32_t *tab,
                              cudaStream_t st);
 cudaError_t launch_occ_runs(const OccRunsArgs &a, int batch, cudaStream_t st);

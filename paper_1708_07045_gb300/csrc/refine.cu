@@ -158,7 +158,7 @@ __global__ void k_window(const RefTab *tabs, int K, double g0, double g1, double
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
   const RefTab t = tabs[k];
-  const double vol = (double)t.N0 * t.N1 * t.N2;
+  const double vol = t.vol;
   const double B = 8.0 * 5.9604644775390625e-08 * sqrt(log2P3) *
                    (sqrt(t.sumsq[0] / vol) * g0 + sqrt(t.sumsq[1] / vol) * g1 + sqrt(t.sumsq[2] / vol) * g2);
   window[k] = kT * fmax(20.0, log(1e5 * nS)) + 2.0 * B;
