@@ -80,6 +80,7 @@ struct bpmf_rec {
     double vol = 0;                     // cropped nodes per channel
   };
   std::map<std::array<int, 3>, Crop> crops;
+  cudaEvent_t crop_ev = nullptr;        // recorded after the last crop was made (on the stream that made it)
 };
 
 struct bpmf_lig {
@@ -903,7 +904,7 @@ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 // of edge u lies in the crop when Pc >= site_n + u - 1: the crop starts
 // floor((site_n - Pc) / 2) nodes from the site, moved inside the grid.
 std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *> &rs, const std::array<int, 3> &Pc,
-                                      cudaStream_t st, bool &made) {
+                                      cudaStream_t st) {
   std::vector<bpmf_rec::Crop> out(rs.size());
   std::vector<size_t> todo;
   std::vector<std::array<int, 3>> ext;
@@ -982,8 +983,12 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
     }
     throw;
   }
-  for (int i = 0; i < n; ++i) rs[todo[i]]->crops[Pc] = out[todo[i]];
-  made = true;
+  for (int i = 0; i < n; ++i) {
+    bpmf_rec *r = rs[todo[i]];
+    r->crops[Pc] = out[todo[i]];
+    if (!r->crop_ev) CK(cudaEventCreateWithFlags(&r->crop_ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(r->crop_ev, st));
+  }
   resolve();
   return out;
 }
@@ -1056,6 +1061,7 @@ void bpmf_receptor_free(bpmf_rec_t r) {
     if (r->occ) cudaFree(r->occ);
     if (r->grid) cudaFree(r->grid);
     if (r->sumsq) cudaFree(r->sumsq);
+    if (r->crop_ev) cudaEventDestroy(r->crop_ev);
     for (auto &kv : r->crops) {
       if (kv.second.hi) cudaFree(kv.second.hi);
       if (kv.second.lo) cudaFree(kv.second.lo);
@@ -1346,7 +1352,6 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   std::vector<PairInfo> info;
   std::vector<long long> nv;
   size_t ws_need = 0;
-  bool crops_made = false;
   for (int li = lig_begin; li < lig_end; ++li) {
     ligand_tables(lg, li, recs, K, h, meta, info, nv);
     LigPlan pl;
@@ -1462,7 +1467,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         std::vector<RefTab> rt(Kg);
         std::vector<bpmf_rec *> rg(Kg);
         for (int kg = 0; kg < Kg; ++kg) rg[kg] = recs[g.ks[kg]];
-        const std::vector<bpmf_rec::Crop> crs = rec_crops(c, rg, Pc, st, crops_made);
+        const std::vector<bpmf_rec::Crop> crs = rec_crops(c, rg, Pc, st);
         for (int kg = 0; kg < Kg; ++kg) {
           bpmf_rec *r = rg[kg];
           const bpmf_rec::Crop &cr = crs[kg];
@@ -1536,9 +1541,9 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   if (!blob.empty()) std::memcpy(c->pinned, blob.data(), blob.size());
   for (const auto &g : groups)
     for (int d = 0; d < 3; ++d) twiddles(c, g.P[d]);
-  // new receptor crops were made on this stream: complete them before any
-  // other stream can read them
-  if (crops_made) CK(cudaStreamSynchronize(st));
+  // receptor crops may have been made on another stream: order this call after them
+  for (int k = 0; k < K; ++k)
+    if (recs[k]->crop_ev) CK(cudaStreamWaitEvent(st, recs[k]->crop_ev, 0));
   c->warn_last = warn;
 
   // -------------------------------------------------------------- execute

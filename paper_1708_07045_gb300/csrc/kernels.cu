@@ -301,16 +301,17 @@ cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st) {
 }
 
 // --------------------------------------------------------------------------
-// C2C along a strided axis for a tile of LW consecutive innermost indices.
-template <class T>
+// C2C along a strided axis for a tile of LW consecutive innermost indices
+// (LWC > 0: LW fixed at compile time, so tile indices are shifts and masks).
+template <class T, int LWC>
 __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::a_min_blocks) k_axis(AxisArgs a) {
   extern __shared__ float4 smem[];
-  const int P = a.plan.n, LW = a.LW;
+  const int P = a.plan.n, LW = LWC > 0 ? LWC : a.LW;
   float4 *s_tw = smem;
   cx<T> *b0 = reinterpret_cast<cx<T> *>(smem + P);
   cx<T> *b1 = b0 + P * LW;
   __shared__ long long s_in[64], s_out[64];  // per tile column: base offsets of input / output
-  __shared__ int s_w0[64];
+  __shared__ int s_w0[64];                   // per tile column: output window start mod P
   load_tw(s_tw, a.tw, P);
   // columns are the flattened (outer, inner) pairs, so a tile never wastes
   // lanes on a short inner edge
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::a_min_blocks) k_axi
     const long long o = c < ncols ? c / a.inner : 0, i = c < ncols ? c % a.inner : 0;
     s_in[threadIdx.x] = c < ncols ? o * a.in_os + i : -1;
     s_out[threadIdx.x] = c < ncols ? o * a.out_os + i : -1;
-    s_w0[threadIdx.x] = a.info ? a.info[o / a.w0_div].wc[a.axis] : 0;
+    s_w0[threadIdx.x] = a.info ? imod(a.info[o / a.w0_div].wc[a.axis], P) : 0;
   }
   __syncthreads();
   const int n_in = a.n_in < P ? a.n_in : P;
@@ -333,25 +334,35 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::a_min_blocks) k_axi
   for (int idx = n_in * LW + threadIdx.x; idx < P * LW; idx += blockDim.x) b0[idx] = c_zero<T>();
   cp_async_wait_all();
   __syncthreads();
-  cx<T> *res = cta_fft_auto<T, 16, KCfg<T>::threads, false>(b0, b1, LW, 1, LW, a.plan, s_tw, a.inverse != 0);
+  cx<T> *res = cta_fft_auto<T, (LWC > 0 ? LWC : 16), KCfg<T>::threads, false>(b0, b1, LW, 1, LW, a.plan, s_tw,
+                                                                             a.inverse != 0);
+  // outputs s < n_out <= P, read at (w0 + s) mod P
   for (int idx = threadIdx.x; idx < a.n_out * LW; idx += blockDim.x) {
     const int s = idx / LW, l = idx % LW;
     const long long base = s_out[l];
-    if (base >= 0) st_cx<T>(a.out, base + s * a.inner, res[imod(s_w0[l] + s, P) * LW + l]);
+    const int m = s_w0[l] + s;
+    if (base >= 0) st_cx<T>(a.out, base + s * a.inner, res[(m >= P ? m - P : m) * LW + l]);
   }
+}
+
+template <class T, int LWC>
+cudaError_t launch_axis_lw(const AxisArgs &a, cudaStream_t st) {
+  const int P = a.plan.n;
+  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * a.LW;
+  cudaError_t e = cudaFuncSetAttribute(k_axis<T, LWC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (a.n_outer * a.inner + a.LW - 1) / a.LW;
+  k_axis<T, LWC><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
   if (a.n_outer <= 0 || a.inner <= 0) return cudaSuccess;
-  const int P = a.plan.n;
-  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * a.LW;
-  cudaError_t e = cudaFuncSetAttribute(k_axis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (a.LW < 1 || a.LW > 64) return cudaErrorInvalidValue;
-  const long long blocks = (a.n_outer * a.inner + a.LW - 1) / a.LW;
-  k_axis<T><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
-  return cudaGetLastError();
+  if (a.LW < 1 || a.LW > 64 || a.n_out > a.plan.n) return cudaErrorInvalidValue;
+  if (a.LW == 16) return launch_axis_lw<T, 16>(a, st);
+  if (a.LW == 8) return launch_axis_lw<T, 8>(a, st);
+  return launch_axis_lw<T, 0>(a, st);
 }
 
 // --------------------------------------------------------------------------
@@ -389,9 +400,11 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfu
   cx<T> *Lsp = cta_fft_auto<T, L3, KCfg<T>::threads, false>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
   cx<T> *W1 = (Lsp == bA) ? bB : bA;
   cx<T> *W2 = W1 + P * LG;
+  __shared__ int s_wm[G];  // per configuration: site window start along x, mod P
   for (int k = 0; k < a.K; ++k) {
     const float2 *rh = a.rhi[k];
     const float2 *rl = a.rlo ? a.rlo[k] : nullptr;
+    if (threadIdx.x < G) s_wm[threadIdx.x] = j0 + (int)threadIdx.x < batch ? imod(a.info[(j0 + threadIdx.x) * a.K + k].wc[0], P) : 0;
     for (int idx = threadIdx.x; idx < P * LW; idx += blockDim.x) {
       const int x = idx / LW, l = idx % LW;
       const long long q = q0 + l;
@@ -415,8 +428,8 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfu
       const int s = idx / LG, c = idx % LG, j = j0 + c / LW, l = c % LW;
       const long long q = q0 + l;
       if (q < a.Q && j < batch) {
-        const int w0 = a.info[j * a.K + k].wc[0];
-        st_cx<T>(a.x2, (((long long)j * a.K + k) * a.S0 + s) * a.Q + q, res[imod(w0 + s, P) * LG + c]);
+        const int m = s_wm[c / LW] + s;  // s < S0 <= P
+        st_cx<T>(a.x2, (((long long)j * a.K + k) * a.S0 + s) * a.Q + q, res[(m >= P ? m - P : m) * LG + c]);
       }
     }
     __syncthreads();
@@ -476,8 +489,14 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
       cp_async_wait_all();
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < L * P; idx += blockDim.x) {
-      const int l = idx / P, n = idx % P;
+    // (l, n) = divmod(idx, P), stepped without a division per element
+    const int dl = (int)blockDim.x / P, dn = (int)blockDim.x % P;
+    for (int idx = threadIdx.x, l = (int)threadIdx.x / P, n = (int)threadIdx.x % P; idx < L * P;
+         idx += blockDim.x, l += dl, n += dn) {
+      if (n >= P) {
+        n -= P;
+        ++l;
+      }
       const int ra = 2 * l, rb = ra + 1;
       cx<T> A = c_zero<T>(), B = c_zero<T>();
       const bool up = n <= P / 2;
@@ -502,8 +521,18 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
     const int nS = nrow * a.S2;
     T vmax = s_mk<T>(-CUDART_INF_F, 0.f);
     float emin = CUDART_INF_F;  // refined form: plane minimum of the energies
-    for (int idx = threadIdx.x; idx < nS; idx += blockDim.x) {
-      const int r = idx / a.S2, s2 = idx % a.S2, s1 = r0 + r;
+    // (r, s2) = divmod(idx, S2) stepped the same way; z index (wc + s2) mod P
+    // from its value at s2 = 0 (s2 < S2 <= P)
+    const int dr = (int)blockDim.x / a.S2, ds = (int)blockDim.x % a.S2;
+    const int zb = imod(inf.wc[2], P);
+    for (int idx = threadIdx.x, r = (int)threadIdx.x / a.S2, s2 = (int)threadIdx.x % a.S2; idx < nS;
+         idx += blockDim.x, r += dr, s2 += ds) {
+      if (s2 >= a.S2) {
+        s2 -= a.S2;
+        ++r;
+      }
+      const int s1 = r0 + r;
+      const int zi = zb + s2 >= P ? zb + s2 - P : zb + s2;
       bool ok = row_ok && s1 >= inf.sa[1] && s1 <= inf.sb[1] && s2 >= inf.sa[2] && s2 <= inf.sb[2];
       if (ok && a.clash) {  // a clashing translation has infinite energy (it stays counted in n)
         const uint32_t w = a.clash[((long long)blockIdx.x * a.S1 + s1) * a.CW + (s2 >> 5)];
@@ -511,7 +540,7 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
       }
       T x = s_mk<T>(-CUDART_INF_F, 0.f);
       if (ok) {
-        const cx<T> z = res[(r >> 1) * ls + imod(inf.wc[2] + s2, P)];
+        const cx<T> z = res[(r >> 1) * ls + zi];
         const T val = (r & 1) ? z.im : z.re;
         x = s_norm(s_mul(val, nscale));
         if (ff_gt(x, vmax)) vmax = x;
@@ -520,7 +549,7 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
       if (a.Ebuf) {
         float ef = CUDART_INF_F;
         if (ok) {
-          const cx<T> z = res[(r >> 1) * ls + imod(inf.wc[2] + s2, P)];
+          const cx<T> z = res[(r >> 1) * ls + zi];
           ef = s_hi(s_norm(s_mul((r & 1) ? z.im : z.re, escale)));
           emin = fminf(emin, ef);
         }
@@ -529,7 +558,7 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
       if (a.export_E && jk == 0) {
         double e = CUDART_INF;
         if (ok) {
-          const cx<T> z = res[(r >> 1) * ls + imod(inf.wc[2] + s2, P)];
+          const cx<T> z = res[(r >> 1) * ls + zi];
           const T E = s_norm(s_mul((r & 1) ? z.im : z.re, escale));
           e = (double)s_hi(E) + (double)s_lo(E);
         }
