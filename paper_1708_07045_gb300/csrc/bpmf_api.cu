@@ -66,6 +66,7 @@ struct bpmf_rec {
   double h = 0;
   double origin[3] = {0, 0, 0};
   int site_lo[3] = {0, 0, 0}, site_n[3] = {0, 0, 0};
+  void *mem = nullptr;                  // one device block holding grid, sumsq, hi and lo
   float2 *hi = nullptr, *lo = nullptr;  // [3][P0][Q]
   uint32_t *occ = nullptr;              // occupancy tables [kOccLevels][N0 + 32][occW][N1 + 32], or null
   int occW = 0;
@@ -74,6 +75,7 @@ struct bpmf_rec {
   // spectra of the grids cropped to a box of transform edges P around the
   // site, made on first use, per P (the uncropped spectrum is hi / lo)
   struct Crop {
+    void *mem = nullptr;                // the device block holding hi, lo and sumsq (null: a view)
     int c0[3] = {0, 0, 0};              // first node of the crop
     float2 *hi = nullptr, *lo = nullptr;  // [3][P0][P1 (P2/2+1)]
     double *sumsq = nullptr;            // [3] over the cropped nodes
@@ -96,6 +98,7 @@ struct bpmf_lig {
   std::vector<float> R_host;  // host [total_atoms] (occupancy radii)
   std::vector<float> q_host, eps_host;  // host [total_atoms] (FP32 error bound)
   double *gamma64 = nullptr;  // device [3][total_atoms] FP64 generalised charges (refined form)
+  void *mem = nullptr;        // one device block holding coords, gamma, q, eps, R and gamma64
   int p_rep = 12, p_att = 6;
 };
 
@@ -270,7 +273,6 @@ void *workspace(bpmf_ctx *c, size_t bytes, cudaStream_t st) {
 
 inline size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
-
 cudaEvent_t pool_event(bpmf_ctx *c) {
   if (!c->event_pool.empty()) {
     cudaEvent_t e = c->event_pool.back();
@@ -281,6 +283,24 @@ cudaEvent_t pool_event(bpmf_ctx *c) {
   CK(cudaEventCreate(&e));
   return e;
 }
+
+// Sub-buffers of one device allocation: add() reserves 256-byte aligned
+// ranges, alloc() makes the block and returns its base.
+struct Carve {
+  std::vector<std::pair<void **, size_t>> parts;
+  size_t total = 0;
+  template <class P>
+  void add(P **ptr, size_t bytes) {
+    parts.push_back({reinterpret_cast<void **>(ptr), total});
+    total += align_up(std::max<size_t>(bytes, 1));
+  }
+  void *alloc() {
+    void *base = nullptr;
+    CK(cudaMalloc(&base, total));
+    for (auto &pr : parts) *pr.first = static_cast<char *>(base) + pr.second;
+    return base;
+  }
+};
 
 // Launch `fn` (returning cudaError_t); when profiling, bracket it with events.
 template <class F>
@@ -954,9 +974,11 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
   try {
     for (int i = 0; i < n; ++i) {
       bpmf_rec::Crop &cr = out[todo[i]];
-      CK(cudaMalloc(&cr.hi, 3ull * Pc[0] * Q * sizeof(float2)));
-      CK(cudaMalloc(&cr.lo, 3ull * Pc[0] * Q * sizeof(float2)));
-      CK(cudaMalloc(&cr.sumsq, 3 * sizeof(double)));
+      Carve cv;
+      cv.add(&cr.hi, 3ull * Pc[0] * Q * sizeof(float2));
+      cv.add(&cr.lo, 3ull * Pc[0] * Q * sizeof(float2));
+      cv.add(&cr.sumsq, 3 * sizeof(double));
+      cr.mem = cv.alloc();
       his[i] = cr.hi;
       los[i] = cr.lo;
     }
@@ -975,12 +997,8 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
   } catch (Fail) {
     if (buf) cudaFreeAsync(buf, st);
     cudaStreamSynchronize(st);
-    for (int i = 0; i < n; ++i) {
-      bpmf_rec::Crop &cr = out[todo[i]];
-      if (cr.hi) cudaFree(cr.hi);
-      if (cr.lo) cudaFree(cr.lo);
-      if (cr.sumsq) cudaFree(cr.sumsq);
-    }
+    for (int i = 0; i < n; ++i)
+      if (out[todo[i]].mem) cudaFree(out[todo[i]].mem);
     throw;
   }
   for (int i = 0; i < n; ++i) {
@@ -1035,12 +1053,14 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
     r->Q = (long long)P[1] * r->F2;
     const size_t vol = (size_t)nx * ny * nz;
     DevIn g(grids, 3 * vol * sizeof(float), st);
-    CK(cudaMalloc(&r->grid, 3 * vol * sizeof(float)));
+    Carve cv;
+    cv.add(&r->grid, 3 * vol * sizeof(float));
+    cv.add(&r->sumsq, 3 * sizeof(double));
+    cv.add(&r->hi, 3ull * P[0] * r->Q * sizeof(float2));
+    cv.add(&r->lo, 3ull * P[0] * r->Q * sizeof(float2));
+    r->mem = cv.alloc();
     CK(cudaMemcpyAsync(r->grid, g.p, 3 * vol * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMalloc(&r->sumsq, 3 * sizeof(double)));
     launch(c, "k_sumsq", st, [&] { return launch_sumsq(r->grid, (long long)vol, r->sumsq, st); });
-    CK(cudaMalloc(&r->hi, 3ull * P[0] * r->Q * sizeof(float2)));
-    CK(cudaMalloc(&r->lo, 3ull * P[0] * r->Q * sizeof(float2)));
     grid_spectrum(c, static_cast<const float *>(g.p), 1, N, P, &r->hi, &r->lo, st);
     if (!is_device_ptr(grids)) CK(cudaStreamSynchronize(st));
   } catch (Fail f) {
@@ -1056,17 +1076,11 @@ void bpmf_receptor_free(bpmf_rec_t r) {
   if (!r) return;
   if (r->ctx) {
     DeviceGuard g(r->ctx->device);
-    if (r->hi) cudaFree(r->hi);
-    if (r->lo) cudaFree(r->lo);
+    if (r->mem) cudaFree(r->mem);
     if (r->occ) cudaFree(r->occ);
-    if (r->grid) cudaFree(r->grid);
-    if (r->sumsq) cudaFree(r->sumsq);
     if (r->crop_ev) cudaEventDestroy(r->crop_ev);
-    for (auto &kv : r->crops) {
-      if (kv.second.hi) cudaFree(kv.second.hi);
-      if (kv.second.lo) cudaFree(kv.second.lo);
-      if (kv.second.sumsq) cudaFree(kv.second.sumsq);
-    }
+    for (auto &kv : r->crops)
+      if (kv.second.mem) cudaFree(kv.second.mem);
   }
   delete r;
 }
@@ -1150,10 +1164,14 @@ int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_
       throw Fail{BPMF_ERR_INVALID_ARG};
     }
     const size_t na = lg->total_atoms;
-    CK(cudaMalloc(&lg->gamma, 3 * na * sizeof(float2)));
-    CK(cudaMalloc(&lg->q, na * sizeof(float)));
-    CK(cudaMalloc(&lg->eps, na * sizeof(float)));
-    CK(cudaMalloc(&lg->R, na * sizeof(float)));
+    Carve cv;
+    cv.add(&lg->gamma, 3 * na * sizeof(float2));
+    cv.add(&lg->q, na * sizeof(float));
+    cv.add(&lg->eps, na * sizeof(float));
+    cv.add(&lg->R, na * sizeof(float));
+    cv.add(&lg->gamma64, 3 * std::max<size_t>(na, 1) * sizeof(double));
+    cv.add(&lg->coords, std::max<size_t>(1, 3 * lg->total_coord_atoms) * sizeof(float));
+    lg->mem = cv.alloc();
     CK(cudaMemcpyAsync(lg->q, q, na * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaMemcpyAsync(lg->eps, eps, na * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaMemcpyAsync(lg->R, R, na * sizeof(float), cudaMemcpyDefault, st));
@@ -1165,8 +1183,6 @@ int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_
     CK(cudaMemcpyAsync(lg->eps_host.data(), lg->eps, na * sizeof(float), cudaMemcpyDeviceToHost, st));
     lg->p_rep = p_rep;
     lg->p_att = p_att;
-    CK(cudaMalloc(&lg->gamma64, 3 * std::max<size_t>(na, 1) * sizeof(double)));
-    CK(cudaMalloc(&lg->coords, std::max<size_t>(1, 3 * lg->total_coord_atoms) * sizeof(float)));
     {
       DevIn dq(q, na * sizeof(float), st), de(eps, na * sizeof(float), st), dr(R, na * sizeof(float), st);
       launch(c, "k_gamma", st, [&] {
@@ -1220,11 +1236,7 @@ void bpmf_ligand_free(bpmf_lig_t lg) {
   if (!lg) return;
   if (lg->ctx) {
     DeviceGuard g(lg->ctx->device);
-    if (lg->coords) cudaFree(lg->coords);
-    if (lg->gamma) cudaFree(lg->gamma);
-    for (float *p : {lg->q, lg->eps, lg->R})
-      if (p) cudaFree(p);
-    if (lg->gamma64) cudaFree(lg->gamma64);
+    if (lg->mem) cudaFree(lg->mem);
   }
   delete lg;
 }
