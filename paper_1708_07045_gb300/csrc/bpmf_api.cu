@@ -56,6 +56,11 @@ struct bpmf_ctx {
   };
   std::map<std::vector<int>, Tune> tune;
   bool warn_last = false;  // BPMF_WARN_NO_VALID of the plan behind the cached graph
+  // library streams on which independent receptor crops are transformed
+  // concurrently (forked from and joined back into the caller's stream)
+  static constexpr int kSide = 4;
+  cudaStream_t side[kSide] = {};
+  int side_next = 0;
 };
 
 struct bpmf_rec {
@@ -818,6 +823,8 @@ void bpmf_destroy(bpmf_ctx_t c) {
   if (!c) return;
   DeviceGuard g(c->device);
   for (auto &kv : c->tw) cudaFree(kv.second);
+  for (cudaStream_t &x : c->side)
+    if (x) cudaStreamDestroy(x);
   if (c->tca) cudaFree(c->tca);
   if (c->ws) cudaFree(c->ws);
   for (auto &r : c->pending) {
@@ -919,12 +926,16 @@ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // Views of receptors' spectra for transform edges Pc <= P: the stored one of
 // a receptor when Pc == P, else its grids cropped to Pc nodes per axis around
-// the site.  Crops made on first use (stream st) are transformed together.
+// the site.  Crops made on first use are transformed together, on one of the
+// library's side streams after the event `fork` of the caller's stream; the
+// event recorded when they are done is appended to `joins` (the caller's
+// stream waits for it) and the receptors made to `touched`.
 // Every node that a translation of the site window reaches with a ligand box
 // of edge u lies in the crop when Pc >= site_n + u - 1: the crop starts
 // floor((site_n - Pc) / 2) nodes from the site, moved inside the grid.
 std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *> &rs, const std::array<int, 3> &Pc,
-                                      cudaStream_t st) {
+                                      cudaEvent_t fork, std::vector<cudaEvent_t> &joins,
+                                      std::vector<bpmf_rec *> &touched) {
   std::vector<bpmf_rec::Crop> out(rs.size());
   std::vector<size_t> todo;
   std::vector<std::array<int, 3>> ext;
@@ -969,6 +980,10 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
   const int n = (int)todo.size();
   const long long Q = (long long)Pc[1] * (Pc[2] / 2 + 1);
   const long long chan = (long long)Emax[0] * Emax[1] * Emax[2];
+  cudaStream_t &cs_slot = c->side[c->side_next++ % bpmf_ctx::kSide];
+  if (!cs_slot) CK(cudaStreamCreateWithFlags(&cs_slot, cudaStreamNonBlocking));
+  const cudaStream_t st = cs_slot;
+  CK(cudaStreamWaitEvent(st, fork, 0));
   float *buf = nullptr;
   std::vector<float2 *> his(n, nullptr), los(n, nullptr);
   try {
@@ -1001,11 +1016,13 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
       if (out[todo[i]].mem) cudaFree(out[todo[i]].mem);
     throw;
   }
+  cudaEvent_t done = pool_event(c);
+  CK(cudaEventRecord(done, st));
+  joins.push_back(done);
   for (int i = 0; i < n; ++i) {
     bpmf_rec *r = rs[todo[i]];
     r->crops[Pc] = out[todo[i]];
-    if (!r->crop_ev) CK(cudaEventCreateWithFlags(&r->crop_ev, cudaEventDisableTiming));
-    CK(cudaEventRecord(r->crop_ev, st));
+    touched.push_back(r);
   }
   resolve();
   return out;
@@ -1364,6 +1381,11 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   std::vector<PairInfo> info;
   std::vector<long long> nv;
   size_t ws_need = 0;
+  // receptor crops made by this call: forked from this point of the stream
+  cudaEvent_t fork = pool_event(c);
+  CK(cudaEventRecord(fork, st));
+  std::vector<cudaEvent_t> joins;
+  std::vector<bpmf_rec *> touched;
   for (int li = lig_begin; li < lig_end; ++li) {
     ligand_tables(lg, li, recs, K, h, meta, info, nv);
     LigPlan pl;
@@ -1410,6 +1432,16 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
             W = std::max(W, recs[g.ks[kg]]->site_n[d] + std::min(mj[i].u[d], g.P[d]) - 1);
           pc[i][d] = split ? g.P[d] : crop_edge(W, g.P[d]);
         }
+      // a crop costs one transform of the group's grids: keep it only where its
+      // configurations save at least 24 configurations' worth of spectrum volume
+      {
+        auto vol = [](const std::array<int, 3> &p) { return (double)p[0] * p[1] * (p[2] / 2 + 1); };
+        const std::array<int, 3> Pf{g.P[0], g.P[1], g.P[2]};
+        std::map<std::array<int, 3>, int> count;
+        for (int i = 0; i < J; ++i) ++count[pc[i]];
+        for (int i = 0; i < J; ++i)
+          if (pc[i] != Pf && count[pc[i]] * (1.0 - vol(pc[i]) / vol(Pf)) < 24.0) pc[i] = Pf;
+      }
       // processing order: by crop, then by ligand-box extent, so each batch's
       // box (the maximum over its members) stays tight; the merge scatters
       // results back to the caller's order
@@ -1479,7 +1511,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         std::vector<RefTab> rt(Kg);
         std::vector<bpmf_rec *> rg(Kg);
         for (int kg = 0; kg < Kg; ++kg) rg[kg] = recs[g.ks[kg]];
-        const std::vector<bpmf_rec::Crop> crs = rec_crops(c, rg, Pc, st);
+        const std::vector<bpmf_rec::Crop> crs = rec_crops(c, rg, Pc, fork, joins, touched);
         for (int kg = 0; kg < Kg; ++kg) {
           bpmf_rec *r = rg[kg];
           const bpmf_rec::Crop &cr = crs[kg];
@@ -1553,9 +1585,19 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   if (!blob.empty()) std::memcpy(c->pinned, blob.data(), blob.size());
   for (const auto &g : groups)
     for (int d = 0; d < 3; ++d) twiddles(c, g.P[d]);
-  // receptor crops may have been made on another stream: order this call after them
+  // join the crops made here; crops made earlier (perhaps on another stream)
+  // are ordered by their receptor's event
   for (int k = 0; k < K; ++k)
     if (recs[k]->crop_ev) CK(cudaStreamWaitEvent(st, recs[k]->crop_ev, 0));
+  for (cudaEvent_t e : joins) {
+    CK(cudaStreamWaitEvent(st, e, 0));
+    c->event_pool.push_back(e);
+  }
+  c->event_pool.push_back(fork);
+  for (bpmf_rec *r : touched) {
+    if (!r->crop_ev) CK(cudaEventCreateWithFlags(&r->crop_ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(r->crop_ev, st));
+  }
   c->warn_last = warn;
 
   // -------------------------------------------------------------- execute

@@ -99,6 +99,32 @@ __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, 
     v[4] = c_sub(t1, u1);
     v[2] = c_add(t2, u2);
     v[3] = c_sub(t2, u2);
+  } else if constexpr (R == 9 || R == 10 || R == 12) {
+    // composite radix R = R1 R2 in registers (Cooley-Tukey, decimation in
+    // time): R2 DFTs of length R1 over the strided inputs v[R2 n1 + n2],
+    // internal twiddles w_R^(n2 k1), then R1 DFTs of length R2; output
+    // k1 + R1 k2
+    constexpr int R1 = R == 9 ? 3 : (R == 10 ? 2 : 4);
+    constexpr int R2 = R / R1;
+    cx<T> a[R2][R1];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) a[n2][n1] = v[R2 * n1 + n2];
+      dft_small<T, R1>(a[n2], inv, tw, P);
+#pragma unroll
+      for (int k1 = 1; k1 < R1; ++k1)
+        if (n2 > 0) a[n2][k1] = c_mul(a[n2][k1], tw_load<T>(tw[(n2 * k1) * (P / R)], inv));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      cx<T> b[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) b[n2] = a[n2][k1];
+      dft_small<T, R2>(b, inv, tw, P);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = b[k2];
+    }
   } else {
     // radix 7: X[a] = sum_b v[b] w_R^(a b), w_R^m = tw[m P / R]
     cx<T> out[R];
@@ -173,57 +199,71 @@ __device__ cx<T> *cta_fft(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, cons
 // ---------------------------------------------------------------------------
 // Compile-time plans for common transform lengths: radices, stage strides and
 // the line count are constants, so the per-butterfly index arithmetic folds
-// away.  Same Stockham stages (and the same rounding) as the generic engine.
-template <int P>
+// away.  CtPlan<P, false> has the stages of the generic engine (the same
+// rounding); CtPlan<P, true> ("few") combines them into two stages with a
+// composite last radix (9, 10 or 12 in registers): one shared-memory pass and
+// one barrier fewer, for callers with enough lines per stage and registers.
+template <int P, bool FEW>
 struct CtPlan {
   static constexpr int nst = 0;
   __host__ __device__ static constexpr int r(int) { return 1; }
 };
-template <>
-struct CtPlan<32> {
+template <bool FEW>
+struct CtPlan<32, FEW> {
   static constexpr int nst = 2;
   __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : 4; }
 };
-template <>
-struct CtPlan<64> {
+template <bool FEW>
+struct CtPlan<64, FEW> {
   static constexpr int nst = 2;
   __host__ __device__ static constexpr int r(int) { return 8; }
 };
 template <>
-struct CtPlan<96> {
+struct CtPlan<96, false> {
   static constexpr int nst = 3;
   __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : (s == 1 ? 4 : 3); }
 };
 template <>
-struct CtPlan<80> {
+struct CtPlan<96, true> {
+  static constexpr int nst = 2;
+  __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : 12; }
+};
+template <>
+struct CtPlan<80, false> {
   static constexpr int nst = 3;
   __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : (s == 1 ? 2 : 5); }
 };
 template <>
-struct CtPlan<72> {
+struct CtPlan<80, true> {
+  static constexpr int nst = 2;
+  __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : 10; }
+};
+template <>
+struct CtPlan<72, false> {
   static constexpr int nst = 3;
   __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : 3; }
 };
 template <>
-struct CtPlan<128> {
+struct CtPlan<72, true> {
+  static constexpr int nst = 2;
+  __host__ __device__ static constexpr int r(int s) { return s == 0 ? 8 : 9; }
+};
+template <bool FEW>
+struct CtPlan<128, FEW> {
   static constexpr int nst = 3;
   __host__ __device__ static constexpr int r(int s) { return s < 2 ? 8 : 2; }
 };
-template <int P>
-__host__ __device__ constexpr bool ct_supported() {
-  return CtPlan<P>::nst > 0;
-}
-template <int P, int S>
+template <int P, bool FEW, int S>
 __host__ __device__ constexpr int ct_ns() {  // product of the radices before stage S
   int n = 1;
-  for (int i = 0; i < S; ++i) n *= CtPlan<P>::r(i);
+  for (int i = 0; i < S; ++i) n *= CtPlan<P, FEW>::r(i);
   return n;
 }
 
-template <class T, int P, int S, int NL, int ES, int LS, int NT>
+template <class T, int P, bool FEW, int S, int NL, int ES, int LS, int NT>
 __device__ __forceinline__ void fft_stage_ct(const cx<T> *src, cx<T> *dst, const float4 *tw, bool inv) {
-  constexpr int R = CtPlan<P>::r(S);
-  constexpr int Ns = ct_ns<P, S>();
+  constexpr int R = CtPlan<P, FEW>::r(S);
+  constexpr int Ns = ct_ns<P, FEW, S>();
   constexpr int nb = P / R;
   constexpr int items = nb * NL;
   constexpr int tstride = P / (Ns * R);
@@ -245,42 +285,42 @@ __device__ __forceinline__ void fft_stage_ct(const cx<T> *src, cx<T> *dst, const
   }
 }
 
-template <class T, int P, int S, int NL, int ES, int LS, int NT>
+template <class T, int P, bool FEW, int S, int NL, int ES, int LS, int NT>
 __device__ __forceinline__ cx<T> *cta_fft_ct_from(cx<T> *src, cx<T> *dst, const float4 *tw, bool inv) {
-  if constexpr (S == CtPlan<P>::nst) {
+  if constexpr (S == CtPlan<P, FEW>::nst) {
     return src;
   } else {
-    fft_stage_ct<T, P, S, NL, ES, LS, NT>(src, dst, tw, inv);
+    fft_stage_ct<T, P, FEW, S, NL, ES, LS, NT>(src, dst, tw, inv);
     __syncthreads();
-    return cta_fft_ct_from<T, P, S + 1, NL, ES, LS, NT>(dst, src, tw, inv);
+    return cta_fft_ct_from<T, P, FEW, S + 1, NL, ES, LS, NT>(dst, src, tw, inv);
   }
 }
 
-// Compile-time counterpart of cta_fft for P in {32, 64, 72, 80, 96, 128}; NT must
-// equal blockDim.x.
-template <class T, int P, int NL, int ES, int LS, int NT>
+// Compile-time counterpart of cta_fft for P in {32, 64, 72, 80, 96, 128}; NT
+// must equal blockDim.x.
+template <class T, int P, bool FEW, int NL, int ES, int LS, int NT>
 __device__ __forceinline__ cx<T> *cta_fft_ct(cx<T> *b0, cx<T> *b1, const float4 *tw, bool inv) {
-  return cta_fft_ct_from<T, P, 0, NL, ES, LS, NT>(b0, b1, tw, inv);
+  return cta_fft_ct_from<T, P, FEW, 0, NL, ES, LS, NT>(b0, b1, tw, inv);
 }
 
 // Transform with the compile-time engine when the plan and line count match a
 // specialisation (lines contiguous: CONTIG, element stride 1, line stride
 // P + 1; otherwise element stride NL, line stride 1), else the generic engine.
-template <class T, int NL, int NT, bool CONTIG>
+template <class T, int NL, int NT, bool CONTIG, bool FEW = false>
 __device__ __forceinline__ cx<T> *cta_fft_auto(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, const FftPlan &pl,
                                                const float4 *tw, bool inv) {
   if (nlines == NL && pl.tca == nullptr) {
     switch (pl.n) {
-      case 96:
-        return CONTIG ? cta_fft_ct<T, 96, NL, 1, 97, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 96, NL, NL, 1, NT>(b0, b1, tw, inv);
-      case 80:
-        return CONTIG ? cta_fft_ct<T, 80, NL, 1, 81, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 80, NL, NL, 1, NT>(b0, b1, tw, inv);
-      case 72:
-        return CONTIG ? cta_fft_ct<T, 72, NL, 1, 73, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 72, NL, NL, 1, NT>(b0, b1, tw, inv);
-      case 64:
-        return CONTIG ? cta_fft_ct<T, 64, NL, 1, 65, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 64, NL, NL, 1, NT>(b0, b1, tw, inv);
-      case 32:
-        return CONTIG ? cta_fft_ct<T, 32, NL, 1, 33, NT>(b0, b1, tw, inv) : cta_fft_ct<T, 32, NL, NL, 1, NT>(b0, b1, tw, inv);
+#define BPMF_CT_CASE(PP)                                                                    \
+  case PP:                                                                                 \
+    return CONTIG ? cta_fft_ct<T, PP, FEW, NL, 1, PP + 1, NT>(b0, b1, tw, inv)             \
+                  : cta_fft_ct<T, PP, FEW, NL, NL, 1, NT>(b0, b1, tw, inv);
+      BPMF_CT_CASE(96)
+      BPMF_CT_CASE(80)
+      BPMF_CT_CASE(72)
+      BPMF_CT_CASE(64)
+      BPMF_CT_CASE(32)
+#undef BPMF_CT_CASE
       default:
         break;
     }

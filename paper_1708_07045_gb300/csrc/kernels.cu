@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::a_min_blocks) k_axi
   for (int idx = n_in * LW + threadIdx.x; idx < P * LW; idx += blockDim.x) b0[idx] = c_zero<T>();
   cp_async_wait_all();
   __syncthreads();
-  cx<T> *res = cta_fft_auto<T, (LWC > 0 ? LWC : 16), KCfg<T>::threads, false>(b0, b1, LW, 1, LW, a.plan, s_tw,
+  cx<T> *res = cta_fft_auto<T, (LWC > 0 ? LWC : 16), KCfg<T>::threads, false, true>(b0, b1, LW, 1, LW, a.plan, s_tw,
                                                                              a.inverse != 0);
   // outputs s < n_out <= P, read at (w0 + s) mod P
   for (int idx = threadIdx.x; idx < a.n_out * LW; idx += blockDim.x) {
