@@ -203,31 +203,69 @@ def run_reference(args):
     return 0
 
 
-def alg_work(w, n_valid, mode):
+def smooth_edge(n):
+    """Smallest even 2^a 3^b 5^c 7^d >= n (the library's transform edges)."""
+    p = max(n, 2)
+    while True:
+        if p % 2 == 0:
+            m = p
+            for r in (2, 3, 5, 7):
+                while m % r == 0:
+                    m //= r
+            if m == 1:
+                return p
+        p += 1
+
+
+def crop_edges(u, S, P, J):
+    """Transform edges per configuration as the library chooses them: the crop
+    edge near 5P/6 on each axis where the site reach S + u - 1 fits, kept for a
+    crop only when its configurations save at least 24 configurations' worth
+    of spectrum volume.  u: [J, 3] ligand-box edges."""
+    p1 = smooth_edge((5 * P + 5) // 6)
+    pc = np.where(S + np.minimum(u, P) - 1 <= p1, p1, P)
+    vol = lambda t: t[0] * t[1] * (t[2] // 2 + 1)
+    keys = [tuple(int(v) for v in r) for r in pc]
+    cnt = {}
+    for k in keys:
+        cnt[k] = cnt.get(k, 0) + 1
+    full = (P, P, P)
+    for j, k in enumerate(keys):
+        if k != full and cnt[k] * (1 - vol(k) / vol(full)) < 24:
+            pc[j] = P
+    return pc
+
+
+def alg_work(w, n_valid, mode, launches_per_step=None):
     """Algorithmic FLOPs (5 P log2 P per complex line transform, 8 per complex
-    multiply-add) and bytes per kernel for the whole step."""
+    multiply-add) and bytes per kernel for the whole step, on each
+    configuration's transform edges (the receptor crop it runs on).  Bytes:
+    the ligand spectra read and x-pass outputs written per configuration, and
+    the receptor spectra read once per launch (launches_per_step launches
+    share them; one per configuration when not given)."""
     P = 96
-    F2 = P // 2 + 1
-    Q = P * F2
     S = 40
     K = N_REC
     J = N_CONF
-    lg = np.log2(P)
-    cfft = 5 * P * lg
     E = 16 if mode == "ff" else 8
-    u = []
     lig = w.ligands[0]
-    for j in range(J):
-        ext = (lig.coords[j].max(0) - lig.coords[j].min(0)).astype(np.float32)
-        u.append(np.minimum(np.ceil((ext / np.float32(0.25)).astype(np.float32)).astype(int) + 4, P))
-    u = np.array(u)
+    ext = (lig.coords.max(1) - lig.coords.min(1)).astype(np.float32)
+    u = np.minimum(np.ceil((ext / np.float32(0.25)).astype(np.float32)).astype(int) + 4, P)
+    pc = crop_edges(u, S, P, J)
+    P0, P1, P2 = pc[:, 0].astype(float), pc[:, 1].astype(float), pc[:, 2].astype(float)
+    F2 = np.floor(P2 / 2) + 1
+    Q = P1 * F2
+    cfft = lambda p: 5 * p * np.log2(p)
+    per_launch = J / launches_per_step if launches_per_step else 1.0
+    rec_mult = 2 if mode == "ff" else 1
     work = {}
     # x-pass: forward of 3 channels, then per receptor product + inverse, per (y, zf) column
-    work["k_xfused"] = {"flops": J * Q * (3 * cfft + K * (cfft + 3 * 8 * P)),
-                        "bytes": float(np.sum(3 * u[:, 0] * Q * E) + J * K * 3 * P * Q * E / 2 * (2 if mode == "ff" else 1)
-                                       + J * K * S * Q * E)}
-    work["k_axis(y inv)"] = {"flops": J * K * S * F2 * cfft, "bytes": J * K * S * (Q + S * F2) * E}
-    work["k_zinv"] = {"flops": J * K * S * (S / 2) * cfft, "bytes": J * K * S * S * F2 * E}
+    work["k_xfused"] = {"flops": float(np.sum(Q * (3 * cfft(P0) + K * (cfft(P0) + 3 * 8 * P0)))),
+                        "bytes": float(np.sum(3 * u[:, 0] * Q * E + K * S * Q * E
+                                              + K * 3 * P0 * Q * 8 * rec_mult / per_launch))}
+    work["k_axis(y inv)"] = {"flops": float(np.sum(K * S * F2 * cfft(P1))),
+                             "bytes": float(np.sum(K * S * (Q + S * F2) * E))}
+    work["k_zinv"] = {"flops": float(np.sum(K * S * (S / 2) * cfft(P2))), "bytes": float(np.sum(K * S * S * F2 * E))}
     return work
 
 
@@ -784,8 +822,8 @@ def run_ours(args):
                    "kind": "oracle", "sample": f"first {ns} of {N_CONF} configurations x {K} receptors, "
                                               f"all valid translations ({dt:.1f} s)"}
         # roofline of the dominant kernel, from the live per-kernel event times
-        work = alg_work(w, res_chosen["n_valid"], chosen)
         top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else None
+        work = alg_work(w, res_chosen["n_valid"], chosen, launches_per_step=top[1][1] / args.steps if top else None)
         roof = None
         if top:
             name, (ms_tot, nl) = top

@@ -51,7 +51,7 @@ struct bpmf_ctx {
   // them changes a result bit (every line transform is independent)
   struct Tune {
     int batch_cap = 0;  // configurations per batch (0: as many as the workspace holds)
-    int axis_lw = 16;   // lines per CTA cap of the strided passes
+    int axis_lw = 0;    // lines per CTA of the strided passes (0: 32 for FP32 lines, 16 for float pairs)
     int zfwd_l = 16;    // complex lines per CTA of the z R2C pass
   };
   std::map<std::vector<int>, Tune> tune;
@@ -542,7 +542,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     ya.inverse = 0;
     ya.plan = plan(g.P[1]);
     ya.tw = twiddles(c, g.P[1]);
-    ya.LW = tn.axis_lw;
+    ya.LW = tn.axis_lw > 0 ? tn.axis_lw : (sizeof(T) == 4 ? 32 : 16);
     launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y fwd)" : "k_axis<ff>(y fwd)", st, [&] { return launch_axis<T>(ya, st); });
   }
 
@@ -576,7 +576,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   yi.inverse = 1;
   yi.plan = plan(g.P[1]);
   yi.tw = twiddles(c, g.P[1]);
-  yi.LW = tn.axis_lw;
+  yi.LW = tn.axis_lw > 0 ? tn.axis_lw : (sizeof(T) == 4 ? 32 : 16);
   launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y inv)" : "k_axis<ff>(y inv)", st, [&] { return launch_axis<T>(yi, st); });
 
   ZinvArgs zi{};
@@ -1816,7 +1816,7 @@ int bpmf_autotune(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, un
       const float tt = timeit(t);
       if (tt < tbest) tbest = tt, best = t;
     }
-    for (int lw : {8}) {
+    for (int lw : {8, 16}) {
       bpmf_ctx::Tune t = best;
       t.axis_lw = lw;
       const float tt = timeit(t);

@@ -360,6 +360,7 @@ template <class T>
 cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
   if (a.n_outer <= 0 || a.inner <= 0) return cudaSuccess;
   if (a.LW < 1 || a.LW > 64 || a.n_out > a.plan.n) return cudaErrorInvalidValue;
+  if (a.LW == 32) return launch_axis_lw<T, 32>(a, st);
   if (a.LW == 16) return launch_axis_lw<T, 16>(a, st);
   if (a.LW == 8) return launch_axis_lw<T, 8>(a, st);
   return launch_axis_lw<T, 0>(a, st);
