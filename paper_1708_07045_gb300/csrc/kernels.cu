@@ -373,14 +373,20 @@ cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
 // inverse DFT, keep the site window along x.  Each receptor element is loaded
 // once per CTA and used for all G configurations; the ligand spectra never
 // leave shared memory.
-template <class T>
+template <class T, int KP>
 __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfused(XfusedArgs a, int batch) {
   extern __shared__ float4 smem[];
   constexpr int LW = KCfg<T>::xlw, G = KCfg<T>::xconf, LG = G * LW, L3 = 3 * LG;
+  constexpr int LK = KP * LG;  // inverse lines per pass: KP receptors x G configurations x LW columns
+  constexpr int LB = L3 > 2 * LK ? L3 : 2 * LK;
   const int P = a.plan.n;
   float4 *s_tw = smem;
-  cx<T> *bA = reinterpret_cast<cx<T> *>(smem + P);
-  cx<T> *bB = bA + P * L3;
+  // R = [bB: LB lines][bA: L3 lines]; the forward transform runs bA -> bB ->
+  // ..., and whichever buffer holds its result, the other P (L3 + LB) - P L3
+  // elements form one contiguous free region of at least 2 LK lines
+  cx<T> *R = reinterpret_cast<cx<T> *>(smem + P);
+  cx<T> *bB = R;
+  cx<T> *bA = R + P * LB;
   load_tw(s_tw, a.tw, P);
   // tile-major order: CTAs resident together share a column tile across many
   // configurations, so that tile's receptor spectra are served from L2
@@ -399,55 +405,79 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfu
   cp_async_wait_all();
   __syncthreads();
   cx<T> *Lsp = cta_fft_auto<T, L3, KCfg<T>::threads, false>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
-  cx<T> *W1 = (Lsp == bA) ? bB : bA;
-  cx<T> *W2 = W1 + P * LG;
-  __shared__ int s_wm[G];  // per configuration: site window start along x, mod P
-  for (int k = 0; k < a.K; ++k) {
-    const float2 *rh = a.rhi[k];
-    const float2 *rl = a.rlo ? a.rlo[k] : nullptr;
-    if (threadIdx.x < G) s_wm[threadIdx.x] = j0 + (int)threadIdx.x < batch ? imod(a.info[(j0 + threadIdx.x) * a.K + k].wc[0], P) : 0;
+  cx<T> *W1 = (Lsp == bB) ? R + P * L3 : R;
+  cx<T> *W2 = W1 + P * LK;
+  __shared__ int s_wm[KP * G];  // per (receptor of the pass, configuration): site window start along x, mod P
+  for (int k0 = 0; k0 < a.K; k0 += KP) {
+    if (threadIdx.x < KP * G) {
+      const int kk = threadIdx.x / G, j = j0 + (int)threadIdx.x % G;
+      s_wm[threadIdx.x] = (j < batch && k0 + kk < a.K) ? imod(a.info[j * a.K + k0 + kk].wc[0], P) : 0;
+    }
+    // inverse line c = (kk * G + g) * LW + l
     for (int idx = threadIdx.x; idx < P * LW; idx += blockDim.x) {
       const int x = idx / LW, l = idx % LW;
       const long long q = q0 + l;
-      cx<T> r0 = c_zero<T>(), r1 = c_zero<T>(), r2 = c_zero<T>();
-      if (q < a.Q) {
-        const long long ri = (long long)x * a.Q + q, rs = (long long)P * a.Q;
-        r0 = ld_rec(rh, rl, ri, T{});
-        r1 = ld_rec(rh, rl, ri + rs, T{});
-        r2 = ld_rec(rh, rl, ri + 2 * rs, T{});
-      }
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const cx<T> *lx = Lsp + x * L3 + g * 3 * LW + l;
-        const cx<T> acc = c_add(c_add(c_mulconj(r0, lx[0]), c_mulconj(r1, lx[LW])), c_mulconj(r2, lx[2 * LW]));
-        W1[x * LG + g * LW + l] = c_norm(acc);
+      for (int kk = 0; kk < KP; ++kk) {
+        cx<T> r0 = c_zero<T>(), r1 = c_zero<T>(), r2 = c_zero<T>();
+        if (q < a.Q && k0 + kk < a.K) {
+          const float2 *rh = a.rhi[k0 + kk];
+          const float2 *rl = a.rlo ? a.rlo[k0 + kk] : nullptr;
+          const long long ri = (long long)x * a.Q + q, rs = (long long)P * a.Q;
+          r0 = ld_rec(rh, rl, ri, T{});
+          r1 = ld_rec(rh, rl, ri + rs, T{});
+          r2 = ld_rec(rh, rl, ri + 2 * rs, T{});
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const cx<T> *lx = Lsp + x * L3 + g * 3 * LW + l;
+          const cx<T> acc = c_add(c_add(c_mulconj(r0, lx[0]), c_mulconj(r1, lx[LW])), c_mulconj(r2, lx[2 * LW]));
+          W1[x * LK + (kk * G + g) * LW + l] = c_norm(acc);
+        }
       }
     }
     __syncthreads();
-    cx<T> *res = cta_fft_auto<T, LG, KCfg<T>::threads, false>(W1, W2, LG, 1, LG, a.plan, s_tw, true);
-    for (int idx = threadIdx.x; idx < a.S0 * LG; idx += blockDim.x) {
-      const int s = idx / LG, c = idx % LG, j = j0 + c / LW, l = c % LW;
+    cx<T> *res = cta_fft_auto<T, LK, KCfg<T>::threads, false>(W1, W2, LK, 1, LK, a.plan, s_tw, true);
+    for (int idx = threadIdx.x; idx < a.S0 * LK; idx += blockDim.x) {
+      const int s = idx / LK, c = idx % LK, kg = c / LW, l = c % LW;
+      const int k = k0 + kg / G, j = j0 + kg % G;
       const long long q = q0 + l;
-      if (q < a.Q && j < batch) {
-        const int m = s_wm[c / LW] + s;  // s < S0 <= P
-        st_cx<T>(a.x2, (((long long)j * a.K + k) * a.S0 + s) * a.Q + q, res[(m >= P ? m - P : m) * LG + c]);
+      if (q < a.Q && j < batch && k < a.K) {
+        const int m = s_wm[kg] + s;  // s < S0 <= P
+        st_cx<T>(a.x2, (((long long)j * a.K + k) * a.S0 + s) * a.Q + q, res[(m >= P ? m - P : m) * LK + c]);
       }
     }
     __syncthreads();
   }
 }
 
+template <class T, int KP>
+size_t xfused_smem(int P) {
+  constexpr int LW = KCfg<T>::xlw, G = KCfg<T>::xconf, L3 = 3 * G * LW, LK = KP * G * LW;
+  constexpr int LB = L3 > 2 * LK ? L3 : 2 * LK;
+  return sizeof(float4) * P + sizeof(cx<T>) * (size_t)P * (L3 + LB);
+}
+
+template <class T, int KP>
+cudaError_t launch_xfused_kp(const XfusedArgs &a, int batch, cudaStream_t st) {
+  constexpr int LW = KCfg<T>::xlw, G = KCfg<T>::xconf;
+  const size_t smem = xfused_smem<T, KP>(a.plan.n);
+  cudaError_t e = cudaFuncSetAttribute(k_xfused<T, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (long long)((batch + G - 1) / G) * ((a.Q + LW - 1) / LW);
+  k_xfused<T, KP><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a, batch);
+  return cudaGetLastError();
+}
+
+// Two receptors per inverse pass (twice the lines per transform stage) when
+// several receptors share the pass and the larger shared-memory footprint
+// still leaves x_min_blocks CTAs per SM.
 template <class T>
 cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  const int P = a.plan.n;
-  constexpr int LW = KCfg<T>::xlw, G = KCfg<T>::xconf;
-  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * 3 * G * LW;
-  cudaError_t e = cudaFuncSetAttribute(k_xfused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const long long blocks = (long long)((batch + G - 1) / G) * ((a.Q + LW - 1) / LW);
-  k_xfused<T><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a, batch);
-  return cudaGetLastError();
+  if (a.K >= 2 && xfused_smem<T, 2>(a.plan.n) * KCfg<T>::x_min_blocks <= 227 * 1024)
+    return launch_xfused_kp<T, 2>(a, batch, st);
+  return launch_xfused_kp<T, 1>(a, batch, st);
 }
 
 // --------------------------------------------------------------------------
