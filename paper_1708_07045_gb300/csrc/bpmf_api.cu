@@ -61,6 +61,10 @@ struct bpmf_ctx {
   static constexpr int kSide = 4;
   cudaStream_t side[kSide] = {};
   int side_next = 0;
+  // device blocks of freed handles, by size, reused by later handles of the
+  // same size (the free synchronises the device first, as cudaFree does)
+  std::multimap<size_t, void *> blocks;
+  size_t block_bytes = 0;
 };
 
 struct bpmf_rec {
@@ -72,6 +76,7 @@ struct bpmf_rec {
   double origin[3] = {0, 0, 0};
   int site_lo[3] = {0, 0, 0}, site_n[3] = {0, 0, 0};
   void *mem = nullptr;                  // one device block holding grid, sumsq, hi and lo
+  size_t mem_bytes = 0;
   float2 *hi = nullptr, *lo = nullptr;  // [3][P0][Q]
   uint32_t *occ = nullptr;              // occupancy tables [kOccLevels][N0 + 32][occW][N1 + 32], or null
   int occW = 0;
@@ -81,6 +86,7 @@ struct bpmf_rec {
   // site, made on first use, per P (the uncropped spectrum is hi / lo)
   struct Crop {
     void *mem = nullptr;                // the device block holding hi, lo and sumsq (null: a view)
+    size_t mem_bytes = 0;
     int c0[3] = {0, 0, 0};              // first node of the crop
     float2 *hi = nullptr, *lo = nullptr;  // [3][P0][P1 (P2/2+1)]
     double *sumsq = nullptr;            // [3] over the cropped nodes
@@ -104,6 +110,7 @@ struct bpmf_lig {
   std::vector<float> q_host, eps_host;  // host [total_atoms] (FP32 error bound)
   double *gamma64 = nullptr;  // device [3][total_atoms] FP64 generalised charges (refined form)
   void *mem = nullptr;        // one device block holding coords, gamma, q, eps, R and gamma64
+  size_t mem_bytes = 0;
   int p_rep = 12, p_att = 6;
 };
 
@@ -289,8 +296,36 @@ cudaEvent_t pool_event(bpmf_ctx *c) {
   return e;
 }
 
+// Handle blocks: a cached block of exactly `bytes` if one is free, else a
+// new allocation.  block_put returns a block to the cache (up to 2 GiB) or
+// frees it; callers synchronise the device before returning a block.
+constexpr size_t kBlockCacheCap = size_t(2) << 30;
+
+void *block_get(bpmf_ctx *c, size_t bytes) {
+  auto it = c->blocks.find(bytes);
+  if (it != c->blocks.end()) {
+    void *p = it->second;
+    c->blocks.erase(it);
+    c->block_bytes -= bytes;
+    return p;
+  }
+  void *p = nullptr;
+  CK(cudaMalloc(&p, bytes));
+  return p;
+}
+
+void block_put(bpmf_ctx *c, void *p, size_t bytes) {
+  if (!p) return;
+  if (c->block_bytes + bytes <= kBlockCacheCap) {
+    c->blocks.insert({bytes, p});
+    c->block_bytes += bytes;
+  } else {
+    cudaFree(p);
+  }
+}
+
 // Sub-buffers of one device allocation: add() reserves 256-byte aligned
-// ranges, alloc() makes the block and returns its base.
+// ranges, alloc() takes the block (block_get) and returns its base.
 struct Carve {
   std::vector<std::pair<void **, size_t>> parts;
   size_t total = 0;
@@ -299,9 +334,8 @@ struct Carve {
     parts.push_back({reinterpret_cast<void **>(ptr), total});
     total += align_up(std::max<size_t>(bytes, 1));
   }
-  void *alloc() {
-    void *base = nullptr;
-    CK(cudaMalloc(&base, total));
+  void *alloc(bpmf_ctx *c) {
+    void *base = block_get(c, total);
     for (auto &pr : parts) *pr.first = static_cast<char *>(base) + pr.second;
     return base;
   }
@@ -825,6 +859,7 @@ void bpmf_destroy(bpmf_ctx_t c) {
   for (auto &kv : c->tw) cudaFree(kv.second);
   for (cudaStream_t &x : c->side)
     if (x) cudaStreamDestroy(x);
+  for (auto &kv : c->blocks) cudaFree(kv.second);
   if (c->tca) cudaFree(c->tca);
   if (c->ws) cudaFree(c->ws);
   for (auto &r : c->pending) {
@@ -993,7 +1028,8 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
       cv.add(&cr.hi, 3ull * Pc[0] * Q * sizeof(float2));
       cv.add(&cr.lo, 3ull * Pc[0] * Q * sizeof(float2));
       cv.add(&cr.sumsq, 3 * sizeof(double));
-      cr.mem = cv.alloc();
+      cr.mem = cv.alloc(c);
+      cr.mem_bytes = cv.total;
       his[i] = cr.hi;
       los[i] = cr.lo;
     }
@@ -1075,7 +1111,8 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
     cv.add(&r->sumsq, 3 * sizeof(double));
     cv.add(&r->hi, 3ull * P[0] * r->Q * sizeof(float2));
     cv.add(&r->lo, 3ull * P[0] * r->Q * sizeof(float2));
-    r->mem = cv.alloc();
+    r->mem = cv.alloc(c);
+    r->mem_bytes = cv.total;
     CK(cudaMemcpyAsync(r->grid, g.p, 3 * vol * sizeof(float), cudaMemcpyDeviceToDevice, st));
     launch(c, "k_sumsq", st, [&] { return launch_sumsq(r->grid, (long long)vol, r->sumsq, st); });
     grid_spectrum(c, static_cast<const float *>(g.p), 1, N, P, &r->hi, &r->lo, st);
@@ -1093,11 +1130,19 @@ void bpmf_receptor_free(bpmf_rec_t r) {
   if (!r) return;
   if (r->ctx) {
     DeviceGuard g(r->ctx->device);
-    if (r->mem) cudaFree(r->mem);
+    // blocks return to the context's cache once no queued work can read them
+    const bool idle = cudaDeviceSynchronize() == cudaSuccess;
+    if (!idle) cudaGetLastError();
+    auto put = [&](void *p, size_t bytes) {
+      if (idle)
+        block_put(r->ctx, p, bytes);
+      else if (p)
+        cudaFree(p);
+    };
+    put(r->mem, r->mem_bytes);
     if (r->occ) cudaFree(r->occ);
     if (r->crop_ev) cudaEventDestroy(r->crop_ev);
-    for (auto &kv : r->crops)
-      if (kv.second.mem) cudaFree(kv.second.mem);
+    for (auto &kv : r->crops) put(kv.second.mem, kv.second.mem_bytes);
   }
   delete r;
 }
@@ -1188,7 +1233,8 @@ int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_
     cv.add(&lg->R, na * sizeof(float));
     cv.add(&lg->gamma64, 3 * std::max<size_t>(na, 1) * sizeof(double));
     cv.add(&lg->coords, std::max<size_t>(1, 3 * lg->total_coord_atoms) * sizeof(float));
-    lg->mem = cv.alloc();
+    lg->mem = cv.alloc(c);
+    lg->mem_bytes = cv.total;
     CK(cudaMemcpyAsync(lg->q, q, na * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaMemcpyAsync(lg->eps, eps, na * sizeof(float), cudaMemcpyDefault, st));
     CK(cudaMemcpyAsync(lg->R, R, na * sizeof(float), cudaMemcpyDefault, st));
@@ -1253,7 +1299,15 @@ void bpmf_ligand_free(bpmf_lig_t lg) {
   if (!lg) return;
   if (lg->ctx) {
     DeviceGuard g(lg->ctx->device);
-    if (lg->mem) cudaFree(lg->mem);
+    if (lg->mem) {
+      // the block returns to the context's cache once no queued work can read it
+      if (cudaDeviceSynchronize() == cudaSuccess) {
+        block_put(lg->ctx, lg->mem, lg->mem_bytes);
+      } else {
+        cudaGetLastError();
+        cudaFree(lg->mem);
+      }
+    }
   }
   delete lg;
 }
