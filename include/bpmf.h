@@ -90,7 +90,9 @@ typedef struct bpmf_rec *bpmf_rec_t;
 typedef struct bpmf_lig *bpmf_lig_t;
 
 /* Create a context bound to CUDA device `device`.  Errors: INVALID_ARG (no
- * such device), CUDA. */
+ * such device), CUDA.  bpmf_destroy releases the context's device memory,
+ * including the blocks that freed receptors and ligand batches left in its
+ * cache (see bpmf_receptor_free); free every handle of the context first. */
 int bpmf_create(int device, bpmf_ctx_t *out);
 void bpmf_destroy(bpmf_ctx_t ctx);
 
@@ -127,6 +129,10 @@ const char *bpmf_last_error(bpmf_ctx_t ctx);
 int bpmf_receptor_load(bpmf_ctx_t ctx, const float *grids, int nx, int ny, int nz, double h,
                        const double origin[3], const int site_lo[3], const int site_n[3], void *stream,
                        bpmf_rec_t *out);
+/* Frees a receptor.  It synchronises the device (as cudaFree does) and
+ * keeps the receptor's device blocks (its spectra, and the spectra of its
+ * site crops made by bpmf_eval) in the context's cache, up to 2 GiB, for the
+ * next receptor or crop of the same size; the rest is freed. */
 void bpmf_receptor_free(bpmf_rec_t rec);
 
 /*
@@ -176,6 +182,8 @@ int bpmf_receptor_set_occupancy(bpmf_ctx_t ctx, bpmf_rec_t rec, const uint8_t *o
 int bpmf_ligand_batch(bpmf_ctx_t ctx, int n_lig, const int *n_atoms, const int *n_conf, const float *coords,
                       const float *q, const float *eps, const float *R, int p_rep, int p_att, void *stream,
                       bpmf_lig_t *out);
+/* Frees a ligand batch; synchronises the device and keeps its device block in
+ * the context's cache, as bpmf_receptor_free. */
 void bpmf_ligand_free(bpmf_lig_t lig);
 
 /*
@@ -196,6 +204,15 @@ void bpmf_ligand_free(bpmf_lig_t lig);
  *            SIZE_UNSUPPORTED).  Receptors with different grid sizes are
  *            processed in groups of equal padded FFT edges; the ligand's
  *            forward transforms are shared within a group.
+ * Cropped transforms: a configuration's energies over the site window read
+ * only the receptor nodes within site_n + u - 1 of the site (u its ligand-box
+ * edge).  Where that reach fits a smaller smooth edge (about 5/6 of the
+ * padded edge) on an axis, and enough configurations share the crop to pay
+ * for its transform, the configuration runs on the receptor grids cropped to
+ * that edge around the site: the same energies, up to rounding, from smaller
+ * transforms.  A receptor's crop spectra are made on first use (on library
+ * streams forked from and joined back into `stream`) and kept until
+ * bpmf_receptor_free.  The split-BF16 form always uses the full edges.
  *  kT        > 0 (kcal/mol).
  *  mode      BPMF_MODE_FP32, BPMF_MODE_FF, BPMF_MODE_SPLIT_BF16 or BPMF_MODE_REFINE.
  *  logZ      [total_conf][K] float64, total_conf = sum n_conf, ligand-major.
