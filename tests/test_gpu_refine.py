@@ -123,3 +123,29 @@ def test_refined_matches_float_pairs_on_batches(pkg):
     assert np.abs(a["logZ"][fin] - b["logZ"][fin]).max() * KT <= E_TOL
     okb = np.isfinite(a["bpmf"])
     assert np.abs(a["bpmf"][okb] - b["bpmf"][okb]).max() <= B_TOL
+
+
+def test_refined_protein_scale_full_size_on_cropped_transforms(pkg):
+    """All 2000 configurations of the protein-scale workload in one call, as the
+    benchmark runs it.  Enough configurations share each receptor crop that the
+    transforms run on cropped grids (checked through the launch profile: the
+    crops are made and the x pass runs); log Z of every 16th configuration
+    against the FP64 oracle, and the BPMFs of that sample."""
+    w = synth.protein_scale()
+    lig = w.ligands[0]
+    J, K = lig.coords.shape[0], len(w.receptors)
+    with _session() as s:
+        rhs = [s.load_receptor(r) for r in w.receptors]
+        lh, _, _ = s.load_ligands([lig])
+        pkg.bpmf_profile_enable(s.ctx, True)
+        rc, out = s.eval(lh, rhs, KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=J)
+        prof = pkg.bpmf_profile(s.ctx)
+        pkg.bpmf_profile_enable(s.ctx, False)
+    assert prof.get("k_crop", (0.0, 0))[1] > 0, sorted(prof)
+    idx = np.arange(0, J, 16)
+    ref = oracle.evaluate(w.receptors, lig.coords[idx], lig.params.q, lig.params.eps, lig.params.R, KT)
+    assert np.array_equal(out["n_valid"][idx], ref["n_valid"])
+    ok = np.isfinite(ref["logZ"])
+    assert np.abs(out["logZ"][idx][ok] - ref["logZ"][ok]).max() * KT <= E_TOL
+    logS = out["logZ"][idx] + np.log(out["n_valid"][idx])
+    assert np.abs(oracle.bpmf(logS, out["n_valid"][idx], KT) - ref["bpmf"]).max() <= B_TOL
