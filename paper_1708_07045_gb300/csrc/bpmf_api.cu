@@ -594,24 +594,28 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   xa.tw = twiddles(c, g.P[0]);
   launch(c, sizeof(T) == 4 ? "k_xfused<fp32>" : "k_xfused<ff>", st, [&] { return launch_xfused<T>(xa, batch, st); });
 
-  AxisArgs yi{};
-  yi.in = x2;
-  yi.out = y2;
-  yi.P = g.P[1];
-  yi.n_in = g.P[1];
-  yi.n_out = g.S[1];
-  yi.n_outer = (long long)batch * g.K * g.S[0];
-  yi.inner = g.F2;
-  yi.in_os = g.Q;
-  yi.out_os = (long long)g.S[1] * g.F2;
-  yi.info = d_info;
-  yi.w0_div = g.S[0];
-  yi.axis = 1;
-  yi.inverse = 1;
-  yi.plan = plan(g.P[1]);
-  yi.tw = twiddles(c, g.P[1]);
-  yi.LW = tn.axis_lw > 0 ? tn.axis_lw : (sizeof(T) == 4 ? 32 : 16);
-  launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y inv)" : "k_axis<ff>(y inv)", st, [&] { return launch_axis<T>(yi, st); });
+  // FP32 forms: the y inverse runs inside the z inverse when the window fits
+  const bool fuse_y = sizeof(T) == 4 && !split && zinv_fused_fits(g.P[1], g.P[2], g.S[1], g.S[2]);
+  if (!fuse_y) {
+    AxisArgs yi{};
+    yi.in = x2;
+    yi.out = y2;
+    yi.P = g.P[1];
+    yi.n_in = g.P[1];
+    yi.n_out = g.S[1];
+    yi.n_outer = (long long)batch * g.K * g.S[0];
+    yi.inner = g.F2;
+    yi.in_os = g.Q;
+    yi.out_os = (long long)g.S[1] * g.F2;
+    yi.info = d_info;
+    yi.w0_div = g.S[0];
+    yi.axis = 1;
+    yi.inverse = 1;
+    yi.plan = plan(g.P[1]);
+    yi.tw = twiddles(c, g.P[1]);
+    yi.LW = tn.axis_lw > 0 ? tn.axis_lw : (sizeof(T) == 4 ? 32 : 16);
+    launch(c, sizeof(T) == 4 ? "k_axis<fp32>(y inv)" : "k_axis<ff>(y inv)", st, [&] { return launch_axis<T>(yi, st); });
+  }
 
   ZinvArgs zi{};
   zi.y2 = y2;
@@ -633,7 +637,14 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   zi.CW = CW;
   zi.plan = plan(g.P[2]);
   zi.tw = twiddles(c, g.P[2]);
-  launch(c, sizeof(T) == 4 ? "k_zinv<fp32>" : "k_zinv<ff>", st, [&] { return launch_zinv<T>(zi, batch, st); });
+  if (fuse_y) {
+    zi.x2 = x2;
+    zi.Qx = g.Q;
+    zi.yplan = plan(g.P[1]);
+    zi.tw1 = twiddles(c, g.P[1]);
+  }
+  launch(c, fuse_y ? "k_zinv<fp32>(+y inv)" : (sizeof(T) == 4 ? "k_zinv<fp32>" : "k_zinv<ff>"), st,
+         [&] { return launch_zinv<T>(zi, batch, st); });
   if (g.refine) {
     RefineArgs ra{};
     ra.E = Ebuf;

@@ -486,16 +486,28 @@ cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st) {
 __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 __device__ __forceinline__ bool ff_gt(float a, float b) { return a > b; }
 
-template <class T>
+template <class T, int NY>
 __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, F = a.F2, ls = P + 1;
   const int Lc = a.Lc;  // row pairs per chunk (all of them when they fit)
-  float4 *s_tw = smem;
-  cx<T> *b0 = reinterpret_cast<cx<T> *>(smem + P);
-  cx<T> *b1 = b0 + Lc * ls;
   const int b1n = Lc * ls > 2 * Lc * F ? Lc * ls : 2 * Lc * F;
-  T *xs = reinterpret_cast<T *>(b1 + b1n);  // [2 Lc * S2]
+  float4 *s_tw = smem;
+  cx<T> *b0, *b1;
+  T *xs;  // [2 Lc * S2]
+  float4 *s_tw1 = nullptr;
+  if constexpr (NY == 0) {
+    b0 = reinterpret_cast<cx<T> *>(smem + P);
+    b1 = b0 + Lc * ls;
+    xs = reinterpret_cast<T *>(b1 + b1n);
+  } else {
+    // [tw (P2)][tw1 (P1)][b1][b0][xs]: the y pass's two buffers (2 P1 NY
+    // elements) overlay b0 and xs, which are free until the z transform
+    s_tw1 = smem + P;
+    b1 = reinterpret_cast<cx<T> *>(s_tw1 + a.yplan.n);
+    b0 = b1 + b1n;
+    xs = reinterpret_cast<T *>(b0 + Lc * ls);
+  }
   __shared__ T s_red[8];
   __shared__ float s_sum[8];
   load_tw(s_tw, a.tw, P);
@@ -503,6 +515,33 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
   const int jk = blockIdx.x / a.S0;  // j * K + k
   const PairInfo inf = a.info[jk];
   const bool row_ok = (s0 >= inf.sa[0] && s0 <= inf.sb[0]);
+  if constexpr (NY > 0) {
+    // y inverse of this CTA's plane in sub-passes of NY columns (the per-line
+    // arithmetic of k_axis's two-stage plan, so the values are the same);
+    // the site window rows land in b1 as the z pass's staged input
+    const int P1 = a.yplan.n;
+    load_tw(s_tw1, a.tw1, P1);
+    if (row_ok) {  // uniform over the CTA
+      cx<T> *yb = b0;
+      const int w1 = imod(inf.wc[1], P1);
+      const long long plane = (long long)blockIdx.x * a.Qx;
+      for (int c0 = 0; c0 < F; c0 += NY) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < P1 * NY; idx += blockDim.x) {
+          const int ky = idx / NY, l = idx % NY;
+          cp_cx<T>(&yb[idx], a.x2, plane + (long long)ky * F + c0 + l, c0 + l < F);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        cx<T> *res = cta_fft_auto<T, NY, 256, false, true>(yb, yb + P1 * NY, NY, 1, NY, a.yplan, s_tw1, true);
+        for (int idx = threadIdx.x; idx < a.S1 * NY; idx += blockDim.x) {
+          const int s1 = idx / NY, l = idx % NY;
+          const int m = w1 + s1;  // s1 < S1 <= P1
+          if (c0 + l < F) b1[s1 * F + c0 + l] = res[(m >= P1 ? m - P1 : m) * NY + l];
+        }
+      }
+    }
+  }
   const T nscale = s_mk<T>(a.nscale_hi, a.nscale_lo);
   const T escale = s_mk<T>(a.escale_hi, a.escale_lo);
   // running max-shifted sum over the chunks: M_run and s_run relative to it
@@ -515,7 +554,7 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
     // then pack row pairs as z = A + iB with Hermitian extension
     cx<T> *stg = b1;
     __syncthreads();
-    if (row_ok) {
+    if (NY == 0 && row_ok) {  // fused: the y pass has staged the one chunk already
       for (int idx = threadIdx.x; idx < nrow * F; idx += blockDim.x) cp_cx<T>(&stg[idx], a.y2, base + idx, true);
       cp_async_wait_all();
     }
@@ -655,22 +694,53 @@ size_t zinv_smem(const ZinvArgs &a, int Lc) {
   return sizeof(float4) * P + sizeof(cx<T>) * ((size_t)Lc * (P + 1) + b1n) + sizeof(T) * (size_t)2 * Lc * a.S2;
 }
 
+// Fused y + z inverse (FP32): y sub-pass width for F2 columns (two sub-passes
+// of at most 21 or 25 lines), 0 when F2 is wider
+int zinv_ny(int F2) { return F2 <= 42 ? 21 : (F2 <= 50 ? 25 : 0); }
+
+size_t zinv_fused_smem(int P1, int P2, int S1, int S2) {
+  const int F2 = P2 / 2 + 1, Lc = (S1 + 1) / 2, NY = zinv_ny(F2);
+  const size_t b1n = std::max((size_t)Lc * (P2 + 1), (size_t)2 * Lc * F2);
+  const size_t tail = std::max(sizeof(cx<float>) * Lc * (P2 + 1) + sizeof(float) * 2 * Lc * S2,
+                               sizeof(cx<float>) * 2 * P1 * NY);
+  return sizeof(float4) * (P1 + P2) + sizeof(cx<float>) * b1n + tail;
+}
+
+bool zinv_fused_fits(int P1, int P2, int S1, int S2) {
+  return zinv_ny(P2 / 2 + 1) > 0 && S1 <= P1 && zinv_fused_smem(P1, P2, S1, S2) * 3 <= 227 * 1024;
+}
+
+template <class T, int NY>
+cudaError_t launch_zinv_k(const ZinvArgs &a, size_t smem, int batch, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_zinv<T, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_zinv<T, NY><<<(unsigned)((long long)batch * a.K * a.S0), 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_zinv(const ZinvArgs &a_in, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   ZinvArgs a = a_in;
+  const int L = (a.S1 + 1) / 2;
+  if (a.x2) {  // fused y + z inverse: FP32 only, the whole window in one chunk
+    if constexpr (std::is_same<T, float>::value) {
+      const int P1 = a.yplan.n;
+      if (!zinv_fused_fits(P1, a.plan.n, a.S1, a.S2) || a.F2 != a.plan.n / 2 + 1) return cudaErrorInvalidValue;
+      a.Lc = L;
+      const size_t smem = zinv_fused_smem(P1, a.plan.n, a.S1, a.S2);
+      return zinv_ny(a.F2) == 21 ? launch_zinv_k<float, 21>(a, smem, batch, st)
+                                 : launch_zinv_k<float, 25>(a, smem, batch, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   // all row pairs of the site window in one chunk when they fit in shared
   // memory (227 KB per CTA), else the largest chunk that does
-  const int L = (a.S1 + 1) / 2;
   int Lc = L;
   while (Lc > 1 && zinv_smem<T>(a, Lc) > 227 * 1024) --Lc;
   if (zinv_smem<T>(a, Lc) > 227 * 1024) return cudaErrorInvalidValue;
   a.Lc = Lc;
-  const size_t smem = zinv_smem<T>(a, Lc);
-  cudaError_t e = cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_zinv<T><<<(unsigned)((long long)batch * a.K * a.S0), 256, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_zinv_k<T, 0>(a, zinv_smem<T>(a, Lc), batch, st);
 }
 
 // --------------------------------------------------------------------------

@@ -153,6 +153,13 @@ struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp pa
   float *plane_min;        // with Ebuf: [batch][K][S0] minimum energy of each s0 plane
   FftPlan plan;
   const float4 *tw;
+  // FP32 forms: the y inverse fused in front (y2 unused) when x2 is set: each
+  // CTA transforms its plane x2[(j K + k) S0 + s0] ([P1][F2], Qx = P1 F2)
+  // along y, keeps the site window rows in shared memory and goes on with z
+  const void *x2;
+  long long Qx;
+  FftPlan yplan;
+  const float4 *tw1;
 };
 
 struct MergeArgs {
@@ -220,6 +227,9 @@ template <class T> cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st);
 template <class T> cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st);
 template <class T> cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st);
 template <class T> cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st);
+// whether the FP32 z inverse can take the y inverse in front (whole site
+// window in one shared-memory chunk at 3 CTAs per SM)
+bool zinv_fused_fits(int P1, int P2, int S1, int S2);
 cudaError_t launch_merge_pairs(const MergeArgs &a, cudaStream_t st);  // per receptor group
 cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st);        // B_k and dG over all receptors
 cudaError_t launch_split_ff(const void *spec, float2 *hi, float2 *lo, long long n, cudaStream_t st);
