@@ -1373,6 +1373,7 @@ struct BucketPlan {
   int B = 1;                           // configurations per batch
   size_t off_rptr = 0, off_ref = 0;    // blob: [2 Kg] spectrum pointers (hi, then lo), [Kg] RefTab
   std::vector<std::array<int, 3>> Ub;  // ligand box per batch
+  cudaEvent_t join = nullptr;          // crops made for this bucket by this call are done
 };
 
 struct GroupPlan {
@@ -1499,9 +1500,9 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         }
       // a crop costs one transform of the group's grids: keep it only where its
       // configurations save at least 24 configurations' worth of spectrum volume
+      const std::array<int, 3> Pf{g.P[0], g.P[1], g.P[2]};
       {
         auto vol = [](const std::array<int, 3> &p) { return (double)p[0] * p[1] * (p[2] / 2 + 1); };
-        const std::array<int, 3> Pf{g.P[0], g.P[1], g.P[2]};
         std::map<std::array<int, 3>, int> count;
         for (int i = 0; i < J; ++i) ++count[pc[i]];
         for (int i = 0; i < J; ++i)
@@ -1513,6 +1514,9 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       std::vector<int> order(std::max(J, 1), 0);
       for (int i = 0; i < J; ++i) order[i] = i;
       std::stable_sort(order.begin(), order.begin() + J, [&](int a, int b) {
+        // the uncropped bucket first: its work starts while the crops are made
+        const bool fa = pc[a] == Pf, fb = pc[b] == Pf;
+        if (fa != fb) return fa;
         if (pc[a] != pc[b]) return pc[a] < pc[b];
         for (int d = 0; d < 3; ++d)
           if (mj[a].u[d] != mj[b].u[d]) return mj[a].u[d] < mj[b].u[d];
@@ -1576,7 +1580,9 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         std::vector<RefTab> rt(Kg);
         std::vector<bpmf_rec *> rg(Kg);
         for (int kg = 0; kg < Kg; ++kg) rg[kg] = recs[g.ks[kg]];
+        const size_t nj = joins.size();
         const std::vector<bpmf_rec::Crop> crs = rec_crops(c, rg, Pc, fork, joins, touched);
+        if (joins.size() > nj) bk.join = joins.back();
         for (int kg = 0; kg < Kg; ++kg) {
           bpmf_rec *r = rg[kg];
           const bpmf_rec::Crop &cr = crs[kg];
@@ -1650,18 +1656,23 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   if (!blob.empty()) std::memcpy(c->pinned, blob.data(), blob.size());
   for (const auto &g : groups)
     for (int d = 0; d < 3; ++d) twiddles(c, g.P[d]);
-  // join the crops made here; crops made earlier (perhaps on another stream)
-  // are ordered by their receptor's event
+  // crops made earlier (perhaps on another stream) are ordered by their
+  // receptor's event.  Crops made here: a graph capture waits for all of them
+  // first; otherwise each bucket waits for its own before its first batch, so
+  // the work of the buckets before it overlaps them.  Their receptors' events
+  // complete with the last of them (recorded on a side stream that joins them).
   for (int k = 0; k < K; ++k)
     if (recs[k]->crop_ev) CK(cudaStreamWaitEvent(st, recs[k]->crop_ev, 0));
-  for (cudaEvent_t e : joins) {
-    CK(cudaStreamWaitEvent(st, e, 0));
-    c->event_pool.push_back(e);
-  }
-  c->event_pool.push_back(fork);
-  for (bpmf_rec *r : touched) {
-    if (!r->crop_ev) CK(cudaEventCreateWithFlags(&r->crop_ev, cudaEventDisableTiming));
-    CK(cudaEventRecord(r->crop_ev, st));
+  if (use_graph)
+    for (cudaEvent_t e : joins) CK(cudaStreamWaitEvent(st, e, 0));
+  if (!touched.empty()) {
+    cudaStream_t &sj = c->side[0];
+    if (!sj) CK(cudaStreamCreateWithFlags(&sj, cudaStreamNonBlocking));
+    for (cudaEvent_t e : joins) CK(cudaStreamWaitEvent(sj, e, 0));
+    for (bpmf_rec *r : touched) {
+      if (!r->crop_ev) CK(cudaEventCreateWithFlags(&r->crop_ev, cudaEventDisableTiming));
+      CK(cudaEventRecord(r->crop_ev, sj));
+    }
   }
   c->warn_last = warn;
 
@@ -1703,6 +1714,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         char *d_batch = d_grp + align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
         const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
         for (const BucketPlan &bk : gp.buckets) {
+          if (!use_graph && bk.join) CK(cudaStreamWaitEvent(st, bk.join, 0));
           const double norm = 1.0 / ((double)bk.P[0] * bk.P[1] * bk.P[2]);
           float nsh, nsl, esh, esl;
           split_ff(-norm / kT, nsh, nsl);
@@ -1797,6 +1809,9 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     CK(cudaGraphLaunch(c->gexec, st));
     CK(cudaEventRecord(c->pinned_busy, st));
   }
+  // the fork and join events are queued in every wait that uses them: reusable
+  for (cudaEvent_t e : joins) c->event_pool.push_back(e);
+  c->event_pool.push_back(fork);
   if (host_out) CK(cudaStreamSynchronize(st));
   return warn ? BPMF_WARN_NO_VALID : BPMF_OK;
 }

@@ -120,8 +120,14 @@ __global__ void __launch_bounds__(256) k_ligspec(LigSpecArgs a) {
       sB[e] = make_float2(__fmaf_rn(g1, t1.x, __fmul_rn(g0, t0.x)), __fmaf_rn(g1, t1.y, __fmul_rn(g0, t0.y)));
     }
     __syncthreads();
-    for (long long q = threadIdx.x; q < Q; q += blockDim.x) {
-      const int ky = (int)(q / F2), kz = (int)(q % F2);
+    // (ky, kz) = divmod(q, F2), stepped without a division per output
+    const int dky = (int)blockDim.x / F2, dkz = (int)blockDim.x % F2;
+    for (int q = threadIdx.x, ky = (int)threadIdx.x / F2, kz = (int)threadIdx.x % F2; q < (int)Q;
+         q += blockDim.x, ky += dky, kz += dkz) {
+      if (kz >= F2) {
+        kz -= F2;
+        ++ky;
+      }
       float2 acc[3];
       for (int t = 0; t < 3; ++t) acc[t] = c0 == 0 ? make_float2(0.f, 0.f) : out[t][q];
       for (int e = 0; e < nc; ++e) {
