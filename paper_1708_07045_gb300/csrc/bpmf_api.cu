@@ -425,6 +425,7 @@ struct BatchGeom {
   int occ_cap = 0;  // ligand occupancy runs per configuration (0: no clash channel)
   int occ_rb = 1;   // CTAs per configuration building the runs
   bool refine = false;  // refined form: FP32 energies kept for k_refine
+  int nmax = 0;         // atoms per configuration of the ligand
 };
 
 int clash_words(int S2) { return (S2 + 31) / 32; }
@@ -542,6 +543,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     la.tw1 = twiddles(c, g.P[1]);
     la.tw2 = twiddles(c, g.P[2]);
     la.ly = reinterpret_cast<float2 *>(ly);
+    la.nmax = g.nmax;
     launch(c, "k_ligspec", st, [&] { return launch_ligspec(la, batch, st); });
   } else {
     SpreadArgs sa{lg->coords, lg->gamma, (int)lg->total_atoms, d_meta, hh, hl, g.U[0], g.U[1], g.U[2], box};
@@ -1563,6 +1565,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       gpn.occ_cap = bg.occ_cap;
       gpn.occ_rb = bg.occ_rb;
       bg.refine = refine;
+      bg.nmax = lg->n_atoms[li];
       const size_t part = align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
       const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
       std::vector<PairInfo> info_g((size_t)std::max(J, 1) * Kg);
@@ -1735,6 +1738,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
             gb.occ_cap = gp.occ_cap;
             gb.occ_rb = gp.occ_rb;
             gb.refine = refine;
+            gb.nmax = lg->n_atoms[pl.li];
             if (use_ff)
               run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, d_rptr + Kg, h, nsh, nsl,
                             esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, false, d_tabs);

@@ -50,6 +50,7 @@ struct LigSpecArgs {        // ligand y-z spectra straight from the atoms (FP32 
   long long Q;             // P1 * F2
   const float4 *tw1, *tw2; // exp(-2 pi i k / P) tables for P1, P2
   float2 *ly;              // [batch][3][U0][Q]
+  int nmax;                // atoms per configuration (bounds the atoms on one plane)
   int chunk;               // atoms per shared-memory pass (set by launch_ligspec)
 };
 

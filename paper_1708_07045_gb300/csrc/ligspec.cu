@@ -149,8 +149,11 @@ __global__ void __launch_bounds__(256) k_ligspec(LigSpecArgs a) {
 cudaError_t launch_ligspec(const LigSpecArgs &a_in, int batch, cudaStream_t st) {
   if (batch <= 0 || a_in.U0 <= 0) return cudaSuccess;
   LigSpecArgs a = a_in;
-  // atoms whose factors fit in 96 KB of shared memory at once
-  a.chunk = (int)std::max<size_t>(1, std::min<size_t>(kLsAtoms, (96 * 1024) / (sizeof(float2) * (a.P1 + a.F2))));
+  // atoms whose factors fit in 96 KB of shared memory at once, and no more
+  // than a plane can hold (the ligand's atoms): a small ligand keeps the
+  // footprint small and more CTAs resident
+  const int cap = a.nmax > 0 ? std::min(a.nmax, kLsAtoms) : kLsAtoms;
+  a.chunk = (int)std::max<size_t>(1, std::min<size_t>(cap, (96 * 1024) / (sizeof(float2) * (a.P1 + a.F2))));
   const size_t smem = sizeof(float2) * (size_t)a.chunk * (a.P1 + a.F2);
   cudaError_t e = cudaFuncSetAttribute(k_ligspec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
