@@ -259,6 +259,23 @@ int bpmf_export_energies(bpmf_ctx_t ctx, bpmf_lig_t lig, bpmf_rec_t rec, int lig
 /* Padded FFT edge the library uses for a grid edge n (0 if unsupported). */
 int bpmf_fft_edge(int n);
 
+/*
+ * bpmf_crop_window -- the cropped transform (see bpmf_eval) along one axis of
+ * a receptor grid of n nodes with site box [site_lo, site_lo + site_n), for a
+ * configuration whose ligand box has edge u nodes.  Host only; no device work.
+ *  edge  receives the transform edge: bpmf_fft_edge(n), or the smooth edge
+ *        near 5/6 of it when site_n + min(u, bpmf_fft_edge(n)) - 1 nodes fit
+ *        in it.  (bpmf_eval may still use the full edge for the crop when too
+ *        few configurations share it.)
+ *  c0    receives the crop's first receptor node: 0 for the full edge, else
+ *        floor((site_n - edge) / 2) nodes from site_lo, moved into [0, n - edge].
+ * Every receptor node that a kept translation of the site window reads lies
+ * in [c0, c0 + edge).
+ * Errors: INVALID_ARG (null output, n < 2, site_n < 1 or u < 1),
+ * SIZE_UNSUPPORTED (bpmf_fft_edge(n) == 0).
+ */
+int bpmf_crop_window(int n, int site_lo, int site_n, int u, int *edge, int *c0);
+
 /* Upper bound on the device workspace bpmf_eval may hold (bytes, default
  * 3 GiB); configurations are processed in batches that fit.  Results do not
  * depend on the batch size (every step is deterministic).  Errors:

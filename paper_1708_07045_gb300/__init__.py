@@ -112,6 +112,7 @@ _SIGS = {
     "bpmf_export_energies": (_I, [_P, _P, _P, _I, _I, ctypes.c_uint, _P, _P]),
     "bpmf_receptor_set_occupancy": (_I, [_P, _P, _P, _P]),
     "bpmf_fft_edge": (_I, [_I]),
+    "bpmf_crop_window": (_I, [_I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "bpmf_set_workspace_limit": (_I, [_P, ctypes.c_size_t]),
     "bpmf_profile_enable": (_I, [_P, _I]),
     "bpmf_profile_count": (_I, [_P]),
@@ -215,6 +216,15 @@ def bpmf_last_error(ctx) -> str:
 
 def bpmf_fft_edge(n: int) -> int:
     return int(lib().bpmf_fft_edge(int(n)))
+
+
+def bpmf_crop_window(n: int, site_lo: int, site_n: int, u: int):
+    """(transform edge, first receptor node) of the cropped transform along one
+    axis for a ligand box of edge u (host only)."""
+    edge, c0 = ctypes.c_int(), ctypes.c_int()
+    _check(lib().bpmf_crop_window(int(n), int(site_lo), int(site_n), int(u), ctypes.byref(edge), ctypes.byref(c0)),
+           "bpmf_crop_window", None)
+    return edge.value, c0.value
 
 
 def bpmf_set_workspace_limit(ctx, nbytes: int):

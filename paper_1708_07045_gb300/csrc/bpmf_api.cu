@@ -972,6 +972,14 @@ void grid_spectrum(bpmf_ctx *c, const float *src, int nrec, const int e[3], cons
 
 int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// First node of a crop of edge Pc around the site [site_lo, site_lo + site_n)
+// of a grid of N nodes: floor((site_n - Pc) / 2) nodes from the site, moved
+// inside the grid.
+int crop_start(int N, int site_lo, int site_n, int Pc) {
+  const int c0 = site_lo + floor_div(site_n - Pc, 2);
+  return std::max(0, std::min(c0, std::max(0, N - Pc)));
+}
+
 // Views of receptors' spectra for transform edges Pc <= P: the stored one of
 // a receptor when Pc == P, else its grids cropped to Pc nodes per axis around
 // the site.  Crops made on first use are transformed together, on one of the
@@ -1008,8 +1016,7 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
     }
     std::array<int, 3> e{};
     for (int d = 0; d < 3; ++d) {
-      const int c0 = r->site_lo[d] + floor_div(r->site_n[d] - Pc[d], 2);
-      out[m].c0[d] = std::max(0, std::min(c0, std::max(0, r->N[d] - Pc[d])));
+      out[m].c0[d] = crop_start(r->N[d], r->site_lo[d], r->site_n[d], Pc[d]);
       e[d] = std::min(Pc[d], r->N[d] - out[m].c0[d]);
       Emax[d] = std::max(Emax[d], e[d]);
     }
@@ -1085,6 +1092,16 @@ int crop_edge(int W, int P) {
 }
 
 }  // namespace
+
+int bpmf_crop_window(int n, int site_lo, int site_n, int u, int *edge, int *c0) {
+  if (!edge || !c0 || n < 2 || site_n < 1 || u < 1) return BPMF_ERR_INVALID_ARG;
+  const int P = smooth_edge(n);
+  if (!P) return BPMF_ERR_SIZE_UNSUPPORTED;
+  const int Pc = crop_edge(site_n + std::min(u, P) - 1, P);
+  *edge = Pc;
+  *c0 = Pc == P ? 0 : crop_start(n, site_lo, site_n, Pc);
+  return BPMF_OK;
+}
 
 int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz, double h, const double origin[3],
                        const int site_lo[3], const int site_n[3], void *stream, bpmf_rec_t *out) {

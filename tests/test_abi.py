@@ -60,3 +60,40 @@ def test_python_binding_rejects_wrong_dtypes():
         pkg._ptr(np.zeros(3, dtype=np.float64), np.float32)
     with pytest.raises(TypeError):
         pkg._ptr(np.zeros((3, 3), dtype=np.float32).T, np.float32)
+
+
+def test_crop_window_holds_every_node_a_kept_translation_reads():
+    """Cropped transforms (bpmf_eval): along one axis, with the ligand box of
+    edge u placed at w0 = site_lo - floor(u/2) and translation w0 + s kept for
+    s in [max(0, -w0), min(site_n - 1, n - 1 - u - w0)] (the site window and
+    the rule that the box stays inside the grid), every receptor node a kept
+    translation reads, w0 + s + x for x in [0, u), must lie in the crop
+    [c0, c0 + edge) and in the grid; and the ligand box (its y extent rounded
+    up to even) must fit the edge.  Exhaustive over small grids."""
+    checked = 0
+    for n in range(8, 49):
+        P = pkg.bpmf_fft_edge(n)
+        for site_n in range(1, n + 1, 3):
+            for site_lo in range(0, n - site_n + 1, 2):
+                for u in range(5, n + 2):
+                    edge, c0 = pkg.bpmf_crop_window(n, site_lo, site_n, u)
+                    assert edge == P or edge < P
+                    assert edge % 2 == 0 and pkg.bpmf_fft_edge(edge) == edge
+                    w0 = site_lo - u // 2
+                    sa, sb = max(0, -w0), min(site_n - 1, n - 1 - u - w0)
+                    if sb < sa:
+                        continue
+                    lo, hi = w0 + sa, w0 + sb + u - 1
+                    assert 0 <= lo and hi <= n - 1
+                    assert c0 <= lo and hi <= c0 + edge - 1, (n, site_lo, site_n, u, edge, c0)
+                    if edge < P:
+                        assert c0 + edge <= n or c0 == 0
+                        assert u + (u & 1) <= edge
+                    checked += 1
+    assert checked > 10000
+    # the protein-scale axis: a 40-node site in a 96-node grid crops to 80
+    # for ligand boxes up to 41 nodes
+    assert pkg.bpmf_crop_window(96, 28, 40, 41) == (80, 8)
+    assert pkg.bpmf_crop_window(96, 28, 40, 42)[0] == 96
+    with pytest.raises(pkg.BpmfError):
+        pkg.bpmf_crop_window(96, 28, 0, 10)
