@@ -203,27 +203,16 @@ def run_reference(args):
     return 0
 
 
-def smooth_edge(n):
-    """Smallest even 2^a 3^b 5^c 7^d >= n (the library's transform edges)."""
-    p = max(n, 2)
-    while True:
-        if p % 2 == 0:
-            m = p
-            for r in (2, 3, 5, 7):
-                while m % r == 0:
-                    m //= r
-            if m == 1:
-                return p
-        p += 1
-
-
-def crop_edges(u, S, P, J):
-    """Transform edges per configuration as the library chooses them: the crop
-    edge near 5P/6 on each axis where the site reach S + u - 1 fits, kept for a
-    crop only when its configurations save at least 24 configurations' worth
-    of spectrum volume.  u: [J, 3] ligand-box edges."""
-    p1 = smooth_edge((5 * P + 5) // 6)
-    pc = np.where(S + np.minimum(u, P) - 1 <= p1, p1, P)
+def crop_edges(u, S, P, J, N=96, site_lo=28):
+    """Transform edges per configuration as the library chooses them: the
+    per-axis crop edge from bpmf_crop_window (the library's own rule for a
+    grid of N nodes with the site [site_lo, site_lo + S)), kept for a crop
+    only when its configurations save at least 24 configurations' worth of
+    spectrum volume (the batch-level rule of bpmf_eval).  u: [J, 3]
+    ligand-box edges."""
+    import paper_1708_07045_gb300 as pkg
+    edge = {int(v): pkg.bpmf_crop_window(N, site_lo, S, int(v))[0] for v in np.unique(u)}
+    pc = np.vectorize(lambda v: edge[int(v)])(u)
     vol = lambda t: t[0] * t[1] * (t[2] // 2 + 1)
     keys = [tuple(int(v) for v in r) for r in pc]
     cnt = {}
