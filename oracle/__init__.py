@@ -35,7 +35,7 @@ _SO = os.path.join(_HERE, "_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-C_STANDARD = 1.0 / 1660.5390  # 1 M standard state, molecules per A^3
+C_STANDARD = 6.02214076e23 / 1e27  # 1 M standard state: N_A molecules per litre, in molecules per A^3
 
 
 def build(force: bool = False) -> str:
