@@ -197,7 +197,7 @@ void bpmf_ligand_free(bpmf_lig_t lig);
  *    B_k      = -kT [ ln sum_j S_jk - ln sum_j n_jk ]   (Eq. sample_mean_BPMF
  *                                                      over all valid poses)
  *    dG       = -kT ln[(1/K) sum_k exp(-B_k/kT)] - kT ln(V_site C)
- * with C = 1/1660.539 A^-3 and V_site = h^3 * mean_jk n_jk (Eqs.
+ * with C = N_A / 1e27 = 6.02214076e-4 A^-3 (1 M) and V_site = h^3 * mean_jk n_jk (Eqs.
  * standard_binding_fe and binding_FE_estimate with uniform receptor weights).
  *
  *  recs, K   receptor handles; all must share the grid spacing (else
@@ -412,7 +412,7 @@ int bpmf_sir_poses(bpmf_ctx_t ctx, bpmf_lig_t lig, int lig_index, bpmf_rec_t rec
  * configurations j = min(J - 1, floor(u[r][i] J)) and evaluates, per
  * receptor k, B_k = -kT [ln sum_slots n_jk exp(logZ_jk) - ln sum_slots n_jk],
  * then dG = -kT ln((1/K) sum_k exp(-B_k/kT)) - kT ln(h^3 C mean n) exactly as
- * bpmf_eval does for the full set (C = 1/1660.539 A^-3).
+ * bpmf_eval does for the full set (C = 6.02214076e-4 A^-3, 1 M).
  *   logZ, n_valid  [J][K] as bpmf_eval returns them for one ligand;
  *   u              [R][J] float64 uniforms in [0, 1);
  *   rep            [R][K + 1] out (B_k, then dG per replicate), may be null;
@@ -456,12 +456,16 @@ int bpmf_profile_entry(bpmf_ctx_t ctx, int i, char *name, int name_len, double *
  *  out        [S0][S1][S2] float64 DEVICE memory (S = site_n): energy of
  *             translation m = site_lo + s - floor(u/2), +inf where discarded;
  *             the same values bpmf_export_energies returns.
- * Runs on the current device and on `stream`, and synchronises `stream`
- * before returning.  The first call on a device resolves the array's device
- * address (cudaGetSymbolAddress) once; make that first call before any stream
- * capture.  Every call shares the one array and leaves its contents behind:
- * calls whose GPU work overlaps (other threads, other streams) race and must be
- * serialised by the caller.
+ * Every array argument must be DEVICE memory of the current device (checked
+ * per pointer with cudaPointerGetAttributes; host memory returns INVALID_ARG
+ * before any work is queued).
+ * Runs on the current device and on `stream`.  Each call reads the ligand's
+ * coordinate bounds back to the host and synchronises `stream` before
+ * returning.  The first call on a device also does a one-time set-up: it
+ * resolves the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture begins.  Every call shares the one array and
+ * leaves its contents behind: calls whose GPU work overlaps (other threads,
+ * other streams) race and must be serialised by the caller.
  * Errors: INVALID_ARG; SIZE_UNSUPPORTED when the grid or the ligand box needs
  * more scratch than BPMF_STATIC_SCRATCH_BYTES (a 96^3 grid with a ligand box
  * up to ~60 nodes per edge fits) or exceeds the other limits; CUDA.

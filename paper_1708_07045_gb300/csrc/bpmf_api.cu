@@ -20,6 +20,69 @@
 
 using namespace bpmf;
 
+// ------------------------------------------------ host plan helpers (shared)
+namespace bpmf {
+
+// smallest 2^a 3^b 5^c 7^d >= n with a >= 1
+int smooth_edge(int n) {
+  if (n < 2) n = 2;
+  for (int p = n; p <= BPMF_MAX_FFT_EDGE; ++p) {
+    if (p % 2) continue;
+    int m = p;
+    for (int r : {2, 3, 5, 7})
+      while (m % r == 0) m /= r;
+    if (m == 1) return p;
+  }
+  return 0;
+}
+
+
+FftPlan make_plan(int P) {
+  FftPlan pl{};
+  pl.n = P;
+  int m = P, k = 0;
+  while (m % 8 == 0) pl.r[k++] = 8, m /= 8;
+  while (m % 4 == 0) pl.r[k++] = 4, m /= 4;
+  while (m % 2 == 0) pl.r[k++] = 2, m /= 2;
+  for (int r : {3, 5, 7})
+    while (m % r == 0) pl.r[k++] = r, m /= r;
+  pl.nst = k;
+  return pl;
+}
+
+
+// exp(-2 pi i k / P), k < P, as float pairs {re hi, im hi, re lo, im lo},
+// each from the exact fraction k / P in long double
+void twiddle_values(int P, float4 *out) {
+  const long double two_pi = 6.283185307179586476925286766559L;
+  for (int k = 0; k < P; ++k) {
+    const long double a = two_pi * (long double)k / (long double)P;
+    const long double re = cosl(a), im = -sinl(a);
+    const float rh = (float)re, ih = (float)im;
+    out[k] = make_float4(rh, ih, (float)(re - (long double)rh), (float)(im - (long double)ih));
+  }
+}
+
+// ligand-box extent u = ceil((hi - lo) / h) + 4 ("two additional grid
+// spacings" per side), decided in single precision exactly as the oracle does
+int box_extent(float lo, float hi, float hf) {
+  volatile float ext = hi - lo;
+  volatile float r = ext / hf;
+  return (int)std::ceil(r) + 4;
+}
+
+// Site window of one (configuration, receptor) pair along axis d: the ligand
+// box centre floor(u/2) lands in [site_lo, site_lo + site_n) and the whole box
+// [m, m + u] stays inside the N nodes of the grid.  Returns the valid count.
+long long site_window(int N, int site_lo, int site_n, int u, int &w0, int &sa, int &sb) {
+  w0 = site_lo - u / 2;
+  sa = std::max(0, -w0);
+  sb = std::min(site_n - 1, N - 1 - u - w0);
+  return sb >= sa ? (long long)(sb - sa + 1) : 0;
+}
+
+}  // namespace bpmf
+
 // ---------------------------------------------------------------- handles
 struct ProfRec {
   const char *name;
@@ -159,36 +222,10 @@ struct DeviceGuard {
   }
 };
 
-// smallest 2^a 3^b 5^c 7^d >= n with a >= 1
-int smooth_edge(int n) {
-  if (n < 2) n = 2;
-  for (int p = n; p <= BPMF_MAX_FFT_EDGE; ++p) {
-    if (p % 2) continue;
-    int m = p;
-    for (int r : {2, 3, 5, 7})
-      while (m % r == 0) m /= r;
-    if (m == 1) return p;
-  }
-  return 0;
-}
-
 // Fragment tables of the tensor-core radix-32 stage: the real 64 x 64 DFT-32
 // matrix (rows 2r'+c', columns 2r+c), split into bf16 high and low parts and
 // laid out in mma.sync m16n8k16 A-fragment order, forward then inverse.
 const uint4 *tc_table(bpmf_ctx *c);
-
-FftPlan make_plan(int P) {
-  FftPlan pl{};
-  pl.n = P;
-  int m = P, k = 0;
-  while (m % 8 == 0) pl.r[k++] = 8, m /= 8;
-  while (m % 4 == 0) pl.r[k++] = 4, m /= 4;
-  while (m % 2 == 0) pl.r[k++] = 2, m /= 2;
-  for (int r : {3, 5, 7})
-    while (m % r == 0) pl.r[k++] = r, m /= r;
-  pl.nst = k;
-  return pl;
-}
 
 // split-bf16 plan: the radix-32 factor as a final tensor-core stage when 32 | P
 FftPlan make_plan_split(bpmf_ctx *c, int P) {
@@ -205,14 +242,7 @@ const float4 *twiddles(bpmf_ctx *c, int P) {
   auto it = c->tw.find(P);
   if (it != c->tw.end()) return it->second;
   std::vector<float4> h(P);
-  const long double two_pi = 6.283185307179586476925286766559L;
-  for (int k = 0; k < P; ++k) {
-    // exp(-2 pi i k / P) from the exact fraction k / P
-    long double a = two_pi * (long double)k / (long double)P;
-    long double re = cosl(a), im = -sinl(a);
-    float rh = (float)re, ih = (float)im;
-    h[k] = make_float4(rh, ih, (float)(re - (long double)rh), (float)(im - (long double)ih));
-  }
+  twiddle_values(P, h.data());
   float4 *d = nullptr;
   CK(cudaMalloc(&d, sizeof(float4) * P));
   CK(cudaMemcpy(d, h.data(), sizeof(float4) * P, cudaMemcpyHostToDevice));
@@ -388,12 +418,6 @@ void split_ff(double v, float &hi, float &lo) {
   lo = (float)(v - (double)hi);
 }
 
-// ligand-box extent, decided in single precision exactly as the oracle does
-int box_extent(float lo, float hi, float hf) {
-  volatile float ext = hi - lo;
-  volatile float r = ext / hf;
-  return (int)std::ceil(r) + 4;
-}
 
 // temporary device copy of a host or device input
 struct DevIn {
@@ -710,14 +734,9 @@ void ligand_tables(const bpmf_lig *lg, int li, const bpmf_rec_t *recs, int K, do
       PairInfo pi{};
       long long n = 1;
       for (int d = 0; d < 3; ++d) {
-        const int w0 = recs[k]->site_lo[d] - m.u[d] / 2;
-        const int sa = std::max(0, -w0);
-        const int sb = std::min(recs[k]->site_n[d] - 1, recs[k]->N[d] - 1 - m.u[d] - w0);
-        pi.w0[d] = w0;
-        pi.wc[d] = w0;  // uncropped transforms
-        pi.sa[d] = sa;
-        pi.sb[d] = sb;
-        n *= (sb >= sa) ? (sb - sa + 1) : 0;
+        n *= site_window(recs[k]->N[d], recs[k]->site_lo[d], recs[k]->site_n[d], m.u[d], pi.w0[d], pi.sa[d],
+                         pi.sb[d]);
+        pi.wc[d] = pi.w0[d];  // uncropped transforms
       }
       info[(size_t)j * K + k] = pi;
       nvalid[(size_t)j * K + k] = n;
@@ -1788,7 +1807,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       mf.J = J;
       mf.K = K;
       mf.kT = kT;
-      mf.vsite_scale = h * h * h / 1660.5390;
+      mf.vsite_scale = h * h * h * kStandardConc;
       mf.logS = d_logS;
       mf.logZ = d_logZ;
       mf.bpmf = d_B;

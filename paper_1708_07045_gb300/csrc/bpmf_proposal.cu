@@ -353,7 +353,7 @@ int bpmf_bootstrap(bpmf_ctx_t c, const double *logZ, const int64_t *n_valid, int
       PCK(cudaMallocAsync(&buf, sizeof(double) * (size_t)R * (K + 1), st));
       r = buf;
     }
-    PCK(launch_bootstrap(logZ, reinterpret_cast<const long long *>(n_valid), J, K, kT, h * h * h / 1660.5390, u, R,
+    PCK(launch_bootstrap(logZ, reinterpret_cast<const long long *>(n_valid), J, K, kT, h * h * h * kStandardConc, u, R,
                          r, stats, st));
     if (buf) PCK(cudaFreeAsync(buf, st));
   } catch (PFail f) {

@@ -54,39 +54,14 @@ int scratch_address(int dev, unsigned char **out) {
   return BPMF_OK;
 }
 
-int edge(int n) {  // smallest even 2^a 3^b 5^c 7^d >= n (<= BPMF_MAX_FFT_EDGE)
-  for (int p = std::max(n, 2); p <= BPMF_MAX_FFT_EDGE; ++p) {
-    if (p % 2) continue;
-    int m = p;
-    for (int r : {2, 3, 5, 7})
-      while (m % r == 0) m /= r;
-    if (m == 1) return p;
+// Every pointer argument must be device (or managed) memory of device `dev`.
+bool on_device(const void *p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
-  return 0;
-}
-
-FftPlan plan(int P) {
-  FftPlan pl{};
-  pl.n = P;
-  int m = P, k = 0;
-  while (m % 8 == 0) pl.r[k++] = 8, m /= 8;
-  while (m % 4 == 0) pl.r[k++] = 4, m /= 4;
-  while (m % 2 == 0) pl.r[k++] = 2, m /= 2;
-  for (int r : {3, 5, 7})
-    while (m % r == 0) pl.r[k++] = r, m /= r;
-  pl.nst = k;
-  return pl;
-}
-
-void twiddle_table(int P, std::vector<float4> &h) {
-  h.resize(P);
-  const long double two_pi = 6.283185307179586476925286766559L;
-  for (int k = 0; k < P; ++k) {
-    const long double a = two_pi * (long double)k / (long double)P;
-    const long double re = cosl(a), im = -sinl(a);
-    const float rh = (float)re, ih = (float)im;
-    h[k] = make_float4(rh, ih, (float)(re - (long double)rh), (float)(im - (long double)ih));
-  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 struct Fail {
@@ -208,7 +183,7 @@ extern "C" int bpmf_export_energies_static(const float *grids, int nx, int ny, i
   const int N[3] = {nx, ny, nz};
   int P[3];
   for (int d = 0; d < 3; ++d) {
-    P[d] = edge(N[d]);
+    P[d] = smooth_edge(N[d]);
     if (!P[d]) {
       return BPMF_ERR_SIZE_UNSUPPORTED;
     }
@@ -218,6 +193,10 @@ extern "C" int bpmf_export_energies_static(const float *grids, int nx, int ny, i
     cudaGetLastError();
     return BPMF_ERR_CUDA;
   }
+  // the arrays go straight to kernels: host memory is rejected before any work
+  for (const void *p : {(const void *)grids, (const void *)coords, (const void *)q, (const void *)eps,
+                        (const void *)R, (const void *)out})
+    if (!on_device(p, dev)) return BPMF_ERR_INVALID_ARG;
   unsigned char *base = nullptr;
   int rc = scratch_address(dev, &base);
   if (rc != BPMF_OK) return rc;
@@ -251,15 +230,17 @@ extern "C" int bpmf_export_energies_static(const float *grids, int nx, int ny, i
     if (o_var + rz + ry > kScratchBytes) return BPMF_ERR_SIZE_UNSUPPORTED;  // grid too large
     float4 *tw0 = reinterpret_cast<float4 *>(base + o_tw0), *tw1 = reinterpret_cast<float4 *>(base + o_tw1),
            *tw2 = reinterpret_cast<float4 *>(base + o_tw2);
-    std::vector<float4> ht;
-    twiddle_table(P[0], ht);
+    // the three tables in one host staging vector (read by the copies until the
+    // final synchronisation)
+    std::vector<float4> ht((size_t)P[0] + P[1] + P[2]);
+    twiddle_values(P[0], ht.data());
+    twiddle_values(P[1], ht.data() + P[0]);
+    twiddle_values(P[2], ht.data() + P[0] + P[1]);
     SCK(cudaMemcpyAsync(tw0, ht.data(), sizeof(float4) * P[0], cudaMemcpyHostToDevice, st));
-    twiddle_table(P[1], ht);
-    SCK(cudaMemcpyAsync(tw1, ht.data(), sizeof(float4) * P[1], cudaMemcpyHostToDevice, st));
-    twiddle_table(P[2], ht);
-    SCK(cudaMemcpyAsync(tw2, ht.data(), sizeof(float4) * P[2], cudaMemcpyHostToDevice, st));
+    SCK(cudaMemcpyAsync(tw1, ht.data() + P[0], sizeof(float4) * P[1], cudaMemcpyHostToDevice, st));
+    SCK(cudaMemcpyAsync(tw2, ht.data() + P[0] + P[1], sizeof(float4) * P[2], cudaMemcpyHostToDevice, st));
     const float4 *tws[3] = {tw0, tw1, tw2};
-    const FftPlan pls[3] = {plan(P[0]), plan(P[1]), plan(P[2])};
+    const FftPlan pls[3] = {make_plan(P[0]), make_plan(P[1]), make_plan(P[2])};
 
     // generalised charges and coordinate bounds
     float2 *gam = reinterpret_cast<float2 *>(base + o_gam);
@@ -279,15 +260,10 @@ extern "C" int bpmf_export_energies_static(const float *grids, int nx, int ny, i
     const float hf = (float)h;
     int U[3];
     for (int d = 0; d < 3; ++d) {
-      volatile float ext = mm[3 + d] - mm[d];
-      volatile float rat = ext / hf;
       m.lo[d] = mm[d];
-      m.u[d] = (int)std::ceil(rat) + 4;
-      const int w0 = site_lo[d] - m.u[d] / 2;
-      pi.w0[d] = w0;
-      pi.wc[d] = w0;
-      pi.sa[d] = std::max(0, -w0);
-      pi.sb[d] = std::min(site_n[d] - 1, N[d] - 1 - m.u[d] - w0);
+      m.u[d] = box_extent(mm[d], mm[3 + d], hf);
+      site_window(N[d], site_lo[d], site_n[d], m.u[d], pi.w0[d], pi.sa[d], pi.sb[d]);
+      pi.wc[d] = pi.w0[d];
       U[d] = std::max(1, std::min(m.u[d], P[d]));
     }
     U[1] += U[1] & 1;

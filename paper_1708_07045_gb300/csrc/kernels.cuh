@@ -7,6 +7,13 @@
 
 namespace bpmf {
 
+// Standard-state concentration of Eq. standard_binding_fe: 1 mol/L, i.e.
+// N_A molecules per litre = N_A / 1e27 molecules per A^3.
+#ifndef BPMF_STANDARD_CONC_DEFINED
+#define BPMF_STANDARD_CONC_DEFINED
+constexpr double kStandardConc = 6.02214076e23 / 1e27;
+#endif
+
 // Per-configuration placement metadata (computed from the FP32 coordinates).
 struct ConfMeta {
   float lo[3];   // minimum coordinate per axis (A)
@@ -210,6 +217,14 @@ struct RefineArgs {
   float4 *part;            // [batch][K][S0] LSE partials (planes with candidates rewritten)
   double *export_E;        // optional, batch entry 0, receptor 0: [S0][S1][S2] (exact where refined)
 };
+
+// ---- host plan helpers (bpmf_api.cu), shared by every entry point ----------
+int smooth_edge(int n);              // smallest even 2^a 3^b 5^c 7^d >= n (<= BPMF_MAX_FFT_EDGE), else 0
+FftPlan make_plan(int P);            // radix stages 8, 4, 2, then 3, 5, 7
+void twiddle_values(int P, float4 *out);  // exp(-2 pi i k / P), k < P, as float pairs
+int box_extent(float lo, float hi, float hf);  // ligand-box edge in nodes (single precision rule)
+// site window of a (configuration, receptor) pair along one axis; returns its valid count
+long long site_window(int N, int site_lo, int site_n, int u, int &w0, int &sa, int &sb);
 
 // ---- launch wrappers (kernels.cu, ligspec.cu, occupancy.cu, refine.cu) ---------
 cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st);

@@ -6,6 +6,11 @@
 namespace bpmf {
 
 constexpr int kFeatures = 24;
+// Standard-state concentration (1 M = N_A / 1e27 molecules per A^3), as in kernels.cuh
+#ifndef BPMF_STANDARD_CONC_DEFINED
+#define BPMF_STANDARD_CONC_DEFINED
+constexpr double kStandardConc = 6.02214076e23 / 1e27;
+#endif
 
 struct GemmArgs {
   const float *A;          // element (m, k) at A[m * sam + k * sak]
