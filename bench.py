@@ -29,7 +29,7 @@ import synth  # noqa: E402
 METRIC = "pose energies/s & BPMFs/s, chosen form vs plain FP32 path at 0.01 kcal/mol"
 WORKLOAD = "protein-scale: 96^3 grid h=0.25 A, 4 receptor conformations, 30-atom ligand, 2000 configurations, 40^3 site box"
 N_CONF, N_REC, N_ATOMS = 2000, 4, 30
-FP32_LANES_PER_SM, N_SM = 128, 152
+FP32_LANES_PER_SM = 128
 # FP32 instructions per float-pair flop for the add/mul mix of the radix
 # stages (add: TwoSum 6 + 2 + FastTwoSum 3 = 11; mul: 1 + 3 FMA + 3 = 7; ~70 % adds)
 FF_INSTR_PER_FLOP = 9.8
@@ -203,45 +203,41 @@ def run_reference(args):
     return 0
 
 
-def crop_edges(u, S, P, J, N=96, site_lo=28):
-    """Transform edges per configuration as the library chooses them: the
-    per-axis crop edge from bpmf_crop_window (the library's own rule for a
-    grid of N nodes with the site [site_lo, site_lo + S)), kept for a crop
-    only when its configurations save at least 24 configurations' worth of
-    spectrum volume (the batch-level rule of bpmf_eval).  u: [J, 3]
-    ligand-box edges."""
-    import paper_1708_07045_gb300 as pkg
-    edge = {int(v): pkg.bpmf_crop_window(N, site_lo, S, int(v))[0] for v in np.unique(u)}
-    pc = np.vectorize(lambda v: edge[int(v)])(u)
-    vol = lambda t: t[0] * t[1] * (t[2] // 2 + 1)
-    keys = [tuple(int(v) for v in r) for r in pc]
-    cnt = {}
-    for k in keys:
-        cnt[k] = cnt.get(k, 0) + 1
-    full = (P, P, P)
-    for j, k in enumerate(keys):
-        if k != full and cnt[k] * (1 - vol(k) / vol(full)) < 24:
-            pc[j] = P
-    return pc
+def transform_edges(pkg, sess, w, mode_id):
+    """[J, K, 3] transform edges that bpmf_eval uses for every (configuration,
+    receptor) pair of the workload, from the library's own plan query."""
+    lig = w.ligands[0]
+    J = lig.coords.shape[0]
+    recs = [pkg.bpmf_receptor_load(sess.ctx, r.grids, r.h, r.origin, r.site_lo, r.site_n) for r in w.receptors]
+    lh = pkg.bpmf_ligand_batch(sess.ctx, [lig.params.n_atoms], [J], np.ascontiguousarray(lig.coords.reshape(-1, 3)),
+                               lig.params.q, lig.params.eps, lig.params.R)
+    try:
+        return pkg.bpmf_transform_edges(sess.ctx, lh, recs, J, mode_id)
+    finally:
+        pkg.bpmf_ligand_free(lh)
+        for r in recs:
+            pkg.bpmf_receptor_free(r)
 
 
-def alg_work(w, n_valid, mode, launches_per_step=None):
+def alg_work(w, edges, mode, launches_per_step=None):
     """Algorithmic FLOPs (5 P log2 P per complex line transform, 8 per complex
     multiply-add) and bytes per kernel for the whole step, on each
-    configuration's transform edges (the receptor crop it runs on).  Bytes:
-    the ligand spectra read and x-pass outputs written per configuration, and
-    the receptor spectra read once per launch (launches_per_step launches
-    share them; one per configuration when not given)."""
-    P = 96
-    S = 40
-    K = N_REC
-    J = N_CONF
-    E = 16 if mode == "ff" else 8
+    configuration's transform edges (``edges`` [J, K, 3] from
+    bpmf_transform_edges; the receptors of the workload share one padded edge,
+    so one group).  Bytes: the ligand spectra read and x-pass outputs written
+    per configuration, and the receptor spectra read once per launch
+    (launches_per_step launches share them; one per configuration when not
+    given)."""
+    K = len(w.receptors)
+    S = np.array(w.receptors[0].site_n, dtype=float)
+    h = w.receptors[0].h
     lig = w.ligands[0]
+    J = lig.coords.shape[0]
+    E = 16 if mode == "ff" else 8
+    pc = edges[:, 0, :].astype(float)
     ext = (lig.coords.max(1) - lig.coords.min(1)).astype(np.float32)
-    u = np.minimum(np.ceil((ext / np.float32(0.25)).astype(np.float32)).astype(int) + 4, P)
-    pc = crop_edges(u, S, P, J)
-    P0, P1, P2 = pc[:, 0].astype(float), pc[:, 1].astype(float), pc[:, 2].astype(float)
+    u = np.minimum(np.ceil((ext / np.float32(h)).astype(np.float32)).astype(int) + 4, pc.astype(int))
+    P0, P1, P2 = pc[:, 0], pc[:, 1], pc[:, 2]
     F2 = np.floor(P2 / 2) + 1
     Q = P1 * F2
     cfft = lambda p: 5 * p * np.log2(p)
@@ -250,11 +246,12 @@ def alg_work(w, n_valid, mode, launches_per_step=None):
     work = {}
     # x-pass: forward of 3 channels, then per receptor product + inverse, per (y, zf) column
     work["k_xfused"] = {"flops": float(np.sum(Q * (3 * cfft(P0) + K * (cfft(P0) + 3 * 8 * P0)))),
-                        "bytes": float(np.sum(3 * u[:, 0] * Q * E + K * S * Q * E
+                        "bytes": float(np.sum(3 * u[:, 0] * Q * E + K * S[0] * Q * E
                                               + K * 3 * P0 * Q * 8 * rec_mult / per_launch))}
-    work["k_axis(y inv)"] = {"flops": float(np.sum(K * S * F2 * cfft(P1))),
-                             "bytes": float(np.sum(K * S * (Q + S * F2) * E))}
-    work["k_zinv"] = {"flops": float(np.sum(K * S * (S / 2) * cfft(P2))), "bytes": float(np.sum(K * S * S * F2 * E))}
+    work["k_axis(y inv)"] = {"flops": float(np.sum(K * S[0] * F2 * cfft(P1))),
+                             "bytes": float(np.sum(K * S[0] * (Q + S[1] * F2) * E))}
+    work["k_zinv"] = {"flops": float(np.sum(K * S[0] * (S[1] / 2) * cfft(P2))),
+                      "bytes": float(np.sum(K * S[0] * S[1] * F2 * E))}
     return work
 
 
@@ -637,6 +634,7 @@ def run_ours(args):
     w = make_workload(rank)
     lig = w.ligands[0]
     dev = torch.device("cuda", local)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     grids = [torch.from_numpy(r.grids).to(dev) for r in w.receptors]
     coords = torch.from_numpy(np.ascontiguousarray(lig.coords.reshape(-1, 3))).to(dev)
     params = [torch.from_numpy(getattr(lig.params, k)).to(dev) for k in ("q", "eps", "R")]
@@ -812,7 +810,8 @@ def run_ours(args):
                                               f"all valid translations ({dt:.1f} s)"}
         # roofline of the dominant kernel, from the live per-kernel event times
         top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else None
-        work = alg_work(w, res_chosen["n_valid"], chosen, launches_per_step=top[1][1] / args.steps if top else None)
+        edges = transform_edges(pkg, sess, w, modes[chosen])
+        work = alg_work(w, edges, chosen, launches_per_step=top[1][1] / args.steps if top else None)
         roof = None
         if top:
             name, (ms_tot, nl) = top
@@ -821,7 +820,7 @@ def run_ours(args):
             if key is not None:
                 flops = work[key]["flops"] * args.steps
                 if chosen == "ff":
-                    peak = N_SM * FP32_LANES_PER_SM * sm_hz / FF_INSTR_PER_FLOP / 1e12
+                    peak = n_sm * FP32_LANES_PER_SM * sm_hz / FF_INSTR_PER_FLOP / 1e12
                     ach = flops / (ms_tot / 1e3) / 1e12
                     traffic = None
                     if name == "k_xfused<ff>" and kernel_src_sha() == XFUSED_TRAFFIC["src_sha"]:
@@ -830,7 +829,7 @@ def run_ours(args):
                             "frac": ach / peak, "traffic": traffic,
                             "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (scaled "
                                             "from a 45-configuration launch by configurations per launch)",
-                            "peak_note": "derived: 152 SM x 128 FP32 lanes x median SM clock / 9.8 FP32 "
+                            "peak_note": f"derived: {n_sm} SM x 128 FP32 lanes x median SM clock / 9.8 FP32 "
                                          "instructions per float-pair flop",
                             "launches": nl, "ms_per_launch": ms_tot / nl}
                 else:
@@ -838,7 +837,7 @@ def run_ours(args):
                     peak_b = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
                         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
                     ach_b = work[key]["bytes"] * args.steps / (ms_tot / 1e3) / 1e9
-                    peak_f = N_SM * FP32_LANES_PER_SM * 2 * sm_hz / 1e12
+                    peak_f = n_sm * FP32_LANES_PER_SM * 2 * sm_hz / 1e12
                     ach_f = flops / (ms_tot / 1e3) / 1e12
                     hbm = {"kernel": name, "bound": "hbm", "achieved": ach_b, "peak": peak_b, "unit": "GB/s",
                            "frac": ach_b / peak_b, "traffic": None,
@@ -846,7 +845,7 @@ def run_ours(args):
                            "launches": nl, "ms_per_launch": ms_tot / nl}
                     alu = {"kernel": name, "bound": "alu", "achieved": ach_f, "peak": peak_f, "unit": "TFLOP/s",
                            "frac": ach_f / peak_f, "traffic": None,
-                           "peak_note": "derived: 152 SM x 128 FP32 lanes x 2 (FMA) x median SM clock",
+                           "peak_note": f"derived: {n_sm} SM x 128 FP32 lanes x 2 (FMA) x median SM clock",
                            "launches": nl, "ms_per_launch": ms_tot / nl}
                     roof, second = (hbm, alu) if hbm["frac"] >= alu["frac"] else (alu, hbm)
                     roof["other_roof"] = {k: second[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
@@ -856,7 +855,7 @@ def run_ours(args):
                 "vs_baseline": None,
                 "dtype": {"ff": "ff (float-pair FP32)", "fp32": "f32",
                           "refine": "f32 correlation + f64 re-evaluation of the low-energy window"}[chosen],
-                "data": "synthetic (seeded receptors and ligand chain, see DESIGN.md)",
+                "data": "synthetic (seeded receptors in a spherical shell, ligand chain with random torsions and rotations)",
                 "config": {"workload": WORKLOAD, "form": chosen, "l2": "flushed (512 MiB write) between timed steps",
                            "poses_per_step": n_poses},
                 "bpmfs_per_s": bpmfs,

@@ -276,6 +276,15 @@ int bpmf_fft_edge(int n);
  */
 int bpmf_crop_window(int n, int site_lo, int site_n, int u, int *edge, int *c0);
 
+/* bpmf_transform_edges -- the transform edges (P0, P1, P2) on which
+ * bpmf_eval runs each configuration against each receptor in `mode`: the
+ * receptor's padded edges, or the edges of the site crop it is given (the
+ * per-axis rule of bpmf_crop_window, kept only where the crop's
+ * configurations save at least 24 configurations' worth of spectrum volume).
+ * Host only; no device work.  edges: HOST int [total_conf][K][3].
+ * Errors: INVALID_ARG, SIZE_UNSUPPORTED (receptors of different spacings). */
+int bpmf_transform_edges(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, int K, unsigned mode, int *edges);
+
 /* Upper bound on the device workspace bpmf_eval may hold (bytes, default
  * 3 GiB); configurations are processed in batches that fit.  Results do not
  * depend on the batch size (every step is deterministic).  Errors:

@@ -118,6 +118,7 @@ _SIGS = {
     "bpmf_profile_count": (_I, [_P]),
     "bpmf_profile_entry": (_I, [_P, _I, ctypes.c_char_p, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)]),
     "bpmf_set_graph_mode": (_I, [_P, _I]),
+    "bpmf_transform_edges": (_I, [_P, _P, _P, _I, ctypes.c_uint, _P]),
     "bpmf_features": (_I, [_P, _P, _D, _P, _P]),
     "bpmf_valid_counts": (_I, [_P, _P, _P, _I, _P]),
     "bpmf_mlp_param_count": (ctypes.c_longlong, [_I, _I, _I]),
@@ -463,4 +464,15 @@ def bpmf_valid_counts(ctx, lig, recs, total_conf):
     out = np.empty((int(total_conf), K), dtype=np.int64)
     _check(lib().bpmf_valid_counts(ctx, lig, ctypes.cast(arr, ctypes.c_void_p), K, _ptr(out, np.int64)),
            "bpmf_valid_counts", ctx)
+    return out
+
+
+def bpmf_transform_edges(ctx, lig, recs, total_conf, mode):
+    """int32 [total_conf, K, 3]: the transform edges bpmf_eval uses for each
+    (configuration, receptor) pair in ``mode`` (host-only query)."""
+    K = len(recs)
+    arr = (ctypes.c_void_p * K)(*[r.value if isinstance(r, ctypes.c_void_p) else r for r in recs])
+    out = np.empty((int(total_conf), K, 3), dtype=np.int32)
+    _check(lib().bpmf_transform_edges(ctx, lig, ctypes.cast(arr, ctypes.c_void_p), K, int(mode), _ptr(out, np.int32)),
+           "bpmf_transform_edges", ctx)
     return out

@@ -1394,6 +1394,31 @@ std::vector<RecGroup> group_receptors(const bpmf_rec_t *recs, int K) {
   return gs;
 }
 
+// Transform edges of each of J configurations against a receptor group:
+// the crop edge that holds every receptor node the site windows of the group
+// reach with the configuration's ligand box (the split-bf16 form keeps the
+// full edges), and a crop is kept only where its configurations save at least
+// 24 configurations' worth of spectrum volume (a crop costs one transform of
+// the group's grids).
+std::vector<std::array<int, 3>> transform_edges(const ConfMeta *mj, int J, const RecGroup &g, const bpmf_rec_t *recs,
+                                                bool split) {
+  const int Kg = (int)g.ks.size();
+  std::vector<std::array<int, 3>> pc(std::max(J, 1));
+  for (int i = 0; i < J; ++i)
+    for (int d = 0; d < 3; ++d) {
+      int W = 0;
+      for (int kg = 0; kg < Kg; ++kg) W = std::max(W, recs[g.ks[kg]]->site_n[d] + std::min(mj[i].u[d], g.P[d]) - 1);
+      pc[i][d] = split ? g.P[d] : crop_edge(W, g.P[d]);
+    }
+  const std::array<int, 3> Pf{g.P[0], g.P[1], g.P[2]};
+  auto vol = [](const std::array<int, 3> &p) { return (double)p[0] * p[1] * (p[2] / 2 + 1); };
+  std::map<std::array<int, 3>, int> count;
+  for (int i = 0; i < J; ++i) ++count[pc[i]];
+  for (int i = 0; i < J; ++i)
+    if (pc[i] != Pf && count[pc[i]] * (1.0 - vol(pc[i]) / vol(Pf)) < 24.0) pc[i] = Pf;
+  return pc;
+}
+
 bpmf_ctx::Tune tune_for(bpmf_ctx *c, const int P[3], unsigned mode) {
   auto it = c->tune.find(std::vector<int>{P[0], P[1], P[2], (int)mode});
   return it == c->tune.end() ? bpmf_ctx::Tune{} : it->second;
@@ -1525,27 +1550,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       const int Kg = (int)g.ks.size();
       GroupPlan gpn;
       const ConfMeta *mj = meta.data() + pl.j_first;
-      // transform edges per configuration: a crop edge that holds every
-      // receptor node the site windows of the group reach with this
-      // configuration's ligand box (the split-bf16 form keeps the full edges)
-      std::vector<std::array<int, 3>> pc(std::max(J, 1));
-      for (int i = 0; i < J; ++i)
-        for (int d = 0; d < 3; ++d) {
-          int W = 0;
-          for (int kg = 0; kg < Kg; ++kg)
-            W = std::max(W, recs[g.ks[kg]]->site_n[d] + std::min(mj[i].u[d], g.P[d]) - 1);
-          pc[i][d] = split ? g.P[d] : crop_edge(W, g.P[d]);
-        }
-      // a crop costs one transform of the group's grids: keep it only where its
-      // configurations save at least 24 configurations' worth of spectrum volume
+      std::vector<std::array<int, 3>> pc = transform_edges(mj, J, g, recs, split);
       const std::array<int, 3> Pf{g.P[0], g.P[1], g.P[2]};
-      {
-        auto vol = [](const std::array<int, 3> &p) { return (double)p[0] * p[1] * (p[2] / 2 + 1); };
-        std::map<std::array<int, 3>, int> count;
-        for (int i = 0; i < J; ++i) ++count[pc[i]];
-        for (int i = 0; i < J; ++i)
-          if (pc[i] != Pf && count[pc[i]] * (1.0 - vol(pc[i]) / vol(Pf)) < 24.0) pc[i] = Pf;
-      }
       // processing order: by crop, then by ligand-box extent, so each batch's
       // box (the maximum over its members) stays tight; the merge scatters
       // results back to the caller's order
@@ -1880,6 +1886,37 @@ int eval_entry(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, doubl
   }
 }
 }  // namespace
+
+int bpmf_transform_edges(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, unsigned mode, int *edges) {
+  if (!c || !lg || !recs || K < 1 || (!edges && lg->total_conf > 0))
+    return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or K < 1");
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE)
+    return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
+  try {
+    last_msg.clear();
+    check_recs(recs, K, c);
+    const std::vector<RecGroup> groups = group_receptors(recs, K);
+    std::vector<ConfMeta> meta;
+    std::vector<PairInfo> info;
+    std::vector<long long> nv;
+    for (int li = 0; li < lg->n_lig; ++li) {
+      ligand_tables(lg, li, recs, K, recs[0]->h, meta, info, nv);
+      const int J = lg->n_conf[li];
+      for (const RecGroup &g : groups) {
+        const std::vector<std::array<int, 3>> pc = transform_edges(meta.data(), J, g, recs,
+                                                                   mode == BPMF_MODE_SPLIT_BF16);
+        for (int i = 0; i < J; ++i)
+          for (int k : g.ks)
+            for (int d = 0; d < 3; ++d) edges[((lg->conf_off[li] + i) * K + k) * 3 + d] = pc[i][d];
+      }
+    }
+    return BPMF_OK;
+  } catch (Fail f) {
+    return set_err(c, f.code, last_msg.empty() ? bpmf_status_string(f.code) : last_msg);
+  } catch (std::bad_alloc &) {
+    return set_err(c, BPMF_ERR_OOM, "host allocation");
+  }
+}
 
 int bpmf_eval(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode, double *logZ,
               int64_t *n_valid, double *bpmf_out, double *dG, void *stream) {

@@ -14,6 +14,25 @@ namespace bpmf {
 
 // --------------------------------------------------------------------------
 // small helpers
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (!cache[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 1;
+    }
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
 __device__ __forceinline__ int imod(int a, int m) {
   int r = a % m;
   return r < 0 ? r + m : r;
@@ -925,7 +944,7 @@ cudaError_t launch_crop(const float *grid, const int N[3], const int c0[3], cons
   cudaError_t err = cudaMemsetAsync(sumsq, 0, 3 * sizeof(double), st);
   if (err != cudaSuccess) return err;
   const int rows = E[0] * E[1];
-  const int blocks = std::min(rows, 152 * 4);
+  const int blocks = std::min(rows, sm_count() * 4);
   const int threads = E[2] >= 128 ? 128 : (E[2] >= 64 ? 64 : 32);
   k_crop<<<dim3(blocks, 3), threads, 0, st>>>(grid, N[0], N[1], N[2], c0[0], c0[1], c0[2], e[0], e[1], e[2], E[0],
                                               E[1], E[2], out, sumsq);

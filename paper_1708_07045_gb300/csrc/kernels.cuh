@@ -218,6 +218,8 @@ struct RefineArgs {
   double *export_E;        // optional, batch entry 0, receptor 0: [S0][S1][S2] (exact where refined)
 };
 
+int sm_count();                      // streaming multiprocessors of the current device (kernels.cu)
+
 // ---- host plan helpers (bpmf_api.cu), shared by every entry point ----------
 int smooth_edge(int n);              // smallest even 2^a 3^b 5^c 7^d >= n (<= BPMF_MAX_FFT_EDGE), else 0
 FftPlan make_plan(int P);            // radix stages 8, 4, 2, then 3, 5, 7

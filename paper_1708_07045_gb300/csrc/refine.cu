@@ -234,7 +234,7 @@ __global__ void k_sumsq(const float *g, long long vol, double *out) {
 cudaError_t launch_sumsq(const float *g, long long vol, double *out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, 3 * sizeof(double), st);
   if (e != cudaSuccess) return e;
-  k_sumsq<<<dim3(152, 3), 256, 0, st>>>(g, vol, out);
+  k_sumsq<<<dim3(sm_count(), 3), 256, 0, st>>>(g, vol, out);
   return cudaGetLastError();
 }
 
