@@ -854,7 +854,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
                 "dtype": {"ff": "ff (float-pair FP32)", "fp32": "f32",
-                          "refine": "f32 correlation + f64 re-evaluation of the low-energy window"}[chosen],
+                          "refine": "f32 correlation + float-pair (FP32-instruction) re-evaluation of the "
+                                    "low-energy window"}[chosen],
                 "data": "synthetic (seeded receptors in a spherical shell, ligand chain with random torsions and rotations)",
                 "config": {"workload": WORKLOAD, "form": chosen, "l2": "flushed (512 MiB write) between timed steps",
                            "poses_per_step": n_poses},

@@ -14,8 +14,9 @@
  *
  * Conventions shared by every call
  *  - Status: every int-returning call returns BPMF_OK (0), a negative
- *    BPMF_ERR_* code, or the positive warning BPMF_WARN_NO_VALID.  No C++
- *    exception crosses the ABI.  bpmf_last_error() gives a one-line reason.
+ *    BPMF_ERR_* code, or a positive value: the OR of the warning bits
+ *    BPMF_WARN_*.  No C++ exception crosses the ABI.  bpmf_last_error() gives
+ *    a one-line reason.
  *  - Pointers: array arguments may be host memory or device memory of the
  *    context's GPU (detected per pointer with cudaPointerGetAttributes), except
  *    the small per-ligand count arrays, which must be host memory.  Inputs are
@@ -47,6 +48,11 @@ extern "C" {
 /* warning: at least one (configuration, receptor) pair has no valid
  * translation; its log Z is -inf (and a BPMF with no valid pose is +inf). */
 #define BPMF_WARN_NO_VALID 1
+/* warning (BPMF_MODE_REFINE): for at least one ligand the certificate check
+ * failed (an FP32 energy further than B from its exact value) or a candidate
+ * list overflowed; that ligand's results were recomputed in float pairs
+ * (BPMF_MODE_FF) and are exact to the float-pair form's precision. */
+#define BPMF_WARN_REFINE_FALLBACK 2
 
 /* Arithmetic of the correlation (forward transforms, spectral product,
  * inverse transforms).  Spreading is FP32 in both; the merge is FP64.
@@ -67,18 +73,27 @@ extern "C" {
  *                     result.  Other edges fall back to the FP32 stages. */
 #define BPMF_MODE_SPLIT_BF16 2u
 /*   BPMF_MODE_REFINE -- the FP32 correlation for every translation, then an
- *     exact re-evaluation, in FP64, of the translations that can matter.  The
- *     FP32 correlation error stays below B = 8 eps32 sqrt(log2 P0 P1 P2)
- *     sum_t rms(G_t) ||gamma_t||_2.  Every translation whose FP32 energy lies
- *     within W + 2B of the configuration's FP32 minimum (W = kT max(20,
- *     ln(1e5 n)), n the site-window size) is re-evaluated as the direct sum
- *     the correlation equals: sum_i sum_t gamma_t,i trilinear(G_t, g_i + m).
- *     Every translation within W of the true minimum is among them; the others
- *     keep their FP32 energies and together weigh less than 1e-5 of S.  The
+ *     exact re-evaluation, in float-pair arithmetic (FP32 instructions,
+ *     about 2^-44 relative), of the translations that can matter.  The FP32
+ *     correlation error is expected below B = 8 eps32 sqrt(log2 P0 P1 P2)
+ *     sum_t rms(G_t) ||gamma_t||_2 (the typical roundoff growth of an FFT
+ *     correlation).  Every translation whose FP32 energy lies within W + 2B
+ *     of the configuration's FP32 minimum (W = kT max(20, ln(1e5 n)), n the
+ *     site-window size) is re-evaluated as the direct sum the correlation
+ *     equals: sum_i sum_t gamma_t,i trilinear(G_t, g_i + m).  While the bound
+ *     holds, every translation within W of the true minimum is among them;
+ *     the others keep their FP32 energies and together weigh less than 1e-5
+ *     of S.  The bound is checked as a certificate on every re-evaluated
+ *     translation (|E_fp32 - E_exact| <= B); a failure, or a candidate list
+ *     that overflows, makes the call recompute that ligand in float pairs and
+ *     return BPMF_WARN_REFINE_FALLBACK.  In this form bpmf_eval synchronises
+ *     `stream` before returning (it reads the certificate flags).  The
  *     energies that can carry weight are exact, and so are log Z, BPMF and dG
  *     up to that 1e-5, at about the FP32 form's cost.  Exported energies
- *     outside the window are the FP32 values.  The receptor handle keeps a
- *     device copy of its FP32 grids for this form. */
+ *     outside the window are the FP32 values.  The energy volume never
+ *     reaches device memory: each site plane appends only its candidates to a
+ *     per-pair list.  The receptor handle keeps a device copy of its FP32
+ *     grids for this form. */
 #define BPMF_MODE_REFINE 3u
 
 /* Largest supported ligand (atoms) and padded FFT edge. */
@@ -284,6 +299,13 @@ int bpmf_crop_window(int n, int site_lo, int site_n, int u, int *edge, int *c0);
  * Host only; no device work.  edges: HOST int [total_conf][K][3].
  * Errors: INVALID_ARG, SIZE_UNSUPPORTED (receptors of different spacings). */
 int bpmf_transform_edges(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, int K, unsigned mode, int *edges);
+
+/* bpmf_set_refine_check_scale -- multiply B in the refined form's
+ * certificate check (not in its window) by `scale` (default 1).  A scale
+ * below the observed error ratio makes the check fail, which exercises the
+ * float-pair fallback; it exists for testing.  Errors: INVALID_ARG
+ * (scale < 0). */
+int bpmf_set_refine_check_scale(bpmf_ctx_t ctx, double scale);
 
 /* Upper bound on the device workspace bpmf_eval may hold (bytes, default
  * 3 GiB); configurations are processed in batches that fit.  Results do not

@@ -32,6 +32,7 @@ BPMF_ERR_CUDA = -3
 BPMF_ERR_TIMEOUT = -4
 BPMF_ERR_SIZE_UNSUPPORTED = -5
 BPMF_WARN_NO_VALID = 1
+BPMF_WARN_REFINE_FALLBACK = 2
 BPMF_MODE_FP32 = 0
 BPMF_MODE_FF = 1
 BPMF_MODE_SPLIT_BF16 = 2
@@ -119,6 +120,7 @@ _SIGS = {
     "bpmf_profile_entry": (_I, [_P, _I, ctypes.c_char_p, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int64)]),
     "bpmf_set_graph_mode": (_I, [_P, _I]),
     "bpmf_transform_edges": (_I, [_P, _P, _P, _I, ctypes.c_uint, _P]),
+    "bpmf_set_refine_check_scale": (_I, [_P, _D]),
     "bpmf_features": (_I, [_P, _P, _D, _P, _P]),
     "bpmf_valid_counts": (_I, [_P, _P, _P, _I, _P]),
     "bpmf_mlp_param_count": (ctypes.c_longlong, [_I, _I, _I]),
@@ -476,3 +478,8 @@ def bpmf_transform_edges(ctx, lig, recs, total_conf, mode):
     _check(lib().bpmf_transform_edges(ctx, lig, ctypes.cast(arr, ctypes.c_void_p), K, int(mode), _ptr(out, np.int32)),
            "bpmf_transform_edges", ctx)
     return out
+
+
+def bpmf_set_refine_check_scale(ctx, scale):
+    """Scale of B in the refined form's certificate check (testing)."""
+    return _check(lib().bpmf_set_refine_check_scale(ctx, float(scale)), "bpmf_set_refine_check_scale", ctx)

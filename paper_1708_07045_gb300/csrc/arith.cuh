@@ -146,4 +146,30 @@ __device__ __forceinline__ cx<T> tw_load(const float4 &w, bool inverse) {
   return cx<T>{re, inverse ? s_neg(im) : im};
 }
 
+// ---- placement ("FFT-based BPMF Estimation": the lowest coordinate of each
+// axis two grid spacings above plane 0) ---------------------------------------
+// Grid-unit position g = (x - lo) / h + 2 as a float pair: x - lo exactly
+// (TwoSum), then a two-step quotient by the float-pair spacing.
+__device__ __forceinline__ ff place_ff(float x, float lo, ff h) {
+  const ff dx = two_sum(x, -lo);
+  const float q1 = __fdiv_rn(dx.hi, h.hi);
+  const float p = __fmul_rn(q1, h.hi);
+  const float pe = __fmaf_rn(q1, h.hi, -p);
+  float r = __fsub_rn(__fsub_rn(dx.hi, p), pe);
+  r = __fadd_rn(r, __fsub_rn(dx.lo, __fmul_rn(q1, h.lo)));
+  const float q2 = __fdiv_rn(r, h.hi);
+  return s_norm(s_add(fast_two_sum(q1, q2), ff{2.f, 0.f}));
+}
+
+// Trilinear cell and fraction of a float-pair coordinate: c = floor(g) (the
+// cell below an exact node position), f = g - c exactly, clamped to [0, 1].
+__device__ __forceinline__ void cell_ff(ff g, int &c, ff &f) {
+  float cf = floorf(g.hi);
+  if (g.hi == cf && g.lo < 0.f) cf -= 1.f;
+  f = two_sum(__fsub_rn(g.hi, cf), g.lo);  // g.hi - cf is exact
+  if (f.hi < 0.f) f = ff{0.f, 0.f};
+  if (f.hi > 1.f || (f.hi == 1.f && f.lo > 0.f)) f = ff{1.f, 0.f};
+  c = (int)cf;
+}
+
 }  // namespace bpmf

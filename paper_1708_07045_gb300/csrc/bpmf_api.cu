@@ -119,6 +119,9 @@ struct bpmf_ctx {
   };
   std::map<std::vector<int>, Tune> tune;
   bool warn_last = false;  // BPMF_WARN_NO_VALID of the plan behind the cached graph
+  int *fail_host = nullptr;  // pinned [fail_n]: refined form, per ligand of the last call, certificate failed
+  size_t fail_n = 0;
+  float refine_check_scale = 1.f;  // multiplies B in the refined form's certificate check
   // library streams on which independent receptor crops are transformed
   // concurrently (forked from and joined back into the caller's stream)
   static constexpr int kSide = 4;
@@ -144,7 +147,8 @@ struct bpmf_rec {
   uint32_t *occ = nullptr;              // occupancy tables [kOccLevels][N0 + 32][occW][N1 + 32], or null
   int occW = 0;
   float *grid = nullptr;                // the FP32 grids [3][N0][N1][N2] (refined form)
-  double *sumsq = nullptr;              // [3] their sums of squares (FP32 error bound)
+  float *sumsq = nullptr;               // [3] their sums of squares (FP32 error bound)
+  float2 *sumsq_scratch = nullptr;      // [kSumsqScratch] partial sums (launch_sumsq)
   // spectra of the grids cropped to a box of transform edges P around the
   // site, made on first use, per P (the uncropped spectrum is hi / lo)
   struct Crop {
@@ -152,7 +156,8 @@ struct bpmf_rec {
     size_t mem_bytes = 0;
     int c0[3] = {0, 0, 0};              // first node of the crop
     float2 *hi = nullptr, *lo = nullptr;  // [3][P0][P1 (P2/2+1)]
-    double *sumsq = nullptr;            // [3] over the cropped nodes
+    float *sumsq = nullptr;             // [3] over the cropped nodes
+    float2 *sumsq_scratch = nullptr;    // [kSumsqScratch] partial sums (launch_sumsq)
     double vol = 0;                     // cropped nodes per channel
   };
   std::map<std::array<int, 3>, Crop> crops;
@@ -171,8 +176,7 @@ struct bpmf_lig {
   std::vector<float> minmax;  // host [total_conf][6]
   std::vector<float> R_host;  // host [total_atoms] (occupancy radii)
   std::vector<float> q_host, eps_host;  // host [total_atoms] (FP32 error bound)
-  double *gamma64 = nullptr;  // device [3][total_atoms] FP64 generalised charges (refined form)
-  void *mem = nullptr;        // one device block holding coords, gamma, q, eps, R and gamma64
+  void *mem = nullptr;        // one device block holding coords, gamma, q, eps and R
   size_t mem_bytes = 0;
   int p_rep = 12, p_att = 6;
 };
@@ -448,9 +452,27 @@ struct BatchGeom {
   int K;
   int occ_cap = 0;  // ligand occupancy runs per configuration (0: no clash channel)
   int occ_rb = 1;   // CTAs per configuration building the runs
-  bool refine = false;  // refined form: FP32 energies kept for k_refine
+  bool refine = false;  // refined form: candidate lists for k_refine
+  int ref_cap = 0;      // refined form: translations per pair list
   int nmax = 0;         // atoms per configuration of the ligand
 };
+
+// Refined form: per-call inputs of run_batch
+struct RefineCtx {
+  const RefTab *rtabs = nullptr;  // [Kg] grids and sums of squares of the bucket's transforms
+  double gnorm[3] = {0, 0, 0};    // ||gamma_t||_2 of the ligand
+  double kT = 1.0;
+  float4 *part_ref = nullptr;     // [batch][Kg][2] corrections (this batch's slice)
+  int *fail = nullptr;            // the ligand's fallback flag
+  float check_scale = 1.f;
+};
+
+// Translations per pair list of the refined form: every translation of a
+// small site window, else 1/16 of them (at least 4096), at most kRefineMaxList.
+int refine_cap(const int S[3]) {
+  const long long nS = (long long)S[0] * S[1] * S[2];
+  return (int)std::min<long long>(std::min<long long>(nS, std::max<long long>(4096, nS / 16)), kRefineMaxList);
+}
 
 int clash_words(int S2) { return (S2 + 31) / 32; }
 
@@ -465,10 +487,9 @@ size_t batch_bytes_per_conf(const BatchGeom &g, size_t E) {
     occ = align_up(2 * (size_t)g.occ_cap * sizeof(OccRun)) + align_up(sizeof(int)) +
           align_up((size_t)g.K * g.S[0] * g.S[1] * clash_words(g.S[2]) * sizeof(uint32_t));
   size_t ref = 0;
-  if (g.refine)
-    ref = align_up((size_t)g.K * g.S[0] * g.S[1] * g.S[2] * sizeof(float)) +
-          align_up((size_t)g.K * g.S[0] * sizeof(float)) + align_up((size_t)g.K * sizeof(double)) +
-          2 * align_up((size_t)g.K * sizeof(float));
+  if (g.refine)  // lists, exact values, running minima and counts; window and bound per receptor
+    ref = align_up((size_t)g.K * g.ref_cap * sizeof(Cand)) + align_up((size_t)g.K * g.ref_cap * sizeof(float2)) +
+          2 * align_up((size_t)g.K * sizeof(int)) + 2 * align_up((size_t)g.K * sizeof(float));
   return align_up(box) + align_up(lz) + align_up(ly) + align_up(x2) + align_up(y2) + occ + ref;
 }
 
@@ -490,8 +511,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
                const PairInfo *d_info, const float2 *const *d_rhi, const float2 *const *d_rlo, double h,
                float nscale_hi, float nscale_lo, float escale_hi, float escale_lo, float4 *d_part,
                double *export_E, char *ws, cudaStream_t st, const bpmf_ctx::Tune &tn, bool split = false,
-               const OccTab *d_tabs = nullptr, const RefTab *d_rtabs = nullptr, const double *gnorm = nullptr,
-               double kT = 1.0) {
+               const OccTab *d_tabs = nullptr, const RefineCtx *rf = nullptr) {
   auto plan = [&](int P) { return split ? make_plan_split(c, P) : make_plan(P); };
   const size_t E = sizeof(cx<T>);
   char *p = ws;
@@ -530,20 +550,43 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     ca.clash = clash;
     launch(c, "k_clash", st, [&] { return launch_clash(ca, batch, st); });
   }
-  float *Ebuf = nullptr, *pmin = nullptr;
-  double *wnd = nullptr;
-  float *pmin_pair = nullptr, *thresh = nullptr;
+  RefineArgs ra{};
   if (g.refine) {
-    Ebuf = reinterpret_cast<float *>(p);
-    p += align_up((size_t)batch * g.K * g.S[0] * g.S[1] * g.S[2] * sizeof(float));
-    pmin = reinterpret_cast<float *>(p);
-    p += align_up((size_t)batch * g.K * g.S[0] * sizeof(float));
-    wnd = reinterpret_cast<double *>(p);
-    p += align_up((size_t)g.K * sizeof(double));
-    pmin_pair = reinterpret_cast<float *>(p);
-    p += align_up((size_t)batch * g.K * sizeof(float));
-    thresh = reinterpret_cast<float *>(p);
-    p += align_up((size_t)batch * g.K * sizeof(float));
+    const size_t np = (size_t)batch * g.K;
+    ra.rs.cand = reinterpret_cast<Cand *>(p);
+    p += align_up(np * g.ref_cap * sizeof(Cand));
+    ra.rs.exact = reinterpret_cast<float2 *>(p);
+    p += align_up(np * g.ref_cap * sizeof(float2));
+    ra.rs.pmin = reinterpret_cast<unsigned *>(p);
+    p += align_up(np * sizeof(unsigned));
+    ra.rs.cnt = reinterpret_cast<int *>(p);
+    p += align_up(np * sizeof(int));
+    ra.win = reinterpret_cast<float *>(p);
+    p += align_up((size_t)g.K * sizeof(float));
+    ra.bnd = reinterpret_cast<float *>(p);
+    p += align_up((size_t)g.K * sizeof(float));
+    ra.rs.win = ra.win;
+    ra.rs.bnd = ra.bnd;
+    ra.rs.cap = g.ref_cap;
+    ra.rs.fail = rf->fail;
+    ra.meta = d_meta;
+    ra.info = d_info;
+    ra.tabs = rf->rtabs;
+    for (int t = 0; t < 3; ++t) ra.gnorm[t] = (float)rf->gnorm[t];
+    ra.log2P3 = (float)std::log2((double)g.P[0] * g.P[1] * g.P[2]);
+    ra.check_scale = rf->check_scale;
+    ra.coords = lg->coords;
+    ra.gamma = lg->gamma;
+    ra.gamma_stride = (int)lg->total_atoms;
+    ra.kT = (float)rf->kT;
+    split_ff(-1.0 / rf->kT, ra.nikT_hi, ra.nikT_lo);
+    ra.K = g.K;
+    ra.S0 = g.S[0];
+    ra.S1 = g.S[1];
+    ra.S2 = g.S[2];
+    ra.part_ref = rf->part_ref;
+    ra.export_E = export_E;
+    launch(c, "k_refine_init", st, [&] { return launch_refine_init(ra, batch, st); });
   }
 
   float hh, hl;
@@ -621,7 +664,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   launch(c, sizeof(T) == 4 ? "k_xfused<fp32>" : "k_xfused<ff>", st, [&] { return launch_xfused<T>(xa, batch, st); });
 
   // FP32 forms: the y inverse runs inside the z inverse when the window fits
-  const bool fuse_y = sizeof(T) == 4 && !split && zinv_fused_fits(g.P[1], g.P[2], g.S[1], g.S[2]);
+  const bool fuse_y = sizeof(T) == 4 && !split && zinv_fused_fits(g.P[1], g.P[2], g.S[1], g.S[2], g.refine);
   if (!fuse_y) {
     AxisArgs yi{};
     yi.in = x2;
@@ -656,9 +699,8 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   zi.escale_hi = escale_hi;
   zi.escale_lo = escale_lo;
   zi.part = d_part;
-  zi.export_E = export_E;  // refined form: k_refine rewrites the planes it refines
-  zi.Ebuf = Ebuf;
-  zi.plane_min = pmin;
+  zi.export_E = export_E;  // refined form: k_refine overwrites the refined translations with exact values
+  if (g.refine) zi.rs = ra.rs;
   zi.clash = clash;
   zi.CW = CW;
   zi.plan = plan(g.P[2]);
@@ -672,29 +714,8 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   launch(c, fuse_y ? "k_zinv<fp32>(+y inv)" : (sizeof(T) == 4 ? "k_zinv<fp32>" : "k_zinv<ff>"), st,
          [&] { return launch_zinv<T>(zi, batch, st); });
   if (g.refine) {
-    RefineArgs ra{};
-    ra.E = Ebuf;
-    ra.plane_min = pmin;
-    ra.meta = d_meta;
-    ra.info = d_info;
-    ra.tabs = d_rtabs;
-    for (int t = 0; t < 3; ++t) ra.gnorm[t] = gnorm[t];
-    ra.log2P3 = std::log2((double)g.P[0] * g.P[1] * g.P[2]);
-    ra.coords = lg->coords;
-    ra.gamma64 = lg->gamma64;
-    ra.gamma_stride = (int)lg->total_atoms;
-    ra.h = h;
-    ra.kT = kT;
-    ra.ikT = (float)(1.0 / kT);
-    ra.window = wnd;
-    ra.pmin_pair = pmin_pair;
-    ra.thresh = thresh;
-    ra.K = g.K;
-    ra.S0 = g.S[0];
-    ra.S1 = g.S[1];
-    ra.S2 = g.S[2];
-    ra.part = d_part;
-    ra.export_E = export_E;
+    ra.h_hi = hh;
+    ra.h_lo = hl;
     launch(c, "k_refine", st, [&] { return launch_refine(ra, batch, st); });
   }
 }
@@ -784,6 +805,10 @@ const char *bpmf_status_string(int s) {
     case BPMF_ERR_TIMEOUT: return "timeout";
     case BPMF_ERR_SIZE_UNSUPPORTED: return "size unsupported";
     case BPMF_WARN_NO_VALID: return "warning: some configuration has no valid translation";
+    case BPMF_WARN_REFINE_FALLBACK:
+      return "warning: refined-form certificate failed; the ligand was recomputed in float pairs";
+    case BPMF_WARN_NO_VALID | BPMF_WARN_REFINE_FALLBACK:
+      return "warnings: some configuration has no valid translation; a ligand was recomputed in float pairs";
     default: return "unknown status";
   }
 }
@@ -857,6 +882,12 @@ int bpmf_set_graph_mode(bpmf_ctx_t c, int on) {
   return BPMF_OK;
 }
 
+int bpmf_set_refine_check_scale(bpmf_ctx_t c, double scale) {
+  if (!c || !(scale >= 0.0)) return set_err(c, BPMF_ERR_INVALID_ARG, "scale must be >= 0");
+  c->refine_check_scale = (float)scale;
+  return BPMF_OK;
+}
+
 int bpmf_set_workspace_limit(bpmf_ctx_t c, size_t bytes) {
   if (!c || bytes < (size_t(1) << 20)) return set_err(c, BPMF_ERR_INVALID_ARG, "workspace limit below 1 MiB");
   c->ws_budget = bytes;
@@ -905,6 +936,7 @@ void bpmf_destroy(bpmf_ctx_t c) {
     cudaEventDestroy(c->pinned_busy);
   }
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->fail_host) cudaFreeHost(c->fail_host);
   delete c;
 }
 
@@ -1066,7 +1098,8 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
       Carve cv;
       cv.add(&cr.hi, 3ull * Pc[0] * Q * sizeof(float2));
       cv.add(&cr.lo, 3ull * Pc[0] * Q * sizeof(float2));
-      cv.add(&cr.sumsq, 3 * sizeof(double));
+      cv.add(&cr.sumsq, 3 * sizeof(float));
+      cv.add(&cr.sumsq_scratch, kSumsqScratch * sizeof(float2));
       cr.mem = cv.alloc(c);
       cr.mem_bytes = cv.total;
       his[i] = cr.hi;
@@ -1078,7 +1111,8 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
       bpmf_rec::Crop &cr = out[todo[i]];
       const int e[3] = {ext[i][0], ext[i][1], ext[i][2]};
       float *dst = buf + 3ll * i * chan;
-      launch(c, "k_crop", st, [&] { return launch_crop(r->grid, r->N, cr.c0, e, Emax, dst, cr.sumsq, st); });
+      launch(c, "k_crop", st,
+             [&] { return launch_crop(r->grid, r->N, cr.c0, e, Emax, dst, cr.sumsq, cr.sumsq_scratch, st); });
     }
     const int P3[3] = {Pc[0], Pc[1], Pc[2]};
     grid_spectrum(c, buf, n, Emax, P3, his.data(), los.data(), st);
@@ -1157,13 +1191,14 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
     DevIn g(grids, 3 * vol * sizeof(float), st);
     Carve cv;
     cv.add(&r->grid, 3 * vol * sizeof(float));
-    cv.add(&r->sumsq, 3 * sizeof(double));
+    cv.add(&r->sumsq, 3 * sizeof(float));
+    cv.add(&r->sumsq_scratch, kSumsqScratch * sizeof(float2));
     cv.add(&r->hi, 3ull * P[0] * r->Q * sizeof(float2));
     cv.add(&r->lo, 3ull * P[0] * r->Q * sizeof(float2));
     r->mem = cv.alloc(c);
     r->mem_bytes = cv.total;
     CK(cudaMemcpyAsync(r->grid, g.p, 3 * vol * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    launch(c, "k_sumsq", st, [&] { return launch_sumsq(r->grid, (long long)vol, r->sumsq, st); });
+    launch(c, "k_sumsq", st, [&] { return launch_sumsq(r->grid, (long long)vol, r->sumsq, r->sumsq_scratch, st); });
     grid_spectrum(c, static_cast<const float *>(g.p), 1, N, P, &r->hi, &r->lo, st);
     if (!is_device_ptr(grids)) CK(cudaStreamSynchronize(st));
   } catch (Fail f) {
@@ -1280,7 +1315,6 @@ int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_
     cv.add(&lg->q, na * sizeof(float));
     cv.add(&lg->eps, na * sizeof(float));
     cv.add(&lg->R, na * sizeof(float));
-    cv.add(&lg->gamma64, 3 * std::max<size_t>(na, 1) * sizeof(double));
     cv.add(&lg->coords, std::max<size_t>(1, 3 * lg->total_coord_atoms) * sizeof(float));
     lg->mem = cv.alloc(c);
     lg->mem_bytes = cv.total;
@@ -1300,10 +1334,6 @@ int bpmf_ligand_batch(bpmf_ctx_t c, int n_lig, const int *n_atoms, const int *n_
       launch(c, "k_gamma", st, [&] {
         return launch_gamma((const float *)dq.p, (const float *)de.p, (const float *)dr.p, (int)na, p_rep, p_att,
                             lg->gamma, st);
-      });
-      launch(c, "k_gamma64", st, [&] {
-        return launch_gamma64((const float *)dq.p, (const float *)de.p, (const float *)dr.p, (int)na, p_rep, p_att,
-                              lg->gamma64, st);
       });
     }
     if (lg->total_coord_atoms > 0)
@@ -1458,7 +1488,8 @@ struct LigPlan {
 
 int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
               double *logZ, int64_t *n_valid, double *bpmf_out, double *dG, cudaStream_t st, int only_lig,
-              int only_conf, double *export_E, double *Emin = nullptr, double *Dom = nullptr) {
+              int only_conf, double *export_E, double *Emin = nullptr, double *Dom = nullptr,
+              std::vector<int> *fail_ligs = nullptr) {
   check_recs(recs, K, c);
   const double h = recs[0]->h;
   const bool use_ff = (mode == BPMF_MODE_FF);
@@ -1492,6 +1523,11 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     if (c->gexec && key == c->gkey) {
       CK(cudaGraphLaunch(c->gexec, st));
       CK(cudaEventRecord(c->pinned_busy, st));
+      if (refine) {  // the certificate flags the graph copied out
+        CK(cudaStreamSynchronize(st));
+        for (int li = lig_begin; li < lig_end; ++li)
+          if (c->fail_host[li - lig_begin] && fail_ligs) fail_ligs->push_back(li);
+      }
       return lg_warn_cached(c) ? BPMF_WARN_NO_VALID : BPMF_OK;
     }
   }
@@ -1607,8 +1643,10 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       gpn.occ_cap = bg.occ_cap;
       gpn.occ_rb = bg.occ_rb;
       bg.refine = refine;
+      bg.ref_cap = refine ? refine_cap(g.S) : 0;
       bg.nmax = lg->n_atoms[li];
-      const size_t part = align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
+      const size_t part = align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]) +
+                          (refine ? align_up(sizeof(float4) * 2 * (size_t)std::max(J, 1) * Kg) : 0);
       const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
       std::vector<PairInfo> info_g((size_t)std::max(J, 1) * Kg);
       for (int j0 = 0; j0 < J;) {
@@ -1633,7 +1671,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
           const bpmf_rec::Crop &cr = crs[kg];
           rp[kg] = cr.hi;
           rp[Kg + kg] = cr.lo;
-          rt[kg] = RefTab{r->grid, cr.sumsq, r->N[0], r->N[1], r->N[2], cr.vol};
+          rt[kg] = RefTab{r->grid, cr.sumsq, r->N[0], r->N[1], r->N[2], (float)cr.vol};
           for (int i = j0; i < j1; ++i) {
             PairInfo pi = info[(size_t)(pl.j_first + order[i]) * K + g.ks[kg]];
             for (int d = 0; d < 3; ++d) pi.wc[d] = pi.w0[d] - cr.c0[d];
@@ -1677,9 +1715,22 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     plans.push_back(std::move(pl));
   }
   const size_t blob_bytes = align_up(blob.size());
+  const int n_plan_ligs = lig_end - lig_begin;
+  const size_t fail_bytes = align_up(sizeof(int) * std::max(n_plan_ligs, 1));
   // device resources are made ready before any work is queued (and so before
-  // a capture begins): workspace, pinned staging, twiddle tables
-  char *ws = static_cast<char *>(workspace(c, blob_bytes + ws_need, st));
+  // a capture begins): workspace, pinned staging, twiddle tables, the pinned
+  // certificate flags
+  char *ws = static_cast<char *>(workspace(c, blob_bytes + fail_bytes + ws_need, st));
+  if (refine && c->fail_n < (size_t)n_plan_ligs) {
+    if (c->fail_host) {
+      CK(cudaStreamSynchronize(st));
+      CK(cudaFreeHost(c->fail_host));
+      c->fail_host = nullptr;
+      c->fail_n = 0;
+    }
+    CK(cudaMallocHost(&c->fail_host, sizeof(int) * n_plan_ligs));
+    c->fail_n = n_plan_ligs;
+  }
   // the pinned staging is rewritten: wait for the last copy or graph replay
   // that reads it, and drop the cached graph, whose copy node points at it
   if (!c->pinned_busy) CK(cudaEventCreateWithFlags(&c->pinned_busy, cudaEventDisableTiming));
@@ -1725,11 +1776,15 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   if (use_graph) CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
   try {
     char *tab = ws;
-    char *lw = ws + blob_bytes;
+    // refined form: one certificate flag per ligand of the call, then the
+    // per-ligand region
+    int *d_fail = reinterpret_cast<int *>(ws + blob_bytes);
+    char *lw = ws + blob_bytes + fail_bytes;
     if (blob_bytes) {
       CK(cudaMemcpyAsync(tab, c->pinned, blob.size(), cudaMemcpyHostToDevice, st));
       if (!use_graph) CK(cudaEventRecord(c->pinned_busy, st));
     }
+    if (refine) CK(cudaMemsetAsync(d_fail, 0, sizeof(int) * n_plan_ligs, st));
     long long conf_base = 0;
     for (int li = 0; li < lig_begin; ++li) conf_base += lg->n_conf[li];
     for (const LigPlan &pl : plans) {
@@ -1757,6 +1812,11 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         const OccTab *d_tabs = reinterpret_cast<const OccTab *>(tab + gp.off_occ);
         float4 *d_part = reinterpret_cast<float4 *>(d_grp);
         char *d_batch = d_grp + align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]);
+        float4 *d_part_ref = nullptr;  // refined form: [J][Kg][2] corrections
+        if (refine) {
+          d_part_ref = reinterpret_cast<float4 *>(d_batch);
+          d_batch += align_up(sizeof(float4) * 2 * (size_t)std::max(J, 1) * Kg);
+        }
         const bpmf_ctx::Tune tn = tune_for(c, g.P, mode);
         for (const BucketPlan &bk : gp.buckets) {
           if (!use_graph && bk.join) CK(cudaStreamWaitEvent(st, bk.join, 0));
@@ -1780,19 +1840,30 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
             gb.occ_cap = gp.occ_cap;
             gb.occ_rb = gp.occ_rb;
             gb.refine = refine;
+            gb.ref_cap = refine ? refine_cap(g.S) : 0;
             gb.nmax = lg->n_atoms[pl.li];
+            RefineCtx rf;
+            if (refine) {
+              rf.rtabs = d_rtabs;
+              for (int t = 0; t < 3; ++t) rf.gnorm[t] = pl.gnorm[t];
+              rf.kT = kT;
+              rf.part_ref = d_part_ref + 2 * (size_t)b0 * Kg;
+              rf.fail = d_fail + (pl.li - lig_begin);
+              rf.check_scale = c->refine_check_scale;
+            }
             if (use_ff)
               run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, d_rptr + Kg, h, nsh, nsl,
                             esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, false, d_tabs);
             else
               run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, nullptr, h, nsh, nsl,
                                esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, split, d_tabs,
-                               d_rtabs, pl.gnorm, kT);
+                               refine ? &rf : nullptr);
           }
         }
         if (export_E) continue;
         MergeArgs ma{};
         ma.part = d_part;
+        ma.part_ref = d_part_ref;
         ma.nvalid = d_nv;
         ma.order = reinterpret_cast<const int *>(tab + gp.off_order);
         ma.kmap = reinterpret_cast<const int *>(tab + gp.off_kmap);
@@ -1836,6 +1907,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       // the next ligand reuses the workspace; stream order keeps these copies first
       conf_base += lg->n_conf[pl.li];
     }
+    if (refine)
+      CK(cudaMemcpyAsync(c->fail_host, d_fail, sizeof(int) * n_plan_ligs, cudaMemcpyDeviceToHost, st));
   } catch (Fail f) {
     if (use_graph) {
       cudaGraph_t gr = nullptr;
@@ -1858,13 +1931,35 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   // the fork and join events are queued in every wait that uses them: reusable
   for (cudaEvent_t e : joins) c->event_pool.push_back(e);
   c->event_pool.push_back(fork);
-  if (host_out) CK(cudaStreamSynchronize(st));
+  if (refine) {  // the certificate flags: the ligands to recompute in float pairs
+    CK(cudaStreamSynchronize(st));
+    for (int li = lig_begin; li < lig_end; ++li)
+      if (c->fail_host[li - lig_begin] && fail_ligs) fail_ligs->push_back(li);
+  } else if (host_out) {
+    CK(cudaStreamSynchronize(st));
+  }
   return warn ? BPMF_WARN_NO_VALID : BPMF_OK;
 }
 
 }  // namespace
 
 namespace {
+// eval_impl plus the refined form's fallback: the ligands whose certificate
+// check failed (or whose candidate list overflowed) are evaluated again in
+// float pairs over the same outputs, and the result carries
+// BPMF_WARN_REFINE_FALLBACK.
+int eval_checked(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
+                 double *logZ, int64_t *n_valid, double *bpmf_out, double *dG, cudaStream_t st, int only_lig,
+                 int only_conf, double *export_E, double *Emin = nullptr, double *Dom = nullptr) {
+  std::vector<int> fails;
+  int rc = eval_impl(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, st, only_lig, only_conf, export_E, Emin,
+                     Dom, &fails);
+  for (int li : fails)
+    eval_impl(c, lg, recs, K, kT, BPMF_MODE_FF, logZ, n_valid, bpmf_out, dG, st, li, only_conf, export_E, Emin, Dom);
+  if (!fails.empty()) rc |= BPMF_WARN_REFINE_FALLBACK;
+  return rc;
+}
+
 int eval_entry(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode, double *logZ,
                int64_t *n_valid, double *bpmf_out, double *dG, double *psi_min, double *psi_dom, void *stream) {
   if (!c || !lg || !recs || K < 1 || !(kT > 0.0) || (!logZ && lg && lg->total_conf > 0))
@@ -1875,8 +1970,8 @@ int eval_entry(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, doubl
   DeviceGuard dg(c->device);
   try {
     last_msg.clear();
-    int rc = eval_impl(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, (cudaStream_t)stream, -1, -1, nullptr,
-                       psi_min, psi_dom);
+    int rc = eval_checked(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, (cudaStream_t)stream, -1, -1,
+                          nullptr, psi_min, psi_dom);
     c->err.clear();
     return rc;
   } catch (Fail f) {
@@ -2025,7 +2120,7 @@ int bpmf_export_energies(bpmf_ctx_t c, bpmf_lig_t lg, bpmf_rec_t rec, int lig_in
       CK(cudaMallocAsync(&d_out, n * sizeof(double), st));
     }
     bpmf_rec_t recs[1] = {rec};
-    eval_impl(c, lg, recs, 1, 1.0, mode, nullptr, nullptr, nullptr, nullptr, st, lig_index, conf_index, d_out);
+    eval_checked(c, lg, recs, 1, 1.0, mode, nullptr, nullptr, nullptr, nullptr, st, lig_index, conf_index, d_out);
     if (!dev) {
       CK(cudaMemcpyAsync(out, d_out, n * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaFreeAsync(d_out, st));
@@ -2079,7 +2174,7 @@ int bpmf_sir_poses(bpmf_ctx_t c, bpmf_lig_t lg, int lig_index, bpmf_rec_t rec, i
     js.erase(std::unique(js.begin(), js.end()), js.end());
     bpmf_rec_t recs[1] = {rec};
     for (int j : js) {
-      eval_impl(c, lg, recs, 1, 1.0, mode, nullptr, nullptr, nullptr, nullptr, st, lig_index, j, d_E);
+      eval_checked(c, lg, recs, 1, 1.0, mode, nullptr, nullptr, nullptr, nullptr, st, lig_index, j, d_E);
       launch(c, "k_sir_translations", st,
              [&] { return launch_sir_translations(d_E, nS, kT, u2, conf, j, M, d_cdf, pose, st); });
     }

@@ -174,22 +174,12 @@ __global__ void __launch_bounds__(256) k_spread(SpreadArgs a) {
   const ff h{a.h_hi, a.h_lo};
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     for (int d = 0; d < 3; ++d) {
-      const float x = a.coords[3ll * (m.atom_off + i) + d];
-      ff dx = two_sum(x, -m.lo[d]);  // exact x - lo
-      // g = dx / h + 2 in float-pair precision
-      const float q1 = __fdiv_rn(dx.hi, h.hi);
-      const float p = __fmul_rn(q1, h.hi);
-      const float pe = __fmaf_rn(q1, h.hi, -p);
-      float r = __fsub_rn(__fsub_rn(dx.hi, p), pe);
-      r = __fadd_rn(r, __fsub_rn(dx.lo, __fmul_rn(q1, h.lo)));
-      const float q2 = __fdiv_rn(r, h.hi);
-      ff g = s_norm(s_add(fast_two_sum(q1, q2), ff{2.f, 0.f}));
-      float c = floorf(g.hi);
-      if (g.hi == c && g.lo < 0.f) c -= 1.f;
-      ff f = two_sum(__fsub_rn(g.hi, c), g.lo);  // g.hi - c is exact
-      if (f.hi < 0.f) f = ff{0.f, 0.f};
-      if (f.hi > 1.f || (f.hi == 1.f && f.lo > 0.f)) f = ff{1.f, 0.f};
-      s_c[i][d] = (int)c;
+      // g = (x - lo) / h + 2 in float-pair precision, then its cell and fraction
+      const ff g = place_ff(a.coords[3ll * (m.atom_off + i) + d], m.lo[d], h);
+      int c;
+      ff f;
+      cell_ff(g, c, f);
+      s_c[i][d] = c;
       s_f[i][d] = f;
     }
   }
@@ -527,13 +517,18 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
     b0 = b1 + b1n;
     xs = reinterpret_cast<T *>(b0 + Lc * ls);
   }
+  // refined form: the FP32 energies of the chunk, after xs
+  float *es = reinterpret_cast<float *>(xs + 2 * Lc * a.S2);
   __shared__ T s_red[8];
   __shared__ float s_sum[8];
+  __shared__ float s_thr;
   load_tw(s_tw, a.tw, P);
   const int s0 = blockIdx.x % a.S0;
   const int jk = blockIdx.x / a.S0;  // j * K + k
   const PairInfo inf = a.info[jk];
   const bool row_ok = (s0 >= inf.sa[0] && s0 <= inf.sb[0]);
+  // refined form (FP32 only): candidate lists of the exact re-evaluation
+  const bool refine = std::is_same<T, float>::value && a.rs.cand != nullptr;
   if constexpr (NY > 0) {
     // y inverse of this CTA's plane in sub-passes of NY columns (the per-line
     // arithmetic of k_axis's two-stage plan, so the values are the same);
@@ -628,22 +623,19 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
         ok = !((w >> (s2 & 31)) & 1u);
       }
       T x = s_mk<T>(-CUDART_INF_F, 0.f);
+      float ef = CUDART_INF_F;
       if (ok) {
         const cx<T> z = res[(r >> 1) * ls + zi];
         const T val = (r & 1) ? z.im : z.re;
         x = s_norm(s_mul(val, nscale));
         if (ff_gt(x, vmax)) vmax = x;
-      }
-      xs[idx] = x;
-      if (a.Ebuf) {
-        float ef = CUDART_INF_F;
-        if (ok) {
-          const cx<T> z = res[(r >> 1) * ls + zi];
-          ef = s_hi(s_norm(s_mul((r & 1) ? z.im : z.re, escale)));
+        if (refine) {
+          ef = s_hi(s_norm(s_mul(val, escale)));
           emin = fminf(emin, ef);
         }
-        a.Ebuf[(((long long)blockIdx.x * a.S1) + s1) * a.S2 + s2] = ef;
       }
+      xs[idx] = x;
+      if (refine) es[idx] = ef;
       if (a.export_E && jk == 0) {
         double e = CUDART_INF;
         if (ok) {
@@ -654,16 +646,40 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
         a.export_E[((long long)s0 * a.S1 + s1) * a.S2 + s2] = e;
       }
     }
-    if (a.Ebuf) {  // plane minimum (s_sum doubles as scratch; it is rewritten below after a barrier)
+    if (refine) {
+      // the chunk's minimum lowers the pair's running minimum; translations
+      // within W + 2B of it are appended to the pair's list (warp-aggregated)
       for (int o = 16; o > 0; o >>= 1) emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
       if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = emin;
       __syncthreads();
       if (threadIdx.x == 0) {
         float v = s_sum[0];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fminf(v, s_sum[w]);
-        a.plane_min[blockIdx.x] = r0 == 0 ? v : fminf(a.plane_min[blockIdx.x], v);
+        float thr = -CUDART_INF_F;
+        if (v < CUDART_INF_F) {
+          const float run = fminf(ord2f(atomicMin(&a.rs.pmin[jk], f2ord(v))), v);
+          thr = __fadd_ru(run, a.rs.win[jk % a.K]);
+        }
+        s_thr = thr;
       }
       __syncthreads();
+      const float thr = s_thr;
+      const int lane = threadIdx.x & 31;
+      Cand *list = a.rs.cand + (long long)jk * a.rs.cap;
+      const unsigned t0 = (unsigned)((s0 * a.S1 + r0) * a.S2);
+      for (int b = (int)(threadIdx.x & ~31u); b < nS; b += blockDim.x) {
+        const int idx = b + lane;
+        const float ef = idx < nS ? es[idx] : CUDART_INF_F;
+        const bool keep = ef <= thr;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (bal) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&a.rs.cnt[jk], __popc(bal));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          const int slot = base + __popc(bal & ((1u << lane) - 1u));
+          if (keep && slot < a.rs.cap) list[slot] = Cand{t0 + (unsigned)idx, ef, s_hi(xs[idx])};
+        }
+      }
     }
     // block max of the chunk
     for (int o = 16; o > 0; o >>= 1) {
@@ -710,23 +726,24 @@ template <class T>
 size_t zinv_smem(const ZinvArgs &a, int Lc) {
   const int P = a.plan.n;
   const size_t b1n = std::max((size_t)Lc * (P + 1), (size_t)2 * Lc * a.F2);
-  return sizeof(float4) * P + sizeof(cx<T>) * ((size_t)Lc * (P + 1) + b1n) + sizeof(T) * (size_t)2 * Lc * a.S2;
+  const size_t es = a.rs.cand ? sizeof(float) * (size_t)2 * Lc * a.S2 : 0;  // refined form's FP32 energies
+  return sizeof(float4) * P + sizeof(cx<T>) * ((size_t)Lc * (P + 1) + b1n) + sizeof(T) * (size_t)2 * Lc * a.S2 + es;
 }
 
 // Fused y + z inverse (FP32): y sub-pass width for F2 columns (two sub-passes
 // of at most 21 or 25 lines), 0 when F2 is wider
 int zinv_ny(int F2) { return F2 <= 42 ? 21 : (F2 <= 50 ? 25 : 0); }
 
-size_t zinv_fused_smem(int P1, int P2, int S1, int S2) {
+size_t zinv_fused_smem(int P1, int P2, int S1, int S2, bool refine) {
   const int F2 = P2 / 2 + 1, Lc = (S1 + 1) / 2, NY = zinv_ny(F2);
   const size_t b1n = std::max((size_t)Lc * (P2 + 1), (size_t)2 * Lc * F2);
-  const size_t tail = std::max(sizeof(cx<float>) * Lc * (P2 + 1) + sizeof(float) * 2 * Lc * S2,
+  const size_t tail = std::max(sizeof(cx<float>) * Lc * (P2 + 1) + sizeof(float) * 2 * Lc * S2 * (refine ? 2 : 1),
                                sizeof(cx<float>) * 2 * P1 * NY);
   return sizeof(float4) * (P1 + P2) + sizeof(cx<float>) * b1n + tail;
 }
 
-bool zinv_fused_fits(int P1, int P2, int S1, int S2) {
-  return zinv_ny(P2 / 2 + 1) > 0 && S1 <= P1 && zinv_fused_smem(P1, P2, S1, S2) * 3 <= 227 * 1024;
+bool zinv_fused_fits(int P1, int P2, int S1, int S2, bool refine) {
+  return zinv_ny(P2 / 2 + 1) > 0 && S1 <= P1 && zinv_fused_smem(P1, P2, S1, S2, refine) * 3 <= 227 * 1024;
 }
 
 template <class T, int NY>
@@ -745,9 +762,11 @@ cudaError_t launch_zinv(const ZinvArgs &a_in, int batch, cudaStream_t st) {
   if (a.x2) {  // fused y + z inverse: FP32 only, the whole window in one chunk
     if constexpr (std::is_same<T, float>::value) {
       const int P1 = a.yplan.n;
-      if (!zinv_fused_fits(P1, a.plan.n, a.S1, a.S2) || a.F2 != a.plan.n / 2 + 1) return cudaErrorInvalidValue;
+      const bool refine = a.rs.cand != nullptr;
+      if (!zinv_fused_fits(P1, a.plan.n, a.S1, a.S2, refine) || a.F2 != a.plan.n / 2 + 1)
+        return cudaErrorInvalidValue;
       a.Lc = L;
-      const size_t smem = zinv_fused_smem(P1, a.plan.n, a.S1, a.S2);
+      const size_t smem = zinv_fused_smem(P1, a.plan.n, a.S1, a.S2, refine);
       return zinv_ny(a.F2) == 21 ? launch_zinv_k<float, 21>(a, smem, batch, st)
                                  : launch_zinv_k<float, 25>(a, smem, batch, st);
     }
@@ -779,10 +798,31 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
   double Mx = -CUDART_INF;
   for (int c = 0; c < a.S0; ++c)
     if (pp[c].z > 0.f) Mx = fmax(Mx, (double)pp[c].x + (double)pp[c].y);
+  // refined form: the pair's correction replaces the FP32 weights of its
+  // refined translations (held by the plane partials) by their exact weights
+  double X = -CUDART_INF;  // largest exact -E/kT
+  float4 rc{0.f, 0.f, 0.f, 0.f};
+  if (a.part_ref) {
+    rc = a.part_ref[2ll * p];
+    const float4 rx = a.part_ref[2ll * p + 1];
+    if (rc.z > 0.f) {
+      X = (double)rx.x + (double)rx.y;
+      Mx = fmax(Mx, (double)rc.x + (double)rc.y);
+    }
+  }
   double s = 0.0;
-  if (Mx > -CUDART_INF)
+  if (Mx > -CUDART_INF) {
     for (int c = 0; c < a.S0; ++c)
       if (pp[c].z > 0.f) s += (double)pp[c].z * exp((double)pp[c].x + (double)pp[c].y - Mx);
+    if (rc.z > 0.f) {
+      const double e = exp((double)rc.x + (double)rc.y - Mx);
+      const double se = (double)rc.z * e;
+      s = s - (double)rc.w * e + se;
+      if (s < se) s = se;  // the translations left at FP32 weigh >= 0 (rounding guard)
+    }
+  }
+  // the dominant state: the largest -E/kT, exact where the pair was refined
+  const double Xd = X > -CUDART_INF ? X : Mx;
   // processing position -> caller's configuration order
   const long long q = (long long)(a.order ? a.order[j] : j) * a.K + k;
   const long long n = a.nvalid[q];
@@ -791,7 +831,7 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
   a.logZ[q] = n > 0 ? ls - log((double)n) : -CUDART_INF;
   if (a.nvalid_out) a.nvalid_out[q] = n;
   // dominant-state energy: the largest -E/kT of all partials, back to kcal/mol
-  if (a.emin) a.emin[q] = (Mx > -CUDART_INF && n > 0) ? -a.kT * Mx : CUDART_INF;
+  if (a.emin) a.emin[q] = (Xd > -CUDART_INF && n > 0) ? -a.kT * Xd : CUDART_INF;
 }
 
 __global__ void __launch_bounds__(256) k_merge(MergeArgs a) {
@@ -907,48 +947,33 @@ cudaError_t launch_split_ff(const void *spec, float2 *hi, float2 *lo, long long 
 // --------------------------------------------------------------------------
 // The receptor grids cropped to the box [c0, c0 + e) and zero-padded to the
 // extents E >= e (CTA row blockIdx.y = channel t):
-//   out[t][i][j][l] = grid[t][c0_0 + i][c0_1 + j][c0_2 + l] (i, j, l < e), else 0,
-// and the sum of squares of each cropped channel (FP32 error bound).  CTA
-// column blockIdx.x walks (i, j) rows; threads walk l.
+//   out[t][i][j][l] = grid[t][c0_0 + i][c0_1 + j][c0_2 + l] (i, j, l < e), else 0.
+// CTA column blockIdx.x walks (i, j) rows; threads walk l.
 __global__ void __launch_bounds__(256) k_crop(const float *grid, int N0, int N1, int N2, int c00, int c01, int c02,
-                                              int e0, int e1, int e2, int E0, int E1, int E2, float *out,
-                                              double *sumsq) {
-  __shared__ double s_d[8];
+                                              int e0, int e1, int e2, int E0, int E1, int E2, float *out) {
   const int t = blockIdx.y;
-  double acc = 0.0;
   for (int row = blockIdx.x; row < E0 * E1; row += gridDim.x) {
     const int ix = row / E1, jy = row % E1;
     float *dst = out + (((long long)t * E0 + ix) * E1 + jy) * E2;
     const bool in = ix < e0 && jy < e1;
     const float *src = grid + (((long long)t * N0 + c00 + ix) * N1 + c01 + jy) * N2 + c02;
-    for (int l = threadIdx.x; l < E2; l += blockDim.x) {
-      const float v = (in && l < e2) ? src[l] : 0.f;
-      dst[l] = v;
-      acc += (double)v * v;
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) s_d[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_d[w];
-    atomicAdd(sumsq + t, v);
+    for (int l = threadIdx.x; l < E2; l += blockDim.x) dst[l] = (in && l < e2) ? src[l] : 0.f;
   }
 }
 
 cudaError_t launch_crop(const float *grid, const int N[3], const int c0[3], const int e[3], const int E[3],
-                        float *out, double *sumsq, cudaStream_t st) {
+                        float *out, float *sumsq, float2 *scratch, cudaStream_t st) {
   for (int d = 0; d < 3; ++d)
     if (c0[d] < 0 || e[d] < 1 || c0[d] + e[d] > N[d] || E[d] < e[d]) return cudaErrorInvalidValue;
-  cudaError_t err = cudaMemsetAsync(sumsq, 0, 3 * sizeof(double), st);
-  if (err != cudaSuccess) return err;
   const int rows = E[0] * E[1];
   const int blocks = std::min(rows, sm_count() * 4);
   const int threads = E[2] >= 128 ? 128 : (E[2] >= 64 ? 64 : 32);
   k_crop<<<dim3(blocks, 3), threads, 0, st>>>(grid, N[0], N[1], N[2], c0[0], c0[1], c0[2], e[0], e[1], e[2], E[0],
-                                              E[1], E[2], out, sumsq);
-  return cudaGetLastError();
+                                              E[1], E[2], out);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  // the padding adds zeros: the sums of squares of the padded crop are the crop's
+  return launch_sumsq(out, (long long)E[0] * E[1] * E[2], sumsq, scratch, st);
 }
 
 // explicit instantiations

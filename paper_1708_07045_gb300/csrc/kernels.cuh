@@ -146,6 +146,72 @@ struct ClashArgs {
   uint32_t *clash;         // [batch][K][S0][S1][CW], bit s2: translation clashes
 };
 
+// ---- refined form (refine.cu) -----------------------------------------------
+struct RefTab {            // one receptor's grids, FP32 [3][N0][N1][N2]
+  const float *grid;
+  const float *sumsq;      // [3] sum of squares of each grid over the transformed (cropped) nodes
+  int N0, N1, N2;
+  float vol;               // transformed nodes per channel (FP32 error bound: rms = sqrt(sumsq / vol))
+};
+
+// A translation kept for the exact re-evaluation: window index
+// t = (s0 S1 + s1) S2 + s2, its FP32 energy e and the FP32 -E/kT value x whose
+// weight exp(x - M) the plane's LSE partial holds.
+struct Cand {
+  unsigned t;
+  float e, x;
+};
+
+// Running per-pair state of one batch of the refined form.  k_refine_init
+// resets it; every k_zinv CTA lowers the pair's running FP32 minimum and
+// appends the translations of its plane that lie within the window of that
+// running minimum (a superset of those within the window of the final
+// minimum), while its LSE partial keeps every translation at its FP32
+// weight; k_refine reads the final minimum and the lists and writes the
+// exact-minus-FP32 correction of each pair's sum, which the merge applies.
+struct RefineState {
+  const float *win;        // [K] W + 2B per receptor (kcal/mol)
+  const float *bnd;        // [K] B per receptor times the check scale (certificate threshold)
+  unsigned *pmin;          // [batch][K] running minimum energy, order-preserving unsigned encoding
+  int *cnt;                // [batch][K] translations appended (may exceed cap: overflow)
+  Cand *cand;              // [batch][K][cap]
+  float2 *exact;           // [batch][K][cap] k_refine: exact -E/kT (float pair) of the refined entries
+  int cap;
+  int *fail;               // set to 1 when a list overflows or a certificate check fails
+};
+
+// Order-preserving encoding of a float as an unsigned (larger float, larger
+// code), so that atomicMin on the code keeps the minimum float.
+__device__ __forceinline__ unsigned f2ord(float f) {
+  const unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+constexpr int kRefineMaxList = 1 << 22;  // translations per pair list (fixed-point sum range)
+
+struct RefineArgs {
+  RefineState rs;
+  float *win, *bnd;        // writable views of rs.win / rs.bnd (k_refine_init)
+  const ConfMeta *meta;    // [batch]
+  const PairInfo *info;    // [batch][K]
+  const RefTab *tabs;      // [K]
+  float gnorm[3];          // ||gamma_t||_2 of the ligand (FP32 error bound)
+  float log2P3;            // log2(P0 P1 P2) of the transforms
+  float check_scale;       // multiplies B in the certificate check (1 in normal use)
+  const float *coords;     // [atoms][3]
+  const float2 *gamma;     // [3][gamma_stride] generalised charges as float pairs
+  int gamma_stride;
+  float h_hi, h_lo;        // grid spacing as a float pair
+  float kT;                // kcal/mol
+  float nikT_hi, nikT_lo;  // -1 / kT as a float pair
+  int K, S0, S1, S2;
+  float4 *part_ref;        // [batch][K][2] per pair: {level M hi, lo, sum of exact weights, sum of FP32
+                           // weights} over the refined translations, then {max exact -E/kT hi, lo, 0, 0}
+  double *export_E;        // optional, batch entry 0, receptor 0: [S0][S1][S2] (exact where refined)
+};
+
 struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp partials
   const void *y2;          // [batch][K][S0][S1][F2] cx<T>
   int K, S0, S1, S2, F2;
@@ -157,8 +223,7 @@ struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp pa
   const uint32_t *clash;   // optional [batch][K][S0][S1][CW] clash flags (excluded, +inf when exported)
   int CW;
   int Lc;                  // row pairs per shared-memory chunk (set by launch_zinv)
-  float *Ebuf;             // optional [batch][K][S0][S1][S2] energies (+inf masked), refined form
-  float *plane_min;        // with Ebuf: [batch][K][S0] minimum energy of each s0 plane
+  RefineState rs;          // refined form (FP32 only): candidate lists; rs.cand null otherwise
   FftPlan plan;
   const float4 *tw;
   // FP32 forms: the y inverse fused in front (y2 unused) when x2 is set: each
@@ -172,6 +237,7 @@ struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp pa
 
 struct MergeArgs {
   const float4 *part;      // [J][Kg][S0] of one receptor group, processing order
+  const float4 *part_ref;  // [J][Kg][2] refined form: each pair's correction (RefineArgs::part_ref), or null
   const long long *nvalid; // [J][K], caller's order, all receptors
   const int *order;        // [J] processing position -> caller's configuration index (null: identity)
   const int *kmap;         // [Kg] group-local receptor -> receptor index in the call (null: identity)
@@ -189,35 +255,6 @@ struct MergeArgs {
                            // receptors, and -kT ln mean_k exp(-min_k / kT) (may be null)
 };
 
-// ---- refined form (refine.cu) -----------------------------------------------
-struct RefTab {            // one receptor's grids, FP32 [3][N0][N1][N2]
-  const float *grid;
-  const double *sumsq;     // [3] sum of squares of each grid over the transformed (cropped) nodes
-  int N0, N1, N2;
-  double vol;              // transformed nodes per channel (FP32 error bound: rms = sqrt(sumsq / vol))
-};
-
-struct RefineArgs {
-  const float *E;          // [batch][K][S0][S1][S2] FP32 energies (+inf masked)
-  const float *plane_min;  // [batch][K][S0]
-  const ConfMeta *meta;    // [batch]
-  const PairInfo *info;    // [batch][K]
-  const RefTab *tabs;      // [K]
-  double gnorm[3];         // ||gamma_t||_2 of the ligand (FP32 error bound)
-  double log2P3;           // log2(P0 P1 P2) of the group
-  const float *coords;     // [atoms][3]
-  const double *gamma64;   // [3][gamma_stride] FP64 generalised charges
-  int gamma_stride;
-  double h, kT;
-  float ikT;               // 1 / kT in FP32 (weights outside the window)
-  double *window;          // [K] scratch: W + 2B per receptor (k_window)
-  float *pmin_pair;        // [batch][K] scratch: FP32 minimum per pair
-  float *thresh;           // [batch][K] scratch: threshold per pair
-  int K, S0, S1, S2;
-  float4 *part;            // [batch][K][S0] LSE partials (planes with candidates rewritten)
-  double *export_E;        // optional, batch entry 0, receptor 0: [S0][S1][S2] (exact where refined)
-};
-
 int sm_count();                      // streaming multiprocessors of the current device (kernels.cu)
 
 // ---- host plan helpers (bpmf_api.cu), shared by every entry point ----------
@@ -229,12 +266,14 @@ int box_extent(float lo, float hi, float hf);  // ligand-box edge in nodes (sing
 long long site_window(int N, int site_lo, int site_n, int u, int &w0, int &sa, int &sb);
 
 // ---- launch wrappers (kernels.cu, ligspec.cu, occupancy.cu, refine.cu) ---------
-cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st);
-cudaError_t launch_gamma64(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, double *g,
-                           cudaStream_t st);
-cudaError_t launch_sumsq(const float *g, long long vol, double *out, cudaStream_t st);
+cudaError_t launch_refine_init(const RefineArgs &a, int batch, cudaStream_t st);  // before k_zinv
+cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st);       // after k_zinv
+// sums of squares of the three grids [3][vol] into out[3] (deterministic;
+// scratch: kSumsqScratch float2 of device memory)
+constexpr int kSumsqScratch = 3 * 256;
+cudaError_t launch_sumsq(const float *g, long long vol, float *out, float2 *scratch, cudaStream_t st);
 cudaError_t launch_crop(const float *grid, const int N[3], const int c0[3], const int e[3], const int E[3],
-                        float *out, double *sumsq, cudaStream_t st);
+                        float *out, float *sumsq, float2 *scratch, cudaStream_t st);
 cudaError_t launch_occ_table(const unsigned char *occ, int N0, int N1, int N2, int W, uint32_t *tab,
                              cudaStream_t st);
 cudaError_t launch_occ_runs(const OccRunsArgs &a, int batch, cudaStream_t st);
@@ -247,7 +286,7 @@ template <class T> cudaError_t launch_xfused(const XfusedArgs &a, int batch, cud
 template <class T> cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st);
 // whether the FP32 z inverse can take the y inverse in front (whole site
 // window in one shared-memory chunk at 3 CTAs per SM)
-bool zinv_fused_fits(int P1, int P2, int S1, int S2);
+bool zinv_fused_fits(int P1, int P2, int S1, int S2, bool refine);
 cudaError_t launch_merge_pairs(const MergeArgs &a, cudaStream_t st);  // per receptor group
 cudaError_t launch_merge(const MergeArgs &a, cudaStream_t st);        // B_k and dG over all receptors
 cudaError_t launch_split_ff(const void *spec, float2 *hi, float2 *lo, long long n, cudaStream_t st);

@@ -41,22 +41,11 @@ __global__ void __launch_bounds__(256) k_ligspec(LigSpecArgs a) {
   // placement in float pairs, as the spreading kernel does it
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     for (int d = 0; d < 3; ++d) {
-      const float x = a.coords[3ll * (m.atom_off + i) + d];
-      ff dx = two_sum(x, -m.lo[d]);
-      const float q1 = __fdiv_rn(dx.hi, h.hi);
-      const float p = __fmul_rn(q1, h.hi);
-      const float pe = __fmaf_rn(q1, h.hi, -p);
-      float r = __fsub_rn(__fsub_rn(dx.hi, p), pe);
-      r = __fadd_rn(r, __fsub_rn(dx.lo, __fmul_rn(q1, h.lo)));
-      const float q2 = __fdiv_rn(r, h.hi);
-      ff g = s_norm(s_add(fast_two_sum(q1, q2), ff{2.f, 0.f}));
-      float c = floorf(g.hi);
-      if (g.hi == c && g.lo < 0.f) c -= 1.f;
-      ff f = two_sum(__fsub_rn(g.hi, c), g.lo);
-      float fv = __fadd_rn(f.hi, f.lo);
-      fv = fminf(fmaxf(fv, 0.f), 1.f);
-      s_c[i][d] = (int)c;
-      s_f[i][d] = fv;
+      int c;
+      ff f;
+      cell_ff(place_ff(a.coords[3ll * (m.atom_off + i) + d], m.lo[d], h), c, f);
+      s_c[i][d] = c;
+      s_f[i][d] = fminf(fmaxf(__fadd_rn(f.hi, f.lo), 0.f), 1.f);
     }
   }
   __syncthreads();

@@ -1,24 +1,36 @@
 // Refined form (BPMF_MODE_REFINE): the FP32 correlation gives every
-// translation's energy with an error below a bound B (8 eps sqrt(log2 P^3)
-// sum_t rms(G_t) ||gamma_t||); only translations whose FP32 energy lies
+// translation's energy with an error that stays below a bound B
+// (8 eps32 sqrt(log2 P^3) sum_t rms(G_t) ||gamma_t||, the typical roundoff
+// growth of an FFT correlation); only translations whose FP32 energy lies
 // within W + 2B of the configuration's FP32 minimum can carry a weight above
 // e^(-W/kT) of the largest, so only they are re-evaluated exactly: the direct
 // sum the FFT correlation equals (trilinear interpolation of each receptor
 // grid at every atom, Eqs. general_form / receptor_grid / correlation_func),
-// in FP64.  The window W = kT max(20, ln(1e5 n)) (n translations in the site
-// window) keeps the weight of the translations left at their FP32 values
+// in float-pair arithmetic built from FP32 instructions (about 2^-44
+// relative).  The window W = kT max(20, ln(1e5 n)) (n translations in the
+// site window) keeps the weight of the translations left at their FP32 values
 // below 1e-5 of S.
 //
-// k_window (W + 2B per receptor), k_threshold (per pair: T = FP32 minimum +
-// W + 2B), then k_refine, one CTA per (configuration, receptor, s0 plane);
-// planes whose minimum lies above T keep the FP32 partial of k_zinv (all
-// their weights lie below e^(-W/kT) of the largest), the others:
-//   * every FP32 energy <= T is a candidate; a warp evaluates its
-//     candidates together (lanes over atoms, FP64, shuffle reduction);
-//   * S = sum over candidates of exp(-E_exact/kT) + sum over the others of
-//     exp(-E_fp32/kT), max-shifted, written as the plane's LSE partial (the
-//     merge is unchanged), and the exported energies (exact where refined)
-//     when asked.
+// Per batch:
+//   k_refine_init  -- W + 2B and B per receptor; reset each pair's running
+//                     minimum and candidate count;
+//   k_zinv         -- (kernels.cu) each plane lowers its pair's running
+//                     minimum and appends the translations within W + 2B of
+//                     it to the pair's list (a superset of those within
+//                     W + 2B of the final minimum); its LSE partial keeps
+//                     every translation at its FP32 weight;
+//   k_refine       -- one CTA per pair: the final threshold from the final
+//                     minimum; every listed translation below it is
+//                     re-evaluated exactly (a warp per translation, lanes
+//                     over atoms) and checked against its FP32 energy
+//                     (|E_fp32 - E_exact| <= B, the certificate); the pair's
+//                     correction {level, sum of exact weights, sum of the
+//                     same translations' FP32 weights} goes to the merge,
+//                     which replaces the one by the other.
+// Both sums are over the same translations, fixed by the final threshold,
+// in order-independent fixed point, so results do not depend on the order in
+// which the planes ran.  A failed check or an overflowing list sets a flag
+// that makes bpmf_eval recompute the ligand in float pairs.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -26,215 +38,251 @@
 
 namespace bpmf {
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// W + 2B and B of every receptor, and the per-pair reset (one thread each).
+__global__ void k_refine_init(RefineArgs a, int n_pairs, float nS) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_pairs) {
+    a.rs.pmin[i] = f2ord(CUDART_INF_F);
+    a.rs.cnt[i] = 0;
+  }
+  if (i < a.K) {
+    const RefTab t = a.tabs[i];
+    const float B = 8.f * 5.9604644775390625e-08f * sqrtf(a.log2P3) *
+                    (sqrtf(t.sumsq[0] / t.vol) * a.gnorm[0] + sqrtf(t.sumsq[1] / t.vol) * a.gnorm[1] +
+                     sqrtf(t.sumsq[2] / t.vol) * a.gnorm[2]);
+    a.win[i] = a.kT * fmaxf(20.f, logf(1e5f * nS)) + 2.f * B;
+    a.bnd[i] = B * a.check_scale;
+  }
 }
 
-// FP64 trilinear interpolation of one grid at p (grid units); a position on
-// the last node uses the cell below it.
-__device__ __forceinline__ double trilinear64(const float *G, int N0, int N1, int N2, double px, double py,
-                                              double pz) {
-  const int cx = min(max((int)floor(px), 0), N0 - 2), cy = min(max((int)floor(py), 0), N1 - 2),
-            cz = min(max((int)floor(pz), 0), N2 - 2);
-  const double fx = px - cx, fy = py - cy, fz = pz - cz;
-  const long long sy = N2, sx = (long long)N1 * N2;
-  const float *g = G + cx * sx + cy * sy + cz;
-  const double c00 = (double)g[0] * (1.0 - fz) + (double)g[1] * fz;
-  const double c01 = (double)g[sy] * (1.0 - fz) + (double)g[sy + 1] * fz;
-  const double c10 = (double)g[sx] * (1.0 - fz) + (double)g[sx + 1] * fz;
-  const double c11 = (double)g[sx + sy] * (1.0 - fz) + (double)g[sx + sy + 1] * fz;
-  const double c0 = c00 * (1.0 - fy) + c01 * fy, c1 = c10 * (1.0 - fy) + c11 * fy;
-  return c0 * (1.0 - fx) + c1 * fx;
+cudaError_t launch_refine_init(const RefineArgs &a, int batch, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  const int n_pairs = batch * a.K;
+  const int n = n_pairs > a.K ? n_pairs : a.K;
+  k_refine_init<<<(n + 127) / 128, 128, 0, st>>>(a, n_pairs, (float)a.S0 * a.S1 * a.S2);
+  return cudaGetLastError();
 }
+
+__device__ __forceinline__ ff lerp_ff(ff a, ff b, ff w0, ff w1) { return s_add(s_mul(a, w0), s_mul(b, w1)); }
+
+// Float-pair trilinear interpolation of one FP32 grid: cell (cx, cy, cz),
+// fractions f (weights 1 - f, f per axis), as nested linear interpolations
+// along z, then y, then x.
+__device__ __forceinline__ ff trilinear_ff(const float *g, long long sx, long long sy, const ff w[3][2]) {
+  const ff c00 = s_norm(lerp_ff(ff{g[0], 0.f}, ff{g[1], 0.f}, w[2][0], w[2][1]));
+  const ff c01 = s_norm(lerp_ff(ff{g[sy], 0.f}, ff{g[sy + 1], 0.f}, w[2][0], w[2][1]));
+  const ff c10 = s_norm(lerp_ff(ff{g[sx], 0.f}, ff{g[sx + 1], 0.f}, w[2][0], w[2][1]));
+  const ff c11 = s_norm(lerp_ff(ff{g[sx + sy], 0.f}, ff{g[sx + sy + 1], 0.f}, w[2][0], w[2][1]));
+  const ff c0 = s_norm(lerp_ff(c00, c01, w[1][0], w[1][1]));
+  const ff c1 = s_norm(lerp_ff(c10, c11, w[1][0], w[1][1]));
+  return s_norm(lerp_ff(c0, c1, w[0][0], w[0][1]));
+}
+
+__device__ __forceinline__ float d_ff(ff a, ff b) {  // a - b, rounded to FP32
+  return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+}
+
+__device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+
+// Weights are summed in 64-bit fixed point (scale 2^40 relative to the
+// pair's level, every weight <= 1): integer adds are exact and
+// order-independent, so the result does not depend on the order in which
+// k_zinv appended the translations.
+constexpr double kFixScale = 1099511627776.0;  // 2^40 (lists of up to 2^22 translations)
 
 __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
-  __shared__ double s_g[3][256];    // atom positions in the ligand-box frame (grid units), FP64
-  __shared__ double s_gam[3][256];  // gamma_t,i, FP64
-  __shared__ double s_mx[8], s_sm[8];
-  __shared__ float s_non[8];
-  const int s0 = blockIdx.x % a.S0;
-  const int pair = blockIdx.x / a.S0;  // j * K + k
+  __shared__ ff s_g[3][256];    // atom positions in the ligand-box frame (grid units)
+  __shared__ ff s_gam[3][256];  // gamma_t,i
+  __shared__ float s_red[8][2];
+  __shared__ float s_redx[8][2];
+  __shared__ unsigned long long s_we, s_wf;
+  const int pair = blockIdx.x;  // j * K + k
   const int j = pair / a.K, k = pair % a.K;
-  // the pair's threshold (k_threshold): a plane whose FP32 minimum lies above
-  // it has no candidate, and the FP32 partial k_zinv wrote for it stands
-  const float Tf = a.thresh[pair];
-  const float *pm = a.plane_min + (long long)pair * a.S0;
-  if (!(pm[s0] <= Tf)) return;
+  const int n_list = min(a.rs.cnt[pair], a.rs.cap);
+  if (threadIdx.x == 0) {
+    s_we = 0ull;
+    s_wf = 0ull;
+    if (a.rs.cnt[pair] > a.rs.cap) atomicOr(a.rs.fail, 1);  // list overflow
+  }
+  const float Emin = ord2f(a.rs.pmin[pair]);
+  // the final threshold (k_zinv listed against thresholds at least as high)
+  const float T = __fadd_ru(Emin, a.rs.win[k]);
+  const float B = a.rs.bnd[k];
   const ConfMeta m = a.meta[j];
   const PairInfo inf = a.info[pair];
-  const RefTab t = a.tabs[k];
+  const RefTab tb = a.tabs[k];
   const int n = m.n_atoms;
-  const float Mf = a.pmin_pair[pair];
-  const double M = (double)Mf;
-  const double kT = a.kT;
-  {
-    const double h = a.h;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const float *x = a.coords + 3ll * (m.atom_off + i);
-      for (int d = 0; d < 3; ++d) s_g[d][i] = ((double)x[d] - (double)m.lo[d]) / h + 2.0;
-      for (int c = 0; c < 3; ++c) s_gam[c][i] = a.gamma64[(long long)c * a.gamma_stride + m.gamma_off + i];
+  const ff h{a.h_hi, a.h_lo};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int d = 0; d < 3; ++d) s_g[d][i] = place_ff(a.coords[3ll * (m.atom_off + i) + d], m.lo[d], h);
+    for (int c = 0; c < 3; ++c) {
+      const float2 g = a.gamma[(long long)c * a.gamma_stride + m.gamma_off + i];
+      s_gam[c][i] = ff{g.x, g.y};
     }
-    __syncthreads();
   }
-  const int nP = a.S1 * a.S2;
-  const float *E = a.E + (long long)blockIdx.x * nP;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double mx = -CUDART_INF, sm = 0.0;  // exact candidates, max-shifted (per warp, identical on its lanes)
-  // the others, relative to exp(-M / kT), per thread: each lies below
-  // e^(-W/kT) of the largest weight, so single precision is ample for them
-  float non_f = 0.f;
-  const float ikT = a.ikT;
-  double *expo = (a.export_E && pair == 0) ? a.export_E + (long long)s0 * nP : nullptr;
-  if (Mf < CUDART_INF_F) {
-    for (int b0 = warp * 32; b0 < nP; b0 += blockDim.x) {
-      const int idx = b0 + lane;
-      const float e = idx < nP ? E[idx] : CUDART_INF_F;
-      const bool fin = e < CUDART_INF_F;
-      const bool cand = fin && e <= Tf;
-      if (fin && !cand) non_f += __expf(-(e - Mf) * ikT);
-      if (expo && idx < nP && !cand) expo[idx] = fin ? (double)e : CUDART_INF;
-      unsigned bal = __ballot_sync(0xffffffffu, cand);
-      while (bal) {
-        const int src = __ffs(bal) - 1;
-        bal &= bal - 1;
-        const int ci = b0 + src;
-        const int s2 = ci % a.S2, s1 = ci / a.S2;
-        const double m0 = inf.w0[0] + s0, m1 = inf.w0[1] + s1, m2 = inf.w0[2] + s2;
-        double part = 0.0;
-        for (int i = lane; i < n; i += 32) {
-          const double px = s_g[0][i] + m0, py = s_g[1][i] + m1, pz = s_g[2][i] + m2;
-          for (int c = 0; c < 3; ++c)
-            part += s_gam[c][i] *
-                    trilinear64(t.grid + (long long)c * t.N0 * t.N1 * t.N2, t.N0, t.N1, t.N2, px, py, pz);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const ff nikT{a.nikT_hi, a.nikT_lo};
+  const long long vol = (long long)tb.N0 * tb.N1 * tb.N2;
+  const long long sx = (long long)tb.N1 * tb.N2, sy = tb.N2;
+  const Cand *list = a.rs.cand + (long long)pair * a.rs.cap;
+  float2 *ex = a.rs.exact + (long long)pair * a.rs.cap;
+  double *expo = (a.export_E && pair == 0) ? a.export_E : nullptr;
+  // pass 1: exact -E/kT of every translation below the final threshold (a
+  // warp per translation, lanes over atoms), the certificate check, and the
+  // largest exact and FP32 -E/kT among them
+  ff Xe{-CUDART_INF_F, 0.f};  // max exact
+  float Xf = -CUDART_INF_F;    // max FP32
+  bool bad = false;
+  for (int b0 = warp * 32; b0 < n_list; b0 += nwarp * 32) {
+    const int idx = b0 + lane;
+    Cand cd{0u, CUDART_INF_F, -CUDART_INF_F};
+    if (idx < n_list) cd = list[idx];
+    const bool cand = idx < n_list && cd.e <= T;
+    unsigned bal = __ballot_sync(0xffffffffu, cand);
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const unsigned t = __shfl_sync(0xffffffffu, cd.t, src);
+      const float ef = __shfl_sync(0xffffffffu, cd.e, src);
+      const float xf = __shfl_sync(0xffffffffu, cd.x, src);
+      const int s2 = (int)(t % (unsigned)a.S2), s01 = (int)(t / (unsigned)a.S2);
+      const int s1 = s01 % a.S1, s0 = s01 / a.S1;
+      const int mt[3] = {inf.w0[0] + s0, inf.w0[1] + s1, inf.w0[2] + s2};
+      ff part{0.f, 0.f};
+      for (int i = lane; i < n; i += 32) {
+        int c[3];
+        ff w[3][2];
+        for (int d = 0; d < 3; ++d) {
+          const ff p = s_norm(s_add(s_g[d][i], ff{(float)mt[d], 0.f}));
+          ff f;
+          cell_ff(p, c[d], f);
+          const int Nd = d == 0 ? tb.N0 : (d == 1 ? tb.N1 : tb.N2);
+          if (c[d] > Nd - 2) {  // a position on the last node uses the cell below it
+            f = s_norm(s_add(f, ff{(float)(c[d] - (Nd - 2)), 0.f}));
+            c[d] = Nd - 2;
+          }
+          if (c[d] < 0) {
+            f = s_norm(s_add(f, ff{(float)c[d], 0.f}));
+            c[d] = 0;
+          }
+          w[d][0] = s_norm(s_sub(ff{1.f, 0.f}, f));
+          w[d][1] = f;
         }
-        const double ex = warp_sum_d(part);
-        const double v = -ex / kT;
-        if (v > mx) {
-          sm = sm * exp(mx - v) + 1.0;
-          mx = v;
-        } else {
-          sm += exp(v - mx);
-        }
-        if (expo && lane == 0) expo[ci] = ex;
+        const float *g0 = tb.grid + c[0] * sx + c[1] * sy + c[2];
+        for (int ch = 0; ch < 3; ++ch)
+          part = s_norm(s_add(part, s_mul(s_gam[ch][i], trilinear_ff(g0 + ch * vol, sx, sy, w))));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const ff other{__shfl_xor_sync(0xffffffffu, part.hi, o), __shfl_xor_sync(0xffffffffu, part.lo, o)};
+        part = s_norm(s_add(part, other));
+      }
+      // the certificate: the FP32 energy lies within B of the exact one
+      if (fabsf(d_ff(ff{ef, 0.f}, part)) > B) bad = true;
+      const ff x = s_norm(s_mul(part, nikT));
+      if (ff_gt(x, Xe)) Xe = x;
+      Xf = fmaxf(Xf, xf);
+      if (lane == src) {
+        ex[idx] = make_float2(x.hi, x.lo);
+        if (expo) expo[t] = (double)part.hi + (double)part.lo;
       }
     }
   }
-  // CTA: combine the warps' exact sums and the threads' FP32 remainders into
-  // this plane's LSE partial {level hi, level lo, sum relative to the level}
-  for (int o = 16; o > 0; o >>= 1) non_f += __shfl_xor_sync(0xffffffffu, non_f, o);
-  const float non = non_f;
-  if (lane == 0) {
-    s_mx[warp] = mx;
-    s_sm[warp] = sm;
-    s_non[warp] = non;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.rs.fail, 1);
+  for (int o = 16; o > 0; o >>= 1) {
+    const ff o2{__shfl_xor_sync(0xffffffffu, Xe.hi, o), __shfl_xor_sync(0xffffffffu, Xe.lo, o)};
+    if (ff_gt(o2, Xe)) Xe = o2;
+    Xf = fmaxf(Xf, __shfl_xor_sync(0xffffffffu, Xf, o));
   }
+  if (lane == 0) {
+    s_redx[warp][0] = Xe.hi;
+    s_redx[warp][1] = Xe.lo;
+    s_red[warp][0] = Xf;
+  }
+  __syncthreads();  // also publishes the exact values written to the list
+  for (int w = 0; w < nwarp; ++w) {
+    const ff o2{s_redx[w][0], s_redx[w][1]};
+    if (ff_gt(o2, Xe)) Xe = o2;
+    Xf = fmaxf(Xf, s_red[w][0]);
+  }
+  if (!(Xe.hi > -CUDART_INF_F)) {  // no translation below the threshold (no valid translation)
+    if (threadIdx.x == 0) {
+      a.part_ref[2 * pair] = make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
+      a.part_ref[2 * pair + 1] = make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
+    }
+    return;
+  }
+  // level: the largest of the exact and the FP32 values, so every weight <= 1
+  const ff L = ff_gt(ff{Xf, 0.f}, Xe) ? ff{Xf, 0.f} : Xe;
+  // pass 2: the exact and the FP32 weights of the same translations
+  unsigned long long we = 0ull, wf = 0ull;
+  for (int idx = threadIdx.x; idx < n_list; idx += blockDim.x) {
+    const Cand cd = list[idx];
+    if (!(cd.e <= T)) continue;
+    const float2 xe = ex[idx];
+    we += (unsigned long long)__double2ll_rn((double)expf(d_ff(ff{xe.x, xe.y}, L)) * kFixScale);
+    wf += (unsigned long long)__double2ll_rn((double)expf(d_ff(ff{cd.x, 0.f}, L)) * kFixScale);
+  }
+  atomicAdd(&s_we, we);
+  atomicAdd(&s_wf, wf);
   __syncthreads();
   if (threadIdx.x == 0) {
-    double MX = -CUDART_INF;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) MX = fmax(MX, s_mx[w]);
-    double S = 0.0, NON = 0.0;  // (NON summed in order from FP32 warp sums)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      if (s_mx[w] > -CUDART_INF) S += s_mx[w] == MX ? s_sm[w] : s_sm[w] * exp(s_mx[w] - MX);
-      NON += s_non[w];
-    }
-    if (!(MX > -CUDART_INF) && NON > 0.0) {  // no candidate here: level of the FP32 minimum
-      MX = -M / kT;
-      S = NON;
-    } else if (MX > -CUDART_INF && NON > 0.0) {
-      S += NON * exp(-M / kT - MX);
-    }
-    const float hi = (float)MX;
-    a.part[blockIdx.x] = MX > -CUDART_INF ? make_float4(hi, (float)(MX - (double)hi), (float)S, 0.f)
-                                          : make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
+    a.part_ref[2 * pair] = make_float4(L.hi, L.lo, (float)((double)s_we / kFixScale),
+                                       (float)((double)s_wf / kFixScale));
+    a.part_ref[2 * pair + 1] = make_float4(Xe.hi, Xe.lo, 0.f, 0.f);
   }
-}
-
-// The window W + 2B of every receptor of a batch (one thread each): the FP32
-// correlation error bound B = 8 eps sqrt(log2 P^3) sum_t rms(G_t) ||gamma_t||
-// and W = kT max(20, ln(1e5 n)), n = S0 S1 S2 translations.
-__global__ void k_window(const RefTab *tabs, int K, double g0, double g1, double g2, double log2P3, double kT,
-                         double nS, double *window) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const RefTab t = tabs[k];
-  const double vol = t.vol;
-  const double B = 8.0 * 5.9604644775390625e-08 * sqrt(log2P3) *
-                   (sqrt(t.sumsq[0] / vol) * g0 + sqrt(t.sumsq[1] / vol) * g1 + sqrt(t.sumsq[2] / vol) * g2);
-  window[k] = kT * fmax(20.0, log(1e5 * nS)) + 2.0 * B;
-}
-
-// Per (configuration, receptor): the FP32 minimum over its planes and the
-// threshold, that minimum plus the receptor's window, rounded up to FP32.
-__global__ void k_threshold(const float *plane_min, int n_pairs, int S0, int K, const double *window, float *pmin_pair,
-                            float *thresh) {
-  const int pr = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pr >= n_pairs) return;
-  float mn = CUDART_INF_F;
-  for (int q = 0; q < S0; ++q) mn = fminf(mn, plane_min[(long long)pr * S0 + q]);
-  pmin_pair[pr] = mn;
-  thresh[pr] = mn < CUDART_INF_F ? __double2float_ru((double)mn + window[pr % K]) : -CUDART_INF_F;
 }
 
 cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  k_window<<<(a.K + 127) / 128, 128, 0, st>>>(a.tabs, a.K, a.gnorm[0], a.gnorm[1], a.gnorm[2], a.log2P3, a.kT,
-                                              (double)a.S0 * a.S1 * a.S2, a.window);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int n_pairs = batch * a.K;
-  k_threshold<<<(n_pairs + 127) / 128, 128, 0, st>>>(a.plane_min, n_pairs, a.S0, a.K, a.window, a.pmin_pair,
-                                                     a.thresh);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_refine<<<(unsigned)((long long)batch * a.K * a.S0), 256, 0, st>>>(a);
+  k_refine<<<(unsigned)((long long)batch * a.K), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-// gamma_t,i in FP64 (Eqs. electrostatic, repulsive_LJ, attractive_LJ): q,
-// sqrt(eps) R^p_rep, sqrt(eps) R^p_att.
-__global__ void k_gamma64(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att,
-                          double *g) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double se = sqrt((double)eps[i]), r = (double)R[i];
-  double rr = 1.0, ra = 1.0;
-  for (int p = 0; p < p_rep; ++p) rr *= r;
-  for (int p = 0; p < p_att; ++p) ra *= r;
-  g[i] = (double)q[i];
-  g[(long long)n + i] = se * rr;
-  g[2ll * n + i] = se * ra;
-}
+// Sum of squares of each of the three grids (FP32 error bound), in float
+// pairs and in a fixed order, so that the bound, and with it the set of
+// refined translations, is the same on every run: CTA b of channel t sums a
+// contiguous slice into part[t][b]; k_sumsq_final adds the slices in order.
+constexpr int kSumsqBlocks = kSumsqScratch / 3;
 
-cudaError_t launch_gamma64(const float *q, const float *eps, const float *R, int n, int p_rep, int p_att, double *g,
-                           cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  k_gamma64<<<(n + 127) / 128, 128, 0, st>>>(q, eps, R, n, p_rep, p_att, g);
-  return cudaGetLastError();
-}
-
-// Sum of squares of each of the three grids (FP64), for the FP32 error bound.
-__global__ void k_sumsq(const float *g, long long vol, double *out) {
-  __shared__ double s_d[256];
-  const int c = blockIdx.y;
-  double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < vol; i += (long long)gridDim.x * blockDim.x) {
-    const double v = g[(long long)c * vol + i];
-    acc += v * v;
+__global__ void __launch_bounds__(256) k_sumsq(const float *g, long long vol, float2 *part) {
+  __shared__ float s_h[256], s_l[256];
+  const int t = blockIdx.y, b = blockIdx.x;
+  const long long chunk = (vol + gridDim.x - 1) / gridDim.x;
+  const long long i0 = b * chunk, i1 = i0 + chunk < vol ? i0 + chunk : vol;
+  ff acc{0.f, 0.f};
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const float v = g[(long long)t * vol + i];
+    acc = s_norm(s_add(acc, s_mul(ff{v, 0.f}, ff{v, 0.f})));
   }
-  s_d[threadIdx.x] = acc;
+  s_h[threadIdx.x] = acc.hi;
+  s_l[threadIdx.x] = acc.lo;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) s_d[threadIdx.x] += s_d[threadIdx.x + o];
+    if ((int)threadIdx.x < o) {
+      const ff r = s_norm(s_add(ff{s_h[threadIdx.x], s_l[threadIdx.x]}, ff{s_h[threadIdx.x + o], s_l[threadIdx.x + o]}));
+      s_h[threadIdx.x] = r.hi;
+      s_l[threadIdx.x] = r.lo;
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(out + c, s_d[0]);
+  if (threadIdx.x == 0) part[t * gridDim.x + b] = make_float2(s_h[0], s_l[0]);
 }
 
-cudaError_t launch_sumsq(const float *g, long long vol, double *out, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(out, 0, 3 * sizeof(double), st);
+__global__ void k_sumsq_final(const float2 *part, int nb, float *out) {
+  const int t = threadIdx.x;
+  if (t >= 3) return;
+  ff acc{0.f, 0.f};
+  for (int b = 0; b < nb; ++b) acc = s_norm(s_add(acc, ff{part[t * nb + b].x, part[t * nb + b].y}));
+  out[t] = __fadd_rn(acc.hi, acc.lo);
+}
+
+cudaError_t launch_sumsq(const float *g, long long vol, float *out, float2 *scratch, cudaStream_t st) {
+  if (vol <= 0) return cudaMemsetAsync(out, 0, 3 * sizeof(float), st);
+  k_sumsq<<<dim3(kSumsqBlocks, 3), 256, 0, st>>>(g, vol, scratch);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sumsq<<<dim3(sm_count(), 3), 256, 0, st>>>(g, vol, out);
+  k_sumsq_final<<<1, 32, 0, st>>>(scratch, kSumsqBlocks, out);
   return cudaGetLastError();
 }
 

@@ -1,9 +1,10 @@
-"""The refined form (BPMF_MODE_REFINE: FP32 correlation, exact FP64
-re-evaluation of every translation that can carry weight) against the FP64
-oracle, through the C ABI.
+"""The refined form (BPMF_MODE_REFINE: FP32 correlation, exact float-pair
+re-evaluation of every translation that can carry weight, checked against a
+certificate) against the FP64 oracle, through the C ABI.
 
-Inside the 20 kT window the energies are the exact direct sum, so they match
-the oracle to FP64 rounding (1e-9 of the grid scale).  log Z, BPMF and dG
+Inside the 20 kT window the energies are the exact direct sum in float pairs,
+so they match the oracle to about 2^-44 of the terms (1e-9 of the grid scale
+is the bound used here).  log Z, BPMF and dG
 must meet the benchmark spec's tolerances (1e-3 and 0.01 kcal/mol); the excluded
 translations weigh less than 1e-5 of S by construction, so the measured error
 is far below."""
@@ -142,6 +143,7 @@ def test_refined_protein_scale_full_size_on_cropped_transforms(pkg):
         prof = pkg.bpmf_profile(s.ctx)
         pkg.bpmf_profile_enable(s.ctx, False)
     assert prof.get("k_crop", (0.0, 0))[1] > 0, sorted(prof)
+    assert not (rc & pkg.BPMF_WARN_REFINE_FALLBACK), "the certificate held on the benchmark workload"
     idx = np.arange(0, J, 16)
     ref = oracle.evaluate(w.receptors, lig.coords[idx], lig.params.q, lig.params.eps, lig.params.R, KT)
     assert np.array_equal(out["n_valid"][idx], ref["n_valid"])
@@ -149,3 +151,61 @@ def test_refined_protein_scale_full_size_on_cropped_transforms(pkg):
     assert np.abs(out["logZ"][idx][ok] - ref["logZ"][ok]).max() * KT <= E_TOL
     logS = out["logZ"][idx] + np.log(out["n_valid"][idx])
     assert np.abs(oracle.bpmf(logS, out["n_valid"][idx], KT) - ref["bpmf"]).max() <= B_TOL
+
+
+def test_refined_certificate_failure_falls_back_to_float_pairs(pkg):
+    """With the certificate's bound scaled to zero every re-evaluated
+    translation fails the check: the call recomputes the ligand in float pairs,
+    says so in its status, and its results are those of the float-pair form
+    (bit for bit) and within the tolerances of the oracle."""
+    w = synth.plain_small(n_conf=16)
+    r, l = w.receptors[0], w.ligands[0]
+    ref = oracle.evaluate([r], l.coords, l.params.q, l.params.eps, l.params.R, KT)
+    with _session() as s:
+        rh = s.load_receptor(r)
+        lh, _, _ = s.load_ligands([l])
+        rc0, base = s.eval(lh, [rh], KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=16)
+        assert not (rc0 & pkg.BPMF_WARN_REFINE_FALLBACK)
+        _, ff = s.eval(lh, [rh], KT, pkg.BPMF_MODE_FF, n_lig=1, total_conf=16)
+        pkg.bpmf_set_refine_check_scale(s.ctx, 0.0)
+        rc, out = s.eval(lh, [rh], KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=16)
+        E = s.export_energies(lh, rh, 0, 3, r.site_n, pkg.BPMF_MODE_REFINE)
+        E_ff = s.export_energies(lh, rh, 0, 3, r.site_n, pkg.BPMF_MODE_FF)
+        pkg.bpmf_set_refine_check_scale(s.ctx, 1.0)
+    assert rc & pkg.BPMF_WARN_REFINE_FALLBACK
+    for k in ("logZ", "n_valid", "bpmf", "dG"):
+        assert np.array_equal(out[k], ff[k]), k
+    assert np.array_equal(E, E_ff)
+    fin = np.isfinite(ref["logZ"])
+    assert np.abs(out["logZ"][fin] - ref["logZ"][fin]).max() * KT <= E_TOL
+    assert abs(out["bpmf"][0, 0] - ref["bpmf"][0]) <= B_TOL
+    assert np.abs(base["logZ"][fin] - ref["logZ"][fin]).max() * KT <= E_TOL
+
+
+def test_refined_results_are_deterministic_with_and_without_graphs(pkg):
+    """The refined sums do not depend on the order in which the site planes
+    append their candidates: repeated calls, and a CUDA-graph replay, give
+    bit-identical results."""
+    import torch
+    w = synth.protein_scale(n_conf=48, n_rec=2)
+    lig = w.ligands[0]
+    J, K = 48, 2
+    with _session() as s:
+        rhs = [s.load_receptor(r) for r in w.receptors]
+        lh, _, _ = s.load_ligands([lig])
+        _, a = s.eval(lh, rhs, KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=J)
+        _, b = s.eval(lh, rhs, KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=J)
+        st = torch.cuda.Stream()
+        dev = {"logZ": torch.empty((J, K), dtype=torch.float64, device="cuda"),
+               "n_valid": torch.empty((J, K), dtype=torch.int64, device="cuda"),
+               "bpmf": torch.empty((1, K), dtype=torch.float64, device="cuda"),
+               "dG": torch.empty(1, dtype=torch.float64, device="cuda")}
+        pkg.bpmf_set_graph_mode(s.ctx, 1)
+        for _ in range(2):  # capture, then replay
+            s.eval(lh, rhs, KT, pkg.BPMF_MODE_REFINE, out=dev, stream=st.cuda_stream)
+            torch.cuda.synchronize()
+            for k in ("logZ", "n_valid", "bpmf", "dG"):
+                assert np.array_equal(dev[k].cpu().numpy(), a[k]), k
+        pkg.bpmf_set_graph_mode(s.ctx, 0)
+    for k in ("logZ", "n_valid", "bpmf", "dG"):
+        assert np.array_equal(a[k], b[k]), k
