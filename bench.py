@@ -248,6 +248,7 @@ def alg_work(w, edges, mode, launches_per_step=None):
     work["k_xfused"] = {"flops": float(np.sum(Q * (3 * cfft(P0) + K * (cfft(P0) + 3 * 8 * P0)))),
                         "bytes": float(np.sum(3 * u[:, 0] * Q * E + K * S[0] * Q * E
                                               + K * 3 * P0 * Q * 8 * rec_mult / per_launch))}
+    work["k_xpass"] = work["k_xfused"]  # the FP32 x pass on compile-time edges: the same work
     work["k_axis(y inv)"] = {"flops": float(np.sum(K * S[0] * F2 * cfft(P1))),
                              "bytes": float(np.sum(K * S[0] * (Q + S[1] * F2) * E))}
     work["k_zinv"] = {"flops": float(np.sum(K * S[0] * (S[1] / 2) * cfft(P2))),

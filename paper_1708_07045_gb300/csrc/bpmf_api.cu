@@ -511,7 +511,8 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
                const PairInfo *d_info, const float2 *const *d_rhi, const float2 *const *d_rlo, double h,
                float nscale_hi, float nscale_lo, float escale_hi, float escale_lo, float4 *d_part,
                double *export_E, char *ws, cudaStream_t st, const bpmf_ctx::Tune &tn, bool split = false,
-               const OccTab *d_tabs = nullptr, const RefineCtx *rf = nullptr) {
+               const OccTab *d_tabs = nullptr, const RefineCtx *rf = nullptr, const float2 *const *h_rhi = nullptr,
+               int *d_err = nullptr) {
   auto plan = [&](int P) { return split ? make_plan_split(c, P) : make_plan(P); };
   const size_t E = sizeof(cx<T>);
   char *p = ws;
@@ -652,6 +653,9 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   XfusedArgs xa{};
   xa.ly = ly;
   xa.U0 = g.U[0];
+  xa.meta = d_meta;
+  xa.rhi_h = h_rhi;
+  xa.err = d_err;
   xa.Q = g.Q;
   xa.K = g.K;
   xa.rhi = d_rhi;
@@ -661,7 +665,10 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   xa.info = d_info;
   xa.plan = plan(g.P[0]);
   xa.tw = twiddles(c, g.P[0]);
-  launch(c, sizeof(T) == 4 ? "k_xfused<fp32>" : "k_xfused<ff>", st, [&] { return launch_xfused<T>(xa, batch, st); });
+  if (sizeof(T) == 4 && !split && xpass_supported(g.P[0]))  // FP32 on a compile-time edge
+    launch(c, "k_xpass<fp32>", st, [&] { return launch_xpass(xa, batch, st); });
+  else
+    launch(c, sizeof(T) == 4 ? "k_xfused<fp32>" : "k_xfused<ff>", st, [&] { return launch_xfused<T>(xa, batch, st); });
 
   // FP32 forms: the y inverse runs inside the z inverse when the window fits
   const bool fuse_y = sizeof(T) == 4 && !split && zinv_fused_fits(g.P[1], g.P[2], g.S[1], g.S[2], g.refine);
@@ -1486,6 +1493,15 @@ struct LigPlan {
   size_t fixed = 0, batch_bytes = 0;
 };
 
+// A kernel whose bounded wait ran out set the last flag the call copied out
+// (read after the stream has synchronised).
+void check_timeout(bpmf_ctx *c, int n_plan_ligs) {
+  if (c->fail_host && c->fail_n > (size_t)n_plan_ligs && c->fail_host[n_plan_ligs]) {
+    last_msg = "a kernel's bounded wait for its tensor copies ran out";
+    throw Fail{BPMF_ERR_TIMEOUT};
+  }
+}
+
 int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
               double *logZ, int64_t *n_valid, double *bpmf_out, double *dG, cudaStream_t st, int only_lig,
               int only_conf, double *export_E, double *Emin = nullptr, double *Dom = nullptr,
@@ -1525,6 +1541,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       CK(cudaEventRecord(c->pinned_busy, st));
       if (refine) {  // the certificate flags the graph copied out
         CK(cudaStreamSynchronize(st));
+        check_timeout(c, lig_end - lig_begin);
         for (int li = lig_begin; li < lig_end; ++li)
           if (c->fail_host[li - lig_begin] && fail_ligs) fail_ligs->push_back(li);
       }
@@ -1716,20 +1733,22 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   }
   const size_t blob_bytes = align_up(blob.size());
   const int n_plan_ligs = lig_end - lig_begin;
-  const size_t fail_bytes = align_up(sizeof(int) * std::max(n_plan_ligs, 1));
+  // per ligand: the refined form's certificate flag; then one flag for a
+  // bounded wait that ran out in a kernel
+  const size_t fail_bytes = align_up(sizeof(int) * (n_plan_ligs + 1));
   // device resources are made ready before any work is queued (and so before
   // a capture begins): workspace, pinned staging, twiddle tables, the pinned
   // certificate flags
   char *ws = static_cast<char *>(workspace(c, blob_bytes + fail_bytes + ws_need, st));
-  if (refine && c->fail_n < (size_t)n_plan_ligs) {
+  if (c->fail_n < (size_t)n_plan_ligs + 1) {
     if (c->fail_host) {
       CK(cudaStreamSynchronize(st));
       CK(cudaFreeHost(c->fail_host));
       c->fail_host = nullptr;
       c->fail_n = 0;
     }
-    CK(cudaMallocHost(&c->fail_host, sizeof(int) * n_plan_ligs));
-    c->fail_n = n_plan_ligs;
+    CK(cudaMallocHost(&c->fail_host, sizeof(int) * (n_plan_ligs + 1)));
+    c->fail_n = n_plan_ligs + 1;
   }
   // the pinned staging is rewritten: wait for the last copy or graph replay
   // that reads it, and drop the cached graph, whose copy node points at it
@@ -1784,7 +1803,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       CK(cudaMemcpyAsync(tab, c->pinned, blob.size(), cudaMemcpyHostToDevice, st));
       if (!use_graph) CK(cudaEventRecord(c->pinned_busy, st));
     }
-    if (refine) CK(cudaMemsetAsync(d_fail, 0, sizeof(int) * n_plan_ligs, st));
+    CK(cudaMemsetAsync(d_fail, 0, sizeof(int) * (n_plan_ligs + 1), st));
     long long conf_base = 0;
     for (int li = 0; li < lig_begin; ++li) conf_base += lg->n_conf[li];
     for (const LigPlan &pl : plans) {
@@ -1857,7 +1876,9 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
             else
               run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, nullptr, h, nsh, nsl,
                                esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, split, d_tabs,
-                               refine ? &rf : nullptr);
+                               refine ? &rf : nullptr,
+                               reinterpret_cast<const float2 *const *>(blob.data() + bk.off_rptr),
+                               d_fail + n_plan_ligs);
           }
         }
         if (export_E) continue;
@@ -1907,8 +1928,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       // the next ligand reuses the workspace; stream order keeps these copies first
       conf_base += lg->n_conf[pl.li];
     }
-    if (refine)
-      CK(cudaMemcpyAsync(c->fail_host, d_fail, sizeof(int) * n_plan_ligs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->fail_host, d_fail, sizeof(int) * (n_plan_ligs + 1), cudaMemcpyDeviceToHost, st));
   } catch (Fail f) {
     if (use_graph) {
       cudaGraph_t gr = nullptr;
@@ -1931,13 +1951,13 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   // the fork and join events are queued in every wait that uses them: reusable
   for (cudaEvent_t e : joins) c->event_pool.push_back(e);
   c->event_pool.push_back(fork);
-  if (refine) {  // the certificate flags: the ligands to recompute in float pairs
+  if (refine || host_out || export_E) {
     CK(cudaStreamSynchronize(st));
+    check_timeout(c, n_plan_ligs);
+  }
+  if (refine)  // the certificate flags: the ligands to recompute in float pairs
     for (int li = lig_begin; li < lig_end; ++li)
       if (c->fail_host[li - lig_begin] && fail_ligs) fail_ligs->push_back(li);
-  } else if (host_out) {
-    CK(cudaStreamSynchronize(st));
-  }
   return warn ? BPMF_WARN_NO_VALID : BPMF_OK;
 }
 

@@ -408,7 +408,9 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfu
     const int x = idx / L3, c = idx % L3, gt = c / LW, l = c % LW;
     const int j = j0 + gt / 3, t = gt % 3;
     const long long q = q0 + l;
-    cp_cx<T>(&bA[idx], a.ly, (((long long)j * 3 + t) * a.U0 + x) * a.Q + q, q < a.Q && j < batch);
+    // rows beyond a configuration's own ligand box are zero (not read)
+    const bool in_box = j < batch && (!a.meta || x < a.meta[j].u[0]);
+    cp_cx<T>(&bA[idx], a.ly, (((long long)j * 3 + t) * a.U0 + x) * a.Q + q, q < a.Q && in_box);
   }
   for (int idx = U0 * L3 + threadIdx.x; idx < P * L3; idx += blockDim.x) bA[idx] = c_zero<T>();
   cp_async_wait_all();

@@ -1,6 +1,8 @@
 // Kernel argument blocks and launch wrappers shared by the C-ABI layer and
 // the kernel translation units.
 #pragma once
+#include <cuda.h>
+
 #include <cstdint>
 
 #include "fft.cuh"
@@ -91,6 +93,7 @@ struct AxisArgs {          // C2C along a strided axis, pruned input / output
 struct XfusedArgs {        // x: forward ligand DFT, product with each receptor, inverse, window
   const void *ly;          // [batch][3][U0][Q] cx<T>
   int U0;
+  const ConfMeta *meta;    // [batch] or null: rows x >= u[0] of configuration j are zero (and need not be read)
   long long Q;
   int K;
   const float2 *const *rhi;  // [K] -> [3][P0][Q]
@@ -100,6 +103,8 @@ struct XfusedArgs {        // x: forward ligand DFT, product with each receptor,
   const PairInfo *info;    // [batch][K]
   FftPlan plan;
   const float4 *tw;
+  const float2 *const *rhi_h;  // host copy of rhi (tensor maps of the FP32 x pass), or null
+  int *err;                // device flag set when a bounded wait of the x pass runs out, or null
 };
 
 // ---- steric clashes (Eq. occupancy_grid) -----------------------------------
@@ -283,6 +288,14 @@ cudaError_t launch_ligspec(const LigSpecArgs &a, int batch, cudaStream_t st);
 template <class T> cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st);
 template <class T> cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st);
 template <class T> cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st);
+// FP32 x pass on compile-time edges (xpass.cu): P in {64, 72, 80, 96}, no tensor-core stage.
+// Receptor tiles arrive by TMA for up to kXpMaxMaps receptors per launch.
+constexpr int kXpMaxMaps = 8;
+struct alignas(64) XpassMaps {
+  CUtensorMap m[kXpMaxMaps];
+};
+bool xpass_supported(int P);
+cudaError_t launch_xpass(const XfusedArgs &a, int batch, cudaStream_t st);
 template <class T> cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st);
 // whether the FP32 z inverse can take the y inverse in front (whole site
 // window in one shared-memory chunk at 3 CTAs per SM)

@@ -36,6 +36,9 @@ __global__ void __launch_bounds__(256) k_ligspec(LigSpecArgs a) {
   __shared__ int s_cnt[9];
   const int ix = blockIdx.x, j = blockIdx.y;
   const ConfMeta m = a.meta[j];
+  // planes beyond this configuration's ligand box hold no atom; the x pass
+  // reads them as zeros without loading them
+  if (ix >= m.u[0]) return;
   const int n = m.n_atoms;
   const ff h{a.h_hi, a.h_lo};
   // placement in float pairs, as the spreading kernel does it

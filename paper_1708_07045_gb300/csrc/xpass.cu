@@ -1,0 +1,348 @@
+// The x pass of the FP32 forms on compile-time transform edges P = 8 R
+// (R = 8, 9, 10, 12: edges 64, 72, 80, 96): forward DFT of the ligand's three
+// channels along x, the conj-multiply-sum with every receptor spectrum (Eq.
+// fft_correlation_func), inverse DFT along x, site window (the same work as
+// k_xfused, organised for fewer instructions per point).
+//
+// Each DFT has two in-place stages (four-step factorisation, n = n1 + 8 n2,
+// f = k2 + R k1):
+//   forward  A: per n1, R-point DFT over n2 of x[n1 + 8 n2], times w_P^(n1 k2)
+//            B: per k2, 8-point DFT over n1                 -> X[k2 + R k1]
+//   inverse  B': per k2, inverse 8-point DFT over k1, times conj(w_P^(n1 k2))
+//            A': per n1, inverse R-point DFT over k2        -> x[n1 + 8 n2]
+// A stage unit reads and writes the same rows, so no second buffer is needed:
+// the spectra live in shared memory in the permuted row order
+// row 8 k2 + k1 <-> frequency k2 + R k1, and the inverse returns natural order.
+//
+// CTA = 2 configurations x 8 consecutive (y, zf) columns, 256 threads.  A
+// half-warp owns one unit at a time and its 16 lanes are the 16 lines of a
+// channel (configuration g = lane / 8, column l = lane % 8): every shared
+// access of a half-warp is 16 consecutive float2 (no bank conflicts), and the
+// index arithmetic is per unit, not per element.
+//
+// Each receptor's spectra for the CTA's columns (3 channels x P frequencies x
+// 8 columns) are staged in shared memory while the previous transform runs:
+// by one TMA tensor copy (cp.async.bulk.tensor, completion on an mbarrier)
+// when the receptor group has at most kXpMaxMaps receptors, else by 16-byte
+// cp.async copies.  Every mbarrier wait is bounded: after about a second it
+// sets the call's error flag and the CTA returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "kernels.cuh"
+
+namespace bpmf {
+
+namespace {
+
+constexpr int kXpNT = 256;     // threads per CTA
+constexpr int kXpLW = 8;       // columns per CTA
+constexpr int kXpG = 2;        // configurations per CTA
+constexpr int kXpNLF = 48;     // forward lines: 3 channels x 2 configurations x 8 columns
+
+__device__ __forceinline__ int imod_p(int a, int m) {
+  const int r = a % m;
+  return r < 0 ? r + m : r;
+}
+
+__device__ __forceinline__ void cp16(void *dst, const void *src, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ---- TMA tensor copies and their mbarrier ------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// one 3D tile of a tensor map into shared memory; the mbarrier expects its bytes
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            unsigned long long *bar, unsigned bytes) {
+  // the buffer was last read by ordinary loads: order them before the async-proxy write
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+// Wait for the mbarrier phase with the given parity, for about 2^31 SM cycles
+// at most (about a second); false when the time ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+// One receptor's spectra for this CTA's 8 columns, all P frequencies and 3
+// channels, into RS[t][row][8] in the permuted row order of the forward
+// spectra (row 8 k2 + k1 <-> frequency k2 + R k1): 16-byte asynchronous
+// copies of column pairs (Q is even and q0 a multiple of 8, so each pair is
+// 16-byte aligned and wholly inside or outside the spectrum).
+template <int P>
+__device__ __forceinline__ void stage_receptor(cx<float> *RS, const float2 *rh, int Q, int q0) {
+  constexpr int R = P / 8;
+  for (int e = threadIdx.x; e < 3 * P * 4; e += kXpNT) {
+    const int c = e & 3, tr = e >> 2, t = tr / P, row = tr - t * P;
+    const int f = (row >> 3) + R * (row & 7);
+    const bool v = q0 + 2 * c < Q;
+    cp16(&RS[tr * kXpLW + 2 * c], v ? rh + ((long long)t * P + f) * Q + q0 + 2 * c : rh, v);
+  }
+}
+
+// Every thread waits for the current tile; the CTA agrees on the outcome.  On
+// a timeout the error flag is set, the copy in flight is waited for once more
+// (again bounded), and the CTA is to return.
+__device__ __forceinline__ bool tile_arrived(unsigned long long *bar, unsigned &parity, int *err) {
+  const bool ok = mbar_wait(bar, parity);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0 && err) atomicOr(err, 1);
+    mbar_wait(bar, parity);
+    return false;
+  }
+  parity ^= 1u;
+  return true;
+}
+
+template <int P, bool TMA>
+__global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, const __grid_constant__ XpassMaps maps) {
+  constexpr int R = P / 8;
+  constexpr unsigned kTileBytes = 3u * P * kXpLW * sizeof(cx<float>);
+  __shared__ alignas(8) unsigned long long s_bar;  // receptor tile arrivals (TMA)
+  unsigned parity = 0;
+  constexpr int NLI = 16;  // inverse lines: 2 configurations x 8 columns (one receptor at a time)
+  extern __shared__ float4 smem[];
+  float4 *tw = smem;                                         // [P] exp(-2 pi i k / P)
+  cx<float> *L = reinterpret_cast<cx<float> *>(tw + P);      // [P][48] ligand spectra (permuted rows)
+  cx<float> *W = L + P * kXpNLF;                             // [P][16] products, inverse
+  // [3][P][8] staged receptor spectra, 128-byte aligned (TMA destination)
+  cx<float> *RS = reinterpret_cast<cx<float> *>((reinterpret_cast<uintptr_t>(W + P * NLI) + 127) & ~uintptr_t(127));
+  __shared__ int s_wm[2];                                    // window start along x, mod P, per g
+  const int tid = threadIdx.x, hw = tid >> 4, hl = tid & 15;
+  const int g = hl >> 3, l = hl & 7;
+  const int nJG = (batch + kXpG - 1) / kXpG;
+  const int j0 = (blockIdx.x % nJG) * kXpG;
+  const int q0 = (blockIdx.x / nJG) * kXpLW;
+  const int Q = (int)a.Q;
+  const int j = j0 + g, q = q0 + l;
+  const bool live = j < batch && q < Q;
+  for (int i = tid; i < P; i += kXpNT) tw[i] = a.tw[i];
+  // ligand spectra of this tile (rows beyond each configuration's ligand box
+  // are zero) and the first receptor's spectra, asynchronously
+  {
+    const int U0 = a.U0 < P ? a.U0 : P;
+    const int u0[2] = {j0 < batch ? min(a.meta ? a.meta[j0].u[0] : U0, U0) : 0,
+                       j0 + 1 < batch ? min(a.meta ? a.meta[j0 + 1].u[0] : U0, U0) : 0};
+    const cx<float> *ly = reinterpret_cast<const cx<float> *>(a.ly);
+    // copy e = ((x * 3 + t) * 2 + gg) * 4 + c: columns 2c, 2c + 1 of row (gg, t, x)
+    for (int e = tid; e < P * 3 * 8; e += kXpNT) {
+      const int c = e & 3, gg = (e >> 2) & 1, xt = e >> 3, x = xt / 3, t = xt - 3 * x;
+      const bool v = x < u0[gg] && q0 + 2 * c < Q;
+      const long long gi = (((long long)(j0 + gg) * 3 + t) * a.U0 + x) * Q + q0 + 2 * c;
+      cp16(&L[x * kXpNLF + t * 16 + gg * 8 + 2 * c], v ? ly + gi : ly, v);
+    }
+    if constexpr (TMA) {
+      if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        if (a.K > 0) tma_load_3d(RS, &maps.m[0], 2 * q0, 0, 0, &s_bar, kTileBytes);
+      }
+    } else {
+      if (a.K > 0) stage_receptor<P>(RS, a.rhi[0], Q, q0);
+    }
+    cp_wait_all();
+  }
+  __syncthreads();
+  // forward A: unit (n1, t), R-point DFT of rows n1 + 8 n2, twiddled
+  for (int u = hw; u < 8 * 3; u += kXpNT / 16) {
+    const int n1 = u & 7, t = u >> 3;
+    cx<float> *col = L + n1 * kXpNLF + t * 16 + hl;
+    cx<float> v[R];
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2) v[n2] = col[8 * n2 * kXpNLF];
+    dft_small<float, R>(v, false, tw, P);
+#pragma unroll
+    for (int k2 = 1; k2 < R; ++k2) v[k2] = c_mul(v[k2], tw_load<float>(tw[n1 * k2], false));
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) col[8 * k2 * kXpNLF] = v[k2];
+  }
+  __syncthreads();
+  // forward B: unit (k2, t), 8-point DFT of rows 8 k2 + n1 -> row 8 k2 + k1 = X[k2 + R k1]
+  for (int u = hw; u < R * 3; u += kXpNT / 16) {
+    const int t = u / R, k2 = u - t * R;
+    cx<float> *col = L + 8 * k2 * kXpNLF + t * 16 + hl;
+    cx<float> v[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) v[n1] = col[n1 * kXpNLF];
+    dft_small<float, 8>(v, false, tw, P);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) col[k1 * kXpNLF] = v[k1];
+  }
+  for (int k = 0; k < a.K; ++k) {
+    if (tid < 2) {
+      const int jj = j0 + tid;
+      s_wm[tid] = jj < batch ? imod_p(a.info[jj * a.K + k].wc[0], P) : 0;
+    }
+    if constexpr (TMA) {  // receptor k's tile (includes the CTA barrier)
+      if (!tile_arrived(&s_bar, parity, a.err)) return;
+    } else {
+      __syncthreads();
+    }
+    // product: unit row, P_k = sum_t R_{k,t} conj(L_t) at frequency f(row)
+    for (int row = hw; row < P; row += kXpNT / 16) {
+      // TMA tiles hold natural frequency order, the cp.async tiles row order
+      const int rrow = TMA ? (row >> 3) + R * (row & 7) : row;
+      const cx<float> *rs = RS + rrow * kXpLW + l;
+      const cx<float> *lx = L + row * kXpNLF + hl;
+      W[row * NLI + hl] = c_add(c_add(c_mulconj(rs[0], lx[0]), c_mulconj(rs[P * kXpLW], lx[16])),
+                                c_mulconj(rs[2 * P * kXpLW], lx[32]));
+    }
+    __syncthreads();
+    // the next receptor's spectra stream in while this one is transformed back
+    if (k + 1 < a.K) {
+      if constexpr (TMA) {
+        if (tid == 0) tma_load_3d(RS, &maps.m[k + 1], 2 * q0, 0, 0, &s_bar, kTileBytes);
+      } else {
+        stage_receptor<P>(RS, a.rhi[k + 1], Q, q0);
+      }
+    }
+    // inverse B': unit k2, inverse 8-point DFT over k1, then conj(w_P^(n1 k2))
+    for (int k2 = hw; k2 < R; k2 += kXpNT / 16) {
+      cx<float> *col = W + 8 * k2 * NLI + hl;
+      cx<float> v[8];
+#pragma unroll
+      for (int k1 = 0; k1 < 8; ++k1) v[k1] = col[k1 * NLI];
+      dft_small<float, 8>(v, true, tw, P);
+#pragma unroll
+      for (int n1 = 1; n1 < 8; ++n1) v[n1] = c_mul(v[n1], tw_load<float>(tw[n1 * k2], true));
+#pragma unroll
+      for (int n1 = 0; n1 < 8; ++n1) col[n1 * NLI] = v[n1];
+    }
+    __syncthreads();
+    // inverse A': unit n1, inverse R-point DFT over k2 -> row n1 + 8 n2 (natural)
+    if (hw < 8) {
+      const int n1 = hw;
+      cx<float> *col = W + n1 * NLI + hl;
+      cx<float> v[R];
+#pragma unroll
+      for (int k2 = 0; k2 < R; ++k2) v[k2] = col[8 * k2 * NLI];
+      dft_small<float, R>(v, true, tw, P);
+#pragma unroll
+      for (int n2 = 0; n2 < R; ++n2) col[8 * n2 * NLI] = v[n2];
+    }
+    __syncthreads();
+    // site window along x: unit s
+    for (int s = hw; s < a.S0; s += kXpNT / 16) {
+      int m = s_wm[g] + s;  // s < S0 <= P
+      m -= m >= P ? P : 0;
+      if (live)
+        reinterpret_cast<cx<float> *>(a.x2)[(((long long)j * a.K + k) * a.S0 + s) * Q + q] = W[m * NLI + hl];
+    }
+    if constexpr (!TMA) cp_wait_all();
+    __syncthreads();
+  }
+}
+
+template <int P>
+size_t xpass_smem() {
+  // tw (16 P bytes), L and W (8 P (48 + 16)), then RS rounded up to 128 bytes
+  return sizeof(float4) * P + sizeof(cx<float>) * (size_t)P * (kXpNLF + 16 + 3 * kXpLW) + 128;
+}
+
+// Tensor maps of the receptor spectra [3][P][Q] float2 as FP32 [3][P][2Q],
+// box [3][P][16 floats] (8 columns), cached by (spectrum, P, Q).
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+std::mutex g_map_mu;
+std::map<std::tuple<const void *, int, long long>, CUtensorMap> g_maps;
+
+bool receptor_map(const float2 *spec, int P, long long Q, CUtensorMap *out) {
+  std::lock_guard<std::mutex> lk(g_map_mu);
+  const auto key = std::make_tuple((const void *)spec, P, Q);
+  auto it = g_maps.find(key);
+  if (it != g_maps.end()) {
+    *out = it->second;
+    return true;
+  }
+  static EncodeTiled encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<EncodeTiled>(fn);
+  }
+  alignas(64) CUtensorMap m;
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * Q), (cuuint64_t)P, 3};
+  const cuuint64_t strides[2] = {(cuuint64_t)(2 * Q * sizeof(float)), (cuuint64_t)(2 * Q * sizeof(float) * P)};
+  const cuuint32_t box[3] = {2 * kXpLW, (cuuint32_t)P, 3};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2 *>(spec), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  g_maps[key] = m;
+  *out = m;
+  return true;
+}
+
+template <int P>
+cudaError_t launch_xpass_p(const XfusedArgs &a, int batch, cudaStream_t st) {
+  const size_t smem = xpass_smem<P>();
+  const long long blocks = (long long)((batch + kXpG - 1) / kXpG) * ((a.Q + kXpLW - 1) / kXpLW);
+  XpassMaps maps;
+  bool tma = a.rhi_h && a.K <= kXpMaxMaps;
+  for (int k = 0; tma && k < a.K; ++k) {
+    // 16-byte aligned spectra whose rows are 16-byte multiples (Q even)
+    tma = ((reinterpret_cast<unsigned long long>(a.rhi_h[k]) & 15ull) == 0) && receptor_map(a.rhi_h[k], P, a.Q, &maps.m[k]);
+  }
+  if (tma) {
+    cudaError_t e = cudaFuncSetAttribute(k_xpass<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_xpass<P, true><<<(unsigned)blocks, kXpNT, smem, st>>>(a, batch, maps);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_xpass<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_xpass<P, false><<<(unsigned)blocks, kXpNT, smem, st>>>(a, batch, maps);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool xpass_supported(int P) { return P == 64 || P == 72 || P == 80 || P == 96; }
+
+cudaError_t launch_xpass(const XfusedArgs &a, int batch, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  if (a.S0 > a.plan.n || a.plan.tca) return cudaErrorInvalidValue;
+  if (a.Q % 2) return cudaErrorInvalidValue;  // 16-byte column pairs
+  switch (a.plan.n) {
+    case 64: return launch_xpass_p<64>(a, batch, st);
+    case 72: return launch_xpass_p<72>(a, batch, st);
+    case 80: return launch_xpass_p<80>(a, batch, st);
+    case 96: return launch_xpass_p<96>(a, batch, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bpmf
