@@ -558,63 +558,195 @@ def whole_surface_leg(torch, pkg, sess, dev, stream, steps, n_conf=32):
             "oracle_one_configuration_s": t_or}
 
 
-def learned_proposal_leg(torch, pkg, sess, w, dev, stream, res_train, coords_train, params_train, budget_frac=0.1):
-    """Train the MLP proposal on the benchmark ligand's full enumeration, then
-    estimate the BPMFs of a held-out ligand from a 10 % budget; the full
-    enumeration of the held-out ligand is the judge and the time baseline."""
-    from paper_1708_07045_gb300 import proposal as PP
-    K, J = N_REC, N_CONF
-    recs = [pkg.bpmf_receptor_load(sess.ctx, r.grids, r.h, r.origin, r.site_lo, r.site_n) for r in w.receptors]
-    h = w.receptors[0].h
+def uneven_receptors():
+    """The ten receptor conformations of the batched workload (64^3-112^3 at
+    0.25 A, sites 24^3-40^3), shared by the batched and learned-proposal legs."""
+    return synth.batched_uneven(n_lig=1, n_conf=1).receptors
+
+
+def proposal_q(pred, mix, tau):
+    """q of every configuration (reporting only; the draws come from bpmf_proposal_sample)."""
+    p = pred.double().cpu().numpy() / tau
+    w = np.exp(p - p.max())
+    return mix * w / w.sum() + (1.0 - mix) / p.size
+
+
+def batched_leg(torch, pkg, sess, recs_in, kT, stream, steps, n_lig=141, n_conf=500, sample_frac=0.005):
+    """The batched uneven workload at full size: n_lig ligands of 8-60 atoms x
+    n_conf configurations against the 10 receptor conformations of 64^3-112^3
+    (receptor groups by padded edge), all in one bpmf_eval (refined form),
+    timed without and with CUDA-graph replay; log Z of a seeded sample of
+    (ligand, configuration) pairs against the FP64 oracle."""
+    import oracle
+    w = synth.batched_uneven(n_lig=n_lig, n_conf=n_conf)
+    K = len(recs_in)
+    ligs = w.ligands
+    T = sum(l.coords.shape[0] for l in ligs)
+    recs = [pkg.bpmf_receptor_load(sess.ctx, r.grids, r.h, r.origin, r.site_lo, r.site_n) for r in recs_in]
+    coords = torch.from_numpy(np.ascontiguousarray(np.concatenate([l.coords.reshape(-1, 3) for l in ligs]))).cuda()
+    params = [torch.from_numpy(np.ascontiguousarray(np.concatenate([getattr(l.params, k) for l in ligs]))).cuda()
+              for k in ("q", "eps", "R")]
+    lh = pkg.bpmf_ligand_batch(sess.ctx, [l.params.n_atoms for l in ligs], [l.coords.shape[0] for l in ligs], coords,
+                               *params)
+    out = {"logZ": torch.empty((T, K), dtype=torch.float64, device="cuda"),
+           "n_valid": torch.empty((T, K), dtype=torch.int64, device="cuda"),
+           "bpmf": torch.empty((n_lig, K), dtype=torch.float64, device="cuda"),
+           "dG": torch.empty(n_lig, dtype=torch.float64, device="cuda")}
     try:
-        lh_tr = pkg.bpmf_ligand_batch(sess.ctx, [N_ATOMS], [J], coords_train, *params_train)
-        X = PP.features(sess.ctx, lh_tr, J, h, dev)
-        pkg.bpmf_ligand_free(lh_tr)
-        t = PP.config_targets(res_train["logZ"], res_train["n_valid"])
-        ok = np.isfinite(t)
-        Xtr = X[torch.from_numpy(np.nonzero(ok)[0]).to(dev)].contiguous()
-        net = PP.LearnedProposal(sess.ctx, PP.fit_norm(Xtr.cpu().numpy(), t[ok]))
-        t0 = time.perf_counter()
-        losses = net.fit(Xtr, torch.from_numpy(t[ok].astype(np.float32)).to(dev), epochs=8, batch=256)
-        t_train = time.perf_counter() - t0
-        held = synth.LigandInput(synth.ligand_params(7001, N_ATOMS), synth.ligand_configs(7002, N_ATOMS, J))
-        coords = torch.from_numpy(held.coords).to(dev)
-        params = [torch.from_numpy(getattr(held.params, k)).to(dev) for k in ("q", "eps", "R")]
-        lh = pkg.bpmf_ligand_batch(sess.ctx, [N_ATOMS], [J], coords.reshape(-1, 3), *params)
-        # full enumeration: judge and time baseline
-        logZ = torch.empty((J, K), dtype=torch.float64, device=dev)
-        nv = torch.empty((J, K), dtype=torch.int64, device=dev)
-        B = torch.empty((1, K), dtype=torch.float64, device=dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pkg.bpmf_eval(sess.ctx, lh, recs, w.kT, pkg.BPMF_MODE_FF, logZ, nv, B, None)
-        torch.cuda.synchronize()
-        t_full = time.perf_counter() - t0
-        B_full = B.cpu().numpy()[0]
-        n_tot = pkg.bpmf_valid_counts(sess.ctx, lh, recs, J).sum(axis=0)
-        M = int(budget_frac * J)
         res = {}
-        for name, mix in (("trained", 0.8), ("uniform", 0.0)):
-            errs, times = [], []
-            for seed in range(6):
+        for graph in (False, True):
+            pkg.bpmf_set_graph_mode(sess.ctx, graph)
+            rc = pkg.bpmf_eval(sess.ctx, lh, recs, kT, pkg.BPMF_MODE_REFINE, out["logZ"], out["n_valid"], out["bpmf"],
+                               out["dG"], stream)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(steps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pkg.bpmf_eval(sess.ctx, lh, recs, kT, pkg.BPMF_MODE_REFINE, out["logZ"], out["n_valid"], out["bpmf"],
+                              out["dG"], stream)
+                b.record(stream)
                 torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                if name == "trained":
-                    pred = net.predict(PP.features(sess.ctx, lh, J, h, dev))
-                else:
-                    pred = torch.zeros(J, dtype=torch.float32, device=dev)
-                Bp, _, _ = PP.proposal_bpmf(sess.ctx, recs, w.kT, coords, params, pred, M, mix=mix, seed=seed,
-                                            n_tot=n_tot)
-                torch.cuda.synchronize()
-                times.append(time.perf_counter() - t0)
-                errs.append(np.abs(Bp - B_full).max())
-            res[name] = {"median_abs_dB_kcal": float(np.median(errs)), "max_abs_dB_kcal": float(np.max(errs)),
-                         "ms": float(np.median(times) * 1e3), "speedup_vs_full": float(t_full / np.median(times))}
+                ts.append(a.elapsed_time(b))
+            res["graph" if graph else "launches"] = float(np.mean(ts))
+        pkg.bpmf_set_graph_mode(sess.ctx, False)
+        pkg.bpmf_profile_enable(sess.ctx, True)
+        pkg.bpmf_eval(sess.ctx, lh, recs, kT, pkg.BPMF_MODE_REFINE, out["logZ"], out["n_valid"], out["bpmf"], out["dG"],
+                      stream)
+        torch.cuda.synchronize()
+        prof = pkg.bpmf_profile(sess.ctx)
+        pkg.bpmf_profile_enable(sess.ctx, False)
+        lz, nv = out["logZ"].cpu().numpy(), out["n_valid"].cpu().numpy()
+        # a seeded sample of (ligand, configuration) pairs, every receptor
+        rng = np.random.default_rng(2002)
+        n_s = max(1, int(sample_frac * T))
+        pick = np.sort(rng.choice(T, n_s, replace=False))
+        offs = np.cumsum([0] + [l.coords.shape[0] for l in ligs])
+        t0 = time.perf_counter()
+        dz, exact = 0.0, True
+        for gidx in pick:
+            li = int(np.searchsorted(offs, gidx, side="right") - 1)
+            j = int(gidx - offs[li])
+            l = ligs[li]
+            ref = oracle.evaluate(recs_in, l.coords[j:j + 1], l.params.q, l.params.eps, l.params.R, kT)
+            exact &= bool(np.array_equal(ref["n_valid"][0], nv[gidx]))
+            fin = np.isfinite(ref["logZ"][0])
+            if fin.any():
+                dz = max(dz, float(np.abs(lz[gidx][fin] - ref["logZ"][0][fin]).max() * kT))
+        t_or = time.perf_counter() - t0
+        poses = int(nv.sum())
+        t_best = min(res.values())
+        return {"workload": f"batched uneven: {n_lig} ligands of 8-60 atoms x {n_conf} configurations x {K} receptor "
+                            "conformations of 64^3-112^3 at 0.25 A, sites 24^3-40^3, one bpmf_eval (refined form)",
+                "ms_per_eval": res["launches"], "ms_per_eval_graph": res["graph"], "poses_per_eval": poses,
+                "value": poses / (t_best / 1e3), "unit": "pose energies/s",
+                "bpmfs_per_s": n_lig * K / (t_best / 1e3), "status": int(rc),
+                "gpu_launches": int(sum(n for _, n in prof.values())),
+                "kernels_ms": {k: v[0] for k, v in prof.items()},
+                "accuracy_vs_oracle": {"sample": f"{n_s} seeded (ligand, configuration) pairs x {K} receptors",
+                                       "counts_exact": exact, "max_kT_dlogZ_kcal": dz, "oracle_s": t_or}}
+    finally:
         pkg.bpmf_ligand_free(lh)
-        net.free()
-        return {"budget": budget_frac, "full_enumeration_ms": t_full * 1e3, "train_s": t_train,
-                "final_train_loss": float(losses[-1]), "held_out": "ligand seeds 7001/7002, 2000 configurations",
-                **res}
+        for r in recs:
+            pkg.bpmf_receptor_free(r)
+
+
+def learned_proposal_leg(torch, pkg, sess, recs_in, kT, n_train=14, n_val=4, n_test=4, j_train=2000, j_test=20000,
+                         budget_frac=0.1, seeds=8):
+    """Learned proposal over configuration features on the batched receptor
+    set (10 conformations, 64^3-112^3): ligands drawn as in the batched
+    workload (8-60 atoms).  n_train fully enumerated ligands train the MLP on
+    their configurations' log weights (relative to each ligand's largest,
+    clipped at -50); n_val more choose the temperature by the exact
+    importance-sampling variance; n_test held-out ligands of j_test
+    configurations are estimated from budget_frac of their configurations.
+    Every estimate is judged against the full enumeration (refined form)."""
+    from paper_1708_07045_gb300 import proposal as PP
+    rng = np.random.default_rng(4004)
+    natoms = rng.integers(8, 61, n_train + n_val + n_test)
+    mode = pkg.BPMF_MODE_REFINE
+    h = recs_in[0].h
+    K = len(recs_in)
+    recs = [pkg.bpmf_receptor_load(sess.ctx, r.grids, r.h, r.origin, r.site_lo, r.site_n) for r in recs_in]
+
+    def enumerate_ligand(lig):
+        J = lig.coords.shape[0]
+        lh = pkg.bpmf_ligand_batch(sess.ctx, [lig.params.n_atoms], [J], np.ascontiguousarray(lig.coords.reshape(-1, 3)),
+                                   lig.params.q, lig.params.eps, lig.params.R)
+        logZ = torch.empty((J, K), dtype=torch.float64, device="cuda")
+        nv = torch.empty((J, K), dtype=torch.int64, device="cuda")
+        B = torch.empty((1, K), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pkg.bpmf_eval(sess.ctx, lh, recs, kT, mode, logZ, nv, B, None)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        X = PP.features(sess.ctx, lh, J, h, "cuda")
+        pkg.bpmf_ligand_free(lh)
+        ls, t = PP.config_targets(sess.ctx, logZ, nv)
+        return {"X": X, "ls": ls, "t": t, "B": B.cpu().numpy()[0], "n_tot": nv.sum(0).cpu().numpy(), "s": dt}
+
+    try:
+        t0 = time.perf_counter()
+        data = []
+        for i in range(n_train + n_val + n_test):
+            J = j_train if i < n_train + n_val else j_test
+            lig = synth.LigandInput(synth.ligand_params(4100 + 2 * i, int(natoms[i])),
+                                    synth.ligand_configs(4101 + 2 * i, int(natoms[i]), J))
+            data.append((lig, enumerate_ligand(lig)))
+        t_enum = time.perf_counter() - t0
+        Xtr = torch.cat([d["X"] for _, d in data[:n_train]]).contiguous()
+        ttr = torch.cat([d["t"] for _, d in data[:n_train]]).contiguous()
+        net = PP.LearnedProposal(sess.ctx, PP.fit_norm(Xtr.cpu().numpy(), ttr.cpu().numpy()))
+        try:
+            t0 = time.perf_counter()
+            losses = net.fit(Xtr, ttr, epochs=20, batch=256, lr=1e-3)
+            t_train = time.perf_counter() - t0
+            val = data[n_train:n_train + n_val]
+            tau = PP.choose_tau(sess.ctx, [net.predict(d["X"]) for _, d in val], [d["ls"] for _, d in val])
+            tests = []
+            for lig, d in data[n_train + n_val:]:
+                J = lig.coords.shape[0]
+                M = int(budget_frac * J)
+                coords = torch.from_numpy(lig.coords).cuda()
+                params = [torch.from_numpy(getattr(lig.params, k)).cuda() for k in ("q", "eps", "R")]
+                pred = net.predict(d["X"])
+                zero = torch.zeros(J, device="cuda")
+                row = {"atoms": lig.params.n_atoms, "configurations": J, "draws": M,
+                       "full_enumeration_s": d["s"]}
+                top = int(torch.argmax(d["ls"]).item())
+                for name, p, mix in (("trained", pred, 0.8), ("uniform", zero, 0.0)):
+                    chi2 = PP.proposal_chi2(sess.ctx, p, d["ls"], mix, tau)
+                    errs, times, zr = [], [], []
+                    for seed in range(seeds):
+                        torch.cuda.synchronize()
+                        ts = time.perf_counter()
+                        Bp, idx, _ = PP.proposal_bpmf(sess.ctx, recs, kT, coords, params, p, M, mix=mix, seed=seed,
+                                                     mode=mode, n_tot=d["n_tot"], tau=tau)
+                        torch.cuda.synchronize()
+                        times.append(time.perf_counter() - ts)
+                        errs.append(float(np.max(np.abs(Bp - d["B"]))))
+                        # Z_hat / Z for the receptors, from the BPMF difference
+                        zr.append(float(np.median(np.exp(-(Bp - d["B"]) / kT))))
+                    med = float(np.median(errs))
+                    row[name] = {"chi2": chi2, "effective_draws": M / (1.0 + chi2),
+                                 "median_max_abs_dB_kcal": med, "median_Zhat_over_Z": float(np.median(zr)),
+                                 "meets_0.01": bool(med <= 0.01), "s": float(np.median(times)),
+                                 "speedup_vs_full": (d["s"] / float(np.median(times))) if med <= 0.01 else None,
+                                 "q_of_top_configuration_x_J": float(proposal_q(pred if name == "trained" else zero,
+                                                                                mix, tau)[top] * J)}
+                row["variance_ratio_uniform_over_trained"] = (1.0 + row["uniform"]["chi2"]) / (1.0 + row["trained"]["chi2"])
+                tests.append(row)
+        finally:
+            net.free()
+        return {"workload": "learned proposal over the batched receptor set: 10 conformations 64^3-112^3, "
+                            f"ligands of 8-60 atoms; train {n_train} x {j_train}, temperature on {n_val} x {j_train}, "
+                            f"held out {n_test} x {j_test} configurations at a {budget_frac:.0%} budget, {seeds} seeds",
+                "form": "refine", "tau": tau, "enumeration_s": t_enum, "train_s": t_train,
+                "final_train_loss": float(losses[-1]), "held_out": tests,
+                "note": "chi2 is the exact relative variance of one importance draw (from the full enumeration); "
+                        "speedup_vs_full is reported only where the median error meets 0.01 kcal/mol"}
     finally:
         for r in recs:
             pkg.bpmf_receptor_free(r)
@@ -777,8 +909,14 @@ def run_ours(args):
         surface = whole_surface_leg(torch, pkg, sess, dev, stream, max(1, args.steps // 2))
 
     proposal = None
+    uneven = None
+    if rank == 0 and not (args.no_proposal and args.no_batched):
+        uneven = uneven_receptors()
     if rank == 0 and not args.no_proposal:
-        proposal = learned_proposal_leg(torch, pkg, sess, w, dev, stream, res_chosen, coords, params)
+        proposal = learned_proposal_leg(torch, pkg, sess, uneven, w.kT)
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_leg(torch, pkg, sess, uneven, w.kT, stream, max(1, args.steps // 2))
 
     cufft = None
     if rank == 0 and not args.no_cufft:
@@ -873,6 +1011,7 @@ def run_ours(args):
                 "whole_surface": surface,
                 "bootstrap": boot,
                 "learned_proposal": proposal,
+                "batched_uneven": batched,
                 "cufft_fp32_path": cufft,
                 "accuracy_vs_oracle": acc,
                 "e2e": {"value": n_poses * world / e2e_t, "unit": "pose energies/s", "h2d_bytes_per_step": int(h2d),
@@ -904,6 +1043,7 @@ def main():
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal leg")
     ap.add_argument("--no-occupancy", action="store_true", help="skip the steric-clash (occupancy grid) leg")
     ap.add_argument("--no-surface", action="store_true", help="skip the whole-surface 248^3 leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-workload leg")
     ap.add_argument("--n-conf", type=int, default=N_CONF,
                     help="configurations per step (default: the full workload; smaller values are for profiling)")
     args = ap.parse_args()

@@ -343,8 +343,9 @@ int bpmf_valid_counts(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, in
 /* ------------------------------------------------------------------------
  * Learned proposal over configurations.  A small MLP predicts, from a
  * configuration's features, log sum_k S_jk (its weight in the sample mean of
- * Eq. sample_mean_BPMF).  Configurations are then drawn from
- * q_j = mix * softmax(pred)_j + (1 - mix) / J, and the BPMF is estimated by
+ * Eq. sample_mean_BPMF) relative to its ligand's largest, clipped below
+ * (bpmf_config_targets).  Configurations are then drawn from
+ * q_j = mix * softmax(pred / tau)_j + (1 - mix) / J, and the BPMF is estimated by
  * importance weighting, which stays unbiased for Z_k = sum_j S_jk thanks to
  * the uniform component.  The full enumeration (bpmf_eval) is the fallback and
  * the judge of its error.
@@ -394,13 +395,34 @@ int bpmf_mlp_forward(bpmf_ctx_t ctx, bpmf_mlp_t mlp, const float *X, int B, floa
 int bpmf_mlp_train_step(bpmf_ctx_t ctx, bpmf_mlp_t mlp, const float *X, const float *t, int B, float lr, int apply,
                         float *loss, float *grads, void *stream);
 
-/* bpmf_proposal_sample -- q = mix softmax(pred) + (1 - mix)/J over J
+/* bpmf_proposal_sample -- q = mix softmax(pred / tau) + (1 - mix)/J over J
  * configurations (FP64); for each caller-supplied uniform u_s in [0,1) the
  * index of the first configuration whose cumulative q exceeds u_s, and q of
- * that configuration.  pred [J] float32, u [M] float64, idx [M] int32, q_s [M]
+ * that configuration.  tau > 0 tempers the prediction (large tau: closer to
+ * uniform).  pred [J] float32, u [M] float64, idx [M] int32, q_s [M]
  * float64: DEVICE memory.  Stream ordered.  Errors: INVALID_ARG, OOM, CUDA. */
-int bpmf_proposal_sample(bpmf_ctx_t ctx, const float *pred, int J, double mix, const double *u, int M, int *idx,
-                         double *q_s, void *stream);
+int bpmf_proposal_sample(bpmf_ctx_t ctx, const float *pred, int J, double mix, double tau, const double *u, int M,
+                         int *idx, double *q_s, void *stream);
+
+/* bpmf_config_targets -- training targets of the proposal for ONE ligand's J
+ * configurations (FP64): ls_j = ln sum_k n_jk exp(logZ_jk) (the
+ * configuration's weight in the sample mean of Eq. sample_mean_BPMF, -inf
+ * without a valid translation) and t_j = max(ls_j - max_j' ls_j', -clip)
+ * (float32; the proposal needs only the ranking within a ligand).
+ * logZ, n_valid [J][K] as bpmf_eval returns them; ls [J] float64, t [J]
+ * float32: DEVICE memory.  Errors: INVALID_ARG (clip <= 0), CUDA. */
+int bpmf_config_targets(bpmf_ctx_t ctx, const double *logZ, const int64_t *n_valid, int J, int K, double clip,
+                        double *ls, float *t, void *stream);
+
+/* bpmf_proposal_chi2 -- exact relative variance of the importance-sampling
+ * estimate of Z = sum_j exp(ls_j) from ONE draw of the proposal q of
+ * bpmf_proposal_sample (mix, tau): chi2 = sum_j exp(2 ls_j) / (q_j Z^2) - 1
+ * (M independent draws: chi2 / M).  Used to choose tau on fully enumerated
+ * ligands and to report a proposal's quality without sampling noise.
+ * pred [J] float32, ls [J] float64, chi2 [1] float64: DEVICE memory.
+ * Errors: INVALID_ARG, CUDA. */
+int bpmf_proposal_chi2(bpmf_ctx_t ctx, const float *pred, const double *ls, int J, double mix, double tau, double *chi2,
+                       void *stream);
 
 /* bpmf_proposal_bpmf -- importance-weighted BPMF per receptor from M sampled
  * configurations: Z_k = (1/M) sum_s S_{j_s k} / q_s with S = exp(logZ) n,

@@ -5,7 +5,10 @@ shares no code with the CUDA library).
   with mean-squared-error loss in normalised units; ``bf16=True`` rounds both
   operands of every matrix product to bfloat16 (round to nearest even) exactly
   where the GPU kernels do, everything else in FP64.
-* ``proposal`` -- q = mix softmax(pred) + (1 - mix)/J and inverse-CDF draws.
+* ``proposal`` -- q = mix softmax(pred / tau) + (1 - mix)/J and inverse-CDF draws.
+* ``config_targets`` -- per-configuration weights ls_j = ln sum_k S_jk of one
+  ligand and the training targets max(ls_j - max ls, -clip).
+* ``chi2`` -- exact relative variance of one importance-sampling draw of Z.
 * ``is_bpmf`` -- importance-weighted BPMF (Eq. sample_mean_BPMF with
   configurations drawn from q): Z_k ~ (1/M) sum_s S_{j_s k}/q_{j_s},
   B_k = -kT [ln Z_k - ln N_k].
@@ -84,10 +87,35 @@ def mlp_grads(params, norm, X, t, n_in, width, depth, bf16_ops=True):
     return loss, flat
 
 
-def proposal(pred, mix):
-    p = np.asarray(pred, dtype=np.float64)
+def proposal(pred, mix, tau=1.0):
+    p = np.asarray(pred, dtype=np.float64) / tau
     w = np.exp(p - p.max())
     return mix * w / w.sum() + (1.0 - mix) / p.size
+
+
+def config_targets(logZ, n_valid, clip):
+    """(ls [J], t [J]): ls_j = ln sum_k n_jk exp(logZ_jk) (-inf without a valid
+    translation) and t_j = max(ls_j - max ls, -clip) for one ligand."""
+    logZ = np.asarray(logZ, dtype=np.float64)
+    n = np.asarray(n_valid, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        terms = np.where(n > 0, logZ + np.log(np.maximum(n, 1)), -np.inf)
+    ls = logsumexp(terms, axis=1)
+    ls = np.where(np.isfinite(ls), ls, -np.inf)
+    mx = ls.max()
+    t = np.where(np.isfinite(ls), np.maximum(ls - mx, -clip), -clip) if np.isfinite(mx) else np.full(ls.shape, -clip)
+    return ls, t
+
+
+def chi2(pred, ls, mix, tau):
+    """sum_j S_j^2 / (q_j Z^2) - 1 with S_j = exp(ls_j), Z = sum S_j, q the
+    proposal: the relative variance of (S_j / q_j) / Z for one draw j ~ q."""
+    q = proposal(pred, mix, tau)
+    ls = np.asarray(ls, dtype=np.float64)
+    ok = np.isfinite(ls)
+    w = np.exp(ls[ok] - ls[ok].max())
+    w /= w.sum()
+    return float(np.sum(w * w / q[ok]) - 1.0)
 
 
 def draw(q, u):

@@ -129,7 +129,9 @@ _SIGS = {
     "bpmf_mlp_get_params": (_I, [_P, _P]),
     "bpmf_mlp_forward": (_I, [_P, _P, _P, _I, _P, _P]),
     "bpmf_mlp_train_step": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, _I, _P, _P, _P]),
-    "bpmf_proposal_sample": (_I, [_P, _P, _I, _D, _P, _I, _P, _P, _P]),
+    "bpmf_proposal_sample": (_I, [_P, _P, _I, _D, _D, _P, _I, _P, _P, _P]),
+    "bpmf_config_targets": (_I, [_P, _P, _P, _I, _I, _D, _P, _P, _P]),
+    "bpmf_proposal_chi2": (_I, [_P, _P, _P, _I, _D, _D, _P, _P]),
     "bpmf_proposal_bpmf": (_I, [_P, _P, _P, _P, _I, _I, _P, _D, _P, _P]),
     "bpmf_sir_poses": (_I, [_P, _P, _I, _P, _I, _I, _D, ctypes.c_uint, _P, _P, _P, _P, _I, _P, _P, _P]),
     "bpmf_bootstrap": (_I, [_P, _P, _P, _I, _I, _D, _D, _P, _I, _P, _P, _P]),
@@ -420,12 +422,28 @@ def bpmf_mlp_train_step(ctx, mlp, X, t, lr, apply=True, grads=None, stream=None)
     return float(loss[0])
 
 
-def bpmf_proposal_sample(ctx, pred, mix, u, idx, q_s, stream=None):
+def bpmf_proposal_sample(ctx, pred, mix, u, idx, q_s, stream=None, tau=1.0):
     J = int(tuple(pred.shape)[0])
     M = int(tuple(u.shape)[0])
-    _check(lib().bpmf_proposal_sample(ctx, _ptr(pred, np.float32), J, float(mix), _ptr(u, np.float64), M,
+    _check(lib().bpmf_proposal_sample(ctx, _ptr(pred, np.float32), J, float(mix), float(tau), _ptr(u, np.float64), M,
                                       _ptr(idx, np.int32), _ptr(q_s, np.float64), _stream(stream)),
            "bpmf_proposal_sample", ctx)
+
+
+def bpmf_config_targets(ctx, logZ, n_valid, clip, ls, t, stream=None):
+    """logZ float64 [J, K], n_valid int64 [J, K] -> ls float64 [J], t float32 [J] (device)."""
+    J, K = (int(v) for v in tuple(logZ.shape))
+    _check(lib().bpmf_config_targets(ctx, _ptr(logZ, np.float64), _ptr(n_valid, np.int64), J, K, float(clip),
+                                     _ptr(ls, np.float64), _ptr(t, np.float32), _stream(stream)),
+           "bpmf_config_targets", ctx)
+
+
+def bpmf_proposal_chi2(ctx, pred, ls, mix, tau, out, stream=None):
+    """Exact relative variance of one importance-sampling draw; out float64 [1] (device)."""
+    J = int(tuple(pred.shape)[0])
+    _check(lib().bpmf_proposal_chi2(ctx, _ptr(pred, np.float32), _ptr(ls, np.float64), J, float(mix), float(tau),
+                                    _ptr(out, np.float64), _stream(stream)),
+           "bpmf_proposal_chi2", ctx)
 
 
 def bpmf_proposal_bpmf(ctx, logZ_s, n_s, q_s, n_tot, kT, bpmf, stream=None):

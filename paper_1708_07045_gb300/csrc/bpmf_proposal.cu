@@ -309,19 +309,45 @@ int bpmf_mlp_train_step(bpmf_ctx_t c, bpmf_mlp_t net, const float *X, const floa
   return BPMF_OK;
 }
 
-int bpmf_proposal_sample(bpmf_ctx_t c, const float *pred, int J, double mix, const double *u, int M, int *idx,
-                         double *q_s, void *stream) {
-  if (!c || !pred || !u || !idx || !q_s || J < 1 || M < 0 || !(mix >= 0.0 && mix <= 1.0))
+int bpmf_proposal_sample(bpmf_ctx_t c, const float *pred, int J, double mix, double tau, const double *u, int M,
+                         int *idx, double *q_s, void *stream) {
+  if (!c || !pred || !u || !idx || !q_s || J < 1 || M < 0 || !(mix >= 0.0 && mix <= 1.0) || !(tau > 0.0))
     return BPMF_ERR_INVALID_ARG;
   Dev dv(bpmf_internal_device(c));
   cudaStream_t st = (cudaStream_t)stream;
   double *buf = nullptr;
   try {
     PCK(cudaMallocAsync(&buf, sizeof(double) * 2 * J, st));
-    PCK(launch_proposal(pred, J, mix, u, M, buf, buf + J, idx, q_s, st));
+    PCK(launch_proposal(pred, J, mix, tau, u, M, buf, buf + J, idx, q_s, st));
     PCK(cudaFreeAsync(buf, st));
   } catch (PFail f) {
     if (buf) cudaFreeAsync(buf, st);
+    return fail(c, f.code);
+  }
+  return BPMF_OK;
+}
+
+int bpmf_config_targets(bpmf_ctx_t c, const double *logZ, const int64_t *n_valid, int J, int K, double clip,
+                        double *ls, float *t, void *stream) {
+  if (!c || !logZ || !n_valid || !ls || !t || J < 1 || K < 1 || !(clip > 0.0)) return BPMF_ERR_INVALID_ARG;
+  Dev dv(bpmf_internal_device(c));
+  try {
+    PCK(launch_config_targets(logZ, reinterpret_cast<const long long *>(n_valid), J, K, clip, ls, t,
+                              (cudaStream_t)stream));
+  } catch (PFail f) {
+    return fail(c, f.code);
+  }
+  return BPMF_OK;
+}
+
+int bpmf_proposal_chi2(bpmf_ctx_t c, const float *pred, const double *ls, int J, double mix, double tau, double *chi2,
+                       void *stream) {
+  if (!c || !pred || !ls || !chi2 || J < 1 || !(mix >= 0.0 && mix <= 1.0) || !(tau > 0.0))
+    return BPMF_ERR_INVALID_ARG;
+  Dev dv(bpmf_internal_device(c));
+  try {
+    PCK(launch_proposal_chi2(pred, ls, J, mix, tau, chi2, (cudaStream_t)stream));
+  } catch (PFail f) {
     return fail(c, f.code);
   }
   return BPMF_OK;

@@ -679,9 +679,19 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
           if (lane == 0) base = atomicAdd(&a.rs.cnt[jk], __popc(bal));
           base = __shfl_sync(0xffffffffu, base, 0);
           const int slot = base + __popc(bal & ((1u << lane) - 1u));
-          if (keep && slot < a.rs.cap) list[slot] = Cand{t0 + (unsigned)idx, ef, s_hi(xs[idx])};
+          if (keep && slot < a.rs.cap) {
+            list[slot] = Cand{t0 + (unsigned)idx, ef, s_hi(xs[idx])};
+            // k_refine accounts for the listed translations: this plane's
+            // partial leaves them out (one that did not fit the list stays
+            // in, and the overflow sends the ligand to the float-pair form)
+            xs[idx] = s_mk<T>(-CUDART_INF_F, 0.f);
+          }
         }
       }
+      __syncthreads();
+      vmax = s_mk<T>(-CUDART_INF_F, 0.f);  // the largest of what is left
+      for (int idx = threadIdx.x; idx < nS; idx += blockDim.x)
+        if (ff_gt(xs[idx], vmax)) vmax = xs[idx];
     }
     // block max of the chunk
     for (int o = 16; o > 0; o >>= 1) {
@@ -800,8 +810,8 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
   double Mx = -CUDART_INF;
   for (int c = 0; c < a.S0; ++c)
     if (pp[c].z > 0.f) Mx = fmax(Mx, (double)pp[c].x + (double)pp[c].y);
-  // refined form: the pair's correction replaces the FP32 weights of its
-  // refined translations (held by the plane partials) by their exact weights
+  // refined form: the pair's listed translations (left out of the plane
+  // partials), exact where they were refined
   double X = -CUDART_INF;  // largest exact -E/kT
   float4 rc{0.f, 0.f, 0.f, 0.f};
   if (a.part_ref) {
@@ -816,12 +826,7 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
   if (Mx > -CUDART_INF) {
     for (int c = 0; c < a.S0; ++c)
       if (pp[c].z > 0.f) s += (double)pp[c].z * exp((double)pp[c].x + (double)pp[c].y - Mx);
-    if (rc.z > 0.f) {
-      const double e = exp((double)rc.x + (double)rc.y - Mx);
-      const double se = (double)rc.z * e;
-      s = s - (double)rc.w * e + se;
-      if (s < se) s = se;  // the translations left at FP32 weigh >= 0 (rounding guard)
-    }
+    if (rc.z > 0.f) s += (double)rc.z * exp((double)rc.x + (double)rc.y - Mx);
   }
   // the dominant state: the largest -E/kT, exact where the pair was refined
   const double Xd = X > -CUDART_INF ? X : Mx;

@@ -160,8 +160,8 @@ struct RefTab {            // one receptor's grids, FP32 [3][N0][N1][N2]
 };
 
 // A translation kept for the exact re-evaluation: window index
-// t = (s0 S1 + s1) S2 + s2, its FP32 energy e and the FP32 -E/kT value x whose
-// weight exp(x - M) the plane's LSE partial holds.
+// t = (s0 S1 + s1) S2 + s2, its FP32 energy e and its FP32 -E/kT value x (the
+// weight it keeps when it lies above the final threshold).
 struct Cand {
   unsigned t;
   float e, x;
@@ -171,9 +171,8 @@ struct Cand {
 // resets it; every k_zinv CTA lowers the pair's running FP32 minimum and
 // appends the translations of its plane that lie within the window of that
 // running minimum (a superset of those within the window of the final
-// minimum), while its LSE partial keeps every translation at its FP32
-// weight; k_refine reads the final minimum and the lists and writes the
-// exact-minus-FP32 correction of each pair's sum, which the merge applies.
+// minimum), and leaves them out of its LSE partial; k_refine reads the final
+// minimum and the lists and writes each pair's partial over its list.
 struct RefineState {
   const float *win;        // [K] W + 2B per receptor (kcal/mol)
   const float *bnd;        // [K] B per receptor times the check scale (certificate threshold)
@@ -212,8 +211,8 @@ struct RefineArgs {
   float kT;                // kcal/mol
   float nikT_hi, nikT_lo;  // -1 / kT as a float pair
   int K, S0, S1, S2;
-  float4 *part_ref;        // [batch][K][2] per pair: {level M hi, lo, sum of exact weights, sum of FP32
-                           // weights} over the refined translations, then {max exact -E/kT hi, lo, 0, 0}
+  float4 *part_ref;        // [batch][K][2] per pair: {level M hi, lo, sum of weights, 0} over the listed
+                           // translations (exact below the threshold), then {max exact -E/kT hi, lo, 0, 0}
   double *export_E;        // optional, batch entry 0, receptor 0: [S0][S1][S2] (exact where refined)
 };
 

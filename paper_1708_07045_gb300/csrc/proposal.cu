@@ -341,14 +341,15 @@ cudaError_t launch_adam(float *w, const float *gw, float *m, float *v, long long
 }
 
 // ---------------------------------------------------------------- proposal
-// q_j = mix * softmax(pred)_j + (1 - mix) / J in FP64; cumulative sums; then
-// index_s = first j with cdf_j > u_s (inverse CDF of caller-supplied uniforms).
-__global__ void k_proposal(const float *pred, int J, double mix, const double *u, int M, double *q, double *cdf,
-                           int *idx, double *q_s) {
+// q_j = mix * softmax(pred / tau)_j + (1 - mix) / J in FP64; cumulative sums;
+// then index_s = first j with cdf_j > u_s (inverse CDF of caller-supplied
+// uniforms).
+__global__ void k_proposal(const float *pred, int J, double mix, double tau, const double *u, int M, double *q,
+                           double *cdf, int *idx, double *q_s) {
   __shared__ double s_d[256];
   // max
   double mx = -CUDART_INF;
-  for (int j = threadIdx.x; j < J; j += blockDim.x) mx = fmax(mx, (double)pred[j]);
+  for (int j = threadIdx.x; j < J; j += blockDim.x) mx = fmax(mx, (double)pred[j] / tau);
   s_d[threadIdx.x] = mx;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -358,7 +359,7 @@ __global__ void k_proposal(const float *pred, int J, double mix, const double *u
   const double M0 = s_d[0];
   __syncthreads();
   double acc = 0.0;
-  for (int j = threadIdx.x; j < J; j += blockDim.x) acc += exp((double)pred[j] - M0);
+  for (int j = threadIdx.x; j < J; j += blockDim.x) acc += exp((double)pred[j] / tau - M0);
   s_d[threadIdx.x] = acc;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -366,7 +367,8 @@ __global__ void k_proposal(const float *pred, int J, double mix, const double *u
     __syncthreads();
   }
   const double Zs = s_d[0];
-  for (int j = threadIdx.x; j < J; j += blockDim.x) q[j] = mix * exp((double)pred[j] - M0) / Zs + (1.0 - mix) / J;
+  for (int j = threadIdx.x; j < J; j += blockDim.x)
+    q[j] = mix * exp((double)pred[j] / tau - M0) / Zs + (1.0 - mix) / J;
   __syncthreads();
   if (threadIdx.x == 0) {  // sequential prefix sum: deterministic, J is modest
     double c = 0.0;
@@ -390,9 +392,116 @@ __global__ void k_proposal(const float *pred, int J, double mix, const double *u
   }
 }
 
-cudaError_t launch_proposal(const float *pred, int J, double mix, const double *u, int M, double *q, double *cdf,
-                            int *idx, double *q_s, cudaStream_t st) {
-  k_proposal<<<1, 256, 0, st>>>(pred, J, mix, u, M, q, cdf, idx, q_s);
+cudaError_t launch_proposal(const float *pred, int J, double mix, double tau, const double *u, int M, double *q,
+                            double *cdf, int *idx, double *q_s, cudaStream_t st) {
+  k_proposal<<<1, 256, 0, st>>>(pred, J, mix, tau, u, M, q, cdf, idx, q_s);
+  return cudaGetLastError();
+}
+
+// Training targets of the proposal for one ligand (FP64 log-sum-exp over
+// receptors, Eq. sample_mean_BPMF's per-configuration weight):
+//   ls_j = ln sum_k n_jk exp(log Z_jk)   (-inf without a valid translation)
+//   t_j  = max(ls_j - max_j' ls_j', -clip)
+// The proposal only needs the ranking within a ligand; the offset between
+// ligands and the tail below -clip carry no information for it.
+__global__ void k_config_targets(const double *logZ, const long long *n_valid, int J, int K, double clip,
+                                 double *ls, float *t) {
+  __shared__ double s_d[256];
+  double mx = -CUDART_INF;
+  for (int j = threadIdx.x; j < J; j += blockDim.x) {
+    double m = -CUDART_INF;
+    for (int k = 0; k < K; ++k)
+      if (n_valid[(long long)j * K + k] > 0)
+        m = fmax(m, logZ[(long long)j * K + k] + log((double)n_valid[(long long)j * K + k]));
+    double v = -CUDART_INF;
+    if (m > -CUDART_INF) {
+      double acc = 0.0;
+      for (int k = 0; k < K; ++k)
+        if (n_valid[(long long)j * K + k] > 0)
+          acc += exp(logZ[(long long)j * K + k] + log((double)n_valid[(long long)j * K + k]) - m);
+      v = m + log(acc);
+    }
+    ls[j] = v;
+    mx = fmax(mx, v);
+  }
+  s_d[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) s_d[threadIdx.x] = fmax(s_d[threadIdx.x], s_d[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double M0 = s_d[0];
+  for (int j = threadIdx.x; j < J; j += blockDim.x) {
+    const double v = ls[j];
+    t[j] = (float)((M0 > -CUDART_INF && v > -CUDART_INF) ? fmax(v - M0, -clip) : -clip);
+  }
+}
+
+cudaError_t launch_config_targets(const double *logZ, const long long *n_valid, int J, int K, double clip, double *ls,
+                                  float *t, cudaStream_t st) {
+  k_config_targets<<<1, 256, 0, st>>>(logZ, n_valid, J, K, clip, ls, t);
+  return cudaGetLastError();
+}
+
+// Exact relative variance of the importance-sampling estimate of
+// Z = sum_j S_j from one draw of q (FP64):  chi2 = sum_j S_j^2 / (q_j Z^2) - 1,
+// with q_j = mix softmax(pred / tau)_j + (1 - mix) / J and S_j = exp(ls_j)
+// (-inf: S_j = 0).  M independent draws have relative variance chi2 / M.
+__global__ void k_proposal_chi2(const float *pred, const double *ls, int J, double mix, double tau, double *out) {
+  __shared__ double s_d[256], s_e[256];
+  double mp = -CUDART_INF, ms = -CUDART_INF;
+  for (int j = threadIdx.x; j < J; j += blockDim.x) {
+    mp = fmax(mp, (double)pred[j] / tau);
+    ms = fmax(ms, ls[j]);
+  }
+  s_d[threadIdx.x] = mp;
+  s_e[threadIdx.x] = ms;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s_d[threadIdx.x] = fmax(s_d[threadIdx.x], s_d[threadIdx.x + o]);
+      s_e[threadIdx.x] = fmax(s_e[threadIdx.x], s_e[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  const double MP = s_d[0], MS = s_e[0];
+  __syncthreads();
+  double zp = 0.0, zs = 0.0;
+  for (int j = threadIdx.x; j < J; j += blockDim.x) {
+    zp += exp((double)pred[j] / tau - MP);
+    if (ls[j] > -CUDART_INF) zs += exp(ls[j] - MS);
+  }
+  s_d[threadIdx.x] = zp;
+  s_e[threadIdx.x] = zs;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s_d[threadIdx.x] += s_d[threadIdx.x + o];
+      s_e[threadIdx.x] += s_e[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  const double ZP = s_d[0], ZS = s_e[0];
+  __syncthreads();
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < J; j += blockDim.x) {
+    if (!(ls[j] > -CUDART_INF)) continue;
+    const double q = mix * exp((double)pred[j] / tau - MP) / ZP + (1.0 - mix) / J;
+    const double w = exp(ls[j] - MS) / ZS;
+    acc += w * w / q;
+  }
+  s_d[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) s_d[threadIdx.x] += s_d[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = ZS > 0.0 ? s_d[0] - 1.0 : CUDART_INF;
+}
+
+cudaError_t launch_proposal_chi2(const float *pred, const double *ls, int J, double mix, double tau, double *out,
+                                 cudaStream_t st) {
+  k_proposal_chi2<<<1, 256, 0, st>>>(pred, ls, J, mix, tau, out);
   return cudaGetLastError();
 }
 

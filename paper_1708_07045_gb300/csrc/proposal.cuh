@@ -38,8 +38,12 @@ cudaError_t launch_adam(float *w, const float *gw, float *m, float *v, long long
 cudaError_t launch_mask_relu_grad(float *D, const float *Z, long long n, cudaStream_t st);
 cudaError_t launch_affine(const float *x, const float *shift, const float *scale, int B, int N, int invert, float *out,
                           cudaStream_t st);
-cudaError_t launch_proposal(const float *pred, int J, double mix, const double *u, int M, double *q, double *cdf,
-                            int *idx, double *q_s, cudaStream_t st);
+cudaError_t launch_proposal(const float *pred, int J, double mix, double tau, const double *u, int M, double *q,
+                            double *cdf, int *idx, double *q_s, cudaStream_t st);
+cudaError_t launch_config_targets(const double *logZ, const long long *n_valid, int J, int K, double clip, double *ls,
+                                  float *t, cudaStream_t st);
+cudaError_t launch_proposal_chi2(const float *pred, const double *ls, int J, double mix, double tau, double *out,
+                                 cudaStream_t st);
 cudaError_t launch_is_estimate(const double *logZ_s, const long long *n_s, const double *q_s, int M, int K,
                                const long long *n_tot, double kT, double *bpmf, cudaStream_t st);
 cudaError_t launch_sir_configs(const double *logZ, const long long *nvalid, int J, int K, int k, const double *u,

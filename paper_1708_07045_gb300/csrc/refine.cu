@@ -17,20 +17,23 @@
 //   k_zinv         -- (kernels.cu) each plane lowers its pair's running
 //                     minimum and appends the translations within W + 2B of
 //                     it to the pair's list (a superset of those within
-//                     W + 2B of the final minimum); its LSE partial keeps
-//                     every translation at its FP32 weight;
+//                     W + 2B of the final minimum); its LSE partial leaves
+//                     the listed translations out;
 //   k_refine       -- one CTA per pair: the final threshold from the final
 //                     minimum; every listed translation below it is
 //                     re-evaluated exactly (a warp per translation, lanes
 //                     over atoms) and checked against its FP32 energy
-//                     (|E_fp32 - E_exact| <= B, the certificate); the pair's
-//                     correction {level, sum of exact weights, sum of the
-//                     same translations' FP32 weights} goes to the merge,
-//                     which replaces the one by the other.
-// Both sums are over the same translations, fixed by the final threshold,
-// in order-independent fixed point, so results do not depend on the order in
-// which the planes ran.  A failed check or an overflowing list sets a flag
-// that makes bpmf_eval recompute the ligand in float pairs.
+//                     (|E_fp32 - E_exact| <= B, the certificate); the listed
+//                     translations above it keep their FP32 weights; the
+//                     pair's partial over its list joins the planes'
+//                     partials in the merge.
+// The refined weights are summed in order-independent fixed point.  Which
+// translations above the final threshold a plane lists depends on the order
+// in which the planes ran, so those weights (each below e^(-W/kT) of the
+// largest) are summed in one place or the other: results agree between runs
+// to rounding of that remainder (about 1e-12 relative).  A failed check or an
+// overflowing list sets a flag that makes bpmf_eval recompute the ligand in
+// float pairs.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -95,13 +98,12 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
   __shared__ ff s_gam[3][256];  // gamma_t,i
   __shared__ float s_red[8][2];
   __shared__ float s_redx[8][2];
-  __shared__ unsigned long long s_we, s_wf;
+  __shared__ unsigned long long s_we;
   const int pair = blockIdx.x;  // j * K + k
   const int j = pair / a.K, k = pair % a.K;
   const int n_list = min(a.rs.cnt[pair], a.rs.cap);
   if (threadIdx.x == 0) {
     s_we = 0ull;
-    s_wf = 0ull;
     if (a.rs.cnt[pair] > a.rs.cap) atomicOr(a.rs.fail, 1);  // list overflow
   }
   const float Emin = ord2f(a.rs.pmin[pair]);
@@ -128,9 +130,10 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
   const Cand *list = a.rs.cand + (long long)pair * a.rs.cap;
   float2 *ex = a.rs.exact + (long long)pair * a.rs.cap;
   double *expo = (a.export_E && pair == 0) ? a.export_E : nullptr;
-  // pass 1: exact -E/kT of every translation below the final threshold (a
-  // warp per translation, lanes over atoms), the certificate check, and the
-  // largest exact and FP32 -E/kT among them
+  // pass 1: exact -E/kT of every listed translation below the final
+  // threshold (a warp per translation, lanes over atoms), the certificate
+  // check, the largest exact -E/kT, and the largest FP32 -E/kT of the listed
+  // translations above the threshold
   ff Xe{-CUDART_INF_F, 0.f};  // max exact
   float Xf = -CUDART_INF_F;    // max FP32
   bool bad = false;
@@ -139,13 +142,14 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
     Cand cd{0u, CUDART_INF_F, -CUDART_INF_F};
     if (idx < n_list) cd = list[idx];
     const bool cand = idx < n_list && cd.e <= T;
+    if (idx < n_list && !cand) Xf = fmaxf(Xf, cd.x);  // kept at its FP32 weight
     unsigned bal = __ballot_sync(0xffffffffu, cand);
     while (bal) {
       const int src = __ffs(bal) - 1;
       bal &= bal - 1;
       const unsigned t = __shfl_sync(0xffffffffu, cd.t, src);
       const float ef = __shfl_sync(0xffffffffu, cd.e, src);
-      const float xf = __shfl_sync(0xffffffffu, cd.x, src);
+
       const int s2 = (int)(t % (unsigned)a.S2), s01 = (int)(t / (unsigned)a.S2);
       const int s1 = s01 % a.S1, s0 = s01 / a.S1;
       const int mt[3] = {inf.w0[0] + s0, inf.w0[1] + s1, inf.w0[2] + s2};
@@ -181,7 +185,6 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
       if (fabsf(d_ff(ff{ef, 0.f}, part)) > B) bad = true;
       const ff x = s_norm(s_mul(part, nikT));
       if (ff_gt(x, Xe)) Xe = x;
-      Xf = fmaxf(Xf, xf);
       if (lane == src) {
         ex[idx] = make_float2(x.hi, x.lo);
         if (expo) expo[t] = (double)part.hi + (double)part.lo;
@@ -214,21 +217,21 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
   }
   // level: the largest of the exact and the FP32 values, so every weight <= 1
   const ff L = ff_gt(ff{Xf, 0.f}, Xe) ? ff{Xf, 0.f} : Xe;
-  // pass 2: the exact and the FP32 weights of the same translations
-  unsigned long long we = 0ull, wf = 0ull;
+  // pass 2: the weight of every listed translation, exact below the threshold
+  unsigned long long wt = 0ull;
   for (int idx = threadIdx.x; idx < n_list; idx += blockDim.x) {
     const Cand cd = list[idx];
-    if (!(cd.e <= T)) continue;
-    const float2 xe = ex[idx];
-    we += (unsigned long long)__double2ll_rn((double)expf(d_ff(ff{xe.x, xe.y}, L)) * kFixScale);
-    wf += (unsigned long long)__double2ll_rn((double)expf(d_ff(ff{cd.x, 0.f}, L)) * kFixScale);
+    ff x{cd.x, 0.f};
+    if (cd.e <= T) {
+      const float2 xe = ex[idx];
+      x = ff{xe.x, xe.y};
+    }
+    wt += (unsigned long long)__double2ll_rn((double)expf(d_ff(x, L)) * kFixScale);
   }
-  atomicAdd(&s_we, we);
-  atomicAdd(&s_wf, wf);
+  atomicAdd(&s_we, wt);
   __syncthreads();
   if (threadIdx.x == 0) {
-    a.part_ref[2 * pair] = make_float4(L.hi, L.lo, (float)((double)s_we / kFixScale),
-                                       (float)((double)s_wf / kFixScale));
+    a.part_ref[2 * pair] = make_float4(L.hi, L.lo, (float)((double)s_we / kFixScale), 0.f);
     a.part_ref[2 * pair + 1] = make_float4(Xe.hi, Xe.lo, 0.f, 0.f);
   }
 }

@@ -4,18 +4,25 @@ kernels).
 
 Flow for one ligand with J configurations against K receptors:
   features (bpmf_features) -> prediction (bpmf_mlp_forward) ->
-  q = mix softmax(pred) + (1 - mix)/J and M draws (bpmf_proposal_sample, on
-  uniforms from a seeded numpy generator) -> bpmf_eval on the drawn
+  q = mix softmax(pred / tau) + (1 - mix)/J and M draws (bpmf_proposal_sample,
+  on uniforms from a seeded numpy generator) -> bpmf_eval on the drawn
   configurations -> importance-weighted BPMF (bpmf_proposal_bpmf) with the
   valid-translation totals of all J configurations (bpmf_valid_counts).
+Training: fully enumerated ligands give each configuration's log weight
+relative to its ligand's largest, clipped below (bpmf_config_targets); the
+temperature tau is the one whose exact importance-sampling variance
+(bpmf_proposal_chi2) is lowest on held-out, fully enumerated ligands.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import (BPMF_MODE_FF, BPMF_N_FEATURES, bpmf_eval, bpmf_features, bpmf_ligand_batch, bpmf_ligand_free,
-               bpmf_mlp_create, bpmf_mlp_forward, bpmf_mlp_free, bpmf_mlp_param_count, bpmf_mlp_train_step,
-               bpmf_proposal_bpmf, bpmf_proposal_sample, bpmf_valid_counts)
+from . import (BPMF_MODE_FF, BPMF_N_FEATURES, bpmf_config_targets, bpmf_eval, bpmf_features, bpmf_ligand_batch,
+               bpmf_ligand_free, bpmf_mlp_create, bpmf_mlp_forward, bpmf_mlp_free, bpmf_mlp_param_count,
+               bpmf_mlp_train_step, bpmf_proposal_bpmf, bpmf_proposal_chi2, bpmf_proposal_sample, bpmf_valid_counts)
+
+TARGET_CLIP = 50.0  # training targets: log weight relative to the ligand's largest, clipped at -50
+TAUS = (0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0, 32.0, 64.0)
 
 
 def init_params(n_in: int, width: int, depth: int, seed: int = 0) -> np.ndarray:
@@ -39,16 +46,37 @@ def fit_norm(X: np.ndarray, t: np.ndarray) -> np.ndarray:
     return np.concatenate([X.mean(axis=0), sd, [t.mean(), ts]]).astype(np.float32)
 
 
-def config_targets(logZ: np.ndarray, n_valid: np.ndarray) -> np.ndarray:
-    """Per-configuration weight in the pooled sample mean summed over
-    receptors: log sum_k S_jk (-inf when no translation is valid)."""
-    with np.errstate(divide="ignore"):
-        ls = np.where(n_valid > 0, logZ + np.log(np.maximum(n_valid, 1)), -np.inf)
-    m = ls.max(axis=1, keepdims=True)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        s = np.where(np.isfinite(m[:, 0]), m[:, 0] + np.log(np.exp(ls - np.where(np.isfinite(m), m, 0)).sum(1)),
-                     -np.inf)
-    return s
+def config_targets(ctx, logZ, n_valid, clip=TARGET_CLIP):
+    """One ligand's (ls, t) on the device: ls [J] float64, each configuration's
+    log weight ln sum_k S_jk; t [J] float32, the training target
+    max(ls - max ls, -clip) (bpmf_config_targets)."""
+    import torch
+    lz = torch.as_tensor(logZ, dtype=torch.float64).cuda().contiguous()
+    nv = torch.as_tensor(n_valid, dtype=torch.int64).cuda().contiguous()
+    J = lz.shape[0]
+    ls = torch.empty(J, dtype=torch.float64, device="cuda")
+    t = torch.empty(J, dtype=torch.float32, device="cuda")
+    bpmf_config_targets(ctx, lz, nv, clip, ls, t)
+    return ls, t
+
+
+def proposal_chi2(ctx, pred, ls, mix, tau) -> float:
+    """Exact relative variance of one importance-sampling draw (bpmf_proposal_chi2)."""
+    import torch
+    out = torch.empty(1, dtype=torch.float64, device=pred.device)
+    bpmf_proposal_chi2(ctx, pred, ls, mix, tau, out)
+    return float(out.item())
+
+
+def choose_tau(ctx, preds, lss, mix=0.8, taus=TAUS):
+    """The temperature with the lowest mean log(1 + chi2) over fully
+    enumerated validation ligands (preds, lss: per-ligand device tensors)."""
+    best = None
+    for tau in taus:
+        v = float(np.mean([np.log1p(proposal_chi2(ctx, p, l, mix, tau)) for p, l in zip(preds, lss)]))
+        if best is None or v < best[0]:
+            best = (v, tau)
+    return best[1]
 
 
 class LearnedProposal:
@@ -92,7 +120,7 @@ def features(ctx, lig_handle, total_conf, h, device):
 
 
 def proposal_bpmf(ctx, recs, kT, coords, params, pred, budget, mix=0.8, seed=0, mode=BPMF_MODE_FF,
-                  n_tot=None, lig_full=None, stream=None):
+                  n_tot=None, lig_full=None, stream=None, tau=1.0):
     """Importance-sampled BPMF per receptor for one ligand.
 
     coords: device float32 [J, n_atoms, 3]; params: (q, eps, R) device float32
@@ -111,7 +139,7 @@ def proposal_bpmf(ctx, recs, kT, coords, params, pred, budget, mix=0.8, seed=0, 
     u = torch.from_numpy(np.random.default_rng(seed).random(budget)).to(dev)
     idx = torch.empty(budget, dtype=torch.int32, device=dev)
     q_s = torch.empty(budget, dtype=torch.float64, device=dev)
-    bpmf_proposal_sample(ctx, pred, mix, u, idx, q_s, stream)
+    bpmf_proposal_sample(ctx, pred, mix, u, idx, q_s, stream, tau=tau)
     sub = coords.index_select(0, idx.long()).reshape(-1, 3).contiguous()
     lh = bpmf_ligand_batch(ctx, [n_atoms], [budget], sub, *params, stream=stream)
     try:

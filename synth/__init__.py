@@ -199,16 +199,39 @@ def random_rotations(rng, n: int) -> np.ndarray:
         np.stack([2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)], -1)], 1)
 
 
+def _chains(n: int, torsions: np.ndarray, bond: float = 1.5, angle_deg: float = 109.5) -> np.ndarray:
+    """_chain for many torsion sets at once: torsions [J, n - 3] -> [J, n, 3]
+    (the same construction, vectorised over configurations)."""
+    J = torsions.shape[0]
+    th = np.deg2rad(angle_deg)
+    x = np.zeros((J, n, 3))
+    if n > 1:
+        x[:, 1] = [bond, 0.0, 0.0]
+    if n > 2:
+        x[:, 2] = x[:, 1] + bond * np.array([-np.cos(th), np.sin(th), 0.0])
+    for i in range(3, n):
+        a, b, c = x[:, i - 3], x[:, i - 2], x[:, i - 1]
+        bc = c - b
+        bc /= np.linalg.norm(bc, axis=1, keepdims=True)
+        nrm = np.cross(b - a, bc)
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        m = np.stack([bc, np.cross(nrm, bc), nrm], axis=2)  # [J, 3, 3], columns as in _chain
+        phi = torsions[:, i - 3]
+        d = bond * np.stack([np.full(J, -np.cos(th)), np.sin(th) * np.cos(phi), np.sin(th) * np.sin(phi)], axis=1)
+        x[:, i] = c + np.einsum("jrk,jk->jr", m, d)
+    return x
+
+
 def ligand_configs(seed: int, n_atoms: int, n_conf: int) -> np.ndarray:
-    """[n_conf, n_atoms, 3] float32: random torsions, then a Haar rotation about the centroid."""
+    """[n_conf, n_atoms, 3] float32: random torsions, then a Haar rotation about
+    the centroid (all rotations are drawn first, then each configuration's
+    torsions in turn)."""
     rng = np.random.default_rng(seed)
-    out = np.empty((n_conf, n_atoms, 3), dtype=np.float32)
     rots = random_rotations(rng, n_conf)
-    for j in range(n_conf):
-        x = _chain(n_atoms, rng.uniform(0.0, 2 * np.pi, max(n_atoms - 3, 0)))
-        x -= x.mean(axis=0)
-        out[j] = (x @ rots[j].T).astype(np.float32)
-    return out
+    tors = rng.uniform(0.0, 2 * np.pi, (n_conf, max(n_atoms - 3, 0)))
+    x = _chains(n_atoms, tors)
+    x -= x.mean(axis=1, keepdims=True)
+    return np.einsum("jnk,jrk->jnr", x, rots).astype(np.float32)
 
 
 @dataclass

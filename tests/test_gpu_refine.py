@@ -183,9 +183,10 @@ def test_refined_certificate_failure_falls_back_to_float_pairs(pkg):
 
 
 def test_refined_results_are_deterministic_with_and_without_graphs(pkg):
-    """The refined sums do not depend on the order in which the site planes
-    append their candidates: repeated calls, and a CUDA-graph replay, give
-    bit-identical results."""
+    """Repeated calls and a CUDA-graph replay give the same results: the
+    refined weights are summed in order-independent fixed point; only the
+    FP32 remainder below e^(-W/kT) may be summed in a different place when
+    the planes run in another order (about 1e-12 relative)."""
     import torch
     w = synth.protein_scale(n_conf=48, n_rec=2)
     lig = w.ligands[0]
@@ -204,8 +205,10 @@ def test_refined_results_are_deterministic_with_and_without_graphs(pkg):
         for _ in range(2):  # capture, then replay
             s.eval(lh, rhs, KT, pkg.BPMF_MODE_REFINE, out=dev, stream=st.cuda_stream)
             torch.cuda.synchronize()
-            for k in ("logZ", "n_valid", "bpmf", "dG"):
-                assert np.array_equal(dev[k].cpu().numpy(), a[k]), k
+            assert np.array_equal(dev["n_valid"].cpu().numpy(), a["n_valid"])
+            for k in ("logZ", "bpmf", "dG"):
+                assert np.allclose(dev[k].cpu().numpy(), a[k], rtol=1e-11, atol=0), k
         pkg.bpmf_set_graph_mode(s.ctx, 0)
-    for k in ("logZ", "n_valid", "bpmf", "dG"):
-        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(a["n_valid"], b["n_valid"])
+    for k in ("logZ", "bpmf", "dG"):
+        assert np.allclose(a[k], b[k], rtol=1e-11, atol=0), k

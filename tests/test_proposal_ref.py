@@ -85,3 +85,52 @@ def test_features_rotation_behaviour():
     q0 = Rotation.from_quat([f0[1], f0[2], f0[3], f0[0]])
     q1 = Rotation.from_quat([f1[1], f1[2], f1[3], f1[0]])
     assert (rot * q0).approx_equal(q1, atol=1e-7)
+
+
+def test_tempered_proposal_limits():
+    """tau -> infinity flattens the softmax to uniform; tau = 1 is the plain
+    softmax; mix = 0 is uniform whatever the prediction."""
+    rng = np.random.default_rng(9)
+    pred = rng.normal(0, 5, 64)
+    assert np.allclose(P.proposal(pred, 0.8, 1e12), 1.0 / 64, rtol=1e-9)
+    e = np.exp(pred - pred.max())
+    assert np.allclose(P.proposal(pred, 1.0, 1.0), e / e.sum(), rtol=1e-12)
+    assert np.allclose(P.proposal(pred, 0.0, 0.3), 1.0 / 64)
+    # halving tau squares the softmax weights before renormalising
+    q2 = P.proposal(pred, 1.0, 0.5)
+    assert np.allclose(q2, e ** 2 / np.sum(e ** 2), rtol=1e-9)
+
+
+def test_chi2_closed_forms():
+    """chi2 vanishes when q is proportional to S (the zero-variance proposal),
+    equals J sum w^2 - 1 for the uniform proposal, and matches the Monte-Carlo
+    variance of S_j / (q_j Z) for j ~ q."""
+    rng = np.random.default_rng(10)
+    J = 200
+    ls = rng.normal(0, 3, J)
+    ls[5] = -np.inf  # a configuration without a valid translation
+    w = np.exp(ls - ls[np.isfinite(ls)].max())
+    w[~np.isfinite(ls)] = 0
+    w /= w.sum()
+    pred_exact = np.where(np.isfinite(ls), ls, -1e30)
+    assert abs(P.chi2(pred_exact, ls, 1.0, 1.0)) < 1e-9
+    assert abs(P.chi2(np.zeros(J), ls, 0.8, 1.0) - (J * np.sum(w ** 2) - 1.0)) < 1e-9
+    pred = ls + rng.normal(0, 1.0, J)
+    pred[5] = 0.0
+    q = P.proposal(pred, 0.8, 2.0)
+    draws = rng.choice(J, size=400_000, p=q)
+    r = w[draws] / q[draws]
+    assert abs(np.var(r) - P.chi2(pred, ls, 0.8, 2.0)) <= 0.03 * max(1.0, P.chi2(pred, ls, 0.8, 2.0))
+
+
+def test_config_targets_clip_and_offset():
+    """ls is the log of the configuration's summed weight over receptors;
+    the targets are relative to the ligand's largest and clipped below."""
+    logZ = np.array([[0.0, 1.0], [5.0, -np.inf], [-200.0, -300.0], [-np.inf, -np.inf]])
+    n = np.array([[1, 3], [2, 0], [4, 4], [0, 0]])
+    ls, t = P.config_targets(logZ, n, 50.0)
+    assert abs(ls[0] - np.log(1 + 3 * np.e)) < 1e-12
+    assert abs(ls[1] - (5.0 + np.log(2))) < 1e-12
+    assert np.isneginf(ls[3])
+    assert t[1] == 0.0 and abs(t[0] - (ls[0] - ls[1])) < 1e-12
+    assert t[2] == -50.0 and t[3] == -50.0
