@@ -331,7 +331,7 @@ def precision_sweep(torch, pkg, sess, w, dev, stream, n_sample=8, n_eval=64):
     lig = w.ligands[0]
     out = {}
     modes = {"refine": pkg.BPMF_MODE_REFINE, "ff": pkg.BPMF_MODE_FF, "fp32": pkg.BPMF_MODE_FP32,
-             "split_bf16": pkg.BPMF_MODE_SPLIT_BF16}
+             "split_bf16": pkg.BPMF_MODE_SPLIT_BF16, "split_refine": pkg.BPMF_MODE_SPLIT_REFINE}
     for clip in (1e3, 1e4, 1e5):
         wc = synth.protein_scale(n_conf=n_eval, n_rec=N_REC, seed=1001, clip=clip, n_atoms_lig=N_ATOMS)
         wc.ligands = [synth.LigandInput(lig.params, lig.coords[:n_eval])]
@@ -858,8 +858,20 @@ def run_ours(args):
         eb1.record(stream)
         torch.cuda.synchronize()
         sb = st_boot.cpu().numpy()
+        # convergence with the number of configurations: the first J of the set
+        series = []
+        for Js in (125, 250, 500, 1000, J):
+            us = torch.from_numpy(np.random.default_rng(78).random((R_boot, Js))).to(dev)
+            st_s = torch.empty((2, K + 1), dtype=torch.float64, device=dev)
+            pkg.bpmf_bootstrap(sess.ctx, outs["logZ"][:Js].contiguous(), outs["n_valid"][:Js].contiguous(), w.kT,
+                               w.receptors[0].h, us, None, st_s, stream)
+            torch.cuda.synchronize()
+            v = st_s.cpu().numpy()
+            series.append({"J": Js, "mean_bpmf": v[0, :K].tolist(), "sigma_bpmf_kcal": v[1, :K].tolist(),
+                           "mean_dG": float(v[0, K]), "sigma_dG_kcal": float(v[1, K])})
         boot = {"replicates": R_boot, "bpmf": res_chosen["bpmf"][0].tolist(), "sigma_bpmf_kcal": sb[1, :K].tolist(),
-                "dG": float(res_chosen["dG"][0]), "sigma_dG_kcal": float(sb[1, K]), "ms": eb0.elapsed_time(eb1)}
+                "dG": float(res_chosen["dG"][0]), "sigma_dG_kcal": float(sb[1, K]), "ms": eb0.elapsed_time(eb1),
+                "convergence_with_J": series}
     # the other forms on the same workload (half the timed steps)
     others = {}
     for name in modes:
@@ -892,9 +904,11 @@ def run_ours(args):
     h2d = sum(g.numel() * 4 for g in host_grids) + host_coords.numel() * 4 + sum(p.numel() * 4 for p in host_params)
     d2h = sum(v.nbytes for v in host_outs.values())
 
-    # split-bf16 tensor-core form on the same workload
+    # split-bf16 tensor-core form on the same workload: raw, and as the refined form's locator
     t_split, _, prof_split = timed(pkg.BPMF_MODE_SPLIT_BF16, max(1, args.steps // 2), 1, prof=True)
     res_split = {k: v.cpu().numpy() for k, v in outs.items()}
+    t_split_ref, _, prof_split_ref = timed(pkg.BPMF_MODE_SPLIT_REFINE, max(1, args.steps // 2), 1, prof=True)
+    res_split_ref = {k: v.cpu().numpy() for k, v in outs.items()}
 
     sweep = None
     if rank == 0 and not args.no_sweep:
@@ -934,7 +948,8 @@ def run_ours(args):
         if not args.no_cpu_baseline:
             ref, dt, ns = sized_sample(w, args.ref_sample)
             okz = np.isfinite(ref["logZ"])
-            cmp = [(chosen, res_chosen)] + [(nm, o[2]) for nm, o in others.items()] + [("split_bf16", res_split)]
+            cmp = [(chosen, res_chosen)] + [(nm, o[2]) for nm, o in others.items()] + [("split_bf16", res_split),
+                                                                                      ("split_refine", res_split_ref)]
             if cufft is not None:
                 cmp.append(("cufft_fp32", {"logZ": logZ_cu, "n_valid": res_chosen["n_valid"]}))
             for name, res in cmp:
@@ -1005,7 +1020,14 @@ def run_ours(args):
                                 for nm, o in others.items()},
                 "split_bf16_path": {"value": n_poses * world / (t_split / 1e3), "ms_per_step": t_split,
                                     "kernels_ms_per_step": {k: v[0] / max(1, args.steps // 2)
-                                                            for k, v in prof_split.items()}},
+                                                            for k, v in prof_split.items()},
+                                    "what": "six-term bf16 (hi/mid/lo) radix-32 tensor-core stages, full edges"},
+                "split_refine_path": {"value": n_poses * world / (t_split_ref / 1e3), "ms_per_step": t_split_ref,
+                                      "speedup_vs_fp32_form": (others["fp32"][0] / t_split_ref) if "fp32" in others
+                                      else None,
+                                      "kernels_ms_per_step": {k: v[0] / max(1, args.steps // 2)
+                                                              for k, v in prof_split_ref.items()},
+                                      "what": "the split-bf16 correlation as the refined form's locator"},
                 "precision_sweep": sweep,
                 "occupancy_path": occupancy,
                 "whole_surface": surface,

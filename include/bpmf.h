@@ -66,11 +66,12 @@ extern "C" {
 /*   BPMF_MODE_SPLIT_BF16 -- the FP32 form with every radix-32 stage (padded
  *                     edges divisible by 32) run as a dense tensor-core
  *                     contraction: the 64 x 64 real DFT-32 matrix times the
- *                     twiddled data, each split into bf16 high and low parts,
- *                     three products (hi.hi + hi.lo + lo.hi) accumulated in
- *                     FP32.  About 2^-16 relative error per stage: coarser than
- *                     FP32, with the error against the oracle reported per
- *                     result.  Other edges fall back to the FP32 stages. */
+ *                     twiddled data, each split into three bf16 parts
+ *                     (hi, mid, lo), the six products of order up to 2^-16
+ *                     accumulated by the tensor cores (FP32 without IEEE
+ *                     rounding): errors up to several times the FP32 form's,
+ *                     reported against the oracle per result.
+ *                     Other edges fall back to the FP32 stages. */
 #define BPMF_MODE_SPLIT_BF16 2u
 /*   BPMF_MODE_REFINE -- the FP32 correlation for every translation, then an
  *     exact re-evaluation, in float-pair arithmetic (FP32 instructions,
@@ -95,6 +96,14 @@ extern "C" {
  *     per-pair list.  The receptor handle keeps a device copy of its FP32
  *     grids for this form. */
 #define BPMF_MODE_REFINE 3u
+/*   BPMF_MODE_SPLIT_REFINE -- the refined form with the split-bf16
+ *     tensor-core correlation (BPMF_MODE_SPLIT_BF16) as its locator: the
+ *     same window, certificate and float-pair fallback, with the bound B taken
+ *     eight times as wide (the six-term split carries FP32's significand, but
+ *     the tensor cores accumulate without IEEE rounding: measured errors reach
+ *     several times the FP32 form's).  Runs on the full padded edges (the
+ *     tensor-core stage needs edges divisible by 32). */
+#define BPMF_MODE_SPLIT_REFINE 4u
 
 /* Largest supported ligand (atoms) and padded FFT edge. */
 #define BPMF_MAX_ATOMS 256
@@ -229,7 +238,8 @@ void bpmf_ligand_free(bpmf_lig_t lig);
  * streams forked from and joined back into `stream`) and kept until
  * bpmf_receptor_free.  The split-BF16 form always uses the full edges.
  *  kT        > 0 (kcal/mol).
- *  mode      BPMF_MODE_FP32, BPMF_MODE_FF, BPMF_MODE_SPLIT_BF16 or BPMF_MODE_REFINE.
+ *  mode      BPMF_MODE_FP32, BPMF_MODE_FF, BPMF_MODE_SPLIT_BF16, BPMF_MODE_REFINE or
+ *            BPMF_MODE_SPLIT_REFINE.
  *  logZ      [total_conf][K] float64, total_conf = sum n_conf, ligand-major.
  *  n_valid   [total_conf][K] int64 (may be NULL).
  *  bpmf      [n_lig][K] float64 (may be NULL).

@@ -37,6 +37,7 @@ BPMF_MODE_FP32 = 0
 BPMF_MODE_FF = 1
 BPMF_MODE_SPLIT_BF16 = 2
 BPMF_MODE_REFINE = 3
+BPMF_MODE_SPLIT_REFINE = 4
 BPMF_MAX_ATOMS = 256
 BPMF_MAX_FFT_EDGE = 256
 

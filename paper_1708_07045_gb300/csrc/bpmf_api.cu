@@ -100,6 +100,7 @@ struct bpmf_ctx {
   std::string err;
   std::map<int, float4 *> tw;  // twiddle tables per transform length
   uint4 *tca = nullptr;        // tensor-core radix-32 fragment table (split-bf16 mode)
+  const __nv_bfloat16 *tc05 = nullptr;  // the same stage's matrix in the tcgen05 layout
   void *ws = nullptr;          // grow-only device workspace
   size_t ws_bytes = 0;
   size_t ws_budget = size_t(3) << 30;
@@ -227,11 +228,15 @@ struct DeviceGuard {
 };
 
 // Fragment tables of the tensor-core radix-32 stage: the real 64 x 64 DFT-32
-// matrix (rows 2r'+c', columns 2r+c), split into bf16 high and low parts and
-// laid out in mma.sync m16n8k16 A-fragment order, forward then inverse.
+// matrix (rows 2r'+c', columns 2r+c), split into bf16 high, middle and low
+// parts and laid out in mma.sync m16n8k16 A-fragment order, forward then
+// inverse.
 const uint4 *tc_table(bpmf_ctx *c);
 
+const __nv_bfloat16 *tc05_table(bpmf_ctx *c);
+
 // split-bf16 plan: the radix-32 factor as a final tensor-core stage when 32 | P
+// (tcgen05 form; the mma.sync fragments stay as the reference form)
 FftPlan make_plan_split(bpmf_ctx *c, int P) {
   if (P % 32) return make_plan(P);
   FftPlan pl = make_plan(P / 32);
@@ -239,6 +244,7 @@ FftPlan make_plan_split(bpmf_ctx *c, int P) {
   if (P == 32) pl.nst = 0;
   pl.r[pl.nst++] = 32;
   pl.tca = tc_table(c);
+  pl.tc05_f = tc05_table(c);
   return pl;
 }
 
@@ -269,7 +275,7 @@ static inline float bf16_val(unsigned short b) {
 
 const uint4 *tc_table(bpmf_ctx *c) {
   if (c->tca) return c->tca;
-  std::vector<uint4> h(2 * 2 * 4 * 4 * 32);
+  std::vector<uint4> h(2 * 3 * 4 * 4 * 32);
   const long double two_pi = 6.283185307179586476925286766559L;
   for (int dir = 0; dir < 2; ++dir) {
     float A[64][64];
@@ -282,18 +288,21 @@ const uint4 *tc_table(bpmf_ctx *c) {
         A[2 * rp + 1][2 * r] = wi;
         A[2 * rp + 1][2 * r + 1] = wr;
       }
-    for (int term = 0; term < 2; ++term)
+    for (int term = 0; term < 3; ++term)
       for (int t = 0; t < 4; ++t)
         for (int q = 0; q < 4; ++q)
           for (int lane = 0; lane < 32; ++lane) {
             const int gid = lane >> 2, tig = lane & 3;
-            auto part = [&](int m, int k) {
-              const unsigned short hb = bf16_bits(A[m][k]);
-              return term == 0 ? hb : bf16_bits(A[m][k] - bf16_val(hb));
+            auto part = [&](int m, int k) {  // a = hi + mid + lo, each bf16
+              const float a = A[m][k];
+              const unsigned short hb = bf16_bits(a);
+              const float r = a - bf16_val(hb);
+              const unsigned short mb = bf16_bits(r);
+              return term == 0 ? hb : (term == 1 ? mb : bf16_bits(r - bf16_val(mb)));
             };
             auto pack = [&](int m, int k) { return (unsigned)part(m, k) | ((unsigned)part(m, k + 1) << 16); };
             const int m = 16 * t + gid, k = 16 * q + 2 * tig;
-            h[(((dir * 2 + term) * 4 + t) * 4 + q) * 32 + lane] =
+            h[(((dir * 3 + term) * 4 + t) * 4 + q) * 32 + lane] =
                 make_uint4(pack(m, k), pack(m + 8, k), pack(m, k + 8), pack(m + 8, k + 8));
           }
   }
@@ -302,6 +311,39 @@ const uint4 *tc_table(bpmf_ctx *c) {
   CK(cudaMemcpy(d, h.data(), sizeof(uint4) * h.size(), cudaMemcpyHostToDevice));
   c->tca = d;
   return d;
+}
+
+// The real 64 x 64 DFT-32 matrix of the tcgen05 stage, [dir][part][64 x 64]
+// bf16 (hi, mid, lo with hi + mid + lo = the FP32 coefficient), each part in
+// the tensor cores' K-major core-matrix layout: element (n, k) at
+// (n / 8) 512 + (k / 8) 64 + (n % 8) 8 + k % 8.
+const __nv_bfloat16 *tc05_table(bpmf_ctx *c) {
+  if (c->tc05) return c->tc05;
+  std::vector<unsigned short> h(2 * 3 * 64 * 64);
+  const long double two_pi = 6.283185307179586476925286766559L;
+  for (int dir = 0; dir < 2; ++dir)
+    for (int rp = 0; rp < 32; ++rp)
+      for (int r = 0; r < 32; ++r) {
+        const long double a = two_pi * (long double)((rp * r) % 32) / 32.0L;
+        const float wr = (float)cosl(a), wi = (float)((dir ? 1 : -1) * sinl(a));
+        const float F[2][2] = {{wr, -wi}, {wi, wr}};  // rows 2r' + c', columns 2r + c
+        for (int cp = 0; cp < 2; ++cp)
+          for (int cc = 0; cc < 2; ++cc) {
+            const int n = 2 * rp + cp, k = 2 * r + cc;
+            const int off = (n >> 3) * 512 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);
+            float v = F[cp][cc];
+            for (int part = 0; part < 3; ++part) {
+              const unsigned short b = bf16_bits(v);
+              h[(dir * 3 + part) * 64 * 64 + off] = b;
+              v -= bf16_val(b);
+            }
+          }
+      }
+  void *d = nullptr;
+  CK(cudaMalloc(&d, sizeof(unsigned short) * h.size()));
+  CK(cudaMemcpy(d, h.data(), sizeof(unsigned short) * h.size(), cudaMemcpyHostToDevice));
+  c->tc05 = static_cast<const __nv_bfloat16 *>(d);
+  return c->tc05;
 }
 
 void *workspace(bpmf_ctx *c, size_t bytes, cudaStream_t st) {
@@ -465,6 +507,7 @@ struct RefineCtx {
   float4 *part_ref = nullptr;     // [batch][Kg][2] corrections (this batch's slice)
   int *fail = nullptr;            // the ligand's fallback flag
   float check_scale = 1.f;
+  float bound_scale = 1.f;        // multiplies B (window and certificate)
 };
 
 // Translations per pair list of the refined form: every translation of a
@@ -513,7 +556,11 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
                double *export_E, char *ws, cudaStream_t st, const bpmf_ctx::Tune &tn, bool split = false,
                const OccTab *d_tabs = nullptr, const RefineCtx *rf = nullptr, const float2 *const *h_rhi = nullptr,
                int *d_err = nullptr) {
-  auto plan = [&](int P) { return split ? make_plan_split(c, P) : make_plan(P); };
+  auto plan = [&](int P) {
+    FftPlan pl = split ? make_plan_split(c, P) : make_plan(P);
+    pl.err = d_err;  // a bounded tensor-core wait that ran out
+    return pl;
+  };
   const size_t E = sizeof(cx<T>);
   char *p = ws;
   float2 *box = reinterpret_cast<float2 *>(p);
@@ -576,6 +623,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     for (int t = 0; t < 3; ++t) ra.gnorm[t] = (float)rf->gnorm[t];
     ra.log2P3 = (float)std::log2((double)g.P[0] * g.P[1] * g.P[2]);
     ra.check_scale = rf->check_scale;
+    ra.bound_scale = rf->bound_scale;
     ra.coords = lg->coords;
     ra.gamma = lg->gamma;
     ra.gamma_stride = (int)lg->total_atoms;
@@ -931,6 +979,7 @@ void bpmf_destroy(bpmf_ctx_t c) {
     if (x) cudaStreamDestroy(x);
   for (auto &kv : c->blocks) cudaFree(kv.second);
   if (c->tca) cudaFree(c->tca);
+  if (c->tc05) cudaFree(const_cast<__nv_bfloat16 *>(c->tc05));
   if (c->ws) cudaFree(c->ws);
   for (auto &r : c->pending) {
     cudaEventDestroy(r.a);
@@ -1509,8 +1558,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   check_recs(recs, K, c);
   const double h = recs[0]->h;
   const bool use_ff = (mode == BPMF_MODE_FF);
-  const bool split = (mode == BPMF_MODE_SPLIT_BF16);
-  const bool refine = (mode == BPMF_MODE_REFINE);
+  const bool split = (mode == BPMF_MODE_SPLIT_BF16 || mode == BPMF_MODE_SPLIT_REFINE);
+  const bool refine = (mode == BPMF_MODE_REFINE || mode == BPMF_MODE_SPLIT_REFINE);
   const size_t E = use_ff ? sizeof(cx<ff>) : sizeof(cx<float>);
   const std::vector<RecGroup> groups = group_receptors(recs, K);
   if (split) tc_table(c);
@@ -1869,6 +1918,9 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
               rf.part_ref = d_part_ref + 2 * (size_t)b0 * Kg;
               rf.fail = d_fail + (pl.li - lig_begin);
               rf.check_scale = c->refine_check_scale;
+              // the split locator's error: measured up to ~8x the FP32 form's (the
+              // tensor cores' FP32 accumulation is not IEEE-rounded)
+              rf.bound_scale = split ? 8.f : 1.f;
             }
             if (use_ff)
               run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, d_rptr + Kg, h, nsh, nsl,
@@ -1984,7 +2036,8 @@ int eval_entry(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, doubl
                int64_t *n_valid, double *bpmf_out, double *dG, double *psi_min, double *psi_dom, void *stream) {
   if (!c || !lg || !recs || K < 1 || !(kT > 0.0) || (!logZ && lg && lg->total_conf > 0))
     return set_err(c, BPMF_ERR_INVALID_ARG, "null argument, K < 1 or kT <= 0");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE)
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE &&
+      mode != BPMF_MODE_SPLIT_REFINE)
     return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   if (lg->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "ligand batch from another context");
   DeviceGuard dg(c->device);
@@ -2005,7 +2058,8 @@ int eval_entry(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, doubl
 int bpmf_transform_edges(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, unsigned mode, int *edges) {
   if (!c || !lg || !recs || K < 1 || (!edges && lg->total_conf > 0))
     return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or K < 1");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE)
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE &&
+      mode != BPMF_MODE_SPLIT_REFINE)
     return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   try {
     last_msg.clear();
@@ -2018,8 +2072,8 @@ int bpmf_transform_edges(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, in
       ligand_tables(lg, li, recs, K, recs[0]->h, meta, info, nv);
       const int J = lg->n_conf[li];
       for (const RecGroup &g : groups) {
-        const std::vector<std::array<int, 3>> pc = transform_edges(meta.data(), J, g, recs,
-                                                                   mode == BPMF_MODE_SPLIT_BF16);
+        const std::vector<std::array<int, 3>> pc = transform_edges(
+            meta.data(), J, g, recs, mode == BPMF_MODE_SPLIT_BF16 || mode == BPMF_MODE_SPLIT_REFINE);
         for (int i = 0; i < J; ++i)
           for (int k : g.ks)
             for (int d = 0; d < 3; ++d) edges[((lg->conf_off[li] + i) * K + k) * 3 + d] = pc[i][d];
@@ -2047,7 +2101,8 @@ int bpmf_eval_dominant(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int 
 
 int bpmf_autotune(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, unsigned mode, void *stream) {
   if (!c || !lg || !recs || K < 1 || lg->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or K < 1");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE)
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE &&
+      mode != BPMF_MODE_SPLIT_REFINE)
     return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   DeviceGuard dg(c->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -2125,7 +2180,8 @@ int bpmf_export_energies(bpmf_ctx_t c, bpmf_lig_t lg, bpmf_rec_t rec, int lig_in
   if (!c || !lg || !rec || !out || lig_index < 0 || lig_index >= lg->n_lig || conf_index < 0 ||
       conf_index >= lg->n_conf[lig_index])
     return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or index out of range");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE)
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE &&
+      mode != BPMF_MODE_SPLIT_REFINE)
     return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   DeviceGuard dg(c->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -2161,7 +2217,8 @@ int bpmf_sir_poses(bpmf_ctx_t c, bpmf_lig_t lg, int lig_index, bpmf_rec_t rec, i
   if (!c || !lg || !rec || !logZ || !n_valid || !u1 || !u2 || !conf || !pose || lig_index < 0 ||
       lig_index >= lg->n_lig || K < 1 || k < 0 || k >= K || !(kT > 0.0) || M < 0)
     return set_err(c, BPMF_ERR_INVALID_ARG, "null argument or index out of range");
-  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE)
+  if (mode != BPMF_MODE_FP32 && mode != BPMF_MODE_FF && mode != BPMF_MODE_SPLIT_BF16 && mode != BPMF_MODE_REFINE &&
+      mode != BPMF_MODE_SPLIT_REFINE)
     return set_err(c, BPMF_ERR_INVALID_ARG, "unknown mode");
   if (lg->ctx != c || rec->ctx != c) return set_err(c, BPMF_ERR_INVALID_ARG, "handle from another context");
   for (const void *q : {(const void *)logZ, (const void *)n_valid, (const void *)u1, (const void *)u2,

@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "arith.cuh"
+#include "tc05.cuh"
 #include "tc_dft.cuh"
 
 namespace bpmf {
@@ -25,6 +26,12 @@ struct FftPlan {
   int nst;     // number of stages
   int r[12];   // radix of each stage, product = n; 32 = tensor-core stage
   const uint4 *tca;  // fragment table of the tensor-core radix-32 stage (split-bf16), or null
+  // tcgen05 form of that stage (when set): the DFT-32 matrix parts in the
+  // tensor cores' shared-memory layout, the byte offset of kTc05Smem bytes of
+  // scratch in the kernel's dynamic shared memory, and an error flag
+  const __nv_bfloat16 *tc05_f;
+  int tc05_off;
+  int *err;
 };
 
 template <class T, int R>
@@ -169,7 +176,8 @@ __device__ __forceinline__ void fft_stage(const cx<T> *src, cx<T> *dst, int es, 
 // visible to the CTA (caller syncs before).  Returns the buffer holding the
 // result; the CTA is synchronised on return.  NL > 0 fixes the line count at
 // compile time (it must equal nlines).
-template <class T, int NL = 0>
+// TC: compile the tensor-core radix-32 stages (split-bf16 kernels only).
+template <class T, int NL = 0, bool TC = false>
 __device__ cx<T> *cta_fft(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, const FftPlan &pl, const float4 *tw,
                           bool inv) {
   int Ns = 1;
@@ -178,7 +186,14 @@ __device__ cx<T> *cta_fft(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, cons
     const int R = pl.r[s];
     switch (R) {
       case 32:
-        if constexpr (std::is_same<T, float>::value) tc_dft32_stage(src, dst, es, ls, nlines, pl.n, Ns, tw, inv, pl.tca);
+        if constexpr (TC && std::is_same<T, float>::value) {
+          if (pl.tc05_f) {
+            extern __shared__ unsigned char tc05_dyn[];
+            tc05_dft32_stage(src, dst, es, ls, nlines, pl.n, Ns, tw, inv, pl.tc05_f, tc05_dyn + pl.tc05_off, pl.err);
+          } else {
+            tc_dft32_stage(src, dst, es, ls, nlines, pl.n, Ns, tw, inv, pl.tca);
+          }
+        }
         break;
       case 8: fft_stage<T, 8, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
       case 4: fft_stage<T, 4, NL>(src, dst, es, ls, nlines, pl.n, Ns, tw, inv); break;
@@ -306,7 +321,7 @@ __device__ __forceinline__ cx<T> *cta_fft_ct(cx<T> *b0, cx<T> *b1, const float4 
 // Transform with the compile-time engine when the plan and line count match a
 // specialisation (lines contiguous: CONTIG, element stride 1, line stride
 // P + 1; otherwise element stride NL, line stride 1), else the generic engine.
-template <class T, int NL, int NT, bool CONTIG, bool FEW = false>
+template <class T, int NL, int NT, bool CONTIG, bool FEW = false, bool TC = false>
 __device__ __forceinline__ cx<T> *cta_fft_auto(cx<T> *b0, cx<T> *b1, int es, int ls, int nlines, const FftPlan &pl,
                                                const float4 *tw, bool inv) {
   if (nlines == NL && pl.tca == nullptr) {
@@ -325,7 +340,7 @@ __device__ __forceinline__ cx<T> *cta_fft_auto(cx<T> *b0, cx<T> *b1, int es, int
         break;
     }
   }
-  return cta_fft<T>(b0, b1, es, ls, nlines, pl, tw, inv);
+  return cta_fft<T, 0, TC>(b0, b1, es, ls, nlines, pl, tw, inv);
 }
 
 }  // namespace bpmf

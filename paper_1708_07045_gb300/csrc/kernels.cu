@@ -251,7 +251,7 @@ cudaError_t launch_spread(const SpreadArgs &a_in, int batch, cudaStream_t st) {
 
 // --------------------------------------------------------------------------
 // (b) R2C along the contiguous axis: two real rows packed as one complex line.
-template <class T>
+template <class T, bool TC = false>
 __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::z_min_blocks) k_zfwd(ZfwdArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, L = a.L, ls = P + 1, F = P / 2 + 1;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::z_min_blocks) k_zfw
   }
   cp_async_wait_all();
   __syncthreads();
-  cx<T> *res = cta_fft_auto<T, 16, KCfg<T>::threads, true>(b0, b1, 1, ls, L, a.plan, s_tw, false);
+  cx<T> *res = cta_fft_auto<T, 16, KCfg<T>::threads, true, false, TC>(b0, b1, 1, ls, L, a.plan, s_tw, false);
   const T half = s_from<T>(0.5f);
   for (int idx = threadIdx.x; idx < L * F; idx += blockDim.x) {
     const int l = idx / F, k = idx % F;
@@ -297,22 +297,36 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::z_min_blocks) k_zfw
   }
 }
 
+// Kernels whose plan has a tcgen05 stage get kTc05Smem bytes of scratch at
+// the end of their dynamic shared memory.
+inline size_t with_tc05(FftPlan &pl, size_t smem) {
+  if (!pl.tc05_f) return smem;
+  pl.tc05_off = (int)smem;
+  return smem + kTc05Smem;
+}
+
 template <class T>
-cudaError_t launch_zfwd(const ZfwdArgs &a, cudaStream_t st) {
-  if (a.n_rows <= 0) return cudaSuccess;
+cudaError_t launch_zfwd(const ZfwdArgs &a_in, cudaStream_t st) {
+  if (a_in.n_rows <= 0) return cudaSuccess;
+  ZfwdArgs a = a_in;
   const int P = a.plan.n;
-  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)a.L * (P + 1);
-  cudaError_t e = cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  const size_t smem = with_tc05(a.plan, sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)a.L * (P + 1));
   const long long blocks = (a.n_rows + 2 * a.L - 1) / (2 * a.L);
-  k_zfwd<T><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
-  return cudaGetLastError();
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
+    return cudaGetLastError();
+  };
+  if constexpr (std::is_same<T, float>::value)
+    if (a.plan.tca) return go(k_zfwd<T, true>);
+  return go(k_zfwd<T, false>);
 }
 
 // --------------------------------------------------------------------------
 // C2C along a strided axis for a tile of LW consecutive innermost indices
 // (LWC > 0: LW fixed at compile time, so tile indices are shifts and masks).
-template <class T, int LWC>
+template <class T, int LWC, bool TC = false>
 __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::a_min_blocks) k_axis(AxisArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, LW = LWC > 0 ? LWC : a.LW;
@@ -343,8 +357,8 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::a_min_blocks) k_axi
   for (int idx = n_in * LW + threadIdx.x; idx < P * LW; idx += blockDim.x) b0[idx] = c_zero<T>();
   cp_async_wait_all();
   __syncthreads();
-  cx<T> *res = cta_fft_auto<T, (LWC > 0 ? LWC : 16), KCfg<T>::threads, false, true>(b0, b1, LW, 1, LW, a.plan, s_tw,
-                                                                             a.inverse != 0);
+  cx<T> *res = cta_fft_auto<T, (LWC > 0 ? LWC : 16), KCfg<T>::threads, false, true, TC>(b0, b1, LW, 1, LW, a.plan,
+                                                                                 s_tw, a.inverse != 0);
   // outputs s < n_out <= P, read at (w0 + s) mod P
   for (int idx = threadIdx.x; idx < a.n_out * LW; idx += blockDim.x) {
     const int s = idx / LW, l = idx % LW;
@@ -355,14 +369,20 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::a_min_blocks) k_axi
 }
 
 template <class T, int LWC>
-cudaError_t launch_axis_lw(const AxisArgs &a, cudaStream_t st) {
+cudaError_t launch_axis_lw(const AxisArgs &a_in, cudaStream_t st) {
+  AxisArgs a = a_in;
   const int P = a.plan.n;
-  const size_t smem = sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * a.LW;
-  cudaError_t e = cudaFuncSetAttribute(k_axis<T, LWC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  const size_t smem = with_tc05(a.plan, sizeof(float4) * P + 2 * sizeof(cx<T>) * (size_t)P * a.LW);
   const long long blocks = (a.n_outer * a.inner + a.LW - 1) / a.LW;
-  k_axis<T, LWC><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
-  return cudaGetLastError();
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a);
+    return cudaGetLastError();
+  };
+  if constexpr (std::is_same<T, float>::value)
+    if (a.plan.tca) return go(k_axis<T, LWC, true>);
+  return go(k_axis<T, LWC, false>);
 }
 
 template <class T>
@@ -382,7 +402,7 @@ cudaError_t launch_axis(const AxisArgs &a, cudaStream_t st) {
 // inverse DFT, keep the site window along x.  Each receptor element is loaded
 // once per CTA and used for all G configurations; the ligand spectra never
 // leave shared memory.
-template <class T, int KP>
+template <class T, int KP, bool TC = false>
 __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfused(XfusedArgs a, int batch) {
   extern __shared__ float4 smem[];
   constexpr int LW = KCfg<T>::xlw, G = KCfg<T>::xconf, LG = G * LW, L3 = 3 * LG;
@@ -415,7 +435,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfu
   for (int idx = U0 * L3 + threadIdx.x; idx < P * L3; idx += blockDim.x) bA[idx] = c_zero<T>();
   cp_async_wait_all();
   __syncthreads();
-  cx<T> *Lsp = cta_fft_auto<T, L3, KCfg<T>::threads, false>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
+  cx<T> *Lsp = cta_fft_auto<T, L3, KCfg<T>::threads, false, false, TC>(bA, bB, L3, 1, L3, a.plan, s_tw, false);
   cx<T> *W1 = (Lsp == bB) ? R + P * L3 : R;
   cx<T> *W2 = W1 + P * LK;
   __shared__ int s_wm[KP * G];  // per (receptor of the pass, configuration): site window start along x, mod P
@@ -448,7 +468,7 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::x_min_blocks) k_xfu
       }
     }
     __syncthreads();
-    cx<T> *res = cta_fft_auto<T, LK, KCfg<T>::threads, false>(W1, W2, LK, 1, LK, a.plan, s_tw, true);
+    cx<T> *res = cta_fft_auto<T, LK, KCfg<T>::threads, false, false, TC>(W1, W2, LK, 1, LK, a.plan, s_tw, true);
     for (int idx = threadIdx.x; idx < a.S0 * LK; idx += blockDim.x) {
       const int s = idx / LK, c = idx % LK, kg = c / LW, l = c % LW;
       const int k = k0 + kg / G, j = j0 + kg % G;
@@ -470,14 +490,20 @@ size_t xfused_smem(int P) {
 }
 
 template <class T, int KP>
-cudaError_t launch_xfused_kp(const XfusedArgs &a, int batch, cudaStream_t st) {
+cudaError_t launch_xfused_kp(const XfusedArgs &a_in, int batch, cudaStream_t st) {
   constexpr int LW = KCfg<T>::xlw, G = KCfg<T>::xconf;
-  const size_t smem = xfused_smem<T, KP>(a.plan.n);
-  cudaError_t e = cudaFuncSetAttribute(k_xfused<T, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  XfusedArgs a = a_in;
+  const size_t smem = with_tc05(a.plan, xfused_smem<T, KP>(a.plan.n));
   const long long blocks = (long long)((batch + G - 1) / G) * ((a.Q + LW - 1) / LW);
-  k_xfused<T, KP><<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a, batch);
-  return cudaGetLastError();
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)blocks, KCfg<T>::threads, smem, st>>>(a, batch);
+    return cudaGetLastError();
+  };
+  if constexpr (std::is_same<T, float>::value)
+    if (a.plan.tca) return go(k_xfused<T, KP, true>);
+  return go(k_xfused<T, KP, false>);
 }
 
 // Two receptors per inverse pass (twice the lines per transform stage) when
@@ -486,7 +512,7 @@ cudaError_t launch_xfused_kp(const XfusedArgs &a, int batch, cudaStream_t st) {
 template <class T>
 cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  if (a.K >= 2 && xfused_smem<T, 2>(a.plan.n) * KCfg<T>::x_min_blocks <= 227 * 1024)
+  if (a.K >= 2 && !a.plan.tc05_f && xfused_smem<T, 2>(a.plan.n) * KCfg<T>::x_min_blocks <= 227 * 1024)
     return launch_xfused_kp<T, 2>(a, batch, st);
   return launch_xfused_kp<T, 1>(a, batch, st);
 }
@@ -497,7 +523,7 @@ cudaError_t launch_xfused(const XfusedArgs &a, int batch, cudaStream_t st) {
 __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 __device__ __forceinline__ bool ff_gt(float a, float b) { return a > b; }
 
-template <class T, int NY>
+template <class T, int NY, bool TC = false>
 __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a) {
   extern __shared__ float4 smem[];
   const int P = a.plan.n, F = a.F2, ls = P + 1;
@@ -603,7 +629,7 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
       b0[l * ls + n] = c_norm(cx<T>{s_sub(A.re, B.im), s_add(A.im, B.re)});
     }
     __syncthreads();
-    cx<T> *res = cta_fft_auto<T, 20, 256, true>(b0, b1, 1, ls, L, a.plan, s_tw, true);
+    cx<T> *res = cta_fft_auto<T, 20, 256, true, false, TC>(b0, b1, 1, ls, L, a.plan, s_tw, true);
     const int nS = nrow * a.S2;
     T vmax = s_mk<T>(-CUDART_INF_F, 0.f);
     float emin = CUDART_INF_F;  // refined form: plane minimum of the energies
@@ -739,7 +765,8 @@ size_t zinv_smem(const ZinvArgs &a, int Lc) {
   const int P = a.plan.n;
   const size_t b1n = std::max((size_t)Lc * (P + 1), (size_t)2 * Lc * a.F2);
   const size_t es = a.rs.cand ? sizeof(float) * (size_t)2 * Lc * a.S2 : 0;  // refined form's FP32 energies
-  return sizeof(float4) * P + sizeof(cx<T>) * ((size_t)Lc * (P + 1) + b1n) + sizeof(T) * (size_t)2 * Lc * a.S2 + es;
+  return sizeof(float4) * P + sizeof(cx<T>) * ((size_t)Lc * (P + 1) + b1n) + sizeof(T) * (size_t)2 * Lc * a.S2 + es +
+         (a.plan.tc05_f ? (size_t)kTc05Smem : 0);  // tcgen05 scratch (placed last)
 }
 
 // Fused y + z inverse (FP32): y sub-pass width for F2 columns (two sub-passes
@@ -758,11 +785,11 @@ bool zinv_fused_fits(int P1, int P2, int S1, int S2, bool refine) {
   return zinv_ny(P2 / 2 + 1) > 0 && S1 <= P1 && zinv_fused_smem(P1, P2, S1, S2, refine) * 3 <= 227 * 1024;
 }
 
-template <class T, int NY>
+template <class T, int NY, bool TC = false>
 cudaError_t launch_zinv_k(const ZinvArgs &a, size_t smem, int batch, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_zinv<T, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_zinv<T, NY, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_zinv<T, NY><<<(unsigned)((long long)batch * a.K * a.S0), 256, smem, st>>>(a);
+  k_zinv<T, NY, TC><<<(unsigned)((long long)batch * a.K * a.S0), 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -790,7 +817,11 @@ cudaError_t launch_zinv(const ZinvArgs &a_in, int batch, cudaStream_t st) {
   while (Lc > 1 && zinv_smem<T>(a, Lc) > 227 * 1024) --Lc;
   if (zinv_smem<T>(a, Lc) > 227 * 1024) return cudaErrorInvalidValue;
   a.Lc = Lc;
-  return launch_zinv_k<T, 0>(a, zinv_smem<T>(a, Lc), batch, st);
+  const size_t smem = zinv_smem<T>(a, Lc);
+  if (a.plan.tc05_f) a.plan.tc05_off = (int)(smem - kTc05Smem);
+  if constexpr (std::is_same<T, float>::value)
+    if (a.plan.tca) return launch_zinv_k<T, 0, true>(a, smem, batch, st);
+  return launch_zinv_k<T, 0>(a, smem, batch, st);
 }
 
 // --------------------------------------------------------------------------

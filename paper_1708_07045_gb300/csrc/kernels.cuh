@@ -204,6 +204,7 @@ struct RefineArgs {
   float gnorm[3];          // ||gamma_t||_2 of the ligand (FP32 error bound)
   float log2P3;            // log2(P0 P1 P2) of the transforms
   float check_scale;       // multiplies B in the certificate check (1 in normal use)
+  float bound_scale;       // multiplies B in both the window and the check (the locator's error scale)
   const float *coords;     // [atoms][3]
   const float2 *gamma;     // [3][gamma_stride] generalised charges as float pairs
   int gamma_stride;

@@ -50,7 +50,7 @@ __global__ void k_refine_init(RefineArgs a, int n_pairs, float nS) {
   }
   if (i < a.K) {
     const RefTab t = a.tabs[i];
-    const float B = 8.f * 5.9604644775390625e-08f * sqrtf(a.log2P3) *
+    const float B = a.bound_scale * 8.f * 5.9604644775390625e-08f * sqrtf(a.log2P3) *
                     (sqrtf(t.sumsq[0] / t.vol) * a.gnorm[0] + sqrtf(t.sumsq[1] / t.vol) * a.gnorm[1] +
                      sqrtf(t.sumsq[2] / t.vol) * a.gnorm[2]);
     a.win[i] = a.kT * fmaxf(20.f, logf(1e5f * nS)) + 2.f * B;

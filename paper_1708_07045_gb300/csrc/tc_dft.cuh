@@ -4,12 +4,14 @@
 //   y[r'] = sum_r w32^(r r') * (w_P^(r j stride) * x[i + r P/32])
 // which, with complex values interleaved (k = 2r + re/im), is the real
 // 64 x 64 matrix A (rows m = 2r' + c') times a 64-vector.  A and the twiddled
-// data are each split into bf16 high and low parts (x = x_hi + x_lo, 16
-// significant bits) and the product is taken as A_hi x_hi + A_hi x_lo +
-// A_lo x_hi with mma.sync m16n8k16 (bf16 in, FP32 accumulate): three terms,
-// relative error about 2^-16 per stage.  A's fragments are precomputed on the
-// host in mma register order ([dir][term][mtile 4][kchunk 4][lane 32] x uint4)
-// and read through the read-only cache.
+// data are each split into three bf16 parts (x = x_hi + x_mid + x_lo, about
+// 24 significant bits) and the product is taken as the six terms of order up
+// to 2^-16: A_mid x_mid + A_lo x_hi + A_hi x_lo + A_mid x_hi + A_hi x_mid +
+// A_hi x_hi (smallest first), with mma.sync m16n8k16 (bf16 in, FP32
+// accumulate): relative error near FP32's per stage.  A's fragments are
+// precomputed on the host in mma register order
+// ([dir][term 3][mtile 4][kchunk 4][lane 32] x uint4) and read through the
+// read-only cache.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -17,9 +19,11 @@
 
 namespace bpmf {
 
-__device__ __forceinline__ void split_bf16(float v, float &hi, float &lo) {
+__device__ __forceinline__ void split_bf16(float v, float &hi, float &mid, float &lo) {
   hi = __bfloat162float(__float2bfloat16_rn(v));
-  lo = v - hi;
+  const float r = __fsub_rn(v, hi);  // exact
+  mid = __bfloat162float(__float2bfloat16_rn(r));
+  lo = __fsub_rn(r, mid);            // exact; rounded to bf16 when packed
 }
 __device__ __forceinline__ unsigned pk_bf16(float a, float b) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -43,14 +47,14 @@ __device__ inline void tc_dft32_stage(const cx<float> *src, cx<float> *dst, int 
   const int nb = P / 32;
   const int ncol = nb * nlines;
   const int tstride = P / (Ns * 32);
-  const uint4 *A = tca + (inv ? 2 * 4 * 4 * 32 : 0);  // [term][mtile][kchunk][lane]
+  const uint4 *A = tca + (inv ? 3 * 4 * 4 * 32 : 0);  // [term][mtile][kchunk][lane]
   for (int n0 = warp * 8; n0 < ncol; n0 += nwarps * 8) {
     // B fragments: column n0 + gid, values r = 8q + tig and 8q + tig + 4
     const int col = n0 + gid;
     const bool live = col < ncol;
     const int l = live ? col % nlines : 0, i = live ? col / nlines : 0;
     const int j = i % Ns;
-    unsigned bh[4][2], bl[4][2];
+    unsigned bh[4][2], bm[4][2], bl[4][2];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -61,10 +65,11 @@ __device__ inline void tc_dft32_stage(const cx<float> *src, cx<float> *dst, int 
           v = src[(i + r * nb) * es + l * ls];
           if (Ns > 1 && r > 0) v = c_mul(v, tw_load<float>(tw[r * j * tstride], inv));
         }
-        float rh, rl, ih, il;
-        split_bf16(v.re, rh, rl);
-        split_bf16(v.im, ih, il);
+        float rh, rm, rl, ih, im, il;
+        split_bf16(v.re, rh, rm, rl);
+        split_bf16(v.im, ih, im, il);
         bh[q][h] = pk_bf16(rh, ih);
+        bm[q][h] = pk_bf16(rm, im);
         bl[q][h] = pk_bf16(rl, il);
       }
     // output: columns n0 + 2 tig, n0 + 2 tig + 1 of the warp's tile
@@ -84,10 +89,14 @@ __device__ inline void tc_dft32_stage(const cx<float> *src, cx<float> *dst, int 
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const uint4 ah = __ldg(&A[((0 * 4 + t) * 4 + q) * 32 + lane]);
-        const uint4 al = __ldg(&A[((1 * 4 + t) * 4 + q) * 32 + lane]);
-        mma_bf16(acc, ah, bh[q][0], bh[q][1]);
-        mma_bf16(acc, ah, bl[q][0], bl[q][1]);
+        const uint4 am = __ldg(&A[((1 * 4 + t) * 4 + q) * 32 + lane]);
+        const uint4 al = __ldg(&A[((2 * 4 + t) * 4 + q) * 32 + lane]);
+        mma_bf16(acc, am, bm[q][0], bm[q][1]);
         mma_bf16(acc, al, bh[q][0], bh[q][1]);
+        mma_bf16(acc, ah, bl[q][0], bl[q][1]);
+        mma_bf16(acc, am, bh[q][0], bh[q][1]);
+        mma_bf16(acc, ah, bm[q][0], bm[q][1]);
+        mma_bf16(acc, ah, bh[q][0], bh[q][1]);
       }
       // rows m = 16 t + gid (+8): output r' = m / 2, real (m even) or imaginary part
 #pragma unroll
