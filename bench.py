@@ -29,6 +29,7 @@ import synth  # noqa: E402
 METRIC = "pose energies/s & BPMFs/s, chosen form vs plain FP32 path at 0.01 kcal/mol"
 WORKLOAD = "protein-scale: 96^3 grid h=0.25 A, 4 receptor conformations, 30-atom ligand, 2000 configurations, 40^3 site box"
 N_CONF, N_REC, N_ATOMS = 2000, 4, 30
+WORKLOAD_IS_DEFAULT = True  # the full 2000 configurations (--n-conf changes it)
 FP32_LANES_PER_SM = 128
 # FP32 instructions per float-pair flop for the add/mul mix of the radix
 # stages (add: TwoSum 6 + 2 + FastTwoSum 3 = 11; mul: 1 + 3 FMA + 3 = 7; ~70 % adds)
@@ -56,6 +57,25 @@ def kernel_src_sha(texts=None):
     i0 = h.index("struct XfusedArgs")
     xstruct = h[i0:h.index("};", i0)]
     src = "".join([prelude, xsec, xstruct, texts["fft.cuh"], texts["arith.cuh"], texts["tc_dft.cuh"]])
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
+# DRAM bytes (read + write) per launch of the FP32 x pass on the protein-scale
+# workload, averaged over one step's launches, from the ncu capture summarised
+# in profiles/xpass_fp32_protein_scale_traffic.md; valid only for the sources
+# it was taken with
+XPASS_TRAFFIC = {"bytes_per_launch": None, "launches_per_step": None, "src_sha": None}
+
+
+def xpass_src_sha():
+    """Fingerprint of the code k_xpass compiles from: xpass.cu, its argument
+    struct and the FFT / arithmetic headers."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1708_07045_gb300", "csrc")
+    h = open(os.path.join(d, "kernels.cuh")).read()
+    i0 = h.index("struct XfusedArgs")
+    src = "".join([open(os.path.join(d, "xpass.cu")).read(), h[i0:h.index("};", i0)],
+                   open(os.path.join(d, "fft.cuh")).read(), open(os.path.join(d, "arith.cuh")).read()])
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
@@ -393,7 +413,8 @@ def occupancy_leg(torch, pkg, sess, dev, stream, steps, n_acc=4, n_energy=2):
             for k, r in enumerate(w.receptors):
                 recs.append(pkg.bpmf_receptor_load(sess.ctx, grids[k], r.h, r.origin, r.site_lo, r.site_n, stream))
                 pkg.bpmf_receptor_set_occupancy(sess.ctx, recs[-1], occs[k], stream)
-            pkg.bpmf_eval(sess.ctx, lh, recs, w.kT, mode, logZ, nv, B, None, stream)
+            rc = pkg.bpmf_eval(sess.ctx, lh, recs, w.kT, mode, logZ, nv, B, None, stream)
+            return rc, pkg.bpmf_last_error(sess.ctx)
         finally:
             pkg.bpmf_ligand_free(lh)
             for r in recs:
@@ -430,12 +451,15 @@ def occupancy_leg(torch, pkg, sess, dev, stream, steps, n_acc=4, n_energy=2):
     dz = float(np.abs(lz[:n_acc][fin] - ref["logZ"][fin]).max() * w.kT) if fin.any() else None
     with np.errstate(divide="ignore"):
         free = float(np.isfinite(lz).mean())
-    # the refined form (FP32 correlation + exact window) on this workload
+    # the refined form (FP32 correlation + exact window) on this workload,
+    # after one untimed call
+    step(pkg.BPMF_MODE_REFINE)
+    flush.fill_(1.0)
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    step(pkg.BPMF_MODE_REFINE)
+    rc_ref, note_ref = step(pkg.BPMF_MODE_REFINE)
     b.record(stream)
     torch.cuda.synchronize()
     lzr = logZ.cpu().numpy()
@@ -443,8 +467,12 @@ def occupancy_leg(torch, pkg, sess, dev, stream, steps, n_acc=4, n_energy=2):
     refine = {"ms_per_step": a.elapsed_time(b),
               "max_kT_dlogZ_kcal": float(np.abs(lzr[:n_acc][finr] - ref["logZ"][finr]).max() * w.kT)
               if finr.any() else None,
-              "mask_and_counts_exact": bool(np.array_equal(np.isfinite(lzr[:n_acc]), fin))}
-    # the plain FP32 form on the bounded (cutoff) grids of this workload
+              "mask_and_counts_exact": bool(np.array_equal(np.isfinite(lzr[:n_acc]), fin)),
+              "status": int(rc_ref), "note": note_ref}
+    # the plain FP32 form on the bounded (cutoff) grids of this workload,
+    # after one untimed call
+    step(pkg.BPMF_MODE_FP32)
+    flush.fill_(1.0)
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
@@ -514,7 +542,8 @@ def whole_surface_leg(torch, pkg, sess, dev, stream, steps, n_conf=32):
         rh = None
         try:
             rh = pkg.bpmf_receptor_load(sess.ctx, grid, r.h, r.origin, r.site_lo, r.site_n, stream)
-            pkg.bpmf_eval(sess.ctx, lh, [rh], w.kT, mode, logZ, nv, None, None, stream)
+            rc = pkg.bpmf_eval(sess.ctx, lh, [rh], w.kT, mode, logZ, nv, None, None, stream)
+            return rc, pkg.bpmf_last_error(sess.ctx)
         finally:
             pkg.bpmf_ligand_free(lh)
             if rh is not None:
@@ -538,7 +567,7 @@ def whole_surface_leg(torch, pkg, sess, dev, stream, steps, n_conf=32):
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    step(pkg.BPMF_MODE_REFINE)
+    rc_ref, note_ref = step(pkg.BPMF_MODE_REFINE)
     b.record(stream)
     torch.cuda.synchronize()
     t_ref = a.elapsed_time(b)
@@ -554,7 +583,8 @@ def whole_surface_leg(torch, pkg, sess, dev, stream, steps, n_conf=32):
             "accuracy_vs_oracle": {"configurations": 1, "counts_exact": bool(n[0, 0] == ref["n_valid"][0, 0]),
                                    "kT_dlogZ_kcal": float(abs(lz[0, 0] - ref["logZ"][0, 0]) * w.kT)},
             "refine_form": {"ms_per_step": t_ref, "value": int(n.sum()) / (t_ref / 1e3),
-                            "kT_dlogZ_kcal": float(abs(lzr[0, 0] - ref["logZ"][0, 0]) * w.kT)},
+                            "kT_dlogZ_kcal": float(abs(lzr[0, 0] - ref["logZ"][0, 0]) * w.kT),
+                            "status": int(rc_ref), "note": note_ref},
             "oracle_one_configuration_s": t_or}
 
 
@@ -571,7 +601,7 @@ def proposal_q(pred, mix, tau):
     return mix * w / w.sum() + (1.0 - mix) / p.size
 
 
-def batched_leg(torch, pkg, sess, recs_in, kT, stream, steps, n_lig=141, n_conf=500, sample_frac=0.005):
+def batched_leg(torch, pkg, sess, recs_in, kT, stream, steps, n_lig=141, n_conf=500, sample_frac=0.002):
     """The batched uneven workload at full size: n_lig ligands of 8-60 atoms x
     n_conf configurations against the 10 receptor conformations of 64^3-112^3
     (receptor groups by padded edge), all in one bpmf_eval (refined form),
@@ -612,8 +642,9 @@ def batched_leg(torch, pkg, sess, recs_in, kT, stream, steps, n_lig=141, n_conf=
             res["graph" if graph else "launches"] = float(np.mean(ts))
         pkg.bpmf_set_graph_mode(sess.ctx, False)
         pkg.bpmf_profile_enable(sess.ctx, True)
-        pkg.bpmf_eval(sess.ctx, lh, recs, kT, pkg.BPMF_MODE_REFINE, out["logZ"], out["n_valid"], out["bpmf"], out["dG"],
-                      stream)
+        rc = pkg.bpmf_eval(sess.ctx, lh, recs, kT, pkg.BPMF_MODE_REFINE, out["logZ"], out["n_valid"], out["bpmf"],
+                           out["dG"], stream)
+        note = pkg.bpmf_last_error(sess.ctx)
         torch.cuda.synchronize()
         prof = pkg.bpmf_profile(sess.ctx)
         pkg.bpmf_profile_enable(sess.ctx, False)
@@ -641,7 +672,7 @@ def batched_leg(torch, pkg, sess, recs_in, kT, stream, steps, n_lig=141, n_conf=
                             "conformations of 64^3-112^3 at 0.25 A, sites 24^3-40^3, one bpmf_eval (refined form)",
                 "ms_per_eval": res["launches"], "ms_per_eval_graph": res["graph"], "poses_per_eval": poses,
                 "value": poses / (t_best / 1e3), "unit": "pose energies/s",
-                "bpmfs_per_s": n_lig * K / (t_best / 1e3), "status": int(rc),
+                "bpmfs_per_s": n_lig * K / (t_best / 1e3), "status": int(rc), "note": note,
                 "gpu_launches": int(sum(n for _, n in prof.values())),
                 "kernels_ms": {k: v[0] for k, v in prof.items()},
                 "accuracy_vs_oracle": {"sample": f"{n_s} seeded (ligand, configuration) pairs x {K} receptors",
@@ -860,7 +891,7 @@ def run_ours(args):
         sb = st_boot.cpu().numpy()
         # convergence with the number of configurations: the first J of the set
         series = []
-        for Js in (125, 250, 500, 1000, J):
+        for Js in [x for x in (125, 250, 500, 1000) if x < J] + [J]:
             us = torch.from_numpy(np.random.default_rng(78).random((R_boot, Js))).to(dev)
             st_s = torch.empty((2, K + 1), dtype=torch.float64, device=dev)
             pkg.bpmf_bootstrap(sess.ctx, outs["logZ"][:Js].contiguous(), outs["n_valid"][:Js].contiguous(), w.kT,
@@ -993,8 +1024,15 @@ def run_ours(args):
                     ach_b = work[key]["bytes"] * args.steps / (ms_tot / 1e3) / 1e9
                     peak_f = n_sm * FP32_LANES_PER_SM * 2 * sm_hz / 1e12
                     ach_f = flops / (ms_tot / 1e3) / 1e12
+                    traffic = None
+                    if (name == "k_xpass<fp32>" and XPASS_TRAFFIC["src_sha"] == xpass_src_sha()
+                            and WORKLOAD_IS_DEFAULT):
+                        traffic = XPASS_TRAFFIC["bytes_per_launch"]
                     hbm = {"kernel": name, "bound": "hbm", "achieved": ach_b, "peak": peak_b, "unit": "GB/s",
-                           "frac": ach_b / peak_b, "traffic": None,
+                           "frac": ach_b / peak_b, "traffic": traffic,
+                           "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, the "
+                                           "average over one protein-scale step's launches (null when the kernel "
+                                           "sources differ from the captured ones)",
                            "peak_note": "measured hbm_gbs (burst), MEASURED_PEAKS.json",
                            "launches": nl, "ms_per_launch": ms_tot / nl}
                     alu = {"kernel": name, "bound": "alu", "achieved": ach_f, "peak": peak_f, "unit": "TFLOP/s",
@@ -1049,7 +1087,7 @@ def run_ours(args):
 
 
 def main():
-    global N_CONF
+    global N_CONF, WORKLOAD_IS_DEFAULT
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -1069,6 +1107,7 @@ def main():
     ap.add_argument("--n-conf", type=int, default=N_CONF,
                     help="configurations per step (default: the full workload; smaller values are for profiling)")
     args = ap.parse_args()
+    WORKLOAD_IS_DEFAULT = args.n_conf == N_CONF
     N_CONF = args.n_conf
     if args.impl == "reference":
         return run_reference(args)

@@ -50,8 +50,9 @@ extern "C" {
 #define BPMF_WARN_NO_VALID 1
 /* warning (BPMF_MODE_REFINE): for at least one ligand the certificate check
  * failed (an FP32 energy further than B from its exact value) or a candidate
- * list overflowed; that ligand's results were recomputed in float pairs
- * (BPMF_MODE_FF) and are exact to the float-pair form's precision. */
+ * list overflowed again in a second pass from the first pass's minima; that
+ * ligand's results were recomputed in float pairs (BPMF_MODE_FF) and are
+ * exact to the float-pair form's precision. */
 #define BPMF_WARN_REFINE_FALLBACK 2
 
 /* Arithmetic of the correlation (forward transforms, spectral product,
@@ -83,14 +84,19 @@ extern "C" {
  *     site-window size) is re-evaluated as the direct sum the correlation
  *     equals: sum_i sum_t gamma_t,i trilinear(G_t, g_i + m).  While the bound
  *     holds, every translation within W of the true minimum is among them;
- *     the others keep their FP32 energies and together weigh less than 1e-5
- *     of S.  The bound is checked as a certificate on every re-evaluated
- *     translation (|E_fp32 - E_exact| <= B); a failure, or a candidate list
- *     that overflows, makes the call recompute that ligand in float pairs and
- *     return BPMF_WARN_REFINE_FALLBACK.  In this form bpmf_eval synchronises
- *     `stream` before returning (it reads the certificate flags).  The
- *     energies that can carry weight are exact, and so are log Z, BPMF and dG
- *     up to that 1e-5, at about the FP32 form's cost.  Exported energies
+ *     the others together weigh less than 1e-5 of S (6e-6 kcal/mol on
+ *     kT log Z) and are left out.  The bound is checked as a certificate on
+ *     every re-evaluated translation (|E_fp32 - E_exact| <= B).  A candidate
+ *     list that
+ *     overflows (flat landscapes: small ligands in wide sites) makes the call
+ *     evaluate that ligand again in this form, each pair's running minimum
+ *     starting at the first pass's; a failed check, or a second overflow,
+ *     makes it recompute the ligand in float pairs and return
+ *     BPMF_WARN_REFINE_FALLBACK (bpmf_last_error counts both).  In this form
+ *     bpmf_eval synchronises `stream` before returning (it reads the
+ *     certificate flags).  The energies that can carry weight are exact, and
+ *     so are log Z, BPMF and dG up to that 1e-5, at about the FP32 form's
+ *     cost; results are the same on every run.  Exported energies
  *     outside the window are the FP32 values.  The energy volume never
  *     reaches device memory: each site plane appends only its candidates to a
  *     per-pair list.  The receptor handle keeps a device copy of its FP32
@@ -122,7 +128,9 @@ void bpmf_destroy(bpmf_ctx_t ctx);
 
 /* One-line description of a status code (static storage). */
 const char *bpmf_status_string(int status);
-/* Reason for the last failing call on this context ("" if none). */
+/* Reason for the last failing call on this context ("" if none); after a
+ * bpmf_eval that returned BPMF_WARN_REFINE_FALLBACK, how many ligands were
+ * recomputed and why (certificate failed, candidate list overflowed). */
 const char *bpmf_last_error(bpmf_ctx_t ctx);
 
 /*
@@ -316,6 +324,14 @@ int bpmf_transform_edges(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs,
  * float-pair fallback; it exists for testing.  Errors: INVALID_ARG
  * (scale < 0). */
 int bpmf_set_refine_check_scale(bpmf_ctx_t ctx, double scale);
+
+/* bpmf_set_refine_list_cap -- candidate-list capacity per (configuration,
+ * receptor) pair in the refined form (0, the default: every translation of
+ * the site window, up to 2^23).  A small cap makes the first pass's lists
+ * overflow, which exercises the
+ * second pass from the first pass's minima (that pass uses the default
+ * lists); it exists for testing.  Errors: INVALID_ARG (cap < 0). */
+int bpmf_set_refine_list_cap(bpmf_ctx_t ctx, int cap);
 
 /* Upper bound on the device workspace bpmf_eval may hold (bytes, default
  * 3 GiB); configurations are processed in batches that fit.  Results do not

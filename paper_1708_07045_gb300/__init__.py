@@ -122,6 +122,7 @@ _SIGS = {
     "bpmf_set_graph_mode": (_I, [_P, _I]),
     "bpmf_transform_edges": (_I, [_P, _P, _P, _I, ctypes.c_uint, _P]),
     "bpmf_set_refine_check_scale": (_I, [_P, _D]),
+    "bpmf_set_refine_list_cap": (_I, [_P, _I]),
     "bpmf_features": (_I, [_P, _P, _D, _P, _P]),
     "bpmf_valid_counts": (_I, [_P, _P, _P, _I, _P]),
     "bpmf_mlp_param_count": (ctypes.c_longlong, [_I, _I, _I]),
@@ -502,3 +503,8 @@ def bpmf_transform_edges(ctx, lig, recs, total_conf, mode):
 def bpmf_set_refine_check_scale(ctx, scale):
     """Scale of B in the refined form's certificate check (testing)."""
     return _check(lib().bpmf_set_refine_check_scale(ctx, float(scale)), "bpmf_set_refine_check_scale", ctx)
+
+
+def bpmf_set_refine_list_cap(ctx, cap):
+    """Candidate-list capacity per pair in the refined form (0: the default rule; testing)."""
+    return _check(lib().bpmf_set_refine_list_cap(ctx, int(cap)), "bpmf_set_refine_list_cap", ctx)

@@ -98,6 +98,11 @@ struct bpmf_ctx {
   std::vector<double> prof_ms;
   std::vector<long long> prof_n;
   std::string err;
+  std::string note;            // the last evaluation's warning detail (refined-form fallbacks)
+  bool refine_seeded = false;    // refined form: start each pair from the stored minimum (second pass)
+  unsigned *pmin_store = nullptr;  // [total_conf][K] refined form: each pair's final running minimum
+  size_t pmin_store_n = 0;
+  int refine_list_cap = 0;        // refined form: list capacity per pair (0: the default rule)
   std::map<int, float4 *> tw;  // twiddle tables per transform length
   uint4 *tca = nullptr;        // tensor-core radix-32 fragment table (split-bf16 mode)
   const __nv_bfloat16 *tc05 = nullptr;  // the same stage's matrix in the tcgen05 layout
@@ -508,13 +513,21 @@ struct RefineCtx {
   int *fail = nullptr;            // the ligand's fallback flag
   float check_scale = 1.f;
   float bound_scale = 1.f;        // multiplies B (window and certificate)
+  unsigned *store = nullptr;      // [J][K] the ligand's pair minima (RefineArgs::store)
+  const int *order = nullptr;     // [batch] processing position -> configuration (this batch's slice)
+  const int *kmap = nullptr;      // [Kg]
+  int Kall = 0;
+  bool seeded = false;            // start from the stored minima (a second pass)
 };
 
-// Translations per pair list of the refined form: every translation of a
-// small site window, else 1/16 of them (at least 4096), at most kRefineMaxList.
-int refine_cap(const int S[3]) {
+// Translations per pair list of the refined form: every translation of the
+// site window (at most kRefineMaxList), so that no list can overflow; the
+// lists take memory, but only the translations a plane lists are written.
+// `cap` > 0 overrides (tests).
+int refine_cap(const int S[3], int cap = 0) {
   const long long nS = (long long)S[0] * S[1] * S[2];
-  return (int)std::min<long long>(std::min<long long>(nS, std::max<long long>(4096, nS / 16)), kRefineMaxList);
+  if (cap > 0) return (int)std::min<long long>(std::min<long long>(nS, cap), kRefineMaxList);
+  return (int)std::min<long long>(nS, kRefineMaxList);
 }
 
 int clash_words(int S2) { return (S2 + 31) / 32; }
@@ -553,7 +566,8 @@ template <class T>
 void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, const ConfMeta *d_meta,
                const PairInfo *d_info, const float2 *const *d_rhi, const float2 *const *d_rlo, double h,
                float nscale_hi, float nscale_lo, float escale_hi, float escale_lo, float4 *d_part,
-               double *export_E, char *ws, cudaStream_t st, const bpmf_ctx::Tune &tn, bool split = false,
+               double *export_E, char *ws, size_t ws_avail, cudaStream_t st, const bpmf_ctx::Tune &tn,
+               bool split = false,
                const OccTab *d_tabs = nullptr, const RefineCtx *rf = nullptr, const float2 *const *h_rhi = nullptr,
                int *d_err = nullptr) {
   auto plan = [&](int P) {
@@ -575,28 +589,15 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   p += align_up((size_t)batch * g.K * g.S[0] * g.S[1] * g.F2 * E);
   uint32_t *clash = nullptr;
   const int CW = clash_words(g.S[2]);
+  OccRun *runs = nullptr;
+  int *n_runs = nullptr;
   if (g.occ_cap > 0 && d_tabs) {
-    OccRun *runs = reinterpret_cast<OccRun *>(p);
+    runs = reinterpret_cast<OccRun *>(p);
     p += align_up(2 * (size_t)batch * g.occ_cap * sizeof(OccRun));
-    int *n_runs = reinterpret_cast<int *>(p);
+    n_runs = reinterpret_cast<int *>(p);
     p += align_up((size_t)batch * sizeof(int));
     clash = reinterpret_cast<uint32_t *>(p);
     p += align_up((size_t)batch * g.K * g.S[0] * g.S[1] * CW * sizeof(uint32_t));
-    OccRunsArgs ra{lg->coords, lg->R, d_meta, (float)h, g.occ_cap, runs, n_runs, g.occ_rb};
-    launch(c, "k_occ_runs", st, [&] { return launch_occ_runs(ra, batch, st); });
-    ClashArgs ca{};
-    ca.runs = runs;
-    ca.n_runs = n_runs;
-    ca.cap = g.occ_cap;
-    ca.tabs = d_tabs;
-    ca.info = d_info;
-    ca.K = g.K;
-    ca.S0 = g.S[0];
-    ca.S1 = g.S[1];
-    ca.S2 = g.S[2];
-    ca.CW = CW;
-    ca.clash = clash;
-    launch(c, "k_clash", st, [&] { return launch_clash(ca, batch, st); });
   }
   RefineArgs ra{};
   if (g.refine) {
@@ -613,6 +614,30 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     p += align_up((size_t)g.K * sizeof(float));
     ra.bnd = reinterpret_cast<float *>(p);
     p += align_up((size_t)g.K * sizeof(float));
+  }
+  // every buffer of the batch lies inside the region the plan set aside
+  if ((size_t)(p - ws) > ws_avail) {
+    last_msg = "internal: batch buffers exceed the planned workspace";
+    throw Fail{BPMF_ERR_CUDA};
+  }
+  if (g.occ_cap > 0 && d_tabs) {
+    OccRunsArgs ra{lg->coords, lg->R, d_meta, (float)h, g.occ_cap, runs, n_runs, g.occ_rb};
+    launch(c, "k_occ_runs", st, [&] { return launch_occ_runs(ra, batch, st); });
+    ClashArgs ca{};
+    ca.runs = runs;
+    ca.n_runs = n_runs;
+    ca.cap = g.occ_cap;
+    ca.tabs = d_tabs;
+    ca.info = d_info;
+    ca.K = g.K;
+    ca.S0 = g.S[0];
+    ca.S1 = g.S[1];
+    ca.S2 = g.S[2];
+    ca.CW = CW;
+    ca.clash = clash;
+    launch(c, "k_clash", st, [&] { return launch_clash(ca, batch, st); });
+  }
+  if (g.refine) {
     ra.rs.win = ra.win;
     ra.rs.bnd = ra.bnd;
     ra.rs.cap = g.ref_cap;
@@ -635,6 +660,11 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     ra.S2 = g.S[2];
     ra.part_ref = rf->part_ref;
     ra.export_E = export_E;
+    ra.store = rf->store;
+    ra.order = rf->order;
+    ra.kmap = rf->kmap;
+    ra.Kall = rf->Kall;
+    ra.seeded = rf->seeded ? 1 : 0;
     launch(c, "k_refine_init", st, [&] { return launch_refine_init(ra, batch, st); });
   }
 
@@ -943,6 +973,12 @@ int bpmf_set_refine_check_scale(bpmf_ctx_t c, double scale) {
   return BPMF_OK;
 }
 
+int bpmf_set_refine_list_cap(bpmf_ctx_t c, int cap) {
+  if (!c || cap < 0) return set_err(c, BPMF_ERR_INVALID_ARG, "cap must be >= 0");
+  c->refine_list_cap = cap;
+  return BPMF_OK;
+}
+
 int bpmf_set_workspace_limit(bpmf_ctx_t c, size_t bytes) {
   if (!c || bytes < (size_t(1) << 20)) return set_err(c, BPMF_ERR_INVALID_ARG, "workspace limit below 1 MiB");
   c->ws_budget = bytes;
@@ -980,6 +1016,7 @@ void bpmf_destroy(bpmf_ctx_t c) {
   for (auto &kv : c->blocks) cudaFree(kv.second);
   if (c->tca) cudaFree(c->tca);
   if (c->tc05) cudaFree(const_cast<__nv_bfloat16 *>(c->tc05));
+  if (c->pmin_store) cudaFree(c->pmin_store);
   if (c->ws) cudaFree(c->ws);
   for (auto &r : c->pending) {
     cudaEventDestroy(r.a);
@@ -1486,17 +1523,30 @@ std::vector<RecGroup> group_receptors(const bpmf_rec_t *recs, int K) {
 // full edges), and a crop is kept only where its configurations save at least
 // 24 configurations' worth of spectrum volume (a crop costs one transform of
 // the group's grids).
+// x-axis edge of the FP32 forms: the smallest edge of the compile-time x
+// pass (k_xpass) that holds P, when it is at most 5/4 of P (its transforms
+// cost fewer instructions per point than the generic engine's), else P.
+// Padding with zeros past the grid, like any larger edge, changes no energy
+// of the site window (no kept translation wraps).
+int xpass_edge(int P) {
+  for (int e = P; 4 * e <= 5 * P && e <= BPMF_MAX_FFT_EDGE; ++e)
+    if (xpass_supported(e)) return e;
+  return P;
+}
+
 std::vector<std::array<int, 3>> transform_edges(const ConfMeta *mj, int J, const RecGroup &g, const bpmf_rec_t *recs,
-                                                bool split) {
+                                                bool split, bool fp32_x) {
   const int Kg = (int)g.ks.size();
   std::vector<std::array<int, 3>> pc(std::max(J, 1));
-  for (int i = 0; i < J; ++i)
+  for (int i = 0; i < J; ++i) {
     for (int d = 0; d < 3; ++d) {
       int W = 0;
       for (int kg = 0; kg < Kg; ++kg) W = std::max(W, recs[g.ks[kg]]->site_n[d] + std::min(mj[i].u[d], g.P[d]) - 1);
       pc[i][d] = split ? g.P[d] : crop_edge(W, g.P[d]);
     }
-  const std::array<int, 3> Pf{g.P[0], g.P[1], g.P[2]};
+    if (fp32_x) pc[i][0] = xpass_edge(pc[i][0]);
+  }
+  const std::array<int, 3> Pf{fp32_x ? xpass_edge(g.P[0]) : g.P[0], g.P[1], g.P[2]};
   auto vol = [](const std::array<int, 3> &p) { return (double)p[0] * p[1] * (p[2] / 2 + 1); };
   std::map<std::array<int, 3>, int> count;
   for (int i = 0; i < J; ++i) ++count[pc[i]];
@@ -1554,7 +1604,7 @@ void check_timeout(bpmf_ctx *c, int n_plan_ligs) {
 int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
               double *logZ, int64_t *n_valid, double *bpmf_out, double *dG, cudaStream_t st, int only_lig,
               int only_conf, double *export_E, double *Emin = nullptr, double *Dom = nullptr,
-              std::vector<int> *fail_ligs = nullptr) {
+              std::vector<std::pair<int, int>> *fail_ligs = nullptr) {
   check_recs(recs, K, c);
   const double h = recs[0]->h;
   const bool use_ff = (mode == BPMF_MODE_FF);
@@ -1569,7 +1619,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
                                       (bpmf_out && !is_device_ptr(bpmf_out)) || (dG && !is_device_ptr(dG)) ||
                                       (Emin && !is_device_ptr(Emin)) || (Dom && !is_device_ptr(Dom)));
   // graph replay: same handles, mode, kT and output buffers as the cached graph
-  const bool use_graph = c->graph_mode && !export_E && !host_out && st != nullptr && !c->prof;
+  const bool use_graph =
+      c->graph_mode && !export_E && !host_out && st != nullptr && !c->prof && only_lig < 0 && only_conf < 0;
   std::vector<unsigned long long> key;
   if (use_graph) {
     key = {lg->id, (unsigned long long)K, mode, (unsigned long long)c->ws_budget};
@@ -1577,6 +1628,12 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     unsigned long long kb;
     std::memcpy(&kb, &kT, sizeof(kb));
     key.push_back(kb);
+    unsigned cs;  // the refined form's test settings enter the captured launches
+    std::memcpy(&cs, &c->refine_check_scale, sizeof(cs));
+    key.insert(key.end(), {(unsigned long long)cs, (unsigned long long)c->refine_list_cap});
+    // device buffers the captured launches address: a call that grew them
+    // since (outside graph mode) leaves the cached graph stale
+    key.insert(key.end(), {(unsigned long long)(uintptr_t)c->ws, (unsigned long long)(uintptr_t)c->pmin_store});
     for (const void *q : {(const void *)logZ, (const void *)n_valid, (const void *)bpmf_out, (const void *)dG,
                           (const void *)Emin, (const void *)Dom})
       key.push_back((unsigned long long)(uintptr_t)q);
@@ -1592,7 +1649,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
         CK(cudaStreamSynchronize(st));
         check_timeout(c, lig_end - lig_begin);
         for (int li = lig_begin; li < lig_end; ++li)
-          if (c->fail_host[li - lig_begin] && fail_ligs) fail_ligs->push_back(li);
+          if (c->fail_host[li - lig_begin] && fail_ligs) fail_ligs->push_back({li, c->fail_host[li - lig_begin]});
       }
       return lg_warn_cached(c) ? BPMF_WARN_NO_VALID : BPMF_OK;
     }
@@ -1652,7 +1709,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       const int Kg = (int)g.ks.size();
       GroupPlan gpn;
       const ConfMeta *mj = meta.data() + pl.j_first;
-      std::vector<std::array<int, 3>> pc = transform_edges(mj, J, g, recs, split);
+      std::vector<std::array<int, 3>> pc =
+          transform_edges(mj, J, g, recs, split, mode == BPMF_MODE_FP32 || mode == BPMF_MODE_REFINE);
       const std::array<int, 3> Pf{g.P[0], g.P[1], g.P[2]};
       // processing order: by crop, then by ligand-box extent, so each batch's
       // box (the maximum over its members) stays tight; the merge scatters
@@ -1683,7 +1741,10 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       gpn.off_occ = put(ot.data(), sizeof(OccTab) * Kg);
       std::array<int, 3> Um{1, 1, 1};
       for (int i = 0; i < J; ++i)
-        for (int d = 0; d < 3; ++d) Um[d] = std::max(Um[d], std::min(meta_s[i].u[d], g.P[d]));
+        // each box clamped by its own bucket's edges, which may exceed the
+        // padded ones (the FP32 forms' rounded x edge)
+        for (int d = 0; d < 3; ++d)
+          Um[d] = std::max(Um[d], std::min(meta_s[i].u[d], std::max(g.P[d], pc[order[i]][d])));
       Um[1] += Um[1] & 1;
       BatchGeom bg{};
       for (int d = 0; d < 3; ++d) bg.S[d] = g.S[d];
@@ -1709,7 +1770,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       gpn.occ_cap = bg.occ_cap;
       gpn.occ_rb = bg.occ_rb;
       bg.refine = refine;
-      bg.ref_cap = refine ? refine_cap(g.S) : 0;
+      bg.ref_cap = refine ? refine_cap(g.S, c->refine_seeded ? 0 : c->refine_list_cap) : 0;
       bg.nmax = lg->n_atoms[li];
       const size_t part = align_up(sizeof(float4) * (size_t)std::max(J, 1) * Kg * g.S[0]) +
                           (refine ? align_up(sizeof(float4) * 2 * (size_t)std::max(J, 1) * Kg) : 0);
@@ -1789,6 +1850,16 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   // a capture begins): workspace, pinned staging, twiddle tables, the pinned
   // certificate flags
   char *ws = static_cast<char *>(workspace(c, blob_bytes + fail_bytes + ws_need, st));
+  if (refine && (size_t)lg->total_conf * K > c->pmin_store_n) {
+    if (c->pmin_store) {
+      CK(cudaStreamSynchronize(st));
+      CK(cudaFree(c->pmin_store));
+      c->pmin_store = nullptr;
+      c->pmin_store_n = 0;
+    }
+    CK(cudaMalloc(&c->pmin_store, sizeof(unsigned) * (size_t)lg->total_conf * K));
+    c->pmin_store_n = (size_t)lg->total_conf * K;
+  }
   if (c->fail_n < (size_t)n_plan_ligs + 1) {
     if (c->fail_host) {
       CK(cudaStreamSynchronize(st));
@@ -1908,7 +1979,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
             gb.occ_cap = gp.occ_cap;
             gb.occ_rb = gp.occ_rb;
             gb.refine = refine;
-            gb.ref_cap = refine ? refine_cap(g.S) : 0;
+            gb.ref_cap = refine ? refine_cap(g.S, c->refine_seeded ? 0 : c->refine_list_cap) : 0;
             gb.nmax = lg->n_atoms[pl.li];
             RefineCtx rf;
             if (refine) {
@@ -1921,13 +1992,22 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
               // the split locator's error: measured up to ~8x the FP32 form's (the
               // tensor cores' FP32 accumulation is not IEEE-rounded)
               rf.bound_scale = split ? 8.f : 1.f;
+              rf.store = c->pmin_store + ((size_t)lg->conf_off[pl.li] + pl.j_first) * K;
+              rf.order = reinterpret_cast<const int *>(tab + gp.off_order) + b0;
+              rf.kmap = reinterpret_cast<const int *>(tab + gp.off_kmap);
+              rf.Kall = K;
+              rf.seeded = c->refine_seeded;
             }
+            // the batch buffers end inside the workspace allocation
+            const size_t avail = c->ws_bytes - (size_t)(d_batch - static_cast<char *>(c->ws));
             if (use_ff)
               run_batch<ff>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, d_rptr + Kg, h, nsh, nsl,
-                            esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, false, d_tabs);
+                            esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, avail, st, tn, false,
+                            d_tabs);
             else
               run_batch<float>(c, lg, gb, nb, d_meta + b0, d_info + (size_t)b0 * Kg, d_rptr, nullptr, h, nsh, nsl,
-                               esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, st, tn, split, d_tabs,
+                               esh, esl, d_part + (size_t)b0 * Kg * g.S[0], export_E, d_batch, avail, st, tn, split,
+                               d_tabs,
                                refine ? &rf : nullptr,
                                reinterpret_cast<const float2 *const *>(blob.data() + bk.off_rptr),
                                d_fail + n_plan_ligs);
@@ -2009,26 +2089,59 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
   }
   if (refine)  // the certificate flags: the ligands to recompute in float pairs
     for (int li = lig_begin; li < lig_end; ++li)
-      if (c->fail_host[li - lig_begin] && fail_ligs) fail_ligs->push_back(li);
+      if (c->fail_host[li - lig_begin] && fail_ligs) fail_ligs->push_back({li, c->fail_host[li - lig_begin]});
   return warn ? BPMF_WARN_NO_VALID : BPMF_OK;
 }
 
 }  // namespace
 
 namespace {
-// eval_impl plus the refined form's fallback: the ligands whose certificate
-// check failed (or whose candidate list overflowed) are evaluated again in
+// eval_impl plus the refined form's fallbacks.  A ligand whose candidate list
+// overflowed (and whose certificate held) is evaluated again in the refined
+// form, each pair's running minimum starting from the first pass's final
+// minimum; a ligand whose
+// certificate failed, or whose list overflowed again, is evaluated again in
 // float pairs over the same outputs, and the result carries
-// BPMF_WARN_REFINE_FALLBACK.
+// BPMF_WARN_REFINE_FALLBACK.  The context's note (bpmf_last_error) counts both.
 int eval_checked(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
                  double *logZ, int64_t *n_valid, double *bpmf_out, double *dG, cudaStream_t st, int only_lig,
                  int only_conf, double *export_E, double *Emin = nullptr, double *Dom = nullptr) {
-  std::vector<int> fails;
+  std::vector<std::pair<int, int>> fails;  // (ligand, reasons: bit 0 certificate, bit 1 list overflow)
   int rc = eval_impl(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, st, only_lig, only_conf, export_E, Emin,
                      Dom, &fails);
-  for (int li : fails)
-    eval_impl(c, lg, recs, K, kT, BPMF_MODE_FF, logZ, n_valid, bpmf_out, dG, st, li, only_conf, export_E, Emin, Dom);
-  if (!fails.empty()) rc |= BPMF_WARN_REFINE_FALLBACK;
+  int n_cert = 0, n_over = 0, n_rerun = 0;
+  for (const auto &f : fails) {
+    if (f.second == 2) {
+      // only the list overflowed (the certificate held where it was checked):
+      // the ligand again in the same form, every pair starting from its
+      // first-pass minimum, so that the lists hold about the final window
+      struct Seeded {
+        bpmf_ctx *c;
+        ~Seeded() { c->refine_seeded = false; }
+      } guard{c};
+      c->refine_seeded = true;
+      std::vector<std::pair<int, int>> again;
+      eval_impl(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, st, f.first, only_conf, export_E, Emin, Dom,
+                &again);
+      if (again.empty()) {
+        ++n_rerun;
+        continue;
+      }
+    }
+    eval_impl(c, lg, recs, K, kT, BPMF_MODE_FF, logZ, n_valid, bpmf_out, dG, st, f.first, only_conf, export_E, Emin,
+              Dom);
+    n_cert += (f.second & 1) != 0;
+    n_over += (f.second & 2) != 0;
+  }
+  c->note.clear();
+  if (n_rerun)
+    c->note = "refined form: " + std::to_string(n_rerun) + " ligand(s) re-run from the first pass's minima";
+  if (n_cert + n_over) {
+    rc |= BPMF_WARN_REFINE_FALLBACK;
+    c->note += std::string(c->note.empty() ? "" : "; ") + "refined form: " + std::to_string(n_cert + n_over) +
+               " ligand(s) recomputed in float pairs (certificate failed: " + std::to_string(n_cert) +
+               ", candidate list overflowed: " + std::to_string(n_over) + ")";
+  }
   return rc;
 }
 
@@ -2045,7 +2158,7 @@ int eval_entry(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, doubl
     last_msg.clear();
     int rc = eval_checked(c, lg, recs, K, kT, mode, logZ, n_valid, bpmf_out, dG, (cudaStream_t)stream, -1, -1,
                           nullptr, psi_min, psi_dom);
-    c->err.clear();
+    c->err = c->note;  // empty unless a warning has a detail to report
     return rc;
   } catch (Fail f) {
     return set_err(c, f.code, last_msg.empty() ? bpmf_status_string(f.code) : last_msg);
@@ -2072,8 +2185,9 @@ int bpmf_transform_edges(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, in
       ligand_tables(lg, li, recs, K, recs[0]->h, meta, info, nv);
       const int J = lg->n_conf[li];
       for (const RecGroup &g : groups) {
-        const std::vector<std::array<int, 3>> pc = transform_edges(
-            meta.data(), J, g, recs, mode == BPMF_MODE_SPLIT_BF16 || mode == BPMF_MODE_SPLIT_REFINE);
+        const std::vector<std::array<int, 3>> pc =
+            transform_edges(meta.data(), J, g, recs, mode == BPMF_MODE_SPLIT_BF16 || mode == BPMF_MODE_SPLIT_REFINE,
+                            mode == BPMF_MODE_FP32 || mode == BPMF_MODE_REFINE);
         for (int i = 0; i < J; ++i)
           for (int k : g.ks)
             for (int d = 0; d < 3; ++d) edges[((lg->conf_off[li] + i) * K + k) * 3 + d] = pc[i][d];

@@ -106,12 +106,12 @@ __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, 
     v[4] = c_sub(t1, u1);
     v[2] = c_add(t2, u2);
     v[3] = c_sub(t2, u2);
-  } else if constexpr (R == 9 || R == 10 || R == 12) {
+  } else if constexpr (R == 9 || R == 10 || R == 12 || R == 14 || R == 15 || R == 16) {
     // composite radix R = R1 R2 in registers (Cooley-Tukey, decimation in
     // time): R2 DFTs of length R1 over the strided inputs v[R2 n1 + n2],
     // internal twiddles w_R^(n2 k1), then R1 DFTs of length R2; output
     // k1 + R1 k2
-    constexpr int R1 = R == 9 ? 3 : (R == 10 ? 2 : 4);
+    constexpr int R1 = (R == 9 || R == 15) ? 3 : ((R == 10 || R == 14) ? 2 : 4);
     constexpr int R2 = R / R1;
     cx<T> a[R2][R1];
 #pragma unroll

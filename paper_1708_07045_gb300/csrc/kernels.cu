@@ -655,15 +655,18 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
       if (ok) {
         const cx<T> z = res[(r >> 1) * ls + zi];
         const T val = (r & 1) ? z.im : z.re;
-        x = s_norm(s_mul(val, nscale));
-        if (ff_gt(x, vmax)) vmax = x;
         if (refine) {
           ef = s_hi(s_norm(s_mul(val, escale)));
           emin = fminf(emin, ef);
+        } else {
+          x = s_norm(s_mul(val, nscale));
+          if (ff_gt(x, vmax)) vmax = x;
         }
       }
-      xs[idx] = x;
-      if (refine) es[idx] = ef;
+      if (refine)
+        es[idx] = ef;
+      else
+        xs[idx] = x;
       if (a.export_E && jk == 0) {
         double e = CUDART_INF;
         if (ok) {
@@ -676,7 +679,11 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
     }
     if (refine) {
       // the chunk's minimum lowers the pair's running minimum; translations
-      // within W + 2B of it are appended to the pair's list (warp-aggregated)
+      // within W + 2B of it are appended to the pair's list (warp-aggregated).
+      // The list is the pair's whole weight: every translation left out lies
+      // more than W above the pair's minimum (its FP32 energy exceeds the
+      // final minimum + W + 2B), and together they weigh less than 1e-5 of S,
+      // so the plane writes no partial of its own
       for (int o = 16; o > 0; o >>= 1) emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
       if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = emin;
       __syncthreads();
@@ -705,19 +712,11 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
           if (lane == 0) base = atomicAdd(&a.rs.cnt[jk], __popc(bal));
           base = __shfl_sync(0xffffffffu, base, 0);
           const int slot = base + __popc(bal & ((1u << lane) - 1u));
-          if (keep && slot < a.rs.cap) {
-            list[slot] = Cand{t0 + (unsigned)idx, ef, s_hi(xs[idx])};
-            // k_refine accounts for the listed translations: this plane's
-            // partial leaves them out (one that did not fit the list stays
-            // in, and the overflow sends the ligand to the float-pair form)
-            xs[idx] = s_mk<T>(-CUDART_INF_F, 0.f);
-          }
+          // (a translation that does not fit makes k_refine flag the overflow)
+          if (keep && slot < a.rs.cap) list[slot] = Cand{t0 + (unsigned)idx, ef};
         }
       }
-      __syncthreads();
-      vmax = s_mk<T>(-CUDART_INF_F, 0.f);  // the largest of what is left
-      for (int idx = threadIdx.x; idx < nS; idx += blockDim.x)
-        if (ff_gt(xs[idx], vmax)) vmax = xs[idx];
+      continue;  // the next chunk's first barrier orders these reads of es before its writes
     }
     // block max of the chunk
     for (int o = 16; o > 0; o >>= 1) {
@@ -841,8 +840,8 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
   double Mx = -CUDART_INF;
   for (int c = 0; c < a.S0; ++c)
     if (pp[c].z > 0.f) Mx = fmax(Mx, (double)pp[c].x + (double)pp[c].y);
-  // refined form: the pair's listed translations (left out of the plane
-  // partials), exact where they were refined
+  // refined form: the pair's re-evaluated translations (their weight sum as
+  // a float pair)
   double X = -CUDART_INF;  // largest exact -E/kT
   float4 rc{0.f, 0.f, 0.f, 0.f};
   if (a.part_ref) {
@@ -857,7 +856,7 @@ __global__ void __launch_bounds__(128) k_merge_pairs(MergeArgs a) {
   if (Mx > -CUDART_INF) {
     for (int c = 0; c < a.S0; ++c)
       if (pp[c].z > 0.f) s += (double)pp[c].z * exp((double)pp[c].x + (double)pp[c].y - Mx);
-    if (rc.z > 0.f) s += (double)rc.z * exp((double)rc.x + (double)rc.y - Mx);
+    if (rc.z > 0.f) s += ((double)rc.z + (double)rc.w) * exp((double)rc.x + (double)rc.y - Mx);
   }
   // the dominant state: the largest -E/kT, exact where the pair was refined
   const double Xd = X > -CUDART_INF ? X : Mx;

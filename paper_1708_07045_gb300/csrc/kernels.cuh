@@ -160,11 +160,10 @@ struct RefTab {            // one receptor's grids, FP32 [3][N0][N1][N2]
 };
 
 // A translation kept for the exact re-evaluation: window index
-// t = (s0 S1 + s1) S2 + s2, its FP32 energy e and its FP32 -E/kT value x (the
-// weight it keeps when it lies above the final threshold).
+// t = (s0 S1 + s1) S2 + s2 and its FP32 energy e.
 struct Cand {
   unsigned t;
-  float e, x;
+  float e;
 };
 
 // Running per-pair state of one batch of the refined form.  k_refine_init
@@ -193,7 +192,7 @@ __device__ __forceinline__ unsigned f2ord(float f) {
 __device__ __forceinline__ float ord2f(unsigned u) {
   return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
-constexpr int kRefineMaxList = 1 << 22;  // translations per pair list (fixed-point sum range)
+constexpr int kRefineMaxList = 1 << 23;  // translations per pair list (fixed-point sum range)
 
 struct RefineArgs {
   RefineState rs;
@@ -212,9 +211,17 @@ struct RefineArgs {
   float kT;                // kcal/mol
   float nikT_hi, nikT_lo;  // -1 / kT as a float pair
   int K, S0, S1, S2;
-  float4 *part_ref;        // [batch][K][2] per pair: {level M hi, lo, sum of weights, 0} over the listed
-                           // translations (exact below the threshold), then {max exact -E/kT hi, lo, 0, 0}
+  float4 *part_ref;        // [batch][K][2] per pair: {level M hi, lo, sum of weights hi, lo} over the
+                           // re-evaluated translations, then {max exact -E/kT hi, lo, 0, 0}
   double *export_E;        // optional, batch entry 0, receptor 0: [S0][S1][S2] (exact where refined)
+  // each pair's final running minimum, kept per (configuration, receptor) of
+  // the ligand so that a second pass can start from it: store[order[j] Kall +
+  // kmap[k]] (k_refine writes it; k_refine_init reads it when seeded)
+  unsigned *store;
+  const int *order;        // [batch] processing position -> the ligand's configuration index
+  const int *kmap;         // [K] group-local receptor -> receptor index of the call
+  int Kall;
+  int seeded;
 };
 
 struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp partials
@@ -242,7 +249,7 @@ struct ZinvArgs {          // z: C2R + scale + mask + max-shifted log-sum-exp pa
 
 struct MergeArgs {
   const float4 *part;      // [J][Kg][S0] of one receptor group, processing order
-  const float4 *part_ref;  // [J][Kg][2] refined form: each pair's correction (RefineArgs::part_ref), or null
+  const float4 *part_ref;  // [J][Kg][2] refined form: each pair's re-evaluated weight (RefineArgs::part_ref), or null
   const long long *nvalid; // [J][K], caller's order, all receptors
   const int *order;        // [J] processing position -> caller's configuration index (null: identity)
   const int *kmap;         // [Kg] group-local receptor -> receptor index in the call (null: identity)

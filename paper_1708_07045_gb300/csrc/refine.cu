@@ -8,32 +8,29 @@
 // grid at every atom, Eqs. general_form / receptor_grid / correlation_func),
 // in float-pair arithmetic built from FP32 instructions (about 2^-44
 // relative).  The window W = kT max(20, ln(1e5 n)) (n translations in the
-// site window) keeps the weight of the translations left at their FP32 values
-// below 1e-5 of S.
+// site window) keeps the weight of all the other translations below 1e-5 of
+// S together (at most 6e-6 kcal/mol on kT log Z); they are left out.
 //
 // Per batch:
 //   k_refine_init  -- W + 2B and B per receptor; reset each pair's running
-//                     minimum and candidate count;
+//                     minimum (or, in a second pass, set it to the first
+//                     pass's final minimum) and candidate count;
 //   k_zinv         -- (kernels.cu) each plane lowers its pair's running
 //                     minimum and appends the translations within W + 2B of
 //                     it to the pair's list (a superset of those within
-//                     W + 2B of the final minimum); its LSE partial leaves
-//                     the listed translations out;
+//                     W + 2B of the final minimum); it writes no partial;
 //   k_refine       -- one CTA per pair: the final threshold from the final
 //                     minimum; every listed translation below it is
 //                     re-evaluated exactly (a warp per translation, lanes
 //                     over atoms) and checked against its FP32 energy
-//                     (|E_fp32 - E_exact| <= B, the certificate); the listed
-//                     translations above it keep their FP32 weights; the
-//                     pair's partial over its list joins the planes'
-//                     partials in the merge.
-// The refined weights are summed in order-independent fixed point.  Which
-// translations above the final threshold a plane lists depends on the order
-// in which the planes ran, so those weights (each below e^(-W/kT) of the
-// largest) are summed in one place or the other: results agree between runs
-// to rounding of that remainder (about 1e-12 relative).  A failed check or an
-// overflowing list sets a flag that makes bpmf_eval recompute the ligand in
-// float pairs.
+//                     (|E_fp32 - E_exact| <= B, the certificate); their
+//                     weights, summed in order-independent fixed point, are
+//                     the pair's partial in the merge.
+// The set below the final threshold does not depend on the order in which
+// the planes ran, so results are the same on every run.  A failed check sets
+// a flag that makes bpmf_eval recompute the ligand in float pairs; an
+// overflowing list, one that makes it run the ligand again from the stored
+// minima.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -45,7 +42,10 @@ namespace bpmf {
 __global__ void k_refine_init(RefineArgs a, int n_pairs, float nS) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_pairs) {
-    a.rs.pmin[i] = f2ord(CUDART_INF_F);
+    // a second pass starts from the first pass's minimum: an FP32 energy of a
+    // valid translation, so at least E_min - B, and the lists hold no more
+    // than the final window (plus what lower FP32 values add)
+    a.rs.pmin[i] = (a.seeded && a.store) ? a.store[a.order[i / a.K] * a.Kall + a.kmap[i % a.K]] : f2ord(CUDART_INF_F);
     a.rs.cnt[i] = 0;
   }
   if (i < a.K) {
@@ -91,12 +91,11 @@ __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi 
 // pair's level, every weight <= 1): integer adds are exact and
 // order-independent, so the result does not depend on the order in which
 // k_zinv appended the translations.
-constexpr double kFixScale = 1099511627776.0;  // 2^40 (lists of up to 2^22 translations)
+constexpr double kFixScale = 1099511627776.0;  // 2^40 (lists of up to 2^23 translations: sums < 2^63)
 
 __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
   __shared__ ff s_g[3][256];    // atom positions in the ligand-box frame (grid units)
   __shared__ ff s_gam[3][256];  // gamma_t,i
-  __shared__ float s_red[8][2];
   __shared__ float s_redx[8][2];
   __shared__ unsigned long long s_we;
   const int pair = blockIdx.x;  // j * K + k
@@ -104,7 +103,8 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
   const int n_list = min(a.rs.cnt[pair], a.rs.cap);
   if (threadIdx.x == 0) {
     s_we = 0ull;
-    if (a.rs.cnt[pair] > a.rs.cap) atomicOr(a.rs.fail, 1);  // list overflow
+    if (a.rs.cnt[pair] > a.rs.cap) atomicOr(a.rs.fail, 2);  // list overflow (bit 1)
+    if (a.store) a.store[a.order[j] * a.Kall + a.kmap[k]] = a.rs.pmin[pair];
   }
   const float Emin = ord2f(a.rs.pmin[pair]);
   // the final threshold (k_zinv listed against thresholds at least as high)
@@ -132,17 +132,14 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
   double *expo = (a.export_E && pair == 0) ? a.export_E : nullptr;
   // pass 1: exact -E/kT of every listed translation below the final
   // threshold (a warp per translation, lanes over atoms), the certificate
-  // check, the largest exact -E/kT, and the largest FP32 -E/kT of the listed
-  // translations above the threshold
+  // check and the largest exact -E/kT
   ff Xe{-CUDART_INF_F, 0.f};  // max exact
-  float Xf = -CUDART_INF_F;    // max FP32
   bool bad = false;
   for (int b0 = warp * 32; b0 < n_list; b0 += nwarp * 32) {
     const int idx = b0 + lane;
-    Cand cd{0u, CUDART_INF_F, -CUDART_INF_F};
+    Cand cd{0u, CUDART_INF_F};
     if (idx < n_list) cd = list[idx];
     const bool cand = idx < n_list && cd.e <= T;
-    if (idx < n_list && !cand) Xf = fmaxf(Xf, cd.x);  // kept at its FP32 weight
     unsigned bal = __ballot_sync(0xffffffffu, cand);
     while (bal) {
       const int src = __ffs(bal) - 1;
@@ -191,22 +188,19 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
       }
     }
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.rs.fail, 1);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.rs.fail, 1);  // certificate (bit 0)
   for (int o = 16; o > 0; o >>= 1) {
     const ff o2{__shfl_xor_sync(0xffffffffu, Xe.hi, o), __shfl_xor_sync(0xffffffffu, Xe.lo, o)};
     if (ff_gt(o2, Xe)) Xe = o2;
-    Xf = fmaxf(Xf, __shfl_xor_sync(0xffffffffu, Xf, o));
   }
   if (lane == 0) {
     s_redx[warp][0] = Xe.hi;
     s_redx[warp][1] = Xe.lo;
-    s_red[warp][0] = Xf;
   }
   __syncthreads();  // also publishes the exact values written to the list
   for (int w = 0; w < nwarp; ++w) {
     const ff o2{s_redx[w][0], s_redx[w][1]};
     if (ff_gt(o2, Xe)) Xe = o2;
-    Xf = fmaxf(Xf, s_red[w][0]);
   }
   if (!(Xe.hi > -CUDART_INF_F)) {  // no translation below the threshold (no valid translation)
     if (threadIdx.x == 0) {
@@ -215,23 +209,22 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
     }
     return;
   }
-  // level: the largest of the exact and the FP32 values, so every weight <= 1
-  const ff L = ff_gt(ff{Xf, 0.f}, Xe) ? ff{Xf, 0.f} : Xe;
-  // pass 2: the weight of every listed translation, exact below the threshold
+  // level: the largest exact value, so every weight <= 1
+  const ff L = Xe;
+  // pass 2: the exact weight of every listed translation below the threshold
   unsigned long long wt = 0ull;
   for (int idx = threadIdx.x; idx < n_list; idx += blockDim.x) {
-    const Cand cd = list[idx];
-    ff x{cd.x, 0.f};
-    if (cd.e <= T) {
+    if (list[idx].e <= T) {
       const float2 xe = ex[idx];
-      x = ff{xe.x, xe.y};
+      wt += (unsigned long long)__double2ll_rn((double)expf(d_ff(ff{xe.x, xe.y}, L)) * kFixScale);
     }
-    wt += (unsigned long long)__double2ll_rn((double)expf(d_ff(x, L)) * kFixScale);
   }
   atomicAdd(&s_we, wt);
   __syncthreads();
   if (threadIdx.x == 0) {
-    a.part_ref[2 * pair] = make_float4(L.hi, L.lo, (float)((double)s_we / kFixScale), 0.f);
+    const double sw = (double)s_we / kFixScale;  // exact to double rounding; kept as a float pair
+    const float sw_hi = (float)sw;
+    a.part_ref[2 * pair] = make_float4(L.hi, L.lo, sw_hi, (float)(sw - (double)sw_hi));
     a.part_ref[2 * pair + 1] = make_float4(Xe.hi, Xe.lo, 0.f, 0.f);
   }
 }

@@ -1,5 +1,5 @@
 // The x pass of the FP32 forms on compile-time transform edges P = 8 R
-// (R = 8, 9, 10, 12: edges 64, 72, 80, 96): forward DFT of the ligand's three
+// (R = 8, 9, 10, 12, 14, 15, 16: edges 64 to 128): forward DFT of the ligand's three
 // channels along x, the conj-multiply-sum with every receptor spectrum (Eq.
 // fft_correlation_func), inverse DFT along x, site window (the same work as
 // k_xfused, organised for fewer instructions per point).
@@ -18,7 +18,11 @@
 // half-warp owns one unit at a time and its 16 lanes are the 16 lines of a
 // channel (configuration g = lane / 8, column l = lane % 8): every shared
 // access of a half-warp is 16 consecutive float2 (no bank conflicts), and the
-// index arithmetic is per unit, not per element.
+// index arithmetic is per unit, not per element.  Shared-memory round trips
+// are kept to the two transposes each DFT needs: stage A reads the ligand's
+// rows from global memory into registers, the spectral product is formed
+// inside the first inverse stage from the staged receptor tile, and the last
+// inverse stage writes the site-window rows straight to global memory.
 //
 // Each receptor's spectra for the CTA's columns (3 channels x P frequencies x
 // 8 columns) are staged in shared memory while the previous transform runs:
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
   extern __shared__ float4 smem[];
   float4 *tw = smem;                                         // [P] exp(-2 pi i k / P)
   cx<float> *L = reinterpret_cast<cx<float> *>(tw + P);      // [P][48] ligand spectra (permuted rows)
-  cx<float> *W = L + P * kXpNLF;                             // [P][16] products, inverse
+  cx<float> *W = L + P * kXpNLF;                             // [P][16] inverse transform
   // [3][P][8] staged receptor spectra, 128-byte aligned (TMA destination)
   cx<float> *RS = reinterpret_cast<cx<float> *>((reinterpret_cast<uintptr_t>(W + P * NLI) + 127) & ~uintptr_t(127));
   __shared__ int s_wm[2];                                    // window start along x, mod P, per g
@@ -144,43 +148,36 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
   const int j = j0 + g, q = q0 + l;
   const bool live = j < batch && q < Q;
   for (int i = tid; i < P; i += kXpNT) tw[i] = a.tw[i];
-  // ligand spectra of this tile (rows beyond each configuration's ligand box
-  // are zero) and the first receptor's spectra, asynchronously
-  {
-    const int U0 = a.U0 < P ? a.U0 : P;
-    const int u0[2] = {j0 < batch ? min(a.meta ? a.meta[j0].u[0] : U0, U0) : 0,
-                       j0 + 1 < batch ? min(a.meta ? a.meta[j0 + 1].u[0] : U0, U0) : 0};
-    const cx<float> *ly = reinterpret_cast<const cx<float> *>(a.ly);
-    // copy e = ((x * 3 + t) * 2 + gg) * 4 + c: columns 2c, 2c + 1 of row (gg, t, x)
-    for (int e = tid; e < P * 3 * 8; e += kXpNT) {
-      const int c = e & 3, gg = (e >> 2) & 1, xt = e >> 3, x = xt / 3, t = xt - 3 * x;
-      const bool v = x < u0[gg] && q0 + 2 * c < Q;
-      const long long gi = (((long long)(j0 + gg) * 3 + t) * a.U0 + x) * Q + q0 + 2 * c;
-      cp16(&L[x * kXpNLF + t * 16 + gg * 8 + 2 * c], v ? ly + gi : ly, v);
+  // the first receptor's spectra, asynchronously, while the ligand's are transformed
+  if constexpr (TMA) {
+    if (tid == 0) {
+      mbar_init(&s_bar, 1);
+      if (a.K > 0) tma_load_3d(RS, &maps.m[0], 2 * q0, 0, 0, &s_bar, kTileBytes);
     }
-    if constexpr (TMA) {
-      if (tid == 0) {
-        mbar_init(&s_bar, 1);
-        if (a.K > 0) tma_load_3d(RS, &maps.m[0], 2 * q0, 0, 0, &s_bar, kTileBytes);
-      }
-    } else {
-      if (a.K > 0) stage_receptor<P>(RS, a.rhi[0], Q, q0);
-    }
-    cp_wait_all();
+  } else {
+    if (a.K > 0) stage_receptor<P>(RS, a.rhi[0], Q, q0);
   }
   __syncthreads();
-  // forward A: unit (n1, t), R-point DFT of rows n1 + 8 n2, twiddled
-  for (int u = hw; u < 8 * 3; u += kXpNT / 16) {
-    const int n1 = u & 7, t = u >> 3;
-    cx<float> *col = L + n1 * kXpNLF + t * 16 + hl;
-    cx<float> v[R];
+  // forward A: unit (n1, t), R-point DFT over n2 of rows n1 + 8 n2 read
+  // straight from the ligand's y-z spectra (rows at or beyond the
+  // configuration's box extent u0 are zero and not read), twiddled, into L
+  {
+    const int U0 = a.U0 < P ? a.U0 : P;
+    const int u0 = live ? min(a.meta ? a.meta[j].u[0] : U0, U0) : 0;
+    const cx<float> *ly = reinterpret_cast<const cx<float> *>(a.ly);
+    for (int u = hw; u < 8 * 3; u += kXpNT / 16) {
+      const int n1 = u & 7, t = u >> 3;
+      const cx<float> *src = ly + (((long long)j * 3 + t) * a.U0 + n1) * Q + q;
+      cx<float> v[R];
 #pragma unroll
-    for (int n2 = 0; n2 < R; ++n2) v[n2] = col[8 * n2 * kXpNLF];
-    dft_small<float, R>(v, false, tw, P);
+      for (int n2 = 0; n2 < R; ++n2) v[n2] = n1 + 8 * n2 < u0 ? src[(long long)8 * n2 * Q] : cx<float>{0.f, 0.f};
+      dft_small<float, R>(v, false, tw, P);
 #pragma unroll
-    for (int k2 = 1; k2 < R; ++k2) v[k2] = c_mul(v[k2], tw_load<float>(tw[n1 * k2], false));
+      for (int k2 = 1; k2 < R; ++k2) v[k2] = c_mul(v[k2], tw_load<float>(tw[n1 * k2], false));
+      cx<float> *col = L + n1 * kXpNLF + t * 16 + hl;
 #pragma unroll
-    for (int k2 = 0; k2 < R; ++k2) col[8 * k2 * kXpNLF] = v[k2];
+      for (int k2 = 0; k2 < R; ++k2) col[8 * k2 * kXpNLF] = v[k2];
+    }
   }
   __syncthreads();
   // forward B: unit (k2, t), 8-point DFT of rows 8 k2 + n1 -> row 8 k2 + k1 = X[k2 + R k1]
@@ -194,6 +191,7 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
 #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) col[k1 * kXpNLF] = v[k1];
   }
+  if constexpr (!TMA) cp_wait_all();
   for (int k = 0; k < a.K; ++k) {
     if (tid < 2) {
       const int jj = j0 + tid;
@@ -204,14 +202,27 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
     } else {
       __syncthreads();
     }
-    // product: unit row, P_k = sum_t R_{k,t} conj(L_t) at frequency f(row)
-    for (int row = hw; row < P; row += kXpNT / 16) {
-      // TMA tiles hold natural frequency order, the cp.async tiles row order
-      const int rrow = TMA ? (row >> 3) + R * (row & 7) : row;
-      const cx<float> *rs = RS + rrow * kXpLW + l;
-      const cx<float> *lx = L + row * kXpNLF + hl;
-      W[row * NLI + hl] = c_add(c_add(c_mulconj(rs[0], lx[0]), c_mulconj(rs[P * kXpLW], lx[16])),
-                                c_mulconj(rs[2 * P * kXpLW], lx[32]));
+    const int wm = s_wm[g];  // read before the next write, which follows the barrier below
+    // product and inverse B', unit k2: P_k = sum_t R_{k,t} conj(L_t) at the
+    // frequencies k2 + R k1 (rows 8 k2 + k1), inverse 8-point DFT over k1,
+    // then conj(w_P^(n1 k2)), into rows 8 k2 + n1 of W
+    for (int k2 = hw; k2 < R; k2 += kXpNT / 16) {
+      cx<float> v[8];
+#pragma unroll
+      for (int k1 = 0; k1 < 8; ++k1) {
+        const int row = 8 * k2 + k1;
+        // TMA tiles hold natural frequency order, the cp.async tiles row order
+        const cx<float> *rs = RS + (TMA ? k2 + R * k1 : row) * kXpLW + l;
+        const cx<float> *lx = L + row * kXpNLF + hl;
+        v[k1] = c_add(c_add(c_mulconj(rs[0], lx[0]), c_mulconj(rs[P * kXpLW], lx[16])),
+                      c_mulconj(rs[2 * P * kXpLW], lx[32]));
+      }
+      dft_small<float, 8>(v, true, tw, P);
+      cx<float> *col = W + 8 * k2 * NLI + hl;
+#pragma unroll
+      for (int n1 = 1; n1 < 8; ++n1) v[n1] = c_mul(v[n1], tw_load<float>(tw[n1 * k2], true));
+#pragma unroll
+      for (int n1 = 0; n1 < 8; ++n1) col[n1 * NLI] = v[n1];
     }
     __syncthreads();
     // the next receptor's spectra stream in while this one is transformed back
@@ -222,40 +233,26 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
         stage_receptor<P>(RS, a.rhi[k + 1], Q, q0);
       }
     }
-    // inverse B': unit k2, inverse 8-point DFT over k1, then conj(w_P^(n1 k2))
-    for (int k2 = hw; k2 < R; k2 += kXpNT / 16) {
-      cx<float> *col = W + 8 * k2 * NLI + hl;
-      cx<float> v[8];
-#pragma unroll
-      for (int k1 = 0; k1 < 8; ++k1) v[k1] = col[k1 * NLI];
-      dft_small<float, 8>(v, true, tw, P);
-#pragma unroll
-      for (int n1 = 1; n1 < 8; ++n1) v[n1] = c_mul(v[n1], tw_load<float>(tw[n1 * k2], true));
-#pragma unroll
-      for (int n1 = 0; n1 < 8; ++n1) col[n1 * NLI] = v[n1];
-    }
-    __syncthreads();
-    // inverse A': unit n1, inverse R-point DFT over k2 -> row n1 + 8 n2 (natural)
+    // inverse A', unit n1: inverse R-point DFT over k2 -> x[n1 + 8 n2]; the
+    // rows inside the site window along x go straight to the output
     if (hw < 8) {
       const int n1 = hw;
-      cx<float> *col = W + n1 * NLI + hl;
+      const cx<float> *col = W + n1 * NLI + hl;
       cx<float> v[R];
 #pragma unroll
       for (int k2 = 0; k2 < R; ++k2) v[k2] = col[8 * k2 * NLI];
       dft_small<float, R>(v, true, tw, P);
+      if (live) {
+        cx<float> *dst = reinterpret_cast<cx<float> *>(a.x2) + ((long long)j * a.K + k) * a.S0 * Q + q;
 #pragma unroll
-      for (int n2 = 0; n2 < R; ++n2) col[8 * n2 * NLI] = v[n2];
-    }
-    __syncthreads();
-    // site window along x: unit s
-    for (int s = hw; s < a.S0; s += kXpNT / 16) {
-      int m = s_wm[g] + s;  // s < S0 <= P
-      m -= m >= P ? P : 0;
-      if (live)
-        reinterpret_cast<cx<float> *>(a.x2)[(((long long)j * a.K + k) * a.S0 + s) * Q + q] = W[m * NLI + hl];
+        for (int n2 = 0; n2 < R; ++n2) {
+          int s = n1 + 8 * n2 - wm;
+          s += s < 0 ? P : 0;
+          if (s < a.S0) dst[(long long)s * Q] = v[n2];
+        }
+      }
     }
     if constexpr (!TMA) cp_wait_all();
-    __syncthreads();
   }
 }
 
@@ -330,7 +327,9 @@ cudaError_t launch_xpass_p(const XfusedArgs &a, int batch, cudaStream_t st) {
 
 }  // namespace
 
-bool xpass_supported(int P) { return P == 64 || P == 72 || P == 80 || P == 96; }
+bool xpass_supported(int P) {
+  return P == 64 || P == 72 || P == 80 || P == 96 || P == 112 || P == 120 || P == 128;
+}
 
 cudaError_t launch_xpass(const XfusedArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
@@ -341,6 +340,9 @@ cudaError_t launch_xpass(const XfusedArgs &a, int batch, cudaStream_t st) {
     case 72: return launch_xpass_p<72>(a, batch, st);
     case 80: return launch_xpass_p<80>(a, batch, st);
     case 96: return launch_xpass_p<96>(a, batch, st);
+    case 112: return launch_xpass_p<112>(a, batch, st);
+    case 120: return launch_xpass_p<120>(a, batch, st);
+    case 128: return launch_xpass_p<128>(a, batch, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -44,7 +44,10 @@ def _check(out, ligs, recs):
         if ok.any():
             assert np.abs(out["logZ"][off:off + J][ok] - ref["logZ"][ok]).max() * KT <= E_TOL
         fin = np.isfinite(ref["bpmf"])
-        assert np.abs(out["bpmf"][i][fin] - ref["bpmf"][fin]).max() <= B_TOL
+        if fin.any():
+            assert np.abs(out["bpmf"][i][fin] - ref["bpmf"][fin]).max() <= B_TOL
+        else:
+            assert not np.isfinite(out["bpmf"][i]).any()
         off += J
 
 
@@ -78,3 +81,63 @@ def test_largest_fft_edge_and_chunked_spreading(pkg):
     rc, out = _run(pkg, [r2], [lig2])
     _check(out, [lig2], [r2])
     assert out["n_valid"].sum() > 0
+
+
+@pytest.mark.parametrize("n0,edge", [(84, 96), (100, 112), (117, 120), (126, 128)])
+def test_fp32_x_edge_rounded_to_the_compile_time_x_pass(pkg, n0, edge):
+    """In the FP32 forms the x-axis transform edge is rounded up to the
+    compile-time x pass's edges (8 R, R = 8 ... 16) when that costs at most
+    5/4 of the edge: zero padding past the grid changes no energy of the site
+    window.  The refined form on such edges still meets the tolerances against
+    the oracle, and the transform-edge query reports the rounded edge (the
+    y and z edges stay the padded ones)."""
+    from paper_1708_07045_gb300.session import Session
+    h = 0.25
+    atoms = synth.receptor_atoms(60 + n0, 300, 3.0, 14.0)
+    shape = (n0, 24, 24)
+    g, o = synth.receptor_grids(atoms, shape, h)
+    lo, sn = synth.central_site(shape, (8, 6, 6))
+    r = synth.ReceptorInput(g, h, o, lo, sn)
+    lig = synth.LigandInput(synth.ligand_params(61, 5), synth.ligand_configs(62, 5, 4))
+    with Session(0) as s:
+        rh = s.load_receptor(r)
+        lh, _, _ = s.load_ligands([lig])
+        edges = pkg.bpmf_transform_edges(s.ctx, lh, [rh], 4, pkg.BPMF_MODE_REFINE)
+        edges_ff = pkg.bpmf_transform_edges(s.ctx, lh, [rh], 4, pkg.BPMF_MODE_FF)
+        rc, out = s.eval(lh, [rh], KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=4)
+    assert np.all(edges[:, 0, 0] == edge)
+    assert np.all(edges[:, 0, 1:] == pkg.bpmf_fft_edge(24))
+    assert np.all(edges_ff[:, 0, 0] == pkg.bpmf_fft_edge(n0))
+    assert not (rc & pkg.BPMF_WARN_REFINE_FALLBACK)
+    _check(out, [lig], [r])
+
+
+def test_fp32_box_wider_than_the_padded_edge_next_to_a_small_one(pkg):
+    """A ligand whose box (90 nodes along x) is wider than the receptor's
+    padded edge (84) but not than the rounded x edge of the FP32 forms (96),
+    batched with a small ligand: the batch buffers are sized by the boxes
+    clamped to the bucket's own edges.  The wide ligand has no valid
+    translation; the small one meets the tolerances."""
+    from paper_1708_07045_gb300.session import Session
+    h = 0.25
+    atoms = synth.receptor_atoms(71, 300, 3.0, 14.0)
+    shape = (84, 24, 24)
+    g, o = synth.receptor_grids(atoms, shape, h)
+    lo, sn = synth.central_site(shape, (8, 6, 6))
+    r = synth.ReceptorInput(g, h, o, lo, sn)
+    small = synth.LigandInput(synth.ligand_params(72, 5), synth.ligand_configs(73, 5, 4))
+    wide_xyz = np.zeros((2, 3, 3), dtype=np.float32)
+    wide_xyz[:, 1, 0] = 10.0
+    wide_xyz[:, 2, 0] = 21.5  # u0 = ceil(21.5 / 0.25) + 4 = 90
+    wide_xyz[1, :, 1] = 0.5
+    wide = synth.LigandInput(synth.ligand_params(74, 3), wide_xyz)
+    ligs = [small, wide]
+    with Session(0) as s:
+        rh = s.load_receptor(r)
+        lh, _, _ = s.load_ligands(ligs)
+        edges = pkg.bpmf_transform_edges(s.ctx, lh, [rh], 6, pkg.BPMF_MODE_REFINE)
+        rc, out = s.eval(lh, [rh], KT, pkg.BPMF_MODE_REFINE, n_lig=2, total_conf=6)
+    assert np.all(edges[:, 0, 0] == 96)
+    assert rc & pkg.BPMF_WARN_NO_VALID
+    assert np.all(out["n_valid"][4:] == 0)
+    _check(out, ligs, [r])

@@ -183,10 +183,10 @@ def test_refined_certificate_failure_falls_back_to_float_pairs(pkg):
 
 
 def test_refined_results_are_deterministic_with_and_without_graphs(pkg):
-    """Repeated calls and a CUDA-graph replay give the same results: the
-    refined weights are summed in order-independent fixed point; only the
-    FP32 remainder below e^(-W/kT) may be summed in a different place when
-    the planes run in another order (about 1e-12 relative)."""
+    """Repeated calls and a CUDA-graph replay give bit-identical results: the
+    set of re-evaluated translations depends only on the final minimum, not
+    on the order in which the planes ran, and their weights are summed in
+    order-independent fixed point."""
     import torch
     w = synth.protein_scale(n_conf=48, n_rec=2)
     lig = w.ligands[0]
@@ -207,8 +207,48 @@ def test_refined_results_are_deterministic_with_and_without_graphs(pkg):
             torch.cuda.synchronize()
             assert np.array_equal(dev["n_valid"].cpu().numpy(), a["n_valid"])
             for k in ("logZ", "bpmf", "dG"):
-                assert np.allclose(dev[k].cpu().numpy(), a[k], rtol=1e-11, atol=0), k
+                assert np.array_equal(dev[k].cpu().numpy(), a[k]), k
         pkg.bpmf_set_graph_mode(s.ctx, 0)
     assert np.array_equal(a["n_valid"], b["n_valid"])
     for k in ("logZ", "bpmf", "dG"):
-        assert np.allclose(a[k], b[k], rtol=1e-11, atol=0), k
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_refined_list_overflow_reruns_from_first_pass_minima(pkg):
+    """Candidate lists capped at one translation overflow on every pair that
+    lists two (every plane lists its own minimum when it runs before the
+    pair's lower planes): the call evaluates the ligand again in the refined
+    form (lists of the default size, each pair's running minimum starting at
+    the first pass's), so the results are the refined form's (no float-pair
+    fallback, no warning bit) and bpmf_last_error says what happened.  With
+    the certificate also forced to fail, the ligand falls back to float
+    pairs, bit for bit."""
+    w = synth.plain_small(n_conf=16)
+    r, l = w.receptors[0], w.ligands[0]
+    ref = oracle.evaluate([r], l.coords, l.params.q, l.params.eps, l.params.R, KT)
+    with _session() as s:
+        rh = s.load_receptor(r)
+        lh, _, _ = s.load_ligands([l])
+        _, base = s.eval(lh, [rh], KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=16)
+        assert pkg.bpmf_last_error(s.ctx) == ""
+        _, ff = s.eval(lh, [rh], KT, pkg.BPMF_MODE_FF, n_lig=1, total_conf=16)
+        pkg.bpmf_set_refine_list_cap(s.ctx, 1)
+        rc, out = s.eval(lh, [rh], KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=16)
+        note = pkg.bpmf_last_error(s.ctx)
+        pkg.bpmf_set_refine_check_scale(s.ctx, 0.0)
+        rc2, out2 = s.eval(lh, [rh], KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=16)
+        note2 = pkg.bpmf_last_error(s.ctx)
+        pkg.bpmf_set_refine_check_scale(s.ctx, 1.0)
+        pkg.bpmf_set_refine_list_cap(s.ctx, 0)
+    assert not (rc & pkg.BPMF_WARN_REFINE_FALLBACK)
+    assert "1 ligand(s) re-run from the first pass's minima" in note, note
+    assert np.array_equal(out["n_valid"], base["n_valid"])
+    for k in ("logZ", "bpmf", "dG"):
+        assert np.allclose(out[k], base[k], rtol=1e-11, atol=0), k
+    fin = np.isfinite(ref["logZ"])
+    assert np.abs(out["logZ"][fin] - ref["logZ"][fin]).max() * KT <= E_TOL
+    assert abs(out["bpmf"][0, 0] - ref["bpmf"][0]) <= B_TOL
+    assert rc2 & pkg.BPMF_WARN_REFINE_FALLBACK
+    assert "recomputed in float pairs (certificate failed: 1" in note2, note2
+    for k in ("logZ", "n_valid", "bpmf", "dG"):
+        assert np.array_equal(out2[k], ff[k]), k
