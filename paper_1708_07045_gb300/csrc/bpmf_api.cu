@@ -543,9 +543,10 @@ size_t batch_bytes_per_conf(const BatchGeom &g, size_t E) {
     occ = align_up(2 * (size_t)g.occ_cap * sizeof(OccRun)) + align_up(sizeof(int)) +
           align_up((size_t)g.K * g.S[0] * g.S[1] * clash_words(g.S[2]) * sizeof(uint32_t));
   size_t ref = 0;
-  if (g.refine)  // lists, exact values, running minima and counts; window and bound per receptor
+  if (g.refine)  // lists, exact values, running minima, counts, levels, sums, CTA counters; window and bound
     ref = align_up((size_t)g.K * g.ref_cap * sizeof(Cand)) + align_up((size_t)g.K * g.ref_cap * sizeof(float2)) +
-          2 * align_up((size_t)g.K * sizeof(int)) + 2 * align_up((size_t)g.K * sizeof(float));
+          3 * align_up((size_t)g.K * sizeof(int)) + 2 * align_up((size_t)g.K * sizeof(unsigned long long)) +
+          2 * align_up((size_t)g.K * sizeof(float));
   return align_up(box) + align_up(lz) + align_up(ly) + align_up(x2) + align_up(y2) + occ + ref;
 }
 
@@ -610,6 +611,12 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
     p += align_up(np * sizeof(unsigned));
     ra.rs.cnt = reinterpret_cast<int *>(p);
     p += align_up(np * sizeof(int));
+    ra.rs.lvl = reinterpret_cast<unsigned long long *>(p);
+    p += align_up(np * sizeof(unsigned long long));
+    ra.rs.wsum = reinterpret_cast<unsigned long long *>(p);
+    p += align_up(np * sizeof(unsigned long long));
+    ra.rs.done = reinterpret_cast<unsigned *>(p);
+    p += align_up(np * sizeof(unsigned));
     ra.win = reinterpret_cast<float *>(p);
     p += align_up((size_t)g.K * sizeof(float));
     ra.bnd = reinterpret_cast<float *>(p);

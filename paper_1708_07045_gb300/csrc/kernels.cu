@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(256, KCfg<T>::zi_min_blocks) k_zinv(ZinvArgs a
       b0[l * ls + n] = c_norm(cx<T>{s_sub(A.re, B.im), s_add(A.im, B.re)});
     }
     __syncthreads();
-    cx<T> *res = cta_fft_auto<T, 20, 256, true, false, TC>(b0, b1, 1, ls, L, a.plan, s_tw, true);
+    cx<T> *res = cta_fft_auto<T, 20, 256, true, (std::is_same<T, float>::value && NY > 0), TC>(b0, b1, 1, ls, L, a.plan, s_tw, true);
     const int nS = nrow * a.S2;
     T vmax = s_mk<T>(-CUDART_INF_F, 0.f);
     float emin = CUDART_INF_F;  // refined form: plane minimum of the energies

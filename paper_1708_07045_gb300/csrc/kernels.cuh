@@ -179,6 +179,9 @@ struct RefineState {
   int *cnt;                // [batch][K] translations appended (may exceed cap: overflow)
   Cand *cand;              // [batch][K][cap]
   float2 *exact;           // [batch][K][cap] k_refine: exact -E/kT (float pair) of the refined entries
+  unsigned long long *lvl; // [batch][K] largest exact -E/kT, as an ordered key of its float pair
+  unsigned long long *wsum;  // [batch][K] fixed-point sum of the weights relative to lvl
+  unsigned *done;          // [batch][K] CTAs of k_refine_sum finished
   int cap;
   int *fail;               // set to 1 when a list overflows or a certificate check fails
 };
@@ -279,7 +282,7 @@ long long site_window(int N, int site_lo, int site_n, int u, int &w0, int &sa, i
 
 // ---- launch wrappers (kernels.cu, ligspec.cu, occupancy.cu, refine.cu) ---------
 cudaError_t launch_refine_init(const RefineArgs &a, int batch, cudaStream_t st);  // before k_zinv
-cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st);       // after k_zinv
+cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st);       // after k_zinv (two kernels)
 // sums of squares of the three grids [3][vol] into out[3] (deterministic;
 // scratch: kSumsqScratch float2 of device memory)
 constexpr int kSumsqScratch = 3 * 256;

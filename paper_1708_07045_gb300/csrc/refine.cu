@@ -32,6 +32,8 @@
 // overflowing list, one that makes it run the ligand again from the stored
 // minima.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math_constants.h>
 
 #include "kernels.cuh"
@@ -47,6 +49,9 @@ __global__ void k_refine_init(RefineArgs a, int n_pairs, float nS) {
     // than the final window (plus what lower FP32 values add)
     a.rs.pmin[i] = (a.seeded && a.store) ? a.store[a.order[i / a.K] * a.Kall + a.kmap[i % a.K]] : f2ord(CUDART_INF_F);
     a.rs.cnt[i] = 0;
+    a.rs.lvl[i] = 0ull;  // below every key
+    a.rs.wsum[i] = 0ull;
+    a.rs.done[i] = 0u;
   }
   if (i < a.K) {
     const RefTab t = a.tabs[i];
@@ -90,21 +95,35 @@ __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi 
 // Weights are summed in 64-bit fixed point (scale 2^40 relative to the
 // pair's level, every weight <= 1): integer adds are exact and
 // order-independent, so the result does not depend on the order in which
-// k_zinv appended the translations.
+// k_zinv appended the translations nor on how the list is split among CTAs.
 constexpr double kFixScale = 1099511627776.0;  // 2^40 (lists of up to 2^23 translations: sums < 2^63)
 
+// Ordered 64-bit key of a normalised float pair (hi, then lo): a larger value,
+// a larger key, so atomicMax on keys keeps the largest pair.
+__device__ __forceinline__ unsigned long long ff_key(ff x) {
+  return ((unsigned long long)f2ord(x.hi) << 32) | (unsigned long long)f2ord(x.lo);
+}
+__device__ __forceinline__ ff key_ff(unsigned long long k) {
+  return ff{ord2f((unsigned)(k >> 32)), ord2f((unsigned)(k & 0xffffffffull))};
+}
+
+// Pass 1, CTA c of gridDim.y per pair (blockIdx.x = pair): the exact -E/kT of
+// every listed translation below the final threshold in its share of the
+// list (a warp per translation, lanes over atoms), the certificate check, and
+// the largest exact value into the pair's level.
 __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
   __shared__ ff s_g[3][256];    // atom positions in the ligand-box frame (grid units)
   __shared__ ff s_gam[3][256];  // gamma_t,i
-  __shared__ float s_redx[8][2];
-  __shared__ unsigned long long s_we;
+  __shared__ unsigned long long s_key;
   const int pair = blockIdx.x;  // j * K + k
   const int j = pair / a.K, k = pair % a.K;
   const int n_list = min(a.rs.cnt[pair], a.rs.cap);
   if (threadIdx.x == 0) {
-    s_we = 0ull;
-    if (a.rs.cnt[pair] > a.rs.cap) atomicOr(a.rs.fail, 2);  // list overflow (bit 1)
-    if (a.store) a.store[a.order[j] * a.Kall + a.kmap[k]] = a.rs.pmin[pair];
+    s_key = 0ull;
+    if (blockIdx.y == 0) {
+      if (a.rs.cnt[pair] > a.rs.cap) atomicOr(a.rs.fail, 2);  // list overflow (bit 1)
+      if (a.store) a.store[a.order[j] * a.Kall + a.kmap[k]] = a.rs.pmin[pair];
+    }
   }
   const float Emin = ord2f(a.rs.pmin[pair]);
   // the final threshold (k_zinv listed against thresholds at least as high)
@@ -130,12 +149,10 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
   const Cand *list = a.rs.cand + (long long)pair * a.rs.cap;
   float2 *ex = a.rs.exact + (long long)pair * a.rs.cap;
   double *expo = (a.export_E && pair == 0) ? a.export_E : nullptr;
-  // pass 1: exact -E/kT of every listed translation below the final
-  // threshold (a warp per translation, lanes over atoms), the certificate
-  // check and the largest exact -E/kT
   ff Xe{-CUDART_INF_F, 0.f};  // max exact
   bool bad = false;
-  for (int b0 = warp * 32; b0 < n_list; b0 += nwarp * 32) {
+  const int step = (int)gridDim.y * nwarp * 32;
+  for (int b0 = ((int)blockIdx.y * nwarp + warp) * 32; b0 < n_list; b0 += step) {
     const int idx = b0 + lane;
     Cand cd{0u, CUDART_INF_F};
     if (idx < n_list) cd = list[idx];
@@ -193,45 +210,104 @@ __global__ void __launch_bounds__(256) k_refine(RefineArgs a) {
     const ff o2{__shfl_xor_sync(0xffffffffu, Xe.hi, o), __shfl_xor_sync(0xffffffffu, Xe.lo, o)};
     if (ff_gt(o2, Xe)) Xe = o2;
   }
-  if (lane == 0) {
-    s_redx[warp][0] = Xe.hi;
-    s_redx[warp][1] = Xe.lo;
+  if (lane == 0 && Xe.hi > -CUDART_INF_F) atomicMax(&s_key, ff_key(Xe));
+  __syncthreads();
+  if (gridDim.y > 1) {  // the level over every CTA of the pair; k_refine_sum sums
+    if (threadIdx.x == 0 && s_key) atomicMax(&a.rs.lvl[pair], s_key);
+    return;
   }
-  __syncthreads();  // also publishes the exact values written to the list
-  for (int w = 0; w < nwarp; ++w) {
-    const ff o2{s_redx[w][0], s_redx[w][1]};
-    if (ff_gt(o2, Xe)) Xe = o2;
-  }
-  if (!(Xe.hi > -CUDART_INF_F)) {  // no translation below the threshold (no valid translation)
+  // one CTA per pair: it holds the level already and sums the weights itself
+  // (the same fixed-point sum k_refine_sum forms)
+  const unsigned long long key = s_key;
+  if (!key) {  // no translation below the threshold (no valid translation)
     if (threadIdx.x == 0) {
       a.part_ref[2 * pair] = make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
       a.part_ref[2 * pair + 1] = make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
     }
     return;
   }
-  // level: the largest exact value, so every weight <= 1
-  const ff L = Xe;
-  // pass 2: the exact weight of every listed translation below the threshold
+  __shared__ unsigned long long s_we;
+  if (threadIdx.x == 0) s_we = 0ull;
+  __syncthreads();
+  const ff L = key_ff(key);
   unsigned long long wt = 0ull;
-  for (int idx = threadIdx.x; idx < n_list; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < n_list; idx += blockDim.x)
     if (list[idx].e <= T) {
       const float2 xe = ex[idx];
       wt += (unsigned long long)__double2ll_rn((double)expf(d_ff(ff{xe.x, xe.y}, L)) * kFixScale);
     }
-  }
-  atomicAdd(&s_we, wt);
+  if (wt) atomicAdd(&s_we, wt);
   __syncthreads();
   if (threadIdx.x == 0) {
-    const double sw = (double)s_we / kFixScale;  // exact to double rounding; kept as a float pair
+    const double sw = (double)s_we / kFixScale;  // exact to double rounding
     const float sw_hi = (float)sw;
     a.part_ref[2 * pair] = make_float4(L.hi, L.lo, sw_hi, (float)(sw - (double)sw_hi));
-    a.part_ref[2 * pair + 1] = make_float4(Xe.hi, Xe.lo, 0.f, 0.f);
+    a.part_ref[2 * pair + 1] = make_float4(L.hi, L.lo, 0.f, 0.f);
   }
 }
 
+// Pass 2, the same CTAs: the weight exp(x - L) of every re-evaluated
+// translation in the CTA's share, in fixed point relative to the pair's level
+// L, added to the pair's sum; the last CTA of the pair writes its partial
+// {L, sum} for the merge (none when nothing lies below the threshold).
+__global__ void __launch_bounds__(256) k_refine_sum(RefineArgs a) {
+  __shared__ unsigned long long s_we;
+  __shared__ bool s_last;
+  const int pair = blockIdx.x;
+  const int k = pair % a.K;
+  const int n_list = min(a.rs.cnt[pair], a.rs.cap);
+  const unsigned long long key = a.rs.lvl[pair];
+  const float T = __fadd_ru(ord2f(a.rs.pmin[pair]), a.rs.win[k]);
+  if (threadIdx.x == 0) s_we = 0ull;
+  __syncthreads();
+  const Cand *list = a.rs.cand + (long long)pair * a.rs.cap;
+  const float2 *ex = a.rs.exact + (long long)pair * a.rs.cap;
+  unsigned long long wt = 0ull;
+  if (key) {
+    const ff L = key_ff(key);  // the largest exact value: every weight <= 1
+    const int step = (int)(gridDim.y * blockDim.x);
+    for (int idx = (int)(blockIdx.y * blockDim.x + threadIdx.x); idx < n_list; idx += step)
+      if (list[idx].e <= T) {
+        const float2 xe = ex[idx];
+        wt += (unsigned long long)__double2ll_rn((double)expf(d_ff(ff{xe.x, xe.y}, L)) * kFixScale);
+      }
+  }
+  if (wt) atomicAdd(&s_we, wt);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_we) atomicAdd(&a.rs.wsum[pair], s_we);
+    __threadfence();
+    s_last = atomicAdd(&a.rs.done[pair], 1u) == gridDim.y - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    if (!key) {  // no translation below the threshold (no valid translation)
+      a.part_ref[2 * pair] = make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
+      a.part_ref[2 * pair + 1] = make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
+      return;
+    }
+    const ff L = key_ff(key);
+    const double sw = (double)atomicAdd(&a.rs.wsum[pair], 0ull) / kFixScale;  // exact to double rounding
+    const float sw_hi = (float)sw;
+    a.part_ref[2 * pair] = make_float4(L.hi, L.lo, sw_hi, (float)(sw - (double)sw_hi));
+    a.part_ref[2 * pair + 1] = make_float4(L.hi, L.lo, 0.f, 0.f);
+  }
+}
+
+// CTAs per pair: one (and one kernel) when the pairs fill the SMs; else
+// enough to cover the GPU twice over, at most 64 per pair (long lists on few
+// pairs, e.g. one wide site window), and k_refine_sum as the second pass.
 cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  k_refine<<<(unsigned)((long long)batch * a.K), 256, 0, st>>>(a);
+  const long long pairs = (long long)batch * a.K;
+  const int n_sm = sm_count();
+  const int C = pairs >= n_sm ? 1 : (int)std::min<long long>(64, (2ll * n_sm + pairs - 1) / pairs);
+  const dim3 grid((unsigned)pairs, (unsigned)C);
+  k_refine<<<grid, 256, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || C == 1) return e;
+  k_refine_sum<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

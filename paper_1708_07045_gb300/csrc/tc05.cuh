@@ -8,7 +8,8 @@
 //   1. every thread writes its share of the tile X [128 rows][64 reals] as
 //      three bf16 parts into shared memory, K-major core-matrix layout
 //      (8 rows x 16 bytes per core matrix; 128 bytes between core matrices
-//      along K, 1024 bytes between 8-row groups);
+//      along K, 1024 bytes between 8-row groups), a warp filling one core
+//      matrix per part at a time;
 //   2. one thread issues 4 K-steps x 6 terms of tcgen05.mma.kind::f16
 //      (M = 128 rows, N = 64 outputs, K = 16), D[row][n] += sum_k X[row][k]
 //      F[n][k], into a 64-column TMEM accumulator, and commits them to an
@@ -107,9 +108,12 @@ __device__ __forceinline__ void tc05_dft32_stage(const cx<float> *src, cx<float>
   unsigned parity = 0;
   bool timed_out = false;
   for (int c0 = 0; c0 < ncol; c0 += kTc05Rows) {
-    // 1. the tile's data, twiddled and split, rows = columns c0 .. c0 + 127
+    // 1. the tile's data, twiddled and split, rows = columns c0 .. c0 + 127;
+    // a warp takes 8 rows x 4 consecutive values, one 128-byte core matrix
+    // per part (no bank conflicts)
     for (int e = tid; e < kTc05Rows * 32; e += nt) {
-      const int row = e >> 5, r = e & 31, col = c0 + row;
+      const int ln = e & 31, rest = e >> 5;
+      const int row = ((rest >> 3) << 3) + (ln >> 2), r = ((rest & 7) << 2) + (ln & 3), col = c0 + row;
       cx<float> v{0.f, 0.f};
       if (col < ncol) {
         const int l = col % nlines, i = col / nlines, j = i % Ns;
