@@ -328,9 +328,9 @@ int bpmf_set_refine_check_scale(bpmf_ctx_t ctx, double scale);
 /* bpmf_set_refine_list_cap -- candidate-list capacity per (configuration,
  * receptor) pair in the refined form (0, the default: every translation of
  * the site window, up to 2^23).  A small cap makes the first pass's lists
- * overflow, which exercises the
- * second pass from the first pass's minima (that pass uses the default
- * lists); it exists for testing.  Errors: INVALID_ARG (cap < 0). */
+ * overflow, which exercises the second pass from the first pass's minima
+ * (that pass uses the default lists); it exists for testing.  Errors:
+ * INVALID_ARG (cap < 0). */
 int bpmf_set_refine_list_cap(bpmf_ctx_t ctx, int cap);
 
 /* Upper bound on the device workspace bpmf_eval may hold (bytes, default
@@ -353,9 +353,12 @@ int bpmf_set_graph_mode(bpmf_ctx_t ctx, int on);
 /*
  * bpmf_autotune -- time bpmf_eval on (lig, recs) under candidate launch
  * shapes (configurations per batch, lines per CTA of the strided passes, rows
- * per CTA of the z pass) and keep the fastest for every padded grid size of
- * `recs` and this mode.  The FFT plan itself is fixed, so every choice gives
- * bit-identical results.  Runs ~10 evaluations and synchronises `stream`.
+ * per CTA of the z pass) and, in the FP32 and refined forms, the x transform's
+ * plan (the x edge rounded up to the compile-time x pass, or the padded or crop
+ * edge on the generic engine), and keep the fastest for every padded grid size
+ * of `recs` and this mode.  The launch shapes give bit-identical results; the
+ * x plan changes FP32 rounding only (the refined form's results stay within
+ * its tolerance).  Runs ~12 evaluations and synchronises `stream`.
  * Errors: INVALID_ARG, SIZE_UNSUPPORTED, OOM, CUDA.
  */
 int bpmf_autotune(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, int K, unsigned mode, void *stream);

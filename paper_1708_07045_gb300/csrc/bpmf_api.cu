@@ -117,11 +117,13 @@ struct bpmf_ctx {
   cudaGraphExec_t gexec = nullptr;
   std::vector<unsigned long long> gkey;
   // launch shapes chosen by bpmf_autotune, per (P0, P1, P2, mode); none of
-  // them changes a result bit (every line transform is independent)
+  // them changes a result bit (every line transform is independent), except
+  // xround, which changes the FP32 forms' x transform length (its radix plan)
   struct Tune {
     int batch_cap = 0;  // configurations per batch (0: as many as the workspace holds)
     int axis_lw = 0;    // lines per CTA of the strided passes (0: 32 for FP32 lines, 16 for float pairs)
     int zfwd_l = 16;    // complex lines per CTA of the z R2C pass
+    bool xround = true; // FP32 forms: x edge rounded up to the compile-time x pass's edges
   };
   std::map<std::vector<int>, Tune> tune;
   bool warn_last = false;  // BPMF_WARN_NO_VALID of the plan behind the cached graph
@@ -1647,7 +1649,7 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
     for (const auto &g : groups) {
       const bpmf_ctx::Tune t = tune_for(c, g.P, mode);
       key.insert(key.end(), {(unsigned long long)t.batch_cap, (unsigned long long)t.axis_lw,
-                             (unsigned long long)t.zfwd_l});
+                             (unsigned long long)t.zfwd_l, (unsigned long long)t.xround});
     }
     if (c->gexec && key == c->gkey) {
       CK(cudaGraphLaunch(c->gexec, st));
@@ -1716,8 +1718,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
       const int Kg = (int)g.ks.size();
       GroupPlan gpn;
       const ConfMeta *mj = meta.data() + pl.j_first;
-      std::vector<std::array<int, 3>> pc =
-          transform_edges(mj, J, g, recs, split, mode == BPMF_MODE_FP32 || mode == BPMF_MODE_REFINE);
+      std::vector<std::array<int, 3>> pc = transform_edges(
+          mj, J, g, recs, split, (mode == BPMF_MODE_FP32 || mode == BPMF_MODE_REFINE) && tune_for(c, g.P, mode).xround);
       const std::array<int, 3> Pf{g.P[0], g.P[1], g.P[2]};
       // processing order: by crop, then by ligand-box extent, so each batch's
       // box (the maximum over its members) stays tight; the merge scatters
@@ -2194,7 +2196,7 @@ int bpmf_transform_edges(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, in
       for (const RecGroup &g : groups) {
         const std::vector<std::array<int, 3>> pc =
             transform_edges(meta.data(), J, g, recs, mode == BPMF_MODE_SPLIT_BF16 || mode == BPMF_MODE_SPLIT_REFINE,
-                            mode == BPMF_MODE_FP32 || mode == BPMF_MODE_REFINE);
+                            (mode == BPMF_MODE_FP32 || mode == BPMF_MODE_REFINE) && tune_for(c, g.P, mode).xround);
         for (int i = 0; i < J; ++i)
           for (int k : g.ks)
             for (int d = 0; d < 3; ++d) edges[((lg->conf_off[li] + i) * K + k) * 3 + d] = pc[i][d];
@@ -2273,6 +2275,15 @@ int bpmf_autotune(bpmf_ctx_t c, bpmf_lig_t lg, const bpmf_rec_t *recs, int K, un
     for (int l : {8}) {
       bpmf_ctx::Tune t = best;
       t.zfwd_l = l;
+      const float tt = timeit(t);
+      if (tt < tbest) tbest = tt, best = t;
+    }
+    // the FP32 forms' x transform: rounded up to the compile-time x pass, or
+    // on the padded / crop edge with the generic engine (a different radix
+    // plan: results agree within rounding, not bit for bit)
+    if (mode == BPMF_MODE_FP32 || mode == BPMF_MODE_REFINE) {
+      bpmf_ctx::Tune t = best;
+      t.xround = false;
       const float tt = timeit(t);
       if (tt < tbest) tbest = tt, best = t;
     }

@@ -102,3 +102,24 @@ def test_graph_replay_and_autotune_are_bit_identical(pkg, uneven):
     for o in outs:
         for k in ("logZ", "n_valid", "bpmf", "dG"):
             assert np.array_equal(o[k], ref[k]), k
+
+
+def test_refined_form_on_uneven_batches_with_the_autotuned_x_plan(pkg, uneven, uneven_ref):
+    """The refined form on the uneven workload (FP32 x edges rounded up to
+    the compile-time x pass, several receptor groups and crops), before and
+    after bpmf_autotune (which may switch a group's x transform back to the
+    padded or crop edge): both meet the tolerances against the oracle, with no
+    float-pair fallback."""
+    import torch
+    from paper_1708_07045_gb300.session import Session
+    J = sum(l.coords.shape[0] for l in uneven.ligands)
+    with Session(0) as s:
+        rhs = [s.load_receptor(r) for r in uneven.receptors]
+        lh, _, _ = s.load_ligands(uneven.ligands)
+        rc0, out0 = s.eval(lh, rhs, KT, pkg.BPMF_MODE_REFINE, n_lig=len(uneven.ligands), total_conf=J)
+        st = torch.cuda.Stream()
+        pkg.bpmf_autotune(s.ctx, lh, rhs, pkg.BPMF_MODE_REFINE, st)
+        rc1, out1 = s.eval(lh, rhs, KT, pkg.BPMF_MODE_REFINE, n_lig=len(uneven.ligands), total_conf=J)
+    for rc, out in ((rc0, out0), (rc1, out1)):
+        assert not (rc & pkg.BPMF_WARN_REFINE_FALLBACK)
+        _check(out, uneven_ref, uneven)
