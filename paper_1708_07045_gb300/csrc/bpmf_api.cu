@@ -757,9 +757,13 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   else
     launch(c, sizeof(T) == 4 ? "k_xfused<fp32>" : "k_xfused<ff>", st, [&] { return launch_xfused<T>(xa, batch, st); });
 
-  // FP32 forms: the y inverse runs inside the z inverse when the window fits
-  const bool fuse_y = sizeof(T) == 4 && !split && zinv_fused_fits(g.P[1], g.P[2], g.S[1], g.S[2], g.refine);
-  if (!fuse_y) {
+  // FP32 forms: the y and z inverses in one compile-time kernel on the edges
+  // it has; else the y inverse inside the z inverse when the window fits
+  const bool yz = sizeof(T) == 4 && !split &&
+                  yzinv_supported(g.P[1], g.P[2], g.S[1], g.S[2], clash != nullptr, export_E != nullptr);
+  const bool fuse_y =
+      !yz && sizeof(T) == 4 && !split && zinv_fused_fits(g.P[1], g.P[2], g.S[1], g.S[2], g.refine);
+  if (!fuse_y && !yz) {
     AxisArgs yi{};
     yi.in = x2;
     yi.out = y2;
@@ -799,14 +803,17 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   zi.CW = CW;
   zi.plan = plan(g.P[2]);
   zi.tw = twiddles(c, g.P[2]);
-  if (fuse_y) {
+  if (fuse_y || yz) {
     zi.x2 = x2;
     zi.Qx = g.Q;
     zi.yplan = plan(g.P[1]);
     zi.tw1 = twiddles(c, g.P[1]);
   }
-  launch(c, fuse_y ? "k_zinv<fp32>(+y inv)" : (sizeof(T) == 4 ? "k_zinv<fp32>" : "k_zinv<ff>"), st,
-         [&] { return launch_zinv<T>(zi, batch, st); });
+  if (yz)
+    launch(c, "k_yzinv<fp32>", st, [&] { return launch_yzinv(zi, batch, st); });
+  else
+    launch(c, fuse_y ? "k_zinv<fp32>(+y inv)" : (sizeof(T) == 4 ? "k_zinv<fp32>" : "k_zinv<ff>"), st,
+           [&] { return launch_zinv<T>(zi, batch, st); });
   if (g.refine) {
     ra.h_hi = hh;
     ra.h_lo = hl;

@@ -305,6 +305,9 @@ struct alignas(64) XpassMaps {
   CUtensorMap m[kXpMaxMaps];
 };
 bool xpass_supported(int P);
+// FP32 y + z inverse on compile-time edges P1 = P2 in {64, 72, 80, 96} (yzinv.cu)
+bool yzinv_supported(int P1, int P2, int S1, int S2, bool clash, bool export_E);
+cudaError_t launch_yzinv(const ZinvArgs &a, int batch, cudaStream_t st);
 cudaError_t launch_xpass(const XfusedArgs &a, int batch, cudaStream_t st);
 template <class T> cudaError_t launch_zinv(const ZinvArgs &a, int batch, cudaStream_t st);
 // whether the FP32 z inverse can take the y inverse in front (whole site
