@@ -3,9 +3,10 @@
 // site mask and the plane's reduction: the work of k_zinv<float, NY> (Eq.
 // fft_correlation_func's inverse transform, pruned to the site window, Eq.
 // sample_mean_BPMF's sum), organised like k_xpass: each inverse DFT is two
-// stages of a four-step factorisation (f = k2 + R k1, n = n1 + 8 n2, P = 8 R), each
-// stage unit a half-warp whose 16 lanes are 16 lines, so index arithmetic is
-// per unit and every shared access of a half-warp is 16 consecutive values.
+// stages of a four-step factorisation (f = k2 + R k1, n = n1 + 8 n2, P = 8 R),
+// each stage unit a half-warp whose 16 lanes are 16 lines (a quarter warp of
+// 8 lines in the z stages, whose row pairs are few), so index arithmetic is
+// per unit and the lanes of a unit access consecutive values.
 //
 // One CTA per (configuration, receptor, site plane s0), 256 threads:
 //   y, unit (k2, g): rows k2 + R1 k1 (k1 < 8) of the x-pass plane [P1][F2],
@@ -13,7 +14,7 @@
 //      inverse 8-point DFT over k1, times conj(w_P1^(n1 k2)) -> Y rows 8 k2 + n1;
 //   y, unit (n1, g): inverse R1-point DFT over k2 -> y rows n1 + 8 n2; the rows
 //      of the site window go to Zs[z frequency][s1];
-//   z, unit (k2, g): lines l = 16 g .. 16 g + 15 are the row pairs (2 l,
+//   z, unit (k2, g), a quarter warp: lines l = 8 g .. 8 g + 7 are the row pairs (2 l,
 //      2 l + 1) packed as A + i B over the Hermitian-extended frequencies
 //      k2 + R2 k1; inverse 8-point DFT, twiddle -> W rows 8 k2 + n1;
 //   z, unit (n1, g): inverse R2-point DFT -> z index n1 + 8 n2, real part row
@@ -51,8 +52,8 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   constexpr int NG1 = (F2 + 15) / 16;  // line groups of the y transform (columns)
   const int S1 = a.S1, S2 = a.S2;
   const int L = (S1 + 1) / 2;          // row pairs: lines of the z transform
-  const int NGz = (L + 15) / 16;
-  const int WS = 16 * NGz;             // row stride of W
+  const int NGz = (L + 7) / 8;         // the z stages' units are 8 lanes (a quarter warp): few lines
+  const int WS = 8 * NGz;              // row stride of W
   const int US = F2 > WS ? F2 : WS;
   const int ZST = yz_zst(S1);
   constexpr int PM = P1 > P2 ? P1 : P2;
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   float *es = reinterpret_cast<float *>(Zs + F2 * ZST);   // [S1][S2]
   __shared__ float s_red[8];
   __shared__ float s_thr;
-  const int tid = threadIdx.x, hw = tid >> 4, hl = tid & 15;
+  const int tid = threadIdx.x, hw = tid >> 4, hl = tid & 15, qw = tid >> 3, ql = tid & 7;
   const int s0 = blockIdx.x % a.S0;
   const int jk = blockIdx.x / a.S0;  // j * K + k
   const PairInfo inf = a.info[jk];
@@ -114,8 +115,8 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   }
   __syncthreads();
   // z, first inverse stage: row pairs as A + i B, Hermitian-extended
-  for (int u = hw; u < R2 * NGz; u += kYzNT / 16) {
-    const int k2 = u % R2, l = (u / R2) * 16 + hl;
+  for (int u = qw; u < R2 * NGz; u += kYzNT / 8) {
+    const int k2 = u % R2, l = (u / R2) * 8 + ql;
     if (l < L) {
       cx<float> v[8];
 #pragma unroll
@@ -143,8 +144,8 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   // z, second inverse stage: energies of rows 2 l and 2 l + 1 at z index n1 + 8 n2
   const float nscale = a.nscale_hi, escale = a.escale_hi;
   float ext = refine ? CUDART_INF_F : -CUDART_INF_F;  // plane minimum of E (refined) or maximum of -E/kT
-  for (int u = hw; u < 8 * NGz; u += kYzNT / 16) {
-    const int n1 = u & 7, l = (u >> 3) * 16 + hl;
+  for (int u = qw; u < 8 * NGz; u += kYzNT / 8) {
+    const int n1 = u & 7, l = (u >> 3) * 8 + ql;
     if (l < L) {
       cx<float> v[R2];
 #pragma unroll
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
 template <int P1, int P2>
 size_t yzinv_smem_p(int S1, int S2) {
   constexpr int F2 = P2 / 2 + 1, PM = P1 > P2 ? P1 : P2;
-  const int L = (S1 + 1) / 2, WS = 16 * ((L + 15) / 16), US = F2 > WS ? F2 : WS;
+  const int L = (S1 + 1) / 2, WS = 8 * ((L + 7) / 8), US = F2 > WS ? F2 : WS;
   return sizeof(float4) * (P1 + P2) + sizeof(cx<float>) * ((size_t)PM * US + (size_t)F2 * yz_zst(S1)) +
          sizeof(float) * (size_t)S1 * S2;
 }
