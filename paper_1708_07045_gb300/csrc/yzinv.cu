@@ -1,23 +1,24 @@
 // The y and z inverse transforms of the FP32 forms on compile-time edges
-// P1, P2 = 8 R (R = 8, 9, 10, 12: edges 64, 72, 80, 96), fused with the
+// P = A R (64, 72, 80, 96 = 8 R; 70 = 7 x 10, 84 = 7 x 12, 90 = 9 x 10,
+// 100 = 10 x 10, 108 = 9 x 12), fused with the
 // site mask and the plane's reduction: the work of k_zinv<float, NY> (Eq.
 // fft_correlation_func's inverse transform, pruned to the site window, Eq.
 // sample_mean_BPMF's sum), organised like k_xpass: each inverse DFT is two
-// stages of a four-step factorisation (f = k2 + R k1, n = n1 + 8 n2, P = 8 R),
+// stages of a four-step factorisation (f = k2 + R k1, n = n1 + A n2, P = A R),
 // each stage unit a half-warp whose 16 lanes are 16 lines (a quarter warp of
 // 8 lines in the z stages, whose row pairs are few), so index arithmetic is
 // per unit and the lanes of a unit access consecutive values.
 //
 // One CTA per (configuration, receptor, site plane s0), 256 threads:
-//   y, unit (k2, g): rows k2 + R1 k1 (k1 < 8) of the x-pass plane [P1][F2],
+//   y, unit (k2, g): rows k2 + R1 k1 (k1 < A1) of the x-pass plane [P1][F2],
 //      columns 16 g .. 16 g + 15, read from global memory into registers;
-//      inverse 8-point DFT over k1, times conj(w_P1^(n1 k2)) -> Y rows 8 k2 + n1;
-//   y, unit (n1, g): inverse R1-point DFT over k2 -> y rows n1 + 8 n2; the rows
+//      inverse A1-point DFT over k1, times conj(w_P1^(n1 k2)) -> Y rows A1 k2 + n1;
+//   y, unit (n1, g): inverse R1-point DFT over k2 -> y rows n1 + A1 n2; the rows
 //      of the site window go to Zs[z frequency][s1];
 //   z, unit (k2, g), a quarter warp: lines l = 8 g .. 8 g + 7 are the row pairs (2 l,
 //      2 l + 1) packed as A + i B over the Hermitian-extended frequencies
-//      k2 + R2 k1; inverse 8-point DFT, twiddle -> W rows 8 k2 + n1;
-//   z, unit (n1, g): inverse R2-point DFT -> z index n1 + 8 n2, real part row
+//      k2 + R2 k1; inverse A2-point DFT, twiddle -> W rows A2 k2 + n1;
+//   z, unit (n1, g): inverse R2-point DFT -> z index n1 + A2 n2, real part row
 //      2 l, imaginary part row 2 l + 1: scaled, masked, into the plane's
 //      energies (refined form) or -E/kT values (FP32 form);
 // then the plane's reduction: the refined form's running minimum and
@@ -45,9 +46,9 @@ __host__ __device__ __forceinline__ int yz_zst(int S1) {
   return (two_l & 2) ? two_l : two_l + 2;
 }
 
-template <int P1, int P2>
+template <int A1, int R1, int A2, int R2>
 __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
-  constexpr int R1 = P1 / 8, R2 = P2 / 8;
+  constexpr int P1 = A1 * R1, P2 = A2 * R2;
   constexpr int F2 = P2 / 2 + 1;
   constexpr int NG1 = (F2 + 15) / 16;  // line groups of the y transform (columns)
   const int S1 = a.S1, S2 = a.S2;
@@ -86,28 +87,28 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   for (int u = hw; u < R1 * NG1; u += kYzNT / 16) {
     const int k2 = u % R1, c = (u / R1) * 16 + hl;
     if (c < F2) {
-      cx<float> v[8];
+      cx<float> v[A1];
 #pragma unroll
-      for (int k1 = 0; k1 < 8; ++k1) v[k1] = plane[(k2 + R1 * k1) * F2 + c];
-      dft_small<float, 8>(v, true, tw1, P1);
+      for (int k1 = 0; k1 < A1; ++k1) v[k1] = plane[(k2 + R1 * k1) * F2 + c];
+      dft_small<float, A1>(v, true, tw1, P1);
 #pragma unroll
-      for (int n1 = 1; n1 < 8; ++n1) v[n1] = c_mul(v[n1], tw_load<float>(tw1[n1 * k2], true));
+      for (int n1 = 1; n1 < A1; ++n1) v[n1] = c_mul(v[n1], tw_load<float>(tw1[n1 * k2], true));
 #pragma unroll
-      for (int n1 = 0; n1 < 8; ++n1) Y[(8 * k2 + n1) * F2 + c] = v[n1];
+      for (int n1 = 0; n1 < A1; ++n1) Y[(A1 * k2 + n1) * F2 + c] = v[n1];
     }
   }
   __syncthreads();
   // y, second inverse stage: the site window's rows into Zs[column][s1]
-  for (int u = hw; u < 8 * NG1; u += kYzNT / 16) {
-    const int n1 = u & 7, c = (u >> 3) * 16 + hl;
+  for (int u = hw; u < A1 * NG1; u += kYzNT / 16) {
+    const int n1 = u % A1, c = (u / A1) * 16 + hl;
     if (c < F2) {
       cx<float> v[R1];
 #pragma unroll
-      for (int k2 = 0; k2 < R1; ++k2) v[k2] = Y[(8 * k2 + n1) * F2 + c];
+      for (int k2 = 0; k2 < R1; ++k2) v[k2] = Y[(A1 * k2 + n1) * F2 + c];
       dft_small<float, R1>(v, true, tw1, P1);
 #pragma unroll
       for (int n2 = 0; n2 < R1; ++n2) {
-        int s1 = n1 + 8 * n2 - wy;
+        int s1 = n1 + A1 * n2 - wy;
         s1 += s1 < 0 ? P1 : 0;
         if (s1 < S1) Zs[c * ZST + s1] = v[n2];
       }
@@ -118,9 +119,9 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   for (int u = qw; u < R2 * NGz; u += kYzNT / 8) {
     const int k2 = u % R2, l = (u / R2) * 8 + ql;
     if (l < L) {
-      cx<float> v[8];
+      cx<float> v[A2];
 #pragma unroll
-      for (int k1 = 0; k1 < 8; ++k1) {
+      for (int k1 = 0; k1 < A2; ++k1) {
         const int f = k2 + R2 * k1;
         const bool up = 2 * f <= P2;
         const int kk = up ? f : P2 - f;
@@ -133,30 +134,30 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
         }
         v[k1] = cx<float>{__fsub_rn(ab.x, bi), __fadd_rn(ai, ab.z)};
       }
-      dft_small<float, 8>(v, true, tw2, P2);
+      dft_small<float, A2>(v, true, tw2, P2);
 #pragma unroll
-      for (int n1 = 1; n1 < 8; ++n1) v[n1] = c_mul(v[n1], tw_load<float>(tw2[n1 * k2], true));
+      for (int n1 = 1; n1 < A2; ++n1) v[n1] = c_mul(v[n1], tw_load<float>(tw2[n1 * k2], true));
 #pragma unroll
-      for (int n1 = 0; n1 < 8; ++n1) W[(8 * k2 + n1) * WS + l] = v[n1];
+      for (int n1 = 0; n1 < A2; ++n1) W[(A2 * k2 + n1) * WS + l] = v[n1];
     }
   }
   __syncthreads();
   // z, second inverse stage: energies of rows 2 l and 2 l + 1 at z index n1 + 8 n2
   const float nscale = a.nscale_hi, escale = a.escale_hi;
   float ext = refine ? CUDART_INF_F : -CUDART_INF_F;  // plane minimum of E (refined) or maximum of -E/kT
-  for (int u = qw; u < 8 * NGz; u += kYzNT / 8) {
-    const int n1 = u & 7, l = (u >> 3) * 8 + ql;
+  for (int u = qw; u < A2 * NGz; u += kYzNT / 8) {
+    const int n1 = u % A2, l = (u / A2) * 8 + ql;
     if (l < L) {
       cx<float> v[R2];
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) v[k2] = W[(8 * k2 + n1) * WS + l];
+      for (int k2 = 0; k2 < R2; ++k2) v[k2] = W[(A2 * k2 + n1) * WS + l];
       dft_small<float, R2>(v, true, tw2, P2);
       const int s1a = 2 * l, s1b = 2 * l + 1;
       const bool oka = s1a >= inf.sa[1] && s1a <= inf.sb[1];
       const bool okb = s1b < S1 && s1b >= inf.sa[1] && s1b <= inf.sb[1];
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) {
-        int s2 = n1 + 8 * n2 - wz;
+        int s2 = n1 + A2 * n2 - wz;
         s2 += s2 < 0 ? P2 : 0;
         if (s2 < S2) {
           const bool ok2 = s2 >= inf.sa[2] && s2 <= inf.sb[2];
@@ -240,59 +241,58 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   }
 }
 
-template <int P1, int P2>
+template <int A1, int R1, int A2, int R2>
 size_t yzinv_smem_p(int S1, int S2) {
-  constexpr int F2 = P2 / 2 + 1, PM = P1 > P2 ? P1 : P2;
+  constexpr int P1 = A1 * R1, P2 = A2 * R2, F2 = P2 / 2 + 1, PM = P1 > P2 ? P1 : P2;
   const int L = (S1 + 1) / 2, WS = 8 * ((L + 7) / 8), US = F2 > WS ? F2 : WS;
   return sizeof(float4) * (P1 + P2) + sizeof(cx<float>) * ((size_t)PM * US + (size_t)F2 * yz_zst(S1)) +
          sizeof(float) * (size_t)S1 * S2;
 }
 
-template <int P1, int P2>
+template <int A1, int R1, int A2, int R2>
 cudaError_t launch_yzinv_p(const ZinvArgs &a, int batch, cudaStream_t st) {
-  const size_t smem = yzinv_smem_p<P1, P2>(a.S1, a.S2);
-  cudaError_t e = cudaFuncSetAttribute(k_yzinv<P1, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = yzinv_smem_p<A1, R1, A2, R2>(a.S1, a.S2);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_yzinv<A1, R1, A2, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_yzinv<P1, P2><<<(unsigned)((long long)batch * a.K * a.S0), kYzNT, smem, st>>>(a);
+  k_yzinv<A1, R1, A2, R2><<<(unsigned)((long long)batch * a.K * a.S0), kYzNT, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-bool yz_edge(int P) { return P == 64 || P == 72 || P == 80 || P == 96; }
+// The compiled (y edge, z edge) pairs, each edge as A x R: every pair of the
+// 8 R edges 64, 72, 80, 96, and each padded edge with its crop edge (the
+// smooth edge near 5/6 of it) for 80, 84, 90, 96, 100 and 108.
+#define BPMF_YZ_PAIRS(X)                                                                                        \
+  X(8, 8, 8, 8) X(8, 8, 8, 9) X(8, 8, 8, 10) X(8, 8, 8, 12) X(8, 9, 8, 8) X(8, 9, 8, 9) X(8, 9, 8, 10)          \
+  X(8, 9, 8, 12) X(8, 10, 8, 8) X(8, 10, 8, 9) X(8, 10, 8, 10) X(8, 10, 8, 12) X(8, 12, 8, 8) X(8, 12, 8, 9)    \
+  X(8, 12, 8, 10) X(8, 12, 8, 12)                                                                              \
+  X(7, 10, 7, 10) X(8, 10, 7, 10) X(7, 10, 8, 10)                                                              \
+  X(7, 12, 7, 12) X(7, 12, 7, 10) X(7, 10, 7, 12)                                                              \
+  X(9, 10, 9, 10) X(9, 10, 8, 10) X(8, 10, 9, 10)                                                              \
+  X(10, 10, 10, 10) X(10, 10, 7, 12) X(7, 12, 10, 10)                                                          \
+  X(9, 12, 9, 12) X(9, 12, 9, 10) X(9, 10, 9, 12)
 
-// (P1, P2) -> f<P1, P2>(args...) over the compile-time edges
-template <template <int, int> class F, class... A>
-auto yz_dispatch(int P1, int P2, A... args) -> decltype(F<64, 64>::run(args...)) {
-#define BPMF_YZ_ROW(Q1)                                           \
-  if (P1 == Q1) {                                                 \
-    if (P2 == 64) return F<Q1, 64>::run(args...);                 \
-    if (P2 == 72) return F<Q1, 72>::run(args...);                 \
-    if (P2 == 80) return F<Q1, 80>::run(args...);                 \
-    if (P2 == 96) return F<Q1, 96>::run(args...);                 \
-  }
-  BPMF_YZ_ROW(64)
-  BPMF_YZ_ROW(72)
-  BPMF_YZ_ROW(80)
-  BPMF_YZ_ROW(96)
-#undef BPMF_YZ_ROW
-  return F<64, 64>::fail(args...);
+size_t yz_smem(int P1, int P2, int S1, int S2) {
+#define BPMF_YZ_SMEM(a1, r1, a2, r2) \
+  if (P1 == a1 * r1 && P2 == a2 * r2) return yzinv_smem_p<a1, r1, a2, r2>(S1, S2);
+  BPMF_YZ_PAIRS(BPMF_YZ_SMEM)
+#undef BPMF_YZ_SMEM
+  return 0;
 }
 
-template <int P1, int P2>
-struct YzSmem {
-  static size_t run(int S1, int S2) { return yzinv_smem_p<P1, P2>(S1, S2); }
-  static size_t fail(int, int) { return 0; }
-};
-template <int P1, int P2>
-struct YzLaunch {
-  static cudaError_t run(const ZinvArgs *a, int batch, cudaStream_t st) { return launch_yzinv_p<P1, P2>(*a, batch, st); }
-  static cudaError_t fail(const ZinvArgs *, int, cudaStream_t) { return cudaErrorInvalidValue; }
-};
+cudaError_t yz_launch(int P1, int P2, const ZinvArgs &a, int batch, cudaStream_t st) {
+#define BPMF_YZ_LAUNCH(a1, r1, a2, r2) \
+  if (P1 == a1 * r1 && P2 == a2 * r2) return launch_yzinv_p<a1, r1, a2, r2>(a, batch, st);
+  BPMF_YZ_PAIRS(BPMF_YZ_LAUNCH)
+#undef BPMF_YZ_LAUNCH
+  return cudaErrorInvalidValue;
+}
 
 }  // namespace
 
 bool yzinv_supported(int P1, int P2, int S1, int S2, bool clash, bool export_E) {
-  if (clash || export_E || S1 < 1 || S2 < 1 || S1 > P1 || S2 > P2 || !yz_edge(P1) || !yz_edge(P2)) return false;
-  const size_t smem = yz_dispatch<YzSmem>(P1, P2, S1, S2);
+  if (clash || export_E || S1 < 1 || S2 < 1 || S1 > P1 || S2 > P2) return false;
+  const size_t smem = yz_smem(P1, P2, S1, S2);
   return smem > 0 && smem <= 227 * 1024;
 }
 
@@ -302,7 +302,7 @@ cudaError_t launch_yzinv(const ZinvArgs &a, int batch, cudaStream_t st) {
   if (!a.x2 || a.F2 != P2 / 2 + 1 || a.clash || a.export_E || !yzinv_supported(P1, P2, a.S1, a.S2, false, false) ||
       a.Qx != (long long)P1 * a.F2 || !a.tw1)
     return cudaErrorInvalidValue;
-  return yz_dispatch<YzLaunch>(P1, P2, &a, batch, st);
+  return yz_launch(P1, P2, a, batch, st);
 }
 
 }  // namespace bpmf

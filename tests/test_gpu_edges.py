@@ -141,3 +141,34 @@ def test_fp32_box_wider_than_the_padded_edge_next_to_a_small_one(pkg):
     assert rc & pkg.BPMF_WARN_NO_VALID
     assert np.all(out["n_valid"][4:] == 0)
     _check(out, ligs, [r])
+
+
+@pytest.mark.parametrize("shape", [(24, 84, 70), (24, 70, 84), (24, 90, 108), (24, 100, 100), (24, 108, 90)])
+def test_fp32_yz_inverse_on_composite_edges(pkg, shape):
+    """The FP32 forms' fused y + z inverse on compile-time edges A x R with a
+    first factor other than 8 (70 = 7 x 10, 84 = 7 x 12, 90 = 9 x 10,
+    100 = 10 x 10, 108 = 9 x 12): the refined form meets the tolerances
+    against the oracle and the FP32 form stays within its error bound of it."""
+    from paper_1708_07045_gb300.session import Session
+    h = 0.25
+    atoms = synth.receptor_atoms(80 + shape[1], 300, 3.0, 14.0)
+    g, o = synth.receptor_grids(atoms, shape, h)
+    lo, sn = synth.central_site(shape, (4, 8, 7))
+    r = synth.ReceptorInput(g, h, o, lo, sn)
+    lig = synth.LigandInput(synth.ligand_params(81, 5), synth.ligand_configs(82, 5, 4))
+    with Session(0) as s:
+        rh = s.load_receptor(r)
+        lh, _, _ = s.load_ligands([lig])
+        edges = pkg.bpmf_transform_edges(s.ctx, lh, [rh], 4, pkg.BPMF_MODE_REFINE)
+        rc, out = s.eval(lh, [rh], KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=4)
+        _, out32 = s.eval(lh, [rh], KT, pkg.BPMF_MODE_FP32, n_lig=1, total_conf=4)
+    assert np.all(edges[:, 0, 1] == shape[1]) and np.all(edges[:, 0, 2] == shape[2])
+    assert not (rc & pkg.BPMF_WARN_REFINE_FALLBACK)
+    _check(out, [lig], [r])
+    ref = oracle.evaluate([r], lig.coords, lig.params.q, lig.params.eps, lig.params.R, KT)
+    gam = oracle.gamma(lig.params.q, lig.params.eps, lig.params.R)
+    bound = sum(8 * 2.0 ** -24 * np.sqrt(np.log2(24.0 * shape[1] * shape[2])) *
+                np.sqrt(np.mean(g[t].astype(np.float64) ** 2)) * np.linalg.norm(gam[t]) for t in range(3))
+    fin = np.isfinite(ref["logZ"])
+    assert np.array_equal(out32["n_valid"], ref["n_valid"])
+    assert np.abs(out32["logZ"][fin] - ref["logZ"][fin]).max() * KT <= 2 * bound
