@@ -125,6 +125,43 @@ __device__ __forceinline__ bool tile_arrived(unsigned long long *bar, unsigned &
   return true;
 }
 
+// Half of an inverse composite R-point DFT (R = R1 R2, decimation in time as
+// in dft_small: R2 length-R1 DFTs over the inputs v[R2 n1 + n2], twiddles
+// w_R^(n2 k1), then R1 length-R2 DFTs): the R1 / 2 sub-transforms k1 = h R1 / 2
+// ... of half h, outputs o[i] = X[k1 + R1 k2] with k1 = h R1 / 2 + i / R2,
+// k2 = i % R2.
+template <int R>
+struct HalfSplit {
+  static constexpr int R1 = (R == 12 || R == 16) ? 4 : 2;
+  static constexpr bool ok = R == 8 || R == 10 || R == 12 || R == 14 || R == 16;
+};
+
+template <int R>
+__device__ __forceinline__ void idft_half(const cx<float> *v, int h, const float4 *tw, int P, cx<float> *o) {
+  constexpr int R1 = HalfSplit<R>::R1, R2 = R / R1, H = R1 / 2;
+  cx<float> b[H][R2];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    cx<float> a[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) a[m] = v[R2 * m + n2];
+    dft_small<float, R1>(a, true, tw, P);
+#pragma unroll
+    for (int kk = 0; kk < H; ++kk) {
+      const int k1 = h * H + kk;
+      cx<float> x = h ? a[H + kk] : a[kk];
+      if (n2 > 0 && k1 > 0) x = c_mul(x, tw_load<float>(tw[(n2 * k1) * (P / R)], true));
+      b[kk][n2] = x;
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < H; ++kk) {
+    dft_small<float, R2>(b[kk], true, tw, P);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) o[kk * R2 + k2] = b[kk][k2];
+  }
+}
+
 template <int P, bool TMA>
 __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, const __grid_constant__ XpassMaps maps) {
   constexpr int R = P / 8;
@@ -234,8 +271,29 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
       }
     }
     // inverse A', unit n1: inverse R-point DFT over k2 -> x[n1 + 8 n2]; the
-    // rows inside the site window along x go straight to the output
-    if (hw < 8) {
+    // rows inside the site window along x go straight to the output.  Where R
+    // splits as R1 x R2 with R1 even, two half-warps share a unit, each taking
+    // half of the R1 length-R2 sub-transforms (half of the outputs)
+    if constexpr (HalfSplit<R>::ok) {
+      constexpr int R1 = HalfSplit<R>::R1, R2 = R / R1, H = R1 / 2;
+      const int n1 = hw & 7, h = hw >> 3;
+      const cx<float> *col = W + n1 * NLI + hl;
+      cx<float> v[R];
+#pragma unroll
+      for (int k2 = 0; k2 < R; ++k2) v[k2] = col[8 * k2 * NLI];
+      cx<float> o[R / 2];
+      idft_half<R>(v, h, tw, P, o);
+      if (live) {
+        cx<float> *dst = reinterpret_cast<cx<float> *>(a.x2) + ((long long)j * a.K + k) * a.S0 * Q + q;
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+          const int n2 = h * H + i / R2 + R1 * (i % R2);  // output k1 + R1 k2
+          int s = n1 + 8 * n2 - wm;
+          s += s < 0 ? P : 0;
+          if (s < a.S0) dst[(long long)s * Q] = o[i];
+        }
+      }
+    } else if (hw < 8) {
       const int n1 = hw;
       const cx<float> *col = W + n1 * NLI + hl;
       cx<float> v[R];
