@@ -43,6 +43,11 @@ extern "C" {
 #define BPMF_ERR_INVALID_ARG (-1)
 #define BPMF_ERR_OOM (-2)
 #define BPMF_ERR_CUDA (-3)
+/* A kernel's bounded wait (for its tensor-memory copies or tensor-core
+ * operations) ran out: it set a flag, waited once more (bounded) for what it
+ * had in flight and returned, so the context stays usable.  Reported by the
+ * calls that synchronise the stream (the refined forms, host outputs,
+ * exports). */
 #define BPMF_ERR_TIMEOUT (-4)
 #define BPMF_ERR_SIZE_UNSUPPORTED (-5)
 /* warning: at least one (configuration, receptor) pair has no valid
@@ -332,6 +337,13 @@ int bpmf_set_refine_check_scale(bpmf_ctx_t ctx, double scale);
  * (that pass uses the default lists); it exists for testing.  Errors:
  * INVALID_ARG (cap < 0). */
 int bpmf_set_refine_list_cap(bpmf_ctx_t ctx, int cap);
+
+/* bpmf_set_wait_test -- when on, the FP32 x pass does not request its first
+ * receptor tile and waits for it about 2^20 cycles only, so every CTA's
+ * bounded wait runs out and the next synchronising bpmf_eval returns
+ * BPMF_ERR_TIMEOUT (no fault, no hang; CUDA graphs are not used meanwhile).
+ * It exists for testing the timeout path.  Errors: INVALID_ARG. */
+int bpmf_set_wait_test(bpmf_ctx_t ctx, int on);
 
 /* Upper bound on the device workspace bpmf_eval may hold (bytes, default
  * 3 GiB); configurations are processed in batches that fit.  Results do not

@@ -123,6 +123,7 @@ _SIGS = {
     "bpmf_transform_edges": (_I, [_P, _P, _P, _I, ctypes.c_uint, _P]),
     "bpmf_set_refine_check_scale": (_I, [_P, _D]),
     "bpmf_set_refine_list_cap": (_I, [_P, _I]),
+    "bpmf_set_wait_test": (_I, [_P, _I]),
     "bpmf_features": (_I, [_P, _P, _D, _P, _P]),
     "bpmf_valid_counts": (_I, [_P, _P, _P, _I, _P]),
     "bpmf_mlp_param_count": (ctypes.c_longlong, [_I, _I, _I]),
@@ -503,6 +504,11 @@ def bpmf_transform_edges(ctx, lig, recs, total_conf, mode):
 def bpmf_set_refine_check_scale(ctx, scale):
     """Scale of B in the refined form's certificate check (testing)."""
     return _check(lib().bpmf_set_refine_check_scale(ctx, float(scale)), "bpmf_set_refine_check_scale", ctx)
+
+
+def bpmf_set_wait_test(ctx, on):
+    """Testing: the x pass's first receptor-tile wait runs out (BPMF_ERR_TIMEOUT)."""
+    return _check(lib().bpmf_set_wait_test(ctx, int(bool(on))), "bpmf_set_wait_test", ctx)
 
 
 def bpmf_set_refine_list_cap(ctx, cap):

@@ -103,6 +103,7 @@ struct bpmf_ctx {
   unsigned *pmin_store = nullptr;  // [total_conf][K] refined form: each pair's final running minimum
   size_t pmin_store_n = 0;
   int refine_list_cap = 0;        // refined form: list capacity per pair (0: the default rule)
+  int wait_test = 0;              // testing: the x pass's first tile wait runs out (bpmf_set_wait_test)
   std::map<int, float4 *> tw;  // twiddle tables per transform length
   uint4 *tca = nullptr;        // tensor-core radix-32 fragment table (split-bf16 mode)
   const __nv_bfloat16 *tc05 = nullptr;  // the same stage's matrix in the tcgen05 layout
@@ -743,6 +744,7 @@ void run_batch(bpmf_ctx *c, const bpmf_lig *lg, const BatchGeom &g, int batch, c
   xa.meta = d_meta;
   xa.rhi_h = h_rhi;
   xa.err = d_err;
+  xa.wait_test = c->wait_test;
   xa.Q = g.Q;
   xa.K = g.K;
   xa.rhi = d_rhi;
@@ -992,6 +994,12 @@ int bpmf_set_refine_check_scale(bpmf_ctx_t c, double scale) {
 int bpmf_set_refine_list_cap(bpmf_ctx_t c, int cap) {
   if (!c || cap < 0) return set_err(c, BPMF_ERR_INVALID_ARG, "cap must be >= 0");
   c->refine_list_cap = cap;
+  return BPMF_OK;
+}
+
+int bpmf_set_wait_test(bpmf_ctx_t c, int on) {
+  if (!c) return BPMF_ERR_INVALID_ARG;
+  c->wait_test = on != 0;
   return BPMF_OK;
 }
 
@@ -1636,7 +1644,8 @@ int eval_impl(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, do
                                       (Emin && !is_device_ptr(Emin)) || (Dom && !is_device_ptr(Dom)));
   // graph replay: same handles, mode, kT and output buffers as the cached graph
   const bool use_graph =
-      c->graph_mode && !export_E && !host_out && st != nullptr && !c->prof && only_lig < 0 && only_conf < 0;
+      c->graph_mode && !export_E && !host_out && st != nullptr && !c->prof && only_lig < 0 && only_conf < 0 &&
+      !c->wait_test;
   std::vector<unsigned long long> key;
   if (use_graph) {
     key = {lg->id, (unsigned long long)K, mode, (unsigned long long)c->ws_budget};

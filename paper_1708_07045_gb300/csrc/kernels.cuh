@@ -105,6 +105,7 @@ struct XfusedArgs {        // x: forward ligand DFT, product with each receptor,
   const float4 *tw;
   const float2 *const *rhi_h;  // host copy of rhi (tensor maps of the FP32 x pass), or null
   int *err;                // device flag set when a bounded wait of the x pass runs out, or null
+  int wait_test;           // testing: the first receptor tile is not requested, so its (short) wait runs out
 };
 
 // ---- steric clashes (Eq. occupancy_grid) -----------------------------------

@@ -79,9 +79,9 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
       "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
-// Wait for the mbarrier phase with the given parity, for about 2^31 SM cycles
-// at most (about a second); false when the time ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+// Wait for the mbarrier phase with the given parity, for `limit` SM cycles at
+// most (2^31, about a second, in normal use); false when the time ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit) {
   const long long t0 = clock64();
   while (true) {
     unsigned done;
@@ -91,7 +91,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -114,11 +114,11 @@ __device__ __forceinline__ void stage_receptor(cx<float> *RS, const float2 *rh, 
 // Every thread waits for the current tile; the CTA agrees on the outcome.  On
 // a timeout the error flag is set, the copy in flight is waited for once more
 // (again bounded), and the CTA is to return.
-__device__ __forceinline__ bool tile_arrived(unsigned long long *bar, unsigned &parity, int *err) {
-  const bool ok = mbar_wait(bar, parity);
+__device__ __forceinline__ bool tile_arrived(unsigned long long *bar, unsigned &parity, int *err, long long limit) {
+  const bool ok = mbar_wait(bar, parity, limit);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0 && err) atomicOr(err, 1);
-    mbar_wait(bar, parity);
+    mbar_wait(bar, parity, limit);
     return false;
   }
   parity ^= 1u;
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
   if constexpr (TMA) {
     if (tid == 0) {
       mbar_init(&s_bar, 1);
-      if (a.K > 0) tma_load_3d(RS, &maps.m[0], 2 * q0, 0, 0, &s_bar, kTileBytes);
+      if (a.K > 0 && !a.wait_test) tma_load_3d(RS, &maps.m[0], 2 * q0, 0, 0, &s_bar, kTileBytes);
     }
   } else {
     if (a.K > 0) stage_receptor<P>(RS, a.rhi[0], Q, q0);
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
       s_wm[tid] = jj < batch ? imod_p(a.info[jj * a.K + k].wc[0], P) : 0;
     }
     if constexpr (TMA) {  // receptor k's tile (includes the CTA barrier)
-      if (!tile_arrived(&s_bar, parity, a.err)) return;
+      if (!tile_arrived(&s_bar, parity, a.err, a.wait_test ? (1ll << 20) : (1ll << 31))) return;
     } else {
       __syncthreads();
     }

@@ -83,7 +83,7 @@ def test_largest_fft_edge_and_chunked_spreading(pkg):
     assert out["n_valid"].sum() > 0
 
 
-@pytest.mark.parametrize("n0,edge", [(84, 96), (100, 112), (117, 120), (126, 128)])
+@pytest.mark.parametrize("n0,edge", [(60, 64), (70, 72), (84, 96), (100, 112), (117, 120), (126, 128)])
 def test_fp32_x_edge_rounded_to_the_compile_time_x_pass(pkg, n0, edge):
     """In the FP32 forms the x-axis transform edge is rounded up to the
     compile-time x pass's edges (8 R, R = 8 ... 16) when that costs at most
