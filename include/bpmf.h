@@ -135,7 +135,9 @@ void bpmf_destroy(bpmf_ctx_t ctx);
 const char *bpmf_status_string(int status);
 /* Reason for the last failing call on this context ("" if none); after a
  * bpmf_eval that returned BPMF_WARN_REFINE_FALLBACK, how many ligands were
- * recomputed and why (certificate failed, candidate list overflowed). */
+ * recomputed and why (certificate failed, candidate list overflowed), by
+ * the reasons of each ligand's last refined pass (its re-run, when the first
+ * pass only overflowed). */
 const char *bpmf_last_error(bpmf_ctx_t ctx);
 
 /*

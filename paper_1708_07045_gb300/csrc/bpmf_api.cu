@@ -2127,7 +2127,10 @@ namespace {
 // minimum; a ligand whose
 // certificate failed, or whose list overflowed again, is evaluated again in
 // float pairs over the same outputs, and the result carries
-// BPMF_WARN_REFINE_FALLBACK.  The context's note (bpmf_last_error) counts both.
+// BPMF_WARN_REFINE_FALLBACK.  The context's note (bpmf_last_error) counts both,
+// the fallbacks by the reasons of the ligand's last refined pass (a first
+// pass with a capped list may check no translation of the final window, so
+// only its re-run can tell whether the certificate holds).
 int eval_checked(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K, double kT, unsigned mode,
                  double *logZ, int64_t *n_valid, double *bpmf_out, double *dG, cudaStream_t st, int only_lig,
                  int only_conf, double *export_E, double *Emin = nullptr, double *Dom = nullptr) {
@@ -2136,6 +2139,7 @@ int eval_checked(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K,
                      Dom, &fails);
   int n_cert = 0, n_over = 0, n_rerun = 0;
   for (const auto &f : fails) {
+    int reasons = f.second;  // of the last refined pass of this ligand
     if (f.second == 2) {
       // only the list overflowed (the certificate held where it was checked):
       // the ligand again in the same form, every pair starting from its
@@ -2152,11 +2156,12 @@ int eval_checked(bpmf_ctx *c, const bpmf_lig *lg, const bpmf_rec_t *recs, int K,
         ++n_rerun;
         continue;
       }
+      reasons = again.front().second;  // why the re-run failed
     }
     eval_impl(c, lg, recs, K, kT, BPMF_MODE_FF, logZ, n_valid, bpmf_out, dG, st, f.first, only_conf, export_E, Emin,
               Dom);
-    n_cert += (f.second & 1) != 0;
-    n_over += (f.second & 2) != 0;
+    n_cert += (reasons & 1) != 0;
+    n_over += (reasons & 2) != 0;
   }
   c->note.clear();
   if (n_rerun)

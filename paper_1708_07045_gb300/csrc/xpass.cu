@@ -14,22 +14,27 @@
 // the spectra live in shared memory in the permuted row order
 // row 8 k2 + k1 <-> frequency k2 + R k1, and the inverse returns natural order.
 //
-// CTA = 2 configurations x 8 consecutive (y, zf) columns, 256 threads.  A
-// half-warp owns one unit at a time and its 16 lanes are the 16 lines of a
-// channel (configuration g = lane / 8, column l = lane % 8): every shared
-// access of a half-warp is 16 consecutive float2 (no bank conflicts), and the
-// index arithmetic is per unit, not per element.  Shared-memory round trips
-// are kept to the two transposes each DFT needs: stage A reads the ligand's
-// rows from global memory into registers, the spectral product is formed
-// inside the first inverse stage from the staged receptor tile, and the last
+// CTA = 2 configurations x 8 consecutive (y, zf) columns, one half-warp per
+// k2 (16 R threads).  A half-warp owns one unit at a time and its 16 lanes are
+// the 16 lines of a channel (configuration g = lane / 8, column l = lane % 8):
+// every shared access of a half-warp is 16 consecutive float2 (no bank
+// conflicts), and the index arithmetic is per unit, not per element.
+// Shared-memory round trips are kept to the one transpose each DFT needs:
+// stage A reads the ligand's rows from global memory into registers, stage B
+// leaves the three channels' spectra at the half-warp's frequencies k2 + R k1
+// in its registers for every receptor, the spectral product is formed there
+// with the staged receptor tile inside the first inverse stage, and the last
 // inverse stage writes the site-window rows straight to global memory.
 //
 // Each receptor's spectra for the CTA's columns (3 channels x P frequencies x
-// 8 columns) are staged in shared memory while the previous transform runs:
-// by one TMA tensor copy (cp.async.bulk.tensor, completion on an mbarrier)
-// when the receptor group has at most kXpMaxMaps receptors, else by 16-byte
-// cp.async copies.  Every mbarrier wait is bounded: after about a second it
-// sets the call's error flag and the CTA returns.
+// 8 columns) are staged in one of two shared-memory tiles two receptors
+// ahead: by one TMA tensor copy (cp.async.bulk.tensor, completion on an
+// mbarrier per tile) when the receptor group has at most kXpMaxMaps
+// receptors, else by 16-byte cp.async copies.  With two inverse buffers the
+// CTA meets one barrier per receptor: the product of receptor k + 1 (other
+// buffer) runs while receptor k's last stage does.  Every mbarrier wait is
+// bounded: after about a second it sets the call's error flag, waits
+// (bounded) for the tiles still in flight, and the CTA returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -43,7 +48,6 @@ namespace bpmf {
 
 namespace {
 
-constexpr int kXpNT = 256;     // threads per CTA
 constexpr int kXpLW = 8;       // columns per CTA
 constexpr int kXpG = 2;        // configurations per CTA
 constexpr int kXpNLF = 48;     // forward lines: 3 channels x 2 configurations x 8 columns
@@ -100,10 +104,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // spectra (row 8 k2 + k1 <-> frequency k2 + R k1): 16-byte asynchronous
 // copies of column pairs (Q is even and q0 a multiple of 8, so each pair is
 // 16-byte aligned and wholly inside or outside the spectrum).
-template <int P>
+template <int P, int NT>
 __device__ __forceinline__ void stage_receptor(cx<float> *RS, const float2 *rh, int Q, int q0) {
   constexpr int R = P / 8;
-  for (int e = threadIdx.x; e < 3 * P * 4; e += kXpNT) {
+  for (int e = threadIdx.x; e < 3 * P * 4; e += NT) {
     const int c = e & 3, tr = e >> 2, t = tr / P, row = tr - t * P;
     const int f = (row >> 3) + R * (row & 7);
     const bool v = q0 + 2 * c < Q;
@@ -111,19 +115,17 @@ __device__ __forceinline__ void stage_receptor(cx<float> *RS, const float2 *rh, 
   }
 }
 
-// Every thread waits for the current tile; the CTA agrees on the outcome.  On
-// a timeout the error flag is set, the copy in flight is waited for once more
-// (again bounded), and the CTA is to return.
-__device__ __forceinline__ bool tile_arrived(unsigned long long *bar, unsigned &parity, int *err, long long limit) {
-  const bool ok = mbar_wait(bar, parity, limit);
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0 && err) atomicOr(err, 1);
-    mbar_wait(bar, parity, limit);
-    return false;
-  }
-  parity ^= 1u;
-  return true;
-}
+// Launch shape of the x pass on edge P = 8 R: one half-warp per k2 (16 R
+// threads), and the CTAs per SM the registers are budgeted for (the shared
+// memory of P <= 96 fits three CTAs per SM, of P <= 72 four).
+template <int P>
+struct XpCfg {
+  static constexpr int R = P / 8;
+  static constexpr int NT = 16 * R;
+  static constexpr int MINB = P <= 72 ? 4 : (P <= 96 ? 3 : 2);
+  // the last inverse stage has 8 units (n1); with 16 half-warps two share one
+  static constexpr bool kSplitA = R == 16;
+};
 
 // Half of an inverse composite R-point DFT (R = R1 R2, decimation in time as
 // in dft_small: R2 length-R1 DFTs over the inputs v[R2 n1 + n2], twiddles
@@ -131,14 +133,8 @@ __device__ __forceinline__ bool tile_arrived(unsigned long long *bar, unsigned &
 // ... of half h, outputs o[i] = X[k1 + R1 k2] with k1 = h R1 / 2 + i / R2,
 // k2 = i % R2.
 template <int R>
-struct HalfSplit {
-  static constexpr int R1 = (R == 12 || R == 16) ? 4 : 2;
-  static constexpr bool ok = R == 8 || R == 10 || R == 12 || R == 14 || R == 16;
-};
-
-template <int R>
 __device__ __forceinline__ void idft_half(const cx<float> *v, int h, const float4 *tw, int P, cx<float> *o) {
-  constexpr int R1 = HalfSplit<R>::R1, R2 = R / R1, H = R1 / 2;
+  constexpr int R1 = 4, R2 = R / R1, H = R1 / 2;
   cx<float> b[H][R2];
 #pragma unroll
   for (int n2 = 0; n2 < R2; ++n2) {
@@ -162,37 +158,48 @@ __device__ __forceinline__ void idft_half(const cx<float> *v, int h, const float
   }
 }
 
+// Shared memory of k_xpass<P>: the twiddles, the ligand spectra L [P][48]
+// (reused as the two inverse buffers W [2][P][16] once the forward transform
+// is done), two receptor tiles [2][3][P][8] (128-byte aligned TMA
+// destinations), and slack for that alignment.
+template <int P>
+constexpr size_t xpass_smem_bytes() {
+  return sizeof(float4) * P + sizeof(cx<float>) * (size_t)P * (kXpNLF + 2 * 3 * kXpLW) + 128;
+}
+
 template <int P, bool TMA>
-__global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, const __grid_constant__ XpassMaps maps) {
-  constexpr int R = P / 8;
-  constexpr unsigned kTileBytes = 3u * P * kXpLW * sizeof(cx<float>);
-  __shared__ alignas(8) unsigned long long s_bar;  // receptor tile arrivals (TMA)
-  unsigned parity = 0;
-  constexpr int NLI = 16;  // inverse lines: 2 configurations x 8 columns (one receptor at a time)
+__global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
+    k_xpass(XfusedArgs a, int batch, const __grid_constant__ XpassMaps maps) {
+  constexpr int R = P / 8, NT = XpCfg<P>::NT;
+  constexpr int NLI = 16;                    // inverse lines: 2 configurations x 8 columns
+  constexpr int kTile = 3 * P * kXpLW;       // complex values of one receptor tile
+  constexpr unsigned kTileBytes = kTile * sizeof(cx<float>);
+  __shared__ alignas(8) unsigned long long s_bar[2];  // arrivals of the two receptor tiles (TMA)
   extern __shared__ float4 smem[];
-  float4 *tw = smem;                                         // [P] exp(-2 pi i k / P)
-  cx<float> *L = reinterpret_cast<cx<float> *>(tw + P);      // [P][48] ligand spectra (permuted rows)
-  cx<float> *W = L + P * kXpNLF;                             // [P][16] inverse transform
-  // [3][P][8] staged receptor spectra, 128-byte aligned (TMA destination)
-  cx<float> *RS = reinterpret_cast<cx<float> *>((reinterpret_cast<uintptr_t>(W + P * NLI) + 127) & ~uintptr_t(127));
-  __shared__ int s_wm[2];                                    // window start along x, mod P, per g
+  float4 *tw = smem;                                     // [P] exp(-2 pi i k / P)
+  cx<float> *L = reinterpret_cast<cx<float> *>(tw + P);  // [P][48], then W [2][P][16]
+  cx<float> *RS = reinterpret_cast<cx<float> *>((reinterpret_cast<uintptr_t>(L + P * kXpNLF) + 127) & ~uintptr_t(127));
   const int tid = threadIdx.x, hw = tid >> 4, hl = tid & 15;
   const int g = hl >> 3, l = hl & 7;
   const int nJG = (batch + kXpG - 1) / kXpG;
   const int j0 = (blockIdx.x % nJG) * kXpG;
   const int q0 = (blockIdx.x / nJG) * kXpLW;
-  const int Q = (int)a.Q;
+  const int Q = (int)a.Q, K = a.K;
   const int j = j0 + g, q = q0 + l;
   const bool live = j < batch && q < Q;
-  for (int i = tid; i < P; i += kXpNT) tw[i] = a.tw[i];
-  // the first receptor's spectra, asynchronously, while the ligand's are transformed
+  const long long limit = a.wait_test ? (1ll << 20) : (1ll << 31);
+  for (int i = tid; i < P; i += NT) tw[i] = a.tw[i];
+  // the first two receptors' spectra, asynchronously, while the ligand's are transformed
   if constexpr (TMA) {
     if (tid == 0) {
-      mbar_init(&s_bar, 1);
-      if (a.K > 0 && !a.wait_test) tma_load_3d(RS, &maps.m[0], 2 * q0, 0, 0, &s_bar, kTileBytes);
+      mbar_init(&s_bar[0], 1);
+      mbar_init(&s_bar[1], 1);
+      if (K > 0 && !a.wait_test) tma_load_3d(RS, &maps.m[0], 2 * q0, 0, 0, &s_bar[0], kTileBytes);
+      if (K > 1) tma_load_3d(RS + kTile, &maps.m[1], 2 * q0, 0, 0, &s_bar[1], kTileBytes);
     }
   } else {
-    if (a.K > 0) stage_receptor<P>(RS, a.rhi[0], Q, q0);
+    if (K > 0) stage_receptor<P, NT>(RS, a.rhi[0], Q, q0);
+    if (K > 1) stage_receptor<P, NT>(RS + kTile, a.rhi[1], Q, q0);
   }
   __syncthreads();
   // forward A: unit (n1, t), R-point DFT over n2 of rows n1 + 8 n2 read
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
     const int U0 = a.U0 < P ? a.U0 : P;
     const int u0 = live ? min(a.meta ? a.meta[j].u[0] : U0, U0) : 0;
     const cx<float> *ly = reinterpret_cast<const cx<float> *>(a.ly);
-    for (int u = hw; u < 8 * 3; u += kXpNT / 16) {
+    for (int u = hw; u < 8 * 3; u += R) {
       const int n1 = u & 7, t = u >> 3;
       const cx<float> *src = ly + (((long long)j * 3 + t) * a.U0 + n1) * Q + q;
       cx<float> v[R];
@@ -217,74 +224,79 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
     }
   }
   __syncthreads();
-  // forward B: unit (k2, t), 8-point DFT of rows 8 k2 + n1 -> row 8 k2 + k1 = X[k2 + R k1]
-  for (int u = hw; u < R * 3; u += kXpNT / 16) {
-    const int t = u / R, k2 = u - t * R;
-    cx<float> *col = L + 8 * k2 * kXpNLF + t * 16 + hl;
-    cx<float> v[8];
+  // forward B: unit k2 = hw, 8-point DFTs over n1 of the three channels' rows
+  // 8 k2 + n1 -> X_t[k2 + R k1], kept in registers for every receptor
+  const int k2 = hw;
+  cx<float> Lr[3][8];
 #pragma unroll
-    for (int n1 = 0; n1 < 8; ++n1) v[n1] = col[n1 * kXpNLF];
-    dft_small<float, 8>(v, false, tw, P);
+  for (int t = 0; t < 3; ++t) {
+    const cx<float> *col = L + 8 * k2 * kXpNLF + t * 16 + hl;
 #pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1) col[k1 * kXpNLF] = v[k1];
+    for (int n1 = 0; n1 < 8; ++n1) Lr[t][n1] = col[n1 * kXpNLF];
+    dft_small<float, 8>(Lr[t], false, tw, P);
   }
   if constexpr (!TMA) cp_wait_all();
-  for (int k = 0; k < a.K; ++k) {
-    if (tid < 2) {
-      const int jj = j0 + tid;
-      s_wm[tid] = jj < batch ? imod_p(a.info[jj * a.K + k].wc[0], P) : 0;
-    }
-    if constexpr (TMA) {  // receptor k's tile (includes the CTA barrier)
-      if (!tile_arrived(&s_bar, parity, a.err, a.wait_test ? (1ll << 20) : (1ll << 31))) return;
-    } else {
-      __syncthreads();
-    }
-    const int wm = s_wm[g];  // read before the next write, which follows the barrier below
-    // product and inverse B', unit k2: P_k = sum_t R_{k,t} conj(L_t) at the
-    // frequencies k2 + R k1 (rows 8 k2 + k1), inverse 8-point DFT over k1,
-    // then conj(w_P^(n1 k2)), into rows 8 k2 + n1 of W
-    for (int k2 = hw; k2 < R; k2 += kXpNT / 16) {
+  __syncthreads();  // L is the inverse buffers W from here on
+  for (int k = 0; k < K; ++k) {
+    const int b = k & 1;
+    const cx<float> *rs0 = RS + b * kTile;
+    cx<float> *Wb = L + b * P * NLI;
+    const int wm = live ? imod_p(a.info[j * K + k].wc[0], P) : 0;  // window start along x, mod P
+    bool ok = true;
+    if constexpr (TMA) ok = mbar_wait(&s_bar[b], (k >> 1) & 1, limit);
+    // product and inverse B', unit k2: P_f = sum_t R_{f,t} conj(L_t) at the
+    // frequencies f = k2 + R k1, inverse 8-point DFT over k1, then
+    // conj(w_P^(n1 k2)), into rows 8 k2 + n1 of W[b]
+    {
       cx<float> v[8];
 #pragma unroll
       for (int k1 = 0; k1 < 8; ++k1) {
-        const int row = 8 * k2 + k1;
         // TMA tiles hold natural frequency order, the cp.async tiles row order
-        const cx<float> *rs = RS + (TMA ? k2 + R * k1 : row) * kXpLW + l;
-        const cx<float> *lx = L + row * kXpNLF + hl;
-        v[k1] = c_add(c_add(c_mulconj(rs[0], lx[0]), c_mulconj(rs[P * kXpLW], lx[16])),
-                      c_mulconj(rs[2 * P * kXpLW], lx[32]));
+        const cx<float> *rs = rs0 + (TMA ? k2 + R * k1 : 8 * k2 + k1) * kXpLW + l;
+        v[k1] = c_add(c_add(c_mulconj(rs[0], Lr[0][k1]), c_mulconj(rs[P * kXpLW], Lr[1][k1])),
+                      c_mulconj(rs[2 * P * kXpLW], Lr[2][k1]));
       }
       dft_small<float, 8>(v, true, tw, P);
-      cx<float> *col = W + 8 * k2 * NLI + hl;
 #pragma unroll
       for (int n1 = 1; n1 < 8; ++n1) v[n1] = c_mul(v[n1], tw_load<float>(tw[n1 * k2], true));
+      cx<float> *col = Wb + 8 * k2 * NLI + hl;
 #pragma unroll
       for (int n1 = 0; n1 < 8; ++n1) col[n1 * NLI] = v[n1];
     }
-    __syncthreads();
-    // the next receptor's spectra stream in while this one is transformed back
-    if (k + 1 < a.K) {
+    if constexpr (!TMA) cp_wait_all();  // receptor k + 1's tile, for the next product
+    // W[b] is complete and tile b has been read.  On a timeout the CTA agrees,
+    // waits (bounded) for the tiles still in flight and returns.
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0 && a.err) atomicOr(a.err, 1);
       if constexpr (TMA) {
-        if (tid == 0) tma_load_3d(RS, &maps.m[k + 1], 2 * q0, 0, 0, &s_bar, kTileBytes);
+        mbar_wait(&s_bar[b], (k >> 1) & 1, limit);
+        if (k + 1 < K) mbar_wait(&s_bar[b ^ 1], ((k + 1) >> 1) & 1, limit);
+      }
+      return;
+    }
+    // receptor k + 2's spectra stream into tile b while this one is
+    // transformed back and the next multiplied
+    if (k + 2 < K) {
+      if constexpr (TMA) {
+        if (tid == 0) tma_load_3d(RS + b * kTile, &maps.m[k + 2], 2 * q0, 0, 0, &s_bar[b], kTileBytes);
       } else {
-        stage_receptor<P>(RS, a.rhi[k + 1], Q, q0);
+        stage_receptor<P, NT>(RS + b * kTile, a.rhi[k + 2], Q, q0);
       }
     }
     // inverse A', unit n1: inverse R-point DFT over k2 -> x[n1 + 8 n2]; the
-    // rows inside the site window along x go straight to the output.  Where R
-    // splits as R1 x R2 with R1 even, two half-warps share a unit, each taking
-    // half of the R1 length-R2 sub-transforms (half of the outputs)
-    if constexpr (HalfSplit<R>::ok) {
-      constexpr int R1 = HalfSplit<R>::R1, R2 = R / R1, H = R1 / 2;
+    // rows inside the site window along x go straight to the output.  The
+    // next receptor's product needs no barrier first: it writes the other W.
+    cx<float> *dst = reinterpret_cast<cx<float> *>(a.x2) + ((long long)j * K + k) * a.S0 * Q + q;
+    if constexpr (XpCfg<P>::kSplitA) {
+      constexpr int R1 = 4, R2 = R / R1, H = R1 / 2;
       const int n1 = hw & 7, h = hw >> 3;
-      const cx<float> *col = W + n1 * NLI + hl;
+      const cx<float> *col = Wb + n1 * NLI + hl;
       cx<float> v[R];
 #pragma unroll
-      for (int k2 = 0; k2 < R; ++k2) v[k2] = col[8 * k2 * NLI];
+      for (int m = 0; m < R; ++m) v[m] = col[8 * m * NLI];
       cx<float> o[R / 2];
       idft_half<R>(v, h, tw, P, o);
       if (live) {
-        cx<float> *dst = reinterpret_cast<cx<float> *>(a.x2) + ((long long)j * a.K + k) * a.S0 * Q + q;
 #pragma unroll
         for (int i = 0; i < R / 2; ++i) {
           const int n2 = h * H + i / R2 + R1 * (i % R2);  // output k1 + R1 k2
@@ -295,13 +307,12 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
       }
     } else if (hw < 8) {
       const int n1 = hw;
-      const cx<float> *col = W + n1 * NLI + hl;
+      const cx<float> *col = Wb + n1 * NLI + hl;
       cx<float> v[R];
 #pragma unroll
-      for (int k2 = 0; k2 < R; ++k2) v[k2] = col[8 * k2 * NLI];
+      for (int m = 0; m < R; ++m) v[m] = col[8 * m * NLI];
       dft_small<float, R>(v, true, tw, P);
       if (live) {
-        cx<float> *dst = reinterpret_cast<cx<float> *>(a.x2) + ((long long)j * a.K + k) * a.S0 * Q + q;
 #pragma unroll
         for (int n2 = 0; n2 < R; ++n2) {
           int s = n1 + 8 * n2 - wm;
@@ -310,14 +321,12 @@ __global__ void __launch_bounds__(kXpNT, 3) k_xpass(XfusedArgs a, int batch, con
         }
       }
     }
-    if constexpr (!TMA) cp_wait_all();
   }
 }
 
 template <int P>
 size_t xpass_smem() {
-  // tw (16 P bytes), L and W (8 P (48 + 16)), then RS rounded up to 128 bytes
-  return sizeof(float4) * P + sizeof(cx<float>) * (size_t)P * (kXpNLF + 16 + 3 * kXpLW) + 128;
+  return xpass_smem_bytes<P>();
 }
 
 // Tensor maps of the receptor spectra [3][P][Q] float2 as FP32 [3][P][2Q],
@@ -371,15 +380,13 @@ cudaError_t launch_xpass_p(const XfusedArgs &a, int batch, cudaStream_t st) {
     // 16-byte aligned spectra whose rows are 16-byte multiples (Q even)
     tma = ((reinterpret_cast<unsigned long long>(a.rhi_h[k]) & 15ull) == 0) && receptor_map(a.rhi_h[k], P, a.Q, &maps.m[k]);
   }
-  if (tma) {
-    cudaError_t e = cudaFuncSetAttribute(k_xpass<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_xpass<P, true><<<(unsigned)blocks, kXpNT, smem, st>>>(a, batch, maps);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_xpass<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_xpass<P, false><<<(unsigned)blocks, kXpNT, smem, st>>>(a, batch, maps);
-  }
+  constexpr int NT = XpCfg<P>::NT;
+  auto kern = tma ? k_xpass<P, true> : k_xpass<P, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)blocks, NT, smem, st>>>(a, batch, maps);
   return cudaGetLastError();
 }
 
