@@ -34,6 +34,226 @@ struct FftPlan {
   int *err;
 };
 
+// exp(-2 pi i m / R) for the radices of dft_small (R <= 16, 0 <= m < R): the
+// float nearest to the real and the imaginary part, the same values as the
+// hi parts of the shared-memory twiddle table, as compile-time constants so
+// that the float path of dft_small reads no table for its internal twiddles.
+__host__ __device__ constexpr float unit_root_re(int R, int m) {
+  switch (R * 16 + m) {
+    case 3 * 16 + 1: return -0.5f;
+    case 3 * 16 + 2: return -0.5f;
+    case 5 * 16 + 1: return 0.309017f;
+    case 5 * 16 + 2: return -0.809017f;
+    case 5 * 16 + 3: return -0.809017f;
+    case 5 * 16 + 4: return 0.309017f;
+    case 7 * 16 + 1: return 0.6234898f;
+    case 7 * 16 + 2: return -0.22252093f;
+    case 7 * 16 + 3: return -0.90096885f;
+    case 7 * 16 + 4: return -0.90096885f;
+    case 7 * 16 + 5: return -0.22252093f;
+    case 7 * 16 + 6: return 0.6234898f;
+    case 8 * 16 + 1: return 0.70710677f;
+    case 8 * 16 + 2: return -0.0f;
+    case 8 * 16 + 3: return -0.70710677f;
+    case 8 * 16 + 4: return -1.0f;
+    case 8 * 16 + 5: return -0.70710677f;
+    case 8 * 16 + 6: return 0.0f;
+    case 8 * 16 + 7: return 0.70710677f;
+    case 9 * 16 + 1: return 0.76604444f;
+    case 9 * 16 + 2: return 0.17364818f;
+    case 9 * 16 + 3: return -0.5f;
+    case 9 * 16 + 4: return -0.9396926f;
+    case 9 * 16 + 5: return -0.9396926f;
+    case 9 * 16 + 6: return -0.5f;
+    case 9 * 16 + 7: return 0.17364818f;
+    case 9 * 16 + 8: return 0.76604444f;
+    case 10 * 16 + 1: return 0.809017f;
+    case 10 * 16 + 2: return 0.309017f;
+    case 10 * 16 + 3: return -0.309017f;
+    case 10 * 16 + 4: return -0.809017f;
+    case 10 * 16 + 5: return -1.0f;
+    case 10 * 16 + 6: return -0.809017f;
+    case 10 * 16 + 7: return -0.309017f;
+    case 10 * 16 + 8: return 0.309017f;
+    case 10 * 16 + 9: return 0.809017f;
+    case 12 * 16 + 1: return 0.8660254f;
+    case 12 * 16 + 2: return 0.5f;
+    case 12 * 16 + 3: return -0.0f;
+    case 12 * 16 + 4: return -0.5f;
+    case 12 * 16 + 5: return -0.8660254f;
+    case 12 * 16 + 6: return -1.0f;
+    case 12 * 16 + 7: return -0.8660254f;
+    case 12 * 16 + 8: return -0.5f;
+    case 12 * 16 + 9: return 0.0f;
+    case 12 * 16 + 10: return 0.5f;
+    case 12 * 16 + 11: return 0.8660254f;
+    case 14 * 16 + 1: return 0.90096885f;
+    case 14 * 16 + 2: return 0.6234898f;
+    case 14 * 16 + 3: return 0.22252093f;
+    case 14 * 16 + 4: return -0.22252093f;
+    case 14 * 16 + 5: return -0.6234898f;
+    case 14 * 16 + 6: return -0.90096885f;
+    case 14 * 16 + 7: return -1.0f;
+    case 14 * 16 + 8: return -0.90096885f;
+    case 14 * 16 + 9: return -0.6234898f;
+    case 14 * 16 + 10: return -0.22252093f;
+    case 14 * 16 + 11: return 0.22252093f;
+    case 14 * 16 + 12: return 0.6234898f;
+    case 14 * 16 + 13: return 0.90096885f;
+    case 15 * 16 + 1: return 0.9135454f;
+    case 15 * 16 + 2: return 0.6691306f;
+    case 15 * 16 + 3: return 0.309017f;
+    case 15 * 16 + 4: return -0.104528464f;
+    case 15 * 16 + 5: return -0.5f;
+    case 15 * 16 + 6: return -0.809017f;
+    case 15 * 16 + 7: return -0.9781476f;
+    case 15 * 16 + 8: return -0.9781476f;
+    case 15 * 16 + 9: return -0.809017f;
+    case 15 * 16 + 10: return -0.5f;
+    case 15 * 16 + 11: return -0.104528464f;
+    case 15 * 16 + 12: return 0.309017f;
+    case 15 * 16 + 13: return 0.6691306f;
+    case 15 * 16 + 14: return 0.9135454f;
+    case 16 * 16 + 1: return 0.9238795f;
+    case 16 * 16 + 2: return 0.70710677f;
+    case 16 * 16 + 3: return 0.38268343f;
+    case 16 * 16 + 4: return -0.0f;
+    case 16 * 16 + 5: return -0.38268343f;
+    case 16 * 16 + 6: return -0.70710677f;
+    case 16 * 16 + 7: return -0.9238795f;
+    case 16 * 16 + 8: return -1.0f;
+    case 16 * 16 + 9: return -0.9238795f;
+    case 16 * 16 + 10: return -0.70710677f;
+    case 16 * 16 + 11: return -0.38268343f;
+    case 16 * 16 + 12: return 0.0f;
+    case 16 * 16 + 13: return 0.38268343f;
+    case 16 * 16 + 14: return 0.70710677f;
+    case 16 * 16 + 15: return 0.9238795f;
+    default: return 1.f;  // m = 0
+  }
+}
+__host__ __device__ constexpr float unit_root_im(int R, int m) {
+  switch (R * 16 + m) {
+    case 3 * 16 + 1: return -0.8660254f;
+    case 3 * 16 + 2: return 0.8660254f;
+    case 5 * 16 + 1: return -0.95105654f;
+    case 5 * 16 + 2: return -0.58778524f;
+    case 5 * 16 + 3: return 0.58778524f;
+    case 5 * 16 + 4: return 0.95105654f;
+    case 7 * 16 + 1: return -0.7818315f;
+    case 7 * 16 + 2: return -0.9749279f;
+    case 7 * 16 + 3: return -0.43388373f;
+    case 7 * 16 + 4: return 0.43388373f;
+    case 7 * 16 + 5: return 0.9749279f;
+    case 7 * 16 + 6: return 0.7818315f;
+    case 8 * 16 + 1: return -0.70710677f;
+    case 8 * 16 + 2: return -1.0f;
+    case 8 * 16 + 3: return -0.70710677f;
+    case 8 * 16 + 4: return 0.0f;
+    case 8 * 16 + 5: return 0.70710677f;
+    case 8 * 16 + 6: return 1.0f;
+    case 8 * 16 + 7: return 0.70710677f;
+    case 9 * 16 + 1: return -0.64278764f;
+    case 9 * 16 + 2: return -0.9848077f;
+    case 9 * 16 + 3: return -0.8660254f;
+    case 9 * 16 + 4: return -0.34202015f;
+    case 9 * 16 + 5: return 0.34202015f;
+    case 9 * 16 + 6: return 0.8660254f;
+    case 9 * 16 + 7: return 0.9848077f;
+    case 9 * 16 + 8: return 0.64278764f;
+    case 10 * 16 + 1: return -0.58778524f;
+    case 10 * 16 + 2: return -0.95105654f;
+    case 10 * 16 + 3: return -0.95105654f;
+    case 10 * 16 + 4: return -0.58778524f;
+    case 10 * 16 + 5: return 0.0f;
+    case 10 * 16 + 6: return 0.58778524f;
+    case 10 * 16 + 7: return 0.95105654f;
+    case 10 * 16 + 8: return 0.95105654f;
+    case 10 * 16 + 9: return 0.58778524f;
+    case 12 * 16 + 1: return -0.5f;
+    case 12 * 16 + 2: return -0.8660254f;
+    case 12 * 16 + 3: return -1.0f;
+    case 12 * 16 + 4: return -0.8660254f;
+    case 12 * 16 + 5: return -0.5f;
+    case 12 * 16 + 6: return 0.0f;
+    case 12 * 16 + 7: return 0.5f;
+    case 12 * 16 + 8: return 0.8660254f;
+    case 12 * 16 + 9: return 1.0f;
+    case 12 * 16 + 10: return 0.8660254f;
+    case 12 * 16 + 11: return 0.5f;
+    case 14 * 16 + 1: return -0.43388373f;
+    case 14 * 16 + 2: return -0.7818315f;
+    case 14 * 16 + 3: return -0.9749279f;
+    case 14 * 16 + 4: return -0.9749279f;
+    case 14 * 16 + 5: return -0.7818315f;
+    case 14 * 16 + 6: return -0.43388373f;
+    case 14 * 16 + 7: return 0.0f;
+    case 14 * 16 + 8: return 0.43388373f;
+    case 14 * 16 + 9: return 0.7818315f;
+    case 14 * 16 + 10: return 0.9749279f;
+    case 14 * 16 + 11: return 0.9749279f;
+    case 14 * 16 + 12: return 0.7818315f;
+    case 14 * 16 + 13: return 0.43388373f;
+    case 15 * 16 + 1: return -0.40673664f;
+    case 15 * 16 + 2: return -0.7431448f;
+    case 15 * 16 + 3: return -0.95105654f;
+    case 15 * 16 + 4: return -0.9945219f;
+    case 15 * 16 + 5: return -0.8660254f;
+    case 15 * 16 + 6: return -0.58778524f;
+    case 15 * 16 + 7: return -0.20791169f;
+    case 15 * 16 + 8: return 0.20791169f;
+    case 15 * 16 + 9: return 0.58778524f;
+    case 15 * 16 + 10: return 0.8660254f;
+    case 15 * 16 + 11: return 0.9945219f;
+    case 15 * 16 + 12: return 0.95105654f;
+    case 15 * 16 + 13: return 0.7431448f;
+    case 15 * 16 + 14: return 0.40673664f;
+    case 16 * 16 + 1: return -0.38268343f;
+    case 16 * 16 + 2: return -0.70710677f;
+    case 16 * 16 + 3: return -0.9238795f;
+    case 16 * 16 + 4: return -1.0f;
+    case 16 * 16 + 5: return -0.9238795f;
+    case 16 * 16 + 6: return -0.70710677f;
+    case 16 * 16 + 7: return -0.38268343f;
+    case 16 * 16 + 8: return 0.0f;
+    case 16 * 16 + 9: return 0.38268343f;
+    case 16 * 16 + 10: return 0.70710677f;
+    case 16 * 16 + 11: return 0.9238795f;
+    case 16 * 16 + 12: return 1.0f;
+    case 16 * 16 + 13: return 0.9238795f;
+    case 16 * 16 + 14: return 0.70710677f;
+    case 16 * 16 + 15: return 0.38268343f;
+    default: return 0.f;  // m = 0
+  }
+}
+
+// v times w_R^m = exp(-2 pi i m / R) (conjugated for the inverse), for the
+// twiddles inside dft_small: the float path takes the constants above (-i, +i
+// and -1 as a rotation and a negation), the float-pair path the table, whose
+// entries for R lie P / R apart.
+template <class T, int R>
+__device__ __forceinline__ cx<T> tw_small_mul(cx<T> v, int m, bool inv, const float4 *tw, int P) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (4 * m == R) return c_rot(v, inv);
+    if (4 * m == 3 * R) return c_rot(v, !inv);
+    if (2 * m == R) return cx<float>{-v.re, -v.im};
+    const float im = unit_root_im(R, m);
+    return c_mul(v, cx<float>{unit_root_re(R, m), inv ? -im : im});
+  } else {
+    return c_mul(v, tw_load<T>(tw[m * (P / R)], inv));
+  }
+}
+// w_R^m as a table entry {re hi, im hi, re lo, im lo} (the float path: the
+// constants, lo parts zero)
+template <class T, int R>
+__device__ __forceinline__ float4 root_q(int m, const float4 *tw, int P) {
+  if constexpr (std::is_same<T, float>::value) {
+    return make_float4(unit_root_re(R, m), unit_root_im(R, m), 0.f, 0.f);
+  } else {
+    return tw[m * (P / R)];
+  }
+}
+
 template <class T, int R>
 __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, int P) {
   if constexpr (R == 2) {
@@ -55,7 +275,7 @@ __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, 
       b[k] = c_sub(v[k], v[k + 4]);
     }
     // b1 *= w8, b2 *= w8^2 = -i (fwd), b3 *= w8^3; conjugated for inverse
-    const float4 q = tw[P / 8];                 // exp(-i pi/4): (c, -c)
+    const float4 q = root_q<T, 8>(1, tw, P);    // exp(-i pi/4): (c, -c)
     const T c = s_mk<T>(q.x, q.z);                 // cos(pi/4) as hi/lo
     {
       T x = b[1].re, y = b[1].im;
@@ -77,7 +297,7 @@ __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, 
     }
   } else if constexpr (R == 3) {
     // X0 = a + (b + c);  X1,2 = a - (b + c)/2 -/+ i (sqrt(3)/2)(b - c)  (forward)
-    const float4 q = tw[P / 3];                  // exp(-2 pi i / 3) = (-1/2, -sqrt(3)/2)
+    const float4 q = root_q<T, 3>(1, tw, P);     // exp(-2 pi i / 3) = (-1/2, -sqrt(3)/2)
     const T s3 = s_neg(s_mk<T>(q.y, q.w));       // sqrt(3)/2 as hi/lo
     const T half = s_mk<T>(0.5f, 0.f);
     const cx<T> sp = c_add(v[1], v[2]), sm = c_sub(v[1], v[2]);
@@ -92,7 +312,7 @@ __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, 
     //   X1,4 = v0 + c1 (v1 + v4) + c2 (v2 + v3) -/+ i (sa (v1 - v4) + sb (v2 - v3))
     //   X2,3 = v0 + c2 (v1 + v4) + c1 (v2 + v3) -/+ i (sb (v1 - v4) - sa (v2 - v3))
     // (forward; the inverse flips the sign of i)
-    const float4 q1 = tw[P / 5], q2 = tw[2 * (P / 5)];
+    const float4 q1 = root_q<T, 5>(1, tw, P), q2 = root_q<T, 5>(2, tw, P);
     const T c1 = s_mk<T>(q1.x, q1.z), sa = s_neg(s_mk<T>(q1.y, q1.w));
     const T c2 = s_mk<T>(q2.x, q2.z), sb = s_neg(s_mk<T>(q2.y, q2.w));
     const cx<T> s1 = c_add(v[1], v[4]), d1 = c_sub(v[1], v[4]);
@@ -121,7 +341,7 @@ __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, 
       dft_small<T, R1>(a[n2], inv, tw, P);
 #pragma unroll
       for (int k1 = 1; k1 < R1; ++k1)
-        if (n2 > 0) a[n2][k1] = c_mul(a[n2][k1], tw_load<T>(tw[(n2 * k1) * (P / R)], inv));
+        if (n2 > 0) a[n2][k1] = tw_small_mul<T, R>(a[n2][k1], n2 * k1, inv, tw, P);
     }
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
@@ -133,14 +353,13 @@ __device__ __forceinline__ void dft_small(cx<T> *v, bool inv, const float4 *tw, 
       for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = b[k2];
     }
   } else {
-    // radix 7: X[a] = sum_b v[b] w_R^(a b), w_R^m = tw[m P / R]
+    // radix 7: X[a] = sum_b v[b] w_R^(a b)
     cx<T> out[R];
-    const int st = P / R;
 #pragma unroll
     for (int a = 0; a < R; ++a) {
       cx<T> acc = v[0];
 #pragma unroll
-      for (int b = 1; b < R; ++b) acc = c_add(acc, c_mul(v[b], tw_load<T>(tw[((a * b) % R) * st], inv)));
+      for (int b = 1; b < R; ++b) acc = c_add(acc, tw_small_mul<T, R>(v[b], (a * b) % R, inv, tw, P));
       out[a] = acc;
     }
 #pragma unroll

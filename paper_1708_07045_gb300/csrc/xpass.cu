@@ -146,7 +146,7 @@ __device__ __forceinline__ void idft_half(const cx<float> *v, int h, const float
     for (int kk = 0; kk < H; ++kk) {
       const int k1 = h * H + kk;
       cx<float> x = h ? a[H + kk] : a[kk];
-      if (n2 > 0 && k1 > 0) x = c_mul(x, tw_load<float>(tw[(n2 * k1) * (P / R)], true));
+      if (n2 > 0 && k1 > 0) x = tw_small_mul<float, R>(x, n2 * k1, true, tw, P);
       b[kk][n2] = x;
     }
   }
