@@ -64,7 +64,7 @@ def kernel_src_sha(texts=None):
 # workload, averaged over one step's launches, from the ncu capture summarised
 # in profiles/xpass_fp32_protein_scale_traffic.md; valid only for the sources
 # it was taken with
-XPASS_TRAFFIC = {"bytes_per_launch": 564.8e6, "launches_per_step": 27, "src_sha": "e23f0dffd2dff4ce"}
+XPASS_TRAFFIC = {"bytes_per_launch": 565.86e6, "launches_per_step": 29, "src_sha": "47e6df69cf90471c"}
 
 
 def xpass_src_sha():

@@ -1314,8 +1314,10 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
     cv.add(&r->lo, 3ull * P[0] * r->Q * sizeof(float2));
     r->mem = cv.alloc(c);
     r->mem_bytes = cv.total;
-    CK(cudaMemcpyAsync(r->grid, g.p, 3 * vol * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    launch(c, "k_sumsq", st, [&] { return launch_sumsq(r->grid, (long long)vol, r->sumsq, r->sumsq_scratch, st); });
+    // the grids copied into the receptor's block with their sums of squares
+    launch(c, "k_sumsq", st, [&] {
+      return launch_sumsq(static_cast<const float *>(g.p), N, r->grid, r->sumsq, r->sumsq_scratch, st);
+    });
     grid_spectrum(c, static_cast<const float *>(g.p), 1, N, P, &r->hi, &r->lo, st);
     if (!is_device_ptr(grids)) CK(cudaStreamSynchronize(st));
   } catch (Fail f) {

@@ -983,34 +983,105 @@ cudaError_t launch_split_ff(const void *spec, float2 *hi, float2 *lo, long long 
 
 // --------------------------------------------------------------------------
 // The receptor grids cropped to the box [c0, c0 + e) and zero-padded to the
-// extents E >= e (CTA row blockIdx.y = channel t):
-//   out[t][i][j][l] = grid[t][c0_0 + i][c0_1 + j][c0_2 + l] (i, j, l < e), else 0.
-// CTA column blockIdx.x walks (i, j) rows; threads walk l.
-__global__ void __launch_bounds__(256) k_crop(const float *grid, int N0, int N1, int N2, int c00, int c01, int c02,
-                                              int e0, int e1, int e2, int E0, int E1, int E2, float *out) {
-  const int t = blockIdx.y;
-  for (int row = blockIdx.x; row < E0 * E1; row += gridDim.x) {
-    const int ix = row / E1, jy = row % E1;
-    float *dst = out + (((long long)t * E0 + ix) * E1 + jy) * E2;
+// extents E >= e (CTA row blockIdx.y = channel t), with out null only summed:
+//   out[t][i][j][l] = grid[t][c0_0 + i][c0_1 + j][c0_2 + l] (i, j, l < e), else 0,
+// and the sum of squares of each channel's crop (the FP32 error bound of the
+// refined form) in float pairs and in a fixed order, so that the bound, and
+// with it the set of refined translations, is the same on every run: CTA b
+// of channel t owns the (i, j) rows [b rpb, (b + 1) rpb), a warp one row at a
+// time with its lanes along l; the warps' sums are added in order into
+// part[t][b], and the last CTA to finish adds each channel's partials by a
+// fixed tree and resets the counter.
+__global__ void __launch_bounds__(256) k_crop_sq(const float *grid, int N0, int N1, int N2, int c00, int c01, int c02,
+                                                 int e0, int e1, int e2, int E0, int E1, int E2, int rpb, float *out,
+                                                 float2 *part, unsigned *count, float *sumsq) {
+  __shared__ float s_h[256], s_l[256];
+  __shared__ bool s_last;
+  const int t = blockIdx.y, b = blockIdx.x, nb = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = E0 * E1;
+  const int r1 = min((b + 1) * rpb, rows);
+  ff acc{0.f, 0.f};
+  for (int row = b * rpb + warp; row < r1; row += 8) {
+    const int ix = row / E1, jy = row - ix * E1;
     const bool in = ix < e0 && jy < e1;
     const float *src = grid + (((long long)t * N0 + c00 + ix) * N1 + c01 + jy) * N2 + c02;
-    for (int l = threadIdx.x; l < E2; l += blockDim.x) dst[l] = (in && l < e2) ? src[l] : 0.f;
+    float *dst = out ? out + (((long long)t * E0 + ix) * E1 + jy) * E2 : nullptr;
+    for (int l = lane; l < E2; l += 32) {
+      const float v = (in && l < e2) ? src[l] : 0.f;
+      if (dst) dst[l] = v;
+      acc = s_norm(s_add(acc, s_mul(ff{v, 0.f}, ff{v, 0.f})));
+    }
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    const ff other{__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)};
+    acc = s_norm(s_add(acc, other));
+  }
+  if (lane == 0) {
+    s_h[warp] = acc.hi;
+    s_l[warp] = acc.lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ff sum{0.f, 0.f};
+    for (int w = 0; w < 8; ++w) sum = s_norm(s_add(sum, ff{s_h[w], s_l[w]}));
+    part[t * nb + b] = make_float2(sum.hi, sum.lo);
+    __threadfence();
+    s_last = atomicAdd(count, 1u) == 3u * nb - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int c = 0; c < 3; ++c) {
+    const float2 pv = threadIdx.x < nb ? __ldcg(&part[c * nb + threadIdx.x]) : make_float2(0.f, 0.f);
+    s_h[threadIdx.x] = pv.x;
+    s_l[threadIdx.x] = pv.y;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) {
+        const ff r = s_norm(s_add(ff{s_h[threadIdx.x], s_l[threadIdx.x]}, ff{s_h[threadIdx.x + o], s_l[threadIdx.x + o]}));
+        s_h[threadIdx.x] = r.hi;
+        s_l[threadIdx.x] = r.lo;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) sumsq[c] = __fadd_rn(s_h[0], s_l[0]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = 0u;  // for the next call on this scratch (stream order)
 }
+
+namespace {
+// CTAs per channel: at most 255, so that the partials and the counter fit
+// the kSumsqScratch float2 of scratch
+constexpr int kCropSqBlocks = (kSumsqScratch - 1) / 3;
+
+cudaError_t launch_crop_sq(const float *grid, const int N[3], const int c0[3], const int e[3], const int E[3],
+                           float *out, float *sumsq, float2 *scratch, cudaStream_t st) {
+  const int rows = E[0] * E[1];
+  const int nb = std::max(1, std::min(kCropSqBlocks, (rows + 15) / 16));
+  const int rpb = (rows + nb - 1) / nb;
+  unsigned *count = reinterpret_cast<unsigned *>(scratch + kSumsqScratch - 1);
+  cudaError_t err = cudaMemsetAsync(count, 0, sizeof(unsigned), st);
+  if (err != cudaSuccess) return err;
+  k_crop_sq<<<dim3(nb, 3), 256, 0, st>>>(grid, N[0], N[1], N[2], c0[0], c0[1], c0[2], e[0], e[1], e[2], E[0], E[1],
+                                         E[2], rpb, out, scratch, count, sumsq);
+  return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t launch_crop(const float *grid, const int N[3], const int c0[3], const int e[3], const int E[3],
                         float *out, float *sumsq, float2 *scratch, cudaStream_t st) {
   for (int d = 0; d < 3; ++d)
     if (c0[d] < 0 || e[d] < 1 || c0[d] + e[d] > N[d] || E[d] < e[d]) return cudaErrorInvalidValue;
-  const int rows = E[0] * E[1];
-  const int blocks = std::min(rows, sm_count() * 4);
-  const int threads = E[2] >= 128 ? 128 : (E[2] >= 64 ? 64 : 32);
-  k_crop<<<dim3(blocks, 3), threads, 0, st>>>(grid, N[0], N[1], N[2], c0[0], c0[1], c0[2], e[0], e[1], e[2], E[0],
-                                              E[1], E[2], out);
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
   // the padding adds zeros: the sums of squares of the padded crop are the crop's
-  return launch_sumsq(out, (long long)E[0] * E[1] * E[2], sumsq, scratch, st);
+  return launch_crop_sq(grid, N, c0, e, E, out, sumsq, scratch, st);
+}
+
+cudaError_t launch_sumsq(const float *g, const int N[3], float *out, float *sumsq, float2 *scratch, cudaStream_t st) {
+  if ((long long)N[0] * N[1] * N[2] <= 0) return cudaMemsetAsync(sumsq, 0, 3 * sizeof(float), st);
+  const int c0[3] = {0, 0, 0};
+  return launch_crop_sq(g, N, c0, N, N, out, sumsq, scratch, st);
 }
 
 // explicit instantiations

@@ -284,10 +284,11 @@ long long site_window(int N, int site_lo, int site_n, int u, int &w0, int &sa, i
 // ---- launch wrappers (kernels.cu, ligspec.cu, occupancy.cu, refine.cu) ---------
 cudaError_t launch_refine_init(const RefineArgs &a, int batch, cudaStream_t st);  // before k_zinv
 cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st);       // after k_zinv (two kernels)
-// sums of squares of the three grids [3][vol] into out[3] (deterministic;
-// scratch: kSumsqScratch float2 of device memory)
+// sums of squares of the three grids [3][N0][N1][N2] into sumsq[3]
+// (deterministic; scratch: kSumsqScratch float2 of device memory), copying
+// the grids to out when it is not null
 constexpr int kSumsqScratch = 3 * 256;
-cudaError_t launch_sumsq(const float *g, long long vol, float *out, float2 *scratch, cudaStream_t st);
+cudaError_t launch_sumsq(const float *g, const int N[3], float *out, float *sumsq, float2 *scratch, cudaStream_t st);
 cudaError_t launch_crop(const float *grid, const int N[3], const int c0[3], const int e[3], const int E[3],
                         float *out, float *sumsq, float2 *scratch, cudaStream_t st);
 cudaError_t launch_occ_table(const unsigned char *occ, int N0, int N1, int N2, int W, uint32_t *tab,

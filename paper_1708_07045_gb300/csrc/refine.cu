@@ -311,51 +311,5 @@ cudaError_t launch_refine(const RefineArgs &a, int batch, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Sum of squares of each of the three grids (FP32 error bound), in float
-// pairs and in a fixed order, so that the bound, and with it the set of
-// refined translations, is the same on every run: CTA b of channel t sums a
-// contiguous slice into part[t][b]; k_sumsq_final adds the slices in order.
-constexpr int kSumsqBlocks = kSumsqScratch / 3;
-
-__global__ void __launch_bounds__(256) k_sumsq(const float *g, long long vol, float2 *part) {
-  __shared__ float s_h[256], s_l[256];
-  const int t = blockIdx.y, b = blockIdx.x;
-  const long long chunk = (vol + gridDim.x - 1) / gridDim.x;
-  const long long i0 = b * chunk, i1 = i0 + chunk < vol ? i0 + chunk : vol;
-  ff acc{0.f, 0.f};
-  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const float v = g[(long long)t * vol + i];
-    acc = s_norm(s_add(acc, s_mul(ff{v, 0.f}, ff{v, 0.f})));
-  }
-  s_h[threadIdx.x] = acc.hi;
-  s_l[threadIdx.x] = acc.lo;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      const ff r = s_norm(s_add(ff{s_h[threadIdx.x], s_l[threadIdx.x]}, ff{s_h[threadIdx.x + o], s_l[threadIdx.x + o]}));
-      s_h[threadIdx.x] = r.hi;
-      s_l[threadIdx.x] = r.lo;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[t * gridDim.x + b] = make_float2(s_h[0], s_l[0]);
-}
-
-__global__ void k_sumsq_final(const float2 *part, int nb, float *out) {
-  const int t = threadIdx.x;
-  if (t >= 3) return;
-  ff acc{0.f, 0.f};
-  for (int b = 0; b < nb; ++b) acc = s_norm(s_add(acc, ff{part[t * nb + b].x, part[t * nb + b].y}));
-  out[t] = __fadd_rn(acc.hi, acc.lo);
-}
-
-cudaError_t launch_sumsq(const float *g, long long vol, float *out, float2 *scratch, cudaStream_t st) {
-  if (vol <= 0) return cudaMemsetAsync(out, 0, 3 * sizeof(float), st);
-  k_sumsq<<<dim3(kSumsqBlocks, 3), 256, 0, st>>>(g, vol, scratch);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_sumsq_final<<<1, 32, 0, st>>>(scratch, kSumsqBlocks, out);
-  return cudaGetLastError();
-}
 
 }  // namespace bpmf
