@@ -348,9 +348,10 @@ int bpmf_set_refine_list_cap(bpmf_ctx_t ctx, int cap);
 int bpmf_set_wait_test(bpmf_ctx_t ctx, int on);
 
 /* Upper bound on the device workspace bpmf_eval may hold (bytes, default
- * 3 GiB); configurations are processed in batches that fit.  Results do not
- * depend on the batch size (every step is deterministic).  Errors:
- * INVALID_ARG (bytes < 1 MiB). */
+ * an eighth of the device's memory, at most 16 GiB and at least 1 GiB);
+ * configurations are processed in batches that fit, and fewer, larger
+ * batches run faster.  Results do not depend on the batch size (every step
+ * is deterministic).  Errors: INVALID_ARG (bytes < 1 MiB). */
 int bpmf_set_workspace_limit(bpmf_ctx_t ctx, size_t bytes);
 
 /*

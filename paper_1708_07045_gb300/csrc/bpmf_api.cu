@@ -109,7 +109,7 @@ struct bpmf_ctx {
   const __nv_bfloat16 *tc05 = nullptr;  // the same stage's matrix in the tcgen05 layout
   void *ws = nullptr;          // grow-only device workspace
   size_t ws_bytes = 0;
-  size_t ws_budget = size_t(3) << 30;
+  size_t ws_budget = size_t(3) << 30;  // set by bpmf_create from the device's memory
   unsigned long long next_id = 1;  // handle identities (graph cache keys)
   void *pinned = nullptr;          // pinned host staging of the eval tables
   size_t pinned_bytes = 0;
@@ -1027,6 +1027,13 @@ int bpmf_create(int device, bpmf_ctx_t *out) {
     delete c;
     return BPMF_ERR_CUDA;
   }
+  // workspace budget: an eighth of the device's memory, at most 16 GiB and at
+  // least 1 GiB (larger batches mean fewer, fuller launches)
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+    c->ws_budget = std::min(size_t(16) << 30, std::max(size_t(1) << 30, total_b / 8));
+  else
+    cudaGetLastError();
   *out = c;
   return BPMF_OK;
 }
