@@ -23,7 +23,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(_ROOT, "include")
 LIB_PATH = os.path.join(_HERE, "libbpmf.so")
 _SOURCES = ["kernels.cu", "xpass.cu", "yzinv.cu", "ligspec.cu", "occupancy.cu", "refine.cu", "bpmf_api.cu", "bpmf_static.cu", "proposal.cu", "bpmf_proposal.cu"]
-_HEADERS = ["arith.cuh", "fft.cuh", "kernels.cuh", "proposal.cuh", "tc_dft.cuh", "tc05.cuh"]
+_HEADERS = ["arith.cuh", "fft.cuh", "kernels.cuh", "proposal.cuh", "tc_dft.cuh", "tc05.cuh", "tma.cuh"]
 
 BPMF_OK = 0
 BPMF_ERR_INVALID_ARG = -1

@@ -43,6 +43,7 @@
 #include <tuple>
 
 #include "kernels.cuh"
+#include "tma.cuh"
 
 namespace bpmf {
 
@@ -63,41 +64,6 @@ __device__ __forceinline__ void cp16(void *dst, const void *src, bool valid) {
                : "memory");
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// ---- TMA tensor copies and their mbarrier ------------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-// one 3D tile of a tensor map into shared memory; the mbarrier expects its bytes
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
-                                            unsigned long long *bar, unsigned bytes) {
-  // the buffer was last read by ordinary loads: order them before the async-proxy write
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
-          "r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-// Wait for the mbarrier phase with the given parity, for `limit` SM cycles at
-// most (2^31, about a second, in normal use); false when the time ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit) {
-  const long long t0 = clock64();
-  while (true) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > limit) return false;
-  }
-}
 
 // One receptor's spectra for this CTA's 8 columns, all P frequencies and 3
 // channels, into RS[t][row][8] in the permuted row order of the forward

@@ -11,11 +11,8 @@
 //
 // One CTA per (configuration, receptor, site plane s0), 256 threads:
 //   y, unit (k2, g): rows k2 + R1 k1 (k1 < A1) of the x-pass plane [P1][F2],
-//      columns WY g .. WY g + WY - 1 (WY = 16 or 8 lanes; column 0 carries
-//      column P2 / 2 as its imaginary part: both are Hermitian along y after
-//      the x inverse, so their y inverses are real), read from global memory
-//      into registers; inverse A1-point DFT over k1, times conj(w_P1^(n1 k2))
-//      -> Y rows A1 k2 + n1;
+//      columns 16 g .. 16 g + 15, read from global memory into registers;
+//      inverse A1-point DFT over k1, times conj(w_P1^(n1 k2)) -> Y rows A1 k2 + n1;
 //   y, unit (n1, g): inverse R1-point DFT over k2 -> y rows n1 + A1 n2; the rows
 //      of the site window go to Zs[z frequency][s1];
 //   z, unit (k2, g), a quarter warp: lines l = 8 g .. 8 g + 7 are the row pairs (2 l,
@@ -53,13 +50,7 @@ template <int A1, int R1, int A2, int R2>
 __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   constexpr int P1 = A1 * R1, P2 = A2 * R2;
   constexpr int F2 = P2 / 2 + 1;
-  // y lines: the columns 1 .. CY - 1, and column 0 packed with column CY as
-  // A + iB (after the x inverse both are Hermitian along y, so their y
-  // inverses are real: one complex transform gives both)
-  constexpr int CY = P2 / 2;
-  constexpr int WY = CY % 16 == 0 ? 16 : 8;  // lanes per y unit: the fewest idle lanes
-  constexpr int NG1 = (CY + WY - 1) / WY;    // line groups of the y transform
-  constexpr int YS = CY | 1;                 // row stride of Y: odd, so the units of a warp hit both bank halves
+  constexpr int NG1 = (F2 + 15) / 16;  // line groups of the y transform (columns)
   const int S1 = a.S1, S2 = a.S2;
   const int L = (S1 + 1) / 2;          // row pairs: lines of the z transform
   const int NGz = (L + 7) / 8;         // the z stages' units are 8 lanes (a quarter warp): few lines
@@ -90,56 +81,36 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   if (S1 & 1)  // the last row pair's second row is zero
     for (int f = tid; f < F2; f += kYzNT) Zs[f * ZST + S1] = cx<float>{0.f, 0.f};
   const int wy = imod_yz(inf.wc[1], P1), wz = imod_yz(inf.wc[2], P2);
-  __builtin_assume(wy >= 0 && wy < P1);
-  __builtin_assume(wz >= 0 && wz < P2);
   const cx<float> *plane = reinterpret_cast<const cx<float> *>(a.x2) + (long long)blockIdx.x * a.Qx;
   __syncthreads();
-  const int yu = WY == 16 ? hw : qw, yl = WY == 16 ? hl : ql;  // y unit and lane
   // y, first inverse stage: rows k2 + R k1 straight from global memory
-  for (int u = yu; u < R1 * NG1; u += kYzNT / WY) {
-    const int k2 = u % R1, c = (u / R1) * WY + yl;
-    __builtin_assume(k2 >= 0 && k2 < R1);
-    if (c < CY) {
+  for (int u = hw; u < R1 * NG1; u += kYzNT / 16) {
+    const int k2 = u % R1, c = (u / R1) * 16 + hl;
+    if (c < F2) {
       cx<float> v[A1];
 #pragma unroll
-      for (int k1 = 0; k1 < A1; ++k1) {
-        const cx<float> *row = plane + (k2 + R1 * k1) * F2;
-        v[k1] = row[c];
-        if (c == 0) {  // + i (column CY)
-          const cx<float> w = row[CY];
-          v[k1] = cx<float>{__fsub_rn(v[k1].re, w.im), __fadd_rn(v[k1].im, w.re)};
-        }
-      }
+      for (int k1 = 0; k1 < A1; ++k1) v[k1] = plane[(k2 + R1 * k1) * F2 + c];
       dft_small<float, A1>(v, true, tw1, P1);
 #pragma unroll
       for (int n1 = 1; n1 < A1; ++n1) v[n1] = c_mul(v[n1], tw_load<float>(tw1[n1 * k2], true));
 #pragma unroll
-      for (int n1 = 0; n1 < A1; ++n1) Y[(A1 * k2 + n1) * YS + c] = v[n1];
+      for (int n1 = 0; n1 < A1; ++n1) Y[(A1 * k2 + n1) * F2 + c] = v[n1];
     }
   }
   __syncthreads();
   // y, second inverse stage: the site window's rows into Zs[column][s1]
-  // (the packed line's real part is column 0's, its imaginary part column CY's)
-  for (int u = yu; u < A1 * NG1; u += kYzNT / WY) {
-    const int n1 = u % A1, c = (u / A1) * WY + yl;
-    __builtin_assume(n1 >= 0 && n1 < A1);
-    if (c < CY) {
+  for (int u = hw; u < A1 * NG1; u += kYzNT / 16) {
+    const int n1 = u % A1, c = (u / A1) * 16 + hl;
+    if (c < F2) {
       cx<float> v[R1];
 #pragma unroll
-      for (int k2 = 0; k2 < R1; ++k2) v[k2] = Y[(A1 * k2 + n1) * YS + c];
+      for (int k2 = 0; k2 < R1; ++k2) v[k2] = Y[(A1 * k2 + n1) * F2 + c];
       dft_small<float, R1>(v, true, tw1, P1);
 #pragma unroll
       for (int n2 = 0; n2 < R1; ++n2) {
         int s1 = n1 + A1 * n2 - wy;
         s1 += s1 < 0 ? P1 : 0;
-        if (s1 < S1) {
-          if (c == 0) {
-            Zs[s1] = cx<float>{v[n2].re, 0.f};
-            Zs[CY * ZST + s1] = cx<float>{v[n2].im, 0.f};
-          } else {
-            Zs[c * ZST + s1] = v[n2];
-          }
-        }
+        if (s1 < S1) Zs[c * ZST + s1] = v[n2];
       }
     }
   }
@@ -147,7 +118,6 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   // z, first inverse stage: row pairs as A + i B, Hermitian-extended
   for (int u = qw; u < R2 * NGz; u += kYzNT / 8) {
     const int k2 = u % R2, l = (u / R2) * 8 + ql;
-    __builtin_assume(k2 >= 0 && k2 < R2);  // most Hermitian-extension tests below fold
     if (l < L) {
       cx<float> v[A2];
 #pragma unroll
@@ -177,7 +147,6 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   float ext = refine ? CUDART_INF_F : -CUDART_INF_F;  // plane minimum of E (refined) or maximum of -E/kT
   for (int u = qw; u < A2 * NGz; u += kYzNT / 8) {
     const int n1 = u % A2, l = (u / A2) * 8 + ql;
-    __builtin_assume(n1 >= 0 && n1 < A2);
     if (l < L) {
       cx<float> v[R2];
 #pragma unroll
