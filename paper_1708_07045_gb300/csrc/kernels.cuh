@@ -305,6 +305,12 @@ template <class T> cudaError_t launch_xfused(const XfusedArgs &a, int batch, cud
 constexpr int kXpMaxMaps = 8;
 struct alignas(64) XpassMaps {
   CUtensorMap m[kXpMaxMaps];
+  // the ligand's y-z spectra [batch][3][U0][Q] float2 as FP32 with the
+  // dimensions (2Q, batch, 3, U0): a box of 8 columns x 2 configurations x 3
+  // channels x U0 rows lands in the x pass's forward buffer in its own row
+  // layout [row][channel][configuration][column]; lig_ok = 0 when not encoded
+  CUtensorMap lig;
+  int lig_ok;
 };
 bool xpass_supported(int P);
 // FP32 y + z inverse on compile-time edges P1 = P2 in {64, 72, 80, 96} (yzinv.cu)

@@ -45,6 +45,25 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
       : "memory");
 }
 
+// The arrival of one thread on the mbarrier, which then expects `bytes` of
+// copies (issued after it, by tma_issue_4d) before its phase completes.
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long *bar, unsigned bytes) {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// One 4D tile of a tensor map into shared memory, completing on the mbarrier
+// (whose expected bytes include it).
+__device__ __forceinline__ void tma_issue_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                             unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // A contiguous block of global memory into shared memory (bulk copy): both
 // addresses 16-byte aligned, bytes a multiple of 16 (below 2^20, the
 // mbarrier's transaction range); the mbarrier expects its bytes.

@@ -140,11 +140,14 @@ __global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
   constexpr int NLI = 16;                    // inverse lines: 2 configurations x 8 columns
   constexpr int kTile = 3 * P * kXpLW;       // complex values of one receptor tile
   constexpr unsigned kTileBytes = kTile * sizeof(cx<float>);
-  __shared__ alignas(8) unsigned long long s_bar[2];  // arrivals of the two receptor tiles (TMA)
+  // arrivals of the two receptor tiles and of the ligand rows (TMA)
+  __shared__ alignas(8) unsigned long long s_bar[3];
   extern __shared__ float4 smem[];
-  float4 *tw = smem;                                     // [P] exp(-2 pi i k / P)
+  // 128-byte aligned TMA destinations: the twiddles (16 P bytes, P a multiple
+  // of 8) and L (384 P bytes) keep RS aligned too
+  float4 *tw = reinterpret_cast<float4 *>((reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));  // [P]
   cx<float> *L = reinterpret_cast<cx<float> *>(tw + P);  // [P][48], then W [2][P][16]
-  cx<float> *RS = reinterpret_cast<cx<float> *>((reinterpret_cast<uintptr_t>(L + P * kXpNLF) + 127) & ~uintptr_t(127));
+  cx<float> *RS = L + P * kXpNLF;                        // [2][3][P][8]
   const int tid = threadIdx.x, hw = tid >> 4, hl = tid & 15;
   const int g = hl >> 3, l = hl & 7;
   const int nJG = (batch + kXpG - 1) / kXpG;
@@ -154,6 +157,17 @@ __global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
   const int j = j0 + g, q = q0 + l;
   const bool live = j < batch && q < Q;
   const long long limit = a.wait_test ? (1ll << 20) : (1ll << 31);
+  const bool lig_tma = maps.lig_ok != 0;
+  const int U0 = a.U0 < P ? a.U0 : P;
+  // the ligand's rows for this CTA straight into L, in its row layout: one
+  // box of the batch's U0 rows, issued at once (rows past a configuration's
+  // own extent are loaded but not read; waiting for the extents first, to
+  // load fewer rows, made the pass slower)
+  if (lig_tma && tid == 0) {
+    mbar_init(&s_bar[2], 1);
+    mbar_arrive_expect(&s_bar[2], 384u * (unsigned)a.U0);
+    tma_issue_4d(L, &maps.lig, 2 * q0, j0, 0, 0, &s_bar[2]);
+  }
   for (int i = tid; i < P; i += NT) tw[i] = a.tw[i];
   // the first two receptors' spectra, asynchronously, while the ligand's are transformed
   if constexpr (TMA) {
@@ -168,19 +182,36 @@ __global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
     if (K > 1) stage_receptor<P, NT>(RS + kTile, a.rhi[1], Q, q0);
   }
   __syncthreads();
-  // forward A: unit (n1, t), R-point DFT over n2 of rows n1 + 8 n2 read
-  // straight from the ligand's y-z spectra (rows at or beyond the
-  // configuration's box extent u0 are zero and not read), twiddled, into L
+  // forward A: unit (n1, t), R-point DFT over n2 of rows n1 + 8 n2 of the
+  // ligand's y-z spectra (rows at or beyond the configuration's box extent u0
+  // are zero and not read), twiddled, into L: from the rows staged in L
+  // (in place: a unit writes the rows it read), else straight from global
+  // memory
   {
-    const int U0 = a.U0 < P ? a.U0 : P;
     const int u0 = live ? min(a.meta ? a.meta[j].u[0] : U0, U0) : 0;
     const cx<float> *ly = reinterpret_cast<const cx<float> *>(a.ly);
+    if (lig_tma) {
+      const bool ok = mbar_wait(&s_bar[2], 0, limit);
+      if (__syncthreads_or(!ok)) {  // the CTA agrees, waits (bounded) for its copies in flight and returns
+        if (tid == 0 && a.err) atomicOr(a.err, 1);
+        mbar_wait(&s_bar[2], 0, limit);
+        if constexpr (TMA) {
+          if (K > 0 && !a.wait_test) mbar_wait(&s_bar[0], 0, limit);
+          if (K > 1) mbar_wait(&s_bar[1], 0, limit);
+        } else {
+          cp_wait_all();
+        }
+        return;
+      }
+    }
     for (int u = hw; u < 8 * 3; u += R) {
       const int n1 = u & 7, t = u >> 3;
       const cx<float> *src = ly + (((long long)j * 3 + t) * a.U0 + n1) * Q + q;
+      const cx<float> *stg = L + n1 * kXpNLF + t * 16 + hl;
       cx<float> v[R];
 #pragma unroll
-      for (int n2 = 0; n2 < R; ++n2) v[n2] = n1 + 8 * n2 < u0 ? src[(long long)8 * n2 * Q] : cx<float>{0.f, 0.f};
+      for (int n2 = 0; n2 < R; ++n2)
+        v[n2] = n1 + 8 * n2 < u0 ? (lig_tma ? stg[8 * n2 * kXpNLF] : src[(long long)8 * n2 * Q]) : cx<float>{0.f, 0.f};
       dft_small<float, R>(v, false, tw, P);
 #pragma unroll
       for (int k2 = 1; k2 < R; ++k2) v[k2] = c_mul(v[k2], tw_load<float>(tw[n1 * k2], false));
@@ -303,6 +334,22 @@ using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
 std::mutex g_map_mu;
 std::map<std::tuple<const void *, int, long long>, CUtensorMap> g_maps;
 
+// the driver's tensor-map encoder (null when unavailable); call under g_map_mu
+EncodeTiled tiled_encoder() {
+  static EncodeTiled encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    encode = reinterpret_cast<EncodeTiled>(fn);
+  }
+  return encode;
+}
+
 bool receptor_map(const float2 *spec, int P, long long Q, CUtensorMap *out) {
   std::lock_guard<std::mutex> lk(g_map_mu);
   const auto key = std::make_tuple((const void *)spec, P, Q);
@@ -311,17 +358,8 @@ bool receptor_map(const float2 *spec, int P, long long Q, CUtensorMap *out) {
     *out = it->second;
     return true;
   }
-  static EncodeTiled encode = nullptr;
-  if (!encode) {
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-      cudaGetLastError();
-      return false;
-    }
-    encode = reinterpret_cast<EncodeTiled>(fn);
-  }
+  const EncodeTiled encode = tiled_encoder();
+  if (!encode) return false;
   alignas(64) CUtensorMap m;
   const cuuint64_t dims[3] = {(cuuint64_t)(2 * Q), (cuuint64_t)P, 3};
   const cuuint64_t strides[2] = {(cuuint64_t)(2 * Q * sizeof(float)), (cuuint64_t)(2 * Q * sizeof(float) * P)};
@@ -336,11 +374,33 @@ bool receptor_map(const float2 *spec, int P, long long Q, CUtensorMap *out) {
   return true;
 }
 
+// Tensor map of the ligand's y-z spectra ly [batch][3][U0][Q] float2 as FP32
+// with dimensions (2Q, batch, 3, U0) and box (16 floats, 2, 3, U0): one CTA's
+// rows in the forward buffer's layout [row][channel][configuration][column]
+// (out-of-range configurations and columns read as zeros).  Needs two
+// configurations, a 16-byte aligned ly and Q even.
+bool ligand_map(const void *ly, long long Q, int U0, int batch, CUtensorMap *out) {
+  if (batch < 2 || U0 < 1 || U0 > 256 || (Q & 1) || (reinterpret_cast<unsigned long long>(ly) & 15ull)) return false;
+  std::lock_guard<std::mutex> lk(g_map_mu);
+  const EncodeTiled encode = tiled_encoder();
+  if (!encode) return false;
+  const cuuint64_t row = (cuuint64_t)(2 * Q * sizeof(float));
+  const cuuint64_t dims[4] = {(cuuint64_t)(2 * Q), (cuuint64_t)batch, 3, (cuuint64_t)U0};
+  const cuuint64_t strides[3] = {row * 3 * U0, row * U0, row};
+  const cuuint32_t box[4] = {2 * kXpLW, (cuuint32_t)kXpG, 3, (cuuint32_t)U0};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(ly), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int P>
 cudaError_t launch_xpass_p(const XfusedArgs &a, int batch, cudaStream_t st) {
   const size_t smem = xpass_smem<P>();
   const long long blocks = (long long)((batch + kXpG - 1) / kXpG) * ((a.Q + kXpLW - 1) / kXpLW);
   XpassMaps maps;
+  // the ligand rows of a CTA (384 U0 bytes) fit the forward buffer (384 P)
+  maps.lig_ok = a.U0 <= P && ligand_map(a.ly, a.Q, a.U0, batch, &maps.lig) ? 1 : 0;
   bool tma = a.rhi_h && a.K <= kXpMaxMaps;
   for (int k = 0; tma && k < a.K; ++k) {
     // 16-byte aligned spectra whose rows are 16-byte multiples (Q even)
