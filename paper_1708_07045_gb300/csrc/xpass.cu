@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
     const cx<float> *rs0 = RS + b * kTile;
     cx<float> *Wb = L + b * P * NLI;
     const int wm = live ? imod_p(a.info[j * K + k].wc[0], P) : 0;  // window start along x, mod P
+    __builtin_assume(wm >= 0 && wm < P);
     bool ok = true;
     if constexpr (TMA) ok = mbar_wait(&s_bar[b], (k >> 1) & 1, limit);
     // product and inverse B', unit k2: P_f = sum_t R_{f,t} conj(L_t) at the
@@ -250,8 +251,18 @@ __global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
       for (int k1 = 0; k1 < 8; ++k1) {
         // TMA tiles hold natural frequency order, the cp.async tiles row order
         const cx<float> *rs = rs0 + (TMA ? k2 + R * k1 : 8 * k2 + k1) * kXpLW + l;
-        v[k1] = c_add(c_add(c_mulconj(rs[0], Lr[0][k1]), c_mulconj(rs[P * kXpLW], Lr[1][k1])),
-                      c_mulconj(rs[2 * P * kXpLW], Lr[2][k1]));
+        const cx<float> r0 = rs[0], r1 = rs[P * kXpLW], r2 = rs[2 * P * kXpLW];
+        // sum_t R_t conj(L_t) as one fused multiply-add chain per part
+        v[k1].re = __fmaf_rn(r0.re, Lr[0][k1].re,
+                             __fmaf_rn(r0.im, Lr[0][k1].im,
+                                       __fmaf_rn(r1.re, Lr[1][k1].re,
+                                                 __fmaf_rn(r1.im, Lr[1][k1].im,
+                                                           __fmaf_rn(r2.re, Lr[2][k1].re, __fmul_rn(r2.im, Lr[2][k1].im))))));
+        v[k1].im = __fmaf_rn(r0.im, Lr[0][k1].re,
+                             __fmaf_rn(-r0.re, Lr[0][k1].im,
+                                       __fmaf_rn(r1.im, Lr[1][k1].re,
+                                                 __fmaf_rn(-r1.re, Lr[1][k1].im,
+                                                           __fmaf_rn(r2.im, Lr[2][k1].re, -__fmul_rn(r2.re, Lr[2][k1].im))))));
       }
       dft_small<float, 8>(v, true, tw, P);
 #pragma unroll
