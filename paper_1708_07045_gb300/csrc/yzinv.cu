@@ -76,20 +76,35 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
     if (tid == 0) a.part[blockIdx.x] = make_float4(-CUDART_INF_F, 0.f, 0.f, 0.f);
     return;
   }
+  const cx<float> *plane = reinterpret_cast<const cx<float> *>(a.x2) + (long long)blockIdx.x * a.Qx;
+  // the first y unit's rows are requested before the twiddle copies, so the
+  // two global-memory latencies overlap
+  cx<float> v0[A1];
+  {
+    const int k2 = hw % R1, c = (hw / R1) * 16 + hl;
+    if (hw < R1 * NG1 && c < F2) {
+#pragma unroll
+      for (int k1 = 0; k1 < A1; ++k1) v0[k1] = plane[(k2 + R1 * k1) * F2 + c];
+    }
+  }
   for (int i = tid; i < P1; i += kYzNT) tw1[i] = a.tw1[i];
   for (int i = tid; i < P2; i += kYzNT) tw2[i] = a.tw[i];
   if (S1 & 1)  // the last row pair's second row is zero
     for (int f = tid; f < F2; f += kYzNT) Zs[f * ZST + S1] = cx<float>{0.f, 0.f};
   const int wy = imod_yz(inf.wc[1], P1), wz = imod_yz(inf.wc[2], P2);
-  const cx<float> *plane = reinterpret_cast<const cx<float> *>(a.x2) + (long long)blockIdx.x * a.Qx;
   __syncthreads();
   // y, first inverse stage: rows k2 + R k1 straight from global memory
   for (int u = hw; u < R1 * NG1; u += kYzNT / 16) {
     const int k2 = u % R1, c = (u / R1) * 16 + hl;
     if (c < F2) {
       cx<float> v[A1];
+      if (u == hw) {
 #pragma unroll
-      for (int k1 = 0; k1 < A1; ++k1) v[k1] = plane[(k2 + R1 * k1) * F2 + c];
+        for (int k1 = 0; k1 < A1; ++k1) v[k1] = v0[k1];
+      } else {
+#pragma unroll
+        for (int k1 = 0; k1 < A1; ++k1) v[k1] = plane[(k2 + R1 * k1) * F2 + c];
+      }
       dft_small<float, A1>(v, true, tw1, P1);
 #pragma unroll
       for (int n1 = 1; n1 < A1; ++n1) v[n1] = c_mul(v[n1], tw_load<float>(tw1[n1 * k2], true));
