@@ -171,6 +171,20 @@ struct bpmf_rec {
   };
   std::map<std::array<int, 3>, Crop> crops;
   cudaEvent_t crop_ev = nullptr;        // recorded after the last crop was made (on the stream that made it)
+  // Float-pair partial spectra the crops start from (a crop along one axis
+  // commutes with the transforms along the others): the z spectra
+  // [3][N0][N1][Pz/2+1] of the grids with z cropped to edge Pz (key Pz), and
+  // their y spectra [3][N0][Py (Pz/2+1)] with y cropped to edge Py (key
+  // (Py, Pz)); the uncropped ones are the load's own intermediates.  ev is
+  // recorded on the stream that made the stage.
+  struct Stage {
+    void *mem = nullptr;
+    size_t mem_bytes = 0;
+    void *v = nullptr;  // cx<ff>
+    cudaEvent_t ev = nullptr;
+  };
+  std::map<int, Stage> zst;
+  std::map<std::pair<int, int>, Stage> yst;
 };
 
 struct bpmf_lig {
@@ -1066,83 +1080,123 @@ void bpmf_destroy(bpmf_ctx_t c) {
 
 namespace {
 
-// Spectra of nrec receptors' three grids, src [nrec][3][e0][e1][e2]
-// zero-padded to transform edges P (Eq. fft_correlation_func, receptor side):
-// z R2C, then y and x C2C, in float pairs, split into each receptor's hi / lo
-// planes [3][P0][P1 (P2/2+1)].
-void grid_spectrum(bpmf_ctx *c, const float *src, int nrec, const int e[3], const int P[3], float2 *const *hi,
-                   float2 *const *lo, cudaStream_t st) {
-  const int F2 = P[2] / 2 + 1;
-  const long long Q = (long long)P[1] * F2;
-  const long long nch = 3ll * nrec;
-  const size_t E = sizeof(cx<ff>);
-  void *tz = nullptr, *ty = nullptr, *tx = nullptr;
+// Float-pair receptor passes (Eq. fft_correlation_func's FT(G_R)), used by
+// the loads and the crops.  z: R2C of `rows` rows of w_in floats (stride
+// in_stride, zero beyond w_in) on edge Pz -> out [rows][Pz/2+1].
+void rz_pass(bpmf_ctx *c, const float *in, long long rows, int w_in, long long in_stride, int Pz, void *out,
+             cudaStream_t st) {
+  ZfwdArgs za{};
+  za.in = in;
+  za.n_rows = rows;
+  za.w_in = w_in;
+  za.in_stride = in_stride;
+  za.out = out;
+  za.out_stride = Pz / 2 + 1;
+  za.plan = make_plan(Pz);
+  za.tw = twiddles(c, Pz);
+  za.L = 16;
+  launch(c, "k_zfwd<ff>(receptor)", st, [&] { return launch_zfwd<ff>(za, st); });
+}
+
+// y (axis 1) or x (axis 0): C2C on edge Pd of n_outer x inner columns whose
+// n_in inputs lie `inner` apart (zero beyond n_in), outer blocks in_os apart
+// -> out [n_outer][Pd][inner].
+void rax_pass(bpmf_ctx *c, const void *in, int n_in, int Pd, long long n_outer, long long inner, long long in_os,
+              void *out, int axis, cudaStream_t st) {
+  AxisArgs ax{};
+  ax.in = in;
+  ax.out = out;
+  ax.P = Pd;
+  ax.n_in = n_in;
+  ax.n_out = Pd;
+  ax.n_outer = n_outer;
+  ax.inner = inner;
+  ax.in_os = in_os;
+  ax.out_os = (long long)Pd * inner;
+  ax.w0_div = 1;
+  ax.axis = axis;
+  ax.plan = make_plan(Pd);
+  ax.tw = twiddles(c, Pd);
+  ax.LW = 16;
+  launch(c, axis == 1 ? "k_axis<ff>(receptor y)" : "k_axis<ff>(receptor x)", st,
+         [&] { return launch_axis<ff>(ax, st); });
+}
+
+// The x pass of a y stage [3][N0][Q] over its rows [x0, x0 + n_in) on edge
+// Px, split into the spectrum's hi / lo planes [3][Px][Q].
+void rx_split(bpmf_ctx *c, const void *ystage, int N0, int x0, int n_in, int Px, long long Q, float2 *hi, float2 *lo,
+              cudaStream_t st) {
+  void *tx = nullptr;
   try {
-    CK(cudaMallocAsync(&tz, nch * e[0] * e[1] * F2 * E, st));
-    CK(cudaMallocAsync(&ty, nch * e[0] * Q * E, st));
-    CK(cudaMallocAsync(&tx, nch * P[0] * Q * E, st));
-    // z: R2C of every (channel, x, y) row
-    ZfwdArgs za{};
-    za.in = src;
-    za.n_rows = nch * e[0] * e[1];
-    za.w_in = e[2];
-    za.in_stride = e[2];
-    za.out = tz;
-    za.out_stride = F2;
-    za.plan = make_plan(P[2]);
-    za.tw = twiddles(c, P[2]);
-    za.L = 16;
-    launch(c, "k_zfwd<ff>(receptor)", st, [&] { return launch_zfwd<ff>(za, st); });
-    // y
-    AxisArgs ya{};
-    ya.in = tz;
-    ya.out = ty;
-    ya.P = P[1];
-    ya.n_in = e[1];
-    ya.n_out = P[1];
-    ya.n_outer = nch * e[0];
-    ya.inner = F2;
-    ya.in_os = (long long)e[1] * F2;
-    ya.out_os = Q;
-    ya.w0_div = 1;
-    ya.axis = 1;
-    ya.plan = make_plan(P[1]);
-    ya.tw = twiddles(c, P[1]);
-    ya.LW = 16;
-    launch(c, "k_axis<ff>(receptor y)", st, [&] { return launch_axis<ff>(ya, st); });
-    // x
-    AxisArgs xa{};
-    xa.in = ty;
-    xa.out = tx;
-    xa.P = P[0];
-    xa.n_in = e[0];
-    xa.n_out = P[0];
-    xa.n_outer = nch;
-    xa.inner = Q;
-    xa.in_os = (long long)e[0] * Q;
-    xa.out_os = (long long)P[0] * Q;
-    xa.w0_div = 1;
-    xa.axis = 0;
-    xa.plan = make_plan(P[0]);
-    xa.tw = twiddles(c, P[0]);
-    xa.LW = 16;
-    launch(c, "k_axis<ff>(receptor x)", st, [&] { return launch_axis<ff>(xa, st); });
-    for (int m = 0; m < nrec; ++m) {
-      const cx<ff> *spec = static_cast<const cx<ff> *>(tx) + 3ll * m * P[0] * Q;
-      launch(c, "k_split_ff", st, [&] { return launch_split_ff(spec, hi[m], lo[m], 3ll * P[0] * Q, st); });
-    }
-    CK(cudaFreeAsync(tz, st));
-    tz = nullptr;
-    CK(cudaFreeAsync(ty, st));
-    ty = nullptr;
+    CK(cudaMallocAsync(&tx, 3ull * Px * Q * sizeof(cx<ff>), st));
+    rax_pass(c, static_cast<const cx<ff> *>(ystage) + (long long)x0 * Q, n_in, Px, 3, Q, (long long)N0 * Q, tx, 0, st);
+    launch(c, "k_split_ff", st, [&] { return launch_split_ff(tx, hi, lo, 3ll * Px * Q, st); });
     CK(cudaFreeAsync(tx, st));
-    tx = nullptr;
   } catch (Fail) {
-    if (tz) cudaFreeAsync(tz, st);
-    if (ty) cudaFreeAsync(ty, st);
     if (tx) cudaFreeAsync(tx, st);
     throw;
   }
+}
+
+// A stage of a receptor (made on `st` and recorded there), in blocks of the
+// context's cache.
+bpmf_rec::Stage new_stage(bpmf_ctx *c, size_t bytes) {
+  bpmf_rec::Stage sg;
+  Carve cv;
+  cv.add(&sg.v, bytes);
+  sg.mem = cv.alloc(c);
+  sg.mem_bytes = cv.total;
+  return sg;
+}
+void record_stage(bpmf_rec::Stage &sg, cudaStream_t st) {
+  if (!sg.ev) CK(cudaEventCreateWithFlags(&sg.ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(sg.ev, st));
+}
+
+// The z stage of receptor r for the z edge Pz (the crop along z starts at z0
+// with ez nodes), made on st if new; st is ordered after it.
+const bpmf_rec::Stage &z_stage(bpmf_ctx *c, bpmf_rec *r, int Pz, int z0, int ez, cudaStream_t st) {
+  auto it = r->zst.find(Pz);
+  if (it != r->zst.end()) {
+    CK(cudaStreamWaitEvent(st, it->second.ev, 0));
+    return it->second;
+  }
+  const long long rows = 3ll * r->N[0] * r->N[1];
+  bpmf_rec::Stage sg = new_stage(c, rows * (Pz / 2 + 1) * sizeof(cx<ff>));
+  try {
+    rz_pass(c, r->grid + z0, rows, ez, r->N[2], Pz, sg.v, st);
+    record_stage(sg, st);
+  } catch (Fail) {
+    cudaFree(sg.mem);
+    if (sg.ev) cudaEventDestroy(sg.ev);
+    throw;
+  }
+  return r->zst[Pz] = sg;
+}
+
+// The y stage of receptor r for the edges (Py, Pz): the y pass of its z stage
+// with y cropped to [y0, y0 + ey), made on st if new; st is ordered after it.
+const bpmf_rec::Stage &y_stage(bpmf_ctx *c, bpmf_rec *r, int Py, int y0, int ey, int Pz, int z0, int ez,
+                               cudaStream_t st) {
+  const auto key = std::make_pair(Py, Pz);
+  auto it = r->yst.find(key);
+  if (it != r->yst.end()) {
+    CK(cudaStreamWaitEvent(st, it->second.ev, 0));
+    return it->second;
+  }
+  const bpmf_rec::Stage &zs = z_stage(c, r, Pz, z0, ez, st);
+  const long long Fz = Pz / 2 + 1;
+  bpmf_rec::Stage sg = new_stage(c, 3ull * r->N[0] * Py * Fz * sizeof(cx<ff>));
+  try {
+    rax_pass(c, static_cast<const cx<ff> *>(zs.v) + (long long)y0 * Fz, ey, Py, 3ll * r->N[0], Fz,
+             (long long)r->N[1] * Fz, sg.v, 1, st);
+    record_stage(sg, st);
+  } catch (Fail) {
+    cudaFree(sg.mem);
+    if (sg.ev) cudaEventDestroy(sg.ev);
+    throw;
+  }
+  return r->yst[key] = sg;
 }
 
 int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -1157,10 +1211,14 @@ int crop_start(int N, int site_lo, int site_n, int Pc) {
 
 // Views of receptors' spectra for transform edges Pc <= P: the stored one of
 // a receptor when Pc == P, else its grids cropped to Pc nodes per axis around
-// the site.  Crops made on first use are transformed together, on one of the
-// library's side streams after the event `fork` of the caller's stream; the
-// event recorded when they are done is appended to `joins` (the caller's
-// stream waits for it) and the receptors made to `touched`.
+// the site.  Crops made on first use run on one of the library's side
+// streams after the event `fork` of the caller's stream; the event recorded
+// when they are done is appended to `joins` (the caller's stream waits for
+// it) and the receptors made to `touched`.  A crop's spectrum is the x pass,
+// over the crop's x rows, of the receptor's y stage for (Pc1, Pc2) (the y
+// pass, over the crop's y rows, of its z stage for Pc2, the z pass over the
+// crop's z nodes): cropping along one axis commutes with the transforms
+// along the others, so crops that share edges share stages.
 // Every node that a translation of the site window reaches with a ligand box
 // of edge u lies in the crop when Pc >= site_n + u - 1: the crop starts
 // floor((site_n - Pc) / 2) nodes from the site, moved inside the grid.
@@ -1171,7 +1229,6 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
   std::vector<size_t> todo;
   std::vector<std::array<int, 3>> ext;
   std::vector<int> alias(rs.size(), -1);  // a receptor passed more than once
-  int Emax[3] = {1, 1, 1};
   for (size_t m = 0; m < rs.size(); ++m) {
     bpmf_rec *r = rs[m];
     for (size_t m2 = 0; m2 < m && alias[m] < 0; ++m2)
@@ -1193,7 +1250,6 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
     for (int d = 0; d < 3; ++d) {
       out[m].c0[d] = crop_start(r->N[d], r->site_lo[d], r->site_n[d], Pc[d]);
       e[d] = std::min(Pc[d], r->N[d] - out[m].c0[d]);
-      Emax[d] = std::max(Emax[d], e[d]);
     }
     out[m].vol = (double)e[0] * e[1] * e[2];
     todo.push_back(m);
@@ -1209,13 +1265,10 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
   }
   const int n = (int)todo.size();
   const long long Q = (long long)Pc[1] * (Pc[2] / 2 + 1);
-  const long long chan = (long long)Emax[0] * Emax[1] * Emax[2];
   cudaStream_t &cs_slot = c->side[c->side_next++ % bpmf_ctx::kSide];
   if (!cs_slot) CK(cudaStreamCreateWithFlags(&cs_slot, cudaStreamNonBlocking));
   const cudaStream_t st = cs_slot;
   CK(cudaStreamWaitEvent(st, fork, 0));
-  float *buf = nullptr;
-  std::vector<float2 *> his(n, nullptr), los(n, nullptr);
   try {
     for (int i = 0; i < n; ++i) {
       bpmf_rec::Crop &cr = out[todo[i]];
@@ -1226,24 +1279,20 @@ std::vector<bpmf_rec::Crop> rec_crops(bpmf_ctx *c, const std::vector<bpmf_rec *>
       cv.add(&cr.sumsq_scratch, kSumsqScratch * sizeof(float2));
       cr.mem = cv.alloc(c);
       cr.mem_bytes = cv.total;
-      his[i] = cr.hi;
-      los[i] = cr.lo;
     }
-    CK(cudaMallocAsync(&buf, 3ull * n * chan * sizeof(float), st));
+    // per receptor: the sums of squares over the crop, then the x pass of
+    // the y stage for (Pc1, Pc2) over the crop's x rows (the stages are made
+    // once per receptor and edge pair and shared by the crops that use them)
     for (int i = 0; i < n; ++i) {
       bpmf_rec *r = rs[todo[i]];
       bpmf_rec::Crop &cr = out[todo[i]];
       const int e[3] = {ext[i][0], ext[i][1], ext[i][2]};
-      float *dst = buf + 3ll * i * chan;
       launch(c, "k_crop", st,
-             [&] { return launch_crop(r->grid, r->N, cr.c0, e, Emax, dst, cr.sumsq, cr.sumsq_scratch, st); });
+             [&] { return launch_crop(r->grid, r->N, cr.c0, e, e, nullptr, cr.sumsq, cr.sumsq_scratch, st); });
+      const bpmf_rec::Stage &ys = y_stage(c, r, Pc[1], cr.c0[1], e[1], Pc[2], cr.c0[2], e[2], st);
+      rx_split(c, ys.v, r->N[0], cr.c0[0], e[0], Pc[0], Q, cr.hi, cr.lo, st);
     }
-    const int P3[3] = {Pc[0], Pc[1], Pc[2]};
-    grid_spectrum(c, buf, n, Emax, P3, his.data(), los.data(), st);
-    CK(cudaFreeAsync(buf, st));
-    buf = nullptr;
   } catch (Fail) {
-    if (buf) cudaFreeAsync(buf, st);
     cudaStreamSynchronize(st);
     for (int i = 0; i < n; ++i)
       if (out[todo[i]].mem) cudaFree(out[todo[i]].mem);
@@ -1325,7 +1374,21 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
     launch(c, "k_sumsq", st, [&] {
       return launch_sumsq(static_cast<const float *>(g.p), N, r->grid, r->sumsq, r->sumsq_scratch, st);
     });
-    grid_spectrum(c, static_cast<const float *>(g.p), 1, N, P, &r->hi, &r->lo, st);
+    // the float-pair spectrum, z then y then x; the z and y stages are kept
+    // for the crops (the uncropped stages of every crop with a full z, or
+    // full y and z, edge)
+    {
+      const long long rows = 3ll * N[0] * N[1];
+      bpmf_rec::Stage zs = new_stage(c, rows * r->F2 * sizeof(cx<ff>));
+      r->zst[P[2]] = zs;
+      rz_pass(c, static_cast<const float *>(g.p), rows, N[2], N[2], P[2], zs.v, st);
+      record_stage(r->zst[P[2]], st);
+      bpmf_rec::Stage ys = new_stage(c, 3ull * N[0] * r->Q * sizeof(cx<ff>));
+      r->yst[std::make_pair(P[1], P[2])] = ys;
+      rax_pass(c, zs.v, N[1], P[1], 3ll * N[0], r->F2, (long long)N[1] * r->F2, ys.v, 1, st);
+      record_stage(r->yst[std::make_pair(P[1], P[2])], st);
+      rx_split(c, ys.v, N[0], 0, N[0], P[0], r->Q, r->hi, r->lo, st);
+    }
     if (!is_device_ptr(grids)) CK(cudaStreamSynchronize(st));
   } catch (Fail f) {
     bpmf_receptor_free(r);
@@ -1353,6 +1416,14 @@ void bpmf_receptor_free(bpmf_rec_t r) {
     if (r->occ) cudaFree(r->occ);
     if (r->crop_ev) cudaEventDestroy(r->crop_ev);
     for (auto &kv : r->crops) put(kv.second.mem, kv.second.mem_bytes);
+    for (auto &kv : r->zst) {
+      put(kv.second.mem, kv.second.mem_bytes);
+      if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+    }
+    for (auto &kv : r->yst) {
+      put(kv.second.mem, kv.second.mem_bytes);
+      if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+    }
   }
   delete r;
 }
