@@ -1102,8 +1102,10 @@ void rz_pass(bpmf_ctx *c, const float *in, long long rows, int w_in, long long i
 // n_in inputs lie `inner` apart (zero beyond n_in), outer blocks in_os apart
 // -> out [n_outer][Pd][inner].
 void rax_pass(bpmf_ctx *c, const void *in, int n_in, int Pd, long long n_outer, long long inner, long long in_os,
-              void *out, int axis, cudaStream_t st) {
+              void *out, int axis, cudaStream_t st, float2 *out_hi = nullptr, float2 *out_lo = nullptr) {
   AxisArgs ax{};
+  ax.out_hi = out_hi;
+  ax.out_lo = out_lo;
   ax.in = in;
   ax.out = out;
   ax.P = Pd;
@@ -1123,19 +1125,11 @@ void rax_pass(bpmf_ctx *c, const void *in, int n_in, int Pd, long long n_outer, 
 }
 
 // The x pass of a y stage [3][N0][Q] over its rows [x0, x0 + n_in) on edge
-// Px, split into the spectrum's hi / lo planes [3][Px][Q].
+// Px, written as the spectrum's hi / lo planes [3][Px][Q].
 void rx_split(bpmf_ctx *c, const void *ystage, int N0, int x0, int n_in, int Px, long long Q, float2 *hi, float2 *lo,
               cudaStream_t st) {
-  void *tx = nullptr;
-  try {
-    CK(cudaMallocAsync(&tx, 3ull * Px * Q * sizeof(cx<ff>), st));
-    rax_pass(c, static_cast<const cx<ff> *>(ystage) + (long long)x0 * Q, n_in, Px, 3, Q, (long long)N0 * Q, tx, 0, st);
-    launch(c, "k_split_ff", st, [&] { return launch_split_ff(tx, hi, lo, 3ll * Px * Q, st); });
-    CK(cudaFreeAsync(tx, st));
-  } catch (Fail) {
-    if (tx) cudaFreeAsync(tx, st);
-    throw;
-  }
+  rax_pass(c, static_cast<const cx<ff> *>(ystage) + (long long)x0 * Q, n_in, Px, 3, Q, (long long)N0 * Q, nullptr, 0,
+           st, hi, lo);
 }
 
 // A stage of a receptor (made on `st` and recorded there), in blocks of the

@@ -364,7 +364,17 @@ __global__ void __launch_bounds__(KCfg<T>::threads, KCfg<T>::a_min_blocks) k_axi
     const int s = idx / LW, l = idx % LW;
     const long long base = s_out[l];
     const int m = s_w0[l] + s;
-    if (base >= 0) st_cx<T>(a.out, base + s * a.inner, res[(m >= P ? m - P : m) * LW + l]);
+    if (base < 0) continue;
+    const cx<T> v = res[(m >= P ? m - P : m) * LW + l];
+    if constexpr (std::is_same<T, ff>::value) {
+      if (a.out_hi) {  // split into the hi / lo planes
+        const cx<ff> w = c_norm(v);
+        a.out_hi[base + s * a.inner] = make_float2(w.re.hi, w.im.hi);
+        a.out_lo[base + s * a.inner] = make_float2(w.re.lo, w.im.lo);
+        continue;
+      }
+    }
+    st_cx<T>(a.out, base + s * a.inner, v);
   }
 }
 

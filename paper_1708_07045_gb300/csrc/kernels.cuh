@@ -88,6 +88,9 @@ struct AxisArgs {          // C2C along a strided axis, pruned input / output
   FftPlan plan;
   const float4 *tw;
   int LW;
+  // float pairs: when set, the outputs go to these hi / lo planes (indexed
+  // like out) instead of out
+  float2 *out_hi, *out_lo;
 };
 
 struct XfusedArgs {        // x: forward ligand DFT, product with each receptor, inverse, window
