@@ -64,6 +64,12 @@ __device__ __forceinline__ void tma_issue_4d(void *dst, const CUtensorMap *map, 
       : "memory");
 }
 
+// A contiguous block of global memory prefetched into the L2 (bulk
+// prefetch; 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // A contiguous block of global memory into shared memory (bulk copy): both
 // addresses 16-byte aligned, bytes a multiple of 16 (below 2^20, the
 // mbarrier's transaction range); the mbarrier expects its bytes.

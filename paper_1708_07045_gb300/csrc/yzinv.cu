@@ -27,6 +27,7 @@
 #include <math_constants.h>
 
 #include "kernels.cuh"
+#include "tma.cuh"
 
 namespace bpmf {
 
@@ -49,6 +50,7 @@ __host__ __device__ __forceinline__ int yz_zst(int S1) {
 template <int A1, int R1, int A2, int R2>
 __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
   constexpr int P1 = A1 * R1, P2 = A2 * R2;
+  static_assert(P1 % 2 == 0, "a plane is a 16-byte multiple (bulk prefetch)");
   constexpr int F2 = P2 / 2 + 1;
   constexpr int NG1 = (F2 + 15) / 16;  // line groups of the y transform (columns)
   const int S1 = a.S1, S2 = a.S2;
@@ -77,6 +79,9 @@ __global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
     return;
   }
   const cx<float> *plane = reinterpret_cast<const cx<float> *>(a.x2) + (long long)blockIdx.x * a.Qx;
+  // the whole plane is prefetched into the L2 (P1 F2 complex values: 16-byte
+  // multiple, P1 even), so the first stage's later rounds hit it there
+  if (tid == 0) bulk_prefetch_l2(plane, (unsigned)(P1 * F2 * sizeof(cx<float>)));
   // the first y unit's rows are requested before the twiddle copies, so the
   // two global-memory latencies overlap
   cx<float> v0[A1];
