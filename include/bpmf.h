@@ -392,7 +392,7 @@ int bpmf_valid_counts(bpmf_ctx_t ctx, bpmf_lig_t lig, const bpmf_rec_t *recs, in
  * q_j = mix * softmax(pred / tau)_j + (1 - mix) / J, and the BPMF is estimated by
  * importance weighting, which stays unbiased for Z_k = sum_j S_jk thanks to
  * the uniform component.  The full enumeration (bpmf_eval) is the fallback and
- * the judge of its error.
+ * the reference for its error.
  * ------------------------------------------------------------------------ */
 #define BPMF_N_FEATURES 24
 
