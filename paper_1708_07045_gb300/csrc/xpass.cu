@@ -83,12 +83,15 @@ __device__ __forceinline__ void stage_receptor(cx<float> *RS, const float2 *rh, 
 
 // Launch shape of the x pass on edge P = 8 R: one half-warp per k2 (16 R
 // threads), and the CTAs per SM the registers are budgeted for (the shared
-// memory of P <= 96 fits three CTAs per SM, of P <= 72 four).
+// memory of P <= 80 fits four CTAs per SM, of P <= 96 three).
 template <int P>
 struct XpCfg {
   static constexpr int R = P / 8;
   static constexpr int NT = 16 * R;
-  static constexpr int MINB = P <= 72 ? 4 : (P <= 96 ? 3 : 2);
+  static constexpr int MINB = P <= 80 ? 4 : (P <= 96 ? 3 : 2);
+  // on 72 and 80 the second receptor tile lies over the forward buffer's
+  // last third (free once stage B has read it): four CTAs fit an SM
+  static constexpr bool kAliasT1 = P == 72 || P == 80;
   // the last inverse stage has 8 units (n1); with 16 half-warps two share one
   static constexpr bool kSplitA = R == 16;
 };
@@ -126,11 +129,12 @@ __device__ __forceinline__ void idft_half(const cx<float> *v, int h, const float
 
 // Shared memory of k_xpass<P>: the twiddles, the ligand spectra L [P][48]
 // (reused as the two inverse buffers W [2][P][16] once the forward transform
-// is done), two receptor tiles [2][3][P][8] (128-byte aligned TMA
-// destinations), and slack for that alignment.
+// is done), two receptor tiles [3][P][8] (128-byte aligned TMA destinations;
+// with kAliasT1 the second starts at L + 32 P, over L's last third, so the
+// region is 80 P complex values instead of 96 P), and slack for the alignment.
 template <int P>
 constexpr size_t xpass_smem_bytes() {
-  return sizeof(float4) * P + sizeof(cx<float>) * (size_t)P * (kXpNLF + 2 * 3 * kXpLW) + 128;
+  return sizeof(float4) * P + sizeof(cx<float>) * (size_t)P * (XpCfg<P>::kAliasT1 ? 80 : 96) + 128;
 }
 
 template <int P, bool TMA>
@@ -144,10 +148,13 @@ __global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
   __shared__ alignas(8) unsigned long long s_bar[3];
   extern __shared__ float4 smem[];
   // 128-byte aligned TMA destinations: the twiddles (16 P bytes, P a multiple
-  // of 8) and L (384 P bytes) keep RS aligned too
+  // of 8) and L (384 P bytes) keep the receptor tiles aligned too
   float4 *tw = reinterpret_cast<float4 *>((reinterpret_cast<uintptr_t>(smem) + 127) & ~uintptr_t(127));  // [P]
   cx<float> *L = reinterpret_cast<cx<float> *>(tw + P);  // [P][48], then W [2][P][16]
-  cx<float> *RS = L + P * kXpNLF;                        // [2][3][P][8]
+  constexpr bool kAlias = XpCfg<P>::kAliasT1;
+  // the receptor tiles [3][P][8]: T1 over L's last third (kAlias) or after T0
+  cx<float> *T0 = L + (kAlias ? 56 : 48) * P;
+  cx<float> *T1 = kAlias ? L + 32 * P : T0 + kTile;
   const int tid = threadIdx.x, hw = tid >> 4, hl = tid & 15;
   const int g = hl >> 3, l = hl & 7;
   const int nJG = (batch + kXpG - 1) / kXpG;
@@ -174,12 +181,12 @@ __global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
     if (tid == 0) {
       mbar_init(&s_bar[0], 1);
       mbar_init(&s_bar[1], 1);
-      if (K > 0 && !a.wait_test) tma_load_3d(RS, &maps.m[0], 2 * q0, 0, 0, &s_bar[0], kTileBytes);
-      if (K > 1) tma_load_3d(RS + kTile, &maps.m[1], 2 * q0, 0, 0, &s_bar[1], kTileBytes);
+      if (K > 0 && !a.wait_test) tma_load_3d(T0, &maps.m[0], 2 * q0, 0, 0, &s_bar[0], kTileBytes);
+      if (!kAlias && K > 1) tma_load_3d(T1, &maps.m[1], 2 * q0, 0, 0, &s_bar[1], kTileBytes);
     }
   } else {
-    if (K > 0) stage_receptor<P, NT>(RS, a.rhi[0], Q, q0);
-    if (K > 1) stage_receptor<P, NT>(RS + kTile, a.rhi[1], Q, q0);
+    if (K > 0) stage_receptor<P, NT>(T0, a.rhi[0], Q, q0);
+    if (!kAlias && K > 1) stage_receptor<P, NT>(T1, a.rhi[1], Q, q0);
   }
   __syncthreads();
   // forward A: unit (n1, t), R-point DFT over n2 of rows n1 + 8 n2 of the
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
         mbar_wait(&s_bar[2], 0, limit);
         if constexpr (TMA) {
           if (K > 0 && !a.wait_test) mbar_wait(&s_bar[0], 0, limit);
-          if (K > 1) mbar_wait(&s_bar[1], 0, limit);
+          if (!kAlias && K > 1) mbar_wait(&s_bar[1], 0, limit);
         } else {
           cp_wait_all();
         }
@@ -234,9 +241,20 @@ __global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
   }
   if constexpr (!TMA) cp_wait_all();
   __syncthreads();  // L is the inverse buffers W from here on
+  // kAlias: the second receptor's spectra into T1, now that L's last third
+  // has been read
+  if constexpr (kAlias) {
+    if (K > 1) {
+      if constexpr (TMA) {
+        if (tid == 0) tma_load_3d(T1, &maps.m[1], 2 * q0, 0, 0, &s_bar[1], kTileBytes);
+      } else {
+        stage_receptor<P, NT>(T1, a.rhi[1], Q, q0);
+      }
+    }
+  }
   for (int k = 0; k < K; ++k) {
     const int b = k & 1;
-    const cx<float> *rs0 = RS + b * kTile;
+    const cx<float> *rs0 = b ? T1 : T0;
     cx<float> *Wb = L + b * P * NLI;
     const int wm = live ? imod_p(a.info[j * K + k].wc[0], P) : 0;  // window start along x, mod P
     __builtin_assume(wm >= 0 && wm < P);
@@ -286,9 +304,9 @@ __global__ void __launch_bounds__(XpCfg<P>::NT, XpCfg<P>::MINB)
     // transformed back and the next multiplied
     if (k + 2 < K) {
       if constexpr (TMA) {
-        if (tid == 0) tma_load_3d(RS + b * kTile, &maps.m[k + 2], 2 * q0, 0, 0, &s_bar[b], kTileBytes);
+        if (tid == 0) tma_load_3d(b ? T1 : T0, &maps.m[k + 2], 2 * q0, 0, 0, &s_bar[b], kTileBytes);
       } else {
-        stage_receptor<P, NT>(RS + b * kTile, a.rhi[k + 2], Q, q0);
+        stage_receptor<P, NT>(b ? T1 : T0, a.rhi[k + 2], Q, q0);
       }
     }
     // inverse A', unit n1: inverse R-point DFT over k2 -> x[n1 + 8 n2]; the
