@@ -64,7 +64,7 @@ def kernel_src_sha(texts=None):
 # workload, averaged over one step's launches, from the ncu capture summarised
 # in profiles/xpass_fp32_protein_scale_traffic.md; valid only for the sources
 # it was taken with
-XPASS_TRAFFIC = {"bytes_per_launch": 2477.25e6, "launches_per_step": 8, "src_sha": "93fc00bfb0b03946"}
+XPASS_TRAFFIC = {"bytes_per_launch": 2476.94e6, "launches_per_step": 8, "src_sha": "769633cd97ee4089"}
 
 
 def xpass_src_sha():

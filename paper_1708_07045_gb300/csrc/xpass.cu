@@ -20,7 +20,8 @@
 // every shared access of a half-warp is 16 consecutive float2 (no bank
 // conflicts), and the index arithmetic is per unit, not per element.
 // Shared-memory round trips are kept to the one transpose each DFT needs:
-// stage A reads the ligand's rows from global memory into registers, stage B
+// stage A transforms the ligand's rows in place where one TMA box per CTA
+// left them in the forward buffer (or reads them from global memory), stage B
 // leaves the three channels' spectra at the half-warp's frequencies k2 + R k1
 // in its registers for every receptor, the spectral product is formed there
 // with the staged receptor tile inside the first inverse stage, and the last
