@@ -47,8 +47,10 @@ __host__ __device__ __forceinline__ int yz_zst(int S1) {
   return (two_l & 2) ? two_l : two_l + 2;
 }
 
+// CTAs per SM the registers are budgeted for: 4 where both edges are at most
+// 80 (whose shared memory, about 49 KB at a 40^2 site, fits four), else 3
 template <int A1, int R1, int A2, int R2>
-__global__ void __launch_bounds__(kYzNT, 3) k_yzinv(ZinvArgs a) {
+__global__ void __launch_bounds__(kYzNT, (A1 * R1 <= 80 && A2 * R2 <= 80) ? 4 : 3) k_yzinv(ZinvArgs a) {
   constexpr int P1 = A1 * R1, P2 = A2 * R2;
   static_assert(P1 % 2 == 0, "a plane is a 16-byte multiple (bulk prefetch)");
   constexpr int F2 = P2 / 2 + 1;
