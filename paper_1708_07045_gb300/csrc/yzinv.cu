@@ -47,10 +47,14 @@ __host__ __device__ __forceinline__ int yz_zst(int S1) {
   return (two_l & 2) ? two_l : two_l + 2;
 }
 
-// CTAs per SM the registers are budgeted for: 4 where both edges are at most
-// 80 (whose shared memory, about 49 KB at a 40^2 site, fits four), else 3
+// Shared memory of the edges (P1, P2) at a 40^2 site (the protein-scale one)
+constexpr int yz_smem_40(int P1, int P2) {
+  return 16 * (P1 + P2) + 8 * ((P1 * (P2 / 2 + 1) > P2 * 24 ? P1 * (P2 / 2 + 1) : P2 * 24) + (P2 / 2 + 1) * 42) + 6400;
+}
+// CTAs per SM the registers are budgeted for: 4 where that shared memory
+// fits four CTAs (56 KB each with the static part), else 3
 template <int A1, int R1, int A2, int R2>
-__global__ void __launch_bounds__(kYzNT, (A1 * R1 <= 80 && A2 * R2 <= 80) ? 4 : 3) k_yzinv(ZinvArgs a) {
+__global__ void __launch_bounds__(kYzNT, yz_smem_40(A1 * R1, A2 * R2) <= 57296 ? 4 : 3) k_yzinv(ZinvArgs a) {
   constexpr int P1 = A1 * R1, P2 = A2 * R2;
   static_assert(P1 % 2 == 0, "a plane is a 16-byte multiple (bulk prefetch)");
   constexpr int F2 = P2 / 2 + 1;
@@ -59,15 +63,14 @@ __global__ void __launch_bounds__(kYzNT, (A1 * R1 <= 80 && A2 * R2 <= 80) ? 4 : 
   const int L = (S1 + 1) / 2;          // row pairs: lines of the z transform
   const int NGz = (L + 7) / 8;         // the z stages' units are 8 lanes (a quarter warp): few lines
   const int WS = 8 * NGz;              // row stride of W
-  const int US = F2 > WS ? F2 : WS;
+  const int YW = P1 * F2 > P2 * WS ? P1 * F2 : P2 * WS;  // Y [P1][F2], then W [P2][WS]
   const int ZST = yz_zst(S1);
-  constexpr int PM = P1 > P2 ? P1 : P2;
   extern __shared__ float4 smem[];
   float4 *tw1 = smem;                                     // [P1] exp(-2 pi i k / P1)
   float4 *tw2 = tw1 + P1;                                 // [P2]
   cx<float> *Y = reinterpret_cast<cx<float> *>(tw2 + P2); // [P1][F2], then W [P2][WS]
   cx<float> *W = Y;
-  cx<float> *Zs = Y + PM * US;                            // [F2][ZST]
+  cx<float> *Zs = Y + YW;                                 // [F2][ZST]
   float *es = reinterpret_cast<float *>(Zs + F2 * ZST);   // [S1][S2]
   __shared__ float s_red[8];
   __shared__ float s_thr;
@@ -265,9 +268,10 @@ __global__ void __launch_bounds__(kYzNT, (A1 * R1 <= 80 && A2 * R2 <= 80) ? 4 : 
 
 template <int A1, int R1, int A2, int R2>
 size_t yzinv_smem_p(int S1, int S2) {
-  constexpr int P1 = A1 * R1, P2 = A2 * R2, F2 = P2 / 2 + 1, PM = P1 > P2 ? P1 : P2;
-  const int L = (S1 + 1) / 2, WS = 8 * ((L + 7) / 8), US = F2 > WS ? F2 : WS;
-  return sizeof(float4) * (P1 + P2) + sizeof(cx<float>) * ((size_t)PM * US + (size_t)F2 * yz_zst(S1)) +
+  constexpr int P1 = A1 * R1, P2 = A2 * R2, F2 = P2 / 2 + 1;
+  const int L = (S1 + 1) / 2, WS = 8 * ((L + 7) / 8);
+  const size_t YW = (size_t)std::max(P1 * F2, P2 * WS);
+  return sizeof(float4) * (P1 + P2) + sizeof(cx<float>) * (YW + (size_t)F2 * yz_zst(S1)) +
          sizeof(float) * (size_t)S1 * S2;
 }
 
