@@ -149,7 +149,10 @@ const char *bpmf_last_error(bpmf_ctx_t ctx);
  *  grids    [3][nx][ny][nz] float32, C order, terms in the order
  *           electrostatic, LJ-repulsive, LJ-attractive (the -2 of the
  *           attractive term and the Coulomb factor included).  Node (i,j,k)
- *           sits at origin + (i,j,k) h.  Host or device.
+ *           sits at origin + (i,j,k) h.  Host or device.  Host grids are
+ *           copied on a stream of the context's own (so the copy overlaps
+ *           the work already queued on `stream`, which waits for it) and
+ *           the call returns once that copy is done, not the transforms.
  *  h        grid spacing (> 0).
  *  origin   [3] position of node (0,0,0) (informational; energies depend on
  *           grid indices only).

@@ -135,6 +135,10 @@ struct bpmf_ctx {
   // concurrently (forked from and joined back into the caller's stream)
   static constexpr int kSide = 4;
   cudaStream_t side[kSide] = {};
+  // host-to-device copies of receptor grids given in host memory: on their
+  // own stream, so that they overlap the caller's queued work
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t copy_ev = nullptr;
   int side_next = 0;
   // device blocks of freed handles, by size, reused by later handles of the
   // same size (the free synchronises the device first, as cudaFree does)
@@ -1058,6 +1062,8 @@ void bpmf_destroy(bpmf_ctx_t c) {
   for (auto &kv : c->tw) cudaFree(kv.second);
   for (cudaStream_t &x : c->side)
     if (x) cudaStreamDestroy(x);
+  if (c->copy_st) cudaStreamDestroy(c->copy_st);
+  if (c->copy_ev) cudaEventDestroy(c->copy_ev);
   for (auto &kv : c->blocks) cudaFree(kv.second);
   if (c->tca) cudaFree(c->tca);
   if (c->tc05) cudaFree(const_cast<__nv_bfloat16 *>(c->tc05));
@@ -1355,7 +1361,30 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
     r->F2 = P[2] / 2 + 1;
     r->Q = (long long)P[1] * r->F2;
     const size_t vol = (size_t)nx * ny * nz;
-    DevIn g(grids, 3 * vol * sizeof(float), st);
+    // host grids: copied on the context's copy stream (not behind the work
+    // already queued on st), which st then waits for; the call returns once
+    // the copy is done, so the caller may reuse its buffer
+    struct HostIn {
+      const void *p = nullptr;
+      void *own = nullptr;
+      cudaStream_t st = nullptr;
+      ~HostIn() {
+        if (own) cudaFreeAsync(own, st);
+      }
+    } g;
+    g.st = st;
+    const bool host_grids = !is_device_ptr(grids);
+    if (host_grids) {
+      if (!c->copy_st) CK(cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
+      if (!c->copy_ev) CK(cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming));
+      CK(cudaMallocAsync(&g.own, 3 * vol * sizeof(float), c->copy_st));
+      CK(cudaMemcpyAsync(g.own, grids, 3 * vol * sizeof(float), cudaMemcpyHostToDevice, c->copy_st));
+      CK(cudaEventRecord(c->copy_ev, c->copy_st));
+      CK(cudaStreamWaitEvent(st, c->copy_ev, 0));
+      g.p = g.own;
+    } else {
+      g.p = grids;
+    }
     Carve cv;
     cv.add(&r->grid, 3 * vol * sizeof(float));
     cv.add(&r->sumsq, 3 * sizeof(float));
@@ -1383,7 +1412,7 @@ int bpmf_receptor_load(bpmf_ctx_t c, const float *grids, int nx, int ny, int nz,
       record_stage(r->yst[std::make_pair(P[1], P[2])], st);
       rx_split(c, ys.v, N[0], 0, N[0], P[0], r->Q, r->hi, r->lo, st);
     }
-    if (!is_device_ptr(grids)) CK(cudaStreamSynchronize(st));
+    if (host_grids) CK(cudaEventSynchronize(c->copy_ev));
   } catch (Fail f) {
     bpmf_receptor_free(r);
     return set_err(c, f.code, last_msg);
