@@ -64,7 +64,7 @@ def kernel_src_sha(texts=None):
 # workload, averaged over one step's launches, from the ncu capture summarised
 # in profiles/xpass_fp32_protein_scale_traffic.md; valid only for the sources
 # it was taken with
-XPASS_TRAFFIC = {"bytes_per_launch": 2476.94e6, "launches_per_step": 8, "src_sha": "769633cd97ee4089"}
+XPASS_TRAFFIC = {"bytes_per_launch": 2477.06e6, "launches_per_step": 8, "src_sha": "769633cd97ee4089"}
 
 
 def xpass_src_sha():
@@ -1071,7 +1071,7 @@ def run_ours(args):
                            "peak_note": "measured hbm_gbs (burst), MEASURED_PEAKS.json",
                            "launches": nl, "ms_per_launch": ms_tot / nl}
                     alu = {"kernel": name, "bound": "alu", "achieved": ach_f, "peak": peak_f, "unit": "TFLOP/s",
-                           "frac": ach_f / peak_f, "traffic": None,
+                           "frac": ach_f / peak_f, "traffic": traffic, "traffic_note": hbm["traffic_note"],
                            "peak_note": f"derived: {n_sm} SM x 128 FP32 lanes x 2 (FMA) x median SM clock",
                            "launches": nl, "ms_per_launch": ms_tot / nl}
                     roof, second = (hbm, alu) if hbm["frac"] >= alu["frac"] else (alu, hbm)
