@@ -561,9 +561,9 @@ int bpmf_profile_entry(bpmf_ctx_t ctx, int i, char *name, int name_len, double *
  * before any work is queued).
  * Runs on the current device and on `stream`.  Each call reads the ligand's
  * coordinate bounds back to the host and synchronises `stream` before
- * returning.  The first call on a device also does a one-time set-up: it
- * resolves the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture begins.  Every call shares the one array and
+ * returning, so no call can be captured into a CUDA graph.  The first call on
+ * a device also resolves the array's device address (cudaGetSymbolAddress).
+ * Every call shares the one array and
  * leaves its contents behind: calls whose GPU work overlaps (other threads,
  * other streams) race and must be serialised by the caller.
  * Errors: INVALID_ARG; SIZE_UNSUPPORTED when the grid or the ligand box needs
