@@ -172,3 +172,32 @@ def test_fp32_yz_inverse_on_composite_edges(pkg, shape):
     fin = np.isfinite(ref["logZ"])
     assert np.array_equal(out32["n_valid"], ref["n_valid"])
     assert np.abs(out32["logZ"][fin] - ref["logZ"][fin]).max() * KT <= 2 * bound
+
+
+def test_crops_from_kept_receptor_stages_match_fresh_receptors(pkg):
+    """Receptor crops are x passes of float-pair y stages the receptor keeps
+    per edge pair (made on first use, on side streams, ordered by events).
+    A ligand evaluated against receptors whose stages and crops another
+    ligand made first must give bit for bit the results of the same
+    evaluation against freshly loaded copies of the receptors, in the refined
+    and the float-pair forms; and the evaluation must use several crops."""
+    from paper_1708_07045_gb300.session import Session
+    w = synth.protein_scale(n_conf=1600, n_rec=2)
+    lig = w.ligands[0]
+    first = synth.LigandInput(lig.params, np.ascontiguousarray(lig.coords[:800]))
+    second = synth.LigandInput(lig.params, np.ascontiguousarray(lig.coords[800:]))
+    J = second.coords.shape[0]
+    for mode in (pkg.BPMF_MODE_REFINE, pkg.BPMF_MODE_FF):
+        with Session(0) as s:
+            kept = [s.load_receptor(r) for r in w.receptors]
+            lh1, _, _ = s.load_ligands([first])
+            s.eval(lh1, kept, KT, mode, n_lig=1, total_conf=first.coords.shape[0])
+            lh2, _, _ = s.load_ligands([second])
+            edges = pkg.bpmf_transform_edges(s.ctx, lh2, kept, J, mode)
+            classes = {tuple(e) for e in edges[:, 0, :]}
+            assert len(classes) >= 3, classes  # several crops (and the full edge) in play
+            _, reused = s.eval(lh2, kept, KT, mode, n_lig=1, total_conf=J)
+            fresh = [s.load_receptor(r) for r in w.receptors]
+            _, direct = s.eval(lh2, fresh, KT, mode, n_lig=1, total_conf=J)
+        for k in ("logZ", "n_valid", "bpmf", "dG"):
+            assert np.array_equal(reused[k], direct[k]), (mode, k)
