@@ -201,3 +201,28 @@ def test_crops_from_kept_receptor_stages_match_fresh_receptors(pkg):
             _, direct = s.eval(lh2, fresh, KT, mode, n_lig=1, total_conf=J)
         for k in ("logZ", "n_valid", "bpmf", "dG"):
             assert np.array_equal(reused[k], direct[k]), (mode, k)
+
+
+def test_receptors_from_host_and_device_grids_agree(pkg):
+    """bpmf_receptor_load copies host grids on the context's copy stream (the
+    caller's stream waits for the copy; the call returns once it is done).
+    Two host-memory loads queued back to back, and the same grids given as
+    device memory, give the same results bit for bit; the host buffers may be
+    overwritten as soon as each load returns."""
+    torch = pytest.importorskip("torch")
+    from paper_1708_07045_gb300.session import Session
+    w = synth.protein_scale(n_conf=64, n_rec=2)
+    lig = w.ligands[0]
+    with Session(0) as s:
+        host = []
+        for r in w.receptors:
+            buf = np.array(r.grids, dtype=np.float32, copy=True)
+            host.append(s.load_receptor(r, grids=buf))
+            buf[...] = np.nan  # the load has returned: the buffer is free again
+        dev = [s.load_receptor(r, grids=torch.from_numpy(r.grids).cuda()) for r in w.receptors]
+        lh, _, _ = s.load_ligands([lig])
+        _, a = s.eval(lh, host, KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=64)
+        _, b = s.eval(lh, dev, KT, pkg.BPMF_MODE_REFINE, n_lig=1, total_conf=64)
+    for k in ("logZ", "n_valid", "bpmf", "dG"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.all(np.isfinite(a["bpmf"]))
